@@ -1,0 +1,328 @@
+"""Benchmark: energy + adjoint-gradient (+ 1-RDM) evaluations per second at 30 qubits.
+
+One step = one pass of the whole hot path over one synthetic problem: prepare the
+Jordan-Wigner HF reference, apply the 200-operator ADAPT-style ansatz, evaluate
+E = <psi|H|psi> and lambda = (H - c) psi, run the adjoint sweep for dE/dtheta,
+restore psi(theta) and take the spin-resolved 1-RDM.  Workload: 30 qubits
+(15 spatial orbitals, 10 electrons), seeded synthetic integrals shaped like the
+paper's molecules (config 5 of the workload list).  The complex64-state path
+(float64 reductions) is the headline; the complex128 path is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica (the path does not shard in this build: "replicas only"); value is the
+evaluations of all ranks divided by the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "energy+adjoint-grad evals/s at 30 qubits, FP32-state vs FP64; % of HBM peak"
+UNIT = "evals/s"
+CONFIG_ID = 5
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def touched_bytes(ops, n, amp_bytes):
+    """Algorithmic bytes of one rotation per op: read + write of the 2 * 2^(n - nbits) touched amplitudes."""
+    nbits = np.where(np.asarray(ops)[:, 0] == 1, 2, 4)
+    return (4.0 * (2.0 ** (n - nbits)) * amp_bytes)
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
+
+def oracle_eval_sample(p, sector=None, sigma_rows=6000, ops_sample=4):
+    """Time the CPU oracle on a bounded sample of one evaluation and scale to a full one.
+
+    Sample: `ops_sample` rotations and generator applications over the full sector,
+    sigma = H psi on `sigma_rows` evenly spaced determinants (scaled by D / rows),
+    the full 1-RDM.  One evaluation = L forward rotations + sigma + L reverse
+    steps (two rotations and one generator application each) + 1-RDM.
+    """
+    import oracle
+    from oracle import route_a as A
+    sec = sector or oracle.Sector(p["n_qubits"], p["na"], p["nb"])
+    psi = A.hf_state(sec, p["occ"])
+    ops, theta, L = p["ops"], p["theta"], len(p["ops"])
+    t0 = time.perf_counter()
+    for k in range(ops_sample):
+        psi = A.rotate(sec, ops[k], theta[k], psi)
+    t_rot = (time.perf_counter() - t0) / ops_sample
+    t0 = time.perf_counter()
+    for k in range(ops_sample):
+        A.generator_apply(sec, ops[k], psi)
+    t_gen = (time.perf_counter() - t0) / ops_sample
+    rows = np.linspace(0, sec.D - 1, min(sigma_rows, sec.D)).astype(np.int64)
+    t0 = time.perf_counter()
+    A.hamiltonian_apply(sec, p["h"], p["eri"], p["e_nuc"], psi, rows=rows)
+    t_sig = (time.perf_counter() - t0) * sec.D / len(rows)
+    t0 = time.perf_counter()
+    A.rdm1(sec, psi)
+    t_rdm = time.perf_counter() - t0
+    t_eval = L * t_rot + t_sig + L * (2 * t_rot + t_gen) + t_rdm
+    sample = ("%d of %d rotations and generator applications over the full %d-determinant sector, "
+              "H psi on %d of %d determinants (scaled), full 1-RDM; scaled to one eval"
+              % (ops_sample, L, sec.D, len(rows), sec.D))
+    return 1.0 / t_eval, sample, sec
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2405_11567_gb300 import inputs
+    import oracle
+    p = inputs.config_problem(CONFIG_ID)
+    sec = None
+    for _ in range(args.warmup):
+        _, _, sec = oracle_eval_sample(p, sec, sigma_rows=1500, ops_sample=1)
+    vals = []
+    sample = ""
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, sample, sec = oracle_eval_sample(p, sec)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = float(statistics.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(p),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample, "wall_s": wall},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(p):
+    return {"workload": "n30_ne10_adapt200_synthetic", "n_qubits": p["n_qubits"], "n_electrons": p["n_elec"],
+            "n_ops": int(len(p["ops"])), "seed": p["seed"],
+            "step": "prepare_hf + energy_grad (forward, sigma, adjoint) + rdm1",
+            "l2": "inputs larger than L2 (state vector 8 GiB complex64 / 16 GiB complex128)"}
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2405_11567_gb300 import build as libbuild
+    from paper_2405_11567_gb300 import inputs, sv
+
+    libbuild.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    p = inputs.config_problem(CONFIG_ID)
+    n, L = p["n_qubits"], len(p["ops"])
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    stream = torch.cuda.Stream()
+    peak, peak_kind = measured_peaks()
+
+    def timed(dtype):
+        st = sv.StateVector(n, dtype, stream)
+        st.set_option(sv.SV_OPT_PROFILE, 1)
+        outs = {}
+
+        def step():
+            st.prepare_hf(p["occ"])
+            E, g = st.energy_grad(ham, p["ops"], p["theta"])
+            rdm = st.rdm1()
+            outs["E"], outs["g"], outs["rdm"] = E, g, rdm
+            return st.phase_times()
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        launches0 = st.launches
+        phases = []
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            phases.append(step())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_host = time.perf_counter() - t0
+        ms = ev0.elapsed_time(ev1)
+        launches = st.launches - launches0
+        clk = clocks.stop()
+        if dist:
+            t = torch.tensor([ms, t_host], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms, t_host = float(t[0]), float(t[1])
+        avg = {k: statistics.mean(ph[k] for ph in phases) for k in phases[0]}
+        st.close()
+        return dict(ms=ms, t_host=t_host, phases=avg, clocks=clk, launches=launches, out=outs)
+
+    r64 = timed("c64")
+    r128 = None if args.no_c128 else timed("c128")
+    if rank != 0:
+        return 0
+    K = args.steps
+    value = world * K / (r64["ms"] / 1000.0)
+    e2e = world * K / r64["t_host"]
+    # roofline of the dominant kernel (by phase time), algorithmic bytes per launch / mean launch time
+    amp = 8
+    rot_bytes = touched_bytes(p["ops"], n, amp)
+    kernels = {
+        "adjoint_step": dict(phase="reverse", launches=L, bytes=2.0 * rot_bytes.sum(),
+                             desc="fused adjoint step (k_adjoint): psi and lambda pairs, read + write"),
+        "rotation": dict(phase="forward", launches=L, bytes=rot_bytes.sum(),
+                         desc="excitation rotation (k_rotate): touched pairs, read + write"),
+    }
+    rows = {}
+    for name, kd in kernels.items():
+        t_launch = r64["phases"][kd["phase"]] / kd["launches"] / 1000.0
+        per_launch = kd["bytes"] / kd["launches"]
+        ach = per_launch / t_launch / 1e9
+        rows[name] = {"achieved_gbs": ach, "frac": ach / peak, "mean_launch_ms": t_launch * 1e3,
+                      "bytes_per_launch": per_launch, "launches_per_step": kd["launches"]}
+    dom = max(kernels, key=lambda k: r64["phases"][kernels[k]["phase"]])
+    roof = {"bound": "hbm", "kernel": dom, "achieved": rows[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": rows[dom]["frac"], "traffic": None, "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
+            if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": r64["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "precision": "complex64 state, float64 reductions", "data": "synthetic",
+        "config": workload_config(p),
+        "roofline": roof,
+        "kernels": rows,
+        "phases_ms": r64["phases"],
+        "clocks": r64["clocks"],
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(L * (20 + 8) + len(p["occ"]) * 4),
+                "d2h_bytes_per_step": int((1 + L) * 8 + 2 * 2 * p["n_orb"] ** 2 * 8)},
+        "gpu_launches": int(r64["launches"]),
+    }
+    if r128 is not None:
+        v128 = world * K / (r128["ms"] / 1000.0)
+        line["fp64_state"] = {"value": v128, "ms_per_step": r128["ms"] / K, "phases_ms": r128["phases"],
+                              "clocks": r128["clocks"]}
+        line["speedup_fp32_over_fp64"] = value / v128
+        line["fp32_vs_fp64"] = {
+            "abs_dE": abs(r64["out"]["E"] - r128["out"]["E"]),
+            "max_abs_dg": float(np.max(np.abs(r64["out"]["g"] - r128["out"]["g"]))),
+            "max_abs_drdm": float(np.max(np.abs(r64["out"]["rdm"] - r128["out"]["rdm"]))),
+            "E_fp64": r128["out"]["E"]}
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        v, sample, _ = oracle_eval_sample(p)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-c128", action="store_true", help="skip the complex128 comparison run")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend="nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * sv.h -- C-ABI of the GB300 (sm_103a) state-vector library for the hot path
+ * of arXiv:2405.11567: the emulator that stands in for the QPU (Fig. 1;
+ * Methodology, "GPU-accelerated QPU emulation").  It prepares the
+ * Jordan-Wigner Hartree-Fock reference, applies a fermionic-excitation
+ * (UCCSD / ADAPT-VQE) ansatz, and returns the energy <psi|H|psi> of the
+ * second-quantised Hamiltonian, its exact gradient with respect to the ansatz
+ * angles, and the spin-resolved one-particle density matrix n_{pq,sigma}.
+ *
+ * Conventions (fixed by this library where the paper is silent):
+ *   - qubit j = spin-orbital j = 2p + sigma (sigma 0 = alpha, 1 = beta);
+ *     bit j of a basis index x is the occupation of spin-orbital j.
+ *   - Jordan-Wigner: a_j^(+) on |x> carries (-1)^(number of occupied
+ *     spin-orbitals with index < j) (Methodology, Strategy 2: the
+ *     Jordan-Wigner mapping used for n_{pq,sigma}).
+ *   - excitation: single T = a+_a a_i; double T = a+_a a+_b a_j a_i with
+ *     i < j and a < b; U = exp(theta (T - T^dagger)); the ansatz is
+ *     U_L ... U_1 |ref>, ops[0] acting first ("Computational Details":
+ *     ADAPT-VQE with an operator pool).
+ *   - Hamiltonian (FCIDUMP chemist notation, "Computational Details"):
+ *     H = E_nuc + sum h_pq a+_{p s} a_{q s}
+ *               + 1/2 sum (pq|rs) a+_{p s} a+_{r t} a_{s t} a_{q s}.
+ *   - E = <psi|H|psi> / <psi|psi>; dE/dtheta_k in Hartree per radian.
+ *
+ * State storage: one dense vector of 2^n complex amplitudes in device memory,
+ * interleaved (re, im), complex64 (SV_C64, float) or complex128 (SV_C128,
+ * double), index = basis index x.  Every reduction (energy, gradient, norm,
+ * density matrix) is accumulated and returned in float64 whatever the state
+ * precision.
+ *
+ * Ownership: the caller owns every host array passed in and out; the library
+ * copies what it keeps.  Device buffers are owned by the library unless they
+ * are passed to sv_create_with_buffers, in which case the caller owns them and
+ * must keep them alive until sv_destroy.
+ *
+ * Errors: every call returns an sv_status; nothing aborts or throws across
+ * this boundary.  SV_ERR_ARG = invalid argument (nothing was changed on the
+ * device); SV_ERR_OOM = a device allocation failed; SV_ERR_CUDA = a CUDA call
+ * failed (the handle becomes unusable: SV_ERR_STATE on later calls until
+ * sv_prepare_hf / sv_prepare_state succeeds); SV_ERR_TIMEOUT = a bounded
+ * device-side wait expired (batched launch only); SV_ERR_STATE = the call
+ * needs a prepared state and there is none.  sv_last_error() returns a
+ * message for the last failing call on a handle (or, with NULL, on this
+ * thread).
+ *
+ * Streams: all device work of a handle is ordered on the stream given at
+ * creation (NULL = the legacy default stream).  Calls that return host values
+ * synchronise that stream before returning.
+ */
+#ifndef SV_GB300_H
+#define SV_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sv_ctx *sv_handle;
+typedef struct sv_ham *sv_ham_handle;
+
+typedef enum {
+    SV_OK = 0,
+    SV_ERR_ARG = 1,
+    SV_ERR_OOM = 2,
+    SV_ERR_CUDA = 3,
+    SV_ERR_TIMEOUT = 4,
+    SV_ERR_STATE = 5
+} sv_status;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
+
+/* One excitation operator.  kind 1: single, occ[0] -> vir[0] (occ[1], vir[1]
+ * ignored); kind 2: double, occ[0] < occ[1], vir[0] < vir[1].  Indices are
+ * spin-orbitals in [0, n_qubits); the four (two) indices are distinct and the
+ * operator conserves S_z (same number of alpha spin-orbitals among occ and
+ * vir).  Anything else is SV_ERR_ARG. */
+typedef struct {
+    int32_t kind;
+    int32_t occ[2];
+    int32_t vir[2];
+} sv_excitation;
+
+/* Largest qubit count accepted (basis indices fit in 32 bits). */
+#define SV_MAX_QUBITS 32
+
+/* ---- state handles ------------------------------------------------------ */
+
+/* Create a handle for an n_qubits state (2 <= n_qubits <= SV_MAX_QUBITS, even)
+ * in precision dtype on the current CUDA device, ordered on cuda_stream
+ * (a cudaStream_t, may be NULL).  Allocates the state vector (2^n amplitudes);
+ * further buffers (the adjoint vector, checkpoints, reduction scratch) are
+ * allocated on first use.  The state is unprepared until sv_prepare_hf or
+ * sv_prepare_state.  Paper: the emulator's state vector (Fig. 1;
+ * "Computational Details": state-vector emulation up to 32 qubits). */
+sv_status sv_create(int n_qubits, sv_dtype dtype, void *cuda_stream, sv_handle *out);
+
+/* As sv_create, but the state vector and the adjoint vector live in caller-owned
+ * device buffers of 2^n amplitudes each (psi_dev required, lam_dev may be NULL:
+ * then the library allocates it on first use).  Lets a caller allocate with its
+ * own allocator (e.g. PyTorch's).  Both must be 256-byte aligned. */
+sv_status sv_create_with_buffers(int n_qubits, sv_dtype dtype, void *cuda_stream,
+                                 void *psi_dev, void *lam_dev, sv_handle *out);
+
+/* Release the handle and every device buffer it owns.  NULL is accepted. */
+sv_status sv_destroy(sv_handle h);
+
+/* Prepare the Hartree-Fock reference |x_HF>: the spin-orbitals listed in occ
+ * (n_occ distinct indices in [0, n), any order) are occupied, all others
+ * empty ("Computational Details": computations start from a HF state).  The
+ * handle records this reference for sv_energy_grad. */
+sv_status sv_prepare_hf(sv_handle h, const int32_t *occ, int n_occ);
+
+/* Prepare an arbitrary initial state from host memory: 2^n amplitudes of the
+ * handle's dtype (interleaved re, im), which must vanish (exactly) outside the
+ * sector with n_alpha alpha and n_beta beta electrons (SV_ERR_ARG otherwise).
+ * The handle keeps a device copy as the reference for sv_energy_grad (a
+ * multi-determinant start such as the CIPSI states of "Computational
+ * Details"). */
+sv_status sv_prepare_state(sv_handle h, const void *amplitudes_host, int n_alpha, int n_beta);
+
+/* Copy the current state (2^n amplitudes, dtype of the handle) to host memory. */
+sv_status sv_get_state(sv_handle h, void *amplitudes_host);
+
+/* Device pointer of the state vector (2^n amplitudes), for callers that read
+ * it on the GPU.  Valid until sv_destroy. */
+sv_status sv_state_device_ptr(sv_handle h, void **psi_dev);
+
+/* ---- Hamiltonian handles -------------------------------------------------- */
+
+/* Build a Hamiltonian from integrals in the FCIDUMP chemist convention
+ * ("Computational Details"): h[p*n_orb+q] (symmetric), eri[((p*n_orb+q)*n_orb+r)*n_orb+s]
+ * = (pq|rs) with the 8-fold symmetry of real orbitals (checked to 1e-12,
+ * SV_ERR_ARG otherwise), e_nuc.  1 <= n_orb <= SV_MAX_QUBITS/2.  The X-mask
+ * tables (every group of Pauli strings sharing a flip pattern, evaluated in
+ * closed form) and the tile schedule are built lazily per state size and
+ * cached in the handle. */
+sv_status sv_ham_create(int n_orb, const double *h, const double *eri, double e_nuc,
+                        sv_ham_handle *out);
+sv_status sv_ham_destroy(sv_ham_handle ham);
+
+/* ---- the hot path ---------------------------------------------------------- */
+
+/* psi <- U_L ... U_1 psi with U_k = exp(theta[k] (T_k - T_k^dagger)), ops[0] first.
+ * cos/sin of theta are taken on the host in float64.  One kernel per operator. */
+sv_status sv_apply_ansatz(sv_handle h, const sv_excitation *ops, int n_ops, const double *theta);
+
+/* *e_out = <psi|H|psi> / <psi|psi> of the current state (Fig. 1: the QPU/GPU
+ * returns <H>; FCI energy functional of Methodology).  n_orb of the
+ * Hamiltonian must equal n_qubits / 2. */
+sv_status sv_energy(sv_handle h, sv_ham_handle ham, double *e_out);
+
+/* Energy and exact gradient of E(theta) for psi(theta) = U_L..U_1 |ref>, where
+ * |ref> is the reference recorded by the last sv_prepare_hf / sv_prepare_state.
+ * grad_out[k] = dE/dtheta_k (n_ops values).  Adjoint method: one forward sweep,
+ * lambda = (H - c) psi, one reverse sweep that uncomputes psi and lambda gate by
+ * gate (the constant c does not change the gradient of a unitary ansatz).  On
+ * return the handle holds psi(theta).  Either output may be NULL. */
+sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *ops, int n_ops,
+                         const double *theta, double *e_out, double *grad_out);
+
+/* Spin-resolved one-particle density matrix of the current state,
+ * n_{pq,sigma} = <psi|a+_{p sigma} a_{q sigma}|psi> / <psi|psi> (Methodology,
+ * Strategy 2, equation for n_{pq,sigma}).  re_out[(sigma*N + p)*N + q] = Re n,
+ * im_out likewise Im n (im_out may be NULL), N = n_qubits/2, sigma 0 = alpha. */
+sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out);
+
+/* ---- options ------------------------------------------------------------------ */
+
+typedef enum {
+    SV_OPT_CHECKPOINT_INTERVAL = 1, /* store psi every C gates in the forward sweep of
+                                       sv_energy_grad and restore it in the reverse sweep
+                                       (0 = none; default 0) */
+    SV_OPT_MAX_BYTES = 2,           /* cap on device bytes this handle may allocate
+                                       (0 = no cap); checkpoints are dropped to fit */
+    SV_OPT_EXPECT_VARIANT = 3,      /* 0 auto, 1 sector gather, 2 tiled passes */
+    SV_OPT_RDM_VARIANT = 4,         /* 0 auto, 1 sector gather, 2 tiled passes */
+    SV_OPT_PROFILE = 5              /* 1: record CUDA events around each phase (sv_phase_times) */
+} sv_option;
+
+sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value);
+
+/* ---- introspection ------------------------------------------------------------ */
+
+/* Number of phases reported by sv_phase_times. */
+#define SV_PHASES 6
+
+/* Device time (ms) of each phase of the last sv_energy_grad / sv_rdm1 call,
+ * measured with CUDA events on the handle's stream while SV_OPT_PROFILE is 1:
+ * [0] reference preparation, [1] forward sweep (one rotation kernel per op),
+ * [2] expectation (sigma and energy), [3] reverse sweep (one adjoint kernel per
+ * op plus the gradient reduction), [4] restoring psi(theta), [5] the last
+ * sv_rdm1.  Writes min(n_out, SV_PHASES) values; phases not run are 0. */
+sv_status sv_phase_times(sv_handle h, double *ms_out, int n_out);
+
+/* Message of the last failing call on h (h == NULL: on this thread). Never NULL. */
+const char *sv_last_error(sv_handle h);
+
+/* Number of kernels this handle has launched since creation. */
+uint64_t sv_launch_count(sv_handle h);
+
+/* Library version string. */
+const char *sv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SV_GB300_H */

@@ -1,0 +1,739 @@
+// sv_api.cu -- the C-ABI entry points declared in include/sv.h.
+//
+// Host orchestration only: argument validation (every check runs before any
+// device work, so SV_ERR_ARG leaves the device untouched), buffer management,
+// and the order of kernel launches on the handle's stream.  Every step of the
+// path itself runs in the kernels of k_state.cu, k_expect.cu, k_tiles.cu and
+// k_rdm.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sv_internal.h"
+
+namespace svk {
+int rotate_grid(uint64_t npairs, int sm_count);
+cudaError_t launch_set_basis(void *psi, int dtype, uint32_t x, cudaStream_t st);
+cudaError_t launch_rotate(void *psi, int dtype, int n, const OpDesc &d, int sm_count, cudaStream_t st);
+cudaError_t launch_adjoint(void *psi, void *lam, int dtype, int n, const OpDesc &d, int grid,
+                           double *partial, cudaStream_t st);
+cudaError_t launch_reduce_rows(const double *partials, int rows, int cols, double *out, cudaStream_t st);
+int expect_gather_grid(uint64_t count, int sm_count);
+cudaError_t launch_expect_gather(const void *psi, void *sigma, int dtype, int n, const uint32_t *sector,
+                                 uint64_t count, const DevTables &T, double e_shift, int grid,
+                                 double *partial, cudaStream_t st);
+int rdm_gather_grid(uint64_t count, int sm_count);
+int rdm_elements_bytes(int n, std::vector<uint8_t> &out);
+cudaError_t launch_rdm_gather(const void *psi, int dtype, const uint32_t *sector, uint64_t count,
+                              const void *elems, int n_el, int grid, double *partial, cudaStream_t st);
+
+DevTables::~DevTables() {
+    void *ptrs[] = {dbl, sgl, W, hdiag, Jp, pass_dbl, pass_sgl, pass_W};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+}  // namespace svk
+
+using namespace svk;
+
+// ---------------------------------------------------------------- errors
+
+static thread_local std::string g_err = "no error";
+
+static sv_status fail(sv_handle h, sv_status st, const std::string &msg) {
+    g_err = msg;
+    if (h) {
+        h->err = msg;
+        if (st == SV_ERR_CUDA) h->failed = true;
+    }
+    return st;
+}
+
+#define SV_CUDA(h, call)                                                                          \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            cudaGetLastError();                                                                   \
+            return fail((h), SV_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+        }                                                                                         \
+    } while (0)
+
+#define SV_TRY(expr)                       \
+    do {                                   \
+        sv_status s_ = (expr);             \
+        if (s_ != SV_OK) return s_;        \
+    } while (0)
+
+// Makes the handle's device current for the duration of a call and restores the
+// caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------- buffers
+
+static sv_status dev_alloc(sv_handle h, void **p, size_t bytes, const char *what) {
+    *p = nullptr;
+    if (h->max_bytes > 0 && h->bytes_owned + bytes > (uint64_t)h->max_bytes)
+        return fail(h, SV_ERR_OOM, std::string("device byte cap reached allocating ") + what);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(h, SV_ERR_OOM, std::string("cudaMalloc failed for ") + what + ": " + cudaGetErrorString(e));
+    }
+    h->bytes_owned += bytes;
+    return SV_OK;
+}
+
+static void dev_free(sv_handle h, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    h->bytes_owned -= std::min<uint64_t>(h->bytes_owned, bytes);
+}
+
+static size_t vec_bytes(sv_handle h) { return (size_t)h->dim * h->amp_bytes; }
+
+static sv_status ensure_lam(sv_handle h) {
+    if (h->lam) return SV_OK;
+    SV_TRY(dev_alloc(h, &h->lam, vec_bytes(h), "adjoint vector"));
+    h->own_lam = true;
+    return SV_OK;
+}
+
+static sv_status ensure_partials(sv_handle h, size_t doubles) {
+    if (h->partials_cap >= doubles) return SV_OK;
+    if (h->partials) dev_free(h, h->partials, h->partials_cap * sizeof(double));
+    h->partials = nullptr;
+    h->partials_cap = 0;
+    void *p;
+    SV_TRY(dev_alloc(h, &p, doubles * sizeof(double), "reduction scratch"));
+    h->partials = (double *)p;
+    h->partials_cap = doubles;
+    return SV_OK;
+}
+
+static sv_status ensure_out(sv_handle h, size_t doubles) {
+    if (h->dout_cap < doubles) {
+        if (h->dout) dev_free(h, h->dout, h->dout_cap * sizeof(double));
+        h->dout = nullptr;
+        h->dout_cap = 0;
+        void *p;
+        SV_TRY(dev_alloc(h, &p, doubles * sizeof(double), "device outputs"));
+        h->dout = (double *)p;
+        h->dout_cap = doubles;
+    }
+    if (h->hpinned_cap < doubles) {
+        if (h->hpinned) cudaFreeHost(h->hpinned);
+        h->hpinned = nullptr;
+        h->hpinned_cap = 0;
+        void *p = nullptr;
+        cudaError_t e = cudaMallocHost(&p, doubles * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, SV_ERR_OOM, "pinned host staging allocation failed");
+        }
+        h->hpinned = (double *)p;
+        h->hpinned_cap = doubles;
+    }
+    return SV_OK;
+}
+
+// Phase events: record event i on the handle's stream when profiling.
+static sv_status mark(sv_handle h, int i) {
+    if (!h->profile) return SV_OK;
+    if (!h->ev[i]) SV_CUDA(h, cudaEventCreate(&h->ev[i]));
+    SV_CUDA(h, cudaEventRecord(h->ev[i], h->stream));
+    return SV_OK;
+}
+
+static float elapsed(sv_handle h, int a, int b) {
+    float ms = 0.f;
+    if (h->ev[a] && h->ev[b] && cudaEventElapsedTime(&ms, h->ev[a], h->ev[b]) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 0.f;
+    }
+    return ms;
+}
+
+// Basis indices of the (na, nb) sector in ascending order, on the device.
+static sv_status ensure_sector(sv_handle h) {
+    if (h->sector && h->sector_na == h->na && h->sector_nb == h->nb) return SV_OK;
+    if (h->sector) dev_free(h, h->sector, h->sector_len * sizeof(uint32_t));
+    h->sector = nullptr;
+    const int N = h->n / 2;
+    std::vector<uint32_t> sa, sb;
+    for (uint32_t s = 0; s < (1u << N); ++s) {
+        int c = __builtin_popcount(s);
+        if (c == h->na) sa.push_back(s);
+        if (c == h->nb) sb.push_back(s);
+    }
+    auto spread = [&](uint32_t s, int off) {
+        uint32_t x = 0;
+        for (int p = 0; p < N; ++p)
+            if ((s >> p) & 1u) x |= 1u << (2 * p + off);
+        return x;
+    };
+    std::vector<uint32_t> ea(sa.size()), eb(sb.size());
+    for (size_t i = 0; i < sa.size(); ++i) ea[i] = spread(sa[i], 0);
+    for (size_t i = 0; i < sb.size(); ++i) eb[i] = spread(sb[i], 1);
+    std::vector<uint32_t> list;
+    list.reserve(ea.size() * eb.size());
+    for (uint32_t a : ea)
+        for (uint32_t b : eb) list.push_back(a | b);
+    std::sort(list.begin(), list.end());
+    void *p;
+    SV_TRY(dev_alloc(h, &p, std::max<size_t>(1, list.size()) * sizeof(uint32_t), "sector list"));
+    h->sector = (uint32_t *)p;
+    h->sector_len = list.size();
+    h->sector_na = h->na;
+    h->sector_nb = h->nb;
+    if (!list.empty())
+        SV_CUDA(h, cudaMemcpyAsync(h->sector, list.data(), list.size() * sizeof(uint32_t),
+                                   cudaMemcpyHostToDevice, h->stream));
+    SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SV_OK;
+}
+
+// ---------------------------------------------------------------- Hamiltonian tables
+
+template <typename R>
+static sv_status upload_tables(sv_handle h, sv_ham_handle ham, DevTables &T) {
+    HostTables<R> ht;
+    build_tables<R>(*ham, h->n, ht);
+    T.n_dbl = (int)ht.dbl.size();
+    T.n_sgl = (int)ht.sgl.size();
+    auto up = [&](void **dst, const void *src, size_t bytes) -> sv_status {
+        cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *dst = nullptr;
+            return fail(h, SV_ERR_OOM, "Hamiltonian table allocation failed");
+        }
+        if (bytes) SV_CUDA(h, cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+        return SV_OK;
+    };
+    SV_TRY(up(&T.dbl, ht.dbl.data(), ht.dbl.size() * sizeof(DoubleRec<R>)));
+    SV_TRY(up(&T.sgl, ht.sgl.data(), ht.sgl.size() * sizeof(SingleRec<R>)));
+    SV_TRY(up(&T.W, ht.W.data(), ht.W.size() * sizeof(R)));
+    SV_TRY(up((void **)&T.hdiag, ht.hdiag.data(), ht.hdiag.size() * sizeof(double)));
+    SV_TRY(up((void **)&T.Jp, ht.Jp.data(), ht.Jp.size() * sizeof(double)));
+    return SV_OK;
+}
+
+static sv_status get_tables(sv_handle h, sv_ham_handle ham, DevTables **out) {
+    int key = h->device * 1000 + h->n * 2 + (int)h->dtype;
+    auto it = ham->dev.find(key);
+    if (it != ham->dev.end()) {
+        *out = it->second.get();
+        return SV_OK;
+    }
+    std::unique_ptr<DevTables> T(new DevTables());
+    T->n = h->n;
+    T->dtype = h->dtype;
+    if (h->dtype == SV_C64) SV_TRY(upload_tables<float>(h, ham, *T));
+    else SV_TRY(upload_tables<double>(h, ham, *T));
+    *out = T.get();
+    ham->dev[key] = std::move(T);
+    return SV_OK;
+}
+
+// ---------------------------------------------------------------- validation helpers
+
+static sv_status check_ready(sv_handle h) {
+    if (!h) return fail(nullptr, SV_ERR_ARG, "NULL handle");
+    if (h->failed) return fail(h, SV_ERR_STATE, "handle failed earlier; prepare a state again");
+    if (!h->prepared) return fail(h, SV_ERR_STATE, "no prepared state (call sv_prepare_hf or sv_prepare_state)");
+    return SV_OK;
+}
+
+static sv_status build_ops(sv_handle h, const sv_excitation *ops, int n_ops, const double *theta,
+                           std::vector<OpDesc> &out) {
+    if (n_ops < 0) return fail(h, SV_ERR_ARG, "n_ops < 0");
+    if (n_ops > 0 && (!ops || !theta)) return fail(h, SV_ERR_ARG, "NULL ops or theta");
+    out.resize(n_ops);
+    for (int k = 0; k < n_ops; ++k) {
+        std::string why;
+        if (!make_op(ops[k], h->n, out[k], why)) {
+            char buf[64];
+            snprintf(buf, sizeof buf, "op %d: ", k);
+            return fail(h, SV_ERR_ARG, buf + why);
+        }
+        if (!std::isfinite(theta[k])) return fail(h, SV_ERR_ARG, "non-finite theta");
+        out[k].c = std::cos(theta[k]);
+        out[k].s = std::sin(theta[k]);
+    }
+    return SV_OK;
+}
+
+static sv_status check_ham(sv_handle h, sv_ham_handle ham) {
+    if (!ham) return fail(h, SV_ERR_ARG, "NULL Hamiltonian handle");
+    if (ham->n_orb * 2 != h->n) return fail(h, SV_ERR_ARG, "Hamiltonian has n_orb != n_qubits / 2");
+    return SV_OK;
+}
+
+// ---------------------------------------------------------------- internal steps
+
+static sv_status prepare_reference(sv_handle h) {
+    if (h->ref_kind == 1) {
+        SV_CUDA(h, cudaMemsetAsync(h->psi, 0, vec_bytes(h), h->stream));
+        SV_CUDA(h, launch_set_basis(h->psi, h->dtype, h->ref_det, h->stream));
+        h->launches++;
+    } else if (h->ref_kind == 2) {
+        SV_CUDA(h, cudaMemcpyAsync(h->psi, h->ref_vec, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+        return fail(h, SV_ERR_STATE, "no reference state recorded");
+    }
+    return SV_OK;
+}
+
+static sv_status forward(sv_handle h, const std::vector<OpDesc> &ops, bool checkpoints) {
+    const int64_t C = h->ckpt_interval;
+    for (size_t k = 0; k < ops.size(); ++k) {
+        SV_CUDA(h, launch_rotate(h->psi, h->dtype, h->n, ops[k], h->sm_count, h->stream));
+        h->launches++;
+        if (checkpoints && C > 0 && (k + 1) % (size_t)C == 0 && k + 1 < ops.size()) {
+            size_t j = (k + 1) / (size_t)C - 1;
+            if (j < h->ckpt.size() && h->ckpt[j])
+                SV_CUDA(h, cudaMemcpyAsync(h->ckpt[j], h->psi, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+        }
+    }
+    return SV_OK;
+}
+
+// Checkpoint slots for an ansatz of L gates (as many as the byte cap allows).
+static void plan_checkpoints(sv_handle h, size_t L) {
+    size_t want = 0;
+    if (h->ckpt_interval > 0 && L > 1) want = (L - 1) / (size_t)h->ckpt_interval;
+    while (h->ckpt.size() > want) {
+        dev_free(h, h->ckpt.back(), vec_bytes(h));
+        h->ckpt.pop_back();
+    }
+    while (h->ckpt.size() < want) {
+        void *p = nullptr;
+        if (dev_alloc(h, &p, vec_bytes(h), "checkpoint") != SV_OK) {
+            cudaGetLastError();
+            break;  // fewer checkpoints: the reverse sweep uncomputes instead
+        }
+        h->ckpt.push_back(p);
+    }
+}
+
+// Expectation pass over the current state: writes the float64 sums of
+// <psi|(H - c)|psi> and <psi|psi> into dout[out_off], dout[out_off + 1] (device),
+// and sigma = (H - c) psi into `sigma` when it is not NULL.
+static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void *sigma, double c, int out_off) {
+    SV_TRY(ensure_sector(h));
+    int grid = expect_gather_grid(h->sector_len, h->sm_count);
+    SV_TRY(ensure_partials(h, 2 * (size_t)grid));
+    if (sigma) SV_CUDA(h, cudaMemsetAsync(sigma, 0, vec_bytes(h), h->stream));
+    SV_CUDA(h, launch_expect_gather(h->psi, sigma, h->dtype, h->n, h->sector, h->sector_len, *T,
+                                    ham->e_nuc - c, grid, h->partials, h->stream));
+    h->launches++;
+    SV_CUDA(h, launch_reduce_rows(h->partials, 2, grid, h->dout + out_off, h->stream));
+    h->launches++;
+    return SV_OK;
+}
+
+// Shift constant c of lambda = (H - c) psi: the diagonal energy of the reference
+// determinant (HF) or of the largest-weight determinant of a stored reference.
+static double shift_for(sv_handle h, sv_ham_handle ham) {
+    return diag_energy(*ham, h->ref_det, h->n);
+}
+
+// ---------------------------------------------------------------- C-ABI
+
+extern "C" {
+
+const char *sv_version(void) { return "sv-gb300 0.1 (sm_103a)"; }
+
+const char *sv_last_error(sv_handle h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+uint64_t sv_launch_count(sv_handle h) { return h ? h->launches : 0; }
+
+static sv_status create_common(int n_qubits, sv_dtype dtype, void *cuda_stream, void *psi_dev, void *lam_dev,
+                               sv_handle *out) {
+    if (!out) return fail(nullptr, SV_ERR_ARG, "NULL output handle pointer");
+    *out = nullptr;
+    if (n_qubits < 2 || n_qubits > SV_MAX_QUBITS || (n_qubits & 1))
+        return fail(nullptr, SV_ERR_ARG, "n_qubits must be even and in [2, 32]");
+    if (dtype != SV_C64 && dtype != SV_C128) return fail(nullptr, SV_ERR_ARG, "dtype must be SV_C64 or SV_C128");
+    if ((psi_dev && ((uintptr_t)psi_dev & 255)) || (lam_dev && ((uintptr_t)lam_dev & 255)))
+        return fail(nullptr, SV_ERR_ARG, "device buffers must be 256-byte aligned");
+    sv_handle h = new sv_ctx();
+    h->n = n_qubits;
+    h->dtype = dtype;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->dim = 1ull << n_qubits;
+    h->amp_bytes = dtype == SV_C64 ? 8 : 16;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(nullptr, SV_ERR_CUDA, "no CUDA device");
+    }
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (psi_dev) {
+        h->psi = psi_dev;
+        h->own_psi = false;
+    } else {
+        sv_status s = dev_alloc(h, &h->psi, vec_bytes(h), "state vector");
+        if (s != SV_OK) {
+            delete h;
+            return s;
+        }
+    }
+    if (lam_dev) {
+        h->lam = lam_dev;
+        h->own_lam = false;
+    }
+    *out = h;
+    return SV_OK;
+}
+
+sv_status sv_create(int n_qubits, sv_dtype dtype, void *cuda_stream, sv_handle *out) {
+    return create_common(n_qubits, dtype, cuda_stream, nullptr, nullptr, out);
+}
+
+sv_status sv_create_with_buffers(int n_qubits, sv_dtype dtype, void *cuda_stream, void *psi_dev, void *lam_dev,
+                                 sv_handle *out) {
+    if (!psi_dev) return fail(nullptr, SV_ERR_ARG, "psi_dev is required");
+    return create_common(n_qubits, dtype, cuda_stream, psi_dev, lam_dev, out);
+}
+
+sv_status sv_destroy(sv_handle h) {
+    if (!h) return SV_OK;
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    cudaGetLastError();
+    if (h->own_psi) dev_free(h, h->psi, vec_bytes(h));
+    if (h->own_lam) dev_free(h, h->lam, vec_bytes(h));
+    dev_free(h, h->ref_vec, vec_bytes(h));
+    dev_free(h, h->saved, vec_bytes(h));
+    for (void *p : h->ckpt) dev_free(h, p, vec_bytes(h));
+    dev_free(h, h->sector, h->sector_len * sizeof(uint32_t));
+    dev_free(h, h->partials, h->partials_cap * sizeof(double));
+    dev_free(h, h->dout, h->dout_cap * sizeof(double));
+    if (h->hpinned) cudaFreeHost(h->hpinned);
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
+    delete h;
+    return SV_OK;
+}
+
+
+sv_status sv_prepare_hf(sv_handle h, const int32_t *occ, int n_occ) {
+    if (!h) return fail(nullptr, SV_ERR_ARG, "NULL handle");
+    if (n_occ < 0 || n_occ > h->n || (n_occ > 0 && !occ)) return fail(h, SV_ERR_ARG, "bad occupation list");
+    uint32_t x = 0;
+    int na = 0, nb = 0;
+    for (int k = 0; k < n_occ; ++k) {
+        int j = occ[k];
+        if (j < 0 || j >= h->n) return fail(h, SV_ERR_ARG, "occupied index out of range");
+        if ((x >> j) & 1u) return fail(h, SV_ERR_ARG, "repeated occupied index");
+        x |= 1u << j;
+        if (j & 1) ++nb; else ++na;
+    }
+    DeviceGuard g(h->device);
+    h->failed = false;
+    h->prepared = false;
+    h->ref_kind = 1;
+    h->ref_det = x;
+    h->na = na;
+    h->nb = nb;
+    SV_TRY(prepare_reference(h));
+    h->prepared = true;
+    return SV_OK;
+}
+
+sv_status sv_prepare_state(sv_handle h, const void *amplitudes_host, int n_alpha, int n_beta) {
+    if (!h) return fail(nullptr, SV_ERR_ARG, "NULL handle");
+    if (!amplitudes_host) return fail(h, SV_ERR_ARG, "NULL amplitudes");
+    const int N = h->n / 2;
+    if (n_alpha < 0 || n_beta < 0 || n_alpha > N || n_beta > N) return fail(h, SV_ERR_ARG, "bad electron counts");
+    const uint32_t even = 0x55555555u, odd = 0xAAAAAAAAu;
+    double best = -1.0;
+    uint32_t best_x = 0;
+    for (uint64_t x = 0; x < h->dim; ++x) {
+        double re, im;
+        if (h->dtype == SV_C64) {
+            const float *a = (const float *)amplitudes_host + 2 * x;
+            re = a[0]; im = a[1];
+        } else {
+            const double *a = (const double *)amplitudes_host + 2 * x;
+            re = a[0]; im = a[1];
+        }
+        if (!std::isfinite(re) || !std::isfinite(im)) return fail(h, SV_ERR_ARG, "non-finite amplitude");
+        double w = re * re + im * im;
+        if (w == 0.0) continue;
+        if (__builtin_popcount((uint32_t)x & even) != n_alpha || __builtin_popcount((uint32_t)x & odd) != n_beta)
+            return fail(h, SV_ERR_ARG, "amplitude outside the (n_alpha, n_beta) sector");
+        if (w > best) { best = w; best_x = (uint32_t)x; }
+    }
+    if (best <= 0.0) return fail(h, SV_ERR_ARG, "zero state");
+    DeviceGuard g(h->device);
+    h->failed = false;
+    h->prepared = false;
+    if (!h->ref_vec) SV_TRY(dev_alloc(h, &h->ref_vec, vec_bytes(h), "reference copy"));
+    SV_CUDA(h, cudaMemcpyAsync(h->ref_vec, amplitudes_host, vec_bytes(h), cudaMemcpyHostToDevice, h->stream));
+    SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->ref_kind = 2;
+    h->ref_det = best_x;
+    h->na = n_alpha;
+    h->nb = n_beta;
+    SV_TRY(prepare_reference(h));
+    h->prepared = true;
+    return SV_OK;
+}
+
+sv_status sv_get_state(sv_handle h, void *amplitudes_host) {
+    SV_TRY(check_ready(h));
+    if (!amplitudes_host) return fail(h, SV_ERR_ARG, "NULL output");
+    DeviceGuard g(h->device);
+    SV_CUDA(h, cudaMemcpyAsync(amplitudes_host, h->psi, vec_bytes(h), cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SV_OK;
+}
+
+sv_status sv_state_device_ptr(sv_handle h, void **psi_dev) {
+    if (!h || !psi_dev) return fail(h, SV_ERR_ARG, "NULL argument");
+    *psi_dev = h->psi;
+    return SV_OK;
+}
+
+sv_status sv_ham_create(int n_orb, const double *hmat, const double *eri, double e_nuc, sv_ham_handle *out) {
+    if (!out) return fail(nullptr, SV_ERR_ARG, "NULL output handle pointer");
+    *out = nullptr;
+    if (n_orb < 1 || n_orb > SV_MAX_QUBITS / 2) return fail(nullptr, SV_ERR_ARG, "n_orb must be in [1, 16]");
+    if (!hmat || !eri) return fail(nullptr, SV_ERR_ARG, "NULL integrals");
+    if (!std::isfinite(e_nuc)) return fail(nullptr, SV_ERR_ARG, "non-finite e_nuc");
+    const int N = n_orb;
+    auto tol = [](double a, double b) { return std::fabs(a - b) <= 1e-12 * std::max(1.0, std::fabs(a)); };
+    for (int p = 0; p < N; ++p)
+        for (int q = 0; q < N; ++q) {
+            double v = hmat[p * N + q];
+            if (!std::isfinite(v)) return fail(nullptr, SV_ERR_ARG, "non-finite h");
+            if (!tol(v, hmat[q * N + p])) return fail(nullptr, SV_ERR_ARG, "h is not symmetric");
+        }
+    auto E = [&](int p, int q, int r, int s) { return eri[(((size_t)p * N + q) * N + r) * N + s]; };
+    for (int p = 0; p < N; ++p)
+        for (int q = 0; q < N; ++q)
+            for (int r = 0; r < N; ++r)
+                for (int s = 0; s < N; ++s) {
+                    double v = E(p, q, r, s);
+                    if (!std::isfinite(v)) return fail(nullptr, SV_ERR_ARG, "non-finite eri");
+                    if (!tol(v, E(q, p, r, s)) || !tol(v, E(p, q, s, r)) || !tol(v, E(r, s, p, q)))
+                        return fail(nullptr, SV_ERR_ARG, "eri lacks the 8-fold symmetry of real orbitals");
+                }
+    sv_ham_handle H = new sv_ham();
+    H->n_orb = N;
+    H->e_nuc = e_nuc;
+    H->h.assign(hmat, hmat + (size_t)N * N);
+    H->eri.assign(eri, eri + (size_t)N * N * N * N);
+    *out = H;
+    return SV_OK;
+}
+
+sv_status sv_ham_destroy(sv_ham_handle ham) {
+    if (!ham) return SV_OK;
+    ham->dev.clear();
+    delete ham;
+    return SV_OK;
+}
+
+sv_status sv_apply_ansatz(sv_handle h, const sv_excitation *ops, int n_ops, const double *theta) {
+    SV_TRY(check_ready(h));
+    std::vector<OpDesc> d;
+    SV_TRY(build_ops(h, ops, n_ops, theta, d));
+    DeviceGuard g(h->device);
+    SV_TRY(forward(h, d, false));
+    return SV_OK;
+}
+
+sv_status sv_energy(sv_handle h, sv_ham_handle ham, double *e_out) {
+    SV_TRY(check_ready(h));
+    SV_TRY(check_ham(h, ham));
+    if (!e_out) return fail(h, SV_ERR_ARG, "NULL e_out");
+    DeviceGuard g(h->device);
+    DevTables *T;
+    SV_TRY(get_tables(h, ham, &T));
+    SV_TRY(ensure_out(h, 2));
+    const double c = shift_for(h, ham);
+    SV_TRY(expectation(h, ham, T, nullptr, c, 0));
+    SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    *e_out = c + h->hpinned[0] / h->hpinned[1];
+    return SV_OK;
+}
+
+sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *ops, int n_ops, const double *theta,
+                         double *e_out, double *grad_out) {
+    if (!h) return fail(nullptr, SV_ERR_ARG, "NULL handle");
+    if (h->ref_kind == 0) return fail(h, SV_ERR_STATE, "no reference state recorded");
+    SV_TRY(check_ham(h, ham));
+    std::vector<OpDesc> d;
+    SV_TRY(build_ops(h, ops, n_ops, theta, d));
+    DeviceGuard g(h->device);
+    const size_t L = d.size();
+    DevTables *T;
+    SV_TRY(get_tables(h, ham, &T));
+    SV_TRY(ensure_lam(h));
+    SV_TRY(ensure_out(h, 2 + L));
+    // state buffers first (so the byte cap drops checkpoints, not required scratch)
+    if (!h->saved) {
+        void *p = nullptr;
+        if (dev_alloc(h, &p, vec_bytes(h), "saved final state") == SV_OK) h->saved = p;
+        else cudaGetLastError();
+    }
+    const int G = rotate_grid(1ull << (h->n - 2), h->sm_count);
+    SV_TRY(ensure_sector(h));
+    const int Ge = expect_gather_grid(h->sector_len, h->sm_count);
+    SV_TRY(ensure_partials(h, std::max<size_t>((size_t)G * std::max<size_t>(L, 1), 2 * (size_t)Ge)));
+    plan_checkpoints(h, L);
+    h->prepared = false;
+    SV_TRY(mark(h, 0));
+    SV_TRY(prepare_reference(h));
+    h->prepared = true;
+    SV_TRY(mark(h, 1));
+    SV_TRY(forward(h, d, true));
+    SV_TRY(mark(h, 2));
+    if (h->saved)
+        SV_CUDA(h, cudaMemcpyAsync(h->saved, h->psi, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    const double c = shift_for(h, ham);
+    SV_TRY(mark(h, 3));
+    SV_TRY(expectation(h, ham, T, h->lam, c, 0));
+    SV_TRY(mark(h, 4));
+    // reverse sweep
+    const int64_t C = h->ckpt_interval;
+    for (size_t kk = L; kk-- > 0;) {
+        SV_CUDA(h, launch_adjoint(h->psi, h->lam, h->dtype, h->n, d[kk], G, h->partials + kk * (size_t)G,
+                                  h->stream));
+        h->launches++;
+        // psi now holds the state after ops[0..kk-1]; resynchronise from a checkpoint if one holds it
+        if (C > 0 && kk > 0 && kk % (size_t)C == 0) {
+            size_t j = kk / (size_t)C - 1;
+            if (j < h->ckpt.size() && h->ckpt[j])
+                SV_CUDA(h, cudaMemcpyAsync(h->psi, h->ckpt[j], vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+        }
+    }
+    SV_CUDA(h, launch_reduce_rows(h->partials, (int)L, G, h->dout + 2, h->stream));
+    h->launches++;
+    SV_TRY(mark(h, 5));
+    SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, (2 + L) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    // leave psi(theta) in the handle
+    if (h->saved) {
+        SV_CUDA(h, cudaMemcpyAsync(h->psi, h->saved, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+        SV_TRY(prepare_reference(h));
+        SV_TRY(forward(h, d, false));
+    }
+    SV_TRY(mark(h, 6));
+    SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->profile) {
+        h->phase_ms[0] = elapsed(h, 0, 1);
+        h->phase_ms[1] = elapsed(h, 1, 2);
+        h->phase_ms[2] = elapsed(h, 3, 4);
+        h->phase_ms[3] = elapsed(h, 4, 5);
+        h->phase_ms[4] = elapsed(h, 5, 6);
+    }
+    const double nrm = h->hpinned[1];
+    if (e_out) *e_out = c + h->hpinned[0] / nrm;
+    if (grad_out)
+        for (size_t k = 0; k < L; ++k) grad_out[k] = 2.0 * h->hpinned[2 + k] / nrm;
+    return SV_OK;
+}
+
+sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
+    SV_TRY(check_ready(h));
+    if (!re_out) return fail(h, SV_ERR_ARG, "NULL re_out");
+    DeviceGuard g(h->device);
+    SV_TRY(ensure_sector(h));
+    // element list (host) -> device scratch after the partial sums
+    std::vector<uint8_t> host_el;
+    const int n_el = rdm_elements_bytes(h->n, host_el);
+    const int grid = rdm_gather_grid(h->sector_len, h->sm_count);
+    const size_t part = (size_t)2 * n_el * grid;
+    const size_t el_doubles = (host_el.size() + sizeof(double) - 1) / sizeof(double);
+    SV_TRY(ensure_partials(h, part + el_doubles));
+    SV_TRY(ensure_out(h, 2 * (size_t)n_el));
+    double *d_el = h->partials + part;
+    SV_CUDA(h, cudaMemcpyAsync(d_el, host_el.data(), host_el.size(), cudaMemcpyHostToDevice, h->stream));
+    SV_TRY(mark(h, 0));
+    SV_CUDA(h, launch_rdm_gather(h->psi, h->dtype, h->sector, h->sector_len, d_el, n_el, grid, h->partials,
+                                 h->stream));
+    h->launches++;
+    SV_CUDA(h, launch_reduce_rows(h->partials, 2 * n_el, grid, h->dout, h->stream));
+    h->launches++;
+    SV_TRY(mark(h, 7));
+    SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, 2 * (size_t)n_el * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+    SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->profile) h->phase_ms[5] = elapsed(h, 0, 7);
+    const int n = h->n, N = n / 2;
+    const double *o = h->hpinned;
+    const double nrm = o[0];
+    for (int s = 0; s < 2; ++s)
+        for (int p = 0; p < N; ++p) {
+            re_out[(s * N + p) * N + p] = o[2 * (1 + 2 * p + s)] / nrm;
+            if (im_out) im_out[(s * N + p) * N + p] = 0.0;
+        }
+    int e = 1 + n;
+    for (int s = 0; s < 2; ++s)
+        for (int p = 0; p < N; ++p)
+            for (int q = p + 1; q < N; ++q, ++e) {
+                double re = o[2 * e] / nrm, im = o[2 * e + 1] / nrm;
+                re_out[(s * N + p) * N + q] = re;
+                re_out[(s * N + q) * N + p] = re;
+                if (im_out) {
+                    im_out[(s * N + p) * N + q] = im;
+                    im_out[(s * N + q) * N + p] = -im;
+                }
+            }
+    return SV_OK;
+}
+
+sv_status sv_phase_times(sv_handle h, double *ms_out, int n_out) {
+    if (!h || !ms_out || n_out < 0) return fail(h, SV_ERR_ARG, "bad arguments");
+    for (int i = 0; i < n_out && i < SV_PHASES; ++i) ms_out[i] = h->phase_ms[i];
+    return SV_OK;
+}
+
+sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
+    if (!h) return fail(nullptr, SV_ERR_ARG, "NULL handle");
+    switch (opt) {
+        case SV_OPT_CHECKPOINT_INTERVAL:
+            if (value < 0) return fail(h, SV_ERR_ARG, "checkpoint interval < 0");
+            h->ckpt_interval = value;
+            return SV_OK;
+        case SV_OPT_MAX_BYTES:
+            if (value < 0) return fail(h, SV_ERR_ARG, "max bytes < 0");
+            h->max_bytes = value;
+            return SV_OK;
+        case SV_OPT_EXPECT_VARIANT:
+            if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "expect variant must be 0, 1 or 2");
+            h->expect_variant = (int)value;
+            return SV_OK;
+        case SV_OPT_RDM_VARIANT:
+            if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "rdm variant must be 0, 1 or 2");
+            h->rdm_variant = (int)value;
+            return SV_OK;
+        case SV_OPT_PROFILE:
+            h->profile = value != 0;
+            return SV_OK;
+    }
+    return fail(h, SV_ERR_ARG, "unknown option");
+}
+
+}  // extern "C"

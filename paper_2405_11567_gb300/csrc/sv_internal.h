@@ -1,0 +1,172 @@
+// sv_internal.h -- host-side structures shared by the library's translation units.
+// Not part of the public C-ABI (include/sv.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "sv.h"
+
+struct sv_ham;
+
+namespace svk {
+
+// ---------------------------------------------------------------- excitation ops
+
+// One excitation prepared for the rotation kernels.  The pair (x, x ^ m) is
+// rotated for every basis index x whose bits on the mask equal `from` (the
+// determinant that T maps to x ^ m).  The Jordan-Wigner sign of T on x is
+// (-1)^popc(x & sm): for a single i->a, sm = bits strictly between i and a; for a
+// double with sorted mask positions q0<q1<q2<q3, sm = bits strictly between q0 and
+// q1 plus bits strictly between q2 and q3, whichever two of the four are occupied.
+struct OpDesc {
+    uint32_t m = 0;     // flip mask
+    uint32_t from = 0;  // bits of the "from" determinant on the mask
+    uint32_t sm = 0;    // sign mask
+    int nbits = 0;      // 2 (single) or 4 (double)
+    int pos[4] = {0, 0, 0, 0};  // mask positions, ascending
+    double c = 1.0, s = 0.0;    // cos(theta), sin(theta), taken on the host in float64
+};
+
+// Validate one excitation for an n-qubit register and fill `d` (without angles).
+bool make_op(const sv_excitation &e, int n, OpDesc &d, std::string &why);
+
+// Bits strictly between positions a and b (order irrelevant).
+inline uint32_t bits_between(int a, int b) {
+    if (a > b) { int t = a; a = b; b = t; }
+    if (b - a <= 1) return 0u;
+    uint64_t hi = (1ull << b) - 1ull;        // bits < b
+    uint64_t lo = (1ull << (a + 1)) - 1ull;  // bits <= a
+    return (uint32_t)(hi & ~lo);
+}
+
+// ---------------------------------------------------------------- Hamiltonian tables
+
+// Double-excitation group: every Pauli string whose X-part is the 4-bit mask m.
+// At a basis index x with exactly two of the four mask bits set, the sum of those
+// strings equals <x^m|H|x> = (-1)^popc(x & sm) * v[split], where split says which
+// mask bit pairs with the lowest one among the occupied (or, equivalently, the
+// empty) pair: 0 -> q1, 1 -> q2, 2 -> q3, and v = [ai|bj] - [aj|bi] for occupied
+// i<j and empty a<b.  Other x are not connected by this mask.
+template <typename R>
+struct DoubleRec {
+    uint32_t m, sm;
+    uint32_t b0, b1, b2;  // bit(q0), bit(q1), bit(q2)
+    uint32_t pad;
+    R v[3];
+};
+
+// Single-excitation group (mask {i, a}, same spin): at x with exactly one of the
+// two bits set, <x^m|H|x> = (-1)^popc(x & sm) * (h_ai + sum_k x_k W[k]),
+// W[k] = [ai|kk] - [ak|ki] (zero for k in {i, a}).
+template <typename R>
+struct SingleRec {
+    uint32_t m, sm;
+    R h;
+    R pad;
+};
+
+// Host copy of the tables for one (n, precision).
+template <typename R>
+struct HostTables {
+    std::vector<DoubleRec<R>> dbl;
+    std::vector<SingleRec<R>> sgl;
+    std::vector<R> W;          // [n_singles][n]
+    std::vector<double> hdiag; // [n] h_kk per spin-orbital
+    std::vector<double> Jp;    // [n][n] [kk|ll] - [kl|lk] (0 on the diagonal)
+};
+
+// Device copy of the tables, built lazily per (n, dtype) and cached in the Hamiltonian.
+struct DevTables {
+    int n = 0;
+    int dtype = 0;
+    int n_dbl = 0, n_sgl = 0;
+    void *dbl = nullptr;   // DoubleRec<R>[n_dbl]
+    void *sgl = nullptr;   // SingleRec<R>[n_sgl]
+    void *W = nullptr;     // R[n_sgl * n]
+    double *hdiag = nullptr;
+    double *Jp = nullptr;
+    // tiled-pass schedule (k_expect.cu); empty until first needed
+    struct Pass {
+        uint32_t S;        // local qubit set (bit mask over storage positions)
+        int first_dbl, n_dbl, first_sgl, n_sgl;
+        int owns_diag;
+    };
+    std::vector<Pass> passes;
+    void *pass_dbl = nullptr;  // doubles regrouped by pass, local-index form
+    void *pass_sgl = nullptr;
+    void *pass_W = nullptr;
+    int tile_bits = 0;
+    ~DevTables();
+};
+
+template <typename R>
+void build_tables(const sv_ham &H, int n, HostTables<R> &out);
+
+// <x|H|x> in float64 on the host.
+double diag_energy(const sv_ham &H, uint32_t x, int n);
+
+}  // namespace svk
+
+// ---------------------------------------------------------------- handles
+
+struct sv_ham {
+    int n_orb = 0;
+    double e_nuc = 0.0;
+    std::vector<double> h;    // [N][N]
+    std::vector<double> eri;  // [N][N][N][N] chemist (pq|rs)
+    std::map<int, std::unique_ptr<svk::DevTables>> dev;  // key: n*2 + dtype
+    int device = -1;
+};
+
+struct sv_ctx {
+    int n = 0;
+    sv_dtype dtype = SV_C64;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    uint64_t dim = 0;          // 2^n
+    size_t amp_bytes = 8;      // bytes per amplitude
+    void *psi = nullptr;
+    void *lam = nullptr;
+    bool own_psi = true, own_lam = true;
+    // prepared state
+    bool prepared = false;
+    bool failed = false;
+    int na = -1, nb = -1;
+    int ref_kind = 0;          // 0 none, 1 HF determinant, 2 stored vector
+    uint32_t ref_det = 0;      // HF determinant (ref_kind 1)
+    void *ref_vec = nullptr;   // device copy of the reference (ref_kind 2)
+    double ref_shift = 0.0;    // c in lambda = (H - c) psi
+    // sector list (basis indices of the (na, nb) sector, ascending) for gather kernels
+    uint32_t *sector = nullptr;
+    uint64_t sector_len = 0;
+    int sector_na = -1, sector_nb = -1;
+    // reduction scratch
+    double *partials = nullptr;
+    size_t partials_cap = 0;   // doubles
+    double *dout = nullptr;    // small device output buffer
+    size_t dout_cap = 0;
+    double *hpinned = nullptr; // pinned host staging
+    size_t hpinned_cap = 0;
+    // checkpoints / saved final state
+    std::vector<void *> ckpt;
+    void *saved = nullptr;
+    int64_t ckpt_interval = 0;
+    int64_t max_bytes = 0;
+    uint64_t bytes_owned = 0;
+    int expect_variant = 0;
+    int rdm_variant = 0;
+    // phase profiling (SV_OPT_PROFILE)
+    bool profile = false;
+    cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double phase_ms[SV_PHASES] = {0, 0, 0, 0, 0, 0};
+    // bookkeeping
+    uint64_t launches = 0;
+    std::string err;
+    int sm_count = 148;
+};

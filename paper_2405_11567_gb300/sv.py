@@ -1,0 +1,289 @@
+"""Thin ctypes binding of the C-ABI declared in include/sv.h.
+
+Functions carry the C names and do argument marshalling only: every step of
+the path runs in the library's CUDA kernels.  The shared library is loaded on
+first use; if it has not been built (``paper_2405_11567_gb300.build.build()``)
+or no GPU is present, calls raise -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SV_C64, SV_C128 = 0, 1
+SV_OPT_CHECKPOINT_INTERVAL, SV_OPT_MAX_BYTES, SV_OPT_EXPECT_VARIANT, SV_OPT_RDM_VARIANT = 1, 2, 3, 4
+SV_OPT_PROFILE = 5
+SV_PHASES = 6
+PHASE_NAMES = ("reference", "forward", "expectation", "reverse", "restore", "rdm1")
+STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV_ERR_TIMEOUT", 5: "SV_ERR_STATE"}
+
+# every symbol include/sv.h declares
+EXPORTS = (
+    "sv_create", "sv_create_with_buffers", "sv_destroy", "sv_prepare_hf", "sv_prepare_state",
+    "sv_get_state", "sv_state_device_ptr", "sv_ham_create", "sv_ham_destroy", "sv_apply_ansatz",
+    "sv_energy", "sv_energy_grad", "sv_rdm1", "sv_set_option", "sv_phase_times", "sv_last_error",
+    "sv_launch_count", "sv_version",
+)
+
+
+class SvError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = int(status)
+        super().__init__("%s: %s" % (STATUS.get(self.status, str(status)), message))
+
+
+class sv_excitation(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("occ", ctypes.c_int32 * 2), ("vir", ctypes.c_int32 * 2)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded C-ABI library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError("CUDA library %s is missing: build it with paper_2405_11567_gb300.build.build()"
+                               % path)
+        L = ctypes.CDLL(path)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "sv_create": (i32, [i32, i32, vp, pp]),
+            "sv_create_with_buffers": (i32, [i32, i32, vp, vp, vp, pp]),
+            "sv_destroy": (i32, [vp]),
+            "sv_prepare_hf": (i32, [vp, vp, i32]),
+            "sv_prepare_state": (i32, [vp, vp, i32, i32]),
+            "sv_get_state": (i32, [vp, vp]),
+            "sv_state_device_ptr": (i32, [vp, pp]),
+            "sv_ham_create": (i32, [i32, vp, vp, dbl, pp]),
+            "sv_ham_destroy": (i32, [vp]),
+            "sv_apply_ansatz": (i32, [vp, vp, i32, vp]),
+            "sv_energy": (i32, [vp, vp, vp]),
+            "sv_energy_grad": (i32, [vp, vp, vp, i32, vp, vp, vp]),
+            "sv_rdm1": (i32, [vp, vp, vp]),
+            "sv_set_option": (i32, [vp, i32, i64]),
+            "sv_phase_times": (i32, [vp, vp, i32]),
+            "sv_last_error": (ctypes.c_char_p, [vp]),
+            "sv_launch_count": (ctypes.c_uint64, [vp]),
+            "sv_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _ck(status, handle=None):
+    if status != 0:
+        msg = lib().sv_last_error(handle)
+        raise SvError(status, msg.decode() if msg else "")
+
+
+def _ops_array(ops):
+    a = np.ascontiguousarray(np.asarray(ops, dtype=np.int32).reshape(-1, 5))
+    return a
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+# ---------------------------------------------------------------- C names
+
+def sv_version() -> str:
+    return lib().sv_version().decode()
+
+
+def sv_last_error(handle=None) -> str:
+    return lib().sv_last_error(handle).decode()
+
+
+def sv_create(n_qubits: int, dtype: int, stream=None):
+    h = ctypes.c_void_p()
+    _ck(lib().sv_create(int(n_qubits), int(dtype), _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def sv_create_with_buffers(n_qubits: int, dtype: int, stream, psi_dev: int, lam_dev=None):
+    h = ctypes.c_void_p()
+    _ck(lib().sv_create_with_buffers(int(n_qubits), int(dtype), _stream_ptr(stream), ctypes.c_void_p(psi_dev),
+                                     ctypes.c_void_p(lam_dev) if lam_dev else None, ctypes.byref(h)))
+    return h
+
+
+def sv_destroy(h):
+    _ck(lib().sv_destroy(h))
+
+
+def sv_prepare_hf(h, occ):
+    occ = np.ascontiguousarray(np.asarray(occ, dtype=np.int32).reshape(-1))
+    _ck(lib().sv_prepare_hf(h, _ptr(occ), len(occ)), h)
+
+
+def sv_prepare_state(h, amplitudes, n_alpha: int, n_beta: int):
+    a = np.ascontiguousarray(amplitudes)
+    if a.dtype not in (np.complex64, np.complex128):
+        raise TypeError("amplitudes must be complex64 or complex128 (the handle's dtype)")
+    _ck(lib().sv_prepare_state(h, _ptr(a), int(n_alpha), int(n_beta)), h)
+
+
+def sv_get_state(h, n_qubits: int, dtype: int) -> np.ndarray:
+    out = np.empty(1 << n_qubits, dtype=np.complex64 if dtype == SV_C64 else np.complex128)
+    _ck(lib().sv_get_state(h, _ptr(out)), h)
+    return out
+
+
+def sv_state_device_ptr(h) -> int:
+    p = ctypes.c_void_p()
+    _ck(lib().sv_state_device_ptr(h, ctypes.byref(p)), h)
+    return p.value
+
+
+def sv_ham_create(h_mat, eri, e_nuc: float):
+    hm = np.ascontiguousarray(np.asarray(h_mat, dtype=np.float64))
+    N = hm.shape[0]
+    er = np.ascontiguousarray(np.asarray(eri, dtype=np.float64).reshape(N, N, N, N))
+    out = ctypes.c_void_p()
+    _ck(lib().sv_ham_create(N, _ptr(hm), _ptr(er), float(e_nuc), ctypes.byref(out)))
+    return out
+
+
+def sv_ham_destroy(ham):
+    _ck(lib().sv_ham_destroy(ham))
+
+
+def sv_apply_ansatz(h, ops, theta):
+    o = _ops_array(ops)
+    t = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1))
+    if len(t) != len(o):
+        raise ValueError("one angle per excitation")
+    _ck(lib().sv_apply_ansatz(h, _ptr(o), len(o), _ptr(t)), h)
+
+
+def sv_energy(h, ham) -> float:
+    e = np.zeros(1)
+    _ck(lib().sv_energy(h, ham, _ptr(e)), h)
+    return float(e[0])
+
+
+def sv_energy_grad(h, ham, ops, theta):
+    o = _ops_array(ops)
+    t = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1))
+    if len(t) != len(o):
+        raise ValueError("one angle per excitation")
+    e = np.zeros(1)
+    g = np.zeros(max(len(o), 1))
+    _ck(lib().sv_energy_grad(h, ham, _ptr(o), len(o), _ptr(t), _ptr(e), _ptr(g)), h)
+    return float(e[0]), g[:len(o)]
+
+
+def sv_rdm1(h, n_orb: int) -> np.ndarray:
+    re = np.zeros((2, n_orb, n_orb))
+    im = np.zeros((2, n_orb, n_orb))
+    _ck(lib().sv_rdm1(h, _ptr(re), _ptr(im)), h)
+    return re + 1j * im
+
+
+def sv_set_option(h, opt: int, value: int):
+    _ck(lib().sv_set_option(h, int(opt), int(value)), h)
+
+
+def sv_phase_times(h) -> dict:
+    ms = np.zeros(SV_PHASES)
+    _ck(lib().sv_phase_times(h, _ptr(ms), SV_PHASES), h)
+    return dict(zip(PHASE_NAMES, ms.tolist()))
+
+
+def sv_launch_count(h) -> int:
+    return int(lib().sv_launch_count(h))
+
+
+# ---------------------------------------------------------------- convenience objects
+
+class Hamiltonian:
+    """Owns an ``sv_ham_handle`` built from (h, eri, e_nuc)."""
+
+    def __init__(self, h_mat, eri, e_nuc):
+        self.n_orb = int(np.asarray(h_mat).shape[0])
+        self.handle = sv_ham_create(h_mat, eri, e_nuc)
+
+    def close(self):
+        if self.handle is not None:
+            sv_ham_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class StateVector:
+    """Owns an ``sv_handle``: an n-qubit state on the current CUDA device."""
+
+    def __init__(self, n_qubits: int, dtype="c64", stream=None):
+        self.n = int(n_qubits)
+        self.dtype = SV_C64 if dtype in ("c64", SV_C64, np.complex64) else SV_C128
+        self.handle = sv_create(self.n, self.dtype, stream)
+
+    def close(self):
+        if self.handle is not None:
+            sv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def prepare_hf(self, occ):
+        sv_prepare_hf(self.handle, occ)
+
+    def prepare_state(self, amplitudes, n_alpha, n_beta):
+        sv_prepare_state(self.handle, amplitudes, n_alpha, n_beta)
+
+    def state(self) -> np.ndarray:
+        return sv_get_state(self.handle, self.n, self.dtype)
+
+    def apply_ansatz(self, ops, theta):
+        sv_apply_ansatz(self.handle, ops, theta)
+
+    def energy(self, ham: Hamiltonian) -> float:
+        return sv_energy(self.handle, ham.handle)
+
+    def energy_grad(self, ham: Hamiltonian, ops, theta):
+        return sv_energy_grad(self.handle, ham.handle, ops, theta)
+
+    def rdm1(self) -> np.ndarray:
+        return sv_rdm1(self.handle, self.n // 2)
+
+    def set_option(self, opt, value):
+        sv_set_option(self.handle, opt, value)
+
+    def phase_times(self) -> dict:
+        return sv_phase_times(self.handle)
+
+    @property
+    def launches(self) -> int:
+        return sv_launch_count(self.handle)

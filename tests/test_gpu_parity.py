@@ -1,0 +1,297 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle.
+
+Tolerances (the workload specification): float64 state |dE| <= 1e-10 Ha,
+|dg| <= 1e-9 Ha/rad; complex64 state with float64 reductions |dE| <= 1e-5 Ha,
+|dg| <= 1e-5.  Integer work (Jordan-Wigner signs, pair indices, which amplitudes
+stay exactly zero) is compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import route_a as A
+from paper_2405_11567_gb300 import inputs
+from paper_2405_11567_gb300 import sv
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": dict(E=1e-10, g=1e-9, amp=1e-12, rdm=1e-12), "c64": dict(E=1e-5, g=1e-5, amp=2e-6, rdm=2e-6)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2405_11567_gb300 import build
+    build.build()
+    sv.lib()
+
+
+def _gpu_state(n, dtype):
+    return sv.StateVector(n, dtype)
+
+
+def _oracle_problem(p, na=None, nb=None):
+    na = p["na"] if na is None else na
+    nb = p["nb"] if nb is None else nb
+    return oracle.Sector(p["n_qubits"], na, nb)
+
+
+def _sector_mask(n, na, nb):
+    x = np.arange(1 << n, dtype=np.int64)
+    ca = sum(((x >> j) & 1) for j in range(0, n, 2))
+    cb = sum(((x >> j) & 1) for j in range(1, n, 2))
+    return (ca == na) & (cb == nb)
+
+
+# ---------------------------------------------------------------- rotations / signs
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,ne,seed", [(8, 2, 1001), (10, 4, 7), (12, 4, 8)])
+def test_ansatz_state_matches_oracle(n, ne, seed, dtype):
+    p = inputs.make_problem(n, ne, "uccsd", seed)
+    theta = p["theta"] * 8
+    sec = _oracle_problem(p)
+    ref = A.apply_ansatz(sec, p["ops"], theta, A.hf_state(sec, p["occ"]))
+    st = _gpu_state(n, dtype)
+    st.prepare_hf(p["occ"])
+    st.apply_ansatz(p["ops"], theta)
+    got = st.state()
+    idx = sec.dets.astype(np.int64)
+    assert np.max(np.abs(got[idx] - ref)) <= TOL[dtype]["amp"]
+    outside = ~_sector_mask(n, p["na"], p["nb"])
+    assert np.count_nonzero(got[outside]) == 0            # exact zeros outside the sector
+    assert np.count_nonzero(got.imag) == 0                # real angles, real start: exactly real
+
+
+def test_jordan_wigner_signs_bit_exact():
+    """Rotation by pi/2 moves a basis state onto T|x> with amplitude exactly +-1: the sign and the
+    partner index must equal the oracle's literal operator application, bit for bit."""
+    n = 10
+    pool = inputs.uccsd_pool(n, 4)
+    extra = np.array([(2, 1, 6, 2, 5), (2, 0, 5, 2, 3), (1, 5, -1, 1, -1), (2, 2, 3, 0, 7), (1, 8, -1, 2, -1)],
+                     np.int32)
+    ops = np.vstack([pool, extra])
+    st = _gpu_state(n, "c128")
+    rng = np.random.default_rng(0)
+    for op in ops:
+        na = 2 if op[0] == 2 else 2
+        sec = oracle.Sector(n, 2, 2)
+        froms = [int(x) for x in sec.dets if A.exc_apply(op, int(x))[0] != 0]
+        for x in rng.choice(froms, size=min(6, len(froms)), replace=False):
+            s, y = A.exc_apply(op, int(x))
+            v = np.zeros(1 << n, np.complex128)
+            v[int(x)] = 1.0
+            st.prepare_state(v, 2, 2)
+            st.apply_ansatz(op[None, :], [np.pi / 2])
+            got = st.state()
+            assert got[y].real == float(s) and got[y].imag == 0.0
+            assert abs(got[int(x)]) < 1e-15
+            assert np.count_nonzero(np.abs(got) > 1e-15) == 1
+
+
+# ---------------------------------------------------------------- energy / gradient
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_config1_energy(dtype):
+    p = inputs.config_problem(1)
+    sec = _oracle_problem(p)
+    Eref = A.energy(sec, p["h"], p["eri"], p["e_nuc"],
+                    A.apply_ansatz(sec, p["ops"], p["theta"], A.hf_state(sec, p["occ"])))
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(p["n_qubits"], dtype)
+    st.prepare_hf(p["occ"])
+    st.apply_ansatz(p["ops"], p["theta"])
+    assert abs(st.energy(ham) - Eref) <= TOL[dtype]["E"]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_config2_energy_grad(dtype):
+    p = inputs.config_problem(2)
+    sec = _oracle_problem(p)
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], p["theta"], A.hf_state(sec, p["occ"]))
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(p["n_qubits"], dtype)
+    st.prepare_hf(p["occ"])
+    E, g = st.energy_grad(ham, p["ops"], p["theta"])
+    assert abs(E - Eref) <= TOL[dtype]["E"]
+    assert np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
+    # the handle holds psi(theta) afterwards
+    psi = A.apply_ansatz(sec, p["ops"], p["theta"], A.hf_state(sec, p["occ"]))
+    assert np.max(np.abs(st.state()[sec.dets.astype(np.int64)] - psi)) <= TOL[dtype]["amp"] * 10
+
+
+def test_config2_gradient_central_differences():
+    p = inputs.config_problem(2)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(p["n_qubits"], "c128")
+    st.prepare_hf(p["occ"])
+    _, g = st.energy_grad(ham, p["ops"], p["theta"])
+    hstep = 1e-5
+    for k in range(0, len(p["ops"]), 23):
+        tp, tm = p["theta"].copy(), p["theta"].copy()
+        tp[k] += hstep
+        tm[k] -= hstep
+        st.prepare_hf(p["occ"])
+        st.apply_ansatz(p["ops"], tp)
+        Ep = st.energy(ham)
+        st.prepare_hf(p["occ"])
+        st.apply_ansatz(p["ops"], tm)
+        Em = st.energy(ham)
+        assert abs((Ep - Em) / (2 * hstep) - g[k]) < 1e-8
+
+
+def test_autograd_function():
+    torch = pytest.importorskip("torch")
+    from paper_2405_11567_gb300.autograd import energy
+    p = inputs.config_problem(2)
+    sec = _oracle_problem(p)
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], p["theta"], A.hf_state(sec, p["occ"]))
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(p["n_qubits"], "c128")
+    st.prepare_hf(p["occ"])
+    th = torch.tensor(p["theta"], dtype=torch.float64, requires_grad=True)
+    E = energy(th, st, ham, p["ops"])
+    (3.0 * E).backward()
+    assert abs(E.item() - Eref) <= 1e-10
+    assert np.max(np.abs(th.grad.numpy() - 3.0 * gref)) <= 3e-9
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_complex_start_open_shell(dtype):
+    """A complex multi-determinant start with N_alpha != N_beta exercises every conj() of the path."""
+    n, na, nb = 12, 3, 2
+    p = inputs.make_problem(n, 4, 40, seed=55)
+    rng = np.random.default_rng(3)
+    dense0 = inputs.random_sector_state(n, na, nb, rng)
+    sec = oracle.Sector(n, na, nb)
+    psi0 = dense0[sec.dets.astype(np.int64)]
+    theta = p["theta"] * 6
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(n, dtype)
+    st.prepare_state(dense0.astype(np.complex64 if dtype == "c64" else np.complex128), na, nb)
+    E, g = st.energy_grad(ham, p["ops"], theta)
+    assert abs(E - Eref) <= TOL[dtype]["E"]
+    assert np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
+    rdm_ref = A.rdm1(sec, A.apply_ansatz(sec, p["ops"], theta, psi0))
+    assert np.max(np.abs(st.rdm1() - rdm_ref)) <= TOL[dtype]["rdm"]
+
+
+# ---------------------------------------------------------------- 1-RDM
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_rdm1_matches_oracle(dtype):
+    p = inputs.make_problem(14, 6, 60, seed=66)
+    sec = _oracle_problem(p)
+    psi = A.apply_ansatz(sec, p["ops"], p["theta"] * 5, A.hf_state(sec, p["occ"]))
+    ref = A.rdm1(sec, psi)
+    st = _gpu_state(14, dtype)
+    st.prepare_hf(p["occ"])
+    st.apply_ansatz(p["ops"], p["theta"] * 5)
+    got = st.rdm1()
+    assert np.max(np.abs(got - ref)) <= TOL[dtype]["rdm"]
+
+
+# ---------------------------------------------------------------- config 3 (24 qubits)
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_config3_energy_grad_rdm(dtype, config3_oracle):
+    p, Eref, gref, rdm_ref = config3_oracle
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(p["n_qubits"], dtype)
+    st.prepare_hf(p["occ"])
+    E, g = st.energy_grad(ham, p["ops"], p["theta"])
+    assert abs(E - Eref) <= TOL[dtype]["E"]
+    assert np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
+    assert np.max(np.abs(st.rdm1() - rdm_ref)) <= TOL[dtype]["rdm"]
+
+
+@pytest.fixture(scope="module")
+def config3_oracle():
+    p = inputs.config_problem(3)
+    sec = _oracle_problem(p)
+    psi0 = A.hf_state(sec, p["occ"])
+    E, g = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], p["theta"], psi0)
+    rdm = A.rdm1(sec, A.apply_ansatz(sec, p["ops"], p["theta"], psi0))
+    return p, E, g, rdm
+
+
+# ---------------------------------------------------------------- options, edges, errors
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_checkpoints_and_byte_cap(dtype):
+    p = inputs.make_problem(14, 4, 50, seed=77)
+    sec = _oracle_problem(p)
+    theta = p["theta"] * 4
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, A.hf_state(sec, p["occ"]))
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    for interval, cap in [(7, 0), (1, 0), (5, 6 * (1 << 14) * (8 if dtype == "c64" else 16))]:
+        st = _gpu_state(14, dtype)
+        st.set_option(sv.SV_OPT_CHECKPOINT_INTERVAL, interval)
+        if cap:
+            st.set_option(sv.SV_OPT_MAX_BYTES, cap + (1 << 22))
+        st.prepare_hf(p["occ"])
+        E, g = st.energy_grad(ham, p["ops"], theta)
+        assert abs(E - Eref) <= TOL[dtype]["E"]
+        assert np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
+
+
+def test_edge_cases():
+    # no operators: E is the reference energy, empty gradient
+    p = inputs.make_problem(8, 2, "uccsd", 3)
+    sec = _oracle_problem(p)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(8, "c128")
+    st.prepare_hf(p["occ"])
+    E, g = st.energy_grad(ham, p["ops"][:0], [])
+    assert abs(E - A.energy(sec, p["h"], p["eri"], p["e_nuc"], A.hf_state(sec, p["occ"]))) <= 1e-12 and len(g) == 0
+    # vacuum and fully occupied registers; the smallest register (one orbital)
+    for n, occ in [(8, []), (8, list(range(8))), (2, [0, 1]), (2, [1])]:
+        q = inputs.make_problem(n, 2, "uccsd", 4)
+        na = sum(1 for j in occ if j % 2 == 0)
+        nb = len(occ) - na
+        s2 = oracle.Sector(n, na, nb)
+        e_ref = A.energy(s2, q["h"], q["eri"], q["e_nuc"], A.hf_state(s2, occ))
+        hq = sv.Hamiltonian(q["h"], q["eri"], q["e_nuc"])
+        st2 = _gpu_state(n, "c128")
+        st2.prepare_hf(occ)
+        assert abs(st2.energy(hq) - e_ref) <= 1e-12
+        r = st2.rdm1()
+        assert abs(np.trace(r[0]).real - na) < 1e-12 and abs(np.trace(r[1]).real - nb) < 1e-12
+
+
+def test_deterministic_reruns():
+    p = inputs.config_problem(2)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(p["n_qubits"], "c64")
+    st.prepare_hf(p["occ"])
+    E1, g1 = st.energy_grad(ham, p["ops"], p["theta"])
+    E2, g2 = st.energy_grad(ham, p["ops"], p["theta"])
+    assert E1 == E2 and np.array_equal(g1, g2)
+
+
+def test_errors_are_reported_not_raised_on_device():
+    p = inputs.config_problem(1)
+    st = _gpu_state(8, "c64")
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    with pytest.raises(sv.SvError) as e:
+        st.energy(ham)                       # no prepared state
+    assert e.value.status == 5
+    st.prepare_hf(p["occ"])
+    for bad in [(2, 1, 0, 2, 3), (2, 0, 1, 2, 2), (1, 0, -1, 1, -1), (2, 0, 1, 2, 9), (3, 0, 1, 2, 3)]:
+        with pytest.raises(sv.SvError) as e:
+            st.apply_ansatz(np.array([bad], np.int32), [0.1])
+        assert e.value.status == 1
+    with pytest.raises(sv.SvError):
+        st.apply_ansatz(p["ops"][:1], [float("nan")])
+    with pytest.raises(sv.SvError):
+        st.prepare_hf([0, 0])
+    v = np.zeros(256, np.complex64)
+    v[3] = 1.0
+    with pytest.raises(sv.SvError):
+        st.prepare_state(v, 2, 0)            # x = 3 has one alpha and one beta electron
+    big = sv.Hamiltonian(*inputs.synthetic_integrals(5, np.random.default_rng(0)))
+    with pytest.raises(sv.SvError):
+        st.energy(big)                       # n_orb mismatch
+    # the handle still works after argument errors
+    st.apply_ansatz(p["ops"], p["theta"])
+    assert np.isfinite(st.energy(ham))
