@@ -174,8 +174,17 @@ def run_reference(args, rank, world):
     return 0
 
 
+def problem(args):
+    from paper_2405_11567_gb300 import inputs
+    if args.qubits:
+        ne = 2 * max(1, round(args.qubits / 6))
+        return inputs.make_problem(args.qubits, ne, 200, 1000 + CONFIG_ID)
+    return inputs.config_problem(CONFIG_ID)
+
+
 def workload_config(p):
-    return {"workload": "n30_ne10_adapt200_synthetic", "n_qubits": p["n_qubits"], "n_electrons": p["n_elec"],
+    return {"workload": "n%d_ne%d_adapt%d_synthetic" % (p["n_qubits"], p["n_elec"], len(p["ops"])),
+            "n_qubits": p["n_qubits"], "n_electrons": p["n_elec"],
             "n_ops": int(len(p["ops"])), "seed": p["seed"],
             "step": "prepare_hf + energy_grad (forward, sigma, adjoint) + rdm1",
             "l2": "inputs larger than L2 (state vector 8 GiB complex64 / 16 GiB complex128)"}
@@ -193,7 +202,7 @@ def run_ours(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    p = inputs.config_problem(CONFIG_ID)
+    p = problem(args)
     n, L = p["n_qubits"], len(p["ops"])
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
     stream = torch.cuda.Stream()
@@ -290,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
             "max_abs_dg": float(np.max(np.abs(r64["out"]["g"] - r128["out"]["g"]))),
             "max_abs_drdm": float(np.max(np.abs(r64["out"]["rdm"] - r128["out"]["rdm"]))),
             "E_fp64": r128["out"]["E"]}
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and not args.qubits:
         import oracle
         v, sample, _ = oracle_eval_sample(p)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
@@ -307,6 +316,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-c128", action="store_true", help="skip the complex128 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--qubits", type=int, default=0,
+                    help="profiling only: a smaller register (same generator, n/3 rounded to even electrons, "
+                         "200 operators); the bench line is then not the headline workload")
     args = ap.parse_args()
     rank, world, local_rank = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":

@@ -174,8 +174,11 @@ typedef enum {
                                        (0 = none; default 0) */
     SV_OPT_MAX_BYTES = 2,           /* cap on device bytes this handle may allocate
                                        (0 = no cap); checkpoints are dropped to fit */
-    SV_OPT_EXPECT_VARIANT = 3,      /* 0 auto, 1 sector gather, 2 tiled passes */
-    SV_OPT_RDM_VARIANT = 4,         /* 0 auto, 1 sector gather, 2 tiled passes */
+    SV_OPT_EXPECT_VARIANT = 3,      /* 0 auto (= 2); 1 record scan: one thread per sector
+                                       determinant tests every mask group; 2 string rows:
+                                       compact alpha/beta-string matrix, one block per
+                                       beta string */
+    SV_OPT_RDM_VARIANT = 4,         /* 0 auto, 1 sector gather (only variant so far) */
     SV_OPT_PROFILE = 5              /* 1: record CUDA events around each phase (sv_phase_times) */
 } sv_option;
 

@@ -56,45 +56,133 @@ __global__ void k_set_basis(cplx<R> *psi, uint32_t x) {
     psi[x] = mk<R>(R(1), R(0));
 }
 
+// ---------------------------------------------------------------- vector access
+
+// V consecutive amplitudes starting at a V-aligned index, moved as 16-byte words
+// (complex64: V = 2 or 4 -> one or two float4; complex128: one double2 each).
+template <typename R, int V> struct VecIO;
+
+template <int V> struct VecIO<float, V> {
+    static __device__ __forceinline__ void ld(const float2 *__restrict__ p, float2 (&v)[V]) {
+        if constexpr (V == 1) {
+            v[0] = p[0];
+        } else {
+            #pragma unroll
+            for (int i = 0; i < V / 2; ++i) {
+                float4 f = reinterpret_cast<const float4 *>(p)[i];
+                v[2 * i] = make_float2(f.x, f.y);
+                v[2 * i + 1] = make_float2(f.z, f.w);
+            }
+        }
+    }
+    static __device__ __forceinline__ void st(float2 *__restrict__ p, const float2 (&v)[V]) {
+        if constexpr (V == 1) {
+            p[0] = v[0];
+        } else {
+            #pragma unroll
+            for (int i = 0; i < V / 2; ++i)
+                reinterpret_cast<float4 *>(p)[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+        }
+    }
+};
+
+template <int V> struct VecIO<double, V> {
+    static __device__ __forceinline__ void ld(const double2 *__restrict__ p, double2 (&v)[V]) {
+        #pragma unroll
+        for (int i = 0; i < V; ++i) v[i] = p[i];
+    }
+    static __device__ __forceinline__ void st(double2 *__restrict__ p, const double2 (&v)[V]) {
+        #pragma unroll
+        for (int i = 0; i < V; ++i) p[i] = v[i];
+    }
+};
+
+template <typename R, int V>
+__device__ __forceinline__ void ld_vec(const cplx<R> *__restrict__ p, cplx<R> (&v)[V]) { VecIO<R, V>::ld(p, v); }
+template <typename R, int V>
+__device__ __forceinline__ void st_vec(cplx<R> *__restrict__ p, const cplx<R> (&v)[V]) { VecIO<R, V>::st(p, v); }
+
 // ---------------------------------------------------------------- forward rotation
 
-template <typename R, int NB>
-__global__ void __launch_bounds__(kThreads) k_rotate(cplx<R> *__restrict__ psi, uint32_t npairs, OpArgs a) {
+// Each thread owns groups of V consecutive pair indices; the lowest mask position is
+// >= log2(V), so a group maps to V consecutive amplitudes on each side of the pair
+// and the sign is the same across the group only if no sign-mask bit lies below
+// log2(V) -- it is therefore evaluated per amplitude.  Two groups per iteration keep
+// four independent vector loads in flight per thread.
+template <typename R, int NB, int V>
+__global__ void __launch_bounds__(kThreads) k_rotate(cplx<R> *__restrict__ psi, uint32_t ngroups, OpArgs a) {
     const R c = (R)a.c, sn = (R)a.s;
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < npairs; k += stride) {
-        uint32_t x = pair_index<NB>(k, a);
-        uint32_t xp = x ^ a.m;
-        R ss = (__popc(x & a.sm) & 1) ? -sn : sn;
-        cplx<R> u = psi[x], v = psi[xp];
-        psi[x] = mk<R>(c * u.x - ss * v.x, c * u.y - ss * v.y);
-        psi[xp] = mk<R>(c * v.x + ss * u.x, c * v.y + ss * u.y);
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += 2 * stride) {
+        const uint32_t g2 = g + stride;
+        const bool two = g2 < ngroups;
+        const uint32_t x = pair_index<NB>(g * V, a), x2 = two ? pair_index<NB>(g2 * V, a) : x;
+        cplx<R> u[V], v[V], u2[V], v2[V];
+        ld_vec<R, V>(psi + x, u);
+        ld_vec<R, V>(psi + (x ^ a.m), v);
+        if (two) {
+            ld_vec<R, V>(psi + x2, u2);
+            ld_vec<R, V>(psi + (x2 ^ a.m), v2);
+        }
+        #pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const R ss = (__popc((x + i) & a.sm) & 1) ? -sn : sn;
+            cplx<R> p = u[i], q = v[i];
+            u[i] = mk<R>(c * p.x - ss * q.x, c * p.y - ss * q.y);
+            v[i] = mk<R>(c * q.x + ss * p.x, c * q.y + ss * p.y);
+        }
+        st_vec<R, V>(psi + x, u);
+        st_vec<R, V>(psi + (x ^ a.m), v);
+        if (two) {
+            #pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const R ss = (__popc((x2 + i) & a.sm) & 1) ? -sn : sn;
+                cplx<R> p = u2[i], q = v2[i];
+                u2[i] = mk<R>(c * p.x - ss * q.x, c * p.y - ss * q.y);
+                v2[i] = mk<R>(c * q.x + ss * p.x, c * q.y + ss * p.y);
+            }
+            st_vec<R, V>(psi + x2, u2);
+            st_vec<R, V>(psi + (x2 ^ a.m), v2);
+        }
     }
 }
 
 // ---------------------------------------------------------------- adjoint step
 
-template <typename R, int NB>
+template <typename R, int NB, int V>
 __global__ void __launch_bounds__(kThreads) k_adjoint(cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam,
-                                                      uint32_t npairs, OpArgs a, double *__restrict__ partial) {
+                                                      uint32_t ngroups, OpArgs a, double *__restrict__ partial) {
     __shared__ double red[kThreads / 32];
     const R c = (R)a.c, sn = (R)a.s;
     const uint32_t stride = gridDim.x * blockDim.x;
     double acc = 0.0;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < npairs; k += stride) {
-        uint32_t x = pair_index<NB>(k, a);
-        uint32_t xp = x ^ a.m;
-        const bool neg = __popc(x & a.sm) & 1;
-        cplx<R> u = psi[x], v = psi[xp], lu = lam[x], lv = lam[xp];
-        // <lambda|G psi> on the pair: conj(lu) * (-s v) + conj(lv) * (s u); real part
-        R t = (lv.x * u.x + lv.y * u.y) - (lu.x * v.x + lu.y * v.y);
-        acc += (double)(neg ? -t : t);
-        // U^dagger: psi'[x] = c u + s sn v ; psi'[x'] = c v - s sn u
-        R ss = neg ? -sn : sn;
-        psi[x] = mk<R>(c * u.x + ss * v.x, c * u.y + ss * v.y);
-        psi[xp] = mk<R>(c * v.x - ss * u.x, c * v.y - ss * u.y);
-        lam[x] = mk<R>(c * lu.x + ss * lv.x, c * lu.y + ss * lv.y);
-        lam[xp] = mk<R>(c * lv.x - ss * lu.x, c * lv.y - ss * lu.y);
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+        const uint32_t x = pair_index<NB>(g * V, a), xp = x ^ a.m;
+        cplx<R> u[V], v[V], lu[V], lv[V];
+        ld_vec<R, V>(psi + x, u);
+        ld_vec<R, V>(psi + xp, v);
+        ld_vec<R, V>(lam + x, lu);
+        ld_vec<R, V>(lam + xp, lv);
+        R t = 0;
+        #pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const bool neg = __popc((x + i) & a.sm) & 1;
+            // <lambda|G psi> on the pair: conj(lu) (-s v) + conj(lv) (s u); real part
+            R ti = (lv[i].x * u[i].x + lv[i].y * u[i].y) - (lu[i].x * v[i].x + lu[i].y * v[i].y);
+            t += neg ? -ti : ti;
+            // U^dagger: psi'[x] = c u + s sn v ; psi'[x'] = c v - s sn u  (lambda alike)
+            const R ss = neg ? -sn : sn;
+            cplx<R> p = u[i], q = v[i], lp = lu[i], lq = lv[i];
+            u[i] = mk<R>(c * p.x + ss * q.x, c * p.y + ss * q.y);
+            v[i] = mk<R>(c * q.x - ss * p.x, c * q.y - ss * p.y);
+            lu[i] = mk<R>(c * lp.x + ss * lq.x, c * lp.y + ss * lq.y);
+            lv[i] = mk<R>(c * lq.x - ss * lp.x, c * lq.y - ss * lp.y);
+        }
+        acc += (double)t;
+        st_vec<R, V>(psi + x, u);
+        st_vec<R, V>(psi + xp, v);
+        st_vec<R, V>(lam + x, lu);
+        st_vec<R, V>(lam + xp, lv);
     }
     double s = block_sum(acc, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -128,16 +216,34 @@ cudaError_t launch_set_basis(void *psi, int dtype, uint32_t x, cudaStream_t st) 
     return cudaGetLastError();
 }
 
+// Vector width: as many consecutive amplitudes as fit in 32 bytes, limited by the
+// lowest mask position (the pairs of a group must be consecutive on both sides).
+static int vec_log2(int dtype, const OpDesc &d, int n) {
+    int vmax = dtype == SV_C64 ? 2 : 1;
+    int v = d.pos[0] < vmax ? d.pos[0] : vmax;
+    while (v > 0 && (n - d.nbits) < v) --v;
+    return v;
+}
+
+template <typename R, int NB>
+static void rot_v(void *psi, int v, uint32_t npairs, OpArgs a, int sm_count, cudaStream_t st) {
+    uint32_t ng = npairs >> v;
+    int grid = rotate_grid((ng + 1) / 2, sm_count);
+    if (v == 0) k_rotate<R, NB, 1><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, ng, a);
+    else if (v == 1) k_rotate<R, NB, 2><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, ng, a);
+    else k_rotate<R, NB, 4><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, ng, a);
+}
+
 cudaError_t launch_rotate(void *psi, int dtype, int n, const OpDesc &d, int sm_count, cudaStream_t st) {
     OpArgs a = to_args(d);
     uint32_t npairs = (uint32_t)(1ull << (n - d.nbits));
-    int grid = rotate_grid(npairs, sm_count);
+    int v = vec_log2(dtype, d, n);
     if (dtype == SV_C64) {
-        if (d.nbits == 2) k_rotate<float, 2><<<grid, kThreads, 0, st>>>((float2 *)psi, npairs, a);
-        else k_rotate<float, 4><<<grid, kThreads, 0, st>>>((float2 *)psi, npairs, a);
+        if (d.nbits == 2) rot_v<float, 2>(psi, v, npairs, a, sm_count, st);
+        else rot_v<float, 4>(psi, v, npairs, a, sm_count, st);
     } else {
-        if (d.nbits == 2) k_rotate<double, 2><<<grid, kThreads, 0, st>>>((double2 *)psi, npairs, a);
-        else k_rotate<double, 4><<<grid, kThreads, 0, st>>>((double2 *)psi, npairs, a);
+        if (d.nbits == 2) rot_v<double, 2>(psi, v, npairs, a, sm_count, st);
+        else rot_v<double, 4>(psi, v, npairs, a, sm_count, st);
     }
     return cudaGetLastError();
 }
@@ -146,16 +252,27 @@ int adjoint_grid(int n, const OpDesc &d, int sm_count) {
     return rotate_grid(1ull << (n - d.nbits), sm_count);
 }
 
+template <typename R, int NB>
+static void adj_v(void *psi, void *lam, int v, uint32_t npairs, OpArgs a, int grid, double *partial,
+                  cudaStream_t st) {
+    uint32_t ng = npairs >> v;
+    if (v == 0) k_adjoint<R, NB, 1><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, (cplx<R> *)lam, ng, a, partial);
+    else if (v == 1) k_adjoint<R, NB, 2><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, (cplx<R> *)lam, ng, a, partial);
+    else k_adjoint<R, NB, 4><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, (cplx<R> *)lam, ng, a, partial);
+}
+
+// `grid` blocks write partial[0 .. grid); the caller gives every op the same grid.
 cudaError_t launch_adjoint(void *psi, void *lam, int dtype, int n, const OpDesc &d, int grid,
                            double *partial, cudaStream_t st) {
     OpArgs a = to_args(d);
     uint32_t npairs = (uint32_t)(1ull << (n - d.nbits));
+    int v = vec_log2(dtype, d, n);
     if (dtype == SV_C64) {
-        if (d.nbits == 2) k_adjoint<float, 2><<<grid, kThreads, 0, st>>>((float2 *)psi, (float2 *)lam, npairs, a, partial);
-        else k_adjoint<float, 4><<<grid, kThreads, 0, st>>>((float2 *)psi, (float2 *)lam, npairs, a, partial);
+        if (d.nbits == 2) adj_v<float, 2>(psi, lam, v, npairs, a, grid, partial, st);
+        else adj_v<float, 4>(psi, lam, v, npairs, a, grid, partial, st);
     } else {
-        if (d.nbits == 2) k_adjoint<double, 2><<<grid, kThreads, 0, st>>>((double2 *)psi, (double2 *)lam, npairs, a, partial);
-        else k_adjoint<double, 4><<<grid, kThreads, 0, st>>>((double2 *)psi, (double2 *)lam, npairs, a, partial);
+        if (d.nbits == 2) adj_v<double, 2>(psi, lam, v, npairs, a, grid, partial, st);
+        else adj_v<double, 4>(psi, lam, v, npairs, a, grid, partial, st);
     }
     return cudaGetLastError();
 }

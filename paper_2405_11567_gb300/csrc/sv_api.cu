@@ -32,8 +32,19 @@ int rdm_elements_bytes(int n, std::vector<uint8_t> &out);
 cudaError_t launch_rdm_gather(const void *psi, int dtype, const uint32_t *sector, uint64_t count,
                               const void *elems, int n_el, int grid, double *partial, cudaStream_t st);
 
+struct RowTables {
+    const uint32_t *sa, *sb;
+    const uint16_t *stra, *strb, *ra, *rb;
+    const void *eri, *hm, *Dt, *Jt;
+    int N, Da, Db;
+};
+cudaError_t launch_compact(const void *psi, void *C, int dtype, const uint32_t *sa, const uint32_t *sb, int Da,
+                           int Db, int sm_count, cudaStream_t st);
+cudaError_t launch_sigma_rows(const void *C, void *lam, int dtype, int n, const RowTables &T, const double *hdiag,
+                              const double *Jp, double e_shift, double *partial, cudaStream_t st);
+
 DevTables::~DevTables() {
-    void *ptrs[] = {dbl, sgl, W, hdiag, Jp, pass_dbl, pass_sgl, pass_W};
+    void *ptrs[] = {dbl, sgl, W, hdiag, Jp, eri_r, hm_r, Dt, Jt, pass_dbl, pass_sgl, pass_W};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -208,6 +219,70 @@ static sv_status ensure_sector(sv_handle h) {
     return SV_OK;
 }
 
+// String-row view of the (na, nb) sector: strings with na (nb) set bits among N,
+// ascending; their ranks; their spread over the even (odd) bit positions.
+static sv_status ensure_strings(sv_handle h) {
+    if (h->str_sa && h->str_na == h->na && h->str_nb == h->nb) return SV_OK;
+    if (h->str_sa) {
+        for (void *p : {(void *)h->str_sa, (void *)h->str_sb, (void *)h->str_a, (void *)h->str_b,
+                        (void *)h->rank_a, (void *)h->rank_b})
+            cudaFree(p);
+        h->bytes_owned -= std::min<uint64_t>(h->bytes_owned, h->str_bytes);
+        h->str_sa = h->str_sb = nullptr;
+    }
+    const int N = h->n / 2;
+    auto strings = [&](int k, std::vector<uint16_t> &str, std::vector<uint16_t> &rank) {
+        rank.assign((size_t)1 << N, 0xFFFFu);
+        str.clear();
+        for (uint32_t s = 0; s < (1u << N); ++s)
+            if (__builtin_popcount(s) == k) {
+                rank[s] = (uint16_t)str.size();
+                str.push_back((uint16_t)s);
+            }
+    };
+    std::vector<uint16_t> sa16, sb16, ra, rb;
+    strings(h->na, sa16, ra);
+    strings(h->nb, sb16, rb);
+    std::vector<uint32_t> spa(sa16.size()), spb(sb16.size());
+    for (size_t i = 0; i < sa16.size(); ++i) {
+        uint32_t x = 0;
+        for (int p = 0; p < N; ++p) if ((sa16[i] >> p) & 1u) x |= 1u << (2 * p);
+        spa[i] = x;
+    }
+    for (size_t i = 0; i < sb16.size(); ++i) {
+        uint32_t x = 0;
+        for (int p = 0; p < N; ++p) if ((sb16[i] >> p) & 1u) x |= 1u << (2 * p + 1);
+        spb[i] = x;
+    }
+    size_t bytes = 0;
+    auto up = [&](void **dst, const void *src, size_t nb) -> sv_status {
+        SV_TRY(dev_alloc(h, dst, std::max<size_t>(nb, 16), "string tables"));
+        bytes += std::max<size_t>(nb, 16);
+        SV_CUDA(h, cudaMemcpy(*dst, src, nb, cudaMemcpyHostToDevice));
+        return SV_OK;
+    };
+    SV_TRY(up((void **)&h->str_sa, spa.data(), spa.size() * 4));
+    SV_TRY(up((void **)&h->str_sb, spb.data(), spb.size() * 4));
+    SV_TRY(up((void **)&h->str_a, sa16.data(), sa16.size() * 2));
+    SV_TRY(up((void **)&h->str_b, sb16.data(), sb16.size() * 2));
+    SV_TRY(up((void **)&h->rank_a, ra.data(), ra.size() * 2));
+    SV_TRY(up((void **)&h->rank_b, rb.data(), rb.size() * 2));
+    h->str_bytes = bytes;
+    h->Da = (int)sa16.size();
+    h->Db = (int)sb16.size();
+    h->str_na = h->na;
+    h->str_nb = h->nb;
+    size_t cb = (size_t)h->Da * h->Db * h->amp_bytes;
+    if (h->Cbuf_bytes < cb) {
+        dev_free(h, h->Cbuf, h->Cbuf_bytes);
+        h->Cbuf = nullptr;
+        h->Cbuf_bytes = 0;
+        SV_TRY(dev_alloc(h, &h->Cbuf, std::max<size_t>(cb, 16), "compact sector amplitudes"));
+        h->Cbuf_bytes = std::max<size_t>(cb, 16);
+    }
+    return SV_OK;
+}
+
 // ---------------------------------------------------------------- Hamiltonian tables
 
 template <typename R>
@@ -231,6 +306,21 @@ static sv_status upload_tables(sv_handle h, sv_ham_handle ham, DevTables &T) {
     SV_TRY(up(&T.W, ht.W.data(), ht.W.size() * sizeof(R)));
     SV_TRY(up((void **)&T.hdiag, ht.hdiag.data(), ht.hdiag.size() * sizeof(double)));
     SV_TRY(up((void **)&T.Jp, ht.Jp.data(), ht.Jp.size() * sizeof(double)));
+    // spatial integrals in the state precision for the string-row kernel
+    const int N = ham->n_orb;
+    std::vector<R> eri(ham->eri.begin(), ham->eri.end()), hm(ham->h.begin(), ham->h.end());
+    std::vector<R> Dt((size_t)N * N * N), Jt((size_t)N * N * N);
+    auto E = [&](int p, int q, int r, int s) { return ham->eri[(((size_t)p * N + q) * N + r) * N + s]; };
+    for (int q = 0; q < N; ++q)
+        for (int p = 0; p < N; ++p)
+            for (int k = 0; k < N; ++k) {
+                Jt[((size_t)q * N + p) * N + k] = (R)E(q, p, k, k);
+                Dt[((size_t)q * N + p) * N + k] = (R)(E(q, p, k, k) - E(q, k, k, p));
+            }
+    SV_TRY(up(&T.eri_r, eri.data(), eri.size() * sizeof(R)));
+    SV_TRY(up(&T.hm_r, hm.data(), hm.size() * sizeof(R)));
+    SV_TRY(up(&T.Dt, Dt.data(), Dt.size() * sizeof(R)));
+    SV_TRY(up(&T.Jt, Jt.data(), Jt.size() * sizeof(R)));
     return SV_OK;
 }
 
@@ -336,6 +426,23 @@ static void plan_checkpoints(sv_handle h, size_t L) {
 // <psi|(H - c)|psi> and <psi|psi> into dout[out_off], dout[out_off + 1] (device),
 // and sigma = (H - c) psi into `sigma` when it is not NULL.
 static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void *sigma, double c, int out_off) {
+    if (h->expect_variant != 1) {
+        // string rows (default)
+        SV_TRY(ensure_strings(h));
+        SV_TRY(ensure_partials(h, 2 * (size_t)h->Db));
+        if (sigma) SV_CUDA(h, cudaMemsetAsync(sigma, 0, vec_bytes(h), h->stream));
+        SV_CUDA(h, launch_compact(h->psi, h->Cbuf, h->dtype, h->str_sa, h->str_sb, h->Da, h->Db, h->sm_count,
+                                  h->stream));
+        h->launches++;
+        RowTables R{h->str_sa, h->str_sb, h->str_a, h->str_b, h->rank_a, h->rank_b,
+                    T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db};
+        SV_CUDA(h, launch_sigma_rows(h->Cbuf, sigma, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
+                                     h->partials, h->stream));
+        h->launches++;
+        SV_CUDA(h, launch_reduce_rows(h->partials, 2, h->Db, h->dout + out_off, h->stream));
+        h->launches++;
+        return SV_OK;
+    }
     SV_TRY(ensure_sector(h));
     int grid = expect_gather_grid(h->sector_len, h->sm_count);
     SV_TRY(ensure_partials(h, 2 * (size_t)grid));
@@ -424,6 +531,10 @@ sv_status sv_destroy(sv_handle h) {
     dev_free(h, h->saved, vec_bytes(h));
     for (void *p : h->ckpt) dev_free(h, p, vec_bytes(h));
     dev_free(h, h->sector, h->sector_len * sizeof(uint32_t));
+    for (void *p : {(void *)h->str_sa, (void *)h->str_sb, (void *)h->str_a, (void *)h->str_b,
+                    (void *)h->rank_a, (void *)h->rank_b})
+        if (p) cudaFree(p);
+    dev_free(h, h->Cbuf, h->Cbuf_bytes);
     dev_free(h, h->partials, h->partials_cap * sizeof(double));
     dev_free(h, h->dout, h->dout_cap * sizeof(double));
     if (h->hpinned) cudaFreeHost(h->hpinned);
@@ -598,9 +709,15 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
         else cudaGetLastError();
     }
     const int G = rotate_grid(1ull << (h->n - 2), h->sm_count);
-    SV_TRY(ensure_sector(h));
-    const int Ge = expect_gather_grid(h->sector_len, h->sm_count);
-    SV_TRY(ensure_partials(h, std::max<size_t>((size_t)G * std::max<size_t>(L, 1), 2 * (size_t)Ge)));
+    size_t need = 0;
+    if (h->expect_variant == 1) {
+        SV_TRY(ensure_sector(h));
+        need = 2 * (size_t)expect_gather_grid(h->sector_len, h->sm_count);
+    } else {
+        SV_TRY(ensure_strings(h));
+        need = 2 * (size_t)h->Db;
+    }
+    SV_TRY(ensure_partials(h, std::max<size_t>((size_t)G * std::max<size_t>(L, 1), need)));
     plan_checkpoints(h, L);
     h->prepared = false;
     SV_TRY(mark(h, 0));

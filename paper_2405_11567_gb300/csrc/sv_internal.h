@@ -91,6 +91,11 @@ struct DevTables {
     void *W = nullptr;     // R[n_sgl * n]
     double *hdiag = nullptr;
     double *Jp = nullptr;
+    // string-row tables (k_rows.cu), state precision
+    void *eri_r = nullptr;  // [N^4] (pq|rs)
+    void *hm_r = nullptr;   // [N^2] h_pq
+    void *Dt = nullptr;     // [N^3] (qp|kk) - (qk|kp)
+    void *Jt = nullptr;     // [N^3] (qp|kk)
     // tiled-pass schedule (k_expect.cu); empty until first needed
     struct Pass {
         uint32_t S;        // local qubit set (bit mask over storage positions)
@@ -146,6 +151,13 @@ struct sv_ctx {
     uint32_t *sector = nullptr;
     uint64_t sector_len = 0;
     int sector_na = -1, sector_nb = -1;
+    // string-row view of the sector (k_rows.cu): alpha / beta strings, ranks, spreads
+    uint32_t *str_sa = nullptr, *str_sb = nullptr;
+    uint16_t *str_a = nullptr, *str_b = nullptr, *rank_a = nullptr, *rank_b = nullptr;
+    int Da = 0, Db = 0, str_na = -1, str_nb = -1;
+    size_t str_bytes = 0;
+    void *Cbuf = nullptr;      // compact amplitudes [Db][Da]
+    size_t Cbuf_bytes = 0;
     // reduction scratch
     double *partials = nullptr;
     size_t partials_cap = 0;   // doubles

@@ -295,3 +295,56 @@ def test_errors_are_reported_not_raised_on_device():
     # the handle still works after argument errors
     st.apply_ansatz(p["ops"], p["theta"])
     assert np.isfinite(st.energy(ham))
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_expectation_variants_match_oracle(variant, dtype):
+    """Record scan (1) and string rows (2) on an open-shell complex state and on config 2."""
+    n, na, nb = 12, 3, 2
+    p = inputs.make_problem(n, 4, 30, seed=88)
+    rng = np.random.default_rng(11)
+    dense0 = inputs.random_sector_state(n, na, nb, rng)
+    sec = oracle.Sector(n, na, nb)
+    psi0 = dense0[sec.dets.astype(np.int64)]
+    theta = p["theta"] * 7
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(n, dtype)
+    st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
+    st.prepare_state(dense0.astype(np.complex64 if dtype == "c64" else np.complex128), na, nb)
+    E, g = st.energy_grad(ham, p["ops"], theta)
+    assert abs(E - Eref) <= TOL[dtype]["E"]
+    assert np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
+    q = inputs.config_problem(2)
+    s2 = _oracle_problem(q)
+    Eq, gq = A.energy_grad(s2, q["h"], q["eri"], q["e_nuc"], q["ops"], q["theta"], A.hf_state(s2, q["occ"]))
+    hq = sv.Hamiltonian(q["h"], q["eri"], q["e_nuc"])
+    st2 = _gpu_state(q["n_qubits"], dtype)
+    st2.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
+    st2.prepare_hf(q["occ"])
+    E2, g2 = st2.energy_grad(hq, q["ops"], q["theta"])
+    assert abs(E2 - Eq) <= TOL[dtype]["E"]
+    assert np.max(np.abs(g2 - gq)) <= TOL[dtype]["g"]
+
+
+def test_sigma_vector_matches_oracle():
+    """At theta = 0 every gradient entry is 2 Re <(H - c) psi0| G_k psi0>, a projection of sigma
+    onto G_k psi0: a random complex start and many directions G_k probe sigma from both
+    expectation variants in complex128 to 1e-11."""
+    n = 12
+    p = inputs.make_problem(n, 4, "uccsd", seed=91)
+    sec = _oracle_problem(p)
+    rng = np.random.default_rng(2)
+    dense0 = inputs.random_sector_state(n, 2, 2, rng)
+    psi0 = dense0[sec.dets.astype(np.int64)]
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    ops = p["ops"][::9]
+    zeros = np.zeros(len(ops))
+    _, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], ops, zeros, psi0)
+    for variant in (1, 2):
+        st = _gpu_state(n, "c128")
+        st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
+        st.prepare_state(dense0, 2, 2)
+        _, g = st.energy_grad(ham, ops, zeros)
+        assert np.max(np.abs(g - gref)) <= 1e-11
