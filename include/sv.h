@@ -124,8 +124,21 @@ sv_status sv_prepare_state(sv_handle h, const void *amplitudes_host, int n_alpha
 sv_status sv_get_state(sv_handle h, void *amplitudes_host);
 
 /* Device pointer of the state vector (2^n amplitudes), for callers that read
- * it on the GPU.  Valid until sv_destroy. */
+ * it on the GPU.  Valid until sv_destroy.  Amplitudes are stored in the handle's
+ * layout (sv_get_layout): the amplitude of basis state x sits at the address
+ * whose bit storage_of_qubit[q] is bit q of x. */
 sv_status sv_state_device_ptr(sv_handle h, void **psi_dev);
+
+/* Storage layout: bit storage_of_qubit[q] of an amplitude's device address holds
+ * qubit q (a permutation of [0, n); identity after sv_create).  A rotation whose
+ * lowest address bit is b moves runs of 2^b consecutive amplitudes, so placing
+ * rarely excited qubits on the low bits keeps the streaming kernels' runs long.
+ * sv_set_layout moves the current state (and a stored reference) to the new
+ * layout on the device and turns SV_OPT_LAYOUT_AUTO off.  Host-side views
+ * (sv_prepare_state, sv_get_state, every returned value) are always in qubit
+ * order.  No counterpart in the paper: a storage choice of this library. */
+sv_status sv_set_layout(sv_handle h, const int32_t *storage_of_qubit);
+sv_status sv_get_layout(sv_handle h, int32_t *storage_of_qubit);
 
 /* ---- Hamiltonian handles -------------------------------------------------- */
 
@@ -166,6 +179,52 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
  * im_out likewise Im n (im_out may be NULL), N = n_qubits/2, sigma 0 = alpha. */
 sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out);
 
+/* ---- many small problems in one launch --------------------------------------- */
+
+typedef struct sv_batch *sv_batch_handle;
+
+/* One independent problem of a batch.  n_qubits even, 2..32 (n_qubits/2 <= 16
+ * orbitals and a sector of at most 2^22 determinants); occ: the reference
+ * determinant's occupied spin-orbitals; h, eri, e_nuc: integrals as for
+ * sv_ham_create (checked the same way); ops: its ansatz (rules of sv_excitation).
+ * The library copies everything at sv_batch_create. */
+typedef struct {
+    int32_t n_qubits;
+    const int32_t *occ;
+    int32_t n_occ;
+    const double *h;
+    const double *eri;
+    double e_nuc;
+    const sv_excitation *ops;
+    int32_t n_ops;
+} sv_instance;
+
+/* Plan a batch: tables, integrals and operators of every instance move to the
+ * device once; states are kept per block in compact (N_alpha, N_beta)-sector form.
+ * Work is ordered by estimated cost (largest first) and taken by the blocks of one
+ * persistent kernel.  cuda_stream may be NULL (the plan then owns a stream; the
+ * launch is captured in a CUDA graph, which the legacy default stream cannot
+ * hold).  No counterpart in the paper beyond running many emulations; the
+ * batched configuration of this library's workload list. */
+sv_status sv_batch_create(int n_inst, const sv_instance *inst, sv_dtype dtype, void *cuda_stream,
+                          sv_batch_handle *out);
+
+/* Energy and gradient of every instance for the angles theta (concatenated in
+ * instance order, sum of n_ops values): e_out[i] = E_i, grad_out (same layout as
+ * theta) = dE_i/dtheta.  One graph launch (angles up, kernel, results down), then
+ * a stream synchronisation.  SV_ERR_TIMEOUT when the time limit stopped the
+ * kernel early: the outputs of instances not run are NaN. */
+sv_status sv_batch_energy_grad(sv_batch_handle b, const double *theta, double *e_out, double *grad_out);
+
+/* Device-side time budget (ms, 0 = none): blocks stop taking new instances once it
+ * is spent (checked before each instance; no block ever waits on another). */
+sv_status sv_batch_set_time_limit(sv_batch_handle b, double ms);
+
+/* Kernels launched by this batch so far (one per sv_batch_energy_grad). */
+uint64_t sv_batch_launch_count(sv_batch_handle b);
+
+sv_status sv_batch_destroy(sv_batch_handle b);
+
 /* ---- options ------------------------------------------------------------------ */
 
 typedef enum {
@@ -179,7 +238,9 @@ typedef enum {
                                        compact alpha/beta-string matrix, one block per
                                        beta string */
     SV_OPT_RDM_VARIANT = 4,         /* 0 auto, 1 sector gather (only variant so far) */
-    SV_OPT_PROFILE = 5              /* 1: record CUDA events around each phase (sv_phase_times) */
+    SV_OPT_PROFILE = 5,             /* 1: record CUDA events around each phase (sv_phase_times) */
+    SV_OPT_LAYOUT_AUTO = 6          /* 1 (default): sv_energy_grad chooses the storage layout
+                                       from its operator list (sv_set_layout); 0: keep it */
 } sv_option;
 
 sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value);

@@ -1,0 +1,551 @@
+// k_batch.cu -- many independent small problems (uneven qubit counts) in one
+// persistent, graph-captured launch: reference preparation, the fermionic
+// ansatz, sigma = (H - c) psi and the energy, and the adjoint sweep for the
+// gradient, per instance ("Computational Details": ADAPT-VQE runs on many small
+// systems; the emulator's workload for every optimiser step).
+//
+// Each block takes instances from a work queue (one atomicAdd per instance, no
+// device-side waiting) in descending order of estimated cost, and runs the whole
+// pipeline for it on a compact state: the amplitudes of the instance's
+// (N_alpha, N_beta) sector in the string-row order C[rank(b)][rank(a)] (at 20
+// qubits and 6 electrons 14,400 amplitudes instead of 2^20), in a per-block
+// scratch slot that stays in L2.  The rotations pair every determinant that has
+// the excitation's "from" pattern with its partner (found by string ranks), the
+// sigma element is the same closed-form X-mask evaluation as the string-row
+// kernel (sv_sigma.cuh), and the gradient sums are float64 with fixed-order block
+// reductions, so an instance's results do not depend on which block ran it.
+//
+// An optional time budget makes every block stop taking new instances once the
+// budget is spent (checked with %globaltimer before each instance); the host then
+// reports SV_ERR_TIMEOUT and leaves the outputs of skipped instances as NaN.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "sv_internal.h"
+#include "sv_sigma.cuh"
+
+namespace svk {
+
+struct BatchOp {
+    uint32_t m, from, sm;  // qubit-space flip mask, "from" pattern, sign mask
+    uint32_t mab;          // low 16 bits: alpha-string flip mask, high 16: beta-string flip mask
+};
+
+struct BatchInst {
+    int n, N, Da, Db, L;
+    uint32_t hf;                 // compact index of the reference determinant
+    double shift;                // c of lambda = (H - c) psi
+    double e_shift;              // E_nuc - c
+    long long ops, cs;           // offsets into the op and (cos, sin) arrays
+    long long eri, hm, dt, jt;   // offsets into the state-precision integral arena
+    long long hd, jp;            // offsets into the float64 arena
+    long long sa, sb;            // offsets into the uint32 spread arena
+    long long stra, strb, ra, rb;  // offsets into the uint16 string arena
+    long long out;               // E at out, gradient at out + 1 ...
+};
+
+template <typename R>
+struct BatchArgs {
+    const BatchInst *inst;
+    const int *order;
+    int count;
+    const BatchOp *ops;
+    const cplx<R> *cs;           // (cos, sin) per op
+    const R *rarena;
+    const double *darena;
+    const uint32_t *u32;
+    const uint16_t *u16;
+    double *out;
+    cplx<R> *scratch;            // per block: psi then lambda, Dmax each
+    int Dmax;
+    int *ctrl;                   // [0] work counter, [1] timeout flag
+    unsigned long long budget_ns;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_batch(BatchArgs<R> B) {
+    __shared__ int s_inst;
+    __shared__ double red[2 * kThreads / 32];
+    __shared__ unsigned long long s_t0;
+    cplx<R> *psi = B.scratch + (size_t)blockIdx.x * 2 * B.Dmax;
+    cplx<R> *lam = psi + B.Dmax;
+    if (threadIdx.x == 0) s_t0 = global_ns();
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int next = -1;
+            if (B.budget_ns && global_ns() - s_t0 > B.budget_ns) {
+                atomicExch(&B.ctrl[1], 1);
+            } else {
+                int k = atomicAdd(&B.ctrl[0], 1);
+                if (k < B.count) next = B.order[k];
+            }
+            s_inst = next;
+        }
+        __syncthreads();
+        const int ii = s_inst;
+        if (ii < 0) break;
+        const BatchInst I = B.inst[ii];
+        SigmaTables<R> T;
+        T.sa = B.u32 + I.sa; T.sb = B.u32 + I.sb;
+        T.stra = B.u16 + I.stra; T.strb = B.u16 + I.strb; T.ra = B.u16 + I.ra; T.rb = B.u16 + I.rb;
+        T.eri = B.rarena + I.eri; T.hm = B.rarena + I.hm; T.Dt = B.rarena + I.dt; T.Jt = B.rarena + I.jt;
+        T.hdiag = B.darena + I.hd; T.Jp = B.darena + I.jp; T.e_shift = I.e_shift;
+        T.N = I.N; T.n = I.n; T.Da = I.Da; T.maskN = (1u << I.N) - 1u;
+        const int Da = I.Da, D = I.Da * I.Db;
+        // reference determinant
+        for (int i = threadIdx.x; i < D; i += blockDim.x) psi[i] = mk<R>(0, 0);
+        __syncthreads();
+        if (threadIdx.x == 0) psi[I.hf] = mk<R>(1, 0);
+        __syncthreads();
+        // forward sweep
+        for (int k = 0; k < I.L; ++k) {
+            const BatchOp op = B.ops[I.ops + k];
+            const cplx<R> csk = B.cs[I.cs + k];
+            for (int i = threadIdx.x; i < D; i += blockDim.x) {
+                const int Ib = i / Da, Ia = i - Ib * Da;
+                const uint32_t x = T.sa[Ia] | T.sb[Ib];
+                if ((x & op.m) != op.from) continue;
+                const int j = (int)T.rb[T.strb[Ib] ^ (op.mab >> 16)] * Da + T.ra[T.stra[Ia] ^ (op.mab & 0xFFFFu)];
+                const R ss = par(x & op.sm) ? -csk.y : csk.y;
+                const cplx<R> u = psi[i], v = psi[j];
+                psi[i] = mk<R>(csk.x * u.x - ss * v.x, csk.x * u.y - ss * v.y);
+                psi[j] = mk<R>(csk.x * v.x + ss * u.x, csk.x * v.y + ss * u.y);
+            }
+            __syncthreads();
+        }
+        // sigma and the energy
+        double e_acc = 0.0, n_acc = 0.0;
+        for (int i = threadIdx.x; i < D; i += blockDim.x) {
+            const int Ib = i / Da, Ia = i - Ib * Da;
+            const cplx<R> c0 = psi[i];
+            const cplx<R> s = sigma_at<R>(T, psi, Ia, Ib, c0);
+            lam[i] = s;
+            e_acc += (double)c0.x * (double)s.x + (double)c0.y * (double)s.y;
+            n_acc += (double)c0.x * (double)c0.x + (double)c0.y * (double)c0.y;
+        }
+        block_sum2(e_acc, n_acc, red);  // contains the barrier that publishes lambda
+        __shared__ double s_norm;
+        if (threadIdx.x == 0) {
+            s_norm = n_acc;
+            B.out[I.out] = I.shift + e_acc / n_acc;
+        }
+        __syncthreads();
+        const double nrm = s_norm;
+        // reverse sweep
+        for (int k = I.L - 1; k >= 0; --k) {
+            const BatchOp op = B.ops[I.ops + k];
+            const cplx<R> csk = B.cs[I.cs + k];
+            double g = 0.0;
+            for (int i = threadIdx.x; i < D; i += blockDim.x) {
+                const int Ib = i / Da, Ia = i - Ib * Da;
+                const uint32_t x = T.sa[Ia] | T.sb[Ib];
+                if ((x & op.m) != op.from) continue;
+                const int j = (int)T.rb[T.strb[Ib] ^ (op.mab >> 16)] * Da + T.ra[T.stra[Ia] ^ (op.mab & 0xFFFFu)];
+                const bool neg = par(x & op.sm);
+                const cplx<R> u = psi[i], v = psi[j], lu = lam[i], lv = lam[j];
+                const R t = (lv.x * u.x + lv.y * u.y) - (lu.x * v.x + lu.y * v.y);
+                g += (double)(neg ? -t : t);
+                const R ss = neg ? -csk.y : csk.y;
+                psi[i] = mk<R>(csk.x * u.x + ss * v.x, csk.x * u.y + ss * v.y);
+                psi[j] = mk<R>(csk.x * v.x - ss * u.x, csk.x * v.y - ss * u.y);
+                lam[i] = mk<R>(csk.x * lu.x + ss * lv.x, csk.x * lu.y + ss * lv.y);
+                lam[j] = mk<R>(csk.x * lv.x - ss * lu.x, csk.x * lv.y - ss * lu.y);
+            }
+            const double gs = block_sum(g, red);
+            if (threadIdx.x == 0) B.out[I.out + 1 + k] = 2.0 * gs / nrm;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace svk
+
+using namespace svk;
+
+namespace svk {
+void set_thread_error(const std::string &m);  // sv_api.cu: the message sv_last_error(NULL) returns
+}
+
+namespace {
+sv_status bfail(sv_status s, const std::string &m) {
+    set_thread_error(m);
+    return s;
+}
+
+template <typename R> cplx<R> mk_host(double c, double s);
+template <> float2 mk_host<float>(double c, double s) { return make_float2((float)c, (float)s); }
+template <> double2 mk_host<double>(double c, double s) { return make_double2(c, s); }
+}  // namespace
+
+struct sv_batch {
+    int n_inst = 0;
+    sv_dtype dtype = SV_C64;
+    cudaStream_t stream = nullptr;
+    int device = 0, sm_count = 148, grid = 0, Dmax = 0;
+    std::vector<int> L;
+    std::vector<long long> cs_off, out_off;
+    long long total_ops = 0, total_out = 0;
+    std::vector<void *> dev;  // every device allocation
+    BatchInst *d_inst = nullptr;
+    int *d_order = nullptr, *d_ctrl = nullptr;
+    BatchOp *d_ops = nullptr;
+    void *d_cs = nullptr, *d_r = nullptr, *d_scratch = nullptr;
+    double *d_d = nullptr, *d_out = nullptr;
+    uint32_t *d_u32 = nullptr;
+    uint16_t *d_u16 = nullptr;
+    void *h_cs = nullptr;
+    double *h_out = nullptr;
+    int *h_ctrl = nullptr;
+    unsigned long long budget_ns = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool own_stream = false;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+template <typename R>
+struct HostArena {
+    std::vector<R> r;
+    std::vector<double> d;
+    std::vector<uint32_t> u32;
+    std::vector<uint16_t> u16;
+};
+
+// String table set for (N, k electrons of one spin, spin offset 0 alpha / 1 beta).
+struct StrSet {
+    long long str, rank, spread;
+    int count;
+};
+
+template <typename R>
+sv_status build_plan(sv_batch *b, int n_inst, const sv_instance *inst) {
+    HostArena<R> A;
+    std::vector<BatchInst> hi(n_inst);
+    std::vector<BatchOp> hops;
+    std::vector<double> cost(n_inst);
+    std::map<std::string, StrSet> sets;
+    auto strset = [&](int N, int k, int spin) -> StrSet {
+        std::string key = std::to_string(N) + "/" + std::to_string(k) + "/" + std::to_string(spin);
+        auto it = sets.find(key);
+        if (it != sets.end()) return it->second;
+        StrSet s;
+        s.rank = (long long)A.u16.size();
+        A.u16.resize(A.u16.size() + ((size_t)1 << N), 0xFFFFu);
+        std::vector<uint16_t> strs;
+        for (uint32_t v = 0; v < (1u << N); ++v)
+            if (__builtin_popcount(v) == k) {
+                A.u16[s.rank + v] = (uint16_t)strs.size();
+                strs.push_back((uint16_t)v);
+            }
+        s.str = (long long)A.u16.size();
+        A.u16.insert(A.u16.end(), strs.begin(), strs.end());
+        s.spread = (long long)A.u32.size();
+        for (uint16_t v : strs) {
+            uint32_t x = 0;
+            for (int p = 0; p < N; ++p)
+                if ((v >> p) & 1u) x |= 1u << (2 * p + spin);
+            A.u32.push_back(x);
+        }
+        s.count = (int)strs.size();
+        sets[key] = s;
+        return s;
+    };
+    long long cs = 0, out = 0;
+    b->L.resize(n_inst);
+    b->cs_off.resize(n_inst);
+    b->out_off.resize(n_inst);
+    b->Dmax = 1;
+    for (int t = 0; t < n_inst; ++t) {
+        const sv_instance &in = inst[t];
+        const int n = in.n_qubits, N = n / 2;
+        if (n < 2 || n > 32 || (n & 1)) return bfail(SV_ERR_ARG, "instance qubit count must be even, 2..32");
+        if (N > 16) return bfail(SV_ERR_ARG, "instance too large for the batched kernel");
+        if (!in.h || !in.eri || (in.n_ops > 0 && !in.ops) || in.n_ops < 0 || in.n_occ < 0 || in.n_occ > n ||
+            (in.n_occ > 0 && !in.occ))
+            return bfail(SV_ERR_ARG, "bad instance description");
+        uint32_t ref = 0;
+        int na = 0, nb = 0;
+        for (int k = 0; k < in.n_occ; ++k) {
+            int j = in.occ[k];
+            if (j < 0 || j >= n || ((ref >> j) & 1u)) return bfail(SV_ERR_ARG, "bad reference occupation");
+            ref |= 1u << j;
+            (j & 1) ? ++nb : ++na;
+        }
+        StrSet sa = strset(N, na, 0), sb = strset(N, nb, 1);
+        const long long D = (long long)sa.count * sb.count;
+        if (D > (1 << 22)) return bfail(SV_ERR_ARG, "instance sector too large for the batched kernel");
+        b->Dmax = std::max<int>(b->Dmax, (int)D);
+        BatchInst I{};
+        I.n = n; I.N = N; I.Da = sa.count; I.Db = sb.count; I.L = in.n_ops;
+        I.sa = sa.spread; I.sb = sb.spread; I.stra = sa.str; I.strb = sb.str; I.ra = sa.rank; I.rb = sb.rank;
+        // reference index
+        uint32_t ra_str = 0, rb_str = 0;
+        for (int p = 0; p < N; ++p) {
+            if ((ref >> (2 * p)) & 1u) ra_str |= 1u << p;
+            if ((ref >> (2 * p + 1)) & 1u) rb_str |= 1u << p;
+        }
+        I.hf = (uint32_t)A.u16[sb.rank + rb_str] * sa.count + A.u16[sa.rank + ra_str];
+        // integrals: validated like sv_ham_create, then cast
+        sv_ham H;
+        H.n_orb = N;
+        H.e_nuc = in.e_nuc;
+        H.h.assign(in.h, in.h + (size_t)N * N);
+        H.eri.assign(in.eri, in.eri + (size_t)N * N * N * N);
+        for (int p = 0; p < N; ++p)
+            for (int q = 0; q < N; ++q)
+                if (std::fabs(H.h[p * N + q] - H.h[q * N + p]) > 1e-12 * std::max(1.0, std::fabs(H.h[p * N + q])))
+                    return bfail(SV_ERR_ARG, "instance h is not symmetric");
+        auto E = [&](int p, int q, int r, int s) { return H.eri[(((size_t)p * N + q) * N + r) * N + s]; };
+        for (int p = 0; p < N; ++p)
+            for (int q = 0; q < N; ++q)
+                for (int r = 0; r < N; ++r)
+                    for (int s = 0; s < N; ++s) {
+                        double v = E(p, q, r, s), tol = 1e-12 * std::max(1.0, std::fabs(v));
+                        if (!std::isfinite(v) || std::fabs(v - E(q, p, r, s)) > tol || std::fabs(v - E(p, q, s, r)) > tol ||
+                            std::fabs(v - E(r, s, p, q)) > tol)
+                            return bfail(SV_ERR_ARG, "instance eri lacks the 8-fold symmetry");
+                    }
+        I.shift = diag_energy(H, ref, n);
+        I.e_shift = in.e_nuc - I.shift;
+        I.eri = (long long)A.r.size();
+        for (double v : H.eri) A.r.push_back((R)v);
+        I.hm = (long long)A.r.size();
+        for (double v : H.h) A.r.push_back((R)v);
+        I.dt = (long long)A.r.size();
+        for (int q = 0; q < N; ++q)
+            for (int p = 0; p < N; ++p)
+                for (int k = 0; k < N; ++k) A.r.push_back((R)(E(q, p, k, k) - E(q, k, k, p)));
+        I.jt = (long long)A.r.size();
+        for (int q = 0; q < N; ++q)
+            for (int p = 0; p < N; ++p)
+                for (int k = 0; k < N; ++k) A.r.push_back((R)E(q, p, k, k));
+        HostTables<double> ht;
+        build_tables<double>(H, n, ht);
+        I.hd = (long long)A.d.size();
+        A.d.insert(A.d.end(), ht.hdiag.begin(), ht.hdiag.end());
+        I.jp = (long long)A.d.size();
+        A.d.insert(A.d.end(), ht.Jp.begin(), ht.Jp.end());
+        // operators, qubit space
+        I.ops = (long long)hops.size();
+        const int ident[32] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15,
+                               16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31};
+        for (int k = 0; k < in.n_ops; ++k) {
+            OpDesc d;
+            std::string why;
+            if (!make_op(in.ops[k], n, ident, d, why)) return bfail(SV_ERR_ARG, "instance op: " + why);
+            uint32_t ma = 0, mb = 0;
+            for (int p = 0; p < N; ++p) {
+                if ((d.m >> (2 * p)) & 1u) ma |= 1u << p;
+                if ((d.m >> (2 * p + 1)) & 1u) mb |= 1u << p;
+            }
+            hops.push_back(BatchOp{d.m, d.from, d.sm, ma | (mb << 16)});
+        }
+        I.cs = cs;
+        b->cs_off[t] = cs;
+        cs += in.n_ops;
+        I.out = out;
+        b->out_off[t] = out;
+        out += 1 + in.n_ops;
+        b->L[t] = in.n_ops;
+        hi[t] = I;
+        // cost: sector size x (connections + 3 sweeps over the operators)
+        const double conn = (double)na * (N - na) + (double)nb * (N - nb);
+        cost[t] = (double)D * (conn * conn + 3.0 * in.n_ops + 1.0);
+    }
+    b->total_ops = cs;
+    b->total_out = out;
+    std::vector<int> order(n_inst);
+    for (int t = 0; t < n_inst; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    // device arenas
+    auto up = [&](void **dst, const void *src, size_t bytes) -> sv_status {
+        cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(SV_ERR_OOM, "batch arena allocation failed");
+        }
+        b->dev.push_back(*dst);
+        if (bytes && src) {
+            e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return bfail(SV_ERR_CUDA, cudaGetErrorString(e));
+        }
+        return SV_OK;
+    };
+    sv_status s;
+    if ((s = up((void **)&b->d_inst, hi.data(), hi.size() * sizeof(BatchInst))) != SV_OK) return s;
+    if ((s = up((void **)&b->d_order, order.data(), order.size() * sizeof(int))) != SV_OK) return s;
+    if ((s = up((void **)&b->d_ops, hops.data(), hops.size() * sizeof(BatchOp))) != SV_OK) return s;
+    if ((s = up(&b->d_r, A.r.data(), A.r.size() * sizeof(R))) != SV_OK) return s;
+    if ((s = up((void **)&b->d_d, A.d.data(), A.d.size() * sizeof(double))) != SV_OK) return s;
+    if ((s = up((void **)&b->d_u32, A.u32.data(), A.u32.size() * sizeof(uint32_t))) != SV_OK) return s;
+    if ((s = up((void **)&b->d_u16, A.u16.data(), A.u16.size() * sizeof(uint16_t))) != SV_OK) return s;
+    if ((s = up(&b->d_cs, nullptr, std::max<long long>(cs, 1) * sizeof(cplx<R>))) != SV_OK) return s;
+    if ((s = up((void **)&b->d_out, nullptr, std::max<long long>(out, 1) * sizeof(double))) != SV_OK) return s;
+    if ((s = up((void **)&b->d_ctrl, nullptr, 2 * sizeof(int))) != SV_OK) return s;
+    b->grid = std::max(1, std::min(n_inst, b->sm_count * 2));
+    if ((s = up(&b->d_scratch, nullptr, (size_t)b->grid * 2 * b->Dmax * sizeof(cplx<R>))) != SV_OK) return s;
+    if (cudaMallocHost(&b->h_cs, std::max<long long>(cs, 1) * sizeof(cplx<R>)) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_out, std::max<long long>(out, 1) * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_ctrl, 2 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(SV_ERR_OOM, "pinned host allocation failed");
+    }
+    return SV_OK;
+}
+
+template <typename R>
+sv_status capture(sv_batch *b) {
+    BatchArgs<R> a;
+    a.inst = b->d_inst; a.order = b->d_order; a.count = b->n_inst; a.ops = b->d_ops;
+    a.cs = (const cplx<R> *)b->d_cs; a.rarena = (const R *)b->d_r; a.darena = b->d_d;
+    a.u32 = b->d_u32; a.u16 = b->d_u16; a.out = b->d_out; a.scratch = (cplx<R> *)b->d_scratch;
+    a.Dmax = b->Dmax; a.ctrl = b->d_ctrl; a.budget_ns = b->budget_ns;
+    cudaStream_t st = b->stream;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(SV_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+    cudaMemcpyAsync(b->d_cs, b->h_cs, std::max<long long>(b->total_ops, 1) * sizeof(cplx<R>), cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(b->d_ctrl, 0, 2 * sizeof(int), st);
+    k_batch<R><<<b->grid, kThreads, 0, st>>>(a);
+    cudaMemcpyAsync(b->h_out, b->d_out, std::max<long long>(b->total_out, 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                    st);
+    cudaMemcpyAsync(b->h_ctrl, b->d_ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    e = cudaStreamEndCapture(st, &b->graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(SV_ERR_CUDA, std::string("capture end: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(SV_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    return SV_OK;
+}
+
+template <typename R>
+void fill_cs(sv_batch *b, const double *theta) {
+    cplx<R> *h = (cplx<R> *)b->h_cs;
+    for (long long k = 0; k < b->total_ops; ++k) h[k] = mk_host<R>(std::cos(theta[k]), std::sin(theta[k]));
+}
+
+}  // namespace
+
+extern "C" {
+
+sv_status sv_batch_create(int n_inst, const sv_instance *inst, sv_dtype dtype, void *cuda_stream,
+                          sv_batch_handle *out) {
+    if (!out) return bfail(SV_ERR_ARG, "NULL output handle pointer");
+    *out = nullptr;
+    if (n_inst < 1 || !inst) return bfail(SV_ERR_ARG, "need at least one instance");
+    if (dtype != SV_C64 && dtype != SV_C128) return bfail(SV_ERR_ARG, "bad dtype");
+    sv_batch *b = new sv_batch();
+    b->n_inst = n_inst;
+    b->dtype = dtype;
+    b->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return bfail(SV_ERR_CUDA, "no CUDA device");
+    }
+    if (!b->stream) {  // graph capture needs a stream other than the legacy default stream
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return bfail(SV_ERR_CUDA, "stream creation failed");
+        }
+        b->own_stream = true;
+    }
+    cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
+    sv_status s = dtype == SV_C64 ? build_plan<float>(b, n_inst, inst) : build_plan<double>(b, n_inst, inst);
+    if (s != SV_OK) {
+        sv_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return SV_OK;
+}
+
+sv_status sv_batch_set_time_limit(sv_batch_handle b, double ms) {
+    if (!b || !(ms >= 0.0) || !std::isfinite(ms)) return bfail(SV_ERR_ARG, "bad time limit");
+    b->budget_ns = (unsigned long long)(ms * 1e6);
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return SV_OK;
+}
+
+sv_status sv_batch_energy_grad(sv_batch_handle b, const double *theta, double *e_out, double *grad_out) {
+    if (!b) return bfail(SV_ERR_ARG, "NULL batch handle");
+    if (b->total_ops > 0 && !theta) return bfail(SV_ERR_ARG, "NULL theta");
+    for (long long k = 0; k < b->total_ops; ++k)
+        if (!std::isfinite(theta[k])) return bfail(SV_ERR_ARG, "non-finite theta");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    sv_status s = SV_OK;
+    if (b->dtype == SV_C64) fill_cs<float>(b, theta);
+    else fill_cs<double>(b, theta);
+    for (long long k = 0; k < b->total_out; ++k) b->h_out[k] = std::nan("");
+    if (!b->exec) s = b->dtype == SV_C64 ? capture<float>(b) : capture<double>(b);
+    if (s == SV_OK) {
+        cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s = bfail(SV_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+        } else {
+            b->launches++;
+        }
+    }
+    if (s == SV_OK) {
+        for (int t = 0; t < b->n_inst; ++t) {
+            const double *o = b->h_out + b->out_off[t];
+            if (e_out) e_out[t] = o[0];
+            if (grad_out)
+                for (int k = 0; k < b->L[t]; ++k) grad_out[b->cs_off[t] + k] = o[1 + k];
+        }
+        if (b->h_ctrl[1]) s = bfail(SV_ERR_TIMEOUT, "batch time limit reached; unfinished instances are NaN");
+    }
+    if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+    return s;
+}
+
+uint64_t sv_batch_launch_count(sv_batch_handle b) { return b ? b->launches : 0; }
+
+sv_status sv_batch_destroy(sv_batch_handle b) {
+    if (!b) return SV_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (void *p : b->dev) cudaFree(p);
+    if (b->h_cs) cudaFreeHost(b->h_cs);
+    if (b->h_out) cudaFreeHost(b->h_out);
+    if (b->h_ctrl) cudaFreeHost(b->h_ctrl);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    cudaGetLastError();
+    delete b;
+    return SV_OK;
+}
+
+}  // extern "C"

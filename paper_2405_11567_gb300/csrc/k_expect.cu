@@ -7,7 +7,7 @@
 // form (sv_tables.cpp), so one pass over the masks serves every string of every
 // group.
 //
-// Sector-gather variant (this file, k_expect_gather): one thread per basis index
+// Record-scan variant (this file, k_expect_gather): one thread per basis index
 // of the (N_alpha, N_beta) sector list (every other amplitude of the state is
 // identically zero: the reference and every excitation conserve both numbers).
 // For its x the thread sums the diagonal element and every single and double
@@ -15,9 +15,10 @@
 // records are staged through shared memory in chunks shared by the block; each
 // thread carries XPT basis indices so every staged record is used XPT times.
 // Accumulation over masks is in the state precision; the energy and norm sums
-// are float64, reduced per block and then in a fixed order.
+// are float64, reduced per block and then in a fixed order.  Indices and masks
+// are in the storage layout (the per-spin-orbital diagonal tables too).
 //
-// The tiled-pass variant for large registers lives in k_tiles.cu.
+// The default variant, string rows, lives in k_rows.cu.
 #include "sv_device.cuh"
 #include "sv_internal.h"
 
@@ -142,12 +143,12 @@ cudaError_t launch_expect_gather(const void *psi, void *sigma, int dtype, int n,
         k_expect_gather<float, kXptGather><<<grid, kThreads, 0, st>>>(
             (const float2 *)psi, (float2 *)sigma, sector, (uint32_t)count,
             (const DoubleRec<float> *)T.dbl, T.n_dbl, (const SingleRec<float> *)T.sgl, T.n_sgl,
-            (const float *)T.W, n, T.hdiag, T.Jp, e_shift, partial);
+            (const float *)T.W, n, T.hdiag_s, T.Jp_s, e_shift, partial);
     } else {
         k_expect_gather<double, kXptGather><<<grid, kThreads, 0, st>>>(
             (const double2 *)psi, (double2 *)sigma, sector, (uint32_t)count,
             (const DoubleRec<double> *)T.dbl, T.n_dbl, (const SingleRec<double> *)T.sgl, T.n_sgl,
-            (const double *)T.W, n, T.hdiag, T.Jp, e_shift, partial);
+            (const double *)T.W, n, T.hdiag_s, T.Jp_s, e_shift, partial);
     }
     return cudaGetLastError();
 }

@@ -97,24 +97,26 @@ int rdm_gather_grid(uint64_t count, int sm_count) {
 
 // Host list of elements for an n-qubit register (norm, n diagonals, then p<q pairs
 // for alpha then beta).  Returns the count.
-int rdm_elements(int n, std::vector<RdmElem> &out) {
+// Masks are mapped to the storage layout `perm`.
+int rdm_elements(int n, const int *perm, std::vector<RdmElem> &out) {
     out.clear();
     out.push_back(RdmElem{0u, 0u, 0u, 0});
-    for (int j = 0; j < n; ++j) out.push_back(RdmElem{1u << j, 0u, 1u << j, 1});
+    for (int j = 0; j < n; ++j) out.push_back(RdmElem{1u << perm[j], 0u, 1u << perm[j], 1});
     const int N = n / 2;
     for (int s = 0; s < 2; ++s)
         for (int p = 0; p < N; ++p)
             for (int q = p + 1; q < N; ++q) {
                 int P = 2 * p + s, Q = 2 * q + s;
-                out.push_back(RdmElem{(1u << P) | (1u << Q), bits_between(P, Q), 1u << Q, 2});
+                out.push_back(RdmElem{map_bits((1u << P) | (1u << Q), perm), map_bits(bits_between(P, Q), perm),
+                                      1u << perm[Q], 2});
             }
     return (int)out.size();
 }
 
 // The element list serialised for upload.
-int rdm_elements_bytes(int n, std::vector<uint8_t> &out) {
+int rdm_elements_bytes(int n, const int *perm, std::vector<uint8_t> &out) {
     std::vector<RdmElem> el;
-    int cnt = rdm_elements(n, el);
+    int cnt = rdm_elements(n, perm, el);
     out.resize(el.size() * sizeof(RdmElem));
     memcpy(out.data(), el.data(), out.size());
     return cnt;

@@ -188,6 +188,37 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(cplx<R> *__restrict__ psi,
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// ---------------------------------------------------------------- layout change
+
+// out[sigma(x)] = in[x]: sigma moves address bit j to address bit sg[j].
+struct PermArgs {
+    int sg[32];
+    int n;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_permute(const cplx<R> *__restrict__ in, cplx<R> *__restrict__ out,
+                                                      uint64_t dim, PermArgs p) {
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < dim; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = (uint32_t)t;
+        uint32_t y = 0;
+        for (int j = 0; j < p.n; ++j) y |= ((v >> j) & 1u) << p.sg[j];
+        out[y] = in[t];
+    }
+}
+
+cudaError_t launch_permute(const void *in, void *out, int dtype, int n, const int *sg, int sm_count, cudaStream_t st) {
+    PermArgs p;
+    for (int j = 0; j < 32; ++j) p.sg[j] = j < n ? sg[j] : j;
+    p.n = n;
+    uint64_t dim = 1ull << n;
+    uint64_t want = (dim + kThreads - 1) / kThreads, cap = (uint64_t)sm_count * 16;
+    int grid = (int)(want < cap ? want : cap);
+    if (dtype == SV_C64) k_permute<float><<<grid, kThreads, 0, st>>>((const float2 *)in, (float2 *)out, dim, p);
+    else k_permute<double><<<grid, kThreads, 0, st>>>((const double2 *)in, (double2 *)out, dim, p);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- reductions
 
 // out[r] = sum_c partials[r * cols + c], fixed order (one block per row).

@@ -28,12 +28,13 @@ cudaError_t launch_expect_gather(const void *psi, void *sigma, int dtype, int n,
                                  uint64_t count, const DevTables &T, double e_shift, int grid,
                                  double *partial, cudaStream_t st);
 int rdm_gather_grid(uint64_t count, int sm_count);
-int rdm_elements_bytes(int n, std::vector<uint8_t> &out);
+int rdm_elements_bytes(int n, const int *perm, std::vector<uint8_t> &out);
+cudaError_t launch_permute(const void *in, void *out, int dtype, int n, const int *sg, int sm_count, cudaStream_t st);
 cudaError_t launch_rdm_gather(const void *psi, int dtype, const uint32_t *sector, uint64_t count,
                               const void *elems, int n_el, int grid, double *partial, cudaStream_t st);
 
 struct RowTables {
-    const uint32_t *sa, *sb;
+    const uint32_t *sa, *sb, *sa_s, *sb_s;
     const uint16_t *stra, *strb, *ra, *rb;
     const void *eri, *hm, *Dt, *Jt;
     int N, Da, Db;
@@ -44,7 +45,7 @@ cudaError_t launch_sigma_rows(const void *C, void *lam, int dtype, int n, const 
                               const double *Jp, double e_shift, double *partial, cudaStream_t st);
 
 DevTables::~DevTables() {
-    void *ptrs[] = {dbl, sgl, W, hdiag, Jp, eri_r, hm_r, Dt, Jt, pass_dbl, pass_sgl, pass_W};
+    void *ptrs[] = {dbl, sgl, W, hdiag, Jp, hdiag_s, Jp_s, eri_r, hm_r, Dt, Jt, pass_dbl, pass_sgl, pass_W};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -55,6 +56,10 @@ using namespace svk;
 // ---------------------------------------------------------------- errors
 
 static thread_local std::string g_err = "no error";
+
+namespace svk {
+void set_thread_error(const std::string &m) { g_err = m; }
+}  // namespace svk
 
 static sv_status fail(sv_handle h, sv_status st, const std::string &msg) {
     g_err = msg;
@@ -204,7 +209,7 @@ static sv_status ensure_sector(sv_handle h) {
     std::vector<uint32_t> list;
     list.reserve(ea.size() * eb.size());
     for (uint32_t a : ea)
-        for (uint32_t b : eb) list.push_back(a | b);
+        for (uint32_t b : eb) list.push_back(map_bits(a | b, h->perm));
     std::sort(list.begin(), list.end());
     void *p;
     SV_TRY(dev_alloc(h, &p, std::max<size_t>(1, list.size()) * sizeof(uint32_t), "sector list"));
@@ -224,11 +229,11 @@ static sv_status ensure_sector(sv_handle h) {
 static sv_status ensure_strings(sv_handle h) {
     if (h->str_sa && h->str_na == h->na && h->str_nb == h->nb) return SV_OK;
     if (h->str_sa) {
-        for (void *p : {(void *)h->str_sa, (void *)h->str_sb, (void *)h->str_a, (void *)h->str_b,
-                        (void *)h->rank_a, (void *)h->rank_b})
+        for (void *p : {(void *)h->str_sa, (void *)h->str_sb, (void *)h->str_sa_s, (void *)h->str_sb_s,
+                        (void *)h->str_a, (void *)h->str_b, (void *)h->rank_a, (void *)h->rank_b})
             cudaFree(p);
         h->bytes_owned -= std::min<uint64_t>(h->bytes_owned, h->str_bytes);
-        h->str_sa = h->str_sb = nullptr;
+        h->str_sa = h->str_sb = h->str_sa_s = h->str_sb_s = nullptr;
     }
     const int N = h->n / 2;
     auto strings = [&](int k, std::vector<uint16_t> &str, std::vector<uint16_t> &rank) {
@@ -243,16 +248,18 @@ static sv_status ensure_strings(sv_handle h) {
     std::vector<uint16_t> sa16, sb16, ra, rb;
     strings(h->na, sa16, ra);
     strings(h->nb, sb16, rb);
-    std::vector<uint32_t> spa(sa16.size()), spb(sb16.size());
+    std::vector<uint32_t> spa(sa16.size()), spb(sb16.size()), spa_s(sa16.size()), spb_s(sb16.size());
     for (size_t i = 0; i < sa16.size(); ++i) {
         uint32_t x = 0;
         for (int p = 0; p < N; ++p) if ((sa16[i] >> p) & 1u) x |= 1u << (2 * p);
         spa[i] = x;
+        spa_s[i] = map_bits(x, h->perm);
     }
     for (size_t i = 0; i < sb16.size(); ++i) {
         uint32_t x = 0;
         for (int p = 0; p < N; ++p) if ((sb16[i] >> p) & 1u) x |= 1u << (2 * p + 1);
         spb[i] = x;
+        spb_s[i] = map_bits(x, h->perm);
     }
     size_t bytes = 0;
     auto up = [&](void **dst, const void *src, size_t nb) -> sv_status {
@@ -263,6 +270,8 @@ static sv_status ensure_strings(sv_handle h) {
     };
     SV_TRY(up((void **)&h->str_sa, spa.data(), spa.size() * 4));
     SV_TRY(up((void **)&h->str_sb, spb.data(), spb.size() * 4));
+    SV_TRY(up((void **)&h->str_sa_s, spa_s.data(), spa_s.size() * 4));
+    SV_TRY(up((void **)&h->str_sb_s, spb_s.data(), spb_s.size() * 4));
     SV_TRY(up((void **)&h->str_a, sa16.data(), sa16.size() * 2));
     SV_TRY(up((void **)&h->str_b, sb16.data(), sb16.size() * 2));
     SV_TRY(up((void **)&h->rank_a, ra.data(), ra.size() * 2));
@@ -289,6 +298,7 @@ template <typename R>
 static sv_status upload_tables(sv_handle h, sv_ham_handle ham, DevTables &T) {
     HostTables<R> ht;
     build_tables<R>(*ham, h->n, ht);
+    permute_tables<R>(ht, h->perm, h->n);
     T.n_dbl = (int)ht.dbl.size();
     T.n_sgl = (int)ht.sgl.size();
     auto up = [&](void **dst, const void *src, size_t bytes) -> sv_status {
@@ -306,6 +316,8 @@ static sv_status upload_tables(sv_handle h, sv_ham_handle ham, DevTables &T) {
     SV_TRY(up(&T.W, ht.W.data(), ht.W.size() * sizeof(R)));
     SV_TRY(up((void **)&T.hdiag, ht.hdiag.data(), ht.hdiag.size() * sizeof(double)));
     SV_TRY(up((void **)&T.Jp, ht.Jp.data(), ht.Jp.size() * sizeof(double)));
+    SV_TRY(up((void **)&T.hdiag_s, ht.hdiag_s.data(), ht.hdiag_s.size() * sizeof(double)));
+    SV_TRY(up((void **)&T.Jp_s, ht.Jp_s.data(), ht.Jp_s.size() * sizeof(double)));
     // spatial integrals in the state precision for the string-row kernel
     const int N = ham->n_orb;
     std::vector<R> eri(ham->eri.begin(), ham->eri.end()), hm(ham->h.begin(), ham->h.end());
@@ -325,7 +337,8 @@ static sv_status upload_tables(sv_handle h, sv_ham_handle ham, DevTables &T) {
 }
 
 static sv_status get_tables(sv_handle h, sv_ham_handle ham, DevTables **out) {
-    int key = h->device * 1000 + h->n * 2 + (int)h->dtype;
+    std::string key = std::to_string(h->device) + "/" + std::to_string(h->n) + "/" + std::to_string((int)h->dtype);
+    for (int q = 0; q < h->n; ++q) key += "," + std::to_string(h->perm[q]);
     auto it = ham->dev.find(key);
     if (it != ham->dev.end()) {
         *out = it->second.get();
@@ -357,7 +370,7 @@ static sv_status build_ops(sv_handle h, const sv_excitation *ops, int n_ops, con
     out.resize(n_ops);
     for (int k = 0; k < n_ops; ++k) {
         std::string why;
-        if (!make_op(ops[k], h->n, out[k], why)) {
+        if (!make_op(ops[k], h->n, h->perm, out[k], why)) {
             char buf[64];
             snprintf(buf, sizeof buf, "op %d: ", k);
             return fail(h, SV_ERR_ARG, buf + why);
@@ -380,7 +393,7 @@ static sv_status check_ham(sv_handle h, sv_ham_handle ham) {
 static sv_status prepare_reference(sv_handle h) {
     if (h->ref_kind == 1) {
         SV_CUDA(h, cudaMemsetAsync(h->psi, 0, vec_bytes(h), h->stream));
-        SV_CUDA(h, launch_set_basis(h->psi, h->dtype, h->ref_det, h->stream));
+        SV_CUDA(h, launch_set_basis(h->psi, h->dtype, map_bits(h->ref_det, h->perm), h->stream));
         h->launches++;
     } else if (h->ref_kind == 2) {
         SV_CUDA(h, cudaMemcpyAsync(h->psi, h->ref_vec, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
@@ -431,10 +444,10 @@ static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void 
         SV_TRY(ensure_strings(h));
         SV_TRY(ensure_partials(h, 2 * (size_t)h->Db));
         if (sigma) SV_CUDA(h, cudaMemsetAsync(sigma, 0, vec_bytes(h), h->stream));
-        SV_CUDA(h, launch_compact(h->psi, h->Cbuf, h->dtype, h->str_sa, h->str_sb, h->Da, h->Db, h->sm_count,
+        SV_CUDA(h, launch_compact(h->psi, h->Cbuf, h->dtype, h->str_sa_s, h->str_sb_s, h->Da, h->Db, h->sm_count,
                                   h->stream));
         h->launches++;
-        RowTables R{h->str_sa, h->str_sb, h->str_a, h->str_b, h->rank_a, h->rank_b,
+        RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
                     T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db};
         SV_CUDA(h, launch_sigma_rows(h->Cbuf, sigma, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
                                      h->partials, h->stream));
@@ -459,6 +472,63 @@ static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void 
 // determinant (HF) or of the largest-weight determinant of a stored reference.
 static double shift_for(sv_handle h, sv_ham_handle ham) {
     return diag_energy(*ham, h->ref_det, h->n);
+}
+
+// ---------------------------------------------------------------- storage layout
+
+// Least-used qubits go to the lowest address bits: an excitation whose lowest
+// address bit is b touches runs of 2^b consecutive amplitudes, so keeping the
+// frequently excited qubits high keeps the rotation kernels' runs long.
+static void layout_from_ops(int n, const sv_excitation *ops, int n_ops, int *perm) {
+    std::vector<long> cnt(n, 0);
+    for (int k = 0; k < n_ops; ++k) {
+        const sv_excitation &e = ops[k];
+        int qs[4] = {e.occ[0], e.vir[0], e.kind == 2 ? e.occ[1] : -1, e.kind == 2 ? e.vir[1] : -1};
+        for (int q : qs)
+            if (q >= 0 && q < n) cnt[q]++;
+    }
+    std::vector<int> order(n);
+    for (int q = 0; q < n; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cnt[a] < cnt[b]; });
+    for (int k = 0; k < n; ++k) perm[order[k]] = k;
+    for (int q = n; q < 32; ++q) perm[q] = q;
+}
+
+static void drop_layout_caches(sv_handle h) {
+    if (h->sector) dev_free(h, h->sector, h->sector_len * sizeof(uint32_t));
+    h->sector = nullptr;
+    h->sector_na = h->sector_nb = -1;
+    h->str_na = h->str_nb = -1;  // string tables rebuilt on next use
+}
+
+// Move the prepared state (and a stored reference) to layout `np`.
+static sv_status relayout(sv_handle h, const int *np) {
+    bool same = true;
+    for (int q = 0; q < h->n; ++q) same = same && (np[q] == h->perm[q]);
+    if (same) return SV_OK;
+    int inv_old[32], sg[32];
+    for (int q = 0; q < h->n; ++q) inv_old[h->perm[q]] = q;
+    for (int j = 0; j < h->n; ++j) sg[j] = np[inv_old[j]];
+    if (h->prepared || h->ref_kind == 2) SV_TRY(ensure_lam(h));
+    if (h->prepared) {
+        SV_CUDA(h, launch_permute(h->psi, h->lam, h->dtype, h->n, sg, h->sm_count, h->stream));
+        h->launches++;
+        SV_CUDA(h, cudaMemcpyAsync(h->psi, h->lam, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    if (h->ref_kind == 2 && h->ref_vec) {
+        SV_CUDA(h, launch_permute(h->ref_vec, h->lam, h->dtype, h->n, sg, h->sm_count, h->stream));
+        h->launches++;
+        SV_CUDA(h, cudaMemcpyAsync(h->ref_vec, h->lam, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    for (int q = 0; q < 32; ++q) h->perm[q] = q < h->n ? np[q] : q;
+    drop_layout_caches(h);
+    return SV_OK;
+}
+
+static bool is_identity(sv_handle h) {
+    for (int q = 0; q < h->n; ++q)
+        if (h->perm[q] != q) return false;
+    return true;
 }
 
 // ---------------------------------------------------------------- C-ABI
@@ -486,6 +556,7 @@ static sv_status create_common(int n_qubits, sv_dtype dtype, void *cuda_stream, 
     h->stream = (cudaStream_t)cuda_stream;
     h->dim = 1ull << n_qubits;
     h->amp_bytes = dtype == SV_C64 ? 8 : 16;
+    for (int q = 0; q < 32; ++q) h->perm[q] = q;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         cudaGetLastError();
         delete h;
@@ -531,8 +602,8 @@ sv_status sv_destroy(sv_handle h) {
     dev_free(h, h->saved, vec_bytes(h));
     for (void *p : h->ckpt) dev_free(h, p, vec_bytes(h));
     dev_free(h, h->sector, h->sector_len * sizeof(uint32_t));
-    for (void *p : {(void *)h->str_sa, (void *)h->str_sb, (void *)h->str_a, (void *)h->str_b,
-                    (void *)h->rank_a, (void *)h->rank_b})
+    for (void *p : {(void *)h->str_sa, (void *)h->str_sb, (void *)h->str_sa_s, (void *)h->str_sb_s,
+                    (void *)h->str_a, (void *)h->str_b, (void *)h->rank_a, (void *)h->rank_b})
         if (p) cudaFree(p);
     dev_free(h, h->Cbuf, h->Cbuf_bytes);
     dev_free(h, h->partials, h->partials_cap * sizeof(double));
@@ -598,7 +669,15 @@ sv_status sv_prepare_state(sv_handle h, const void *amplitudes_host, int n_alpha
     h->failed = false;
     h->prepared = false;
     if (!h->ref_vec) SV_TRY(dev_alloc(h, &h->ref_vec, vec_bytes(h), "reference copy"));
-    SV_CUDA(h, cudaMemcpyAsync(h->ref_vec, amplitudes_host, vec_bytes(h), cudaMemcpyHostToDevice, h->stream));
+    if (is_identity(h)) {
+        SV_CUDA(h, cudaMemcpyAsync(h->ref_vec, amplitudes_host, vec_bytes(h), cudaMemcpyHostToDevice, h->stream));
+    } else {
+        // host order is qubit order: upload to the scratch vector, then move bit q to bit perm[q]
+        SV_TRY(ensure_lam(h));
+        SV_CUDA(h, cudaMemcpyAsync(h->lam, amplitudes_host, vec_bytes(h), cudaMemcpyHostToDevice, h->stream));
+        SV_CUDA(h, launch_permute(h->lam, h->ref_vec, h->dtype, h->n, h->perm, h->sm_count, h->stream));
+        h->launches++;
+    }
     SV_CUDA(h, cudaStreamSynchronize(h->stream));
     h->ref_kind = 2;
     h->ref_det = best_x;
@@ -613,7 +692,17 @@ sv_status sv_get_state(sv_handle h, void *amplitudes_host) {
     SV_TRY(check_ready(h));
     if (!amplitudes_host) return fail(h, SV_ERR_ARG, "NULL output");
     DeviceGuard g(h->device);
-    SV_CUDA(h, cudaMemcpyAsync(amplitudes_host, h->psi, vec_bytes(h), cudaMemcpyDeviceToHost, h->stream));
+    const void *src = h->psi;
+    if (!is_identity(h)) {
+        // back to qubit order through the scratch vector
+        int inv[32];
+        for (int q = 0; q < h->n; ++q) inv[h->perm[q]] = q;
+        SV_TRY(ensure_lam(h));
+        SV_CUDA(h, launch_permute(h->psi, h->lam, h->dtype, h->n, inv, h->sm_count, h->stream));
+        h->launches++;
+        src = h->lam;
+    }
+    SV_CUDA(h, cudaMemcpyAsync(amplitudes_host, src, vec_bytes(h), cudaMemcpyDeviceToHost, h->stream));
     SV_CUDA(h, cudaStreamSynchronize(h->stream));
     return SV_OK;
 }
@@ -695,8 +784,14 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     if (h->ref_kind == 0) return fail(h, SV_ERR_STATE, "no reference state recorded");
     SV_TRY(check_ham(h, ham));
     std::vector<OpDesc> d;
-    SV_TRY(build_ops(h, ops, n_ops, theta, d));
+    SV_TRY(build_ops(h, ops, n_ops, theta, d));  // validates in any layout
     DeviceGuard g(h->device);
+    if (h->layout_auto && n_ops > 0) {
+        int np[32];
+        layout_from_ops(h->n, ops, n_ops, np);
+        SV_TRY(relayout(h, np));
+        SV_TRY(build_ops(h, ops, n_ops, theta, d));
+    }
     const size_t L = d.size();
     DevTables *T;
     SV_TRY(get_tables(h, ham, &T));
@@ -779,7 +874,7 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
     SV_TRY(ensure_sector(h));
     // element list (host) -> device scratch after the partial sums
     std::vector<uint8_t> host_el;
-    const int n_el = rdm_elements_bytes(h->n, host_el);
+    const int n_el = rdm_elements_bytes(h->n, h->perm, host_el);
     const int grid = rdm_gather_grid(h->sector_len, h->sm_count);
     const size_t part = (size_t)2 * n_el * grid;
     const size_t el_doubles = (host_el.size() + sizeof(double) - 1) / sizeof(double);
@@ -821,6 +916,27 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
     return SV_OK;
 }
 
+sv_status sv_set_layout(sv_handle h, const int32_t *storage_of_qubit) {
+    if (!h || !storage_of_qubit) return fail(h, SV_ERR_ARG, "NULL argument");
+    int np[32];
+    uint32_t seen = 0;
+    for (int q = 0; q < h->n; ++q) {
+        int b = storage_of_qubit[q];
+        if (b < 0 || b >= h->n || ((seen >> b) & 1u)) return fail(h, SV_ERR_ARG, "layout is not a permutation of [0, n)");
+        seen |= 1u << b;
+        np[q] = b;
+    }
+    DeviceGuard g(h->device);
+    h->layout_auto = false;
+    return relayout(h, np);
+}
+
+sv_status sv_get_layout(sv_handle h, int32_t *storage_of_qubit) {
+    if (!h || !storage_of_qubit) return fail(h, SV_ERR_ARG, "NULL argument");
+    for (int q = 0; q < h->n; ++q) storage_of_qubit[q] = h->perm[q];
+    return SV_OK;
+}
+
 sv_status sv_phase_times(sv_handle h, double *ms_out, int n_out) {
     if (!h || !ms_out || n_out < 0) return fail(h, SV_ERR_ARG, "bad arguments");
     for (int i = 0; i < n_out && i < SV_PHASES; ++i) ms_out[i] = h->phase_ms[i];
@@ -848,6 +964,9 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
             return SV_OK;
         case SV_OPT_PROFILE:
             h->profile = value != 0;
+            return SV_OK;
+        case SV_OPT_LAYOUT_AUTO:
+            h->layout_auto = value != 0;
             return SV_OK;
     }
     return fail(h, SV_ERR_ARG, "unknown option");

@@ -33,8 +33,21 @@ struct OpDesc {
     double c = 1.0, s = 0.0;    // cos(theta), sin(theta), taken on the host in float64
 };
 
-// Validate one excitation for an n-qubit register and fill `d` (without angles).
-bool make_op(const sv_excitation &e, int n, OpDesc &d, std::string &why);
+// Storage layout: bit perm[q] of an amplitude's address holds qubit q.
+// map_bits applies it to a qubit-space bit mask.
+inline uint32_t map_bits(uint32_t m, const int *perm) {
+    uint32_t r = 0;
+    while (m) {
+        int q = __builtin_ctz(m);
+        r |= 1u << perm[q];
+        m &= m - 1u;
+    }
+    return r;
+}
+
+// Validate one excitation for an n-qubit register and fill `d` (without angles),
+// with masks and positions in the storage layout `perm`.
+bool make_op(const sv_excitation &e, int n, const int *perm, OpDesc &d, std::string &why);
 
 // Bits strictly between positions a and b (order irrelevant).
 inline uint32_t bits_between(int a, int b) {
@@ -77,8 +90,9 @@ struct HostTables {
     std::vector<DoubleRec<R>> dbl;
     std::vector<SingleRec<R>> sgl;
     std::vector<R> W;          // [n_singles][n]
-    std::vector<double> hdiag; // [n] h_kk per spin-orbital
-    std::vector<double> Jp;    // [n][n] [kk|ll] - [kl|lk] (0 on the diagonal)
+    std::vector<double> hdiag; // [n] h_kk per spin-orbital (qubit order)
+    std::vector<double> Jp;    // [n][n] [kk|ll] - [kl|lk] (0 on the diagonal), qubit order
+    std::vector<double> hdiag_s, Jp_s;  // the same indexed by storage bit (record scan)
 };
 
 // Device copy of the tables, built lazily per (n, dtype) and cached in the Hamiltonian.
@@ -89,8 +103,10 @@ struct DevTables {
     void *dbl = nullptr;   // DoubleRec<R>[n_dbl]
     void *sgl = nullptr;   // SingleRec<R>[n_sgl]
     void *W = nullptr;     // R[n_sgl * n]
-    double *hdiag = nullptr;
+    double *hdiag = nullptr;    // qubit order (string rows)
     double *Jp = nullptr;
+    double *hdiag_s = nullptr;  // storage order (record scan)
+    double *Jp_s = nullptr;
     // string-row tables (k_rows.cu), state precision
     void *eri_r = nullptr;  // [N^4] (pq|rs)
     void *hm_r = nullptr;   // [N^2] h_pq
@@ -113,6 +129,11 @@ struct DevTables {
 template <typename R>
 void build_tables(const sv_ham &H, int n, HostTables<R> &out);
 
+// Re-express the record-scan tables in the storage layout `perm` (masks mapped bit
+// by bit; per-spin-orbital arrays moved to their storage positions).
+template <typename R>
+void permute_tables(HostTables<R> &t, const int *perm, int n);
+
 // <x|H|x> in float64 on the host.
 double diag_energy(const sv_ham &H, uint32_t x, int n);
 
@@ -125,7 +146,7 @@ struct sv_ham {
     double e_nuc = 0.0;
     std::vector<double> h;    // [N][N]
     std::vector<double> eri;  // [N][N][N][N] chemist (pq|rs)
-    std::map<int, std::unique_ptr<svk::DevTables>> dev;  // key: n*2 + dtype
+    std::map<std::string, std::unique_ptr<svk::DevTables>> dev;  // key: device, n, dtype, layout
     int device = -1;
 };
 
@@ -152,7 +173,8 @@ struct sv_ctx {
     uint64_t sector_len = 0;
     int sector_na = -1, sector_nb = -1;
     // string-row view of the sector (k_rows.cu): alpha / beta strings, ranks, spreads
-    uint32_t *str_sa = nullptr, *str_sb = nullptr;
+    uint32_t *str_sa = nullptr, *str_sb = nullptr;    // qubit-space spreads
+    uint32_t *str_sa_s = nullptr, *str_sb_s = nullptr;  // storage-space spreads
     uint16_t *str_a = nullptr, *str_b = nullptr, *rank_a = nullptr, *rank_b = nullptr;
     int Da = 0, Db = 0, str_na = -1, str_nb = -1;
     size_t str_bytes = 0;
@@ -173,6 +195,10 @@ struct sv_ctx {
     uint64_t bytes_owned = 0;
     int expect_variant = 0;
     int rdm_variant = 0;
+    // storage layout: address bit perm[q] holds qubit q (identity by default);
+    // layout_auto: sv_energy_grad picks it from its operator list
+    int perm[32];
+    bool layout_auto = true;
     // phase profiling (SV_OPT_PROFILE)
     bool profile = false;
     cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

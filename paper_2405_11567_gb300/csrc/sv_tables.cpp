@@ -27,7 +27,7 @@
 
 namespace svk {
 
-bool make_op(const sv_excitation &e, int n, OpDesc &d, std::string &why) {
+static bool make_op_qubits(const sv_excitation &e, int n, OpDesc &d, std::string &why) {
     auto inrange = [&](int v) { return v >= 0 && v < n; };
     d = OpDesc();
     if (e.kind == 1) {
@@ -64,6 +64,47 @@ bool make_op(const sv_excitation &e, int n, OpDesc &d, std::string &why) {
     why = "excitation kind must be 1 or 2";
     return false;
 }
+
+bool make_op(const sv_excitation &e, int n, const int *perm, OpDesc &d, std::string &why) {
+    if (!make_op_qubits(e, n, d, why)) return false;
+    // the sign is a parity of popcounts, invariant under relabelling the bits
+    int pos[4];
+    for (int t = 0; t < d.nbits; ++t) pos[t] = perm[d.pos[t]];
+    std::sort(pos, pos + d.nbits);
+    for (int t = 0; t < d.nbits; ++t) d.pos[t] = pos[t];
+    d.m = map_bits(d.m, perm);
+    d.from = map_bits(d.from, perm);
+    d.sm = map_bits(d.sm, perm);
+    return true;
+}
+
+template <typename R>
+void permute_tables(HostTables<R> &t, const int *perm, int n) {
+    for (auto &r : t.dbl) {
+        r.m = map_bits(r.m, perm);
+        r.sm = map_bits(r.sm, perm);
+        r.b0 = map_bits(r.b0, perm);
+        r.b1 = map_bits(r.b1, perm);
+        r.b2 = map_bits(r.b2, perm);
+    }
+    for (auto &r : t.sgl) {
+        r.m = map_bits(r.m, perm);
+        r.sm = map_bits(r.sm, perm);
+    }
+    std::vector<R> W(t.W.size());
+    for (size_t i = 0; i < t.sgl.size(); ++i)
+        for (int k = 0; k < n; ++k) W[i * n + perm[k]] = t.W[i * n + k];
+    t.W.swap(W);
+    t.hdiag_s.assign(n, 0.0);
+    t.Jp_s.assign((size_t)n * n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        t.hdiag_s[perm[k]] = t.hdiag[k];
+        for (int l = 0; l < n; ++l) t.Jp_s[(size_t)perm[k] * n + perm[l]] = t.Jp[(size_t)k * n + l];
+    }
+}
+
+template void permute_tables<float>(HostTables<float> &, const int *, int);
+template void permute_tables<double>(HostTables<double> &, const int *, int);
 
 template <typename R>
 void build_tables(const sv_ham &H, int n, HostTables<R> &out) {

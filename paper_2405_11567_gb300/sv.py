@@ -15,6 +15,7 @@ from . import build as _build
 SV_C64, SV_C128 = 0, 1
 SV_OPT_CHECKPOINT_INTERVAL, SV_OPT_MAX_BYTES, SV_OPT_EXPECT_VARIANT, SV_OPT_RDM_VARIANT = 1, 2, 3, 4
 SV_OPT_PROFILE = 5
+SV_OPT_LAYOUT_AUTO = 6
 SV_PHASES = 6
 PHASE_NAMES = ("reference", "forward", "expectation", "reverse", "restore", "rdm1")
 STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV_ERR_TIMEOUT", 5: "SV_ERR_STATE"}
@@ -22,9 +23,10 @@ STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV
 # every symbol include/sv.h declares
 EXPORTS = (
     "sv_create", "sv_create_with_buffers", "sv_destroy", "sv_prepare_hf", "sv_prepare_state",
-    "sv_get_state", "sv_state_device_ptr", "sv_ham_create", "sv_ham_destroy", "sv_apply_ansatz",
+    "sv_get_state", "sv_state_device_ptr", "sv_set_layout", "sv_get_layout", "sv_ham_create", "sv_ham_destroy", "sv_apply_ansatz",
     "sv_energy", "sv_energy_grad", "sv_rdm1", "sv_set_option", "sv_phase_times", "sv_last_error",
-    "sv_launch_count", "sv_version",
+    "sv_launch_count", "sv_version", "sv_batch_create", "sv_batch_energy_grad", "sv_batch_set_time_limit",
+    "sv_batch_launch_count", "sv_batch_destroy",
 )
 
 
@@ -36,6 +38,12 @@ class SvError(RuntimeError):
 
 class sv_excitation(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("occ", ctypes.c_int32 * 2), ("vir", ctypes.c_int32 * 2)]
+
+
+class sv_instance(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("occ", ctypes.c_void_p), ("n_occ", ctypes.c_int32),
+                ("h", ctypes.c_void_p), ("eri", ctypes.c_void_p), ("e_nuc", ctypes.c_double),
+                ("ops", ctypes.c_void_p), ("n_ops", ctypes.c_int32)]
 
 
 _lib = None
@@ -64,6 +72,8 @@ def lib():
             "sv_prepare_state": (i32, [vp, vp, i32, i32]),
             "sv_get_state": (i32, [vp, vp]),
             "sv_state_device_ptr": (i32, [vp, pp]),
+            "sv_set_layout": (i32, [vp, vp]),
+            "sv_get_layout": (i32, [vp, vp]),
             "sv_ham_create": (i32, [i32, vp, vp, dbl, pp]),
             "sv_ham_destroy": (i32, [vp]),
             "sv_apply_ansatz": (i32, [vp, vp, i32, vp]),
@@ -75,6 +85,11 @@ def lib():
             "sv_last_error": (ctypes.c_char_p, [vp]),
             "sv_launch_count": (ctypes.c_uint64, [vp]),
             "sv_version": (ctypes.c_char_p, []),
+            "sv_batch_create": (i32, [i32, vp, i32, vp, pp]),
+            "sv_batch_energy_grad": (i32, [vp, vp, vp, vp]),
+            "sv_batch_set_time_limit": (i32, [vp, dbl]),
+            "sv_batch_launch_count": (ctypes.c_uint64, [vp]),
+            "sv_batch_destroy": (i32, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -158,6 +173,17 @@ def sv_state_device_ptr(h) -> int:
     return p.value
 
 
+def sv_set_layout(h, storage_of_qubit):
+    a = np.ascontiguousarray(np.asarray(storage_of_qubit, dtype=np.int32).reshape(-1))
+    _ck(lib().sv_set_layout(h, _ptr(a)), h)
+
+
+def sv_get_layout(h, n_qubits: int) -> np.ndarray:
+    out = np.zeros(n_qubits, dtype=np.int32)
+    _ck(lib().sv_get_layout(h, _ptr(out)), h)
+    return out
+
+
 def sv_ham_create(h_mat, eri, e_nuc: float):
     hm = np.ascontiguousarray(np.asarray(h_mat, dtype=np.float64))
     N = hm.shape[0]
@@ -217,7 +243,80 @@ def sv_launch_count(h) -> int:
     return int(lib().sv_launch_count(h))
 
 
+def sv_batch_create(problems, dtype: int, stream=None):
+    """problems: dicts with n_qubits, occ, h, eri, e_nuc, ops (the inputs module's format)."""
+    keep = []
+    arr = (sv_instance * len(problems))()
+    for k, p in enumerate(problems):
+        occ = np.ascontiguousarray(np.asarray(p["occ"], dtype=np.int32).reshape(-1))
+        hm = np.ascontiguousarray(np.asarray(p["h"], dtype=np.float64))
+        er = np.ascontiguousarray(np.asarray(p["eri"], dtype=np.float64))
+        ops = _ops_array(p["ops"])
+        keep += [occ, hm, er, ops]
+        arr[k] = sv_instance(int(p["n_qubits"]), occ.ctypes.data, len(occ), hm.ctypes.data, er.ctypes.data,
+                             float(p["e_nuc"]), ops.ctypes.data, len(ops))
+    out = ctypes.c_void_p()
+    _ck(lib().sv_batch_create(len(problems), ctypes.cast(arr, ctypes.c_void_p), int(dtype), _stream_ptr(stream),
+                              ctypes.byref(out)))
+    return out
+
+
+def sv_batch_energy_grad(b, theta_concat, n_inst: int, total_ops: int):
+    t = np.ascontiguousarray(np.asarray(theta_concat, dtype=np.float64).reshape(-1))
+    if len(t) != total_ops:
+        raise ValueError("theta must hold every instance's angles, concatenated")
+    e = np.zeros(n_inst)
+    g = np.zeros(max(total_ops, 1))
+    _ck(lib().sv_batch_energy_grad(b, _ptr(t), _ptr(e), _ptr(g)))
+    return e, g[:total_ops]
+
+
+def sv_batch_set_time_limit(b, ms: float):
+    _ck(lib().sv_batch_set_time_limit(b, float(ms)))
+
+
+def sv_batch_launch_count(b) -> int:
+    return int(lib().sv_batch_launch_count(b))
+
+
+def sv_batch_destroy(b):
+    _ck(lib().sv_batch_destroy(b))
+
+
 # ---------------------------------------------------------------- convenience objects
+
+class Batch:
+    """Owns an ``sv_batch_handle``: many independent problems in one persistent launch."""
+
+    def __init__(self, problems, dtype="c64", stream=None):
+        self.dtype = SV_C64 if dtype in ("c64", SV_C64) else SV_C128
+        self.sizes = [len(p["ops"]) for p in problems]
+        self.n_inst = len(problems)
+        self.total_ops = int(sum(self.sizes))
+        self.handle = sv_batch_create(problems, self.dtype, stream)
+
+    def energy_grad(self, theta_concat):
+        """(E per instance, list of gradient arrays per instance)."""
+        e, g = sv_batch_energy_grad(self.handle, theta_concat, self.n_inst, self.total_ops)
+        return e, np.split(g, np.cumsum(self.sizes)[:-1])
+
+    def set_time_limit(self, ms):
+        sv_batch_set_time_limit(self.handle, ms)
+
+    @property
+    def launches(self) -> int:
+        return sv_batch_launch_count(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            sv_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 class Hamiltonian:
     """Owns an ``sv_ham_handle`` built from (h, eri, e_nuc)."""
@@ -280,6 +379,12 @@ class StateVector:
 
     def set_option(self, opt, value):
         sv_set_option(self.handle, opt, value)
+
+    def set_layout(self, storage_of_qubit):
+        sv_set_layout(self.handle, storage_of_qubit)
+
+    def layout(self) -> np.ndarray:
+        return sv_get_layout(self.handle, self.n)
 
     def phase_times(self) -> dict:
         return sv_phase_times(self.handle)

@@ -348,3 +348,67 @@ def test_sigma_vector_matches_oracle():
         st.prepare_state(dense0, 2, 2)
         _, g = st.energy_grad(ham, ops, zeros)
         assert np.max(np.abs(g - gref)) <= 1e-11
+
+
+# ---------------------------------------------------------------- storage layout
+
+def test_layout_roundtrip_bit_exact():
+    n = 12
+    rng = np.random.default_rng(21)
+    v = inputs.random_sector_state(n, 3, 2, rng)
+    for dtype, cast in (("c128", np.complex128), ("c64", np.complex64)):
+        st = _gpu_state(n, dtype)
+        st.prepare_state(v.astype(cast), 3, 2)
+        perm = rng.permutation(n)
+        st.set_layout(perm)
+        assert np.array_equal(st.layout(), perm)
+        assert np.array_equal(st.state(), v.astype(cast))          # moved on the device, read back in qubit order
+        st.set_layout(np.arange(n)[::-1].copy())
+        assert np.array_equal(st.state(), v.astype(cast))
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_permuted_layout_parity(variant, dtype):
+    """A random storage permutation changes nothing observable: state, energy, gradient, 1-RDM."""
+    n, na, nb = 12, 3, 2
+    p = inputs.make_problem(n, 4, 30, seed=99)
+    rng = np.random.default_rng(5)
+    dense0 = inputs.random_sector_state(n, na, nb, rng)
+    sec = oracle.Sector(n, na, nb)
+    psi0 = dense0[sec.dets.astype(np.int64)]
+    theta = p["theta"] * 7
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
+    psi_ref = A.apply_ansatz(sec, p["ops"], theta, psi0)
+    rdm_ref = A.rdm1(sec, psi_ref)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(n, dtype)
+    st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
+    st.set_layout(rng.permutation(n))                              # also turns the automatic layout off
+    st.prepare_state(dense0.astype(np.complex64 if dtype == "c64" else np.complex128), na, nb)
+    st.apply_ansatz(p["ops"], theta)
+    got = st.state()
+    assert np.max(np.abs(got[sec.dets.astype(np.int64)] - psi_ref)) <= TOL[dtype]["amp"] * 10
+    assert np.count_nonzero(got[~_sector_mask(n, na, nb)]) == 0
+    assert abs(st.energy(ham) - Eref) <= TOL[dtype]["E"]
+    assert np.max(np.abs(st.rdm1() - rdm_ref)) <= TOL[dtype]["rdm"]
+    E, g = st.energy_grad(ham, p["ops"], theta)
+    assert abs(E - Eref) <= TOL[dtype]["E"]
+    assert np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
+
+
+def test_automatic_layout_moves_frequent_qubits_high():
+    p = inputs.config_problem(2)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(p["n_qubits"], "c64")
+    st.prepare_hf(p["occ"])
+    st.energy_grad(ham, p["ops"], p["theta"])
+    lay = st.layout()
+    assert sorted(lay) == list(range(p["n_qubits"]))
+    cnt = np.zeros(p["n_qubits"])
+    for k, i, j, a, b in p["ops"]:
+        for q in ((i, a) if k == 1 else (i, j, a, b)):
+            cnt[q] += 1
+    # address bit order follows usage: counts are non-decreasing along the address bits
+    by_bit = cnt[np.argsort(lay)]
+    assert np.all(np.diff(by_bit) >= 0)
