@@ -249,8 +249,31 @@ def run_ours(args, rank, world, local_rank):
         st.close()
         return dict(ms=ms, t_host=t_host, phases=avg, clocks=clk, launches=launches, out=outs)
 
+    def timed_batch():
+        """Config 4: 512 instances (10-20 qubits, 40 operators each), one graph launch per step."""
+        probs = inputs.batch_problems(512)
+        b = sv.Batch(probs, "c64", stream)
+        theta = np.concatenate([q["theta"] for q in probs])
+        for _ in range(args.warmup):
+            b.energy_grad(theta)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = b.launches
+        ev0.record(stream)
+        for _ in range(args.steps):
+            b.energy_grad(theta)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        out = {"workload": "512 instances, 10-20 qubits, 40-operator ADAPT-style ansatz each, complex64",
+               "ms_per_batch": ms, "instance_evals_per_s": 512 / (ms / 1000.0),
+               "gpu_launches_per_batch": (b.launches - l0) // args.steps}
+        b.close()
+        return out
+
     r64 = timed("c64")
     r128 = None if args.no_c128 else timed("c128")
+    rbatch = None if (args.qubits or args.no_batch) else timed_batch()
     if rank != 0:
         return 0
     K = args.steps
@@ -299,6 +322,8 @@ def run_ours(args, rank, world, local_rank):
             "max_abs_dg": float(np.max(np.abs(r64["out"]["g"] - r128["out"]["g"]))),
             "max_abs_drdm": float(np.max(np.abs(r64["out"]["rdm"] - r128["out"]["rdm"]))),
             "E_fp64": r128["out"]["E"]}
+    if rbatch is not None:
+        line["batch_config4"] = rbatch
     if world == 1 and not args.no_cpu_baseline and not args.qubits:
         import oracle
         v, sample, _ = oracle_eval_sample(p)
@@ -316,6 +341,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-c128", action="store_true", help="skip the complex128 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) timing")
     ap.add_argument("--qubits", type=int, default=0,
                     help="profiling only: a smaller register (same generator, n/3 rounded to even electrons, "
                          "200 operators); the bench line is then not the headline workload")
