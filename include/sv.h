@@ -179,6 +179,26 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
  * im_out likewise Im n (im_out may be NULL), N = n_qubits/2, sigma 0 = alpha. */
 sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out);
 
+/* ---- no device allocation ------------------------------------------------------ */
+
+/* The spin-resolved 1-RDM (same values and layout as sv_rdm1) of a state the
+ * caller holds in device memory, computed without allocating any device memory:
+ * for callers whose device memory is entirely owned by another allocator, or who
+ * must not trigger the device-wide synchronisation cudaFree implies.  psi_dev:
+ * 2^n_qubits amplitudes of dtype in qubit order (address bit q = qubit q), zero
+ * outside the sector with n_alpha alpha and n_beta beta electrons.  All scratch
+ * lives in one fixed 8 MiB device array that the library reserves on every GPU
+ * that loads it, until the process exits; it holds 4 bytes per sector
+ * determinant plus about 1.4 MB of partial sums, so sectors above roughly 1.7
+ * million determinants are rejected with SV_ERR_ARG (use sv_rdm1).  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  Every call reuses the same
+ * array, so calls whose work overlaps on the GPU (other streams, other threads)
+ * race: serialise them.  Runs on cuda_stream (may be NULL) and synchronises it.
+ * No counterpart in the paper: an operational variant of sv_rdm1. */
+sv_status sv_rdm1_noalloc(const void *psi_dev, int n_qubits, sv_dtype dtype, int n_alpha, int n_beta,
+                          void *cuda_stream, double *re_out, double *im_out);
+
 /* ---- many small problems in one launch --------------------------------------- */
 
 typedef struct sv_batch *sv_batch_handle;

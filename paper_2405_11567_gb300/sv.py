@@ -26,7 +26,7 @@ EXPORTS = (
     "sv_get_state", "sv_state_device_ptr", "sv_set_layout", "sv_get_layout", "sv_ham_create", "sv_ham_destroy", "sv_apply_ansatz",
     "sv_energy", "sv_energy_grad", "sv_rdm1", "sv_set_option", "sv_phase_times", "sv_last_error",
     "sv_launch_count", "sv_version", "sv_batch_create", "sv_batch_energy_grad", "sv_batch_set_time_limit",
-    "sv_batch_launch_count", "sv_batch_destroy",
+    "sv_batch_launch_count", "sv_batch_destroy", "sv_rdm1_noalloc",
 )
 
 
@@ -90,6 +90,7 @@ def lib():
             "sv_batch_set_time_limit": (i32, [vp, dbl]),
             "sv_batch_launch_count": (ctypes.c_uint64, [vp]),
             "sv_batch_destroy": (i32, [vp]),
+            "sv_rdm1_noalloc": (i32, [vp, i32, i32, i32, i32, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -226,6 +227,16 @@ def sv_rdm1(h, n_orb: int) -> np.ndarray:
     re = np.zeros((2, n_orb, n_orb))
     im = np.zeros((2, n_orb, n_orb))
     _ck(lib().sv_rdm1(h, _ptr(re), _ptr(im)), h)
+    return re + 1j * im
+
+
+def sv_rdm1_noalloc(psi_dev: int, n_qubits: int, dtype: int, n_alpha: int, n_beta: int, stream=None) -> np.ndarray:
+    """1-RDM of a device-resident state in qubit order, using only the library's fixed scratch array."""
+    N = n_qubits // 2
+    re = np.zeros((2, N, N))
+    im = np.zeros((2, N, N))
+    _ck(lib().sv_rdm1_noalloc(ctypes.c_void_p(psi_dev), int(n_qubits), int(dtype), int(n_alpha), int(n_beta),
+                              _stream_ptr(stream), _ptr(re), _ptr(im)))
     return re + 1j * im
 
 
