@@ -56,6 +56,25 @@ def touched_bytes(ops, n, amp_bytes):
     return (4.0 * (2.0 ** (n - nbits)) * amp_bytes)
 
 
+# ---------------------------------------------------------------- ranks
+
+def reduce_max(values):
+    """Element-wise maximum over all ranks (identity without torch.distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def throughput(world, steps, max_ms):
+    """Evaluations of all ranks per second of the slowest rank: each rank runs `steps` of its own replica."""
+    return world * steps / (max_ms / 1000.0)
+
+
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -241,10 +260,7 @@ def run_ours(args, rank, world, local_rank):
         ms = ev0.elapsed_time(ev1)
         launches = st.launches - launches0
         clk = clocks.stop()
-        if dist:
-            t = torch.tensor([ms, t_host], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms, t_host = float(t[0]), float(t[1])
+        ms, t_host = reduce_max([ms, t_host])
         avg = {k: statistics.mean(ph[k] for ph in phases) for k in phases[0]}
         st.close()
         return dict(ms=ms, t_host=t_host, phases=avg, clocks=clk, launches=launches, out=outs)
@@ -277,8 +293,8 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return 0
     K = args.steps
-    value = world * K / (r64["ms"] / 1000.0)
-    e2e = world * K / r64["t_host"]
+    value = throughput(world, K, r64["ms"])
+    e2e = throughput(world, K, 1000.0 * r64["t_host"])
     # roofline of the dominant kernel (by phase time), algorithmic bytes per launch / mean launch time
     amp = 8
     rot_bytes = touched_bytes(p["ops"], n, amp)
@@ -313,7 +329,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(r64["launches"]),
     }
     if r128 is not None:
-        v128 = world * K / (r128["ms"] / 1000.0)
+        v128 = throughput(world, K, r128["ms"])
         line["fp64_state"] = {"value": v128, "ms_per_step": r128["ms"] / K, "phases_ms": r128["phases"],
                               "clocks": r128["clocks"]}
         line["speedup_fp32_over_fp64"] = value / v128

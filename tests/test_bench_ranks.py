@@ -1,0 +1,55 @@
+"""The N > 1 path of bench.py on CPU: two gloo ranks, each timing its own replica
+("replicas only": the path does not shard), rank 0 reporting the evaluations of all
+ranks over the slowest rank's time.  The reference arm runs on rank 0 only."""
+import multiprocessing as mp
+import os
+import socket
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    ms, host = bench.reduce_max([100.0 * (rank + 1), 2.0 - rank])   # rank 1 is the slow device, rank 0 the slow host
+    value = bench.throughput(world, 5, ms)
+    # the reference arm: only rank 0 works, the others return at once
+    import argparse
+    other = bench.run_reference(argparse.Namespace(steps=1, warmup=0, gpus=world), rank, world) if rank else None
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, ms, host, value, other))
+
+
+def test_two_gloo_ranks_take_the_slowest():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, host, value, other in out:
+        assert ms == 200.0 and host == 2.0                 # max over ranks, on every rank
+        assert abs(value - 2 * 5 / 0.2) < 1e-9             # all ranks' evaluations over the slowest time
+    assert out[1][4] == 0                                  # reference arm: rank 1 exits without work
+
+
+def test_single_process_reduce_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_max([3.0, 4.0]) == [3.0, 4.0]
+    assert bench.throughput(1, 4, 2000.0) == 2.0
