@@ -349,6 +349,47 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def op_profile(args):
+    """Per-operator rotation timing (CUDA events per launch) grouped by the operator's lowest
+    address bit in the automatic storage layout: the cost of short contiguous runs."""
+    import torch
+    from paper_2405_11567_gb300 import build as libbuild
+    from paper_2405_11567_gb300 import sv
+    libbuild.build()
+    p = problem(args)
+    n = p["n_qubits"]
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    stream = torch.cuda.Stream()
+    peak, _ = measured_peaks()
+    out = {}
+    for dtype in ("c64", "c128"):
+        st = sv.StateVector(n, dtype, stream)
+        st.prepare_hf(p["occ"])
+        st.energy_grad(ham, p["ops"], p["theta"])          # picks the automatic layout
+        lay = st.layout()
+        st.set_option(sv.SV_OPT_LAYOUT_AUTO, 0)
+        st.prepare_hf(p["occ"])
+        groups = {}
+        for k, op in enumerate(p["ops"]):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st.apply_ansatz(op[None, :], p["theta"][k:k + 1])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            kind = int(op[0])
+            qs = [op[1], op[3]] if kind == 1 else list(op[1:5])
+            low = min(int(min(lay[q] for q in qs)), 5)
+            b = touched_bytes(op[None, :], n, 8 if dtype == "c64" else 16)[0]
+            groups.setdefault("%s, lowest address bit %s" % ("single" if kind == 1 else "double",
+                                                             ">=5" if low == 5 else low), []).append(
+                b / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        out[dtype] = {k: {"ops": len(v), "median_gbs": float(np.median(v)), "frac_of_peak": float(np.median(v)) / peak}
+                      for k, v in sorted(groups.items())}
+        st.close()
+    print(json.dumps({"op_profile": out, "workload": workload_config(p)["workload"], "peak_gbs": peak}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -358,6 +399,8 @@ def main():
     ap.add_argument("--no-c128", action="store_true", help="skip the complex128 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) timing")
+    ap.add_argument("--op-profile", action="store_true",
+                    help="per-operator rotation bandwidth by lowest address bit (diagnostic, not the bench line)")
     ap.add_argument("--qubits", type=int, default=0,
                     help="profiling only: a smaller register (same generator, n/3 rounded to even electrons, "
                          "200 operators); the bench line is then not the headline workload")
@@ -365,6 +408,8 @@ def main():
     rank, world, local_rank = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.op_profile:
+        return op_profile(args)
     if world > 1:
         import torch
         import torch.distributed as dist

@@ -123,6 +123,11 @@ sv_status sv_prepare_state(sv_handle h, const void *amplitudes_host, int n_alpha
 /* Copy the current state (2^n amplitudes, dtype of the handle) to host memory. */
 sv_status sv_get_state(sv_handle h, void *amplitudes_host);
 
+/* Amplitudes of `count` basis states (indices in qubit order, each < 2^n) of the
+ * current state, written to host memory (count amplitudes of the handle's dtype):
+ * sampling a large state without copying all of it. */
+sv_status sv_get_amplitudes(sv_handle h, const uint64_t *basis, int count, void *amplitudes_host);
+
 /* Device pointer of the state vector (2^n amplitudes), for callers that read
  * it on the GPU.  Valid until sv_destroy.  Amplitudes are stored in the handle's
  * layout (sv_get_layout): the amplitude of basis state x sits at the address

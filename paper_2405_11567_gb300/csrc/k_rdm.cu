@@ -11,9 +11,10 @@
 //                      P and Q (Jordan-Wigner sign of a+_P a_Q on x);
 //                      n_{qp} = conj(n_{pq}).
 // Sector-gather variant: one thread per XPT basis indices of the sector list;
-// each element's per-thread sum is reduced across the warp with shuffles and
-// added by lane 0 into the warp's own shared-memory slot (no atomics), and the
-// block adds its warps in a fixed order at the end: bit-identical reruns.
+// each element's per-thread sum is reduced across the warp with shuffles (in the
+// state precision: at most 32 * XPT terms) and added in float64 by lane 0 into the
+// warp's own shared-memory slot (no atomics), and the block adds its warps in a
+// fixed order at the end: bit-identical reruns.
 #include <cstring>
 #include <vector>
 
@@ -65,15 +66,15 @@ k_rdm_gather(const cplx<R> *__restrict__ psi, const uint32_t *__restrict__ secto
                     re += px[t].x * px[t].x + px[t].y * px[t].y;
                 }
             }
-            double dre = (double)re, dim = (double)im;
+            // warp sum in the state precision (32 x XPT terms), then float64 per warp
             #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                dre += __shfl_down_sync(0xffffffffu, dre, o);
-                dim += __shfl_down_sync(0xffffffffu, dim, o);
+                re += __shfl_down_sync(0xffffffffu, re, o);
+                im += __shfl_down_sync(0xffffffffu, im, o);
             }
             if (lane == 0) {
-                s_acc[warp * 2 * n_el + 2 * e] += dre;
-                s_acc[warp * 2 * n_el + 2 * e + 1] += dim;
+                s_acc[warp * 2 * n_el + 2 * e] += (double)re;
+                s_acc[warp * 2 * n_el + 2 * e + 1] += (double)im;
             }
         }
     }

@@ -43,15 +43,172 @@ struct RowArgs {
     int Db;
 };
 
+// Per-block lists of everything that depends only on the block's beta string b.
+template <typename R>
+struct BetaSingle {
+    int Jb;        // partner row
+    int t;         // s * N + r: index of (.. |sr) and of the (sr|kk) row
+    uint32_t M;    // bits strictly between 2r+1 and 2s+1
+    uint32_t xbf;  // beta spread of b after r -> s
+    R vb;          // h_sr + sum_{k in b} ((sr|kk) - (sk|kr))
+    int cb;        // parity of the beta bits of b under M
+};
+
+template <typename R>
+struct BetaDouble {
+    int Jb;
+    uint32_t M;    // alpha bits that decide the sign: M1 ^ M2
+    int c;         // sign contribution of the beta bits
+    R v;           // (s1 r1|s2 r2) - (s1 r2|s2 r1)
+};
+
+constexpr int kMaxOrb = 16;
+constexpr int kMaxPairs = 120;   // C(16, 2)
+constexpr int kMaxBS = 64;       // nb (N - nb) <= 8 * 8
+constexpr int kMaxBD = 784;      // C(8, 2)^2
+
 template <typename R>
 __global__ void __launch_bounds__(kRowThreads) k_sigma_rows(RowArgs<R> A) {
+    __shared__ BetaSingle<R> bs[kMaxBS];
+    __shared__ BetaDouble<R> bd[kMaxBD];
+    __shared__ R JB[kMaxOrb * kMaxOrb];
+    __shared__ uint8_t opair[kMaxPairs][2], epair[kMaxPairs][2];
+    __shared__ int n_bs, n_op, n_ep;
     __shared__ double red[2 * kThreads / 32];
-    const int Ib = blockIdx.x;
-    const cplx<R> *row = A.C + (size_t)Ib * A.T.Da;
+    const SigmaTables<R> &T = A.T;
+    const int Ib = blockIdx.x, N = T.N, Da = T.Da;
+    const uint32_t b = T.strb[Ib], xb = T.sb[Ib], eb = ~b & T.maskN;
+    if (threadIdx.x == 0) {
+        int k = 0;
+        for (uint32_t o = b; o; o &= o - 1u) {
+            const int r = __ffs(o) - 1;
+            for (uint32_t e = eb; e; e &= e - 1u) {
+                const int s = __ffs(e) - 1;
+                BetaSingle<R> x;
+                x.Jb = T.rb[b ^ (1u << r) ^ (1u << s)];
+                x.t = s * N + r;
+                x.M = between(2 * r + 1, 2 * s + 1);
+                x.xbf = xb ^ (1u << (2 * r + 1)) ^ (1u << (2 * s + 1));
+                R v = T.hm[s * N + r];
+                for (uint32_t o2 = b; o2; o2 &= o2 - 1u) v += T.Dt[(s * N + r) * N + __ffs(o2) - 1];
+                x.vb = v;
+                x.cb = par(xb & x.M);
+                bs[k++] = x;
+            }
+        }
+        n_bs = k;
+        int no = 0, ne = 0;
+        for (uint32_t o = b; o; o &= o - 1u)
+            for (uint32_t o2 = o & (o - 1u); o2; o2 &= o2 - 1u) {
+                opair[no][0] = (uint8_t)(__ffs(o) - 1);
+                opair[no][1] = (uint8_t)(__ffs(o2) - 1);
+                ++no;
+            }
+        for (uint32_t e = eb; e; e &= e - 1u)
+            for (uint32_t e2 = e & (e - 1u); e2; e2 &= e2 - 1u) {
+                epair[ne][0] = (uint8_t)(__ffs(e) - 1);
+                epair[ne][1] = (uint8_t)(__ffs(e2) - 1);
+                ++ne;
+            }
+        n_op = no;
+        n_ep = ne;
+    }
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        const R *jt = T.Jt + i * N;  // i = q * N + p
+        R v = 0;
+        for (uint32_t o = b; o; o &= o - 1u) v += jt[__ffs(o) - 1];
+        JB[i] = v;
+    }
+    __syncthreads();
+    const int nbd = n_op * n_ep, nbs = n_bs;
+    for (int d = threadIdx.x; d < nbd; d += blockDim.x) {
+        const int oi = d / n_ep, ei = d - oi * n_ep;
+        const int r1 = opair[oi][0], r2 = opair[oi][1], s1 = epair[ei][0], s2 = epair[ei][1];
+        const int i = 2 * r1 + 1, j = 2 * r2 + 1, aa = 2 * s1 + 1, bb = 2 * s2 + 1;
+        const uint32_t M1 = between(i, bb), M2 = between(j, aa);
+        const uint32_t xb1 = xb ^ (1u << i) ^ (1u << bb);
+        BetaDouble<R> x;
+        x.Jb = T.rb[b ^ (1u << r1) ^ (1u << r2) ^ (1u << s1) ^ (1u << s2)];
+        x.M = M1 ^ M2;
+        x.c = 1 ^ par(xb & M1) ^ par(xb1 & M2);  // T = -(a+_a a_j)(a+_b a_i)
+        x.v = eri4<R>(T, s1, r1, s2, r2) - eri4<R>(T, s1, r2, s2, r1);
+        bd[d] = x;
+    }
+    __syncthreads();
+    const cplx<R> *row = A.C + (size_t)Ib * Da;
     double e_acc = 0.0, n_acc = 0.0;
-    for (int Ia = threadIdx.x; Ia < A.T.Da; Ia += blockDim.x) {
+    for (int Ia = threadIdx.x; Ia < Da; Ia += blockDim.x) {
+        const uint32_t a = T.stra[Ia], xa = T.sa[Ia], x = xa | xb;
+        const uint32_t ea = ~a & T.maskN;
         const cplx<R> c0 = row[Ia];
-        const cplx<R> acc = sigma_at<R>(A.T, A.C, Ia, Ib, c0);
+        double d = T.e_shift;
+        for (uint32_t o = x; o; o &= o - 1u) {
+            const int k = __ffs(o) - 1;
+            d += T.hdiag[k];
+            for (uint32_t o2 = o & (o - 1u); o2; o2 &= o2 - 1u) d += T.Jp[k * T.n + __ffs(o2) - 1];
+        }
+        cplx<R> acc = mk<R>((R)d * c0.x, (R)d * c0.y);
+        // alpha singles (this row)
+        for (uint32_t o = a; o; o &= o - 1u) {
+            const int p = __ffs(o) - 1;
+            for (uint32_t e = ea; e; e &= e - 1u) {
+                const int q = __ffs(e) - 1;
+                const R *dt = T.Dt + (q * N + p) * N;
+                R v = T.hm[q * N + p] + JB[q * N + p];
+                for (uint32_t o2 = a; o2; o2 &= o2 - 1u) v += dt[__ffs(o2) - 1];
+                if (par(x & between(2 * p, 2 * q))) v = -v;
+                fma_c<R>(acc, v, row[T.ra[a ^ (1u << p) ^ (1u << q)]]);
+            }
+        }
+        // alpha-alpha doubles (this row)
+        for (uint32_t o = a; o; o &= o - 1u) {
+            const int p1 = __ffs(o) - 1;
+            for (uint32_t o2 = o & (o - 1u); o2; o2 &= o2 - 1u) {
+                const int p2 = __ffs(o2) - 1;
+                for (uint32_t e = ea; e; e &= e - 1u) {
+                    const int q1 = __ffs(e) - 1;
+                    for (uint32_t e2 = e & (e - 1u); e2; e2 &= e2 - 1u) {
+                        const int q2 = __ffs(e2) - 1;
+                        R v = eri4<R>(T, q1, p1, q2, p2) - eri4<R>(T, q1, p2, q2, p1);
+                        const int i = 2 * p1, j = 2 * p2, aa = 2 * q1, bb = 2 * q2;
+                        const uint32_t x1 = x ^ (1u << i) ^ (1u << bb);
+                        if (1 ^ par(x & between(i, bb)) ^ par(x1 & between(j, aa))) v = -v;
+                        fma_c<R>(acc, v, row[T.ra[a ^ (1u << p1) ^ (1u << p2) ^ (1u << q1) ^ (1u << q2)]]);
+                    }
+                }
+            }
+        }
+        // beta singles (partner rows, same column)
+        for (int k = 0; k < nbs; ++k) {
+            const BetaSingle<R> e = bs[k];
+            const R *jt = T.Jt + e.t * N;
+            R v = e.vb;
+            for (uint32_t o = a; o; o &= o - 1u) v += jt[__ffs(o) - 1];
+            if (e.cb ^ par(xa & e.M)) v = -v;
+            fma_c<R>(acc, v, A.C[(size_t)e.Jb * Da + Ia]);
+        }
+        // beta-beta doubles (partner rows, same column)
+        for (int k = 0; k < nbd; ++k) {
+            const BetaDouble<R> e = bd[k];
+            fma_c<R>(acc, (e.c ^ par(xa & e.M)) ? -e.v : e.v, A.C[(size_t)e.Jb * Da + Ia]);
+        }
+        // alpha-beta doubles: alpha p -> q outside, beta r -> s (block list) inside; value (qp|sr)
+        for (uint32_t o = a; o; o &= o - 1u) {
+            const int p = __ffs(o) - 1;
+            for (uint32_t e = ea; e; e &= e - 1u) {
+                const int q = __ffs(e) - 1;
+                const int Ja = T.ra[a ^ (1u << p) ^ (1u << q)];
+                const uint32_t B = between(2 * p, 2 * q);
+                const int sa0 = par(xa & B);
+                const R *erib = T.eri + (size_t)(q * N + p) * N * N;
+                for (int k = 0; k < nbs; ++k) {
+                    const BetaSingle<R> bk = bs[k];
+                    const R v = erib[bk.t];
+                    const int sg = bk.cb ^ par(xa & bk.M) ^ sa0 ^ par(bk.xbf & B);
+                    fma_c<R>(acc, sg ? -v : v, A.C[(size_t)bk.Jb * Da + Ja]);
+                }
+            }
+        }
         if (A.lam) A.lam[A.sa_s[Ia] | A.sb_s[Ib]] = acc;
         e_acc += (double)c0.x * (double)acc.x + (double)c0.y * (double)acc.y;
         n_acc += (double)c0.x * (double)c0.x + (double)c0.y * (double)c0.y;

@@ -219,6 +219,24 @@ cudaError_t launch_permute(const void *in, void *out, int dtype, int n, const in
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- sampling
+
+// out[i] = psi[addr[i]] (addresses already in the storage layout)
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_gather(const cplx<R> *__restrict__ psi, const uint32_t *__restrict__ addr,
+                                                     int count, cplx<R> *__restrict__ out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) out[i] = psi[addr[i]];
+}
+
+cudaError_t launch_gather(const void *psi, int dtype, const uint32_t *addr, int count, void *out, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    int grid = (count + kThreads - 1) / kThreads;
+    if (grid > 1024) grid = 1024;
+    if (dtype == SV_C64) k_gather<float><<<grid, kThreads, 0, st>>>((const float2 *)psi, addr, count, (float2 *)out);
+    else k_gather<double><<<grid, kThreads, 0, st>>>((const double2 *)psi, addr, count, (double2 *)out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- reductions
 
 // out[r] = sum_c partials[r * cols + c], fixed order (one block per row).

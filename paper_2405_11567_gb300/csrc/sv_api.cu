@@ -30,6 +30,7 @@ cudaError_t launch_expect_gather(const void *psi, void *sigma, int dtype, int n,
 int rdm_gather_grid(uint64_t count, int sm_count);
 int rdm_elements_bytes(int n, const int *perm, std::vector<uint8_t> &out);
 cudaError_t launch_permute(const void *in, void *out, int dtype, int n, const int *sg, int sm_count, cudaStream_t st);
+cudaError_t launch_gather(const void *psi, int dtype, const uint32_t *addr, int count, void *out, cudaStream_t st);
 cudaError_t launch_rdm_gather(const void *psi, int dtype, const uint32_t *sector, uint64_t count,
                               const void *elems, int n_el, int grid, double *partial, cudaStream_t st);
 
@@ -703,6 +704,32 @@ sv_status sv_get_state(sv_handle h, void *amplitudes_host) {
         src = h->lam;
     }
     SV_CUDA(h, cudaMemcpyAsync(amplitudes_host, src, vec_bytes(h), cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SV_OK;
+}
+
+sv_status sv_get_amplitudes(sv_handle h, const uint64_t *basis, int count, void *amplitudes_host) {
+    SV_TRY(check_ready(h));
+    if (count < 0 || (count > 0 && (!basis || !amplitudes_host))) return fail(h, SV_ERR_ARG, "bad arguments");
+    if (count == 0) return SV_OK;
+    std::vector<uint32_t> addr(count);
+    for (int i = 0; i < count; ++i) {
+        if (basis[i] >= h->dim) return fail(h, SV_ERR_ARG, "basis index out of range");
+        addr[i] = map_bits((uint32_t)basis[i], h->perm);
+    }
+    DeviceGuard g(h->device);
+    // scratch: the addresses, then the gathered amplitudes, in the reduction buffer
+    const size_t addr_doubles = ((size_t)count * 4 + 7) / 8;
+    const size_t out_off = (addr_doubles + 1) / 2 * 2;  // 16-byte aligned for complex128
+    const size_t amp_doubles = (size_t)count * h->amp_bytes / 8;
+    SV_TRY(ensure_partials(h, out_off + amp_doubles));
+    uint32_t *d_addr = (uint32_t *)h->partials;
+    void *d_out = h->partials + out_off;
+    SV_CUDA(h, cudaMemcpyAsync(d_addr, addr.data(), (size_t)count * 4, cudaMemcpyHostToDevice, h->stream));
+    SV_CUDA(h, launch_gather(h->psi, h->dtype, d_addr, count, d_out, h->stream));
+    h->launches++;
+    SV_CUDA(h, cudaMemcpyAsync(amplitudes_host, d_out, (size_t)count * h->amp_bytes, cudaMemcpyDeviceToHost,
+                               h->stream));
     SV_CUDA(h, cudaStreamSynchronize(h->stream));
     return SV_OK;
 }

@@ -23,7 +23,7 @@ STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV
 # every symbol include/sv.h declares
 EXPORTS = (
     "sv_create", "sv_create_with_buffers", "sv_destroy", "sv_prepare_hf", "sv_prepare_state",
-    "sv_get_state", "sv_state_device_ptr", "sv_set_layout", "sv_get_layout", "sv_ham_create", "sv_ham_destroy", "sv_apply_ansatz",
+    "sv_get_state", "sv_get_amplitudes", "sv_state_device_ptr", "sv_set_layout", "sv_get_layout", "sv_ham_create", "sv_ham_destroy", "sv_apply_ansatz",
     "sv_energy", "sv_energy_grad", "sv_rdm1", "sv_set_option", "sv_phase_times", "sv_last_error",
     "sv_launch_count", "sv_version", "sv_batch_create", "sv_batch_energy_grad", "sv_batch_set_time_limit",
     "sv_batch_launch_count", "sv_batch_destroy", "sv_rdm1_noalloc",
@@ -71,6 +71,7 @@ def lib():
             "sv_prepare_hf": (i32, [vp, vp, i32]),
             "sv_prepare_state": (i32, [vp, vp, i32, i32]),
             "sv_get_state": (i32, [vp, vp]),
+            "sv_get_amplitudes": (i32, [vp, vp, i32, vp]),
             "sv_state_device_ptr": (i32, [vp, pp]),
             "sv_set_layout": (i32, [vp, vp]),
             "sv_get_layout": (i32, [vp, vp]),
@@ -165,6 +166,13 @@ def sv_prepare_state(h, amplitudes, n_alpha: int, n_beta: int):
 def sv_get_state(h, n_qubits: int, dtype: int) -> np.ndarray:
     out = np.empty(1 << n_qubits, dtype=np.complex64 if dtype == SV_C64 else np.complex128)
     _ck(lib().sv_get_state(h, _ptr(out)), h)
+    return out
+
+
+def sv_get_amplitudes(h, basis, dtype: int) -> np.ndarray:
+    idx = np.ascontiguousarray(np.asarray(basis, dtype=np.uint64).reshape(-1))
+    out = np.empty(len(idx), dtype=np.complex64 if dtype == SV_C64 else np.complex128)
+    _ck(lib().sv_get_amplitudes(h, _ptr(idx), len(idx), _ptr(out)), h)
     return out
 
 
@@ -375,6 +383,9 @@ class StateVector:
 
     def state(self) -> np.ndarray:
         return sv_get_state(self.handle, self.n, self.dtype)
+
+    def amplitudes(self, basis) -> np.ndarray:
+        return sv_get_amplitudes(self.handle, basis, self.dtype)
 
     def apply_ansatz(self, ops, theta):
         sv_apply_ansatz(self.handle, ops, theta)
