@@ -52,7 +52,8 @@ def measured_peaks():
 
 def touched_bytes(ops, n, amp_bytes):
     """Algorithmic bytes of one rotation per op: read + write of the 2 * 2^(n - nbits) touched amplitudes."""
-    nbits = np.where(np.asarray(ops)[:, 0] == 1, 2, 4)
+    kind = np.asarray(ops)[:, 0]
+    nbits = np.where((kind == 1) | (kind == 3), 2, 4)
     return (4.0 * (2.0 ** (n - nbits)) * amp_bytes)
 
 
@@ -377,10 +378,10 @@ def op_profile(args):
             e1.record(stream)
             torch.cuda.synchronize()
             kind = int(op[0])
-            qs = [op[1], op[3]] if kind == 1 else list(op[1:5])
+            qs = [op[1], op[3]] if kind in (1, 3) else list(op[1:5])
             low = min(int(min(lay[q] for q in qs)), 5)
             b = touched_bytes(op[None, :], n, 8 if dtype == "c64" else 16)[0]
-            groups.setdefault("%s, lowest address bit %s" % ("single" if kind == 1 else "double",
+            groups.setdefault("%s, lowest address bit %s" % ("single" if kind in (1, 3) else "double",
                                                              ">=5" if low == 5 else low), []).append(
                 b / (e0.elapsed_time(e1) / 1e3) / 1e9)
         out[dtype] = {k: {"ops": len(v), "median_gbs": float(np.median(v)), "frac_of_peak": float(np.median(v)) / peak}

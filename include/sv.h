@@ -72,10 +72,13 @@ typedef enum {
 typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
 
 /* One excitation operator.  kind 1: single, occ[0] -> vir[0] (occ[1], vir[1]
- * ignored); kind 2: double, occ[0] < occ[1], vir[0] < vir[1].  Indices are
- * spin-orbitals in [0, n_qubits); the four (two) indices are distinct and the
- * operator conserves S_z (same number of alpha spin-orbitals among occ and
- * vir).  Anything else is SV_ERR_ARG. */
+ * ignored); kind 2: double, occ[0] < occ[1], vir[0] < vir[1].  Kinds 3 and 4
+ * are the same single and double as qubit excitations (the qubit-excitation-
+ * based pool of "Computational Details"): products of qubit raising / lowering
+ * operators with no Jordan-Wigner string, i.e. the same pairs of basis states
+ * rotated with sign +1.  Indices are spin-orbitals in [0, n_qubits); the four
+ * (two) indices are distinct and the operator conserves S_z (same number of
+ * alpha spin-orbitals among occ and vir).  Anything else is SV_ERR_ARG. */
 typedef struct {
     int32_t kind;
     int32_t occ[2];
@@ -177,6 +180,15 @@ sv_status sv_energy(sv_handle h, sv_ham_handle ham, double *e_out);
  * return the handle holds psi(theta).  Either output may be NULL. */
 sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *ops, int n_ops,
                          const double *theta, double *e_out, double *grad_out);
+
+/* ADAPT-VQE operator screening ("Computational Details": the ansatz grows by the
+ * pool operator with the largest energy gradient): for the current state psi,
+ * grad_out[k] = dE/dtheta at theta = 0 of exp(theta G_k) psi = 2 Re <psi|H G_k|psi>
+ * / <psi|psi> for each of the n_pool pool operators (any kinds), and *e_out (may
+ * be NULL) = E(psi).  One expectation pass writing lambda = (H - c) psi in compact
+ * form, then one block per pool operator. */
+sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation *pool, int n_pool, double *e_out,
+                            double *grad_out);
 
 /* Spin-resolved one-particle density matrix of the current state,
  * n_{pq,sigma} = <psi|a+_{p sigma} a_{q sigma}|psi> / <psi|psi> (Methodology,

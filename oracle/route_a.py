@@ -8,7 +8,9 @@ Conventions (the readings of the paper listed in the design doc):
   basis index is its occupation (introduction; Methodology, Strategy 2, the
   Jordan-Wigner mapping of a+_{p sigma} a_{q sigma}).
 * an excitation row is ``(kind, i, j, a, b)``: kind 1 is T = a+_a a_i (j, b
-  unused), kind 2 is T = a+_a a+_b a_j a_i with i<j and a<b.  The ansatz is
+  unused), kind 2 is T = a+_a a+_b a_j a_i with i<j and a<b; kinds 3 and 4 are
+  the qubit excitations of the QEB pool ("Computational Details"): the same
+  products of qubit raising / lowering operators, without the Jordan-Wigner sign.  The ansatz is
   U_L ... U_1 |ref> with U_k = exp(theta_k (T_k - T_k^dagger)), op 1 acting
   first (ADAPT-VQE pool of fermionic excitations, Methodology, "Computational
   Details").
@@ -201,6 +203,6 @@ def cnot_counts(ops):
     2 N_single + 6 N_double (qubit pool).
     """
     ops = np.asarray(ops, dtype=np.int32).reshape(-1, 5)
-    ns = int(np.sum(ops[:, 0] == 1))
-    nd = int(np.sum(ops[:, 0] == 2))
+    ns = int(np.sum((ops[:, 0] == 1) | (ops[:, 0] == 3)))
+    nd = int(np.sum((ops[:, 0] == 2) | (ops[:, 0] == 4)))
     return 3 * ns + 13 * nd, 2 * ns + 6 * nd

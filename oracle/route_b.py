@@ -40,6 +40,17 @@ def annihilators(n: int):
     return out
 
 
+def qubit_lowering(n: int):
+    """[s_0, ..., s_{n-1}]: |0><1| on one qubit, identity elsewhere (no Jordan-Wigner string)."""
+    out = []
+    for j in range(n):
+        m = sp.identity(1, dtype=np.complex128, format="csr")
+        for q in range(n - 1, -1, -1):
+            m = sp.kron(m, _S if q == j else _I2, format="csr")
+        out.append(m.tocsr())
+    return out
+
+
 def hamiltonian(n: int, h, eri, e_nuc: float, a=None):
     """Dense-index sparse H = E_nuc + sum h[PQ] a+_P a_Q + 1/2 sum [PQ|RS] a+_P a+_R a_S a_Q."""
     N = n // 2
@@ -63,17 +74,21 @@ def hamiltonian(n: int, h, eri, e_nuc: float, a=None):
     return H.tocsr()
 
 
-def excitation_T(op, a):
-    """T for a row (kind, i, j, a, b): a+_a a_i, or a+_a a+_b a_j a_i."""
+def excitation_T(op, a, s=None):
+    """T for a row (kind, i, j, a, b): a+_a a_i (kind 1), a+_a a+_b a_j a_i (kind 2); kinds 3, 4 are the
+    same products of qubit operators s_j = |0><1| (list `s`, from qubit_lowering) with no string."""
     kind, i, j, va, vb = [int(v) for v in op]
-    ad = lambda k: a[k].conj().T  # noqa: E731
-    if kind == 1:
-        return (ad(va) @ a[i]).tocsr()
-    return (ad(va) @ ad(vb) @ a[j] @ a[i]).tocsr()
+    ops = a if kind <= 2 else s
+    if ops is None:
+        raise ValueError("qubit excitations need the qubit operators")
+    ad = lambda k: ops[k].conj().T  # noqa: E731
+    if kind in (1, 3):
+        return (ad(va) @ ops[i]).tocsr()
+    return (ad(va) @ ad(vb) @ ops[j] @ ops[i]).tocsr()
 
 
-def generator(op, a):
-    T = excitation_T(op, a)
+def generator(op, a, s=None):
+    T = excitation_T(op, a, s)
     return (T - T.conj().T).tocsr()
 
 
@@ -83,15 +98,15 @@ def basis_state(n: int, occ) -> np.ndarray:
     return psi
 
 
-def unitary(op, theta: float, a) -> np.ndarray:
+def unitary(op, theta: float, a, s=None) -> np.ndarray:
     """exp(theta G) as a dense matrix (scipy.linalg.expm)."""
-    return scipy.linalg.expm(theta * generator(op, a).toarray())
+    return scipy.linalg.expm(theta * generator(op, a, s).toarray())
 
 
-def apply_ansatz(ops, theta, psi0, a):
+def apply_ansatz(ops, theta, psi0, a, s=None):
     psi = np.array(psi0, dtype=np.complex128, copy=True)
     for op, t in zip(np.asarray(ops).reshape(-1, 5), np.asarray(theta).reshape(-1)):
-        psi = unitary(op, t, a) @ psi
+        psi = unitary(op, t, a, s) @ psi
     return psi
 
 
@@ -99,12 +114,12 @@ def energy(H, psi) -> float:
     return float(np.vdot(psi, H @ psi).real / np.vdot(psi, psi).real)
 
 
-def gradient(H, ops, theta, psi0, a) -> np.ndarray:
+def gradient(H, ops, theta, psi0, a, s=None) -> np.ndarray:
     """dE/dtheta_k = 2 Re <psi_L| H U_L..U_{k+1} G_k U_k..U_1 |psi0>, one k at a time."""
     ops = np.asarray(ops).reshape(-1, 5)
     theta = np.asarray(theta).reshape(-1)
     L = len(ops)
-    Us = [unitary(ops[k], theta[k], a) for k in range(L)]
+    Us = [unitary(ops[k], theta[k], a, s) for k in range(L)]
     psi_L = np.array(psi0, dtype=np.complex128)
     for U in Us:
         psi_L = U @ psi_L
@@ -114,7 +129,7 @@ def gradient(H, ops, theta, psi0, a) -> np.ndarray:
         v = np.array(psi0, dtype=np.complex128)
         for m in range(k + 1):
             v = Us[m] @ v
-        v = generator(ops[k], a) @ v
+        v = generator(ops[k], a, s) @ v
         for m in range(k + 1, L):
             v = Us[m] @ v
         g[k] = 2.0 * np.vdot(Hpsi, v).real

@@ -141,7 +141,11 @@ static int64_t det_index(const uint64_t *dets, int64_t D, uint64_t x)
 int64_t orc_det_index(const uint64_t *dets, int64_t D, uint64_t x) { return det_index(dets, D, x); }
 
 /* ---- excitation operators ------------------------------------------------ */
-/* op[0] = kind (1 single, 2 double); op[1..2] = occupied i, j; op[3..4] = virtual a, b. */
+/* op[0] = kind (1 single, 2 double: fermionic; 3 single, 4 double: qubit
+ * excitations); op[1..2] = occupied i, j; op[3..4] = virtual a, b.
+ * A qubit excitation ("Computational Details": the qubit-excitation-based pool)
+ * uses the qubit lowering / raising operators |0><1|, |1><0| on each qubit with
+ * no Jordan-Wigner string: the same determinants are connected, always with +1. */
 
 /* Apply a product of operators to |x>, right-most first: kinds[k] = 1 for a+,
  * 0 for a; modes[k] the spin-orbital.  Returns the accumulated sign (0 if the
@@ -158,27 +162,44 @@ static int apply_product(int count, const int *kinds, const int *modes, uint64_t
     return s;
 }
 
+/* The same product with qubit operators: a qubit flip that must find the bit in
+ * the right state, no sign. */
+static int apply_qubit_product(int count, const int *kinds, const int *modes, uint64_t x, uint64_t *y)
+{
+    *y = x;
+    for (int k = count - 1; k >= 0; --k) {
+        uint64_t bit = 1ULL << modes[k];
+        if (kinds[k]) { if (*y & bit) return 0; *y |= bit; }
+        else          { if (!(*y & bit)) return 0; *y &= ~bit; }
+    }
+    return 1;
+}
+
 /* T |x> : returns the sign (0 if annihilated) and the resulting determinant in *y. */
 static int exc_T(const int32_t *op, uint64_t x, uint64_t *y)
 {
-    if (op[0] == 1) {                       /* a+_a a_i */
+    int (*apply)(int, const int *, const int *, uint64_t, uint64_t *) =
+        op[0] >= 3 ? apply_qubit_product : apply_product;
+    if (op[0] == 1 || op[0] == 3) {         /* a+_a a_i */
         const int kinds[2] = {1, 0}, modes[2] = {op[3], op[1]};
-        return apply_product(2, kinds, modes, x, y);
+        return apply(2, kinds, modes, x, y);
     }
     /* a+_a a+_b a_j a_i */
     const int kinds[4] = {1, 1, 0, 0}, modes[4] = {op[3], op[4], op[2], op[1]};
-    return apply_product(4, kinds, modes, x, y);
+    return apply(4, kinds, modes, x, y);
 }
 
 /* T^dagger |x> : (a+_a a_i)^dagger = a+_i a_a ; (a+_a a+_b a_j a_i)^dagger = a+_i a+_j a_b a_a. */
 static int exc_Tdag(const int32_t *op, uint64_t x, uint64_t *y)
 {
-    if (op[0] == 1) {
+    int (*apply)(int, const int *, const int *, uint64_t, uint64_t *) =
+        op[0] >= 3 ? apply_qubit_product : apply_product;
+    if (op[0] == 1 || op[0] == 3) {
         const int kinds[2] = {1, 0}, modes[2] = {op[1], op[3]};
-        return apply_product(2, kinds, modes, x, y);
+        return apply(2, kinds, modes, x, y);
     }
     const int kinds[4] = {1, 1, 0, 0}, modes[4] = {op[1], op[2], op[4], op[3]};
-    return apply_product(4, kinds, modes, x, y);
+    return apply(4, kinds, modes, x, y);
 }
 
 /* Sign and target of T|x> for one determinant, exported for the sign-table tests. */

@@ -37,6 +37,7 @@ struct RowArgs {
     SigmaTables<R> T;
     const cplx<R> *C;       // [Db][Da] compact sector amplitudes
     cplx<R> *lam;           // dense sigma output (nullable)
+    cplx<R> *lamc;          // compact sigma output [Db][Da] (nullable)
     const uint32_t *sa_s;   // [Da] alpha spread in the storage layout: addresses
     const uint32_t *sb_s;   // [Db]
     double *partial;        // [2][Db]
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(kRowThreads) k_sigma_rows(RowArgs<R> A) {
             }
         }
         if (A.lam) A.lam[A.sa_s[Ia] | A.sb_s[Ib]] = acc;
+        if (A.lamc) A.lamc[(size_t)Ib * Da + Ia] = acc;
         e_acc += (double)c0.x * (double)acc.x + (double)c0.y * (double)acc.y;
         n_acc += (double)c0.x * (double)c0.x + (double)c0.y * (double)c0.y;
     }
@@ -254,24 +256,24 @@ struct RowTables {
 };
 
 template <typename R>
-static RowArgs<R> row_args(const void *C, void *lam, int n, const RowTables &T, const double *hdiag, const double *Jp,
-                           double e_shift, double *partial) {
+static RowArgs<R> row_args(const void *C, void *lam, void *lamc, int n, const RowTables &T, const double *hdiag,
+                           const double *Jp, double e_shift, double *partial) {
     RowArgs<R> A;
     A.T.sa = T.sa; A.T.sb = T.sb; A.T.stra = T.stra; A.T.strb = T.strb; A.T.ra = T.ra; A.T.rb = T.rb;
     A.T.eri = (const R *)T.eri; A.T.hm = (const R *)T.hm; A.T.Dt = (const R *)T.Dt; A.T.Jt = (const R *)T.Jt;
     A.T.hdiag = hdiag; A.T.Jp = Jp; A.T.e_shift = e_shift;
     A.T.N = T.N; A.T.n = n; A.T.Da = T.Da; A.T.maskN = (1u << T.N) - 1u;
-    A.C = (const cplx<R> *)C; A.lam = (cplx<R> *)lam; A.sa_s = T.sa_s; A.sb_s = T.sb_s;
+    A.C = (const cplx<R> *)C; A.lam = (cplx<R> *)lam; A.lamc = (cplx<R> *)lamc; A.sa_s = T.sa_s; A.sb_s = T.sb_s;
     A.partial = partial; A.Db = T.Db;
     return A;
 }
 
-cudaError_t launch_sigma_rows(const void *C, void *lam, int dtype, int n, const RowTables &T, const double *hdiag,
+cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &T, const double *hdiag,
                               const double *Jp, double e_shift, double *partial, cudaStream_t st) {
     if (dtype == SV_C64) {
-        k_sigma_rows<float><<<T.Db, kRowThreads, 0, st>>>(row_args<float>(C, lam, n, T, hdiag, Jp, e_shift, partial));
+        k_sigma_rows<float><<<T.Db, kRowThreads, 0, st>>>(row_args<float>(C, lam, lamc, n, T, hdiag, Jp, e_shift, partial));
     } else {
-        k_sigma_rows<double><<<T.Db, kRowThreads, 0, st>>>(row_args<double>(C, lam, n, T, hdiag, Jp, e_shift, partial));
+        k_sigma_rows<double><<<T.Db, kRowThreads, 0, st>>>(row_args<double>(C, lam, lamc, n, T, hdiag, Jp, e_shift, partial));
     }
     return cudaGetLastError();
 }

@@ -31,6 +31,11 @@ int rdm_gather_grid(uint64_t count, int sm_count);
 int rdm_elements_bytes(int n, const int *perm, std::vector<uint8_t> &out);
 cudaError_t launch_permute(const void *in, void *out, int dtype, int n, const int *sg, int sm_count, cudaStream_t st);
 cudaError_t launch_gather(const void *psi, int dtype, const uint32_t *addr, int count, void *out, cudaStream_t st);
+void pool_op_from(const OpDesc &d, int N, void *dst);
+size_t pool_op_bytes();
+cudaError_t launch_pool_grad(const void *C, const void *L, int dtype, const void *ops, int n_ops, const uint32_t *sa,
+                             const uint32_t *sb, const uint16_t *stra, const uint16_t *strb, const uint16_t *ra,
+                             const uint16_t *rb, int Da, int Db, double *out, cudaStream_t st);
 cudaError_t launch_rdm_gather(const void *psi, int dtype, const uint32_t *sector, uint64_t count,
                               const void *elems, int n_el, int grid, double *partial, cudaStream_t st);
 
@@ -42,7 +47,7 @@ struct RowTables {
 };
 cudaError_t launch_compact(const void *psi, void *C, int dtype, const uint32_t *sa, const uint32_t *sb, int Da,
                            int Db, int sm_count, cudaStream_t st);
-cudaError_t launch_sigma_rows(const void *C, void *lam, int dtype, int n, const RowTables &T, const double *hdiag,
+cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &T, const double *hdiag,
                               const double *Jp, double e_shift, double *partial, cudaStream_t st);
 
 DevTables::~DevTables() {
@@ -450,7 +455,7 @@ static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void 
         h->launches++;
         RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
                     T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db};
-        SV_CUDA(h, launch_sigma_rows(h->Cbuf, sigma, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
+        SV_CUDA(h, launch_sigma_rows(h->Cbuf, sigma, nullptr, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
                                      h->partials, h->stream));
         h->launches++;
         SV_CUDA(h, launch_reduce_rows(h->partials, 2, h->Db, h->dout + out_off, h->stream));
@@ -484,7 +489,8 @@ static void layout_from_ops(int n, const sv_excitation *ops, int n_ops, int *per
     std::vector<long> cnt(n, 0);
     for (int k = 0; k < n_ops; ++k) {
         const sv_excitation &e = ops[k];
-        int qs[4] = {e.occ[0], e.vir[0], e.kind == 2 ? e.occ[1] : -1, e.kind == 2 ? e.vir[1] : -1};
+        const bool dbl = e.kind == 2 || e.kind == 4;
+        int qs[4] = {e.occ[0], e.vir[0], dbl ? e.occ[1] : -1, dbl ? e.vir[1] : -1};
         for (int q : qs)
             if (q >= 0 && q < n) cnt[q]++;
     }
@@ -607,6 +613,7 @@ sv_status sv_destroy(sv_handle h) {
                     (void *)h->str_a, (void *)h->str_b, (void *)h->rank_a, (void *)h->rank_b})
         if (p) cudaFree(p);
     dev_free(h, h->Cbuf, h->Cbuf_bytes);
+    dev_free(h, h->Lbuf, h->Lbuf_bytes);
     dev_free(h, h->partials, h->partials_cap * sizeof(double));
     dev_free(h, h->dout, h->dout_cap * sizeof(double));
     if (h->hpinned) cudaFreeHost(h->hpinned);
@@ -891,6 +898,67 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     if (e_out) *e_out = c + h->hpinned[0] / nrm;
     if (grad_out)
         for (size_t k = 0; k < L; ++k) grad_out[k] = 2.0 * h->hpinned[2 + k] / nrm;
+    return SV_OK;
+}
+
+sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation *pool, int n_pool, double *e_out,
+                            double *grad_out) {
+    SV_TRY(check_ready(h));
+    SV_TRY(check_ham(h, ham));
+    if (n_pool < 0 || (n_pool > 0 && (!pool || !grad_out))) return fail(h, SV_ERR_ARG, "bad pool arguments");
+    const int ident[32] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15,
+                           16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31};
+    const size_t ob = pool_op_bytes();
+    std::vector<uint8_t> host_ops((size_t)n_pool * ob);
+    for (int k = 0; k < n_pool; ++k) {
+        OpDesc d;
+        std::string why;
+        if (!make_op(pool[k], h->n, ident, d, why)) {
+            char buf[64];
+            snprintf(buf, sizeof buf, "pool op %d: ", k);
+            return fail(h, SV_ERR_ARG, buf + why);
+        }
+        pool_op_from(d, h->n / 2, host_ops.data() + (size_t)k * ob);
+    }
+    DeviceGuard g(h->device);
+    DevTables *T;
+    SV_TRY(get_tables(h, ham, &T));
+    SV_TRY(ensure_strings(h));
+    const size_t cb = (size_t)h->Da * h->Db * h->amp_bytes;
+    if (h->Lbuf_bytes < cb) {
+        dev_free(h, h->Lbuf, h->Lbuf_bytes);
+        h->Lbuf = nullptr;
+        h->Lbuf_bytes = 0;
+        SV_TRY(dev_alloc(h, &h->Lbuf, std::max<size_t>(cb, 16), "compact sigma"));
+        h->Lbuf_bytes = std::max<size_t>(cb, 16);
+    }
+    const size_t op_doubles = ((size_t)n_pool * ob + 7) / 8;
+    SV_TRY(ensure_partials(h, std::max<size_t>(2 * (size_t)h->Db, 1) + op_doubles));
+    SV_TRY(ensure_out(h, 2 + (size_t)n_pool));
+    const double c = shift_for(h, ham);
+    SV_CUDA(h, launch_compact(h->psi, h->Cbuf, h->dtype, h->str_sa_s, h->str_sb_s, h->Da, h->Db, h->sm_count,
+                              h->stream));
+    h->launches++;
+    RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
+                T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db};
+    SV_CUDA(h, launch_sigma_rows(h->Cbuf, nullptr, h->Lbuf, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
+                                 h->partials, h->stream));
+    h->launches++;
+    SV_CUDA(h, launch_reduce_rows(h->partials, 2, h->Db, h->dout, h->stream));
+    h->launches++;
+    if (n_pool > 0) {
+        void *d_ops = h->partials + 2 * (size_t)h->Db;
+        SV_CUDA(h, cudaMemcpyAsync(d_ops, host_ops.data(), host_ops.size(), cudaMemcpyHostToDevice, h->stream));
+        SV_CUDA(h, launch_pool_grad(h->Cbuf, h->Lbuf, h->dtype, d_ops, n_pool, h->str_sa, h->str_sb, h->str_a,
+                                    h->str_b, h->rank_a, h->rank_b, h->Da, h->Db, h->dout + 2, h->stream));
+        h->launches++;
+    }
+    SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, (2 + (size_t)n_pool) * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+    SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    const double nrm = h->hpinned[1];
+    if (e_out) *e_out = c + h->hpinned[0] / nrm;
+    for (int k = 0; k < n_pool; ++k) grad_out[k] = 2.0 * h->hpinned[2 + k] / nrm;
     return SV_OK;
 }
 

@@ -180,6 +180,8 @@ struct sv_ctx {
     size_t str_bytes = 0;
     void *Cbuf = nullptr;      // compact amplitudes [Db][Da]
     size_t Cbuf_bytes = 0;
+    void *Lbuf = nullptr;      // compact sigma [Db][Da] (operator screening)
+    size_t Lbuf_bytes = 0;
     // reduction scratch
     double *partials = nullptr;
     size_t partials_cap = 0;   // doubles

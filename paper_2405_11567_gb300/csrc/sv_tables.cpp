@@ -30,7 +30,7 @@ namespace svk {
 static bool make_op_qubits(const sv_excitation &e, int n, OpDesc &d, std::string &why) {
     auto inrange = [&](int v) { return v >= 0 && v < n; };
     d = OpDesc();
-    if (e.kind == 1) {
+    if (e.kind == 1 || e.kind == 3) {
         int i = e.occ[0], a = e.vir[0];
         if (!inrange(i) || !inrange(a)) { why = "single excitation index out of range"; return false; }
         if (i == a) { why = "single excitation with occ == vir"; return false; }
@@ -38,12 +38,12 @@ static bool make_op_qubits(const sv_excitation &e, int n, OpDesc &d, std::string
         d.nbits = 2;
         d.m = (1u << i) | (1u << a);
         d.from = 1u << i;  // T = a+_a a_i acts on x with i occupied, a empty
-        d.sm = bits_between(i, a);
+        d.sm = e.kind == 1 ? bits_between(i, a) : 0u;  // qubit excitation: no string, sign +1
         d.pos[0] = std::min(i, a);
         d.pos[1] = std::max(i, a);
         return true;
     }
-    if (e.kind == 2) {
+    if (e.kind == 2 || e.kind == 4) {
         int i = e.occ[0], j = e.occ[1], a = e.vir[0], b = e.vir[1];
         if (!inrange(i) || !inrange(j) || !inrange(a) || !inrange(b)) {
             why = "double excitation index out of range"; return false;
@@ -58,10 +58,10 @@ static bool make_op_qubits(const sv_excitation &e, int n, OpDesc &d, std::string
         int q[4] = {i, j, a, b};
         std::sort(q, q + 4);
         for (int t = 0; t < 4; ++t) d.pos[t] = q[t];
-        d.sm = bits_between(q[0], q[1]) | bits_between(q[2], q[3]);
+        d.sm = e.kind == 2 ? (bits_between(q[0], q[1]) | bits_between(q[2], q[3])) : 0u;
         return true;
     }
-    why = "excitation kind must be 1 or 2";
+    why = "excitation kind must be 1, 2 (fermionic) or 3, 4 (qubit)";
     return false;
 }
 

@@ -55,6 +55,13 @@ def hf_occupation(n_elec: int):
     return list(range(int(n_elec)))
 
 
+def qeb_pool(n_qubits: int, n_elec: int) -> np.ndarray:
+    """The same excitations as uccsd_pool as qubit excitations (kinds 3 and 4: no Jordan-Wigner sign)."""
+    pool = uccsd_pool(n_qubits, n_elec).copy()
+    pool[:, 0] += 2
+    return pool
+
+
 def uccsd_pool(n_qubits: int, n_elec: int) -> np.ndarray:
     """All spin-conserving singles then doubles from the HF reference, rows (kind, i, j, a, b).
 

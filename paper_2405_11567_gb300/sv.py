@@ -24,7 +24,7 @@ STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV
 EXPORTS = (
     "sv_create", "sv_create_with_buffers", "sv_destroy", "sv_prepare_hf", "sv_prepare_state",
     "sv_get_state", "sv_get_amplitudes", "sv_state_device_ptr", "sv_set_layout", "sv_get_layout", "sv_ham_create", "sv_ham_destroy", "sv_apply_ansatz",
-    "sv_energy", "sv_energy_grad", "sv_rdm1", "sv_set_option", "sv_phase_times", "sv_last_error",
+    "sv_energy", "sv_energy_grad", "sv_pool_gradients", "sv_rdm1", "sv_set_option", "sv_phase_times", "sv_last_error",
     "sv_launch_count", "sv_version", "sv_batch_create", "sv_batch_energy_grad", "sv_batch_set_time_limit",
     "sv_batch_launch_count", "sv_batch_destroy", "sv_rdm1_noalloc",
 )
@@ -81,6 +81,7 @@ def lib():
             "sv_energy": (i32, [vp, vp, vp]),
             "sv_energy_grad": (i32, [vp, vp, vp, i32, vp, vp, vp]),
             "sv_rdm1": (i32, [vp, vp, vp]),
+            "sv_pool_gradients": (i32, [vp, vp, vp, i32, vp, vp]),
             "sv_set_option": (i32, [vp, i32, i64]),
             "sv_phase_times": (i32, [vp, vp, i32]),
             "sv_last_error": (ctypes.c_char_p, [vp]),
@@ -228,6 +229,14 @@ def sv_energy_grad(h, ham, ops, theta):
     e = np.zeros(1)
     g = np.zeros(max(len(o), 1))
     _ck(lib().sv_energy_grad(h, ham, _ptr(o), len(o), _ptr(t), _ptr(e), _ptr(g)), h)
+    return float(e[0]), g[:len(o)]
+
+
+def sv_pool_gradients(h, ham, pool):
+    o = _ops_array(pool)
+    e = np.zeros(1)
+    g = np.zeros(max(len(o), 1))
+    _ck(lib().sv_pool_gradients(h, ham, _ptr(o), len(o), _ptr(e), _ptr(g)), h)
     return float(e[0]), g[:len(o)]
 
 
@@ -398,6 +407,10 @@ class StateVector:
 
     def rdm1(self) -> np.ndarray:
         return sv_rdm1(self.handle, self.n // 2)
+
+    def pool_gradients(self, ham: Hamiltonian, pool):
+        """(E, gradients of appending each pool operator at angle 0) for the current state."""
+        return sv_pool_gradients(self.handle, ham.handle, pool)
 
     def set_option(self, opt, value):
         sv_set_option(self.handle, opt, value)

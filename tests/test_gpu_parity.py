@@ -412,3 +412,28 @@ def test_automatic_layout_moves_frequent_qubits_high():
     # address bit order follows usage: counts are non-decreasing along the address bits
     by_bit = cnt[np.argsort(lay)]
     assert np.all(np.diff(by_bit) >= 0)
+
+
+# ---------------------------------------------------------------- qubit excitations (QEB pool)
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_qubit_excitation_ansatz_matches_oracle(dtype):
+    n = 14
+    p = inputs.make_problem(n, 4, 50, seed=123)
+    pool = inputs.qeb_pool(n, 4)
+    rng = np.random.default_rng(6)
+    ops = np.vstack([pool[rng.choice(len(pool), size=30, replace=False)], p["ops"][:10]])  # QEB and fermionic mixed
+    theta = rng.normal(0, 0.3, size=len(ops))
+    sec = _oracle_problem(p)
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], ops, theta, A.hf_state(sec, p["occ"]))
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(n, dtype)
+    st.prepare_hf(p["occ"])
+    E, g = st.energy_grad(ham, ops, theta)
+    assert abs(E - Eref) <= TOL[dtype]["E"]
+    assert np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
+    psi = A.apply_ansatz(sec, ops, theta, A.hf_state(sec, p["occ"]))
+    assert np.max(np.abs(st.state()[sec.dets.astype(np.int64)] - psi)) <= TOL[dtype]["amp"] * 10
+    b = sv.Batch([dict(p, ops=ops, theta=theta)], dtype)
+    Eb, gb = b.energy_grad(theta)
+    assert abs(Eb[0] - Eref) <= TOL[dtype]["E"] and np.max(np.abs(gb[0] - gref)) <= TOL[dtype]["g"]

@@ -357,3 +357,38 @@ def test_table_iv_cnot_formula_reading():
         else:
             bad.append((sysname, basis))
     assert bad == [("Be", "cc-pVDZ")]
+
+
+# ---------------------------------------------------------------- qubit excitations (QEB pool)
+
+def test_qubit_excitations_route_a_matches_route_b():
+    n = 10
+    p = _problem(n, 4, 151)
+    pool = inputs.qeb_pool(n, 4)
+    rng = np.random.default_rng(8)
+    ops = pool[rng.choice(len(pool), size=16, replace=False)]
+    theta = rng.normal(0, 0.4, size=len(ops))
+    a = B.annihilators(n)
+    sq = B.qubit_lowering(n)
+    H = B.hamiltonian(n, p["h"], p["eri"], p["e_nuc"], a)
+    sec = oracle.Sector(n, 2, 2)
+    psiA = A.apply_ansatz(sec, ops, theta, A.hf_state(sec, p["occ"]))
+    psiB = B.apply_ansatz(ops, theta, B.basis_state(n, p["occ"]), a, sq)
+    np.testing.assert_allclose(psiA, psiB[sec.dets.astype(np.int64)], atol=1e-13)
+    EA, gA = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], ops, theta, A.hf_state(sec, p["occ"]))
+    assert abs(EA - B.energy(H, psiB)) < 1e-12
+    np.testing.assert_allclose(gA, B.gradient(H, ops, theta, B.basis_state(n, p["occ"]), a, sq), atol=1e-11)
+
+
+def test_qubit_excitation_is_the_fermionic_one_up_to_the_string_sign():
+    """Same partner determinant; the fermionic sign is the JW parity, the qubit one is +1."""
+    n = 10
+    for op in inputs.uccsd_pool(n, 4):
+        q = op.copy()
+        q[0] += 2
+        for x in range(1 << n):
+            sf, yf = A.exc_apply(op, x)
+            sq, yq = A.exc_apply(q, x)
+            assert (sf == 0) == (sq == 0)
+            if sf:
+                assert yf == yq and sq == 1
