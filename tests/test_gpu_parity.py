@@ -277,7 +277,8 @@ def test_errors_are_reported_not_raised_on_device():
         st.energy(ham)                       # no prepared state
     assert e.value.status == 5
     st.prepare_hf(p["occ"])
-    for bad in [(2, 1, 0, 2, 3), (2, 0, 1, 2, 2), (1, 0, -1, 1, -1), (2, 0, 1, 2, 9), (3, 0, 1, 2, 3)]:
+    for bad in [(2, 1, 0, 2, 3), (2, 0, 1, 2, 2), (1, 0, -1, 1, -1), (2, 0, 1, 2, 9), (5, 0, 1, 2, 3),
+                (3, 0, -1, 1, -1), (4, 0, 1, 2, 4)]:
         with pytest.raises(sv.SvError) as e:
             st.apply_ansatz(np.array([bad], np.int32), [0.1])
         assert e.value.status == 1
