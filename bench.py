@@ -57,6 +57,23 @@ def touched_bytes(ops, n, amp_bytes):
     return (4.0 * (2.0 ** (n - nbits)) * amp_bytes)
 
 
+def sector_touched_bytes(ops, n_orb, na, nb, amp_bytes):
+    """Algorithmic bytes of one rotation per op on sector storage: read + write of the
+    2 * C(N - k_a, na - f_a) C(N - k_b, nb - f_b) amplitudes it pairs, where k_a (f_a) is
+    the number of alpha spin-orbitals in the op's mask (among its occupied ones)."""
+    from math import comb
+    out = []
+    for kind, i, j, a, b in np.asarray(ops):
+        occ = [i] if kind in (1, 3) else [i, j]
+        vir = [a] if kind in (1, 3) else [a, b]
+        ka = sum(1 for q in occ + vir if q % 2 == 0)
+        fa = sum(1 for q in occ if q % 2 == 0)
+        kb, fb = len(occ) + len(vir) - ka, len(occ) - fa
+        cnt = comb(n_orb - ka, na - fa) * comb(n_orb - kb, nb - fb) if na >= fa and nb >= fb else 0
+        out.append(4.0 * cnt * amp_bytes)
+    return np.array(out)
+
+
 # ---------------------------------------------------------------- ranks
 
 def reduce_max(values):
@@ -228,8 +245,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     peak, peak_kind = measured_peaks()
 
-    def timed(dtype):
-        st = sv.StateVector(n, dtype, stream)
+    def timed(dtype, sector=False):
+        st = sv.StateVector(n, dtype, stream, sector=(p["na"], p["nb"]) if sector else None)
         st.set_option(sv.SV_OPT_PROFILE, 1)
         outs = {}
 
@@ -290,6 +307,8 @@ def run_ours(args, rank, world, local_rank):
 
     r64 = timed("c64")
     r128 = None if args.no_c128 else timed("c128")
+    rs64 = None if args.no_sector else timed("c64", sector=True)
+    rs128 = None if (args.no_sector or args.no_c128) else timed("c128", sector=True)
     rbatch = None if (args.qubits or args.no_batch) else timed_batch()
     if rank != 0:
         return 0
@@ -339,6 +358,26 @@ def run_ours(args, rank, world, local_rank):
             "max_abs_dg": float(np.max(np.abs(r64["out"]["g"] - r128["out"]["g"]))),
             "max_abs_drdm": float(np.max(np.abs(r64["out"]["rdm"] - r128["out"]["rdm"]))),
             "E_fp64": r128["out"]["E"]}
+    if rs64 is not None:
+        # sector storage: the same step on the compact C(N,na) C(N,nb) matrix (L2-resident at 30 qubits)
+        sb = sector_touched_bytes(p["ops"], p["n_orb"], p["na"], p["nb"], 8)
+        t_rot = rs64["phases"]["forward"] / L / 1000.0
+        t_adj = rs64["phases"]["reverse"] / L / 1000.0
+        sect = {"storage": "sector: C(15,5)^2 = 9,018,009 amplitudes (72 MB complex64)",
+                "value": throughput(world, K, rs64["ms"]), "unit": UNIT, "ms_per_step": rs64["ms"] / K,
+                "phases_ms": rs64["phases"], "clocks": rs64["clocks"], "gpu_launches": int(rs64["launches"]),
+                "kernels": {"rotation_c": {"algorithmic_gbs": sb.sum() / L / t_rot / 1e9,
+                                           "mean_launch_ms": t_rot * 1e3},
+                            "adjoint_c": {"algorithmic_gbs": 2.0 * sb.sum() / L / t_adj / 1e9,
+                                          "mean_launch_ms": t_adj * 1e3}},
+                "abs_dE_vs_dense_c64": abs(rs64["out"]["E"] - r64["out"]["E"]),
+                "max_abs_dg_vs_dense_c64": float(np.max(np.abs(rs64["out"]["g"] - r64["out"]["g"])))}
+        if rs128 is not None:
+            sect["fp64_state"] = {"value": throughput(world, K, rs128["ms"]), "ms_per_step": rs128["ms"] / K,
+                                  "phases_ms": rs128["phases"]}
+            if r128 is not None:
+                sect["abs_dE_vs_dense_c128"] = abs(rs128["out"]["E"] - r128["out"]["E"])
+        line["sector_storage"] = sect
     if rbatch is not None:
         line["batch_config4"] = rbatch
     if world == 1 and not args.no_cpu_baseline and not args.qubits:
@@ -400,6 +439,7 @@ def main():
     ap.add_argument("--no-c128", action="store_true", help="skip the complex128 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) timing")
+    ap.add_argument("--no-sector", action="store_true", help="skip the sector-storage timing")
     ap.add_argument("--op-profile", action="store_true",
                     help="per-operator rotation bandwidth by lowest address bit (diagnostic, not the bench line)")
     ap.add_argument("--qubits", type=int, default=0,

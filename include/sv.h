@@ -106,6 +106,31 @@ sv_status sv_create(int n_qubits, sv_dtype dtype, void *cuda_stream, sv_handle *
 sv_status sv_create_with_buffers(int n_qubits, sv_dtype dtype, void *cuda_stream,
                                  void *psi_dev, void *lam_dev, sv_handle *out);
 
+/* Create a handle whose state keeps only the amplitudes of one particle-number
+ * sector: n_alpha alpha and n_beta beta electrons among N = n_qubits/2 spatial
+ * orbitals, C(N, n_alpha) * C(N, n_beta) amplitudes instead of 2^n (9,018,009
+ * at 30 qubits and 5 + 5 electrons: 72 MB in complex64, held in L2).  Every
+ * operator of the method (the excitations, H, a+_{p s} a_{q s}) conserves both
+ * counts (Methodology: the spin-conserving UCCSD / ADAPT-VQE excitations and
+ * the second-quantised H), so the result of every call equals that of a dense
+ * handle (sv_create) on the same inputs.
+ *
+ * Device order of the amplitudes (sv_state_device_ptr): row-major matrix
+ * C[rank(beta string)][rank(alpha string)], where the alpha (beta) string of
+ * basis state x is its bits 2p (2p + 1), p = 0..N-1, packed into an N-bit
+ * integer, and rank = position among the strings of the same popcount in
+ * ascending order.  Host views are unchanged: sv_prepare_state and sv_get_state
+ * take / give the dense 2^n qubit-order vector (zero outside the sector),
+ * sv_get_amplitudes returns 0 for basis states outside the sector.
+ * sv_prepare_hf and sv_prepare_state reject states of another sector
+ * (SV_ERR_ARG); sv_set_layout accepts only the identity; there is no
+ * sv_create_with_buffers form.  Errors: SV_ERR_ARG for n_qubits outside
+ * [2, 32] or odd, counts outside [0, N], a bad dtype or NULL out; SV_ERR_OOM,
+ * SV_ERR_CUDA as for sv_create.  No counterpart in the paper: a storage choice of
+ * this library. */
+sv_status sv_create_sector(int n_qubits, int n_alpha, int n_beta, sv_dtype dtype, void *cuda_stream,
+                           sv_handle *out);
+
 /* Release the handle and every device buffer it owns.  NULL is accepted. */
 sv_status sv_destroy(sv_handle h);
 

@@ -3,8 +3,9 @@
 // Host orchestration only: argument validation (every check runs before any
 // device work, so SV_ERR_ARG leaves the device untouched), buffer management,
 // and the order of kernel launches on the handle's stream.  Every step of the
-// path itself runs in the kernels of k_state.cu, k_expect.cu, k_tiles.cu and
-// k_rdm.cu.
+// path itself runs in the kernels of k_state.cu (rotations, adjoint sweep),
+// k_rows.cu and k_expect.cu (expectation), k_rdm.cu, k_pool.cu and k_sector.cu
+// (sector storage).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,6 +39,21 @@ cudaError_t launch_pool_grad(const void *C, const void *L, int dtype, const void
                              const uint16_t *rb, int Da, int Db, double *out, cudaStream_t st);
 cudaError_t launch_rdm_gather(const void *psi, int dtype, const uint32_t *sector, uint64_t count,
                               const void *elems, int n_el, int grid, double *partial, cudaStream_t st);
+// sector storage (k_sector.cu)
+void sect_op_from(const OpDesc &d, int N, void *dst);
+size_t sect_op_bytes();
+int sector_grid(int Db, int sm_count);
+cudaError_t launch_rotate_c(void *psi, int dtype, const void *op, const uint32_t *sa, const uint32_t *sb,
+                            const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb, int Da,
+                            int Db, int grid, cudaStream_t st);
+cudaError_t launch_adjoint_c(void *psi, void *lam, int dtype, const void *op, const uint32_t *sa, const uint32_t *sb,
+                             const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb,
+                             int Da, int Db, int grid, double *partial, cudaStream_t st);
+int sect_rdm_elements(int n, std::vector<uint8_t> &out);
+cudaError_t launch_rdm_c(const void *psi, int dtype, const void *elems, int n_el, const uint32_t *sa,
+                         const uint32_t *sb, const uint16_t *stra, const uint16_t *strb, const uint16_t *ra,
+                         const uint16_t *rb, int Da, int Db, double *out, cudaStream_t st);
+cudaError_t launch_gather_c(const void *psi, int dtype, const uint32_t *idx, int count, void *out, cudaStream_t st);
 
 struct RowTables {
     const uint32_t *sa, *sb, *sa_s, *sb_s;
@@ -127,7 +143,9 @@ static void dev_free(sv_handle h, void *p, size_t bytes) {
     h->bytes_owned -= std::min<uint64_t>(h->bytes_owned, bytes);
 }
 
-static size_t vec_bytes(sv_handle h) { return (size_t)h->dim * h->amp_bytes; }
+// Bytes of one state-sized vector: 2^n amplitudes (dense storage) or the
+// C(N, na) C(N, nb) amplitudes of the sector (sector storage).
+static size_t vec_bytes(sv_handle h) { return (size_t)h->elems * h->amp_bytes; }
 
 static sv_status ensure_lam(sv_handle h) {
     if (h->lam) return SV_OK;
@@ -287,6 +305,11 @@ static sv_status ensure_strings(sv_handle h) {
     h->Db = (int)sb16.size();
     h->str_na = h->na;
     h->str_nb = h->nb;
+    h->h_stra = sa16;
+    h->h_strb = sb16;
+    h->h_ra = ra;
+    h->h_rb = rb;
+    if (h->storage == 1) return SV_OK;  // the state itself is the compact matrix
     size_t cb = (size_t)h->Da * h->Db * h->amp_bytes;
     if (h->Cbuf_bytes < cb) {
         dev_free(h, h->Cbuf, h->Cbuf_bytes);
@@ -396,10 +419,29 @@ static sv_status check_ham(sv_handle h, sv_ham_handle ham) {
 
 // ---------------------------------------------------------------- internal steps
 
+// Position of the qubit-space determinant x in the compact sector matrix
+// C[rank(beta string)][rank(alpha string)], or 0xFFFFFFFF when x lies outside the
+// (na, nb) sector.  Needs the host string tables (ensure_strings).
+static uint32_t compact_index(sv_handle h, uint64_t x) {
+    const int N = h->n / 2;
+    uint32_t a = 0, b = 0;
+    for (int p = 0; p < N; ++p) {
+        a |= (uint32_t)((x >> (2 * p)) & 1u) << p;
+        b |= (uint32_t)((x >> (2 * p + 1)) & 1u) << p;
+    }
+    if (__builtin_popcount(a) != h->na || __builtin_popcount(b) != h->nb) return 0xFFFFFFFFu;
+    return (uint32_t)h->h_rb[b] * (uint32_t)h->Da + h->h_ra[a];
+}
+
 static sv_status prepare_reference(sv_handle h) {
     if (h->ref_kind == 1) {
+        uint32_t addr = map_bits(h->ref_det, h->perm);
+        if (h->storage == 1) {
+            SV_TRY(ensure_strings(h));
+            addr = compact_index(h, h->ref_det);
+        }
         SV_CUDA(h, cudaMemsetAsync(h->psi, 0, vec_bytes(h), h->stream));
-        SV_CUDA(h, launch_set_basis(h->psi, h->dtype, map_bits(h->ref_det, h->perm), h->stream));
+        SV_CUDA(h, launch_set_basis(h->psi, h->dtype, addr, h->stream));
         h->launches++;
     } else if (h->ref_kind == 2) {
         SV_CUDA(h, cudaMemcpyAsync(h->psi, h->ref_vec, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
@@ -411,8 +453,17 @@ static sv_status prepare_reference(sv_handle h) {
 
 static sv_status forward(sv_handle h, const std::vector<OpDesc> &ops, bool checkpoints) {
     const int64_t C = h->ckpt_interval;
+    std::vector<uint8_t> so(sect_op_bytes());
+    if (h->storage == 1 && !ops.empty()) SV_TRY(ensure_strings(h));
     for (size_t k = 0; k < ops.size(); ++k) {
-        SV_CUDA(h, launch_rotate(h->psi, h->dtype, h->n, ops[k], h->sm_count, h->stream));
+        if (h->storage == 1) {
+            sect_op_from(ops[k], h->n / 2, so.data());
+            SV_CUDA(h, launch_rotate_c(h->psi, h->dtype, so.data(), h->str_sa, h->str_sb, h->str_a, h->str_b,
+                                       h->rank_a, h->rank_b, h->Da, h->Db, sector_grid(h->Db, h->sm_count),
+                                       h->stream));
+        } else {
+            SV_CUDA(h, launch_rotate(h->psi, h->dtype, h->n, ops[k], h->sm_count, h->stream));
+        }
         h->launches++;
         if (checkpoints && C > 0 && (k + 1) % (size_t)C == 0 && k + 1 < ops.size()) {
             size_t j = (k + 1) / (size_t)C - 1;
@@ -445,6 +496,19 @@ static void plan_checkpoints(sv_handle h, size_t L) {
 // <psi|(H - c)|psi> and <psi|psi> into dout[out_off], dout[out_off + 1] (device),
 // and sigma = (H - c) psi into `sigma` when it is not NULL.
 static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void *sigma, double c, int out_off) {
+    if (h->storage == 1) {
+        // the state is already the compact matrix; sigma is compact too (every entry written)
+        SV_TRY(ensure_strings(h));
+        SV_TRY(ensure_partials(h, 2 * (size_t)h->Db));
+        RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
+                    T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db};
+        SV_CUDA(h, launch_sigma_rows(h->psi, nullptr, sigma, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
+                                     h->partials, h->stream));
+        h->launches++;
+        SV_CUDA(h, launch_reduce_rows(h->partials, 2, h->Db, h->dout + out_off, h->stream));
+        h->launches++;
+        return SV_OK;
+    }
     if (h->expect_variant != 1) {
         // string rows (default)
         SV_TRY(ensure_strings(h));
@@ -548,8 +612,16 @@ const char *sv_last_error(sv_handle h) { return h ? h->err.c_str() : g_err.c_str
 
 uint64_t sv_launch_count(sv_handle h) { return h ? h->launches : 0; }
 
+static uint64_t binom(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    uint64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
+    return r;
+}
+
+// sect_na < 0: dense storage; otherwise sector storage of (sect_na, sect_nb).
 static sv_status create_common(int n_qubits, sv_dtype dtype, void *cuda_stream, void *psi_dev, void *lam_dev,
-                               sv_handle *out) {
+                               sv_handle *out, int sect_na = -1, int sect_nb = -1) {
     if (!out) return fail(nullptr, SV_ERR_ARG, "NULL output handle pointer");
     *out = nullptr;
     if (n_qubits < 2 || n_qubits > SV_MAX_QUBITS || (n_qubits & 1))
@@ -562,6 +634,14 @@ static sv_status create_common(int n_qubits, sv_dtype dtype, void *cuda_stream, 
     h->dtype = dtype;
     h->stream = (cudaStream_t)cuda_stream;
     h->dim = 1ull << n_qubits;
+    h->elems = h->dim;
+    if (sect_na >= 0) {
+        h->storage = 1;
+        h->na = sect_na;
+        h->nb = sect_nb;
+        h->elems = binom(n_qubits / 2, sect_na) * binom(n_qubits / 2, sect_nb);
+        h->layout_auto = false;
+    }
     h->amp_bytes = dtype == SV_C64 ? 8 : 16;
     for (int q = 0; q < 32; ++q) h->perm[q] = q;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
@@ -590,6 +670,16 @@ static sv_status create_common(int n_qubits, sv_dtype dtype, void *cuda_stream, 
 
 sv_status sv_create(int n_qubits, sv_dtype dtype, void *cuda_stream, sv_handle *out) {
     return create_common(n_qubits, dtype, cuda_stream, nullptr, nullptr, out);
+}
+
+sv_status sv_create_sector(int n_qubits, int n_alpha, int n_beta, sv_dtype dtype, void *cuda_stream, sv_handle *out) {
+    if (out) *out = nullptr;
+    if (n_qubits < 2 || n_qubits > SV_MAX_QUBITS || (n_qubits & 1))
+        return fail(nullptr, SV_ERR_ARG, "n_qubits must be even and in [2, 32]");
+    const int N = n_qubits / 2;
+    if (n_alpha < 0 || n_beta < 0 || n_alpha > N || n_beta > N)
+        return fail(nullptr, SV_ERR_ARG, "electron counts must be in [0, n_qubits / 2]");
+    return create_common(n_qubits, dtype, cuda_stream, nullptr, nullptr, out, n_alpha, n_beta);
 }
 
 sv_status sv_create_with_buffers(int n_qubits, sv_dtype dtype, void *cuda_stream, void *psi_dev, void *lam_dev,
@@ -636,6 +726,8 @@ sv_status sv_prepare_hf(sv_handle h, const int32_t *occ, int n_occ) {
         x |= 1u << j;
         if (j & 1) ++nb; else ++na;
     }
+    if (h->storage == 1 && (na != h->na || nb != h->nb))
+        return fail(h, SV_ERR_ARG, "determinant outside the handle's (n_alpha, n_beta) sector");
     DeviceGuard g(h->device);
     h->failed = false;
     h->prepared = false;
@@ -653,6 +745,8 @@ sv_status sv_prepare_state(sv_handle h, const void *amplitudes_host, int n_alpha
     if (!amplitudes_host) return fail(h, SV_ERR_ARG, "NULL amplitudes");
     const int N = h->n / 2;
     if (n_alpha < 0 || n_beta < 0 || n_alpha > N || n_beta > N) return fail(h, SV_ERR_ARG, "bad electron counts");
+    if (h->storage == 1 && (n_alpha != h->na || n_beta != h->nb))
+        return fail(h, SV_ERR_ARG, "electron counts differ from the handle's sector");
     const uint32_t even = 0x55555555u, odd = 0xAAAAAAAAu;
     double best = -1.0;
     uint32_t best_x = 0;
@@ -677,7 +771,22 @@ sv_status sv_prepare_state(sv_handle h, const void *amplitudes_host, int n_alpha
     h->failed = false;
     h->prepared = false;
     if (!h->ref_vec) SV_TRY(dev_alloc(h, &h->ref_vec, vec_bytes(h), "reference copy"));
-    if (is_identity(h)) {
+    if (h->storage == 1) {
+        // host order is the dense qubit-order vector: keep its sector entries in C[rank(b)][rank(a)] order
+        SV_TRY(ensure_strings(h));
+        std::vector<uint8_t> comp(vec_bytes(h));
+        for (int Ib = 0; Ib < h->Db; ++Ib)
+            for (int Ia = 0; Ia < h->Da; ++Ia) {
+                uint64_t x = 0;
+                for (int p = 0; p < N; ++p) {
+                    x |= (uint64_t)((h->h_stra[Ia] >> p) & 1u) << (2 * p);
+                    x |= (uint64_t)((h->h_strb[Ib] >> p) & 1u) << (2 * p + 1);
+                }
+                memcpy(comp.data() + ((size_t)Ib * h->Da + Ia) * h->amp_bytes,
+                       (const uint8_t *)amplitudes_host + x * h->amp_bytes, h->amp_bytes);
+            }
+        SV_CUDA(h, cudaMemcpyAsync(h->ref_vec, comp.data(), comp.size(), cudaMemcpyHostToDevice, h->stream));
+    } else if (is_identity(h)) {
         SV_CUDA(h, cudaMemcpyAsync(h->ref_vec, amplitudes_host, vec_bytes(h), cudaMemcpyHostToDevice, h->stream));
     } else {
         // host order is qubit order: upload to the scratch vector, then move bit q to bit perm[q]
@@ -700,6 +809,26 @@ sv_status sv_get_state(sv_handle h, void *amplitudes_host) {
     SV_TRY(check_ready(h));
     if (!amplitudes_host) return fail(h, SV_ERR_ARG, "NULL output");
     DeviceGuard g(h->device);
+    if (h->storage == 1) {
+        // compact matrix back to the host, scattered into the dense qubit-order vector
+        SV_TRY(ensure_strings(h));
+        std::vector<uint8_t> comp(vec_bytes(h));
+        SV_CUDA(h, cudaMemcpyAsync(comp.data(), h->psi, comp.size(), cudaMemcpyDeviceToHost, h->stream));
+        SV_CUDA(h, cudaStreamSynchronize(h->stream));
+        memset(amplitudes_host, 0, (size_t)h->dim * h->amp_bytes);
+        const int N = h->n / 2;
+        for (int Ib = 0; Ib < h->Db; ++Ib)
+            for (int Ia = 0; Ia < h->Da; ++Ia) {
+                uint64_t x = 0;
+                for (int p = 0; p < N; ++p) {
+                    x |= (uint64_t)((h->h_stra[Ia] >> p) & 1u) << (2 * p);
+                    x |= (uint64_t)((h->h_strb[Ib] >> p) & 1u) << (2 * p + 1);
+                }
+                memcpy((uint8_t *)amplitudes_host + x * h->amp_bytes,
+                       comp.data() + ((size_t)Ib * h->Da + Ia) * h->amp_bytes, h->amp_bytes);
+            }
+        return SV_OK;
+    }
     const void *src = h->psi;
     if (!is_identity(h)) {
         // back to qubit order through the scratch vector
@@ -719,12 +848,13 @@ sv_status sv_get_amplitudes(sv_handle h, const uint64_t *basis, int count, void 
     SV_TRY(check_ready(h));
     if (count < 0 || (count > 0 && (!basis || !amplitudes_host))) return fail(h, SV_ERR_ARG, "bad arguments");
     if (count == 0) return SV_OK;
-    std::vector<uint32_t> addr(count);
-    for (int i = 0; i < count; ++i) {
+    for (int i = 0; i < count; ++i)
         if (basis[i] >= h->dim) return fail(h, SV_ERR_ARG, "basis index out of range");
-        addr[i] = map_bits((uint32_t)basis[i], h->perm);
-    }
     DeviceGuard g(h->device);
+    std::vector<uint32_t> addr(count);
+    if (h->storage == 1) SV_TRY(ensure_strings(h));
+    for (int i = 0; i < count; ++i)
+        addr[i] = h->storage == 1 ? compact_index(h, basis[i]) : map_bits((uint32_t)basis[i], h->perm);
     // scratch: the addresses, then the gathered amplitudes, in the reduction buffer
     const size_t addr_doubles = ((size_t)count * 4 + 7) / 8;
     const size_t out_off = (addr_doubles + 1) / 2 * 2;  // 16-byte aligned for complex128
@@ -733,7 +863,8 @@ sv_status sv_get_amplitudes(sv_handle h, const uint64_t *basis, int count, void 
     uint32_t *d_addr = (uint32_t *)h->partials;
     void *d_out = h->partials + out_off;
     SV_CUDA(h, cudaMemcpyAsync(d_addr, addr.data(), (size_t)count * 4, cudaMemcpyHostToDevice, h->stream));
-    SV_CUDA(h, launch_gather(h->psi, h->dtype, d_addr, count, d_out, h->stream));
+    if (h->storage == 1) SV_CUDA(h, launch_gather_c(h->psi, h->dtype, d_addr, count, d_out, h->stream));
+    else SV_CUDA(h, launch_gather(h->psi, h->dtype, d_addr, count, d_out, h->stream));
     h->launches++;
     SV_CUDA(h, cudaMemcpyAsync(amplitudes_host, d_out, (size_t)count * h->amp_bytes, cudaMemcpyDeviceToHost,
                                h->stream));
@@ -820,7 +951,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     std::vector<OpDesc> d;
     SV_TRY(build_ops(h, ops, n_ops, theta, d));  // validates in any layout
     DeviceGuard g(h->device);
-    if (h->layout_auto && n_ops > 0) {
+    if (h->layout_auto && n_ops > 0 && h->storage == 0) {
         int np[32];
         layout_from_ops(h->n, ops, n_ops, np);
         SV_TRY(relayout(h, np));
@@ -837,9 +968,13 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
         if (dev_alloc(h, &p, vec_bytes(h), "saved final state") == SV_OK) h->saved = p;
         else cudaGetLastError();
     }
-    const int G = rotate_grid(1ull << (h->n - 2), h->sm_count);
+    const bool sect = h->storage == 1;
+    if (sect) SV_TRY(ensure_strings(h));
+    const int G = sect ? sector_grid(h->Db, h->sm_count) : rotate_grid(1ull << (h->n - 2), h->sm_count);
     size_t need = 0;
-    if (h->expect_variant == 1) {
+    if (sect) {
+        need = 2 * (size_t)h->Db;
+    } else if (h->expect_variant == 1) {
         SV_TRY(ensure_sector(h));
         need = 2 * (size_t)expect_gather_grid(h->sector_len, h->sm_count);
     } else {
@@ -863,9 +998,17 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     SV_TRY(mark(h, 4));
     // reverse sweep
     const int64_t C = h->ckpt_interval;
+    std::vector<uint8_t> so(sect_op_bytes());
     for (size_t kk = L; kk-- > 0;) {
-        SV_CUDA(h, launch_adjoint(h->psi, h->lam, h->dtype, h->n, d[kk], G, h->partials + kk * (size_t)G,
-                                  h->stream));
+        if (sect) {
+            sect_op_from(d[kk], h->n / 2, so.data());
+            SV_CUDA(h, launch_adjoint_c(h->psi, h->lam, h->dtype, so.data(), h->str_sa, h->str_sb, h->str_a, h->str_b,
+                                        h->rank_a, h->rank_b, h->Da, h->Db, G, h->partials + kk * (size_t)G,
+                                        h->stream));
+        } else {
+            SV_CUDA(h, launch_adjoint(h->psi, h->lam, h->dtype, h->n, d[kk], G, h->partials + kk * (size_t)G,
+                                      h->stream));
+        }
         h->launches++;
         // psi now holds the state after ops[0..kk-1]; resynchronise from a checkpoint if one holds it
         if (C > 0 && kk > 0 && kk % (size_t)C == 0) {
@@ -936,12 +1079,15 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
     SV_TRY(ensure_partials(h, std::max<size_t>(2 * (size_t)h->Db, 1) + op_doubles));
     SV_TRY(ensure_out(h, 2 + (size_t)n_pool));
     const double c = shift_for(h, ham);
-    SV_CUDA(h, launch_compact(h->psi, h->Cbuf, h->dtype, h->str_sa_s, h->str_sb_s, h->Da, h->Db, h->sm_count,
-                              h->stream));
-    h->launches++;
+    const void *Cm = h->storage == 1 ? h->psi : h->Cbuf;  // compact amplitudes
+    if (h->storage == 0) {
+        SV_CUDA(h, launch_compact(h->psi, h->Cbuf, h->dtype, h->str_sa_s, h->str_sb_s, h->Da, h->Db, h->sm_count,
+                                  h->stream));
+        h->launches++;
+    }
     RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
                 T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db};
-    SV_CUDA(h, launch_sigma_rows(h->Cbuf, nullptr, h->Lbuf, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
+    SV_CUDA(h, launch_sigma_rows(Cm, nullptr, h->Lbuf, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
                                  h->partials, h->stream));
     h->launches++;
     SV_CUDA(h, launch_reduce_rows(h->partials, 2, h->Db, h->dout, h->stream));
@@ -949,7 +1095,7 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
     if (n_pool > 0) {
         void *d_ops = h->partials + 2 * (size_t)h->Db;
         SV_CUDA(h, cudaMemcpyAsync(d_ops, host_ops.data(), host_ops.size(), cudaMemcpyHostToDevice, h->stream));
-        SV_CUDA(h, launch_pool_grad(h->Cbuf, h->Lbuf, h->dtype, d_ops, n_pool, h->str_sa, h->str_sb, h->str_a,
+        SV_CUDA(h, launch_pool_grad(Cm, h->Lbuf, h->dtype, d_ops, n_pool, h->str_sa, h->str_sb, h->str_a,
                                     h->str_b, h->rank_a, h->rank_b, h->Da, h->Db, h->dout + 2, h->stream));
         h->launches++;
     }
@@ -966,27 +1112,44 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
     SV_TRY(check_ready(h));
     if (!re_out) return fail(h, SV_ERR_ARG, "NULL re_out");
     DeviceGuard g(h->device);
-    SV_TRY(ensure_sector(h));
-    // element list (host) -> device scratch after the partial sums
-    std::vector<uint8_t> host_el;
-    const int n_el = rdm_elements_bytes(h->n, h->perm, host_el);
-    const int grid = rdm_gather_grid(h->sector_len, h->sm_count);
-    const size_t part = (size_t)2 * n_el * grid;
-    const size_t el_doubles = (host_el.size() + sizeof(double) - 1) / sizeof(double);
-    SV_TRY(ensure_partials(h, part + el_doubles));
-    SV_TRY(ensure_out(h, 2 * (size_t)n_el));
-    double *d_el = h->partials + part;
-    SV_CUDA(h, cudaMemcpyAsync(d_el, host_el.data(), host_el.size(), cudaMemcpyHostToDevice, h->stream));
-    SV_TRY(mark(h, 0));
-    SV_CUDA(h, launch_rdm_gather(h->psi, h->dtype, h->sector, h->sector_len, d_el, n_el, grid, h->partials,
-                                 h->stream));
-    h->launches++;
-    SV_CUDA(h, launch_reduce_rows(h->partials, 2 * n_el, grid, h->dout, h->stream));
-    h->launches++;
-    SV_TRY(mark(h, 7));
-    SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, 2 * (size_t)n_el * sizeof(double), cudaMemcpyDeviceToHost,
-                               h->stream));
-    SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->storage == 1) {
+        SV_TRY(ensure_strings(h));
+        std::vector<uint8_t> host_el;
+        const int n_el = sect_rdm_elements(h->n, host_el);
+        SV_TRY(ensure_partials(h, (host_el.size() + sizeof(double) - 1) / sizeof(double)));
+        SV_TRY(ensure_out(h, 2 * (size_t)n_el));
+        SV_CUDA(h, cudaMemcpyAsync(h->partials, host_el.data(), host_el.size(), cudaMemcpyHostToDevice, h->stream));
+        SV_TRY(mark(h, 0));
+        SV_CUDA(h, launch_rdm_c(h->psi, h->dtype, h->partials, n_el, h->str_sa, h->str_sb, h->str_a, h->str_b,
+                                h->rank_a, h->rank_b, h->Da, h->Db, h->dout, h->stream));
+        h->launches++;
+        SV_TRY(mark(h, 7));
+        SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, 2 * (size_t)n_el * sizeof(double), cudaMemcpyDeviceToHost,
+                                   h->stream));
+        SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    } else {
+        SV_TRY(ensure_sector(h));
+        // element list (host) -> device scratch after the partial sums
+        std::vector<uint8_t> host_el;
+        const int n_el = rdm_elements_bytes(h->n, h->perm, host_el);
+        const int grid = rdm_gather_grid(h->sector_len, h->sm_count);
+        const size_t part = (size_t)2 * n_el * grid;
+        const size_t el_doubles = (host_el.size() + sizeof(double) - 1) / sizeof(double);
+        SV_TRY(ensure_partials(h, part + el_doubles));
+        SV_TRY(ensure_out(h, 2 * (size_t)n_el));
+        double *d_el = h->partials + part;
+        SV_CUDA(h, cudaMemcpyAsync(d_el, host_el.data(), host_el.size(), cudaMemcpyHostToDevice, h->stream));
+        SV_TRY(mark(h, 0));
+        SV_CUDA(h, launch_rdm_gather(h->psi, h->dtype, h->sector, h->sector_len, d_el, n_el, grid, h->partials,
+                                     h->stream));
+        h->launches++;
+        SV_CUDA(h, launch_reduce_rows(h->partials, 2 * n_el, grid, h->dout, h->stream));
+        h->launches++;
+        SV_TRY(mark(h, 7));
+        SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, 2 * (size_t)n_el * sizeof(double), cudaMemcpyDeviceToHost,
+                                   h->stream));
+        SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
     if (h->profile) h->phase_ms[5] = elapsed(h, 0, 7);
     const int n = h->n, N = n / 2;
     const double *o = h->hpinned;
@@ -1020,6 +1183,11 @@ sv_status sv_set_layout(sv_handle h, const int32_t *storage_of_qubit) {
         if (b < 0 || b >= h->n || ((seen >> b) & 1u)) return fail(h, SV_ERR_ARG, "layout is not a permutation of [0, n)");
         seen |= 1u << b;
         np[q] = b;
+    }
+    if (h->storage == 1) {
+        for (int q = 0; q < h->n; ++q)
+            if (np[q] != q) return fail(h, SV_ERR_ARG, "sector storage has no address layout (identity only)");
+        return SV_OK;
     }
     DeviceGuard g(h->device);
     h->layout_auto = false;

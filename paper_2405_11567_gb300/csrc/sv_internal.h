@@ -157,6 +157,8 @@ struct sv_ctx {
     int device = 0;
     uint64_t dim = 0;          // 2^n
     size_t amp_bytes = 8;      // bytes per amplitude
+    int storage = 0;           // 0 dense 2^n vector, 1 sector (compact string-row matrix)
+    uint64_t elems = 0;        // amplitudes stored per vector
     void *psi = nullptr;
     void *lam = nullptr;
     bool own_psi = true, own_lam = true;
@@ -177,6 +179,7 @@ struct sv_ctx {
     uint32_t *str_sa_s = nullptr, *str_sb_s = nullptr;  // storage-space spreads
     uint16_t *str_a = nullptr, *str_b = nullptr, *rank_a = nullptr, *rank_b = nullptr;
     int Da = 0, Db = 0, str_na = -1, str_nb = -1;
+    std::vector<uint16_t> h_stra, h_strb, h_ra, h_rb;  // host copies (sector storage indexing)
     size_t str_bytes = 0;
     void *Cbuf = nullptr;      // compact amplitudes [Db][Da]
     size_t Cbuf_bytes = 0;

@@ -22,7 +22,7 @@ STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV
 
 # every symbol include/sv.h declares
 EXPORTS = (
-    "sv_create", "sv_create_with_buffers", "sv_destroy", "sv_prepare_hf", "sv_prepare_state",
+    "sv_create", "sv_create_sector", "sv_create_with_buffers", "sv_destroy", "sv_prepare_hf", "sv_prepare_state",
     "sv_get_state", "sv_get_amplitudes", "sv_state_device_ptr", "sv_set_layout", "sv_get_layout", "sv_ham_create", "sv_ham_destroy", "sv_apply_ansatz",
     "sv_energy", "sv_energy_grad", "sv_pool_gradients", "sv_rdm1", "sv_set_option", "sv_phase_times", "sv_last_error",
     "sv_launch_count", "sv_version", "sv_batch_create", "sv_batch_energy_grad", "sv_batch_set_time_limit",
@@ -66,6 +66,7 @@ def lib():
         pp = ctypes.POINTER(ctypes.c_void_p)
         sig = {
             "sv_create": (i32, [i32, i32, vp, pp]),
+            "sv_create_sector": (i32, [i32, i32, i32, i32, vp, pp]),
             "sv_create_with_buffers": (i32, [i32, i32, vp, vp, vp, pp]),
             "sv_destroy": (i32, [vp]),
             "sv_prepare_hf": (i32, [vp, vp, i32]),
@@ -138,6 +139,13 @@ def sv_last_error(handle=None) -> str:
 def sv_create(n_qubits: int, dtype: int, stream=None):
     h = ctypes.c_void_p()
     _ck(lib().sv_create(int(n_qubits), int(dtype), _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def sv_create_sector(n_qubits: int, n_alpha: int, n_beta: int, dtype: int, stream=None):
+    h = ctypes.c_void_p()
+    _ck(lib().sv_create_sector(int(n_qubits), int(n_alpha), int(n_beta), int(dtype), _stream_ptr(stream),
+                               ctypes.byref(h)))
     return h
 
 
@@ -366,12 +374,22 @@ class Hamiltonian:
 
 
 class StateVector:
-    """Owns an ``sv_handle``: an n-qubit state on the current CUDA device."""
+    """Owns an ``sv_handle``: an n-qubit state on the current CUDA device.
 
-    def __init__(self, n_qubits: int, dtype="c64", stream=None):
+    ``sector=(n_alpha, n_beta)`` keeps only that particle-number sector's
+    amplitudes on the device (``sv_create_sector``); the default is the dense
+    2^n vector.
+    """
+
+    def __init__(self, n_qubits: int, dtype="c64", stream=None, sector=None):
         self.n = int(n_qubits)
         self.dtype = SV_C64 if dtype in ("c64", SV_C64, np.complex64) else SV_C128
-        self.handle = sv_create(self.n, self.dtype, stream)
+        self.sector = None if sector is None else (int(sector[0]), int(sector[1]))
+        self.handle = None
+        if self.sector is None:
+            self.handle = sv_create(self.n, self.dtype, stream)
+        else:
+            self.handle = sv_create_sector(self.n, self.sector[0], self.sector[1], self.dtype, stream)
 
     def close(self):
         if self.handle is not None:

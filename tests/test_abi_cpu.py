@@ -63,6 +63,10 @@ def test_null_and_bad_arguments_rejected_without_device(cabi):
     assert cabi.sv_create(34, 0, None, ctypes.byref(out)) == 1     # beyond 32 qubits
     assert cabi.sv_create(8, 5, None, ctypes.byref(out)) == 1      # bad dtype
     assert cabi.sv_create(8, 0, None, None) == 1
+    assert cabi.sv_create_sector(8, 5, 1, 0, None, ctypes.byref(out)) == 1   # more electrons than orbitals
+    assert cabi.sv_create_sector(8, 1, -1, 0, None, ctypes.byref(out)) == 1  # negative count
+    assert cabi.sv_create_sector(9, 1, 1, 0, None, ctypes.byref(out)) == 1   # odd qubit count
+    assert cabi.sv_create_sector(8, 1, 1, 7, None, ctypes.byref(out)) == 1   # bad dtype
     assert cabi.sv_destroy(None) == 0
     assert cabi.sv_energy(None, None, None) == 1
     assert b"NULL" in cabi.sv_last_error(None)

@@ -1,4 +1,5 @@
-"""Full-size parity at 30 qubits (config 5), in the launch configuration bench.py times.
+"""Full-size parity at 30 qubits (config 5), in the launch configuration bench.py times,
+for both state storages (the dense 2^30 vector and the compact sector matrix).
 
 Expected values come from tests/golden/config5_oracle.json, written by
 tests/golden/make_golden.py with the CPU oracle only: the energy, all 200 gradient
@@ -34,11 +35,12 @@ def golden():
     return p, g
 
 
+@pytest.mark.parametrize("storage", ["dense", "sector"])
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
-def test_config5_energy_gradient_rdm_and_state(golden, dtype):
+def test_config5_energy_gradient_rdm_and_state(golden, dtype, storage):
     p, g = golden
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
-    st = sv.StateVector(p["n_qubits"], dtype)
+    st = sv.StateVector(p["n_qubits"], dtype, sector=None if storage == "dense" else (p["na"], p["nb"]))
     st.prepare_hf(p["occ"])
     E, grad = st.energy_grad(ham, p["ops"], p["theta"])
     rdm = st.rdm1()

@@ -1,0 +1,257 @@
+"""GPU parity for sector storage (sv_create_sector): the state held as only its
+(N_alpha, N_beta) sector, C[rank(beta string)][rank(alpha string)], against the
+CPU oracle, with the tolerances of the dense path.  Integer work (signs, partner
+ranks, which amplitudes are exactly zero) is compared bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import route_a as A
+from oracle import route_b as B
+from paper_2405_11567_gb300 import inputs, sv
+from paper_2405_11567_gb300.adapt import adapt_vqe
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": dict(E=1e-10, g=1e-9, amp=1e-12, rdm=1e-12), "c64": dict(E=1e-5, g=1e-5, amp=2e-6, rdm=2e-6)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2405_11567_gb300 import build
+    build.build()
+    sv.lib()
+
+
+def _state(n, na, nb, dtype):
+    return sv.StateVector(n, dtype, sector=(na, nb))
+
+
+def _outside(n, na, nb):
+    x = np.arange(1 << n, dtype=np.int64)
+    ca = sum(((x >> j) & 1) for j in range(0, n, 2))
+    cb = sum(((x >> j) & 1) for j in range(1, n, 2))
+    return (ca != na) | (cb != nb)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,ne,seed", [(8, 2, 1001), (10, 4, 7), (12, 4, 8), (14, 6, 9)])
+def test_ansatz_state_matches_oracle(n, ne, seed, dtype):
+    p = inputs.make_problem(n, ne, "uccsd", seed)
+    theta = p["theta"] * 8
+    sec = oracle.Sector(n, p["na"], p["nb"])
+    ref = A.apply_ansatz(sec, p["ops"], theta, A.hf_state(sec, p["occ"]))
+    st = _state(n, p["na"], p["nb"], dtype)
+    st.prepare_hf(p["occ"])
+    st.apply_ansatz(p["ops"], theta)
+    got = st.state()
+    assert np.max(np.abs(got[sec.dets.astype(np.int64)] - ref)) <= TOL[dtype]["amp"]
+    assert np.count_nonzero(got[_outside(n, p["na"], p["nb"])]) == 0
+    assert np.count_nonzero(got.imag) == 0
+
+
+def test_jordan_wigner_signs_bit_exact():
+    """A rotation by pi/2 sends a basis state to T|x> with amplitude exactly +-1: sign and partner
+    (through the string ranks) must equal the oracle's literal operator application."""
+    n = 10
+    ops = np.vstack([inputs.uccsd_pool(n, 4), inputs.qeb_pool(n, 4)[::3],
+                     np.array([(2, 1, 6, 2, 5), (2, 0, 5, 2, 3), (1, 5, -1, 1, -1), (2, 2, 3, 0, 7),
+                               (1, 8, -1, 2, -1)], np.int32)])
+    st = _state(n, 2, 2, "c128")
+    sec = oracle.Sector(n, 2, 2)
+    rng = np.random.default_rng(0)
+    for op in ops:
+        froms = [int(x) for x in sec.dets if A.exc_apply(op, int(x))[0] != 0]
+        for x in rng.choice(froms, size=min(6, len(froms)), replace=False):
+            s, y = A.exc_apply(op, int(x))
+            v = np.zeros(1 << n, np.complex128)
+            v[int(x)] = 1.0
+            st.prepare_state(v, 2, 2)
+            st.apply_ansatz(op[None, :], [np.pi / 2])
+            got = st.state()
+            assert got[y].real == float(s) and got[y].imag == 0.0
+            assert abs(got[int(x)]) < 1e-15
+            assert np.count_nonzero(np.abs(got) > 1e-15) == 1
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("cid", [1, 2])
+def test_config_energy_grad(cid, dtype):
+    p = inputs.config_problem(cid)
+    sec = oracle.Sector(p["n_qubits"], p["na"], p["nb"])
+    psi0 = A.hf_state(sec, p["occ"])
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], p["theta"], psi0)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _state(p["n_qubits"], p["na"], p["nb"], dtype)
+    st.prepare_hf(p["occ"])
+    E, g = st.energy_grad(ham, p["ops"], p["theta"])
+    assert abs(E - Eref) <= TOL[dtype]["E"]
+    assert np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
+    assert abs(st.energy(ham) - Eref) <= TOL[dtype]["E"]          # the handle holds psi(theta)
+    psi = A.apply_ansatz(sec, p["ops"], p["theta"], psi0)
+    assert np.max(np.abs(st.amplitudes(sec.dets.astype(np.uint64)) - psi)) <= TOL[dtype]["amp"] * 10
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_config3_energy_grad_rdm(dtype, config3_oracle):
+    p, Eref, gref, rdm_ref = config3_oracle
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _state(p["n_qubits"], p["na"], p["nb"], dtype)
+    st.prepare_hf(p["occ"])
+    E, g = st.energy_grad(ham, p["ops"], p["theta"])
+    assert abs(E - Eref) <= TOL[dtype]["E"]
+    assert np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
+    assert np.max(np.abs(st.rdm1() - rdm_ref)) <= TOL[dtype]["rdm"]
+
+
+@pytest.fixture(scope="module")
+def config3_oracle():
+    p = inputs.config_problem(3)
+    sec = oracle.Sector(p["n_qubits"], p["na"], p["nb"])
+    psi0 = A.hf_state(sec, p["occ"])
+    E, g = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], p["theta"], psi0)
+    rdm = A.rdm1(sec, A.apply_ansatz(sec, p["ops"], p["theta"], psi0))
+    return p, E, g, rdm
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_complex_start_open_shell(dtype):
+    """Complex multi-determinant start, N_alpha != N_beta: every conj() of the path."""
+    n, na, nb = 12, 3, 2
+    p = inputs.make_problem(n, 4, 40, seed=55)
+    dense0 = inputs.random_sector_state(n, na, nb, np.random.default_rng(3))
+    sec = oracle.Sector(n, na, nb)
+    psi0 = dense0[sec.dets.astype(np.int64)]
+    theta = p["theta"] * 6
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _state(n, na, nb, dtype)
+    st.prepare_state(dense0.astype(np.complex64 if dtype == "c64" else np.complex128), na, nb)
+    E, g = st.energy_grad(ham, p["ops"], theta)
+    assert abs(E - Eref) <= TOL[dtype]["E"]
+    assert np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
+    rdm_ref = A.rdm1(sec, A.apply_ansatz(sec, p["ops"], theta, psi0))
+    assert np.max(np.abs(st.rdm1() - rdm_ref)) <= TOL[dtype]["rdm"]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_rdm1_matches_oracle(dtype):
+    p = inputs.make_problem(14, 6, 60, seed=66)
+    sec = oracle.Sector(14, 3, 3)
+    psi = A.apply_ansatz(sec, p["ops"], p["theta"] * 5, A.hf_state(sec, p["occ"]))
+    st = _state(14, 3, 3, dtype)
+    st.prepare_hf(p["occ"])
+    st.apply_ansatz(p["ops"], p["theta"] * 5)
+    assert np.max(np.abs(st.rdm1() - A.rdm1(sec, psi))) <= TOL[dtype]["rdm"]
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-9), ("c64", 1e-5)])
+def test_pool_gradients_match_oracle(dtype, tol):
+    n = 14
+    p = inputs.make_problem(n, 6, 30, seed=202)
+    pool = np.vstack([inputs.uccsd_pool(n, 6), inputs.qeb_pool(n, 6)[::5]])
+    sec = oracle.Sector(n, 3, 3)
+    theta = p["theta"] * 6
+    psi = A.apply_ansatz(sec, p["ops"], theta, A.hf_state(sec, p["occ"]))
+    sig = A.hamiltonian_apply(sec, p["h"], p["eri"], p["e_nuc"], psi)
+    nrm = np.vdot(psi, psi).real
+    gref = np.array([2 * np.vdot(sig, A.generator_apply(sec, op, psi)).real / nrm for op in pool])
+    st = _state(n, 3, 3, dtype)
+    st.prepare_hf(p["occ"])
+    st.apply_ansatz(p["ops"], theta)
+    E, g = st.pool_gradients(sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"]), pool)
+    assert abs(E - np.vdot(psi, sig).real / nrm) <= (1e-10 if dtype == "c128" else 1e-5)
+    assert np.max(np.abs(g - gref)) <= tol
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_checkpoints_and_byte_cap(dtype):
+    p = inputs.make_problem(14, 4, 50, seed=77)
+    sec = oracle.Sector(14, 2, 2)
+    theta = p["theta"] * 4
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, A.hf_state(sec, p["occ"]))
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    amp = 8 if dtype == "c64" else 16
+    for interval, cap in [(7, 0), (1, 0), (5, 6 * sec.D * amp)]:
+        st = _state(14, 2, 2, dtype)
+        st.set_option(sv.SV_OPT_CHECKPOINT_INTERVAL, interval)
+        if cap:
+            st.set_option(sv.SV_OPT_MAX_BYTES, cap + (1 << 22))
+        st.prepare_hf(p["occ"])
+        E, g = st.energy_grad(ham, p["ops"], theta)
+        assert abs(E - Eref) <= TOL[dtype]["E"]
+        assert np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
+
+
+@pytest.mark.parametrize("na,nb,ops", [
+    (2, 0, [(1, 0, -1, 4, -1), (1, 2, -1, 6, -1), (2, 0, 2, 4, 6), (1, 0, -1, 6, -1)]),   # one beta row
+    (4, 1, [(1, 1, -1, 3, -1), (1, 1, -1, 7, -1), (1, 3, -1, 5, -1)]),                     # one alpha column
+    (1, 1, [(1, 0, -1, 2, -1), (2, 0, 1, 4, 5), (1, 1, -1, 7, -1), (4, 0, 1, 2, 7)]),
+])
+def test_degenerate_sectors(na, nb, ops):
+    """Sectors with a single string on one spin (D_alpha or D_beta = 1), and an empty ansatz."""
+    n = 8
+    rng = np.random.default_rng(na * 10 + nb)
+    ops = np.array(ops, np.int32)
+    theta = rng.normal(0, 0.7, len(ops))
+    h, eri, e_nuc = inputs.synthetic_integrals(n // 2, rng)
+    dense0 = inputs.random_sector_state(n, na, nb, rng)
+    sec = oracle.Sector(n, na, nb)
+    psi0 = dense0[sec.dets.astype(np.int64)]
+    Eref, gref = A.energy_grad(sec, h, eri, e_nuc, ops, theta, psi0)
+    ham = sv.Hamiltonian(h, eri, e_nuc)
+    st = _state(n, na, nb, "c128")
+    st.prepare_state(dense0, na, nb)
+    E, g = st.energy_grad(ham, ops, theta)
+    assert abs(E - Eref) <= 1e-10 and np.max(np.abs(g - gref)) <= 1e-9
+    assert np.max(np.abs(st.rdm1() - A.rdm1(sec, A.apply_ansatz(sec, ops, theta, psi0)))) <= 1e-12
+    E0, g0 = st.energy_grad(ham, np.zeros((0, 5), np.int32), np.zeros(0))
+    assert abs(E0 - A.energy(sec, h, eri, e_nuc, psi0)) <= 1e-10 and len(g0) == 0
+
+
+def test_host_views_and_errors():
+    n = 10
+    p = inputs.make_problem(n, 4, 20, seed=12)
+    st = _state(n, 2, 2, "c128")
+    with pytest.raises(sv.SvError) as e:
+        st.prepare_hf([0, 1, 2])                                 # 2 alpha + 1 beta: another sector
+    assert e.value.status == 1
+    with pytest.raises(sv.SvError):
+        st.prepare_state(inputs.random_sector_state(n, 3, 1, np.random.default_rng(1)), 3, 1)
+    with pytest.raises(sv.SvError):
+        st.set_layout(np.arange(n)[::-1].copy())
+    st.set_layout(np.arange(n))                                  # identity is accepted
+    st.prepare_hf(p["occ"])
+    st.apply_ansatz(p["ops"], p["theta"] * 3)
+    dense = st.state()
+    xs = np.arange(1 << n, dtype=np.uint64)
+    assert np.array_equal(st.amplitudes(xs), dense)             # gather == host scatter, bit for bit
+    assert np.count_nonzero(dense[_outside(n, 2, 2)]) == 0
+    assert sv.sv_state_device_ptr(st.handle) != 0
+
+
+def test_deterministic_and_equal_to_dense():
+    """Reruns are bit-identical; the sector handle agrees with the dense handle (same arithmetic per pair,
+    different summation order) within the float64 tolerance."""
+    p = inputs.config_problem(2)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _state(p["n_qubits"], p["na"], p["nb"], "c128")
+    st.prepare_hf(p["occ"])
+    E1, g1 = st.energy_grad(ham, p["ops"], p["theta"])
+    E2, g2 = st.energy_grad(ham, p["ops"], p["theta"])
+    assert E1 == E2 and np.array_equal(g1, g2)
+    dn = sv.StateVector(p["n_qubits"], "c128")
+    dn.prepare_hf(p["occ"])
+    E3, g3 = dn.energy_grad(ham, p["ops"], p["theta"])
+    assert abs(E1 - E3) <= 1e-11 and np.max(np.abs(g1 - g3)) <= 1e-10
+
+
+def test_adapt_vqe_on_sector_storage_reaches_fci():
+    n, ne, seed = 8, 4, 305
+    p = inputs.make_problem(n, ne, "uccsd", seed=seed)
+    E0 = B.sector_spectrum(B.hamiltonian(n, p["h"], p["eri"], p["e_nuc"]), n, ne // 2, ne // 2)[0]
+    st = _state(n, ne // 2, ne // 2, "c128")
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    out = adapt_vqe(st, ham, p["occ"], inputs.uccsd_pool(n, ne), max_ops=60, grad_tol=1e-6, energy_tol=1e-12,
+                    vqe_gtol=1e-9)
+    assert out["energy"] >= E0 - 1e-10 and out["energy"] - E0 < 1e-8
