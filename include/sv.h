@@ -24,7 +24,8 @@
  *
  * State storage: one dense vector of 2^n complex amplitudes in device memory,
  * interleaved (re, im), complex64 (SV_C64, float) or complex128 (SV_C128,
- * double), index = basis index x.  Every reduction (energy, gradient, norm,
+ * double), index = basis index x (sv_create), or only the amplitudes of one
+ * (N_alpha, N_beta) sector (sv_create_sector).  Every reduction (energy, gradient, norm,
  * density matrix) is accumulated and returned in float64 whatever the state
  * precision.
  *
@@ -295,14 +296,22 @@ typedef enum {
                                        (0 = none; default 0) */
     SV_OPT_MAX_BYTES = 2,           /* cap on device bytes this handle may allocate
                                        (0 = no cap); checkpoints are dropped to fit */
-    SV_OPT_EXPECT_VARIANT = 3,      /* 0 auto (= 2); 1 record scan: one thread per sector
-                                       determinant tests every mask group; 2 string rows:
-                                       compact alpha/beta-string matrix, one block per
-                                       beta string */
-    SV_OPT_RDM_VARIANT = 4,         /* 0 auto, 1 sector gather (only variant so far) */
+    SV_OPT_EXPECT_VARIANT = 3,      /* 0 auto (= 3 where its rows fit in shared memory,
+                                       else 2); 1 record scan: one thread per sector
+                                       determinant tests every mask group (dense storage
+                                       only); 2 string rows: compact alpha/beta-string
+                                       matrix, one block per beta string; 3 string rows
+                                       split: the alpha-beta doubles in a second kernel
+                                       that stages partner rows in shared memory */
+    SV_OPT_RDM_VARIANT = 4,         /* 0 auto (= 2); 1 sector gather: one thread per sector
+                                       determinant (dense storage only); 2 string rows: one
+                                       block per beta string of the compact matrix */
     SV_OPT_PROFILE = 5,             /* 1: record CUDA events around each phase (sv_phase_times) */
-    SV_OPT_LAYOUT_AUTO = 6          /* 1 (default): sv_energy_grad chooses the storage layout
+    SV_OPT_LAYOUT_AUTO = 6,         /* 1 (default): sv_energy_grad chooses the storage layout
                                        from its operator list (sv_set_layout); 0: keep it */
+    SV_OPT_AB_CHUNK = 7             /* variant 3: most partner rows staged per chunk
+                                       (1, 2, 4 or 8; 0 = as many as fit; a tuning knob,
+                                       results differ only by summation order) */
 } sv_option;
 
 sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value);

@@ -13,7 +13,7 @@
 //   k_rotate_c   psi'[x] = c psi[x] - s sn psi[x'],  psi'[x'] = c psi[x'] + s sn psi[x]
 //   k_adjoint_c  g += s (Re conj(lam[x']) psi[x] - Re conj(lam[x]) psi[x']), then U^dagger
 //                on psi and lambda (float64 per block, fixed-order sums)
-//   k_rdm_c      one block per density-matrix element
+//   k_rdm_rows   one block per beta string: every density-matrix element's share
 // with s = (-1)^popc(x & sm), the Jordan-Wigner sign (sm = 0 for qubit
 // excitations).
 #include <cstring>
@@ -89,51 +89,105 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_c(cplx<R> *__restrict__ ps
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// Density-matrix elements.  kind 0: norm; kind 1: occupation of one spin-orbital
-// (alpha string bit ma or beta string bit mb); kind 2: <psi|a+_P a_Q|psi> for a
-// same-spin pair, from determinants with Q occupied and P empty.
-struct SectElem {
-    int kind;
-    uint32_t sm;
-    uint32_t ma, fa, mb, fb;
-};
-
+// Density matrix by rows: a block takes beta strings (rows) Ib = blockIdx.x,
+// blockIdx.x + gridDim.x, ...; for each row its warps sum, in the state precision,
+//   norm and alpha occupations   sum_a |C[b][a]|^2 (a_p)
+//   beta occupations             the row norm when b holds p
+//   alpha pairs p < q            sum over a with q in a, p not in a of
+//                                conj(C[b][a']) C[b][a] (-1)^popc(x & between(2p, 2q)), a' = a - q + p
+//   beta pairs p < q (b holds q, not p)
+//                                sum_a conj(C[b'][a]) C[b][a] (-1)^popc(x & between(2p+1, 2q+1))
+// (x = spread(a) | spread(b)), in the element order norm, n occupations
+// (j = 2p + sigma), alpha pairs, beta pairs.  Each warp's sum goes to its own
+// shared slot; after each row the block adds the slots in warp order into float64
+// running sums, written to partial[e][blockIdx.x] at the end: fixed-order sums.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_rdm_c(const cplx<R> *__restrict__ psi, const SectElem *__restrict__ el,
-                                                    SectTabs T, double *__restrict__ out) {
-    __shared__ double red[2 * kThreads / 32];
-    const SectElem E = el[blockIdx.x];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    double re = 0.0, im = 0.0;
-    for (int Ib = warp; Ib < T.Db; Ib += nw) {
-        const uint32_t b = T.strb[Ib];
-        if ((b & E.mb) != E.fb) continue;
-        const size_t rowI = (size_t)Ib * T.Da;
-        const size_t rowJ = E.kind == 2 ? (size_t)T.rb[b ^ E.mb] * T.Da : rowI;
-        const uint32_t xb = T.sb[Ib];
-        R r = 0, i = 0;
-        for (int Ia = lane; Ia < T.Da; Ia += 32) {
+__global__ void __launch_bounds__(kThreads) k_rdm_rows(const cplx<R> *__restrict__ C, SectTabs T, int N,
+                                                       double *__restrict__ partial) {
+    extern __shared__ double rdm_s[];  // [2 n_el] running sums, then [kThreads/32][2 n_el] warp slots
+    const int n = 2 * N, npair = N * (N - 1) / 2, n_el = 1 + n + 2 * npair, W = 2 * n_el;
+    double *acc = rdm_s, *slot = rdm_s + W;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double *my = slot + warp * W;
+    for (int i = threadIdx.x; i < W; i += blockDim.x) acc[i] = 0.0;
+    const uint32_t maskN = (1u << N) - 1u;
+    for (int Ib = blockIdx.x; Ib < T.Db; Ib += gridDim.x) {
+        const uint32_t b = T.strb[Ib], xb = T.sb[Ib];
+        const cplx<R> *row = C + (size_t)Ib * T.Da;
+        // norm and alpha occupations
+        R nrm = 0, occ[16];
+        #pragma unroll
+        for (int p = 0; p < 16; ++p) occ[p] = 0;
+        for (int Ia = threadIdx.x; Ia < T.Da; Ia += blockDim.x) {
+            const cplx<R> c = row[Ia];
+            const R w = c.x * c.x + c.y * c.y;
             const uint32_t a = T.stra[Ia];
-            if ((a & E.ma) != E.fa) continue;
-            const cplx<R> u = psi[rowI + Ia];
-            if (E.kind != 2) {
-                r += u.x * u.x + u.y * u.y;
-                continue;
-            }
-            const cplx<R> p = psi[rowJ + T.ra[a ^ E.ma]];
-            R ar = p.x * u.x + p.y * u.y, ai = p.x * u.y - p.y * u.x;  // conj(p) u
-            if (par((T.sa[Ia] | xb) & E.sm)) { ar = -ar; ai = -ai; }
-            r += ar;
-            i += ai;
+            nrm += w;
+            #pragma unroll
+            for (int p = 0; p < 16; ++p)
+                if ((a >> p) & 1u) occ[p] += w;
         }
-        re += (double)r;
-        im += (double)i;
+        nrm = warp_sum(nrm);
+        if (lane == 0) {
+            my[0] = (double)nrm;
+            my[1] = 0.0;
+        }
+        #pragma unroll
+        for (int p = 0; p < 16; ++p) {
+            if (p >= N) break;
+            const R s = warp_sum(occ[p]);
+            if (lane == 0) {
+                my[2 * (1 + 2 * p)] = (double)s;
+                my[2 * (1 + 2 * p) + 1] = 0.0;
+                my[2 * (2 + 2 * p)] = ((b >> p) & 1u) ? (double)nrm : 0.0;
+                my[2 * (2 + 2 * p) + 1] = 0.0;
+            }
+        }
+        // alpha pairs (same row) and beta pairs (row b')
+        int e = 1 + n;
+        for (int s = 0; s < 2; ++s)
+            for (int p = 0; p < N; ++p)
+                for (int q = p + 1; q < N; ++q, ++e) {
+                    const uint32_t m = (1u << p) | (1u << q), f = 1u << q;
+                    const uint32_t bm = between(2 * p + s, 2 * q + s);
+                    R re = 0, im = 0;
+                    if (s == 0) {
+                        for (int Ia = threadIdx.x; Ia < T.Da; Ia += blockDim.x) {
+                            const uint32_t a = T.stra[Ia];
+                            if ((a & m) != f) continue;
+                            const cplx<R> u = row[Ia], v = row[T.ra[a ^ m]];
+                            R ar = v.x * u.x + v.y * u.y, ai = v.x * u.y - v.y * u.x;  // conj(v) u
+                            if (par((T.sa[Ia] | xb) & bm)) { ar = -ar; ai = -ai; }
+                            re += ar;
+                            im += ai;
+                        }
+                    } else if ((b & m) == f) {
+                        const cplx<R> *row2 = C + (size_t)T.rb[b ^ m] * T.Da;
+                        for (int Ia = threadIdx.x; Ia < T.Da; Ia += blockDim.x) {
+                            const cplx<R> u = row[Ia], v = row2[Ia];
+                            R ar = v.x * u.x + v.y * u.y, ai = v.x * u.y - v.y * u.x;
+                            if (par((T.sa[Ia] | xb) & bm)) { ar = -ar; ai = -ai; }
+                            re += ar;
+                            im += ai;
+                        }
+                    }
+                    re = warp_sum(re);
+                    im = warp_sum(im);
+                    if (lane == 0) {
+                        my[2 * e] = (double)re;
+                        my[2 * e + 1] = (double)im;
+                    }
+                }
+        (void)maskN;
+        __syncthreads();
+        for (int i = threadIdx.x; i < W; i += blockDim.x) {
+            double t = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) t += slot[w * W + i];
+            acc[i] += t;
+        }
+        __syncthreads();
     }
-    block_sum2(re, im, red);
-    if (threadIdx.x == 0) {
-        out[2 * blockIdx.x] = re;
-        out[2 * blockIdx.x + 1] = im;
-    }
+    for (int i = threadIdx.x; i < W; i += blockDim.x) partial[(size_t)i * gridDim.x + blockIdx.x] = acc[i];
 }
 
 // out[i] = C[idx[i]] or 0 when idx[i] is 0xFFFFFFFF (a basis state outside the sector)
@@ -193,37 +247,26 @@ cudaError_t launch_adjoint_c(void *psi, void *lam, int dtype, const void *op, co
     return cudaGetLastError();
 }
 
-// Elements in the order norm, n occupations (spin-orbital j = 2p + sigma), then p<q pairs
-// for alpha then beta -- the order sv_rdm1 unpacks.
-int sect_rdm_elements(int n, std::vector<uint8_t> &out) {
-    const int N = n / 2;
-    std::vector<SectElem> el;
-    el.push_back(SectElem{0, 0u, 0u, 0u, 0u, 0u});
-    for (int j = 0; j < n; ++j) {
-        const uint32_t bit = 1u << (j >> 1);
-        if (j & 1) el.push_back(SectElem{1, 0u, 0u, 0u, bit, bit});
-        else el.push_back(SectElem{1, 0u, bit, bit, 0u, 0u});
-    }
-    for (int s = 0; s < 2; ++s)
-        for (int p = 0; p < N; ++p)
-            for (int q = p + 1; q < N; ++q) {
-                const int P = 2 * p + s, Q = 2 * q + s;
-                const uint32_t m = (1u << p) | (1u << q), f = 1u << q;  // Q occupied, P empty
-                SectElem e{2, bits_between(P, Q), 0u, 0u, 0u, 0u};
-                if (s == 0) { e.ma = m; e.fa = f; } else { e.mb = m; e.fb = f; }
-                el.push_back(e);
-            }
-    out.resize(el.size() * sizeof(SectElem));
-    memcpy(out.data(), el.data(), out.size());
-    return (int)el.size();
-}
+int rdm_rows_elements(int n) { return 1 + n + (n / 2) * (n / 2 - 1); }
 
-cudaError_t launch_rdm_c(const void *psi, int dtype, const void *elems, int n_el, const uint32_t *sa,
-                         const uint32_t *sb, const uint16_t *stra, const uint16_t *strb, const uint16_t *ra,
-                         const uint16_t *rb, int Da, int Db, double *out, cudaStream_t st) {
+int rdm_rows_grid(int Db, int sm_count) { return Db < 4 * sm_count ? Db : 4 * sm_count; }
+
+// partial: [2 n_el][grid] doubles (n_el = rdm_rows_elements(n)), reduced by launch_reduce_rows.
+cudaError_t launch_rdm_rows(const void *C, int dtype, int n, const uint32_t *sa, const uint32_t *sb,
+                            const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb, int Da,
+                            int Db, int grid, double *partial, cudaStream_t st) {
     SectTabs T = tabs(sa, sb, stra, strb, ra, rb, Da, Db);
-    if (dtype == SV_C64) k_rdm_c<float><<<n_el, kThreads, 0, st>>>((const float2 *)psi, (const SectElem *)elems, T, out);
-    else k_rdm_c<double><<<n_el, kThreads, 0, st>>>((const double2 *)psi, (const SectElem *)elems, T, out);
+    const size_t smem = sizeof(double) * 2 * rdm_rows_elements(n) * (1 + kThreads / 32);
+    cudaError_t e;
+    if (dtype == SV_C64) {
+        e = cudaFuncSetAttribute(k_rdm_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_rdm_rows<float><<<grid, kThreads, smem, st>>>((const float2 *)C, T, n / 2, partial);
+    } else {
+        e = cudaFuncSetAttribute(k_rdm_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_rdm_rows<double><<<grid, kThreads, smem, st>>>((const double2 *)C, T, n / 2, partial);
+    }
     return cudaGetLastError();
 }
 

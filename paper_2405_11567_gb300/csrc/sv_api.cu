@@ -49,10 +49,11 @@ cudaError_t launch_rotate_c(void *psi, int dtype, const void *op, const uint32_t
 cudaError_t launch_adjoint_c(void *psi, void *lam, int dtype, const void *op, const uint32_t *sa, const uint32_t *sb,
                              const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb,
                              int Da, int Db, int grid, double *partial, cudaStream_t st);
-int sect_rdm_elements(int n, std::vector<uint8_t> &out);
-cudaError_t launch_rdm_c(const void *psi, int dtype, const void *elems, int n_el, const uint32_t *sa,
-                         const uint32_t *sb, const uint16_t *stra, const uint16_t *strb, const uint16_t *ra,
-                         const uint16_t *rb, int Da, int Db, double *out, cudaStream_t st);
+int rdm_rows_elements(int n);
+int rdm_rows_grid(int Db, int sm_count);
+cudaError_t launch_rdm_rows(const void *C, int dtype, int n, const uint32_t *sa, const uint32_t *sb,
+                            const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb, int Da,
+                            int Db, int grid, double *partial, cudaStream_t st);
 cudaError_t launch_gather_c(const void *psi, int dtype, const uint32_t *idx, int count, void *out, cudaStream_t st);
 
 struct RowTables {
@@ -64,7 +65,8 @@ struct RowTables {
 cudaError_t launch_compact(const void *psi, void *C, int dtype, const uint32_t *sa, const uint32_t *sb, int Da,
                            int Db, int sm_count, cudaStream_t st);
 cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &T, const double *hdiag,
-                              const double *Jp, double e_shift, double *partial, cudaStream_t st);
+                              const double *Jp, double e_shift, double *partial, int K, cudaStream_t st);
+int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want, int *ra_in);
 
 DevTables::~DevTables() {
     void *ptrs[] = {dbl, sgl, W, hdiag, Jp, hdiag_s, Jp_s, eri_r, hm_r, Dt, Jt, pass_dbl, pass_sgl, pass_W};
@@ -492,6 +494,14 @@ static void plan_checkpoints(sv_handle h, size_t L) {
     }
 }
 
+// Rows per chunk of the split string-row expectation (0: single kernel).
+static int row_chunk(sv_handle h, const RowTables &R) {
+    if (h->expect_variant == 2) return 0;
+    int ra_in = 0;
+    const int K = sigma_ab_chunk(h->dtype, R, h->nb, (int)h->ab_chunk, &ra_in);
+    return K ? K | (ra_in ? 16 : 0) : 0;
+}
+
 // Expectation pass over the current state: writes the float64 sums of
 // <psi|(H - c)|psi> and <psi|psi> into dout[out_off], dout[out_off + 1] (device),
 // and sigma = (H - c) psi into `sigma` when it is not NULL.
@@ -499,12 +509,13 @@ static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void 
     if (h->storage == 1) {
         // the state is already the compact matrix; sigma is compact too (every entry written)
         SV_TRY(ensure_strings(h));
-        SV_TRY(ensure_partials(h, 2 * (size_t)h->Db));
+        SV_TRY(ensure_partials(h, 3 * (size_t)h->Db));
         RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
                     T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db};
+        const int K = row_chunk(h, R);
         SV_CUDA(h, launch_sigma_rows(h->psi, nullptr, sigma, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
-                                     h->partials, h->stream));
-        h->launches++;
+                                     h->partials, K, h->stream));
+        h->launches += K ? 2 : 1;
         SV_CUDA(h, launch_reduce_rows(h->partials, 2, h->Db, h->dout + out_off, h->stream));
         h->launches++;
         return SV_OK;
@@ -512,16 +523,17 @@ static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void 
     if (h->expect_variant != 1) {
         // string rows (default)
         SV_TRY(ensure_strings(h));
-        SV_TRY(ensure_partials(h, 2 * (size_t)h->Db));
+        SV_TRY(ensure_partials(h, 3 * (size_t)h->Db));
         if (sigma) SV_CUDA(h, cudaMemsetAsync(sigma, 0, vec_bytes(h), h->stream));
         SV_CUDA(h, launch_compact(h->psi, h->Cbuf, h->dtype, h->str_sa_s, h->str_sb_s, h->Da, h->Db, h->sm_count,
                                   h->stream));
         h->launches++;
         RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
                     T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db};
+        const int K = row_chunk(h, R);
         SV_CUDA(h, launch_sigma_rows(h->Cbuf, sigma, nullptr, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
-                                     h->partials, h->stream));
-        h->launches++;
+                                     h->partials, K, h->stream));
+        h->launches += K ? 2 : 1;
         SV_CUDA(h, launch_reduce_rows(h->partials, 2, h->Db, h->dout + out_off, h->stream));
         h->launches++;
         return SV_OK;
@@ -973,13 +985,13 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     const int G = sect ? sector_grid(h->Db, h->sm_count) : rotate_grid(1ull << (h->n - 2), h->sm_count);
     size_t need = 0;
     if (sect) {
-        need = 2 * (size_t)h->Db;
+        need = 3 * (size_t)h->Db;
     } else if (h->expect_variant == 1) {
         SV_TRY(ensure_sector(h));
         need = 2 * (size_t)expect_gather_grid(h->sector_len, h->sm_count);
     } else {
         SV_TRY(ensure_strings(h));
-        need = 2 * (size_t)h->Db;
+        need = 3 * (size_t)h->Db;
     }
     SV_TRY(ensure_partials(h, std::max<size_t>((size_t)G * std::max<size_t>(L, 1), need)));
     plan_checkpoints(h, L);
@@ -1076,7 +1088,7 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
         h->Lbuf_bytes = std::max<size_t>(cb, 16);
     }
     const size_t op_doubles = ((size_t)n_pool * ob + 7) / 8;
-    SV_TRY(ensure_partials(h, std::max<size_t>(2 * (size_t)h->Db, 1) + op_doubles));
+    SV_TRY(ensure_partials(h, 3 * (size_t)h->Db + op_doubles));
     SV_TRY(ensure_out(h, 2 + (size_t)n_pool));
     const double c = shift_for(h, ham);
     const void *Cm = h->storage == 1 ? h->psi : h->Cbuf;  // compact amplitudes
@@ -1087,13 +1099,14 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
     }
     RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
                 T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db};
+    const int K = row_chunk(h, R);
     SV_CUDA(h, launch_sigma_rows(Cm, nullptr, h->Lbuf, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
-                                 h->partials, h->stream));
-    h->launches++;
+                                 h->partials, K, h->stream));
+    h->launches += K ? 2 : 1;
     SV_CUDA(h, launch_reduce_rows(h->partials, 2, h->Db, h->dout, h->stream));
     h->launches++;
     if (n_pool > 0) {
-        void *d_ops = h->partials + 2 * (size_t)h->Db;
+        void *d_ops = h->partials + 3 * (size_t)h->Db;
         SV_CUDA(h, cudaMemcpyAsync(d_ops, host_ops.data(), host_ops.size(), cudaMemcpyHostToDevice, h->stream));
         SV_CUDA(h, launch_pool_grad(Cm, h->Lbuf, h->dtype, d_ops, n_pool, h->str_sa, h->str_sb, h->str_a,
                                     h->str_b, h->rank_a, h->rank_b, h->Da, h->Db, h->dout + 2, h->stream));
@@ -1112,16 +1125,25 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
     SV_TRY(check_ready(h));
     if (!re_out) return fail(h, SV_ERR_ARG, "NULL re_out");
     DeviceGuard g(h->device);
-    if (h->storage == 1) {
+    if (h->storage == 1 || h->rdm_variant != 1) {
+        // string rows: on the state itself (sector storage) or on its compact copy
         SV_TRY(ensure_strings(h));
-        std::vector<uint8_t> host_el;
-        const int n_el = sect_rdm_elements(h->n, host_el);
-        SV_TRY(ensure_partials(h, (host_el.size() + sizeof(double) - 1) / sizeof(double)));
+        const int n_el = rdm_rows_elements(h->n);
+        const int grid = rdm_rows_grid(h->Db, h->sm_count);
+        SV_TRY(ensure_partials(h, (size_t)2 * n_el * grid));
         SV_TRY(ensure_out(h, 2 * (size_t)n_el));
-        SV_CUDA(h, cudaMemcpyAsync(h->partials, host_el.data(), host_el.size(), cudaMemcpyHostToDevice, h->stream));
         SV_TRY(mark(h, 0));
-        SV_CUDA(h, launch_rdm_c(h->psi, h->dtype, h->partials, n_el, h->str_sa, h->str_sb, h->str_a, h->str_b,
-                                h->rank_a, h->rank_b, h->Da, h->Db, h->dout, h->stream));
+        const void *Cm = h->psi;
+        if (h->storage == 0) {
+            SV_CUDA(h, launch_compact(h->psi, h->Cbuf, h->dtype, h->str_sa_s, h->str_sb_s, h->Da, h->Db, h->sm_count,
+                                      h->stream));
+            h->launches++;
+            Cm = h->Cbuf;
+        }
+        SV_CUDA(h, launch_rdm_rows(Cm, h->dtype, h->n, h->str_sa, h->str_sb, h->str_a, h->str_b, h->rank_a,
+                                   h->rank_b, h->Da, h->Db, grid, h->partials, h->stream));
+        h->launches++;
+        SV_CUDA(h, launch_reduce_rows(h->partials, 2 * n_el, grid, h->dout, h->stream));
         h->launches++;
         SV_TRY(mark(h, 7));
         SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, 2 * (size_t)n_el * sizeof(double), cudaMemcpyDeviceToHost,
@@ -1218,7 +1240,7 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
             h->max_bytes = value;
             return SV_OK;
         case SV_OPT_EXPECT_VARIANT:
-            if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "expect variant must be 0, 1 or 2");
+            if (value < 0 || value > 3) return fail(h, SV_ERR_ARG, "expect variant must be 0, 1, 2 or 3");
             h->expect_variant = (int)value;
             return SV_OK;
         case SV_OPT_RDM_VARIANT:
@@ -1230,6 +1252,10 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
             return SV_OK;
         case SV_OPT_LAYOUT_AUTO:
             h->layout_auto = value != 0;
+            return SV_OK;
+        case SV_OPT_AB_CHUNK:
+            if (value < 0 || value > 8) return fail(h, SV_ERR_ARG, "alpha-beta chunk must be in [0, 8]");
+            h->ab_chunk = value;
             return SV_OK;
     }
     return fail(h, SV_ERR_ARG, "unknown option");

@@ -20,6 +20,14 @@ __device__ __forceinline__ uint32_t insert_zero(uint32_t k, int p) {
     return ((k >> p) << (p + 1)) | low;
 }
 
+// Sum over a warp in a fixed shuffle tree; the total is valid in lane 0.
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Threads per block used by every reduction kernel.
 constexpr int kThreads = 256;
 

@@ -199,6 +199,7 @@ struct sv_ctx {
     int64_t max_bytes = 0;
     uint64_t bytes_owned = 0;
     int expect_variant = 0;
+    int64_t ab_chunk = 0;      // SV_OPT_AB_CHUNK: most partner rows per chunk of k_sigma_ab (0 auto)
     int rdm_variant = 0;
     // storage layout: address bit perm[q] holds qubit q (identity by default);
     // layout_auto: sv_energy_grad picks it from its operator list

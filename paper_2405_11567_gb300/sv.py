@@ -16,6 +16,7 @@ SV_C64, SV_C128 = 0, 1
 SV_OPT_CHECKPOINT_INTERVAL, SV_OPT_MAX_BYTES, SV_OPT_EXPECT_VARIANT, SV_OPT_RDM_VARIANT = 1, 2, 3, 4
 SV_OPT_PROFILE = 5
 SV_OPT_LAYOUT_AUTO = 6
+SV_OPT_AB_CHUNK = 7
 SV_PHASES = 6
 PHASE_NAMES = ("reference", "forward", "expectation", "reverse", "restore", "rdm1")
 STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV_ERR_TIMEOUT", 5: "SV_ERR_STATE"}

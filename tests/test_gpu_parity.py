@@ -178,13 +178,15 @@ def test_complex_start_open_shell(dtype):
 
 # ---------------------------------------------------------------- 1-RDM
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_rdm1_matches_oracle(dtype):
+def test_rdm1_matches_oracle(dtype, variant):
     p = inputs.make_problem(14, 6, 60, seed=66)
     sec = _oracle_problem(p)
     psi = A.apply_ansatz(sec, p["ops"], p["theta"] * 5, A.hf_state(sec, p["occ"]))
     ref = A.rdm1(sec, psi)
     st = _gpu_state(14, dtype)
+    st.set_option(sv.SV_OPT_RDM_VARIANT, variant)
     st.prepare_hf(p["occ"])
     st.apply_ansatz(p["ops"], p["theta"] * 5)
     got = st.rdm1()
@@ -298,10 +300,11 @@ def test_errors_are_reported_not_raised_on_device():
     assert np.isfinite(st.energy(ham))
 
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_expectation_variants_match_oracle(variant, dtype):
-    """Record scan (1) and string rows (2) on an open-shell complex state and on config 2."""
+    """Record scan (1), string rows in one kernel (2) and split (3) on an open-shell complex state
+    and on config 2."""
     n, na, nb = 12, 3, 2
     p = inputs.make_problem(n, 4, 30, seed=88)
     rng = np.random.default_rng(11)

@@ -255,3 +255,30 @@ def test_adapt_vqe_on_sector_storage_reaches_fci():
     out = adapt_vqe(st, ham, p["occ"], inputs.uccsd_pool(n, ne), max_ops=60, grad_tol=1e-6, energy_tol=1e-12,
                     vqe_gtol=1e-9)
     assert out["energy"] >= E0 - 1e-10 and out["energy"] - E0 < 1e-8
+
+
+@pytest.mark.parametrize("chunk", [1, 2, 4, 8])
+@pytest.mark.parametrize("variant", [2, 3])
+def test_expectation_forms_and_chunks(variant, chunk):
+    """Single-kernel (2) and split (3) string-row expectation, every partner-row chunk size, on an
+    open-shell complex start: the same energy, gradient and pool gradients to float64 rounding."""
+    n, na, nb = 14, 4, 2
+    p = inputs.make_problem(n, 6, 30, seed=91)
+    dense0 = inputs.random_sector_state(n, na, nb, np.random.default_rng(21))
+    sec = oracle.Sector(n, na, nb)
+    psi0 = dense0[sec.dets.astype(np.int64)]
+    theta = p["theta"] * 5
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _state(n, na, nb, "c128")
+    st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
+    st.set_option(sv.SV_OPT_AB_CHUNK, chunk)
+    st.prepare_state(dense0, na, nb)
+    E, g = st.energy_grad(ham, p["ops"], theta)
+    assert abs(E - Eref) <= 1e-10 and np.max(np.abs(g - gref)) <= 1e-9
+    pool = inputs.uccsd_pool(n, 6)[::4]
+    psi = A.apply_ansatz(sec, p["ops"], theta, psi0)
+    sig = A.hamiltonian_apply(sec, p["h"], p["eri"], p["e_nuc"], psi)
+    gp_ref = np.array([2 * np.vdot(sig, A.generator_apply(sec, op, psi)).real for op in pool])
+    _, gp = st.pool_gradients(ham, pool)
+    assert np.max(np.abs(gp - gp_ref)) <= 1e-9
