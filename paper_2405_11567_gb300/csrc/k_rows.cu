@@ -48,7 +48,8 @@ struct RowArgs {
     cplx<R> *lamc;          // compact sigma output [Db][Da] (nullable)
     const uint32_t *sa_s;   // [Da] alpha spread in the storage layout: addresses
     const uint32_t *sb_s;   // [Db]
-    double *partial;        // [2][Db]
+    double *partial;        // [3][Db]: energy, norm, alpha-beta energy share
+    const R *W2;            // [NP][NP] same-spin antisymmetrised (q1p1|q2p2) - (q1p2|q2p1), pair-indexed
     int Db;
 };
 
@@ -76,9 +77,8 @@ constexpr int kMaxPairs = 120;   // C(16, 2)
 constexpr int kMaxBS = 64;       // nb (N - nb) <= 8 * 8
 constexpr int kMaxBD = 784;      // C(8, 2)^2
 
-template <typename R, bool SPLIT>
+template <typename R>
 __global__ void __launch_bounds__(kRowThreads) k_sigma_rows(RowArgs<R> A) {
-    extern __shared__ __align__(16) unsigned char row_smem[];  // SPLIT: this block's row [Da]
     __shared__ BetaSingle<R> bs[kMaxBS];
     __shared__ BetaDouble<R> bd[kMaxBD];
     __shared__ R JB[kMaxOrb * kMaxOrb];
@@ -144,13 +144,8 @@ __global__ void __launch_bounds__(kRowThreads) k_sigma_rows(RowArgs<R> A) {
         x.v = eri4<R>(T, s1, r1, s2, r2) - eri4<R>(T, s1, r2, s2, r1);
         bd[d] = x;
     }
-    const cplx<R> *row = A.C + (size_t)Ib * Da;
-    if (SPLIT) {
-        cplx<R> *srow = reinterpret_cast<cplx<R> *>(row_smem);
-        for (int i = threadIdx.x; i < Da; i += blockDim.x) srow[i] = row[i];
-        row = srow;
-    }
     __syncthreads();
+    const cplx<R> *row = A.C + (size_t)Ib * Da;
     double e_acc = 0.0, n_acc = 0.0;
     for (int Ia = threadIdx.x; Ia < Da; Ia += blockDim.x) {
         const uint32_t a = T.stra[Ia], xa = T.sa[Ia], x = xa | xb;
@@ -208,7 +203,7 @@ __global__ void __launch_bounds__(kRowThreads) k_sigma_rows(RowArgs<R> A) {
             fma_c<R>(acc, (e.c ^ par(xa & e.M)) ? -e.v : e.v, A.C[(size_t)e.Jb * Da + Ia]);
         }
         // alpha-beta doubles: alpha p -> q outside, beta r -> s (block list) inside; value (qp|sr)
-        for (uint32_t o = SPLIT ? 0u : a; o; o &= o - 1u) {
+        for (uint32_t o = a; o; o &= o - 1u) {
             const int p = __ffs(o) - 1;
             for (uint32_t e = ea; e; e &= e - 1u) {
                 const int q = __ffs(e) - 1;
@@ -224,48 +219,20 @@ __global__ void __launch_bounds__(kRowThreads) k_sigma_rows(RowArgs<R> A) {
                 }
             }
         }
-        e_acc += (double)c0.x * (double)acc.x + (double)c0.y * (double)acc.y;
-        n_acc += (double)c0.x * (double)c0.x + (double)c0.y * (double)c0.y;
-        if (SPLIT) {  // add the alpha-beta part k_sigma_ab wrote to the output
-            if (A.lam) {
-                const cplx<R> u = A.lam[A.sa_s[Ia] | A.sb_s[Ib]];
-                acc.x += u.x; acc.y += u.y;
-            } else if (A.lamc) {
-                const cplx<R> u = A.lamc[(size_t)Ib * Da + Ia];
-                acc.x += u.x; acc.y += u.y;
-            }
-        }
         if (A.lam) A.lam[A.sa_s[Ia] | A.sb_s[Ib]] = acc;
         if (A.lamc) A.lamc[(size_t)Ib * Da + Ia] = acc;
+        e_acc += (double)c0.x * (double)acc.x + (double)c0.y * (double)acc.y;
+        n_acc += (double)c0.x * (double)c0.x + (double)c0.y * (double)c0.y;
     }
     block_sum2(e_acc, n_acc, red);
     if (threadIdx.x == 0) {
-        A.partial[Ib] = SPLIT ? e_acc + A.partial[2 * A.Db + Ib] : e_acc;
+        A.partial[Ib] = e_acc;
         A.partial[A.Db + Ib] = n_acc;
     }
 }
 
-// ---------------------------------------------------------------- alpha-beta part
+// ---------------------------------------------------------------- split form
 
-constexpr int kAbThreads = 512;
-constexpr int kAbIpt = 8;  // alpha strings per thread: Da <= 4096
-
-// sigma_ab[Ib][Ia] = sum over alpha p->q of a and beta r->s of b of
-// (qp|sr) sign C[rank(b')][rank(a')], written to the output (lam at the storage
-// address, else lamc) when there is one; the row's share of <psi|sigma> goes to
-// partial[2 Db + Ib].
-//
-// Partner rows b' are staged K at a time in shared memory (coalesced loads).  The
-// sign of a term is the product of three parities (x = spread(a) | spread(b)):
-//   beta single r -> s on x:           popc(x & between(2r+1, 2s+1)) -- depends on
-//                                      (a, k): one bit per chunk row, applied to
-//                                      that row's sum once per alpha string;
-//   alpha single p -> q, alpha bits:   popc(a & between(p, q)) -- per (a, pq),
-//                                      flips the integral's sign bit;
-//   alpha single p -> q, beta bits of the excited string b'_k between 2p and 2q --
-//                                      per (k, pq): folded into the staged
-//                                      integrals eriS[k][q N + p] = +-(qp|s_k r_k).
-// The rank table of alpha strings is copied to shared memory when it fits.
 template <typename R>
 __device__ __forceinline__ R flip_sign(R v, uint32_t bit);
 template <>
@@ -277,18 +244,232 @@ __device__ __forceinline__ double flip_sign<double>(double v, uint32_t bit) {
     return __longlong_as_double(__double_as_longlong(v) ^ (long long)((unsigned long long)bit << 63));
 }
 
+// Parity prefix of an orbital string: bit u = parity of the bits of s below u.
+__device__ __forceinline__ uint32_t prefix_parity(uint32_t s) {
+    uint32_t y = s << 1;
+    y ^= y << 1;
+    y ^= y << 2;
+    y ^= y << 4;
+    y ^= y << 8;
+    y ^= y << 16;
+    return y;
+}
+
+__device__ __forceinline__ int pair_index(int p, int q, int N) { return p * N - p * (p + 1) / 2 + (q - p - 1); }
+
+// Split form, first kernel: the diagonal, alpha singles, alpha-alpha doubles and
+// beta-beta doubles of the row, with the row, the pair-indexed same-spin integrals
+// W2 and Dt in shared memory.  Adds the part k_sigma_ab wrote to the output (which
+// runs first) and completes the row's energy with its share partial[2 Db + Ib].
+// Jordan-Wigner signs from the prefix-parity words (bit u = parity of the bits
+// below u) of a and b, PP = pp(a) ^ pp(b): the bits of x strictly between 2p and
+// 2q are the alpha orbitals strictly between p and q and the beta orbitals in
+// [min, max), so an alpha single p -> q has sign (-1)^(popc(PP & {p,q}) + [p<q]),
+// and an alpha double p1<p2 -> q1<q2 (taken as -(a+_q1 a_p2)(a+_q2 a_p1)) has
+// (-1)^popc(PP & {p1,p2,q1,q2}) times an orbital-order sign that W2 carries.
+template <typename R>
+__global__ void __launch_bounds__(kRowThreads, 2) k_sigma_same(RowArgs<R> A) {
+    extern __shared__ __align__(16) unsigned char same_dyn[];
+    __shared__ BetaDouble<R> bd[kMaxBD];
+    __shared__ R JB[kMaxOrb * kMaxOrb];
+    __shared__ uint8_t opair[kMaxPairs][2], epair[kMaxPairs][2];
+    __shared__ int n_op, n_ep;
+    __shared__ double red[2 * kThreads / 32];
+    const SigmaTables<R> &T = A.T;
+    const int Ib = blockIdx.x, N = T.N, Da = T.Da, NP = N * (N - 1) / 2;
+    cplx<R> *row = reinterpret_cast<cplx<R> *>(same_dyn);  // [Da]
+    R *W2S = reinterpret_cast<R *>(row + Da);               // [NP][NP]
+    R *DtS = W2S + NP * NP;                                 // [N^3]
+    const uint32_t b = T.strb[Ib], xb = T.sb[Ib], eb = ~b & T.maskN;
+    if (threadIdx.x == 0) {
+        int no = 0, ne = 0;
+        for (uint32_t o = b; o; o &= o - 1u)
+            for (uint32_t o2 = o & (o - 1u); o2; o2 &= o2 - 1u) {
+                opair[no][0] = (uint8_t)(__ffs(o) - 1);
+                opair[no][1] = (uint8_t)(__ffs(o2) - 1);
+                ++no;
+            }
+        for (uint32_t e = eb; e; e &= e - 1u)
+            for (uint32_t e2 = e & (e - 1u); e2; e2 &= e2 - 1u) {
+                epair[ne][0] = (uint8_t)(__ffs(e) - 1);
+                epair[ne][1] = (uint8_t)(__ffs(e2) - 1);
+                ++ne;
+            }
+        n_op = no;
+        n_ep = ne;
+    }
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        const R *jt = T.Jt + i * N;  // i = q * N + p
+        R v = 0;
+        for (uint32_t o = b; o; o &= o - 1u) v += jt[__ffs(o) - 1];
+        JB[i] = v;
+    }
+    const cplx<R> *grow = A.C + (size_t)Ib * Da;
+    for (int i = threadIdx.x; i < Da; i += blockDim.x) row[i] = grow[i];
+    for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) W2S[i] = A.W2[i];
+    for (int i = threadIdx.x; i < N * N * N; i += blockDim.x) DtS[i] = T.Dt[i];
+    __syncthreads();
+    const int nbd = n_op * n_ep;
+    for (int d = threadIdx.x; d < nbd; d += blockDim.x) {
+        const int oi = d / n_ep, ei = d - oi * n_ep;
+        const int r1 = opair[oi][0], r2 = opair[oi][1], s1 = epair[ei][0], s2 = epair[ei][1];
+        const int i = 2 * r1 + 1, j = 2 * r2 + 1, aa = 2 * s1 + 1, bb = 2 * s2 + 1;
+        const uint32_t M1 = between(i, bb), M2 = between(j, aa);
+        const uint32_t xb1 = xb ^ (1u << i) ^ (1u << bb);
+        BetaDouble<R> x;
+        x.Jb = T.rb[b ^ (1u << r1) ^ (1u << r2) ^ (1u << s1) ^ (1u << s2)];
+        x.M = M1 ^ M2;
+        x.c = 1 ^ par(xb & M1) ^ par(xb1 & M2);  // T = -(a+_a a_j)(a+_b a_i)
+        x.v = eri4<R>(T, s1, r1, s2, r2) - eri4<R>(T, s1, r2, s2, r1);
+        bd[d] = x;
+    }
+    __syncthreads();
+    const uint32_t ppb = prefix_parity(b);
+    double e_acc = 0.0, n_acc = 0.0;
+    for (int Ia = threadIdx.x; Ia < Da; Ia += blockDim.x) {
+        const uint32_t a = T.stra[Ia], xa = T.sa[Ia], x = xa | xb;
+        const uint32_t ea = ~a & T.maskN, PP = prefix_parity(a) ^ ppb;
+        const cplx<R> c0 = row[Ia];
+        double d = T.e_shift;
+        for (uint32_t o = x; o; o &= o - 1u) {
+            const int k = __ffs(o) - 1;
+            d += T.hdiag[k];
+            for (uint32_t o2 = o & (o - 1u); o2; o2 &= o2 - 1u) d += T.Jp[k * T.n + __ffs(o2) - 1];
+        }
+        cplx<R> acc = mk<R>((R)d * c0.x, (R)d * c0.y);
+        // alpha singles
+        for (uint32_t o = a; o; o &= o - 1u) {
+            const int p = __ffs(o) - 1;
+            for (uint32_t e = ea; e; e &= e - 1u) {
+                const int q = __ffs(e) - 1;
+                const R *dt = DtS + (q * N + p) * N;
+                R v = T.hm[q * N + p] + JB[q * N + p];
+                for (uint32_t o2 = a; o2; o2 &= o2 - 1u) v += dt[__ffs(o2) - 1];
+                const uint32_t m = (1u << p) | (1u << q);
+                if ((uint32_t)par(PP & m) ^ (uint32_t)(p < q)) v = -v;
+                fma_c<R>(acc, v, row[T.ra[a ^ m]]);
+            }
+        }
+        // alpha-alpha doubles: W2[(p1,p2)][(q1,q2)] holds the value and the orbital-order sign
+        for (uint32_t o = a; o; o &= o - 1u) {
+            const int p1 = __ffs(o) - 1;
+            for (uint32_t o2 = o & (o - 1u); o2; o2 &= o2 - 1u) {
+                const int p2 = __ffs(o2) - 1;
+                const uint32_t m12 = (1u << p1) | (1u << p2);
+                const R *w = W2S + pair_index(p1, p2, N) * NP;
+                for (uint32_t e = ea; e; e &= e - 1u) {
+                    const int q1 = __ffs(e) - 1;
+                    const uint32_t m1 = m12 | (1u << q1);
+                    const R *wq = w + pair_index(q1, 0, N);  // + q2 gives pair (q1, q2)
+                    for (uint32_t e2 = e & (e - 1u); e2; e2 &= e2 - 1u) {
+                        const int q2 = __ffs(e2) - 1;
+                        const uint32_t m = m1 | (1u << q2);
+                        const R v = flip_sign<R>(wq[q2], (uint32_t)par(PP & m));
+                        fma_c<R>(acc, v, row[T.ra[a ^ m]]);
+                    }
+                }
+            }
+        }
+        // beta-beta doubles (partner rows, same column)
+        for (int k = 0; k < nbd; ++k) {
+            const BetaDouble<R> e = bd[k];
+            fma_c<R>(acc, (e.c ^ par(xa & e.M)) ? -e.v : e.v, A.C[(size_t)e.Jb * Da + Ia]);
+        }
+        e_acc += (double)c0.x * (double)acc.x + (double)c0.y * (double)acc.y;
+        n_acc += (double)c0.x * (double)c0.x + (double)c0.y * (double)c0.y;
+        if (A.lam) {
+            const cplx<R> u = A.lam[A.sa_s[Ia] | A.sb_s[Ib]];
+            A.lam[A.sa_s[Ia] | A.sb_s[Ib]] = mk<R>(acc.x + u.x, acc.y + u.y);
+        } else if (A.lamc) {
+            const cplx<R> u = A.lamc[(size_t)Ib * Da + Ia];
+            A.lamc[(size_t)Ib * Da + Ia] = mk<R>(acc.x + u.x, acc.y + u.y);
+        }
+    }
+    block_sum2(e_acc, n_acc, red);
+    if (threadIdx.x == 0) {
+        A.partial[Ib] = e_acc + A.partial[2 * A.Db + Ib];
+        A.partial[A.Db + Ib] = n_acc;
+    }
+}
+
+constexpr int kAbThreads = 512;
+constexpr int kAbIpt = 8;  // alpha strings per thread: Da <= 4096
+
+// Integral slots per (q, p) in the staged table: K rounded up to a 16-byte multiple.
 template <typename R, int K>
-__global__ void __launch_bounds__(kAbThreads) k_sigma_ab(RowArgs<R> A, int ra_smem) {
+struct AbLayout {
+    static constexpr int KP = sizeof(R) == 4 ? (K + 3) & ~3 : (K + 1) & ~1;
+};
+
+// K consecutive complex amplitudes / KP reals from 16-byte-aligned shared memory.
+template <int K>
+__device__ __forceinline__ void lds_c(const float2 *p, float2 (&c)[K]) {
+    static_assert(K % 2 == 0, "complex64 chunks hold an even number of rows");
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    #pragma unroll
+    for (int j = 0; j < K / 2; ++j) {
+        const float4 v = q[j];
+        c[2 * j] = make_float2(v.x, v.y);
+        c[2 * j + 1] = make_float2(v.z, v.w);
+    }
+}
+template <int K>
+__device__ __forceinline__ void lds_c(const double2 *p, double2 (&c)[K]) {
+    #pragma unroll
+    for (int j = 0; j < K; ++j) c[j] = p[j];
+}
+template <int KP>
+__device__ __forceinline__ void lds_r(const float *p, float (&v)[KP]) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    #pragma unroll
+    for (int j = 0; j < KP / 4; ++j) {
+        const float4 t = q[j];
+        v[4 * j] = t.x; v[4 * j + 1] = t.y; v[4 * j + 2] = t.z; v[4 * j + 3] = t.w;
+    }
+}
+template <int KP>
+__device__ __forceinline__ void lds_r(const double *p, double (&v)[KP]) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    #pragma unroll
+    for (int j = 0; j < KP / 2; ++j) {
+        const double2 t = q[j];
+        v[2 * j] = t.x; v[2 * j + 1] = t.y;
+    }
+}
+
+// Split form, second kernel (launched first): the alpha-beta doubles and the beta
+// singles of the row.
+//   sigma_ab[Ib][Ia] = sum over beta r -> s of b (partner row b') of
+//       sign_b [ v_rs(a) C[b'][a] + sum over alpha p -> q of a of (qp|sr) sign_a C[b'][a'] ]
+// with v_rs(a) = h_sr + sum_{k in b} ((sr|kk) - (sk|kr)) + sum_{k in a} (sr|kk).
+// Written to the output (lam at the storage address, else lamc) when there is one;
+// the row's share of <psi|sigma> goes to partial[2 Db + Ib].
+//
+// Partner rows are staged K at a time in shared memory, interleaved by column
+// (part[a][k]), so one vector load brings a column's K partner amplitudes; the
+// integrals are staged as eriS[q N + p][k].  Signs (x = spread(a) | spread(b)):
+//   beta single r -> s on x:  popc(x & between(2r+1, 2s+1)) -- per (a, k): applied
+//                             once to row k's sum for this a;
+//   alpha single p -> q on the excited x': its alpha bits between p and q -- per
+//                             (a, pq): flips the integrals' sign bits; its beta bits
+//                             (orbitals lo..hi-1 of b'_k) -- per (k, pq): folded into
+//                             the staged integrals.
+// The alpha rank table sits in shared memory.
+template <typename R, int K>
+__global__ void __launch_bounds__(kAbThreads) k_sigma_ab(RowArgs<R> A) {
+    constexpr int KP = AbLayout<R, K>::KP;
     extern __shared__ __align__(16) unsigned char ab_dyn[];
     __shared__ int s_Jb[kMaxBS], s_t[kMaxBS], s_cb[kMaxBS];
     __shared__ uint32_t s_M[kMaxBS], s_bf[kMaxBS];
+    __shared__ R s_vb[kMaxBS];
     __shared__ int n_bs;
     __shared__ double red[kAbThreads / 32];
     const SigmaTables<R> &T = A.T;
     const int Ib = blockIdx.x, N = T.N, Da = T.Da, NN = N * N;
-    cplx<R> *part = reinterpret_cast<cplx<R> *>(ab_dyn);         // [K][Da]
-    R *eriS = reinterpret_cast<R *>(part + (size_t)K * Da);      // [K][N*N]
-    uint16_t *raS = reinterpret_cast<uint16_t *>(eriS + (size_t)K * NN);  // [2^N] when ra_smem
+    cplx<R> *part = reinterpret_cast<cplx<R> *>(ab_dyn);          // [Da][K]
+    R *eriS = reinterpret_cast<R *>(part + (size_t)K * Da);       // [N*N][KP]
+    R *JtS = eriS + (size_t)NN * KP;                              // [K][N]: (s_k r_k|kk)
+    uint16_t *raS = reinterpret_cast<uint16_t *>(JtS + (size_t)K * N);  // [2^N]
     const uint32_t b = T.strb[Ib], xb = T.sb[Ib], eb = ~b & T.maskN;
     if (threadIdx.x == 0) {
         int k = 0;
@@ -302,17 +483,18 @@ __global__ void __launch_bounds__(kAbThreads) k_sigma_ab(RowArgs<R> A, int ra_sm
                 s_M[k] = between(2 * r + 1, 2 * s + 1);
                 s_bf[k] = bf;
                 s_cb[k] = par(xb & s_M[k]);
+                R v = T.hm[s * N + r];
+                for (uint32_t o2 = b; o2; o2 &= o2 - 1u) v += T.Dt[(s * N + r) * N + __ffs(o2) - 1];
+                s_vb[k] = v;
                 ++k;
             }
         }
         n_bs = k;
     }
-    const uint16_t *rk = T.ra;
-    if (ra_smem) {
+    {
         const uint32_t *src = reinterpret_cast<const uint32_t *>(T.ra);
         uint32_t *dst = reinterpret_cast<uint32_t *>(raS);
         for (int i = threadIdx.x; i < (1 << N) / 2; i += kAbThreads) dst[i] = src[i];
-        rk = raS;
     }
     __syncthreads();
     const int nbs = n_bs;
@@ -322,16 +504,12 @@ __global__ void __launch_bounds__(kAbThreads) k_sigma_ab(RowArgs<R> A, int ra_sm
     for (int k0 = 0; k0 < nbs; k0 += K) {
         const int kn = min(K, nbs - k0);
         if (k0) __syncthreads();  // the previous chunk is consumed
-        for (int k = 0; k < K; ++k) {
-            if (k < kn) {
-                const cplx<R> *src = A.C + (size_t)s_Jb[k0 + k] * Da;
-                for (int i = threadIdx.x; i < Da; i += kAbThreads) part[k * Da + i] = src[i];
-            } else {  // rows past the end of the list contribute zero
-                for (int i = threadIdx.x; i < Da; i += kAbThreads) part[k * Da + i] = mk<R>(0, 0);
-            }
+        for (int i = threadIdx.x; i < K * Da; i += kAbThreads) {
+            const int k = i / Da, c = i - k * Da;
+            part[(size_t)c * K + k] = k < kn ? A.C[(size_t)s_Jb[k0 + k] * Da + c] : mk<R>(0, 0);
         }
-        for (int i = threadIdx.x; i < K * NN; i += kAbThreads) {
-            const int k = i / NN, qp = i - k * NN, q = qp / N, p = qp - q * N;
+        for (int i = threadIdx.x; i < NN * KP; i += kAbThreads) {
+            const int qp = i / KP, k = i - qp * KP, q = qp / N, p = qp - q * N;
             R v = 0;
             if (k < kn && p != q) {
                 const int lo = min(p, q), hi = max(p, q);
@@ -340,39 +518,54 @@ __global__ void __launch_bounds__(kAbThreads) k_sigma_ab(RowArgs<R> A, int ra_sm
             }
             eriS[i] = v;
         }
+        for (int i = threadIdx.x; i < K * N; i += kAbThreads) {
+            const int k = i / N, o = i - k * N;
+            JtS[i] = k < kn ? T.Jt[(size_t)s_t[k0 + k] * N + o] : (R)0;
+        }
         __syncthreads();
         uint32_t Mk[K];
         int cbk[K];
+        R vbk[K];
         #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int kk = k < kn ? k0 + k : k0;
             Mk[k] = s_M[kk];
             cbk[k] = s_cb[kk];
+            vbk[k] = k < kn ? s_vb[kk] : (R)0;
         }
         #pragma unroll
         for (int t = 0; t < kAbIpt; ++t) {
             const int Ia = threadIdx.x + t * kAbThreads;
             if (Ia >= Da) continue;
-            const uint32_t a = T.stra[Ia], xa = T.sa[Ia], ea = ~a & T.maskN;
+            const uint32_t a = T.stra[Ia], xa = T.sa[Ia], ea = ~a & T.maskN, ppa = prefix_parity(a);
             cplx<R> sk[K];
-            #pragma unroll
-            for (int k = 0; k < K; ++k) sk[k] = mk<R>(0, 0);
+            {   // beta singles: same column of the staged rows
+                cplx<R> c[K];
+                lds_c<K>(part + (size_t)Ia * K, c);
+                #pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    R v = vbk[k];
+                    for (uint32_t o = a; o; o &= o - 1u) v += JtS[k * N + __ffs(o) - 1];
+                    sk[k] = mk<R>(v * c[k].x, v * c[k].y);
+                }
+            }
             for (uint32_t o = a; o; o &= o - 1u) {
                 const int p = __ffs(o) - 1;
                 for (uint32_t e = ea; e; e &= e - 1u) {
                     const int q = __ffs(e) - 1;
-                    const int Ja = rk[a ^ (1u << p) ^ (1u << q)];
-                    const int lo = min(p, q), hi = max(p, q);
-                    const uint32_t mA = ((1u << hi) - 1u) & ~((2u << lo) - 1u);  // alpha orbitals lo+1..hi-1
-                    const uint32_t sa0 = (uint32_t)par(a & mA);
-                    const R *ev = eriS + q * N + p;
-                    const cplx<R> *pc = part + Ja;
+                    const uint32_t m = (1u << p) | (1u << q);
+                    const int Ja = raS[a ^ m];
+                    // alpha bits strictly between p and q
+                    const uint32_t sa0 = (uint32_t)par(ppa & m) ^ (uint32_t)(p < q);
+                    cplx<R> c[K];
+                    R v[KP];
+                    lds_c<K>(part + (size_t)Ja * K, c);
+                    lds_r<KP>(eriS + (q * N + p) * KP, v);
                     #pragma unroll
                     for (int k = 0; k < K; ++k) {
-                        const R v = flip_sign<R>(ev[k * NN], sa0);
-                        const cplx<R> c = pc[k * Da];
-                        sk[k].x += v * c.x;
-                        sk[k].y += v * c.y;
+                        const R w = flip_sign<R>(v[k], sa0);
+                        sk[k].x += w * c[k].x;
+                        sk[k].y += w * c[k].y;
                     }
                 }
             }
@@ -441,6 +634,7 @@ struct RowTables {
     const uint16_t *stra, *strb, *ra, *rb;
     const void *eri, *hm, *Dt, *Jt;
     int N, Da, Db;
+    const void *W2 = nullptr;  // pair-indexed same-spin integrals (split form)
 };
 
 template <typename R>
@@ -452,85 +646,96 @@ static RowArgs<R> row_args(const void *C, void *lam, void *lamc, int n, const Ro
     A.T.hdiag = hdiag; A.T.Jp = Jp; A.T.e_shift = e_shift;
     A.T.N = T.N; A.T.n = n; A.T.Da = T.Da; A.T.maskN = (1u << T.N) - 1u;
     A.C = (const cplx<R> *)C; A.lam = (cplx<R> *)lam; A.lamc = (cplx<R> *)lamc; A.sa_s = T.sa_s; A.sb_s = T.sb_s;
-    A.partial = partial; A.Db = T.Db;
+    A.partial = partial; A.Db = T.Db; A.W2 = (const R *)T.W2;
     return A;
 }
 
-constexpr size_t kAbSmemCap = 225 * 1024;  // dynamic shared memory the split form may use
+constexpr size_t kAbSmemCap = 225 * 1024;  // dynamic shared memory a split kernel may use
 
-static size_t ab_smem(int dtype, int K, const RowTables &T, bool ra_in) {
+// Dynamic shared memory of k_sigma_ab for K staged rows, and of k_sigma_same.
+static size_t ab_smem(int dtype, int K, const RowTables &T) {
     const size_t amp = dtype == SV_C64 ? 8 : 16, real = amp / 2;
-    return (size_t)K * T.Da * amp + (size_t)K * T.N * T.N * real + (ra_in ? ((size_t)2 << T.N) : 0);
+    const size_t KP = dtype == SV_C64 ? (size_t)((K + 3) & ~3) : (size_t)((K + 1) & ~1);
+    return (size_t)K * T.Da * amp + (size_t)T.N * T.N * KP * real + (size_t)K * T.N * real + ((size_t)2 << T.N);
 }
 
-static const int kAbChunks[] = {1, 2, 3, 4, 5, 6, 8};
+static size_t same_smem(int dtype, const RowTables &T) {
+    const size_t amp = dtype == SV_C64 ? 8 : 16, real = amp / 2, NP = (size_t)T.N * (T.N - 1) / 2;
+    return (size_t)T.Da * amp + NP * NP * real + (size_t)T.N * T.N * T.N * real;
+}
 
-// Rows staged per chunk by k_sigma_ab (0: the split form does not fit), and whether
-// the alpha rank table goes to shared memory: the fewest estimated issue slots,
-// chunks * (K + 3), among the sizes that fit, with the table in shared memory if
-// any size allows it.
-int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want, int *ra_in) {
-    if (T.Da > kAbThreads * kAbIpt || T.Db < 1) return 0;
+static const int kChunksC64[] = {2, 4, 6, 8};
+static const int kChunksC128[] = {1, 2, 3, 4};
+
+// Rows staged per chunk by k_sigma_ab, 0 when the split form does not fit (the
+// single-kernel form runs instead): the fewest estimated issue slots,
+// chunks * (K + 3), among the sizes that fit; `want` > 0 caps K.
+int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want) {
+    if (T.Da > kAbThreads * kAbIpt || T.Db < 1 || T.N < 2) return 0;
+    if (same_smem(dtype, T) > kAbSmemCap) return 0;
     const int nbs = nb * (T.N - nb) > 0 ? nb * (T.N - nb) : 1;  // beta singles of a row
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool rin = pass == 0;
-        int best = 0;
-        long best_cost = 0;
-        for (int K : kAbChunks) {
-            if (want > 0 && K > want) continue;
-            if (ab_smem(dtype, K, T, rin) > kAbSmemCap) continue;
-            const long cost = (long)((nbs + K - 1) / K) * (K + 3);
-            if (!best || cost < best_cost || (cost == best_cost && K > best)) {
-                best = K;
-                best_cost = cost;
-            }
-        }
-        if (best) {
-            if (ra_in) *ra_in = rin ? 1 : 0;
-            return best;
+    int best = 0;
+    long best_cost = 0;
+    for (int i = 0; i < 4; ++i) {
+        const int K = dtype == SV_C64 ? kChunksC64[i] : kChunksC128[i];
+        if (want > 0 && K > want) continue;
+        if (ab_smem(dtype, K, T) > kAbSmemCap) continue;
+        const long cost = (long)((nbs + K - 1) / K) * (K + 3);
+        if (!best || cost < best_cost || (cost == best_cost && K > best)) {
+            best = K;
+            best_cost = cost;
         }
     }
-    return 0;
+    return best;
 }
 
 template <typename R, int K>
-static cudaError_t launch_ab(const RowArgs<R> &A, size_t smem, int ra_in, cudaStream_t st) {
+static cudaError_t launch_ab(const RowArgs<R> &A, size_t smem, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_sigma_ab<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sigma_ab<R, K><<<A.Db, kAbThreads, smem, st>>>(A, ra_in);
+    k_sigma_ab<R, K><<<A.Db, kAbThreads, smem, st>>>(A);
     return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t launch_ab_k(const RowArgs<R> &A, int K, size_t smem, cudaStream_t st);
+template <>
+cudaError_t launch_ab_k<float>(const RowArgs<float> &A, int K, size_t smem, cudaStream_t st) {
+    switch (K) {
+        case 2: return launch_ab<float, 2>(A, smem, st);
+        case 4: return launch_ab<float, 4>(A, smem, st);
+        case 6: return launch_ab<float, 6>(A, smem, st);
+        case 8: return launch_ab<float, 8>(A, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+template <>
+cudaError_t launch_ab_k<double>(const RowArgs<double> &A, int K, size_t smem, cudaStream_t st) {
+    switch (K) {
+        case 1: return launch_ab<double, 1>(A, smem, st);
+        case 2: return launch_ab<double, 2>(A, smem, st);
+        case 3: return launch_ab<double, 3>(A, smem, st);
+        case 4: return launch_ab<double, 4>(A, smem, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <typename R>
 static cudaError_t launch_rows_t(const RowArgs<R> &A, const RowTables &T, int dtype, int K, cudaStream_t st) {
     if (K == 0) {
-        k_sigma_rows<R, false><<<T.Db, kRowThreads, 0, st>>>(A);
+        k_sigma_rows<R><<<T.Db, kRowThreads, 0, st>>>(A);
         return cudaGetLastError();
     }
-    const bool rin = (K & 16) != 0;
-    K &= 15;
-    const size_t smem = ab_smem(dtype, K, T, rin);
-    cudaError_t e;
-    switch (K) {
-        case 1: e = launch_ab<R, 1>(A, smem, rin, st); break;
-        case 2: e = launch_ab<R, 2>(A, smem, rin, st); break;
-        case 3: e = launch_ab<R, 3>(A, smem, rin, st); break;
-        case 4: e = launch_ab<R, 4>(A, smem, rin, st); break;
-        case 5: e = launch_ab<R, 5>(A, smem, rin, st); break;
-        case 6: e = launch_ab<R, 6>(A, smem, rin, st); break;
-        case 8: e = launch_ab<R, 8>(A, smem, rin, st); break;
-        default: return cudaErrorInvalidValue;
-    }
+    cudaError_t e = launch_ab_k<R>(A, K, ab_smem(dtype, K, T), st);
     if (e != cudaSuccess) return e;
-    const size_t row_bytes = (size_t)T.Da * sizeof(cplx<R>);
-    e = cudaFuncSetAttribute(k_sigma_rows<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_bytes);
+    const size_t smem = same_smem(dtype, T);
+    e = cudaFuncSetAttribute(k_sigma_same<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sigma_rows<R, true><<<T.Db, kRowThreads, row_bytes, st>>>(A);
+    k_sigma_same<R><<<T.Db, kRowThreads, smem, st>>>(A);
     return cudaGetLastError();
 }
 
-// K: rows per chunk of the split form (sigma_ab_chunk), plus 16 when the alpha rank
-// table is staged in shared memory; 0 for the single-kernel form.
+// K: rows per chunk of the split form (sigma_ab_chunk), 0 for the single-kernel form.
 // partial must hold 3 * Db doubles (rows: energy, norm, alpha-beta energy share).
 cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &T, const double *hdiag,
                               const double *Jp, double e_shift, double *partial, int K, cudaStream_t st) {

@@ -61,15 +61,16 @@ struct RowTables {
     const uint16_t *stra, *strb, *ra, *rb;
     const void *eri, *hm, *Dt, *Jt;
     int N, Da, Db;
+    const void *W2 = nullptr;  // pair-indexed same-spin integrals (split form)
 };
 cudaError_t launch_compact(const void *psi, void *C, int dtype, const uint32_t *sa, const uint32_t *sb, int Da,
                            int Db, int sm_count, cudaStream_t st);
 cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &T, const double *hdiag,
                               const double *Jp, double e_shift, double *partial, int K, cudaStream_t st);
-int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want, int *ra_in);
+int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want);
 
 DevTables::~DevTables() {
-    void *ptrs[] = {dbl, sgl, W, hdiag, Jp, hdiag_s, Jp_s, eri_r, hm_r, Dt, Jt, pass_dbl, pass_sgl, pass_W};
+    void *ptrs[] = {dbl, sgl, W, hdiag, Jp, hdiag_s, Jp_s, eri_r, hm_r, Dt, Jt, W2, pass_dbl, pass_sgl, pass_W};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -364,6 +365,23 @@ static sv_status upload_tables(sv_handle h, sv_ham_handle ham, DevTables &T) {
     SV_TRY(up(&T.hm_r, hm.data(), hm.size() * sizeof(R)));
     SV_TRY(up(&T.Dt, Dt.data(), Dt.size() * sizeof(R)));
     SV_TRY(up(&T.Jt, Jt.data(), Jt.size() * sizeof(R)));
+    // same-spin doubles p1 < p2 -> q1 < q2 by pairs, W2[(p1,p2)][(q1,q2)] =
+    // s0 ((q1p1|q2p2) - (q1p2|q2p1)), with the orbital-order part of the
+    // Jordan-Wigner sign, s0 = (-1)^([p1<q2] + [q2<p2] + [p1<q1] + [p2<q1]), folded in;
+    // the string-dependent part is the parity of the prefix-parity words of a and b
+    // over the four orbitals (k_sigma_same).
+    const int NP = N * (N - 1) / 2;
+    std::vector<R> W2((size_t)std::max(NP, 1) * std::max(NP, 1));
+    auto pidx = [&](int p, int q) { return p * N - p * (p + 1) / 2 + (q - p - 1); };
+    for (int p1 = 0; p1 < N; ++p1)
+        for (int p2 = p1 + 1; p2 < N; ++p2)
+            for (int q1 = 0; q1 < N; ++q1)
+                for (int q2 = q1 + 1; q2 < N; ++q2) {
+                    const int s0 = (p1 < q2) ^ (q2 < p2) ^ (p1 < q1) ^ (p2 < q1);
+                    const double v = E(q1, p1, q2, p2) - E(q1, p2, q2, p1);
+                    W2[(size_t)pidx(p1, p2) * NP + pidx(q1, q2)] = (R)(s0 ? -v : v);
+                }
+    SV_TRY(up(&T.W2, W2.data(), W2.size() * sizeof(R)));
     return SV_OK;
 }
 
@@ -497,9 +515,7 @@ static void plan_checkpoints(sv_handle h, size_t L) {
 // Rows per chunk of the split string-row expectation (0: single kernel).
 static int row_chunk(sv_handle h, const RowTables &R) {
     if (h->expect_variant == 2) return 0;
-    int ra_in = 0;
-    const int K = sigma_ab_chunk(h->dtype, R, h->nb, (int)h->ab_chunk, &ra_in);
-    return K ? K | (ra_in ? 16 : 0) : 0;
+    return sigma_ab_chunk(h->dtype, R, h->nb, (int)h->ab_chunk);
 }
 
 // Expectation pass over the current state: writes the float64 sums of
@@ -511,7 +527,7 @@ static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void 
         SV_TRY(ensure_strings(h));
         SV_TRY(ensure_partials(h, 3 * (size_t)h->Db));
         RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
-                    T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db};
+                    T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db, T->W2};
         const int K = row_chunk(h, R);
         SV_CUDA(h, launch_sigma_rows(h->psi, nullptr, sigma, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
                                      h->partials, K, h->stream));
@@ -529,7 +545,7 @@ static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void 
                                   h->stream));
         h->launches++;
         RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
-                    T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db};
+                    T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db, T->W2};
         const int K = row_chunk(h, R);
         SV_CUDA(h, launch_sigma_rows(h->Cbuf, sigma, nullptr, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
                                      h->partials, K, h->stream));
@@ -1098,7 +1114,7 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
         h->launches++;
     }
     RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
-                T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db};
+                T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db, T->W2};
     const int K = row_chunk(h, R);
     SV_CUDA(h, launch_sigma_rows(Cm, nullptr, h->Lbuf, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
                                  h->partials, K, h->stream));

@@ -112,6 +112,7 @@ struct DevTables {
     void *hm_r = nullptr;   // [N^2] h_pq
     void *Dt = nullptr;     // [N^3] (qp|kk) - (qk|kp)
     void *Jt = nullptr;     // [N^3] (qp|kk)
+    void *W2 = nullptr;     // [NP][NP] same-spin doubles by (q1<q2, p1<p2) pairs
     // tiled-pass schedule (k_expect.cu); empty until first needed
     struct Pass {
         uint32_t S;        // local qubit set (bit mask over storage positions)

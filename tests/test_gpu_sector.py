@@ -257,9 +257,10 @@ def test_adapt_vqe_on_sector_storage_reaches_fci():
     assert out["energy"] >= E0 - 1e-10 and out["energy"] - E0 < 1e-8
 
 
-@pytest.mark.parametrize("chunk", [1, 2, 4, 8])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("chunk", [1, 2, 3, 4, 6, 8])
 @pytest.mark.parametrize("variant", [2, 3])
-def test_expectation_forms_and_chunks(variant, chunk):
+def test_expectation_forms_and_chunks(variant, chunk, dtype):
     """Single-kernel (2) and split (3) string-row expectation, every partner-row chunk size, on an
     open-shell complex start: the same energy, gradient and pool gradients to float64 rounding."""
     n, na, nb = 14, 4, 2
@@ -270,15 +271,15 @@ def test_expectation_forms_and_chunks(variant, chunk):
     theta = p["theta"] * 5
     Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
-    st = _state(n, na, nb, "c128")
+    st = _state(n, na, nb, dtype)
     st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
     st.set_option(sv.SV_OPT_AB_CHUNK, chunk)
-    st.prepare_state(dense0, na, nb)
+    st.prepare_state(dense0.astype(np.complex64 if dtype == "c64" else np.complex128), na, nb)
     E, g = st.energy_grad(ham, p["ops"], theta)
-    assert abs(E - Eref) <= 1e-10 and np.max(np.abs(g - gref)) <= 1e-9
+    assert abs(E - Eref) <= TOL[dtype]["E"] and np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
     pool = inputs.uccsd_pool(n, 6)[::4]
     psi = A.apply_ansatz(sec, p["ops"], theta, psi0)
     sig = A.hamiltonian_apply(sec, p["h"], p["eri"], p["e_nuc"], psi)
     gp_ref = np.array([2 * np.vdot(sig, A.generator_apply(sec, op, psi)).real for op in pool])
     _, gp = st.pool_gradients(ham, pool)
-    assert np.max(np.abs(gp - gp_ref)) <= 1e-9
+    assert np.max(np.abs(gp - gp_ref)) <= TOL[dtype]["g"]
