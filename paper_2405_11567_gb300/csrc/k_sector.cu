@@ -10,8 +10,9 @@
 // matches its beta pattern; its partner is found through the string ranks.  The
 // kernels below give each block one beta string (row) and its threads the alpha
 // strings of that row, so a launch touches only the pairs it rotates:
-//   k_rotate_c   psi'[x] = c psi[x] - s sn psi[x'],  psi'[x'] = c psi[x'] + s sn psi[x]
-//   k_adjoint_c  g += s (Re conj(lam[x']) psi[x] - Re conj(lam[x]) psi[x']), then U^dagger
+//   k_rotate_l   psi'[x] = c psi[x] - s sn psi[x'],  psi'[x'] = c psi[x'] + s sn psi[x]
+//                over the op's pairs (alpha list x beta list, built by k_build_lists)
+//   k_adjoint_l  g += s (Re conj(lam[x']) psi[x] - Re conj(lam[x]) psi[x']), then U^dagger
 //                on psi and lambda (float64 per block, fixed-order sums)
 //   k_rdm_rows   one block per beta string: every density-matrix element's share
 // with s = (-1)^popc(x & sm), the Jordan-Wigner sign (sm = 0 for qubit
@@ -37,19 +38,75 @@ struct SectTabs {
     int Da, Db;
 };
 
+// Per-operator lists.  An operator acts on the determinants whose alpha string
+// matches its alpha pattern and whose beta string matches its beta pattern, so its
+// pairs are the product of an alpha list and a beta list.  Both are built once per
+// operator list (k_build_lists) and kept on the device: one uint32 per string,
+//   rank | sign << 15 | partner rank << 16,
+// with sign = parity of the string's spread under the operator's sign mask (the
+// Jordan-Wigner sign of the pair is the XOR of the alpha and beta entries).
+// Ranks fit in 15 bits: at most C(16, 8) = 12,870 strings.
+struct ListOp {
+    uint32_t sm, ma, fa, mb, fb;
+    uint32_t a_off, b_off;  // entry offsets of the op's alpha and beta lists
+    uint32_t a_n, b_n;      // their lengths (C(N - |m|, n - |f|) per spin)
+};
+
+// Block 2k builds op k's alpha list, block 2k+1 its beta list, in rank order
+// (ordered compaction with warp ballots).
+__global__ void __launch_bounds__(kThreads) k_build_lists(const ListOp *__restrict__ ops, SectTabs T,
+                                                          uint32_t *__restrict__ out) {
+    __shared__ int wcount[kThreads / 32];
+    const ListOp op = ops[blockIdx.x >> 1];
+    const bool beta = blockIdx.x & 1;
+    const int D = beta ? T.Db : T.Da;
+    const uint16_t *str = beta ? T.strb : T.stra, *rk = beta ? T.rb : T.ra;
+    const uint32_t *spr = beta ? T.sb : T.sa;
+    const uint32_t m = beta ? op.mb : op.ma, f = beta ? op.fb : op.fa;
+    uint32_t *dst = out + (beta ? op.b_off : op.a_off);
+    const int cap = (int)(beta ? op.b_n : op.a_n);  // the host's count: writes never pass it
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    int total = 0;
+    for (int base = 0; base < D; base += blockDim.x) {
+        const int I = base + threadIdx.x;
+        uint32_t s = 0;
+        bool hit = false;
+        if (I < D) {
+            s = str[I];
+            hit = (s & m) == f;
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) wcount[warp] = __popc(bal);
+        __syncthreads();
+        int off = total, sum = 0;
+        for (int w = 0; w < nw; ++w) {
+            const int c = wcount[w];
+            if (w < warp) off += c;
+            sum += c;
+        }
+        if (hit && off + __popc(bal & lt) < cap)
+            dst[off + __popc(bal & lt)] = (uint32_t)I | ((uint32_t)par(spr[I] & op.sm) << 15) |
+                                          ((uint32_t)rk[s ^ m] << 16);
+        total += sum;
+        __syncthreads();
+    }
+}
+
+// psi <- exp(theta G) psi over the op's pairs: block r takes beta entries r, r + grid,
+// ..., its threads the alpha entries.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_rotate_c(cplx<R> *__restrict__ psi, SectOp op, SectTabs T) {
-    const R c = (R)op.c, sn = (R)op.s;
-    for (int Ib = blockIdx.x; Ib < T.Db; Ib += gridDim.x) {
-        const uint32_t b = T.strb[Ib];
-        if ((b & op.mb) != op.fb) continue;
-        const size_t rowI = (size_t)Ib * T.Da, rowJ = (size_t)T.rb[b ^ op.mb] * T.Da;
-        const uint32_t xb = T.sb[Ib];
-        for (int Ia = threadIdx.x; Ia < T.Da; Ia += blockDim.x) {
-            const uint32_t a = T.stra[Ia];
-            if ((a & op.ma) != op.fa) continue;
-            const size_t I = rowI + Ia, J = rowJ + T.ra[a ^ op.ma];
-            const R ss = par((T.sa[Ia] | xb) & op.sm) ? -sn : sn;
+__global__ void __launch_bounds__(kThreads) k_rotate_l(cplx<R> *__restrict__ psi, const uint32_t *__restrict__ al,
+                                                       int na_l, const uint32_t *__restrict__ bl, int nb_l, int Da,
+                                                       R c, R sn) {
+    for (int r = blockIdx.x; r < nb_l; r += gridDim.x) {
+        const uint32_t eb = bl[r];
+        const size_t rowI = (size_t)(eb & 0x7FFFu) * Da, rowJ = (size_t)(eb >> 16) * Da;
+        const uint32_t sgb = eb & 0x8000u;
+        for (int i = threadIdx.x; i < na_l; i += blockDim.x) {
+            const uint32_t ea = al[i];
+            const size_t I = rowI + (ea & 0x7FFFu), J = rowJ + (ea >> 16);
+            const R ss = ((ea & 0x8000u) ^ sgb) ? -sn : sn;
             const cplx<R> u = psi[I], v = psi[J];
             psi[I] = mk<R>(c * u.x - ss * v.x, c * u.y - ss * v.y);
             psi[J] = mk<R>(c * v.x + ss * u.x, c * v.y + ss * u.y);
@@ -57,23 +114,24 @@ __global__ void __launch_bounds__(kThreads) k_rotate_c(cplx<R> *__restrict__ psi
     }
 }
 
+// Adjoint step over the op's pairs: the gradient term, then U^dagger on psi and
+// lambda; one float64 partial per block (fixed order).
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_adjoint_c(cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam, SectOp op,
-                                                        SectTabs T, double *__restrict__ partial) {
+__global__ void __launch_bounds__(kThreads) k_adjoint_l(cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam,
+                                                        const uint32_t *__restrict__ al, int na_l,
+                                                        const uint32_t *__restrict__ bl, int nb_l, int Da, R c, R sn,
+                                                        double *__restrict__ partial) {
     __shared__ double red[kThreads / 32];
-    const R c = (R)op.c, sn = (R)op.s;
     double acc = 0.0;
-    for (int Ib = blockIdx.x; Ib < T.Db; Ib += gridDim.x) {
-        const uint32_t b = T.strb[Ib];
-        if ((b & op.mb) != op.fb) continue;
-        const size_t rowI = (size_t)Ib * T.Da, rowJ = (size_t)T.rb[b ^ op.mb] * T.Da;
-        const uint32_t xb = T.sb[Ib];
+    for (int r = blockIdx.x; r < nb_l; r += gridDim.x) {
+        const uint32_t eb = bl[r];
+        const size_t rowI = (size_t)(eb & 0x7FFFu) * Da, rowJ = (size_t)(eb >> 16) * Da;
+        const uint32_t sgb = eb & 0x8000u;
         R t = 0;
-        for (int Ia = threadIdx.x; Ia < T.Da; Ia += blockDim.x) {
-            const uint32_t a = T.stra[Ia];
-            if ((a & op.ma) != op.fa) continue;
-            const size_t I = rowI + Ia, J = rowJ + T.ra[a ^ op.ma];
-            const bool neg = par((T.sa[Ia] | xb) & op.sm);
+        for (int i = threadIdx.x; i < na_l; i += blockDim.x) {
+            const uint32_t ea = al[i];
+            const size_t I = rowI + (ea & 0x7FFFu), J = rowJ + (ea >> 16);
+            const bool neg = (ea & 0x8000u) ^ sgb;
             const cplx<R> u = psi[I], v = psi[J], lu = lam[I], lv = lam[J];
             const R ti = (lv.x * u.x + lv.y * u.y) - (lu.x * v.x + lu.y * v.y);
             t += neg ? -ti : ti;
@@ -223,27 +281,63 @@ void sect_op_from(const OpDesc &d, int N, void *dst) {
     *(SectOp *)dst = o;
 }
 
-size_t sect_op_bytes() { return sizeof(SectOp); }
-
 int sector_grid(int Db, int sm_count) { return Db < sm_count * 8 ? Db : sm_count * 8; }
 
-cudaError_t launch_rotate_c(void *psi, int dtype, const void *op, const uint32_t *sa, const uint32_t *sb,
-                            const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb, int Da,
-                            int Db, int grid, cudaStream_t st) {
+// Host side of the lists: counts from the patterns, offsets, and the build launch.
+static uint64_t choose(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    uint64_t r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
+    return r;
+}
+
+size_t list_op_bytes() { return sizeof(ListOp); }
+
+// Fill the ListOp of op d (qubit-space masks) for a sector with na / nb electrons
+// among N orbitals: its alpha list at entry a_off, its beta list right after it.
+// Returns the alpha and beta list lengths through na_l, nb_l.
+void list_op_from(const OpDesc &d, int N, int na, int nb, uint32_t a_off, void *dst, int *na_l, int *nb_l) {
+    SectOp s;
+    sect_op_from(d, N, &s);
+    *na_l = (int)choose(N - __builtin_popcount(s.ma), na - __builtin_popcount(s.fa));
+    *nb_l = (int)choose(N - __builtin_popcount(s.mb), nb - __builtin_popcount(s.fb));
+    ListOp o;
+    o.sm = s.sm; o.ma = s.ma; o.fa = s.fa; o.mb = s.mb; o.fb = s.fb;
+    o.a_off = a_off;
+    o.b_off = a_off + (uint32_t)*na_l;
+    o.a_n = (uint32_t)*na_l;
+    o.b_n = (uint32_t)*nb_l;
+    *(ListOp *)dst = o;
+}
+
+cudaError_t launch_build_lists(const void *ops, int n_ops, const uint32_t *sa, const uint32_t *sb,
+                               const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb,
+                               int Da, int Db, uint32_t *out, cudaStream_t st) {
+    if (n_ops <= 0) return cudaSuccess;
     SectTabs T = tabs(sa, sb, stra, strb, ra, rb, Da, Db);
-    const SectOp o = *(const SectOp *)op;
-    if (dtype == SV_C64) k_rotate_c<float><<<grid, kThreads, 0, st>>>((float2 *)psi, o, T);
-    else k_rotate_c<double><<<grid, kThreads, 0, st>>>((double2 *)psi, o, T);
+    k_build_lists<<<2 * n_ops, kThreads, 0, st>>>((const ListOp *)ops, T, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_c(void *psi, void *lam, int dtype, const void *op, const uint32_t *sa, const uint32_t *sb,
-                             const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb,
-                             int Da, int Db, int grid, double *partial, cudaStream_t st) {
-    SectTabs T = tabs(sa, sb, stra, strb, ra, rb, Da, Db);
-    const SectOp o = *(const SectOp *)op;
-    if (dtype == SV_C64) k_adjoint_c<float><<<grid, kThreads, 0, st>>>((float2 *)psi, (float2 *)lam, o, T, partial);
-    else k_adjoint_c<double><<<grid, kThreads, 0, st>>>((double2 *)psi, (double2 *)lam, o, T, partial);
+cudaError_t launch_rotate_l(void *psi, int dtype, const uint32_t *al, int na_l, const uint32_t *bl, int nb_l, int Da,
+                            double c, double s, int grid, cudaStream_t st) {
+    if (na_l <= 0 || nb_l <= 0) return cudaSuccess;
+    if (dtype == SV_C64)
+        k_rotate_l<float><<<grid, kThreads, 0, st>>>((float2 *)psi, al, na_l, bl, nb_l, Da, (float)c, (float)s);
+    else
+        k_rotate_l<double><<<grid, kThreads, 0, st>>>((double2 *)psi, al, na_l, bl, nb_l, Da, c, s);
+    return cudaGetLastError();
+}
+
+// partial: grid doubles (every block writes its entry, zero when it has no rows).
+cudaError_t launch_adjoint_l(void *psi, void *lam, int dtype, const uint32_t *al, int na_l, const uint32_t *bl,
+                             int nb_l, int Da, double c, double s, int grid, double *partial, cudaStream_t st) {
+    if (dtype == SV_C64)
+        k_adjoint_l<float><<<grid, kThreads, 0, st>>>((float2 *)psi, (float2 *)lam, al, na_l, bl, nb_l, Da, (float)c,
+                                                      (float)s, partial);
+    else
+        k_adjoint_l<double><<<grid, kThreads, 0, st>>>((double2 *)psi, (double2 *)lam, al, na_l, bl, nb_l, Da, c, s,
+                                                       partial);
     return cudaGetLastError();
 }
 
@@ -256,17 +350,9 @@ cudaError_t launch_rdm_rows(const void *C, int dtype, int n, const uint32_t *sa,
                             const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb, int Da,
                             int Db, int grid, double *partial, cudaStream_t st) {
     SectTabs T = tabs(sa, sb, stra, strb, ra, rb, Da, Db);
-    const size_t smem = sizeof(double) * 2 * rdm_rows_elements(n) * (1 + kThreads / 32);
-    cudaError_t e;
-    if (dtype == SV_C64) {
-        e = cudaFuncSetAttribute(k_rdm_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_rdm_rows<float><<<grid, kThreads, smem, st>>>((const float2 *)C, T, n / 2, partial);
-    } else {
-        e = cudaFuncSetAttribute(k_rdm_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_rdm_rows<double><<<grid, kThreads, smem, st>>>((const double2 *)C, T, n / 2, partial);
-    }
+    const size_t smem = sizeof(double) * 2 * rdm_rows_elements(n) * (1 + kThreads / 32);  // <= 40 KB (n <= 32)
+    if (dtype == SV_C64) k_rdm_rows<float><<<grid, kThreads, smem, st>>>((const float2 *)C, T, n / 2, partial);
+    else k_rdm_rows<double><<<grid, kThreads, smem, st>>>((const double2 *)C, T, n / 2, partial);
     return cudaGetLastError();
 }
 

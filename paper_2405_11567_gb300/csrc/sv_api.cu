@@ -41,14 +41,16 @@ cudaError_t launch_rdm_gather(const void *psi, int dtype, const uint32_t *sector
                               const void *elems, int n_el, int grid, double *partial, cudaStream_t st);
 // sector storage (k_sector.cu)
 void sect_op_from(const OpDesc &d, int N, void *dst);
-size_t sect_op_bytes();
 int sector_grid(int Db, int sm_count);
-cudaError_t launch_rotate_c(void *psi, int dtype, const void *op, const uint32_t *sa, const uint32_t *sb,
-                            const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb, int Da,
-                            int Db, int grid, cudaStream_t st);
-cudaError_t launch_adjoint_c(void *psi, void *lam, int dtype, const void *op, const uint32_t *sa, const uint32_t *sb,
-                             const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb,
-                             int Da, int Db, int grid, double *partial, cudaStream_t st);
+size_t list_op_bytes();
+void list_op_from(const OpDesc &d, int N, int na, int nb, uint32_t a_off, void *dst, int *na_l, int *nb_l);
+cudaError_t launch_build_lists(const void *ops, int n_ops, const uint32_t *sa, const uint32_t *sb,
+                               const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb,
+                               int Da, int Db, uint32_t *out, cudaStream_t st);
+cudaError_t launch_rotate_l(void *psi, int dtype, const uint32_t *al, int na_l, const uint32_t *bl, int nb_l, int Da,
+                            double c, double s, int grid, cudaStream_t st);
+cudaError_t launch_adjoint_l(void *psi, void *lam, int dtype, const uint32_t *al, int na_l, const uint32_t *bl,
+                             int nb_l, int Da, double c, double s, int grid, double *partial, cudaStream_t st);
 int rdm_rows_elements(int n);
 int rdm_rows_grid(int Db, int sm_count);
 cudaError_t launch_rdm_rows(const void *C, int dtype, int n, const uint32_t *sa, const uint32_t *sb,
@@ -471,16 +473,59 @@ static sv_status prepare_reference(sv_handle h) {
     return SV_OK;
 }
 
+// Sector storage: the alpha and beta pair lists of every op (k_build_lists), kept
+// on the device and rebuilt only when the ops' masks change.
+static sv_status ensure_op_lists(sv_handle h, const std::vector<OpDesc> &ops) {
+    SV_TRY(ensure_strings(h));
+    uint64_t key = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
+    mix(ops.size());
+    mix((uint64_t)h->na << 32 | (uint32_t)h->nb);
+    for (const OpDesc &d : ops) mix((uint64_t)d.m << 32 | d.from), mix(d.sm);
+    if (h->list_buf && key == h->list_key && h->list_info.size() == 4 * ops.size()) return SV_OK;
+    const int N = h->n / 2;
+    const size_t ob = list_op_bytes();
+    std::vector<uint8_t> host((ops.size() ? ops.size() : 1) * ob);
+    std::vector<int> info(4 * ops.size());
+    uint32_t off = 0;
+    for (size_t k = 0; k < ops.size(); ++k) {
+        int na_l = 0, nb_l = 0;  // the op's beta list follows its alpha list
+        list_op_from(ops[k], N, h->na, h->nb, off, host.data() + k * ob, &na_l, &nb_l);
+        info[4 * k] = (int)off;
+        info[4 * k + 1] = na_l;
+        info[4 * k + 2] = (int)off + na_l;
+        info[4 * k + 3] = nb_l;
+        off += (uint32_t)(na_l + nb_l);
+    }
+    const size_t lb = ((size_t)off * 4 + 16) / 16 * 16, ob_all = std::max<size_t>(host.size(), 16);
+    if (h->list_bytes < lb + ob_all) {
+        dev_free(h, h->list_buf, h->list_bytes);
+        h->list_buf = nullptr;
+        h->list_bytes = 0;
+        SV_TRY(dev_alloc(h, &h->list_buf, lb + ob_all, "operator pair lists"));
+        h->list_bytes = lb + ob_all;
+    }
+    uint8_t *dops = (uint8_t *)h->list_buf + lb;  // op records after the lists
+    SV_CUDA(h, cudaMemcpyAsync(dops, host.data(), ops.size() * ob, cudaMemcpyHostToDevice, h->stream));
+    SV_CUDA(h, launch_build_lists(dops, (int)ops.size(), h->str_sa, h->str_sb, h->str_a, h->str_b, h->rank_a,
+                                  h->rank_b, h->Da, h->Db, (uint32_t *)h->list_buf, h->stream));
+    h->launches++;
+    SV_CUDA(h, cudaStreamSynchronize(h->stream));  // the host staging vector goes out of scope
+    h->list_key = key;
+    h->list_info = info;
+    return SV_OK;
+}
+
 static sv_status forward(sv_handle h, const std::vector<OpDesc> &ops, bool checkpoints) {
     const int64_t C = h->ckpt_interval;
-    std::vector<uint8_t> so(sect_op_bytes());
-    if (h->storage == 1 && !ops.empty()) SV_TRY(ensure_strings(h));
+    if (h->storage == 1 && !ops.empty()) SV_TRY(ensure_op_lists(h, ops));
+    const uint32_t *L = (const uint32_t *)h->list_buf;
+    const int G = sector_grid(h->Db, h->sm_count);
     for (size_t k = 0; k < ops.size(); ++k) {
         if (h->storage == 1) {
-            sect_op_from(ops[k], h->n / 2, so.data());
-            SV_CUDA(h, launch_rotate_c(h->psi, h->dtype, so.data(), h->str_sa, h->str_sb, h->str_a, h->str_b,
-                                       h->rank_a, h->rank_b, h->Da, h->Db, sector_grid(h->Db, h->sm_count),
-                                       h->stream));
+            const int *li = &h->list_info[4 * k];
+            SV_CUDA(h, launch_rotate_l(h->psi, h->dtype, L + li[0], li[1], L + li[2], li[3], h->Da, ops[k].c,
+                                       ops[k].s, G, h->stream));
         } else {
             SV_CUDA(h, launch_rotate(h->psi, h->dtype, h->n, ops[k], h->sm_count, h->stream));
         }
@@ -732,6 +777,7 @@ sv_status sv_destroy(sv_handle h) {
         if (p) cudaFree(p);
     dev_free(h, h->Cbuf, h->Cbuf_bytes);
     dev_free(h, h->Lbuf, h->Lbuf_bytes);
+    dev_free(h, h->list_buf, h->list_bytes);
     dev_free(h, h->partials, h->partials_cap * sizeof(double));
     dev_free(h, h->dout, h->dout_cap * sizeof(double));
     if (h->hpinned) cudaFreeHost(h->hpinned);
@@ -1026,13 +1072,12 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     SV_TRY(mark(h, 4));
     // reverse sweep
     const int64_t C = h->ckpt_interval;
-    std::vector<uint8_t> so(sect_op_bytes());
     for (size_t kk = L; kk-- > 0;) {
         if (sect) {
-            sect_op_from(d[kk], h->n / 2, so.data());
-            SV_CUDA(h, launch_adjoint_c(h->psi, h->lam, h->dtype, so.data(), h->str_sa, h->str_sb, h->str_a, h->str_b,
-                                        h->rank_a, h->rank_b, h->Da, h->Db, G, h->partials + kk * (size_t)G,
-                                        h->stream));
+            const uint32_t *LB = (const uint32_t *)h->list_buf;
+            const int *li = &h->list_info[4 * kk];
+            SV_CUDA(h, launch_adjoint_l(h->psi, h->lam, h->dtype, LB + li[0], li[1], LB + li[2], li[3], h->Da,
+                                        d[kk].c, d[kk].s, G, h->partials + kk * (size_t)G, h->stream));
         } else {
             SV_CUDA(h, launch_adjoint(h->psi, h->lam, h->dtype, h->n, d[kk], G, h->partials + kk * (size_t)G,
                                       h->stream));

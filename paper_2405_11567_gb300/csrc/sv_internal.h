@@ -186,6 +186,11 @@ struct sv_ctx {
     size_t Cbuf_bytes = 0;
     void *Lbuf = nullptr;      // compact sigma [Db][Da] (operator screening)
     size_t Lbuf_bytes = 0;
+    // sector storage: per-op alpha / beta pair lists (k_build_lists), then the op records
+    void *list_buf = nullptr;
+    size_t list_bytes = 0;
+    uint64_t list_key = 0;
+    std::vector<int> list_info;  // per op: alpha offset, alpha length, beta offset, beta length
     // reduction scratch
     double *partials = nullptr;
     size_t partials_cap = 0;   // doubles
