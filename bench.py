@@ -5,8 +5,13 @@ Jordan-Wigner HF reference, apply the 200-operator ADAPT-style ansatz, evaluate
 E = <psi|H|psi> and lambda = (H - c) psi, run the adjoint sweep for dE/dtheta,
 restore psi(theta) and take the spin-resolved 1-RDM.  Workload: 30 qubits
 (15 spatial orbitals, 10 electrons), seeded synthetic integrals shaped like the
-paper's molecules (config 5 of the workload list).  The complex64-state path
-(float64 reductions) is the headline; the complex128 path is timed beside it.
+paper's molecules (config 5 of the workload list).
+
+Headline: the complex64 state (float64 reductions) in sector storage -- only the
+C(15,5)^2 = 9,018,009 amplitudes of the (5, 5) sector, 72 MB, which L2 holds, so
+L2 is flushed (a 256 MB write) before every timed step, outside its events.  The
+same step is timed beside it in complex128 and in dense 2^30 storage (8 GiB,
+streamed from HBM), and the batched small-instance launch (config 4).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -32,6 +37,10 @@ if ROOT not in sys.path:
 METRIC = "energy+adjoint-grad evals/s at 30 qubits, FP32-state vs FP64; % of HBM peak"
 UNIT = "evals/s"
 CONFIG_ID = 5
+# DRAM bytes (read + write) of one expectation's two kernels (k_sigma_ab 215.7 MB,
+# k_sigma_same 700.8 MB), from the ncu capture summarised in
+# profiles/sigma_split_n30_sector_c64.md; set to None once either kernel changes.
+SIGMA_TRAFFIC_BYTES = 916.5e6
 
 
 def _env_int(k, d):
@@ -224,10 +233,28 @@ def workload_config(p):
             "n_qubits": p["n_qubits"], "n_electrons": p["n_elec"],
             "n_ops": int(len(p["ops"])), "seed": p["seed"],
             "step": "prepare_hf + energy_grad (forward, sigma, adjoint) + rdm1",
-            "l2": "inputs larger than L2 (state vector 8 GiB complex64 / 16 GiB complex128)"}
+            "storage": "sector (9,018,009 amplitudes; dense 2^30 timed beside it)",
+            "l2": "flushed before every timed step (256 MB write outside the step's events)"}
 
 
 # ---------------------------------------------------------------- our arm
+
+def sigma_terms(p):
+    """Hamiltonian connections applied by one sigma = (H - c) psi on the (na, nb) sector:
+    every determinant has the same count (diagonal, singles and doubles of each spin,
+    alpha-beta doubles)."""
+    from math import comb
+    N, na, nb = p["n_orb"], p["na"], p["nb"]
+    D = comb(N, na) * comb(N, nb)
+    sa, sb = na * (N - na), nb * (N - nb)
+    per = 1 + sa + sb + comb(na, 2) * comb(N - na, 2) + comb(nb, 2) * comb(N - nb, 2) + sa * sb
+    return D, per
+
+
+def fp32_peak_tflops(sm_mhz):
+    """Plain (non-tensor) FP32 FMA peak: 152 SMs x 128 lanes x 2 flops x the SM clock."""
+    return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
 
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -244,8 +271,9 @@ def run_ours(args, rank, world, local_rank):
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
     stream = torch.cuda.Stream()
     peak, peak_kind = measured_peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # 256 MB > 126 MB of L2
 
-    def timed(dtype, sector=False):
+    def timed(dtype, sector):
         st = sv.StateVector(n, dtype, stream, sector=(p["na"], p["nb"]) if sector else None)
         st.set_option(sv.SV_OPT_PROFILE, 1)
         outs = {}
@@ -253,7 +281,7 @@ def run_ours(args, rank, world, local_rank):
         def step():
             st.prepare_hf(p["occ"])
             E, g = st.energy_grad(ham, p["ops"], p["theta"])
-            rdm = st.rdm1()
+            rdm = st.rdm1()  # host-synchronising reads: energy, gradient, 1-RDM
             outs["E"], outs["g"], outs["rdm"] = E, g, rdm
             return st.phase_times()
 
@@ -265,19 +293,24 @@ def run_ours(args, rank, world, local_rank):
         clocks = ClockSampler(local_rank)
         clocks.start()
         launches0 = st.launches
-        phases = []
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        phases, evs, t_host = [], [], 0.0
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ev0.record(stream)
         for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()  # L2 flush between timed steps, outside the timed region
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t0 = time.perf_counter()
             phases.append(step())
-        ev1.record(stream)
+            t_host += time.perf_counter() - t0
+            e1.record(stream)
+            evs.append((e0, e1))
         torch.cuda.synchronize()
-        t_host = time.perf_counter() - t0
-        ms = ev0.elapsed_time(ev1)
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
         launches = st.launches - launches0
         clk = clocks.stop()
+        if dist:
+            dist.barrier()
         ms, t_host = reduce_max([ms, t_host])
         avg = {k: statistics.mean(ph[k] for ph in phases) for k in phases[0]}
         st.close()
@@ -305,79 +338,83 @@ def run_ours(args, rank, world, local_rank):
         b.close()
         return out
 
-    r64 = timed("c64")
-    r128 = None if args.no_c128 else timed("c128")
-    rs64 = None if args.no_sector else timed("c64", sector=True)
-    rs128 = None if (args.no_sector or args.no_c128) else timed("c128", sector=True)
+    head = timed("c64", sector=True)
+    head128 = None if args.no_c128 else timed("c128", sector=True)
+    d64 = None if args.no_dense else timed("c64", sector=False)
+    d128 = None if (args.no_dense or args.no_c128) else timed("c128", sector=False)
     rbatch = None if (args.qubits or args.no_batch) else timed_batch()
     if rank != 0:
         return 0
     K = args.steps
-    value = throughput(world, K, r64["ms"])
-    e2e = throughput(world, K, 1000.0 * r64["t_host"])
-    # roofline of the dominant kernel (by phase time), algorithmic bytes per launch / mean launch time
-    amp = 8
-    rot_bytes = touched_bytes(p["ops"], n, amp)
+    value = throughput(world, K, head["ms"])
+    e2e = throughput(world, K, 1000.0 * head["t_host"])
+    # roofline of the dominant kernels: the expectation's two kernels (k_sigma_ab, k_sigma_same)
+    D, per = sigma_terms(p)
+    flops = 4.0 * D * per  # complex amplitude x real matrix element = 2 FMA per connection
+    t_sig = head["phases"]["expectation"] / 1000.0
+    sm_mhz = head["clocks"].get("sm_mhz")
+    fpeak = fp32_peak_tflops(sm_mhz)
+    ach = flops / t_sig / 1e12
+    sb = sector_touched_bytes(p["ops"], p["n_orb"], p["na"], p["nb"], 8)
+    t_rot = head["phases"]["forward"] / L / 1000.0
+    t_adj = head["phases"]["reverse"] / L / 1000.0
+    roof = {"bound": "alu", "kernel": "expectation: k_sigma_ab + k_sigma_same (two launches)",
+            "achieved": ach, "peak": fpeak, "unit": "TFLOP/s", "frac": ach / fpeak,
+            "traffic": SIGMA_TRAFFIC_BYTES,
+            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz (no FP32 peak in MEASURED_PEAKS.json)"
+                         % (sm_mhz or 2070.0),
+            "algorithmic": "%d determinants x %d connections x 4 flops = %.1f GFLOP per expectation"
+                           % (D, per, flops / 1e9)}
     kernels = {
-        "adjoint_step": dict(phase="reverse", launches=L, bytes=2.0 * rot_bytes.sum(),
-                             desc="fused adjoint step (k_adjoint): psi and lambda pairs, read + write"),
-        "rotation": dict(phase="forward", launches=L, bytes=rot_bytes.sum(),
-                         desc="excitation rotation (k_rotate): touched pairs, read + write"),
+        "sigma": {"achieved_tflops": ach, "frac_fp32": ach / fpeak, "ms": t_sig * 1e3, "connections": D * per},
+        "rotation_l": {"algorithmic_gbs": sb.sum() / L / t_rot / 1e9, "mean_launch_ms": t_rot * 1e3,
+                       "note": "72 MB state held in L2: GB/s here are L2, not HBM"},
+        "adjoint_l": {"algorithmic_gbs": 2.0 * sb.sum() / L / t_adj / 1e9, "mean_launch_ms": t_adj * 1e3},
     }
-    rows = {}
-    for name, kd in kernels.items():
-        t_launch = r64["phases"][kd["phase"]] / kd["launches"] / 1000.0
-        per_launch = kd["bytes"] / kd["launches"]
-        ach = per_launch / t_launch / 1e9
-        rows[name] = {"achieved_gbs": ach, "frac": ach / peak, "mean_launch_ms": t_launch * 1e3,
-                      "bytes_per_launch": per_launch, "launches_per_step": kd["launches"]}
-    dom = max(kernels, key=lambda k: r64["phases"][kernels[k]["phase"]])
-    roof = {"bound": "hbm", "kernel": dom, "achieved": rows[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
-            "frac": rows[dom]["frac"], "traffic": None, "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
-            if peak_kind == "measured" else "fallback 6.8 TB/s"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
-        "ms_per_step": r64["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": head["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "precision": "complex64 state, float64 reductions", "data": "synthetic",
         "config": workload_config(p),
         "roofline": roof,
-        "kernels": rows,
-        "phases_ms": r64["phases"],
-        "clocks": r64["clocks"],
+        "kernels": kernels,
+        "phases_ms": head["phases"],
+        "clocks": head["clocks"],
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(L * (20 + 8) + len(p["occ"]) * 4),
                 "d2h_bytes_per_step": int((1 + L) * 8 + 2 * 2 * p["n_orb"] ** 2 * 8)},
-        "gpu_launches": int(r64["launches"]),
+        "gpu_launches": int(head["launches"]),
     }
-    if r128 is not None:
-        v128 = throughput(world, K, r128["ms"])
-        line["fp64_state"] = {"value": v128, "ms_per_step": r128["ms"] / K, "phases_ms": r128["phases"],
-                              "clocks": r128["clocks"]}
+    if head128 is not None:
+        v128 = throughput(world, K, head128["ms"])
+        line["fp64_state"] = {"value": v128, "ms_per_step": head128["ms"] / K, "phases_ms": head128["phases"],
+                              "clocks": head128["clocks"]}
         line["speedup_fp32_over_fp64"] = value / v128
         line["fp32_vs_fp64"] = {
-            "abs_dE": abs(r64["out"]["E"] - r128["out"]["E"]),
-            "max_abs_dg": float(np.max(np.abs(r64["out"]["g"] - r128["out"]["g"]))),
-            "max_abs_drdm": float(np.max(np.abs(r64["out"]["rdm"] - r128["out"]["rdm"]))),
-            "E_fp64": r128["out"]["E"]}
-    if rs64 is not None:
-        # sector storage: the same step on the compact C(N,na) C(N,nb) matrix (L2-resident at 30 qubits)
-        sb = sector_touched_bytes(p["ops"], p["n_orb"], p["na"], p["nb"], 8)
-        t_rot = rs64["phases"]["forward"] / L / 1000.0
-        t_adj = rs64["phases"]["reverse"] / L / 1000.0
-        sect = {"storage": "sector: C(15,5)^2 = 9,018,009 amplitudes (72 MB complex64)",
-                "value": throughput(world, K, rs64["ms"]), "unit": UNIT, "ms_per_step": rs64["ms"] / K,
-                "phases_ms": rs64["phases"], "clocks": rs64["clocks"], "gpu_launches": int(rs64["launches"]),
-                "kernels": {"rotation_c": {"algorithmic_gbs": sb.sum() / L / t_rot / 1e9,
-                                           "mean_launch_ms": t_rot * 1e3},
-                            "adjoint_c": {"algorithmic_gbs": 2.0 * sb.sum() / L / t_adj / 1e9,
-                                          "mean_launch_ms": t_adj * 1e3}},
-                "abs_dE_vs_dense_c64": abs(rs64["out"]["E"] - r64["out"]["E"]),
-                "max_abs_dg_vs_dense_c64": float(np.max(np.abs(rs64["out"]["g"] - r64["out"]["g"])))}
-        if rs128 is not None:
-            sect["fp64_state"] = {"value": throughput(world, K, rs128["ms"]), "ms_per_step": rs128["ms"] / K,
-                                  "phases_ms": rs128["phases"]}
-            if r128 is not None:
-                sect["abs_dE_vs_dense_c128"] = abs(rs128["out"]["E"] - r128["out"]["E"])
-        line["sector_storage"] = sect
+            "abs_dE": abs(head["out"]["E"] - head128["out"]["E"]),
+            "max_abs_dg": float(np.max(np.abs(head["out"]["g"] - head128["out"]["g"]))),
+            "max_abs_drdm": float(np.max(np.abs(head["out"]["rdm"] - head128["out"]["rdm"]))),
+            "E_fp64": head128["out"]["E"]}
+    if d64 is not None:
+        # dense 2^30 storage: the HBM-streaming kernels and their fraction of the measured copy bandwidth
+        rot_bytes = touched_bytes(p["ops"], n, 8)
+        rows = {}
+        for name, phase, mult in (("adjoint_step", "reverse", 2.0), ("rotation", "forward", 1.0)):
+            t_launch = d64["phases"][phase] / L / 1000.0
+            per_launch = mult * rot_bytes.sum() / L
+            a = per_launch / t_launch / 1e9
+            rows[name] = {"achieved_gbs": a, "frac": a / peak, "mean_launch_ms": t_launch * 1e3,
+                          "bytes_per_launch": per_launch}
+        dense = {"storage": "dense 2^30 amplitudes (8 GiB complex64)", "value": throughput(world, K, d64["ms"]),
+                 "ms_per_step": d64["ms"] / K, "phases_ms": d64["phases"], "kernels": rows,
+                 "peak_gbs": peak, "peak_kind": peak_kind, "gpu_launches": int(d64["launches"]),
+                 "abs_dE_vs_sector_c64": abs(d64["out"]["E"] - head["out"]["E"]),
+                 "max_abs_dg_vs_sector_c64": float(np.max(np.abs(d64["out"]["g"] - head["out"]["g"])))}
+        if d128 is not None:
+            dense["fp64_state"] = {"value": throughput(world, K, d128["ms"]), "ms_per_step": d128["ms"] / K,
+                                   "phases_ms": d128["phases"]}
+            if head128 is not None:
+                dense["abs_dE_vs_sector_c128"] = abs(d128["out"]["E"] - head128["out"]["E"])
+        line["dense_storage"] = dense
     if rbatch is not None:
         line["batch_config4"] = rbatch
     if world == 1 and not args.no_cpu_baseline and not args.qubits:
@@ -439,7 +476,7 @@ def main():
     ap.add_argument("--no-c128", action="store_true", help="skip the complex128 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) timing")
-    ap.add_argument("--no-sector", action="store_true", help="skip the sector-storage timing")
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense-storage timing")
     ap.add_argument("--op-profile", action="store_true",
                     help="per-operator rotation bandwidth by lowest address bit (diagnostic, not the bench line)")
     ap.add_argument("--qubits", type=int, default=0,

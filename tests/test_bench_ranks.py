@@ -53,3 +53,19 @@ def test_single_process_reduce_is_identity():
     import bench
     assert bench.reduce_max([3.0, 4.0]) == [3.0, 4.0]
     assert bench.throughput(1, 4, 2000.0) == 2.0
+
+
+def test_sigma_connection_count_brute_force():
+    """bench.sigma_terms (the algorithmic FLOP count of one expectation) against a brute-force
+    count of the sector determinants within two excitations of each determinant."""
+    sys.path.insert(0, ROOT)
+    import itertools
+    import bench
+    for N, na, nb in [(5, 2, 1), (4, 2, 2), (6, 3, 2), (3, 0, 2)]:
+        sa = [sum(1 << (2 * q) for q in c) for c in itertools.combinations(range(N), na)]
+        sb = [sum(1 << (2 * q + 1) for q in c) for c in itertools.combinations(range(N), nb)]
+        dets = [a | b for a in sa for b in sb]
+        counts = {sum(1 for y in dets if bin(x ^ y).count("1") <= 4) for x in dets}
+        D, per = bench.sigma_terms({"n_orb": N, "na": na, "nb": nb})
+        assert D == len(dets) and counts == {per}
+    assert bench.sigma_terms({"n_orb": 15, "na": 5, "nb": 5}) == (9018009, 3501)
