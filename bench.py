@@ -7,11 +7,12 @@ restore psi(theta) and take the spin-resolved 1-RDM.  Workload: 30 qubits
 (15 spatial orbitals, 10 electrons), seeded synthetic integrals shaped like the
 paper's molecules (config 5 of the workload list).
 
-Headline: the complex64 state (float64 reductions) in sector storage -- only the
-C(15,5)^2 = 9,018,009 amplitudes of the (5, 5) sector, 72 MB, which L2 holds, so
-L2 is flushed (a 256 MB write) before every timed step, outside its events.  The
-same step is timed beside it in complex128 and in dense 2^30 storage (8 GiB,
-streamed from HBM), and the batched small-instance launch (config 4).
+Headline: the dense 2^30-amplitude complex64 state (8 GiB per vector, float64
+reductions), the state-vector method the metric is defined on; complex128 beside
+it.  Also timed: the same step in sector storage (only the C(15,5)^2 = 9,018,009
+amplitudes of the (5, 5) sector, 72 MB, a separate row with its own roofline) and
+the batched small-instance launch (config 4).  L2 is flushed (a 256 MB write)
+before every timed step, outside its events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -37,10 +38,13 @@ if ROOT not in sys.path:
 METRIC = "energy+adjoint-grad evals/s at 30 qubits, FP32-state vs FP64; % of HBM peak"
 UNIT = "evals/s"
 CONFIG_ID = 5
-# DRAM bytes (read + write) of one expectation's two kernels (k_sigma_ab 215.7 MB,
-# k_sigma_same 700.8 MB), from the ncu capture summarised in
+# DRAM bytes (read + write) of one expectation's two kernels on sector storage
+# (k_sigma_ab 215.7 MB, k_sigma_same 700.8 MB), from the ncu capture summarised in
 # profiles/sigma_split_n30_sector_c64.md; set to None once either kernel changes.
 SIGMA_TRAFFIC_BYTES = 916.5e6
+# DRAM bytes per k_adjoint launch of the dense headline (scaled to 30 qubits); None
+# until captured for the current kernel.
+ADJOINT_TRAFFIC_BYTES = None
 
 
 def _env_int(k, d):
@@ -233,7 +237,7 @@ def workload_config(p):
             "n_qubits": p["n_qubits"], "n_electrons": p["n_elec"],
             "n_ops": int(len(p["ops"])), "seed": p["seed"],
             "step": "prepare_hf + energy_grad (forward, sigma, adjoint) + rdm1",
-            "storage": "sector (9,018,009 amplitudes; dense 2^30 timed beside it)",
+            "storage": "dense 2^30 amplitudes (8 GiB per vector, complex64); sector storage timed beside it",
             "l2": "flushed before every timed step (256 MB write outside the step's events)"}
 
 
@@ -338,46 +342,42 @@ def run_ours(args, rank, world, local_rank):
         b.close()
         return out
 
-    head = timed("c64", sector=True)
-    head128 = None if args.no_c128 else timed("c128", sector=True)
-    d64 = None if args.no_dense else timed("c64", sector=False)
-    d128 = None if (args.no_dense or args.no_c128) else timed("c128", sector=False)
+    head = timed("c64", sector=False)
+    head128 = None if args.no_c128 else timed("c128", sector=False)
+    s64 = None if args.no_sector else timed("c64", sector=True)
+    s128 = None if (args.no_sector or args.no_c128) else timed("c128", sector=True)
     rbatch = None if (args.qubits or args.no_batch) else timed_batch()
     if rank != 0:
         return 0
     K = args.steps
     value = throughput(world, K, head["ms"])
     e2e = throughput(world, K, 1000.0 * head["t_host"])
-    # roofline of the dominant kernels: the expectation's two kernels (k_sigma_ab, k_sigma_same)
-    D, per = sigma_terms(p)
-    flops = 4.0 * D * per  # complex amplitude x real matrix element = 2 FMA per connection
-    t_sig = head["phases"]["expectation"] / 1000.0
-    sm_mhz = head["clocks"].get("sm_mhz")
-    fpeak = fp32_peak_tflops(sm_mhz)
-    ach = flops / t_sig / 1e12
-    sb = sector_touched_bytes(p["ops"], p["n_orb"], p["na"], p["nb"], 8)
-    t_rot = head["phases"]["forward"] / L / 1000.0
-    t_adj = head["phases"]["reverse"] / L / 1000.0
-    roof = {"bound": "alu", "kernel": "expectation: k_sigma_ab + k_sigma_same (two launches)",
-            "achieved": ach, "peak": fpeak, "unit": "TFLOP/s", "frac": ach / fpeak,
-            "traffic": SIGMA_TRAFFIC_BYTES,
-            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz (no FP32 peak in MEASURED_PEAKS.json)"
-                         % (sm_mhz or 2070.0),
-            "algorithmic": "%d determinants x %d connections x 4 flops = %.1f GFLOP per expectation"
-                           % (D, per, flops / 1e9)}
+    # roofline of the dominant kernel (by phase time): algorithmic bytes per launch / mean launch time
+    rot_bytes = touched_bytes(p["ops"], n, 8)
     kernels = {
-        "sigma": {"achieved_tflops": ach, "frac_fp32": ach / fpeak, "ms": t_sig * 1e3, "connections": D * per},
-        "rotation_l": {"algorithmic_gbs": sb.sum() / L / t_rot / 1e9, "mean_launch_ms": t_rot * 1e3,
-                       "note": "72 MB state held in L2: GB/s here are L2, not HBM"},
-        "adjoint_l": {"algorithmic_gbs": 2.0 * sb.sum() / L / t_adj / 1e9, "mean_launch_ms": t_adj * 1e3},
+        "adjoint_step": dict(phase="reverse", mult=2.0,
+                             desc="fused adjoint step (k_adjoint): psi and lambda pairs, read + write"),
+        "rotation": dict(phase="forward", mult=1.0, desc="excitation rotation (k_rotate): touched pairs, read + write"),
     }
+    rows = {}
+    for name, kd in kernels.items():
+        t_launch = head["phases"][kd["phase"]] / L / 1000.0
+        per_launch = kd["mult"] * rot_bytes.sum() / L
+        a = per_launch / t_launch / 1e9
+        rows[name] = {"achieved_gbs": a, "frac": a / peak, "mean_launch_ms": t_launch * 1e3,
+                      "bytes_per_launch": per_launch, "launches_per_step": L, "desc": kd["desc"]}
+    dom = max(kernels, key=lambda k: head["phases"][kernels[k]["phase"]])
+    roof = {"bound": "hbm", "kernel": dom, "achieved": rows[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": rows[dom]["frac"], "traffic": ADJOINT_TRAFFIC_BYTES if dom == "adjoint_step" else None,
+            "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+            else "fallback 6.8 TB/s"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": head["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "precision": "complex64 state, float64 reductions", "data": "synthetic",
         "config": workload_config(p),
         "roofline": roof,
-        "kernels": kernels,
+        "kernels": rows,
         "phases_ms": head["phases"],
         "clocks": head["clocks"],
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(L * (20 + 8) + len(p["occ"]) * 4),
@@ -394,27 +394,40 @@ def run_ours(args, rank, world, local_rank):
             "max_abs_dg": float(np.max(np.abs(head["out"]["g"] - head128["out"]["g"]))),
             "max_abs_drdm": float(np.max(np.abs(head["out"]["rdm"] - head128["out"]["rdm"]))),
             "E_fp64": head128["out"]["E"]}
-    if d64 is not None:
-        # dense 2^30 storage: the HBM-streaming kernels and their fraction of the measured copy bandwidth
-        rot_bytes = touched_bytes(p["ops"], n, 8)
-        rows = {}
-        for name, phase, mult in (("adjoint_step", "reverse", 2.0), ("rotation", "forward", 1.0)):
-            t_launch = d64["phases"][phase] / L / 1000.0
-            per_launch = mult * rot_bytes.sum() / L
-            a = per_launch / t_launch / 1e9
-            rows[name] = {"achieved_gbs": a, "frac": a / peak, "mean_launch_ms": t_launch * 1e3,
-                          "bytes_per_launch": per_launch}
-        dense = {"storage": "dense 2^30 amplitudes (8 GiB complex64)", "value": throughput(world, K, d64["ms"]),
-                 "ms_per_step": d64["ms"] / K, "phases_ms": d64["phases"], "kernels": rows,
-                 "peak_gbs": peak, "peak_kind": peak_kind, "gpu_launches": int(d64["launches"]),
-                 "abs_dE_vs_sector_c64": abs(d64["out"]["E"] - head["out"]["E"]),
-                 "max_abs_dg_vs_sector_c64": float(np.max(np.abs(d64["out"]["g"] - head["out"]["g"])))}
-        if d128 is not None:
-            dense["fp64_state"] = {"value": throughput(world, K, d128["ms"]), "ms_per_step": d128["ms"] / K,
-                                   "phases_ms": d128["phases"]}
+    if s64 is not None:
+        # sector storage: a separate row (the state is 0.84% of 2^30 amplitudes and L2-resident), with the
+        # expectation's two kernels against the plain FP32 FMA peak
+        D, per = sigma_terms(p)
+        flops = 4.0 * D * per  # complex amplitude x real matrix element = 2 FMA per connection
+        t_sig = s64["phases"]["expectation"] / 1000.0
+        sm_mhz = s64["clocks"].get("sm_mhz")
+        fpeak = fp32_peak_tflops(sm_mhz)
+        ach = flops / t_sig / 1e12
+        sb = sector_touched_bytes(p["ops"], p["n_orb"], p["na"], p["nb"], 8)
+        t_rot = s64["phases"]["forward"] / L / 1000.0
+        t_adj = s64["phases"]["reverse"] / L / 1000.0
+        sect = {"storage": "sector: C(15,5)^2 = 9,018,009 amplitudes (72 MB complex64), L2-resident",
+                "value": throughput(world, K, s64["ms"]), "unit": UNIT, "ms_per_step": s64["ms"] / K,
+                "phases_ms": s64["phases"], "clocks": s64["clocks"], "gpu_launches": int(s64["launches"]),
+                "roofline": {"bound": "alu", "kernel": "expectation: k_sigma_ab + k_sigma_same (two launches)",
+                             "achieved": ach, "peak": fpeak, "unit": "TFLOP/s", "frac": ach / fpeak,
+                             "traffic": SIGMA_TRAFFIC_BYTES,
+                             "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz"
+                                          % (sm_mhz or 2070.0),
+                             "algorithmic": "%d determinants x %d connections x 4 flops = %.1f GFLOP"
+                                            % (D, per, flops / 1e9)},
+                "kernels": {"rotation_l": {"algorithmic_gbs": sb.sum() / L / t_rot / 1e9,
+                                           "mean_launch_ms": t_rot * 1e3},
+                            "adjoint_l": {"algorithmic_gbs": 2.0 * sb.sum() / L / t_adj / 1e9,
+                                          "mean_launch_ms": t_adj * 1e3}},
+                "abs_dE_vs_dense_c64": abs(s64["out"]["E"] - head["out"]["E"]),
+                "max_abs_dg_vs_dense_c64": float(np.max(np.abs(s64["out"]["g"] - head["out"]["g"])))}
+        if s128 is not None:
+            sect["fp64_state"] = {"value": throughput(world, K, s128["ms"]), "ms_per_step": s128["ms"] / K,
+                                  "phases_ms": s128["phases"]}
             if head128 is not None:
-                dense["abs_dE_vs_sector_c128"] = abs(d128["out"]["E"] - head128["out"]["E"])
-        line["dense_storage"] = dense
+                sect["abs_dE_vs_dense_c128"] = abs(s128["out"]["E"] - head128["out"]["E"])
+        line["sector_storage"] = sect
     if rbatch is not None:
         line["batch_config4"] = rbatch
     if world == 1 and not args.no_cpu_baseline and not args.qubits:
@@ -476,7 +489,7 @@ def main():
     ap.add_argument("--no-c128", action="store_true", help="skip the complex128 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) timing")
-    ap.add_argument("--no-dense", action="store_true", help="skip the dense-storage timing")
+    ap.add_argument("--no-sector", action="store_true", help="skip the sector-storage timing")
     ap.add_argument("--op-profile", action="store_true",
                     help="per-operator rotation bandwidth by lowest address bit (diagnostic, not the bench line)")
     ap.add_argument("--qubits", type=int, default=0,
