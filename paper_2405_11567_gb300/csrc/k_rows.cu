@@ -267,19 +267,22 @@ __device__ __forceinline__ int pair_index(int p, int q, int N) { return p * N - 
 // [min, max), so an alpha single p -> q has sign (-1)^(popc(PP & {p,q}) + [p<q]),
 // and an alpha double p1<p2 -> q1<q2 (taken as -(a+_q1 a_p2)(a+_q2 a_p1)) has
 // (-1)^popc(PP & {p1,p2,q1,q2}) times an orbital-order sign that W2 carries.
-template <typename R>
-__global__ void __launch_bounds__(kRowThreads, 2) k_sigma_same(RowArgs<R> A) {
+constexpr int kSameThreads = 512;
+
+template <typename R, bool RA_SMEM>
+__global__ void __launch_bounds__(kSameThreads, 1) k_sigma_same(RowArgs<R> A) {
     extern __shared__ __align__(16) unsigned char same_dyn[];
     __shared__ BetaDouble<R> bd[kMaxBD];
     __shared__ R JB[kMaxOrb * kMaxOrb];
     __shared__ uint8_t opair[kMaxPairs][2], epair[kMaxPairs][2];
     __shared__ int n_op, n_ep;
-    __shared__ double red[2 * kThreads / 32];
+    __shared__ double red[2 * kSameThreads / 32];
     const SigmaTables<R> &T = A.T;
     const int Ib = blockIdx.x, N = T.N, Da = T.Da, NP = N * (N - 1) / 2;
     cplx<R> *row = reinterpret_cast<cplx<R> *>(same_dyn);  // [Da]
     R *W2S = reinterpret_cast<R *>(row + Da);               // [NP][NP]
     R *DtS = W2S + NP * NP;                                 // [N^3]
+    uint16_t *raS = reinterpret_cast<uint16_t *>(DtS + N * N * N);  // [2^N] alpha ranks
     const uint32_t b = T.strb[Ib], xb = T.sb[Ib], eb = ~b & T.maskN;
     if (threadIdx.x == 0) {
         int no = 0, ne = 0;
@@ -308,6 +311,9 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_sigma_same(RowArgs<R> A) {
     for (int i = threadIdx.x; i < Da; i += blockDim.x) row[i] = grow[i];
     for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) W2S[i] = A.W2[i];
     for (int i = threadIdx.x; i < N * N * N; i += blockDim.x) DtS[i] = T.Dt[i];
+    if (RA_SMEM)
+        for (int i = threadIdx.x; i < (1 << N); i += blockDim.x) raS[i] = T.ra[i];
+    const uint16_t *rk = RA_SMEM ? raS : T.ra;
     __syncthreads();
     const int nbd = n_op * n_ep;
     for (int d = threadIdx.x; d < nbd; d += blockDim.x) {
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_sigma_same(RowArgs<R> A) {
                 for (uint32_t o2 = a; o2; o2 &= o2 - 1u) v += dt[__ffs(o2) - 1];
                 const uint32_t m = (1u << p) | (1u << q);
                 if ((uint32_t)par(PP & m) ^ (uint32_t)(p < q)) v = -v;
-                fma_c<R>(acc, v, row[T.ra[a ^ m]]);
+                fma_c<R>(acc, v, row[rk[a ^ m]]);
             }
         }
         // alpha-alpha doubles: W2[(p1,p2)][(q1,q2)] holds the value and the orbital-order sign
@@ -361,17 +367,35 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_sigma_same(RowArgs<R> A) {
                     const int q1 = __ffs(e) - 1;
                     const uint32_t m1 = m12 | (1u << q1);
                     const R *wq = w + pair_index(q1, 0, N);  // + q2 gives pair (q1, q2)
-                    for (uint32_t e2 = e & (e - 1u); e2; e2 &= e2 - 1u) {
-                        const int q2 = __ffs(e2) - 1;
-                        const uint32_t m = m1 | (1u << q2);
-                        const R v = flip_sign<R>(wq[q2], (uint32_t)par(PP & m));
-                        fma_c<R>(acc, v, row[T.ra[a ^ m]]);
+                    for (uint32_t e2 = e & (e - 1u); e2;) {  // two partners per iteration
+                        const int qa = __ffs(e2) - 1;
+                        e2 &= e2 - 1u;
+                        const bool two = e2 != 0u;
+                        const int qb = two ? __ffs(e2) - 1 : qa;
+                        if (two) e2 &= e2 - 1u;
+                        const uint32_t ma = m1 | (1u << qa), mb = m1 | (1u << qb);
+                        const cplx<R> ca = row[rk[a ^ ma]], cb = row[rk[a ^ mb]];
+                        const R va = flip_sign<R>(wq[qa], (uint32_t)par(PP & ma));
+                        const R vb = two ? flip_sign<R>(wq[qb], (uint32_t)par(PP & mb)) : (R)0;
+                        acc.x = fma(vb, cb.x, fma(va, ca.x, acc.x));
+                        acc.y = fma(vb, cb.y, fma(va, ca.y, acc.y));
                     }
                 }
             }
         }
-        // beta-beta doubles (partner rows, same column)
-        for (int k = 0; k < nbd; ++k) {
+        // beta-beta doubles (partner rows, same column), four loads in flight
+        int k = 0;
+        for (; k + 4 <= nbd; k += 4) {
+            cplx<R> cc[4];
+            #pragma unroll
+            for (int j = 0; j < 4; ++j) cc[j] = A.C[(size_t)bd[k + j].Jb * Da + Ia];
+            #pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const BetaDouble<R> e = bd[k + j];
+                fma_c<R>(acc, (e.c ^ par(xa & e.M)) ? -e.v : e.v, cc[j]);
+            }
+        }
+        for (; k < nbd; ++k) {
             const BetaDouble<R> e = bd[k];
             fma_c<R>(acc, (e.c ^ par(xa & e.M)) ? -e.v : e.v, A.C[(size_t)e.Jb * Da + Ia]);
         }
@@ -385,10 +409,22 @@ __global__ void __launch_bounds__(kRowThreads, 2) k_sigma_same(RowArgs<R> A) {
             A.lamc[(size_t)Ib * Da + Ia] = mk<R>(acc.x + u.x, acc.y + u.y);
         }
     }
-    block_sum2(e_acc, n_acc, red);
+    // fixed-order block sums over kSameThreads threads
+    e_acc = warp_sum(e_acc);
+    n_acc = warp_sum(n_acc);
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = e_acc;
+        red[kSameThreads / 32 + (threadIdx.x >> 5)] = n_acc;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        A.partial[Ib] = e_acc + A.partial[2 * A.Db + Ib];
-        A.partial[A.Db + Ib] = n_acc;
+        double se = 0.0, sn = 0.0;
+        for (int w = 0; w < kSameThreads / 32; ++w) {
+            se += red[w];
+            sn += red[kSameThreads / 32 + w];
+        }
+        A.partial[Ib] = se + A.partial[2 * A.Db + Ib];
+        A.partial[A.Db + Ib] = sn;
     }
 }
 
@@ -551,21 +587,31 @@ __global__ void __launch_bounds__(kAbThreads) k_sigma_ab(RowArgs<R> A) {
             }
             for (uint32_t o = a; o; o &= o - 1u) {
                 const int p = __ffs(o) - 1;
-                for (uint32_t e = ea; e; e &= e - 1u) {
-                    const int q = __ffs(e) - 1;
-                    const uint32_t m = (1u << p) | (1u << q);
-                    const int Ja = raS[a ^ m];
+                // two empty orbitals per iteration: both partners' loads in flight together
+                for (uint32_t e = ea; e;) {
+                    const int q0 = __ffs(e) - 1;
+                    e &= e - 1u;
+                    const bool two = e != 0u;
+                    const int q1 = two ? __ffs(e) - 1 : q0;
+                    if (two) e &= e - 1u;
+                    const uint32_t m0 = (1u << p) | (1u << q0), m1 = (1u << p) | (1u << q1);
+                    const int J0 = raS[a ^ m0], J1 = raS[a ^ m1];
                     // alpha bits strictly between p and q
-                    const uint32_t sa0 = (uint32_t)par(ppa & m) ^ (uint32_t)(p < q);
-                    cplx<R> c[K];
-                    R v[KP];
-                    lds_c<K>(part + (size_t)Ja * K, c);
-                    lds_r<KP>(eriS + (q * N + p) * KP, v);
+                    const uint32_t s0 = (uint32_t)par(ppa & m0) ^ (uint32_t)(p < q0);
+                    const uint32_t s1 = (uint32_t)par(ppa & m1) ^ (uint32_t)(p < q1);
+                    cplx<R> c0[K], c1[K];
+                    R v0[KP], v1[KP];
+                    lds_c<K>(part + (size_t)J0 * K, c0);
+                    lds_c<K>(part + (size_t)J1 * K, c1);
+                    lds_r<KP>(eriS + (q0 * N + p) * KP, v0);
+                    lds_r<KP>(eriS + (q1 * N + p) * KP, v1);
                     #pragma unroll
                     for (int k = 0; k < K; ++k) {
-                        const R w = flip_sign<R>(v[k], sa0);
-                        sk[k].x += w * c[k].x;
-                        sk[k].y += w * c[k].y;
+                        const R w0 = flip_sign<R>(v0[k], s0);
+                        const R w1 = two ? flip_sign<R>(v1[k], s1) : (R)0;
+                        // chained multiply-adds: two per term (float64 states are FP64-pipe bound)
+                        sk[k].x = fma(w1, c1[k].x, fma(w0, c0[k].x, sk[k].x));
+                        sk[k].y = fma(w1, c1[k].y, fma(w0, c0[k].y, sk[k].y));
                     }
                 }
             }
@@ -659,9 +705,14 @@ static size_t ab_smem(int dtype, int K, const RowTables &T) {
     return (size_t)K * T.Da * amp + (size_t)T.N * T.N * KP * real + (size_t)K * T.N * real + ((size_t)2 << T.N);
 }
 
-static size_t same_smem(int dtype, const RowTables &T) {
+// k_sigma_same's dynamic shared memory, with or without the alpha rank table; its
+// static shared memory (the beta-double list) is below 24 KB, so 203 KB of dynamic
+// memory keeps the block within the 227 KB a block may use.
+constexpr size_t kSameSmemCap = 203 * 1024;
+
+static size_t same_smem(int dtype, const RowTables &T, bool ra_in) {
     const size_t amp = dtype == SV_C64 ? 8 : 16, real = amp / 2, NP = (size_t)T.N * (T.N - 1) / 2;
-    return (size_t)T.Da * amp + NP * NP * real + (size_t)T.N * T.N * T.N * real;
+    return (size_t)T.Da * amp + NP * NP * real + (size_t)T.N * T.N * T.N * real + (ra_in ? ((size_t)2 << T.N) : 0);
 }
 
 static const int kChunksC64[] = {2, 4, 6, 8};
@@ -672,7 +723,7 @@ static const int kChunksC128[] = {1, 2, 3, 4};
 // chunks * (K + 3), among the sizes that fit; `want` > 0 caps K.
 int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want) {
     if (T.Da > kAbThreads * kAbIpt || T.Db < 1 || T.N < 2) return 0;
-    if (same_smem(dtype, T) > kAbSmemCap) return 0;
+    if (same_smem(dtype, T, false) > kSameSmemCap) return 0;
     const int nbs = nb * (T.N - nb) > 0 ? nb * (T.N - nb) : 1;  // beta singles of a row
     int best = 0;
     long best_cost = 0;
@@ -728,10 +779,17 @@ static cudaError_t launch_rows_t(const RowArgs<R> &A, const RowTables &T, int dt
     }
     cudaError_t e = launch_ab_k<R>(A, K, ab_smem(dtype, K, T), st);
     if (e != cudaSuccess) return e;
-    const size_t smem = same_smem(dtype, T);
-    e = cudaFuncSetAttribute(k_sigma_same<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_sigma_same<R><<<T.Db, kRowThreads, smem, st>>>(A);
+    if (same_smem(dtype, T, true) <= kSameSmemCap) {
+        const size_t smem = same_smem(dtype, T, true);
+        e = cudaFuncSetAttribute(k_sigma_same<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sigma_same<R, true><<<T.Db, kSameThreads, smem, st>>>(A);
+    } else {
+        const size_t smem = same_smem(dtype, T, false);
+        e = cudaFuncSetAttribute(k_sigma_same<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sigma_same<R, false><<<T.Db, kSameThreads, smem, st>>>(A);
+    }
     return cudaGetLastError();
 }
 
