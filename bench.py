@@ -281,6 +281,10 @@ def run_ours(args, rank, world, local_rank):
         st = sv.StateVector(n, dtype, stream, sector=(p["na"], p["nb"]) if sector else None)
         st.set_option(sv.SV_OPT_PROFILE, 1)
         outs = {}
+        tuned = None
+        if not args.no_autotune:  # launch choices timed on this problem, before any timed step
+            st.prepare_hf(p["occ"])
+            tuned = st.autotune(ham, p["ops"], p["theta"])
 
         def step():
             st.prepare_hf(p["occ"])
@@ -318,13 +322,14 @@ def run_ours(args, rank, world, local_rank):
         ms, t_host = reduce_max([ms, t_host])
         avg = {k: statistics.mean(ph[k] for ph in phases) for k in phases[0]}
         st.close()
-        return dict(ms=ms, t_host=t_host, phases=avg, clocks=clk, launches=launches, out=outs)
+        return dict(ms=ms, t_host=t_host, phases=avg, clocks=clk, launches=launches, out=outs, tuned=tuned)
 
     def timed_batch():
         """Config 4: 512 instances (10-20 qubits, 40 operators each), one graph launch per step."""
         probs = inputs.batch_problems(512)
         b = sv.Batch(probs, "c64", stream)
         theta = np.concatenate([q["theta"] for q in probs])
+        grid = None if args.no_autotune else b.autotune(theta)
         for _ in range(args.warmup):
             b.energy_grad(theta)
         torch.cuda.synchronize()
@@ -338,7 +343,7 @@ def run_ours(args, rank, world, local_rank):
         ms = ev0.elapsed_time(ev1) / args.steps
         out = {"workload": "512 instances, 10-20 qubits, 40-operator ADAPT-style ansatz each, complex64",
                "ms_per_batch": ms, "instance_evals_per_s": 512 / (ms / 1000.0),
-               "gpu_launches_per_batch": (b.launches - l0) // args.steps}
+               "gpu_launches_per_batch": (b.launches - l0) // args.steps, "autotuned_grid": grid}
         b.close()
         return out
 
@@ -383,6 +388,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(L * (20 + 8) + len(p["occ"]) * 4),
                 "d2h_bytes_per_step": int((1 + L) * 8 + 2 * 2 * p["n_orb"] ** 2 * 8)},
         "gpu_launches": int(head["launches"]),
+        "autotune": head["tuned"],
     }
     if head128 is not None:
         v128 = throughput(world, K, head128["ms"])
@@ -420,6 +426,7 @@ def run_ours(args, rank, world, local_rank):
                                            "mean_launch_ms": t_rot * 1e3},
                             "adjoint_l": {"algorithmic_gbs": 2.0 * sb.sum() / L / t_adj / 1e9,
                                           "mean_launch_ms": t_adj * 1e3}},
+                "autotune": s64["tuned"],
                 "abs_dE_vs_dense_c64": abs(s64["out"]["E"] - head["out"]["E"]),
                 "max_abs_dg_vs_dense_c64": float(np.max(np.abs(s64["out"]["g"] - head["out"]["g"])))}
         if s128 is not None:
@@ -490,6 +497,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) timing")
     ap.add_argument("--no-sector", action="store_true", help="skip the sector-storage timing")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch choices")
     ap.add_argument("--op-profile", action="store_true",
                     help="per-operator rotation bandwidth by lowest address bit (diagnostic, not the bench line)")
     ap.add_argument("--qubits", type=int, default=0,

@@ -286,6 +286,13 @@ sv_status sv_batch_set_time_limit(sv_batch_handle b, double ms);
 /* Kernels launched by this batch so far (one per sv_batch_energy_grad). */
 uint64_t sv_batch_launch_count(sv_batch_handle b);
 
+/* Autotuner for the persistent batched launch: times the captured launch (angles
+ * up, kernel, results down) with 1, 2, 3 and 4 blocks per SM (capped by the
+ * instance count) at the angles theta (as for sv_batch_energy_grad) and keeps the
+ * fastest grid for later calls; *grid_out (may be NULL) receives it.  Results do not
+ * depend on the grid.  No counterpart in the paper. */
+sv_status sv_batch_autotune(sv_batch_handle b, const double *theta, int *grid_out);
+
 sv_status sv_batch_destroy(sv_batch_handle b);
 
 /* ---- options ------------------------------------------------------------------ */
@@ -309,12 +316,35 @@ typedef enum {
     SV_OPT_PROFILE = 5,             /* 1: record CUDA events around each phase (sv_phase_times) */
     SV_OPT_LAYOUT_AUTO = 6,         /* 1 (default): sv_energy_grad chooses the storage layout
                                        from its operator list (sv_set_layout); 0: keep it */
-    SV_OPT_AB_CHUNK = 7             /* variant 3: most partner rows staged per chunk
-                                       (1, 2, 4 or 8; 0 = as many as fit; a tuning knob,
-                                       results differ only by summation order) */
+    SV_OPT_AB_CHUNK = 7,            /* variant 3: partner rows staged per chunk (complex64:
+                                       2, 4, 6 or 8; complex128: 1, 2, 3 or 4; another value
+                                       takes the largest compiled size below it; 0 = the
+                                       fastest estimate among the sizes that fit) */
+    SV_OPT_ROT_BLOCKS_PER_SM = 8,   /* launch geometry of the dense rotation and adjoint
+                                       kernels: at most this many blocks per SM (1..64,
+                                       default 8) */
+    SV_OPT_SECT_BLOCKS_PER_SM = 9,  /* the same for the sector rotation / adjoint kernels
+                                       (default 8) */
+    SV_OPT_RDM_BLOCKS_PER_SM = 10   /* the same for the string-row 1-RDM (default 4) */
 } sv_option;
 
+/* Options change launch choices or summation order only: results agree within the
+ * precision's rounding.  SV_ERR_ARG for an unknown option or a value out of range. */
 sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value);
+
+/* Current value of an option (after sv_autotune: the values it chose). */
+sv_status sv_get_option(sv_handle h, sv_option opt, int64_t *value);
+
+/* Autotuner: time, on this handle's device with CUDA events, the candidate launch
+ * choices for the given Hamiltonian and ansatz (ops/theta as for sv_energy_grad)
+ * and keep the fastest -- the expectation's form and partner-row chunk size
+ * (SV_OPT_EXPECT_VARIANT 2 or 3, SV_OPT_AB_CHUNK), the rotation and adjoint kernels'
+ * blocks per SM (4, 8, 16, 32; dense or sector storage) and the 1-RDM's (2, 4, 8, 16).
+ * Needs a prepared state; the state itself is left unchanged (candidates run on
+ * copies in the adjoint vector and the saved-state buffer, which sv_energy_grad
+ * allocates anyway).  Takes tens of launches of each kernel: call it once per problem
+ * shape, outside any timed region.  No counterpart in the paper. */
+sv_status sv_autotune(sv_handle h, sv_ham_handle ham, const sv_excitation *ops, int n_ops, const double *theta);
 
 /* ---- introspection ------------------------------------------------------------ */
 

@@ -194,7 +194,7 @@ struct sv_batch {
     int n_inst = 0;
     sv_dtype dtype = SV_C64;
     cudaStream_t stream = nullptr;
-    int device = 0, sm_count = 148, grid = 0, Dmax = 0;
+    int device = 0, sm_count = 148, grid = 0, grid_max = 0, Dmax = 0;
     std::vector<int> L;
     std::vector<long long> cs_off, out_off;
     long long total_ops = 0, total_out = 0;
@@ -397,8 +397,10 @@ sv_status build_plan(sv_batch *b, int n_inst, const sv_instance *inst) {
     if ((s = up(&b->d_cs, nullptr, std::max<long long>(cs, 1) * sizeof(cplx<R>))) != SV_OK) return s;
     if ((s = up((void **)&b->d_out, nullptr, std::max<long long>(out, 1) * sizeof(double))) != SV_OK) return s;
     if ((s = up((void **)&b->d_ctrl, nullptr, 2 * sizeof(int))) != SV_OK) return s;
+    // scratch slots for the largest grid sv_batch_autotune may try (4 blocks per SM)
+    b->grid_max = std::max(1, std::min(n_inst, b->sm_count * 4));
     b->grid = std::max(1, std::min(n_inst, b->sm_count * 2));
-    if ((s = up(&b->d_scratch, nullptr, (size_t)b->grid * 2 * b->Dmax * sizeof(cplx<R>))) != SV_OK) return s;
+    if ((s = up(&b->d_scratch, nullptr, (size_t)b->grid_max * 2 * b->Dmax * sizeof(cplx<R>))) != SV_OK) return s;
     if (cudaMallocHost(&b->h_cs, std::max<long long>(cs, 1) * sizeof(cplx<R>)) != cudaSuccess ||
         cudaMallocHost((void **)&b->h_out, std::max<long long>(out, 1) * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void **)&b->h_ctrl, 2 * sizeof(int)) != cudaSuccess) {
@@ -531,6 +533,63 @@ sv_status sv_batch_energy_grad(sv_batch_handle b, const double *theta, double *e
 }
 
 uint64_t sv_batch_launch_count(sv_batch_handle b) { return b ? b->launches : 0; }
+
+static void drop_graph(sv_batch_handle b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+sv_status sv_batch_autotune(sv_batch_handle b, const double *theta, int *grid_out) {
+    if (!b) return bfail(SV_ERR_ARG, "NULL batch handle");
+    if (b->total_ops > 0 && !theta) return bfail(SV_ERR_ARG, "NULL theta");
+    for (long long k = 0; k < b->total_ops; ++k)
+        if (!std::isfinite(theta[k])) return bfail(SV_ERR_ARG, "non-finite theta");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    if (b->dtype == SV_C64) fill_cs<float>(b, theta);
+    else fill_cs<double>(b, theta);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sv_status s = SV_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) s = bfail(SV_ERR_CUDA, "event creation failed");
+    const int keep = b->grid;
+    int best = keep;
+    float best_t = -1.f;
+    for (int mult = 1; s == SV_OK && mult <= 4; ++mult) {
+        const int g = std::max(1, std::min(b->n_inst, b->sm_count * mult));
+        if (g > b->grid_max || (mult > 1 && g == std::min(b->n_inst, b->sm_count * (mult - 1)))) continue;
+        drop_graph(b);
+        b->grid = g;
+        s = b->dtype == SV_C64 ? capture<float>(b) : capture<double>(b);
+        float ms = 0.f;
+        for (int r = 0; s == SV_OK && r < 2; ++r) {  // the second run is timed
+            cudaError_t e = cudaEventRecord(e0, b->stream);
+            if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                s = bfail(SV_ERR_CUDA, std::string("batch autotune launch: ") + cudaGetErrorString(e));
+            } else {
+                b->launches++;
+            }
+        }
+        if (s == SV_OK && (best_t < 0.f || ms < best_t)) {
+            best_t = ms;
+            best = g;
+        }
+    }
+    drop_graph(b);
+    b->grid = s == SV_OK ? best : keep;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (grid_out) *grid_out = b->grid;
+    if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+    return s;
+}
 
 sv_status sv_batch_destroy(sv_batch_handle b) {
     if (!b) return SV_OK;

@@ -719,17 +719,22 @@ static const int kChunksC64[] = {2, 4, 6, 8};
 static const int kChunksC128[] = {1, 2, 3, 4};
 
 // Rows staged per chunk by k_sigma_ab, 0 when the split form does not fit (the
-// single-kernel form runs instead): the fewest estimated issue slots,
-// chunks * (K + 3), among the sizes that fit; `want` > 0 caps K.
+// single-kernel form runs instead).  `want` > 0 asks for that chunk size (taken when
+// it is one of the compiled sizes and fits, else the largest such size below it);
+// otherwise the fewest estimated issue slots, chunks * (K + 3), among the sizes that fit.
 int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want) {
     if (T.Da > kAbThreads * kAbIpt || T.Db < 1 || T.N < 2) return 0;
     if (same_smem(dtype, T, false) > kSameSmemCap) return 0;
+    const int *sizes = dtype == SV_C64 ? kChunksC64 : kChunksC128;
+    if (want > 0) {
+        for (int i = 3; i >= 0; --i)
+            if (sizes[i] <= want && ab_smem(dtype, sizes[i], T) <= kAbSmemCap) return sizes[i];
+    }
     const int nbs = nb * (T.N - nb) > 0 ? nb * (T.N - nb) : 1;  // beta singles of a row
     int best = 0;
     long best_cost = 0;
     for (int i = 0; i < 4; ++i) {
-        const int K = dtype == SV_C64 ? kChunksC64[i] : kChunksC128[i];
-        if (want > 0 && K > want) continue;
+        const int K = sizes[i];
         if (ab_smem(dtype, K, T) > kAbSmemCap) continue;
         const long cost = (long)((nbs + K - 1) / K) * (K + 3);
         if (!best || cost < best_cost || (cost == best_cost && K > best)) {

@@ -281,7 +281,11 @@ void sect_op_from(const OpDesc &d, int N, void *dst) {
     *(SectOp *)dst = o;
 }
 
-int sector_grid(int Db, int sm_count) { return Db < sm_count * 8 ? Db : sm_count * 8; }
+// Blocks of the list kernels: one per beta-list entry, at most bps per SM (8 by default).
+int sector_grid(int Db, int sm_count, int bps) {
+    const int cap = sm_count * (bps > 0 ? bps : 8);
+    return Db < cap ? Db : cap;
+}
 
 // Host side of the lists: counts from the patterns, offsets, and the build launch.
 static uint64_t choose(int n, int k) {
@@ -343,7 +347,10 @@ cudaError_t launch_adjoint_l(void *psi, void *lam, int dtype, const uint32_t *al
 
 int rdm_rows_elements(int n) { return 1 + n + (n / 2) * (n / 2 - 1); }
 
-int rdm_rows_grid(int Db, int sm_count) { return Db < 4 * sm_count ? Db : 4 * sm_count; }
+int rdm_rows_grid(int Db, int sm_count, int bps) {
+    const int cap = sm_count * (bps > 0 ? bps : 4);
+    return Db < cap ? Db : cap;
+}
 
 // partial: [2 n_el][grid] doubles (n_el = rdm_rows_elements(n)), reduced by launch_reduce_rows.
 cudaError_t launch_rdm_rows(const void *C, int dtype, int n, const uint32_t *sa, const uint32_t *sb,

@@ -252,9 +252,11 @@ __global__ void __launch_bounds__(kThreads) k_reduce_rows(const double *__restri
 
 // ---------------------------------------------------------------- launchers
 
-int rotate_grid(uint64_t npairs, int sm_count) {
+// Blocks for a grid-stride launch over npairs items: enough for one item per thread,
+// at most bps blocks per SM (8 unless sv_autotune / SV_OPT_ROT_BLOCKS_PER_SM chose).
+int rotate_grid(uint64_t npairs, int sm_count, int bps) {
     uint64_t want = (npairs + kThreads - 1) / kThreads;
-    uint64_t cap = (uint64_t)sm_count * 8;
+    uint64_t cap = (uint64_t)sm_count * (uint64_t)(bps > 0 ? bps : 8);
     if (want < 1) want = 1;
     return (int)(want < cap ? want : cap);
 }
@@ -275,30 +277,26 @@ static int vec_log2(int dtype, const OpDesc &d, int n) {
 }
 
 template <typename R, int NB>
-static void rot_v(void *psi, int v, uint32_t npairs, OpArgs a, int sm_count, cudaStream_t st) {
+static void rot_v(void *psi, int v, uint32_t npairs, OpArgs a, int sm_count, int bps, cudaStream_t st) {
     uint32_t ng = npairs >> v;
-    int grid = rotate_grid((ng + 1) / 2, sm_count);
+    int grid = rotate_grid((ng + 1) / 2, sm_count, bps);
     if (v == 0) k_rotate<R, NB, 1><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, ng, a);
     else if (v == 1) k_rotate<R, NB, 2><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, ng, a);
     else k_rotate<R, NB, 4><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, ng, a);
 }
 
-cudaError_t launch_rotate(void *psi, int dtype, int n, const OpDesc &d, int sm_count, cudaStream_t st) {
+cudaError_t launch_rotate(void *psi, int dtype, int n, const OpDesc &d, int sm_count, int bps, cudaStream_t st) {
     OpArgs a = to_args(d);
     uint32_t npairs = (uint32_t)(1ull << (n - d.nbits));
     int v = vec_log2(dtype, d, n);
     if (dtype == SV_C64) {
-        if (d.nbits == 2) rot_v<float, 2>(psi, v, npairs, a, sm_count, st);
-        else rot_v<float, 4>(psi, v, npairs, a, sm_count, st);
+        if (d.nbits == 2) rot_v<float, 2>(psi, v, npairs, a, sm_count, bps, st);
+        else rot_v<float, 4>(psi, v, npairs, a, sm_count, bps, st);
     } else {
-        if (d.nbits == 2) rot_v<double, 2>(psi, v, npairs, a, sm_count, st);
-        else rot_v<double, 4>(psi, v, npairs, a, sm_count, st);
+        if (d.nbits == 2) rot_v<double, 2>(psi, v, npairs, a, sm_count, bps, st);
+        else rot_v<double, 4>(psi, v, npairs, a, sm_count, bps, st);
     }
     return cudaGetLastError();
-}
-
-int adjoint_grid(int n, const OpDesc &d, int sm_count) {
-    return rotate_grid(1ull << (n - d.nbits), sm_count);
 }
 
 template <typename R, int NB>

@@ -18,9 +18,9 @@
 #include "sv_internal.h"
 
 namespace svk {
-int rotate_grid(uint64_t npairs, int sm_count);
+int rotate_grid(uint64_t npairs, int sm_count, int bps);
 cudaError_t launch_set_basis(void *psi, int dtype, uint32_t x, cudaStream_t st);
-cudaError_t launch_rotate(void *psi, int dtype, int n, const OpDesc &d, int sm_count, cudaStream_t st);
+cudaError_t launch_rotate(void *psi, int dtype, int n, const OpDesc &d, int sm_count, int bps, cudaStream_t st);
 cudaError_t launch_adjoint(void *psi, void *lam, int dtype, int n, const OpDesc &d, int grid,
                            double *partial, cudaStream_t st);
 cudaError_t launch_reduce_rows(const double *partials, int rows, int cols, double *out, cudaStream_t st);
@@ -41,7 +41,7 @@ cudaError_t launch_rdm_gather(const void *psi, int dtype, const uint32_t *sector
                               const void *elems, int n_el, int grid, double *partial, cudaStream_t st);
 // sector storage (k_sector.cu)
 void sect_op_from(const OpDesc &d, int N, void *dst);
-int sector_grid(int Db, int sm_count);
+int sector_grid(int Db, int sm_count, int bps);
 size_t list_op_bytes();
 void list_op_from(const OpDesc &d, int N, int na, int nb, uint32_t a_off, void *dst, int *na_l, int *nb_l);
 cudaError_t launch_build_lists(const void *ops, int n_ops, const uint32_t *sa, const uint32_t *sb,
@@ -52,7 +52,7 @@ cudaError_t launch_rotate_l(void *psi, int dtype, const uint32_t *al, int na_l, 
 cudaError_t launch_adjoint_l(void *psi, void *lam, int dtype, const uint32_t *al, int na_l, const uint32_t *bl,
                              int nb_l, int Da, double c, double s, int grid, double *partial, cudaStream_t st);
 int rdm_rows_elements(int n);
-int rdm_rows_grid(int Db, int sm_count);
+int rdm_rows_grid(int Db, int sm_count, int bps);
 cudaError_t launch_rdm_rows(const void *C, int dtype, int n, const uint32_t *sa, const uint32_t *sb,
                             const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb, int Da,
                             int Db, int grid, double *partial, cudaStream_t st);
@@ -520,14 +520,14 @@ static sv_status forward(sv_handle h, const std::vector<OpDesc> &ops, bool check
     const int64_t C = h->ckpt_interval;
     if (h->storage == 1 && !ops.empty()) SV_TRY(ensure_op_lists(h, ops));
     const uint32_t *L = (const uint32_t *)h->list_buf;
-    const int G = sector_grid(h->Db, h->sm_count);
+    const int G = sector_grid(h->Db, h->sm_count, h->sect_bps);
     for (size_t k = 0; k < ops.size(); ++k) {
         if (h->storage == 1) {
             const int *li = &h->list_info[4 * k];
             SV_CUDA(h, launch_rotate_l(h->psi, h->dtype, L + li[0], li[1], L + li[2], li[3], h->Da, ops[k].c,
                                        ops[k].s, G, h->stream));
         } else {
-            SV_CUDA(h, launch_rotate(h->psi, h->dtype, h->n, ops[k], h->sm_count, h->stream));
+            SV_CUDA(h, launch_rotate(h->psi, h->dtype, h->n, ops[k], h->sm_count, h->rot_bps, h->stream));
         }
         h->launches++;
         if (checkpoints && C > 0 && (k + 1) % (size_t)C == 0 && k + 1 < ops.size()) {
@@ -673,6 +673,138 @@ static bool is_identity(sv_handle h) {
     for (int q = 0; q < h->n; ++q)
         if (h->perm[q] != q) return false;
     return true;
+}
+
+// ---------------------------------------------------------------- autotuning
+
+// Fastest of `reps` runs of fn (launches on the handle's stream), in ms, timed with
+// CUDA events on that stream; negative when fn failed.
+template <typename F>
+static float time_best(sv_handle h, cudaEvent_t e0, cudaEvent_t e1, F fn, int reps = 3) {
+    float best = -1.f;
+    for (int r = 0; r < reps; ++r) {
+        if (cudaEventRecord(e0, h->stream) != cudaSuccess) return -1.f;
+        if (fn() != SV_OK) return -1.f;
+        if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.f;
+        if (best < 0.f || ms < best) best = ms;
+    }
+    return best;
+}
+
+static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector<OpDesc> &d, cudaEvent_t e0,
+                               cudaEvent_t e1) {
+    DevTables *T;
+    SV_TRY(get_tables(h, ham, &T));
+    SV_TRY(ensure_lam(h));
+    SV_TRY(ensure_out(h, 2));
+    SV_TRY(ensure_strings(h));
+    const double c = shift_for(h, ham);
+    // 1. expectation form: the one-kernel string rows, and the split form at every chunk size
+    {
+        RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
+                    T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db, T->W2};
+        const int sizes64[] = {2, 4, 6, 8}, sizes128[] = {1, 2, 3, 4};
+        const int *sizes = h->dtype == SV_C64 ? sizes64 : sizes128;
+        int best_v = 2;
+        int64_t best_k = 0;
+        float best_t = -1.f;
+        for (int i = -1; i < 4; ++i) {
+            h->expect_variant = i < 0 ? 2 : 3;
+            h->ab_chunk = i < 0 ? 0 : sizes[i];
+            if (i >= 0 && row_chunk(h, R) != sizes[i]) continue;  // that size does not fit
+            const float t = time_best(h, e0, e1, [&] { return expectation(h, ham, T, h->lam, c, 0); });
+            if (t < 0.f) return fail(h, SV_ERR_CUDA, "autotune: expectation candidate failed");
+            if (best_t < 0.f || t < best_t) {
+                best_t = t;
+                best_v = h->expect_variant;
+                best_k = h->ab_chunk;
+            }
+        }
+        h->expect_variant = best_v;
+        h->ab_chunk = best_k;
+    }
+    // 2. rotation / adjoint launch geometry, on copies of psi in the adjoint vector and the
+    //    saved-state buffer (psi is left alone): one rotation plus one adjoint step per candidate
+    if (!d.empty()) {
+        if (!h->saved) {  // as in sv_energy_grad: optional under the byte cap
+            void *p = nullptr;
+            if (dev_alloc(h, &p, vec_bytes(h), "saved final state") == SV_OK) h->saved = p;
+            else cudaGetLastError();
+        }
+        const bool adj = h->saved != nullptr;  // without it only the rotation is timed
+        SV_CUDA(h, cudaMemcpyAsync(h->lam, h->psi, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+        if (adj) SV_CUDA(h, cudaMemcpyAsync(h->saved, h->psi, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+        size_t k = 0;  // a representative op: the first double whose touched runs are long
+        for (size_t j = 0; j < d.size(); ++j)
+            if (d[j].nbits == 4 && d[j].pos[0] >= 4) { k = j; break; }
+        const int cands[] = {4, 8, 16, 32};
+        int best_b = 8;
+        float best_t = -1.f;
+        if (h->storage == 1) SV_TRY(ensure_op_lists(h, d));
+        SV_TRY(ensure_partials(h, (size_t)h->sm_count * 32));
+        for (int b : cands) {
+            float t;
+            if (h->storage == 1) {
+                const uint32_t *L = (const uint32_t *)h->list_buf;
+                const int *li = &h->list_info[4 * k];
+                const int G = sector_grid(h->Db, h->sm_count, b);
+                t = time_best(h, e0, e1, [&]() -> sv_status {
+                    SV_CUDA(h, launch_rotate_l(h->lam, h->dtype, L + li[0], li[1], L + li[2], li[3], h->Da, d[k].c,
+                                               d[k].s, G, h->stream));
+                    if (adj)
+                        SV_CUDA(h, launch_adjoint_l(h->lam, h->saved, h->dtype, L + li[0], li[1], L + li[2], li[3],
+                                                    h->Da, d[k].c, d[k].s, G, h->partials, h->stream));
+                    return SV_OK;
+                });
+            } else {
+                const int G = rotate_grid(1ull << (h->n - 2), h->sm_count, b);
+                t = time_best(h, e0, e1, [&]() -> sv_status {
+                    SV_CUDA(h, launch_rotate(h->lam, h->dtype, h->n, d[k], h->sm_count, b, h->stream));
+                    if (adj) SV_CUDA(h, launch_adjoint(h->lam, h->saved, h->dtype, h->n, d[k], G, h->partials, h->stream));
+                    return SV_OK;
+                });
+            }
+            if (t < 0.f) return fail(h, SV_ERR_CUDA, "autotune: rotation candidate failed");
+            if (best_t < 0.f || t < best_t) {
+                best_t = t;
+                best_b = b;
+            }
+        }
+        if (h->storage == 1) h->sect_bps = best_b;
+        else h->rot_bps = best_b;
+    }
+    // 3. 1-RDM launch geometry
+    {
+        const void *Cm = h->psi;
+        if (h->storage == 0) {
+            SV_CUDA(h, launch_compact(h->psi, h->Cbuf, h->dtype, h->str_sa_s, h->str_sb_s, h->Da, h->Db, h->sm_count,
+                                      h->stream));
+            Cm = h->Cbuf;
+        }
+        const int n_el = rdm_rows_elements(h->n);
+        const int cands[] = {2, 4, 8, 16};
+        SV_TRY(ensure_partials(h, (size_t)2 * n_el * rdm_rows_grid(h->Db, h->sm_count, 16)));
+        int best_b = 4;
+        float best_t = -1.f;
+        for (int b : cands) {
+            const int grid = rdm_rows_grid(h->Db, h->sm_count, b);
+            const float t = time_best(h, e0, e1, [&]() -> sv_status {
+                SV_CUDA(h, launch_rdm_rows(Cm, h->dtype, h->n, h->str_sa, h->str_sb, h->str_a, h->str_b, h->rank_a,
+                                           h->rank_b, h->Da, h->Db, grid, h->partials, h->stream));
+                return SV_OK;
+            });
+            if (t < 0.f) return fail(h, SV_ERR_CUDA, "autotune: 1-RDM candidate failed");
+            if (best_t < 0.f || t < best_t) {
+                best_t = t;
+                best_b = b;
+            }
+        }
+        h->rdm_bps = best_b;
+    }
+    SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SV_OK;
 }
 
 // ---------------------------------------------------------------- C-ABI
@@ -1044,7 +1176,8 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     }
     const bool sect = h->storage == 1;
     if (sect) SV_TRY(ensure_strings(h));
-    const int G = sect ? sector_grid(h->Db, h->sm_count) : rotate_grid(1ull << (h->n - 2), h->sm_count);
+    const int G = sect ? sector_grid(h->Db, h->sm_count, h->sect_bps)
+                       : rotate_grid(1ull << (h->n - 2), h->sm_count, h->rot_bps);
     size_t need = 0;
     if (sect) {
         need = 3 * (size_t)h->Db;
@@ -1190,7 +1323,7 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
         // string rows: on the state itself (sector storage) or on its compact copy
         SV_TRY(ensure_strings(h));
         const int n_el = rdm_rows_elements(h->n);
-        const int grid = rdm_rows_grid(h->Db, h->sm_count);
+        const int grid = rdm_rows_grid(h->Db, h->sm_count, h->rdm_bps);
         SV_TRY(ensure_partials(h, (size_t)2 * n_el * grid));
         SV_TRY(ensure_out(h, 2 * (size_t)n_el));
         SV_TRY(mark(h, 0));
@@ -1257,6 +1390,42 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
     return SV_OK;
 }
 
+sv_status sv_autotune(sv_handle h, sv_ham_handle ham, const sv_excitation *ops, int n_ops, const double *theta) {
+    SV_TRY(check_ready(h));
+    SV_TRY(check_ham(h, ham));
+    std::vector<OpDesc> d;
+    SV_TRY(build_ops(h, ops, n_ops, theta, d));
+    DeviceGuard g(h->device);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SV_CUDA(h, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        cudaEventDestroy(e0);
+        return fail(h, SV_ERR_CUDA, "autotune: event creation failed");
+    }
+    const sv_status st = autotune_impl(h, ham, d, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+sv_status sv_get_option(sv_handle h, sv_option opt, int64_t *value) {
+    if (!h || !value) return fail(h, SV_ERR_ARG, "NULL argument");
+    switch (opt) {
+        case SV_OPT_CHECKPOINT_INTERVAL: *value = h->ckpt_interval; return SV_OK;
+        case SV_OPT_MAX_BYTES: *value = h->max_bytes; return SV_OK;
+        case SV_OPT_EXPECT_VARIANT: *value = h->expect_variant; return SV_OK;
+        case SV_OPT_RDM_VARIANT: *value = h->rdm_variant; return SV_OK;
+        case SV_OPT_PROFILE: *value = h->profile ? 1 : 0; return SV_OK;
+        case SV_OPT_LAYOUT_AUTO: *value = h->layout_auto ? 1 : 0; return SV_OK;
+        case SV_OPT_AB_CHUNK: *value = h->ab_chunk; return SV_OK;
+        case SV_OPT_ROT_BLOCKS_PER_SM: *value = h->rot_bps; return SV_OK;
+        case SV_OPT_SECT_BLOCKS_PER_SM: *value = h->sect_bps; return SV_OK;
+        case SV_OPT_RDM_BLOCKS_PER_SM: *value = h->rdm_bps; return SV_OK;
+    }
+    return fail(h, SV_ERR_ARG, "unknown option");
+}
+
 sv_status sv_set_layout(sv_handle h, const int32_t *storage_of_qubit) {
     if (!h || !storage_of_qubit) return fail(h, SV_ERR_ARG, "NULL argument");
     int np[32];
@@ -1317,6 +1486,13 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
         case SV_OPT_AB_CHUNK:
             if (value < 0 || value > 8) return fail(h, SV_ERR_ARG, "alpha-beta chunk must be in [0, 8]");
             h->ab_chunk = value;
+            return SV_OK;
+        case SV_OPT_ROT_BLOCKS_PER_SM:
+        case SV_OPT_SECT_BLOCKS_PER_SM:
+        case SV_OPT_RDM_BLOCKS_PER_SM:
+            if (value < 1 || value > 64) return fail(h, SV_ERR_ARG, "blocks per SM must be in [1, 64]");
+            (opt == SV_OPT_ROT_BLOCKS_PER_SM ? h->rot_bps : opt == SV_OPT_SECT_BLOCKS_PER_SM ? h->sect_bps
+                                                                                           : h->rdm_bps) = (int)value;
             return SV_OK;
     }
     return fail(h, SV_ERR_ARG, "unknown option");

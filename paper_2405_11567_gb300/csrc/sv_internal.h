@@ -205,7 +205,11 @@ struct sv_ctx {
     int64_t max_bytes = 0;
     uint64_t bytes_owned = 0;
     int expect_variant = 0;
-    int64_t ab_chunk = 0;      // SV_OPT_AB_CHUNK: most partner rows per chunk of k_sigma_ab (0 auto)
+    int64_t ab_chunk = 0;      // SV_OPT_AB_CHUNK: partner rows per chunk of k_sigma_ab (0 auto)
+    // launch geometry (blocks per SM), set by sv_autotune or the options
+    int rot_bps = 8;           // dense k_rotate / k_adjoint
+    int sect_bps = 8;          // sector k_rotate_l / k_adjoint_l
+    int rdm_bps = 4;           // k_rdm_rows
     int rdm_variant = 0;
     // storage layout: address bit perm[q] holds qubit q (identity by default);
     // layout_auto: sv_energy_grad picks it from its operator list

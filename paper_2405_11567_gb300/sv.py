@@ -17,6 +17,7 @@ SV_OPT_CHECKPOINT_INTERVAL, SV_OPT_MAX_BYTES, SV_OPT_EXPECT_VARIANT, SV_OPT_RDM_
 SV_OPT_PROFILE = 5
 SV_OPT_LAYOUT_AUTO = 6
 SV_OPT_AB_CHUNK = 7
+SV_OPT_ROT_BLOCKS_PER_SM, SV_OPT_SECT_BLOCKS_PER_SM, SV_OPT_RDM_BLOCKS_PER_SM = 8, 9, 10
 SV_PHASES = 6
 PHASE_NAMES = ("reference", "forward", "expectation", "reverse", "restore", "rdm1")
 STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV_ERR_TIMEOUT", 5: "SV_ERR_STATE"}
@@ -27,7 +28,8 @@ EXPORTS = (
     "sv_get_state", "sv_get_amplitudes", "sv_state_device_ptr", "sv_set_layout", "sv_get_layout", "sv_ham_create", "sv_ham_destroy", "sv_apply_ansatz",
     "sv_energy", "sv_energy_grad", "sv_pool_gradients", "sv_rdm1", "sv_set_option", "sv_phase_times", "sv_last_error",
     "sv_launch_count", "sv_version", "sv_batch_create", "sv_batch_energy_grad", "sv_batch_set_time_limit",
-    "sv_batch_launch_count", "sv_batch_destroy", "sv_rdm1_noalloc",
+    "sv_batch_launch_count", "sv_batch_destroy", "sv_rdm1_noalloc", "sv_autotune", "sv_get_option",
+    "sv_batch_autotune",
 )
 
 
@@ -95,6 +97,9 @@ def lib():
             "sv_batch_launch_count": (ctypes.c_uint64, [vp]),
             "sv_batch_destroy": (i32, [vp]),
             "sv_rdm1_noalloc": (i32, [vp, i32, i32, i32, i32, vp, vp, vp]),
+            "sv_autotune": (i32, [vp, vp, vp, i32, vp]),
+            "sv_get_option": (i32, [vp, i32, vp]),
+            "sv_batch_autotune": (i32, [vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -270,6 +275,20 @@ def sv_set_option(h, opt: int, value: int):
     _ck(lib().sv_set_option(h, int(opt), int(value)), h)
 
 
+def sv_get_option(h, opt: int) -> int:
+    v = ctypes.c_int64()
+    _ck(lib().sv_get_option(h, int(opt), ctypes.byref(v)), h)
+    return int(v.value)
+
+
+def sv_autotune(h, ham, ops, theta):
+    o = _ops_array(ops)
+    t = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1))
+    if len(t) != len(o):
+        raise ValueError("one angle per excitation")
+    _ck(lib().sv_autotune(h, ham, _ptr(o), len(o), _ptr(t)), h)
+
+
 def sv_phase_times(h) -> dict:
     ms = np.zeros(SV_PHASES)
     _ck(lib().sv_phase_times(h, _ptr(ms), SV_PHASES), h)
@@ -308,6 +327,15 @@ def sv_batch_energy_grad(b, theta_concat, n_inst: int, total_ops: int):
     return e, g[:total_ops]
 
 
+def sv_batch_autotune(b, theta_concat, total_ops: int) -> int:
+    t = np.ascontiguousarray(np.asarray(theta_concat, dtype=np.float64).reshape(-1))
+    if len(t) != total_ops:
+        raise ValueError("theta must hold every instance's angles, concatenated")
+    grid = ctypes.c_int()
+    _ck(lib().sv_batch_autotune(b, _ptr(t), ctypes.byref(grid)))
+    return int(grid.value)
+
+
 def sv_batch_set_time_limit(b, ms: float):
     _ck(lib().sv_batch_set_time_limit(b, float(ms)))
 
@@ -339,6 +367,10 @@ class Batch:
 
     def set_time_limit(self, ms):
         sv_batch_set_time_limit(self.handle, ms)
+
+    def autotune(self, theta_concat) -> int:
+        """Time the batched launch at 1-4 blocks per SM and keep the fastest grid (returned)."""
+        return sv_batch_autotune(self.handle, theta_concat, self.total_ops)
 
     @property
     def launches(self) -> int:
@@ -433,6 +465,17 @@ class StateVector:
 
     def set_option(self, opt, value):
         sv_set_option(self.handle, opt, value)
+
+    def option(self, opt) -> int:
+        return sv_get_option(self.handle, opt)
+
+    def autotune(self, ham: Hamiltonian, ops, theta) -> dict:
+        """Time the candidate launch choices on this problem and keep the fastest (sv_autotune)."""
+        sv_autotune(self.handle, ham.handle, ops, theta)
+        return {name: self.option(opt) for name, opt in (
+            ("expect_variant", SV_OPT_EXPECT_VARIANT), ("ab_chunk", SV_OPT_AB_CHUNK),
+            ("rot_blocks_per_sm", SV_OPT_ROT_BLOCKS_PER_SM), ("sect_blocks_per_sm", SV_OPT_SECT_BLOCKS_PER_SM),
+            ("rdm_blocks_per_sm", SV_OPT_RDM_BLOCKS_PER_SM))}
 
     def set_layout(self, storage_of_qubit):
         sv_set_layout(self.handle, storage_of_qubit)

@@ -67,6 +67,10 @@ def test_null_and_bad_arguments_rejected_without_device(cabi):
     assert cabi.sv_create_sector(8, 1, -1, 0, None, ctypes.byref(out)) == 1  # negative count
     assert cabi.sv_create_sector(9, 1, 1, 0, None, ctypes.byref(out)) == 1   # odd qubit count
     assert cabi.sv_create_sector(8, 1, 1, 7, None, ctypes.byref(out)) == 1   # bad dtype
+    v = ctypes.c_int64()
+    assert cabi.sv_get_option(None, 1, ctypes.byref(v)) == 1
+    assert cabi.sv_autotune(None, None, None, 0, None) == 1
+    assert cabi.sv_batch_autotune(None, None, None) == 1
     assert cabi.sv_destroy(None) == 0
     assert cabi.sv_energy(None, None, None) == 1
     assert b"NULL" in cabi.sv_last_error(None)
