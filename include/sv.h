@@ -70,7 +70,13 @@ typedef enum {
     SV_ERR_STATE = 5
 } sv_status;
 
-typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
+/* State precision.  SV_C64 / SV_C128: complex amplitudes (float / double pairs).
+ * SV_R32 / SV_R64: real amplitudes (float / double) -- the states of the paper's
+ * real-angle ansatz on a real reference stay real (real integrals, real generators
+ * T - T^dagger), so half the bytes and products suffice; host arrays of such a handle
+ * hold one real per amplitude.  Real states: sv_create, sv_create_sector and every
+ * state call; not the batched launch nor sv_rdm1_noalloc (SV_ERR_ARG). */
+typedef enum { SV_C64 = 0, SV_C128 = 1, SV_R32 = 2, SV_R64 = 3 } sv_dtype;
 
 /* One excitation operator.  kind 1: single, occ[0] -> vir[0] (occ[1], vir[1]
  * ignored); kind 2: double, occ[0] < occ[1], vir[0] < vir[1].  Kinds 3 and 4

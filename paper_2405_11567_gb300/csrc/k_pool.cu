@@ -23,12 +23,13 @@ struct PoolOp {
     uint16_t mb, fb;      // beta-string flip mask and "from" pattern
 };
 
-template <typename R>
+template <typename A>
 __global__ void __launch_bounds__(kThreads)
-k_pool_grad(const cplx<R> *__restrict__ C, const cplx<R> *__restrict__ L, const PoolOp *__restrict__ ops,
+k_pool_grad(const A *__restrict__ C, const A *__restrict__ L, const PoolOp *__restrict__ ops,
             const uint32_t *__restrict__ sa, const uint32_t *__restrict__ sb, const uint16_t *__restrict__ stra,
             const uint16_t *__restrict__ strb, const uint16_t *__restrict__ ra, const uint16_t *__restrict__ rb,
             int Da, int Db, double *__restrict__ out) {
+    using R = real_of<A>;
     __shared__ double red[kThreads / 32];
     const PoolOp op = ops[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -44,8 +45,8 @@ k_pool_grad(const cplx<R> *__restrict__ C, const cplx<R> *__restrict__ L, const 
             if ((a & op.ma) != op.fa) continue;
             const int Ja = ra[a ^ op.ma];
             const size_t I = (size_t)Ib * Da + Ia, J = (size_t)Jb * Da + Ja;
-            const cplx<R> u = C[I], v = C[J], lu = L[I], lv = L[J];
-            const R ti = (lv.x * u.x + lv.y * u.y) - (lu.x * v.x + lu.y * v.y);
+            const A u = C[I], v = C[J], lu = L[I], lv = L[J];
+            const R ti = re_dot(lv, u) - re_dot(lu, v);
             t += par((sa[Ia] | xb) & op.sm) ? -ti : ti;
         }
         acc += (double)t;
@@ -75,12 +76,8 @@ cudaError_t launch_pool_grad(const void *C, const void *L, int dtype, const void
                              const uint32_t *sb, const uint16_t *stra, const uint16_t *strb, const uint16_t *ra,
                              const uint16_t *rb, int Da, int Db, double *out, cudaStream_t st) {
     if (n_ops <= 0) return cudaSuccess;
-    if (dtype == SV_C64)
-        k_pool_grad<float><<<n_ops, kThreads, 0, st>>>((const float2 *)C, (const float2 *)L, (const PoolOp *)ops, sa,
-                                                       sb, stra, strb, ra, rb, Da, Db, out);
-    else
-        k_pool_grad<double><<<n_ops, kThreads, 0, st>>>((const double2 *)C, (const double2 *)L, (const PoolOp *)ops,
-                                                        sa, sb, stra, strb, ra, rb, Da, Db, out);
+    SV_DISPATCH_AMP(dtype, k_pool_grad<A><<<n_ops, kThreads, 0, st>>>((const A *)C, (const A *)L, (const PoolOp *)ops,
+                                                                      sa, sb, stra, strb, ra, rb, Da, Db, out));
     return cudaGetLastError();
 }
 

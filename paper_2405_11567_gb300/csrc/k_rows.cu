@@ -40,12 +40,13 @@ namespace svk {
 
 constexpr int kRowThreads = kThreads;
 
-template <typename R>
+template <typename A>
 struct RowArgs {
+    using R = real_of<A>;
     SigmaTables<R> T;
-    const cplx<R> *C;       // [Db][Da] compact sector amplitudes
-    cplx<R> *lam;           // dense sigma output (nullable)
-    cplx<R> *lamc;          // compact sigma output [Db][Da] (nullable)
+    const A *C;             // [Db][Da] compact sector amplitudes
+    A *lam;                 // dense sigma output (nullable)
+    A *lamc;                // compact sigma output [Db][Da] (nullable)
     const uint32_t *sa_s;   // [Da] alpha spread in the storage layout: addresses
     const uint32_t *sb_s;   // [Db]
     double *partial;        // [3][Db]: energy, norm, alpha-beta energy share
@@ -77,8 +78,9 @@ constexpr int kMaxPairs = 120;   // C(16, 2)
 constexpr int kMaxBS = 64;       // nb (N - nb) <= 8 * 8
 constexpr int kMaxBD = 784;      // C(8, 2)^2
 
-template <typename R>
-__global__ void __launch_bounds__(kRowThreads) k_sigma_rows(RowArgs<R> A) {
+template <typename Amp>
+__global__ void __launch_bounds__(kRowThreads, 2) k_sigma_rows(RowArgs<Amp> A) {
+    using R = real_of<Amp>;
     __shared__ BetaSingle<R> bs[kMaxBS];
     __shared__ BetaDouble<R> bd[kMaxBD];
     __shared__ R JB[kMaxOrb * kMaxOrb];
@@ -145,19 +147,19 @@ __global__ void __launch_bounds__(kRowThreads) k_sigma_rows(RowArgs<R> A) {
         bd[d] = x;
     }
     __syncthreads();
-    const cplx<R> *row = A.C + (size_t)Ib * Da;
+    const Amp *row = A.C + (size_t)Ib * Da;
     double e_acc = 0.0, n_acc = 0.0;
     for (int Ia = threadIdx.x; Ia < Da; Ia += blockDim.x) {
         const uint32_t a = T.stra[Ia], xa = T.sa[Ia], x = xa | xb;
         const uint32_t ea = ~a & T.maskN;
-        const cplx<R> c0 = row[Ia];
+        const Amp c0 = row[Ia];
         double d = T.e_shift;
         for (uint32_t o = x; o; o &= o - 1u) {
             const int k = __ffs(o) - 1;
             d += T.hdiag[k];
             for (uint32_t o2 = o & (o - 1u); o2; o2 &= o2 - 1u) d += T.Jp[k * T.n + __ffs(o2) - 1];
         }
-        cplx<R> acc = mk<R>((R)d * c0.x, (R)d * c0.y);
+        Amp acc = scale_a<Amp>((R)d, c0);
         // alpha singles (this row)
         for (uint32_t o = a; o; o &= o - 1u) {
             const int p = __ffs(o) - 1;
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(kRowThreads) k_sigma_rows(RowArgs<R> A) {
                 R v = T.hm[q * N + p] + JB[q * N + p];
                 for (uint32_t o2 = a; o2; o2 &= o2 - 1u) v += dt[__ffs(o2) - 1];
                 if (par(x & between(2 * p, 2 * q))) v = -v;
-                fma_c<R>(acc, v, row[T.ra[a ^ (1u << p) ^ (1u << q)]]);
+                axpy(acc, v, row[T.ra[a ^ (1u << p) ^ (1u << q)]]);
             }
         }
         // alpha-alpha doubles (this row)
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(kRowThreads) k_sigma_rows(RowArgs<R> A) {
                         const int i = 2 * p1, j = 2 * p2, aa = 2 * q1, bb = 2 * q2;
                         const uint32_t x1 = x ^ (1u << i) ^ (1u << bb);
                         if (1 ^ par(x & between(i, bb)) ^ par(x1 & between(j, aa))) v = -v;
-                        fma_c<R>(acc, v, row[T.ra[a ^ (1u << p1) ^ (1u << p2) ^ (1u << q1) ^ (1u << q2)]]);
+                        axpy(acc, v, row[T.ra[a ^ (1u << p1) ^ (1u << p2) ^ (1u << q1) ^ (1u << q2)]]);
                     }
                 }
             }
@@ -195,12 +197,12 @@ __global__ void __launch_bounds__(kRowThreads) k_sigma_rows(RowArgs<R> A) {
             R v = e.vb;
             for (uint32_t o = a; o; o &= o - 1u) v += jt[__ffs(o) - 1];
             if (e.cb ^ par(xa & e.M)) v = -v;
-            fma_c<R>(acc, v, A.C[(size_t)e.Jb * Da + Ia]);
+            axpy(acc, v, A.C[(size_t)e.Jb * Da + Ia]);
         }
         // beta-beta doubles (partner rows, same column)
         for (int k = 0; k < nbd; ++k) {
             const BetaDouble<R> e = bd[k];
-            fma_c<R>(acc, (e.c ^ par(xa & e.M)) ? -e.v : e.v, A.C[(size_t)e.Jb * Da + Ia]);
+            axpy(acc, (e.c ^ par(xa & e.M)) ? -e.v : e.v, A.C[(size_t)e.Jb * Da + Ia]);
         }
         // alpha-beta doubles: alpha p -> q outside, beta r -> s (block list) inside; value (qp|sr)
         for (uint32_t o = a; o; o &= o - 1u) {
@@ -215,14 +217,14 @@ __global__ void __launch_bounds__(kRowThreads) k_sigma_rows(RowArgs<R> A) {
                     const BetaSingle<R> bk = bs[k];
                     const R v = erib[bk.t];
                     const int sg = bk.cb ^ par(xa & bk.M) ^ sa0 ^ par(bk.xbf & B);
-                    fma_c<R>(acc, sg ? -v : v, A.C[(size_t)bk.Jb * Da + Ja]);
+                    axpy(acc, sg ? -v : v, A.C[(size_t)bk.Jb * Da + Ja]);
                 }
             }
         }
         if (A.lam) A.lam[A.sa_s[Ia] | A.sb_s[Ib]] = acc;
         if (A.lamc) A.lamc[(size_t)Ib * Da + Ia] = acc;
-        e_acc += (double)c0.x * (double)acc.x + (double)c0.y * (double)acc.y;
-        n_acc += (double)c0.x * (double)c0.x + (double)c0.y * (double)c0.y;
+        e_acc += dre_dot(c0, acc);
+        n_acc += dre_dot(c0, c0);
     }
     block_sum2(e_acc, n_acc, red);
     if (threadIdx.x == 0) {
@@ -269,8 +271,9 @@ __device__ __forceinline__ int pair_index(int p, int q, int N) { return p * N - 
 // (-1)^popc(PP & {p1,p2,q1,q2}) times an orbital-order sign that W2 carries.
 constexpr int kSameThreads = 512;
 
-template <typename R, bool RA_SMEM>
-__global__ void __launch_bounds__(kSameThreads, 1) k_sigma_same(RowArgs<R> A) {
+template <typename Amp, bool RA_SMEM>
+__global__ void __launch_bounds__(kSameThreads, 1) k_sigma_same(RowArgs<Amp> A) {
+    using R = real_of<Amp>;
     extern __shared__ __align__(16) unsigned char same_dyn[];
     __shared__ BetaDouble<R> bd[kMaxBD];
     __shared__ R JB[kMaxOrb * kMaxOrb];
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(kSameThreads, 1) k_sigma_same(RowArgs<R> A) {
     __shared__ double red[2 * kSameThreads / 32];
     const SigmaTables<R> &T = A.T;
     const int Ib = blockIdx.x, N = T.N, Da = T.Da, NP = N * (N - 1) / 2;
-    cplx<R> *row = reinterpret_cast<cplx<R> *>(same_dyn);  // [Da]
+    Amp *row = reinterpret_cast<Amp *>(same_dyn);           // [Da]
     R *W2S = reinterpret_cast<R *>(row + Da);               // [NP][NP]
     R *DtS = W2S + NP * NP;                                 // [N^3]
     uint16_t *raS = reinterpret_cast<uint16_t *>(DtS + N * N * N);  // [2^N] alpha ranks
@@ -307,7 +310,7 @@ __global__ void __launch_bounds__(kSameThreads, 1) k_sigma_same(RowArgs<R> A) {
         for (uint32_t o = b; o; o &= o - 1u) v += jt[__ffs(o) - 1];
         JB[i] = v;
     }
-    const cplx<R> *grow = A.C + (size_t)Ib * Da;
+    const Amp *grow = A.C + (size_t)Ib * Da;
     for (int i = threadIdx.x; i < Da; i += blockDim.x) row[i] = grow[i];
     for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) W2S[i] = A.W2[i];
     for (int i = threadIdx.x; i < N * N * N; i += blockDim.x) DtS[i] = T.Dt[i];
@@ -335,14 +338,14 @@ __global__ void __launch_bounds__(kSameThreads, 1) k_sigma_same(RowArgs<R> A) {
     for (int Ia = threadIdx.x; Ia < Da; Ia += blockDim.x) {
         const uint32_t a = T.stra[Ia], xa = T.sa[Ia], x = xa | xb;
         const uint32_t ea = ~a & T.maskN, PP = prefix_parity(a) ^ ppb;
-        const cplx<R> c0 = row[Ia];
+        const Amp c0 = row[Ia];
         double d = T.e_shift;
         for (uint32_t o = x; o; o &= o - 1u) {
             const int k = __ffs(o) - 1;
             d += T.hdiag[k];
             for (uint32_t o2 = o & (o - 1u); o2; o2 &= o2 - 1u) d += T.Jp[k * T.n + __ffs(o2) - 1];
         }
-        cplx<R> acc = mk<R>((R)d * c0.x, (R)d * c0.y);
+        Amp acc = scale_a<Amp>((R)d, c0);
         // alpha singles
         for (uint32_t o = a; o; o &= o - 1u) {
             const int p = __ffs(o) - 1;
@@ -353,7 +356,7 @@ __global__ void __launch_bounds__(kSameThreads, 1) k_sigma_same(RowArgs<R> A) {
                 for (uint32_t o2 = a; o2; o2 &= o2 - 1u) v += dt[__ffs(o2) - 1];
                 const uint32_t m = (1u << p) | (1u << q);
                 if ((uint32_t)par(PP & m) ^ (uint32_t)(p < q)) v = -v;
-                fma_c<R>(acc, v, row[rk[a ^ m]]);
+                axpy(acc, v, row[rk[a ^ m]]);
             }
         }
         // alpha-alpha doubles: W2[(p1,p2)][(q1,q2)] holds the value and the orbital-order sign
@@ -374,11 +377,10 @@ __global__ void __launch_bounds__(kSameThreads, 1) k_sigma_same(RowArgs<R> A) {
                         const int qb = two ? __ffs(e2) - 1 : qa;
                         if (two) e2 &= e2 - 1u;
                         const uint32_t ma = m1 | (1u << qa), mb = m1 | (1u << qb);
-                        const cplx<R> ca = row[rk[a ^ ma]], cb = row[rk[a ^ mb]];
+                        const Amp ca = row[rk[a ^ ma]], cb = row[rk[a ^ mb]];
                         const R va = flip_sign<R>(wq[qa], (uint32_t)par(PP & ma));
                         const R vb = two ? flip_sign<R>(wq[qb], (uint32_t)par(PP & mb)) : (R)0;
-                        acc.x = fma(vb, cb.x, fma(va, ca.x, acc.x));
-                        acc.y = fma(vb, cb.y, fma(va, ca.y, acc.y));
+                        acc2(acc, va, ca, vb, cb);
                     }
                 }
             }
@@ -386,27 +388,27 @@ __global__ void __launch_bounds__(kSameThreads, 1) k_sigma_same(RowArgs<R> A) {
         // beta-beta doubles (partner rows, same column), four loads in flight
         int k = 0;
         for (; k + 4 <= nbd; k += 4) {
-            cplx<R> cc[4];
+            Amp cc[4];
             #pragma unroll
             for (int j = 0; j < 4; ++j) cc[j] = A.C[(size_t)bd[k + j].Jb * Da + Ia];
             #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const BetaDouble<R> e = bd[k + j];
-                fma_c<R>(acc, (e.c ^ par(xa & e.M)) ? -e.v : e.v, cc[j]);
+                axpy(acc, (e.c ^ par(xa & e.M)) ? -e.v : e.v, cc[j]);
             }
         }
         for (; k < nbd; ++k) {
             const BetaDouble<R> e = bd[k];
-            fma_c<R>(acc, (e.c ^ par(xa & e.M)) ? -e.v : e.v, A.C[(size_t)e.Jb * Da + Ia]);
+            axpy(acc, (e.c ^ par(xa & e.M)) ? -e.v : e.v, A.C[(size_t)e.Jb * Da + Ia]);
         }
-        e_acc += (double)c0.x * (double)acc.x + (double)c0.y * (double)acc.y;
-        n_acc += (double)c0.x * (double)c0.x + (double)c0.y * (double)c0.y;
+        e_acc += dre_dot(c0, acc);
+        n_acc += dre_dot(c0, c0);
         if (A.lam) {
-            const cplx<R> u = A.lam[A.sa_s[Ia] | A.sb_s[Ib]];
-            A.lam[A.sa_s[Ia] | A.sb_s[Ib]] = mk<R>(acc.x + u.x, acc.y + u.y);
+            const Amp u = A.lam[A.sa_s[Ia] | A.sb_s[Ib]];
+            A.lam[A.sa_s[Ia] | A.sb_s[Ib]] = add_a<Amp>(acc, u);
         } else if (A.lamc) {
-            const cplx<R> u = A.lamc[(size_t)Ib * Da + Ia];
-            A.lamc[(size_t)Ib * Da + Ia] = mk<R>(acc.x + u.x, acc.y + u.y);
+            const Amp u = A.lamc[(size_t)Ib * Da + Ia];
+            A.lamc[(size_t)Ib * Da + Ia] = add_a<Amp>(acc, u);
         }
     }
     // fixed-order block sums over kSameThreads threads
@@ -436,6 +438,29 @@ template <typename R, int K>
 struct AbLayout {
     static constexpr int KP = sizeof(R) == 4 ? (K + 3) & ~3 : (K + 1) & ~1;
 };
+
+// K consecutive real amplitudes from 16-byte-aligned shared memory (K a multiple of
+// 4 floats / 2 doubles).
+template <int K>
+__device__ __forceinline__ void lds_c(const float *p, float (&c)[K]) {
+    static_assert(K % 4 == 0, "real float chunks hold a multiple of 4 rows");
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    #pragma unroll
+    for (int j = 0; j < K / 4; ++j) {
+        const float4 v = q[j];
+        c[4 * j] = v.x; c[4 * j + 1] = v.y; c[4 * j + 2] = v.z; c[4 * j + 3] = v.w;
+    }
+}
+template <int K>
+__device__ __forceinline__ void lds_c(const double *p, double (&c)[K]) {
+    static_assert(K % 2 == 0, "real double chunks hold an even number of rows");
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    #pragma unroll
+    for (int j = 0; j < K / 2; ++j) {
+        const double2 v = q[j];
+        c[2 * j] = v.x; c[2 * j + 1] = v.y;
+    }
+}
 
 // K consecutive complex amplitudes / KP reals from 16-byte-aligned shared memory.
 template <int K>
@@ -491,8 +516,9 @@ __device__ __forceinline__ void lds_r(const double *p, double (&v)[KP]) {
 //                             (orbitals lo..hi-1 of b'_k) -- per (k, pq): folded into
 //                             the staged integrals.
 // The alpha rank table sits in shared memory.
-template <typename R, int K>
-__global__ void __launch_bounds__(kAbThreads) k_sigma_ab(RowArgs<R> A) {
+template <typename Amp, int K>
+__global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
+    using R = real_of<Amp>;
     constexpr int KP = AbLayout<R, K>::KP;
     extern __shared__ __align__(16) unsigned char ab_dyn[];
     __shared__ int s_Jb[kMaxBS], s_t[kMaxBS], s_cb[kMaxBS];
@@ -502,7 +528,7 @@ __global__ void __launch_bounds__(kAbThreads) k_sigma_ab(RowArgs<R> A) {
     __shared__ double red[kAbThreads / 32];
     const SigmaTables<R> &T = A.T;
     const int Ib = blockIdx.x, N = T.N, Da = T.Da, NN = N * N;
-    cplx<R> *part = reinterpret_cast<cplx<R> *>(ab_dyn);          // [Da][K]
+    Amp *part = reinterpret_cast<Amp *>(ab_dyn);                  // [Da][K]
     R *eriS = reinterpret_cast<R *>(part + (size_t)K * Da);       // [N*N][KP]
     R *JtS = eriS + (size_t)NN * KP;                              // [K][N]: (s_k r_k|kk)
     uint16_t *raS = reinterpret_cast<uint16_t *>(JtS + (size_t)K * N);  // [2^N]
@@ -534,15 +560,15 @@ __global__ void __launch_bounds__(kAbThreads) k_sigma_ab(RowArgs<R> A) {
     }
     __syncthreads();
     const int nbs = n_bs;
-    cplx<R> acc[kAbIpt];
+    Amp acc[kAbIpt];
     #pragma unroll
-    for (int t = 0; t < kAbIpt; ++t) acc[t] = mk<R>(0, 0);
+    for (int t = 0; t < kAbIpt; ++t) acc[t] = mka<Amp>(0, 0);
     for (int k0 = 0; k0 < nbs; k0 += K) {
         const int kn = min(K, nbs - k0);
         if (k0) __syncthreads();  // the previous chunk is consumed
         for (int i = threadIdx.x; i < K * Da; i += kAbThreads) {
             const int k = i / Da, c = i - k * Da;
-            part[(size_t)c * K + k] = k < kn ? A.C[(size_t)s_Jb[k0 + k] * Da + c] : mk<R>(0, 0);
+            part[(size_t)c * K + k] = k < kn ? A.C[(size_t)s_Jb[k0 + k] * Da + c] : mka<Amp>(0, 0);
         }
         for (int i = threadIdx.x; i < NN * KP; i += kAbThreads) {
             const int qp = i / KP, k = i - qp * KP, q = qp / N, p = qp - q * N;
@@ -574,15 +600,15 @@ __global__ void __launch_bounds__(kAbThreads) k_sigma_ab(RowArgs<R> A) {
             const int Ia = threadIdx.x + t * kAbThreads;
             if (Ia >= Da) continue;
             const uint32_t a = T.stra[Ia], xa = T.sa[Ia], ea = ~a & T.maskN, ppa = prefix_parity(a);
-            cplx<R> sk[K];
+            Amp sk[K];
             {   // beta singles: same column of the staged rows
-                cplx<R> c[K];
+                Amp c[K];
                 lds_c<K>(part + (size_t)Ia * K, c);
                 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     R v = vbk[k];
                     for (uint32_t o = a; o; o &= o - 1u) v += JtS[k * N + __ffs(o) - 1];
-                    sk[k] = mk<R>(v * c[k].x, v * c[k].y);
+                    sk[k] = scale_a<Amp>(v, c[k]);
                 }
             }
             for (uint32_t o = a; o; o &= o - 1u) {
@@ -599,7 +625,7 @@ __global__ void __launch_bounds__(kAbThreads) k_sigma_ab(RowArgs<R> A) {
                     // alpha bits strictly between p and q
                     const uint32_t s0 = (uint32_t)par(ppa & m0) ^ (uint32_t)(p < q0);
                     const uint32_t s1 = (uint32_t)par(ppa & m1) ^ (uint32_t)(p < q1);
-                    cplx<R> c0[K], c1[K];
+                    Amp c0[K], c1[K];
                     R v0[KP], v1[KP];
                     lds_c<K>(part + (size_t)J0 * K, c0);
                     lds_c<K>(part + (size_t)J1 * K, c1);
@@ -609,32 +635,29 @@ __global__ void __launch_bounds__(kAbThreads) k_sigma_ab(RowArgs<R> A) {
                     for (int k = 0; k < K; ++k) {
                         const R w0 = flip_sign<R>(v0[k], s0);
                         const R w1 = two ? flip_sign<R>(v1[k], s1) : (R)0;
-                        // chained multiply-adds: two per term (float64 states are FP64-pipe bound)
-                        sk[k].x = fma(w1, c1[k].x, fma(w0, c0[k].x, sk[k].x));
-                        sk[k].y = fma(w1, c1[k].y, fma(w0, c0[k].y, sk[k].y));
+                        acc2(sk[k], w0, c0[k], w1, c1[k]);
                     }
                 }
             }
-            cplx<R> tot = acc[t];
+            Amp tot = acc[t];
             #pragma unroll
             for (int k = 0; k < K; ++k) {
                 if (k < kn) {
                     const bool neg = cbk[k] ^ par(xa & Mk[k]);
-                    tot.x += neg ? -sk[k].x : sk[k].x;
-                    tot.y += neg ? -sk[k].y : sk[k].y;
+                    tot = lin2<Amp>((R)1, tot, neg ? (R)-1 : (R)1, sk[k]);
                 }
             }
             acc[t] = tot;
         }
     }
     double e_acc = 0.0;
-    const cplx<R> *row = A.C + (size_t)Ib * Da;
+    const Amp *row = A.C + (size_t)Ib * Da;
     #pragma unroll
     for (int t = 0; t < kAbIpt; ++t) {
         const int Ia = threadIdx.x + t * kAbThreads;
         if (Ia >= Da) continue;
-        const cplx<R> c0 = row[Ia];
-        e_acc += (double)c0.x * (double)acc[t].x + (double)c0.y * (double)acc[t].y;
+        const Amp c0 = row[Ia];
+        e_acc += dre_dot(c0, acc[t]);
         if (A.lam) A.lam[A.sa_s[Ia] | A.sb_s[Ib]] = acc[t];
         else if (A.lamc) A.lamc[(size_t)Ib * Da + Ia] = acc[t];
     }
@@ -650,8 +673,8 @@ __global__ void __launch_bounds__(kAbThreads) k_sigma_ab(RowArgs<R> A) {
 }
 
 // C[Ib][Ia] = psi[sa[Ia] | sb[Ib]]
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_compact(const cplx<R> *__restrict__ psi, cplx<R> *__restrict__ C,
+template <typename A>
+__global__ void __launch_bounds__(kThreads) k_compact(const A *__restrict__ psi, A *__restrict__ C,
                                                       const uint32_t *__restrict__ sa, const uint32_t *__restrict__ sb,
                                                       int Da, uint64_t total) {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < total;
@@ -667,10 +690,7 @@ cudaError_t launch_compact(const void *psi, void *C, int dtype, const uint32_t *
     uint64_t want = (total + kThreads - 1) / kThreads;
     uint64_t cap = (uint64_t)sm_count * 16;
     int grid = (int)(want < cap ? (want ? want : 1) : cap);
-    if (dtype == SV_C64)
-        k_compact<float><<<grid, kThreads, 0, st>>>((const float2 *)psi, (float2 *)C, sa, sb, Da, total);
-    else
-        k_compact<double><<<grid, kThreads, 0, st>>>((const double2 *)psi, (double2 *)C, sa, sb, Da, total);
+    SV_DISPATCH_AMP(dtype, k_compact<A><<<grid, kThreads, 0, st>>>((const A *)psi, (A *)C, sa, sb, Da, total));
     return cudaGetLastError();
 }
 
@@ -683,15 +703,16 @@ struct RowTables {
     const void *W2 = nullptr;  // pair-indexed same-spin integrals (split form)
 };
 
-template <typename R>
-static RowArgs<R> row_args(const void *C, void *lam, void *lamc, int n, const RowTables &T, const double *hdiag,
-                           const double *Jp, double e_shift, double *partial) {
-    RowArgs<R> A;
+template <typename Amp>
+static RowArgs<Amp> row_args(const void *C, void *lam, void *lamc, int n, const RowTables &T, const double *hdiag,
+                             const double *Jp, double e_shift, double *partial) {
+    using R = real_of<Amp>;
+    RowArgs<Amp> A;
     A.T.sa = T.sa; A.T.sb = T.sb; A.T.stra = T.stra; A.T.strb = T.strb; A.T.ra = T.ra; A.T.rb = T.rb;
     A.T.eri = (const R *)T.eri; A.T.hm = (const R *)T.hm; A.T.Dt = (const R *)T.Dt; A.T.Jt = (const R *)T.Jt;
     A.T.hdiag = hdiag; A.T.Jp = Jp; A.T.e_shift = e_shift;
     A.T.N = T.N; A.T.n = n; A.T.Da = T.Da; A.T.maskN = (1u << T.N) - 1u;
-    A.C = (const cplx<R> *)C; A.lam = (cplx<R> *)lam; A.lamc = (cplx<R> *)lamc; A.sa_s = T.sa_s; A.sb_s = T.sb_s;
+    A.C = (const Amp *)C; A.lam = (Amp *)lam; A.lamc = (Amp *)lamc; A.sa_s = T.sa_s; A.sb_s = T.sb_s;
     A.partial = partial; A.Db = T.Db; A.W2 = (const R *)T.W2;
     return A;
 }
@@ -700,8 +721,8 @@ constexpr size_t kAbSmemCap = 225 * 1024;  // dynamic shared memory a split kern
 
 // Dynamic shared memory of k_sigma_ab for K staged rows, and of k_sigma_same.
 static size_t ab_smem(int dtype, int K, const RowTables &T) {
-    const size_t amp = dtype == SV_C64 ? 8 : 16, real = amp / 2;
-    const size_t KP = dtype == SV_C64 ? (size_t)((K + 3) & ~3) : (size_t)((K + 1) & ~1);
+    const size_t amp = amp_size(dtype), real = single_prec(dtype) ? 4 : 8;
+    const size_t KP = real == 4 ? (size_t)((K + 3) & ~3) : (size_t)((K + 1) & ~1);
     return (size_t)K * T.Da * amp + (size_t)T.N * T.N * KP * real + (size_t)K * T.N * real + ((size_t)2 << T.N);
 }
 
@@ -711,12 +732,16 @@ static size_t ab_smem(int dtype, int K, const RowTables &T) {
 constexpr size_t kSameSmemCap = 203 * 1024;
 
 static size_t same_smem(int dtype, const RowTables &T, bool ra_in) {
-    const size_t amp = dtype == SV_C64 ? 8 : 16, real = amp / 2, NP = (size_t)T.N * (T.N - 1) / 2;
+    const size_t amp = amp_size(dtype), real = single_prec(dtype) ? 4 : 8, NP = (size_t)T.N * (T.N - 1) / 2;
     return (size_t)T.Da * amp + NP * NP * real + (size_t)T.N * T.N * T.N * real + (ra_in ? ((size_t)2 << T.N) : 0);
 }
 
-static const int kChunksC64[] = {2, 4, 6, 8};
-static const int kChunksC128[] = {1, 2, 3, 4};
+// Compiled chunk sizes per state type: a column of K staged amplitudes is a whole
+// number of 16-byte words.
+static const int kChunks[4][4] = {{2, 4, 6, 8},      // complex64
+                                  {1, 2, 3, 4},      // complex128
+                                  {4, 8, 12, 16},    // real float
+                                  {2, 4, 6, 8}};     // real double
 
 // Rows staged per chunk by k_sigma_ab, 0 when the split form does not fit (the
 // single-kernel form runs instead).  `want` > 0 asks for that chunk size (taken when
@@ -725,7 +750,7 @@ static const int kChunksC128[] = {1, 2, 3, 4};
 int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want) {
     if (T.Da > kAbThreads * kAbIpt || T.Db < 1 || T.N < 2) return 0;
     if (same_smem(dtype, T, false) > kSameSmemCap) return 0;
-    const int *sizes = dtype == SV_C64 ? kChunksC64 : kChunksC128;
+    const int *sizes = kChunks[dtype & 3];
     if (want > 0) {
         for (int i = 3; i >= 0; --i)
             if (sizes[i] <= want && ab_smem(dtype, sizes[i], T) <= kAbSmemCap) return sizes[i];
@@ -745,55 +770,56 @@ int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want) {
     return best;
 }
 
-template <typename R, int K>
-static cudaError_t launch_ab(const RowArgs<R> &A, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_sigma_ab<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+const int *sigma_ab_sizes(int dtype) { return kChunks[dtype & 3]; }
+
+template <typename Amp, int K>
+static cudaError_t launch_ab(const RowArgs<Amp> &A, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_sigma_ab<Amp, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sigma_ab<R, K><<<A.Db, kAbThreads, smem, st>>>(A);
+    k_sigma_ab<Amp, K><<<A.Db, kAbThreads, smem, st>>>(A);
     return cudaGetLastError();
 }
 
-template <typename R>
-static cudaError_t launch_ab_k(const RowArgs<R> &A, int K, size_t smem, cudaStream_t st);
-template <>
-cudaError_t launch_ab_k<float>(const RowArgs<float> &A, int K, size_t smem, cudaStream_t st) {
-    switch (K) {
-        case 2: return launch_ab<float, 2>(A, smem, st);
-        case 4: return launch_ab<float, 4>(A, smem, st);
-        case 6: return launch_ab<float, 6>(A, smem, st);
-        case 8: return launch_ab<float, 8>(A, smem, st);
-    }
-    return cudaErrorInvalidValue;
-}
-template <>
-cudaError_t launch_ab_k<double>(const RowArgs<double> &A, int K, size_t smem, cudaStream_t st) {
-    switch (K) {
-        case 1: return launch_ab<double, 1>(A, smem, st);
-        case 2: return launch_ab<double, 2>(A, smem, st);
-        case 3: return launch_ab<double, 3>(A, smem, st);
-        case 4: return launch_ab<double, 4>(A, smem, st);
-    }
+template <typename Amp, int K0, int K1, int K2, int K3>
+static cudaError_t launch_ab_k4(const RowArgs<Amp> &A, int K, size_t smem, cudaStream_t st) {
+    if (K == K0) return launch_ab<Amp, K0>(A, smem, st);
+    if (K == K1) return launch_ab<Amp, K1>(A, smem, st);
+    if (K == K2) return launch_ab<Amp, K2>(A, smem, st);
+    if (K == K3) return launch_ab<Amp, K3>(A, smem, st);
     return cudaErrorInvalidValue;
 }
 
-template <typename R>
-static cudaError_t launch_rows_t(const RowArgs<R> &A, const RowTables &T, int dtype, int K, cudaStream_t st) {
+static cudaError_t launch_ab_k(const RowArgs<float2> &A, int K, size_t smem, cudaStream_t st) {
+    return launch_ab_k4<float2, 2, 4, 6, 8>(A, K, smem, st);
+}
+static cudaError_t launch_ab_k(const RowArgs<double2> &A, int K, size_t smem, cudaStream_t st) {
+    return launch_ab_k4<double2, 1, 2, 3, 4>(A, K, smem, st);
+}
+static cudaError_t launch_ab_k(const RowArgs<float> &A, int K, size_t smem, cudaStream_t st) {
+    return launch_ab_k4<float, 4, 8, 12, 16>(A, K, smem, st);
+}
+static cudaError_t launch_ab_k(const RowArgs<double> &A, int K, size_t smem, cudaStream_t st) {
+    return launch_ab_k4<double, 2, 4, 6, 8>(A, K, smem, st);
+}
+
+template <typename Amp>
+static cudaError_t launch_rows_t(const RowArgs<Amp> &A, const RowTables &T, int dtype, int K, cudaStream_t st) {
     if (K == 0) {
-        k_sigma_rows<R><<<T.Db, kRowThreads, 0, st>>>(A);
+        k_sigma_rows<Amp><<<T.Db, kRowThreads, 0, st>>>(A);
         return cudaGetLastError();
     }
-    cudaError_t e = launch_ab_k<R>(A, K, ab_smem(dtype, K, T), st);
+    cudaError_t e = launch_ab_k(A, K, ab_smem(dtype, K, T), st);
     if (e != cudaSuccess) return e;
     if (same_smem(dtype, T, true) <= kSameSmemCap) {
         const size_t smem = same_smem(dtype, T, true);
-        e = cudaFuncSetAttribute(k_sigma_same<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_sigma_same<Amp, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_sigma_same<R, true><<<T.Db, kSameThreads, smem, st>>>(A);
+        k_sigma_same<Amp, true><<<T.Db, kSameThreads, smem, st>>>(A);
     } else {
         const size_t smem = same_smem(dtype, T, false);
-        e = cudaFuncSetAttribute(k_sigma_same<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_sigma_same<Amp, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_sigma_same<R, false><<<T.Db, kSameThreads, smem, st>>>(A);
+        k_sigma_same<Amp, false><<<T.Db, kSameThreads, smem, st>>>(A);
     }
     return cudaGetLastError();
 }
@@ -802,9 +828,10 @@ static cudaError_t launch_rows_t(const RowArgs<R> &A, const RowTables &T, int dt
 // partial must hold 3 * Db doubles (rows: energy, norm, alpha-beta energy share).
 cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &T, const double *hdiag,
                               const double *Jp, double e_shift, double *partial, int K, cudaStream_t st) {
-    if (dtype == SV_C64)
-        return launch_rows_t<float>(row_args<float>(C, lam, lamc, n, T, hdiag, Jp, e_shift, partial), T, dtype, K, st);
-    return launch_rows_t<double>(row_args<double>(C, lam, lamc, n, T, hdiag, Jp, e_shift, partial), T, dtype, K, st);
+    cudaError_t e = cudaErrorInvalidValue;
+    SV_DISPATCH_AMP(dtype, e = launch_rows_t<A>(row_args<A>(C, lam, lamc, n, T, hdiag, Jp, e_shift, partial), T, dtype,
+                                                K, st));
+    return e;
 }
 
 }  // namespace svk

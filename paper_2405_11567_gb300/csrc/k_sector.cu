@@ -95,10 +95,11 @@ __global__ void __launch_bounds__(kThreads) k_build_lists(const ListOp *__restri
 
 // psi <- exp(theta G) psi over the op's pairs: block r takes beta entries r, r + grid,
 // ..., its threads the alpha entries.
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_rotate_l(cplx<R> *__restrict__ psi, const uint32_t *__restrict__ al,
+template <typename A>
+__global__ void __launch_bounds__(kThreads) k_rotate_l(A *__restrict__ psi, const uint32_t *__restrict__ al,
                                                        int na_l, const uint32_t *__restrict__ bl, int nb_l, int Da,
-                                                       R c, R sn) {
+                                                       real_of<A> c, real_of<A> sn) {
+    using R = real_of<A>;
     for (int r = blockIdx.x; r < nb_l; r += gridDim.x) {
         const uint32_t eb = bl[r];
         const size_t rowI = (size_t)(eb & 0x7FFFu) * Da, rowJ = (size_t)(eb >> 16) * Da;
@@ -107,20 +108,21 @@ __global__ void __launch_bounds__(kThreads) k_rotate_l(cplx<R> *__restrict__ psi
             const uint32_t ea = al[i];
             const size_t I = rowI + (ea & 0x7FFFu), J = rowJ + (ea >> 16);
             const R ss = ((ea & 0x8000u) ^ sgb) ? -sn : sn;
-            const cplx<R> u = psi[I], v = psi[J];
-            psi[I] = mk<R>(c * u.x - ss * v.x, c * u.y - ss * v.y);
-            psi[J] = mk<R>(c * v.x + ss * u.x, c * v.y + ss * u.y);
+            const A u = psi[I], v = psi[J];
+            psi[I] = lin2<A>(c, u, -ss, v);
+            psi[J] = lin2<A>(c, v, ss, u);
         }
     }
 }
 
 // Adjoint step over the op's pairs: the gradient term, then U^dagger on psi and
 // lambda; one float64 partial per block (fixed order).
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_adjoint_l(cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam,
+template <typename A>
+__global__ void __launch_bounds__(kThreads) k_adjoint_l(A *__restrict__ psi, A *__restrict__ lam,
                                                         const uint32_t *__restrict__ al, int na_l,
-                                                        const uint32_t *__restrict__ bl, int nb_l, int Da, R c, R sn,
-                                                        double *__restrict__ partial) {
+                                                        const uint32_t *__restrict__ bl, int nb_l, int Da,
+                                                        real_of<A> c, real_of<A> sn, double *__restrict__ partial) {
+    using R = real_of<A>;
     __shared__ double red[kThreads / 32];
     double acc = 0.0;
     for (int r = blockIdx.x; r < nb_l; r += gridDim.x) {
@@ -132,14 +134,14 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_l(cplx<R> *__restrict__ ps
             const uint32_t ea = al[i];
             const size_t I = rowI + (ea & 0x7FFFu), J = rowJ + (ea >> 16);
             const bool neg = (ea & 0x8000u) ^ sgb;
-            const cplx<R> u = psi[I], v = psi[J], lu = lam[I], lv = lam[J];
-            const R ti = (lv.x * u.x + lv.y * u.y) - (lu.x * v.x + lu.y * v.y);
+            const A u = psi[I], v = psi[J], lu = lam[I], lv = lam[J];
+            const R ti = re_dot(lv, u) - re_dot(lu, v);
             t += neg ? -ti : ti;
             const R ss = neg ? -sn : sn;
-            psi[I] = mk<R>(c * u.x + ss * v.x, c * u.y + ss * v.y);
-            psi[J] = mk<R>(c * v.x - ss * u.x, c * v.y - ss * u.y);
-            lam[I] = mk<R>(c * lu.x + ss * lv.x, c * lu.y + ss * lv.y);
-            lam[J] = mk<R>(c * lv.x - ss * lu.x, c * lv.y - ss * lu.y);
+            psi[I] = lin2<A>(c, u, ss, v);
+            psi[J] = lin2<A>(c, v, -ss, u);
+            lam[I] = lin2<A>(c, lu, ss, lv);
+            lam[J] = lin2<A>(c, lv, -ss, lu);
         }
         acc += (double)t;
     }
@@ -159,9 +161,10 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_l(cplx<R> *__restrict__ ps
 // (j = 2p + sigma), alpha pairs, beta pairs.  Each warp's sum goes to its own
 // shared slot; after each row the block adds the slots in warp order into float64
 // running sums, written to partial[e][blockIdx.x] at the end: fixed-order sums.
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_rdm_rows(const cplx<R> *__restrict__ C, SectTabs T, int N,
+template <typename A>
+__global__ void __launch_bounds__(kThreads) k_rdm_rows(const A *__restrict__ C, SectTabs T, int N,
                                                        double *__restrict__ partial) {
+    using R = real_of<A>;
     extern __shared__ double rdm_s[];  // [2 n_el] running sums, then [kThreads/32][2 n_el] warp slots
     const int n = 2 * N, npair = N * (N - 1) / 2, n_el = 1 + n + 2 * npair, W = 2 * n_el;
     double *acc = rdm_s, *slot = rdm_s + W;
@@ -171,14 +174,14 @@ __global__ void __launch_bounds__(kThreads) k_rdm_rows(const cplx<R> *__restrict
     const uint32_t maskN = (1u << N) - 1u;
     for (int Ib = blockIdx.x; Ib < T.Db; Ib += gridDim.x) {
         const uint32_t b = T.strb[Ib], xb = T.sb[Ib];
-        const cplx<R> *row = C + (size_t)Ib * T.Da;
+        const A *row = C + (size_t)Ib * T.Da;
         // norm and alpha occupations
         R nrm = 0, occ[16];
         #pragma unroll
         for (int p = 0; p < 16; ++p) occ[p] = 0;
         for (int Ia = threadIdx.x; Ia < T.Da; Ia += blockDim.x) {
-            const cplx<R> c = row[Ia];
-            const R w = c.x * c.x + c.y * c.y;
+            const A c = row[Ia];
+            const R w = re_dot(c, c);
             const uint32_t a = T.stra[Ia];
             nrm += w;
             #pragma unroll
@@ -213,17 +216,17 @@ __global__ void __launch_bounds__(kThreads) k_rdm_rows(const cplx<R> *__restrict
                         for (int Ia = threadIdx.x; Ia < T.Da; Ia += blockDim.x) {
                             const uint32_t a = T.stra[Ia];
                             if ((a & m) != f) continue;
-                            const cplx<R> u = row[Ia], v = row[T.ra[a ^ m]];
-                            R ar = v.x * u.x + v.y * u.y, ai = v.x * u.y - v.y * u.x;  // conj(v) u
+                            const A u = row[Ia], v = row[T.ra[a ^ m]];
+                            R ar = re_dot(v, u), ai = im_dot(v, u);  // conj(v) u
                             if (par((T.sa[Ia] | xb) & bm)) { ar = -ar; ai = -ai; }
                             re += ar;
                             im += ai;
                         }
                     } else if ((b & m) == f) {
-                        const cplx<R> *row2 = C + (size_t)T.rb[b ^ m] * T.Da;
+                        const A *row2 = C + (size_t)T.rb[b ^ m] * T.Da;
                         for (int Ia = threadIdx.x; Ia < T.Da; Ia += blockDim.x) {
-                            const cplx<R> u = row[Ia], v = row2[Ia];
-                            R ar = v.x * u.x + v.y * u.y, ai = v.x * u.y - v.y * u.x;
+                            const A u = row[Ia], v = row2[Ia];
+                            R ar = re_dot(v, u), ai = im_dot(v, u);
                             if (par((T.sa[Ia] | xb) & bm)) { ar = -ar; ai = -ai; }
                             re += ar;
                             im += ai;
@@ -249,11 +252,11 @@ __global__ void __launch_bounds__(kThreads) k_rdm_rows(const cplx<R> *__restrict
 }
 
 // out[i] = C[idx[i]] or 0 when idx[i] is 0xFFFFFFFF (a basis state outside the sector)
-template <typename R>
-__global__ void k_gather_c(const cplx<R> *__restrict__ psi, const uint32_t *__restrict__ idx, int count,
-                           cplx<R> *__restrict__ out) {
+template <typename A>
+__global__ void k_gather_c(const A *__restrict__ psi, const uint32_t *__restrict__ idx, int count,
+                           A *__restrict__ out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
-        out[i] = idx[i] == 0xFFFFFFFFu ? mk<R>(0, 0) : psi[idx[i]];
+        out[i] = idx[i] == 0xFFFFFFFFu ? mka<A>(0, 0) : psi[idx[i]];
 }
 
 // ---------------------------------------------------------------- launchers
@@ -326,22 +329,16 @@ cudaError_t launch_build_lists(const void *ops, int n_ops, const uint32_t *sa, c
 cudaError_t launch_rotate_l(void *psi, int dtype, const uint32_t *al, int na_l, const uint32_t *bl, int nb_l, int Da,
                             double c, double s, int grid, cudaStream_t st) {
     if (na_l <= 0 || nb_l <= 0) return cudaSuccess;
-    if (dtype == SV_C64)
-        k_rotate_l<float><<<grid, kThreads, 0, st>>>((float2 *)psi, al, na_l, bl, nb_l, Da, (float)c, (float)s);
-    else
-        k_rotate_l<double><<<grid, kThreads, 0, st>>>((double2 *)psi, al, na_l, bl, nb_l, Da, c, s);
+    SV_DISPATCH_AMP(dtype, k_rotate_l<A><<<grid, kThreads, 0, st>>>((A *)psi, al, na_l, bl, nb_l, Da,
+                                                                     (real_of<A>)c, (real_of<A>)s));
     return cudaGetLastError();
 }
 
 // partial: grid doubles (every block writes its entry, zero when it has no rows).
 cudaError_t launch_adjoint_l(void *psi, void *lam, int dtype, const uint32_t *al, int na_l, const uint32_t *bl,
                              int nb_l, int Da, double c, double s, int grid, double *partial, cudaStream_t st) {
-    if (dtype == SV_C64)
-        k_adjoint_l<float><<<grid, kThreads, 0, st>>>((float2 *)psi, (float2 *)lam, al, na_l, bl, nb_l, Da, (float)c,
-                                                      (float)s, partial);
-    else
-        k_adjoint_l<double><<<grid, kThreads, 0, st>>>((double2 *)psi, (double2 *)lam, al, na_l, bl, nb_l, Da, c, s,
-                                                       partial);
+    SV_DISPATCH_AMP(dtype, k_adjoint_l<A><<<grid, kThreads, 0, st>>>((A *)psi, (A *)lam, al, na_l, bl, nb_l, Da,
+                                                                      (real_of<A>)c, (real_of<A>)s, partial));
     return cudaGetLastError();
 }
 
@@ -358,8 +355,7 @@ cudaError_t launch_rdm_rows(const void *C, int dtype, int n, const uint32_t *sa,
                             int Db, int grid, double *partial, cudaStream_t st) {
     SectTabs T = tabs(sa, sb, stra, strb, ra, rb, Da, Db);
     const size_t smem = sizeof(double) * 2 * rdm_rows_elements(n) * (1 + kThreads / 32);  // <= 40 KB (n <= 32)
-    if (dtype == SV_C64) k_rdm_rows<float><<<grid, kThreads, smem, st>>>((const float2 *)C, T, n / 2, partial);
-    else k_rdm_rows<double><<<grid, kThreads, smem, st>>>((const double2 *)C, T, n / 2, partial);
+    SV_DISPATCH_AMP(dtype, k_rdm_rows<A><<<grid, kThreads, smem, st>>>((const A *)C, T, n / 2, partial));
     return cudaGetLastError();
 }
 
@@ -367,8 +363,7 @@ cudaError_t launch_gather_c(const void *psi, int dtype, const uint32_t *idx, int
     if (count <= 0) return cudaSuccess;
     int grid = (count + kThreads - 1) / kThreads;
     if (grid > 1024) grid = 1024;
-    if (dtype == SV_C64) k_gather_c<float><<<grid, kThreads, 0, st>>>((const float2 *)psi, idx, count, (float2 *)out);
-    else k_gather_c<double><<<grid, kThreads, 0, st>>>((const double2 *)psi, idx, count, (double2 *)out);
+    SV_DISPATCH_AMP(dtype, k_gather_c<A><<<grid, kThreads, 0, st>>>((const A *)psi, idx, count, (A *)out));
     return cudaGetLastError();
 }
 

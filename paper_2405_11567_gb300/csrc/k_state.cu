@@ -51,9 +51,9 @@ __device__ __forceinline__ uint32_t pair_index(uint32_t k, const OpArgs &a) {
 
 // ---------------------------------------------------------------- preparation
 
-template <typename R>
-__global__ void k_set_basis(cplx<R> *psi, uint32_t x) {
-    psi[x] = mk<R>(R(1), R(0));
+template <typename A>
+__global__ void k_set_basis(A *psi, uint32_t x) {
+    psi[x] = mka<A>(real_of<A>(1), real_of<A>(0));
 }
 
 // ---------------------------------------------------------------- vector access
@@ -97,10 +97,54 @@ template <int V> struct VecIO<double, V> {
     }
 };
 
-template <typename R, int V>
-__device__ __forceinline__ void ld_vec(const cplx<R> *__restrict__ p, cplx<R> (&v)[V]) { VecIO<R, V>::ld(p, v); }
-template <typename R, int V>
-__device__ __forceinline__ void st_vec(cplx<R> *__restrict__ p, const cplx<R> (&v)[V]) { VecIO<R, V>::st(p, v); }
+// Real amplitudes: V floats as one float2 / float4, V doubles as double2 words.
+template <int V> struct VecIOr;
+template <> struct VecIOr<1> {
+    template <typename T> static __device__ __forceinline__ void ld(const T *__restrict__ p, T (&v)[1]) { v[0] = p[0]; }
+    template <typename T> static __device__ __forceinline__ void st(T *__restrict__ p, const T (&v)[1]) { p[0] = v[0]; }
+};
+template <> struct VecIOr<2> {
+    static __device__ __forceinline__ void ld(const float *__restrict__ p, float (&v)[2]) {
+        const float2 f = *reinterpret_cast<const float2 *>(p);
+        v[0] = f.x; v[1] = f.y;
+    }
+    static __device__ __forceinline__ void st(float *__restrict__ p, const float (&v)[2]) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    }
+    static __device__ __forceinline__ void ld(const double *__restrict__ p, double (&v)[2]) {
+        const double2 f = *reinterpret_cast<const double2 *>(p);
+        v[0] = f.x; v[1] = f.y;
+    }
+    static __device__ __forceinline__ void st(double *__restrict__ p, const double (&v)[2]) {
+        *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    }
+};
+template <> struct VecIOr<4> {
+    static __device__ __forceinline__ void ld(const float *__restrict__ p, float (&v)[4]) {
+        const float4 f = *reinterpret_cast<const float4 *>(p);
+        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+    }
+    static __device__ __forceinline__ void st(float *__restrict__ p, const float (&v)[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    static __device__ __forceinline__ void ld(const double *__restrict__ p, double (&v)[4]) {
+        const double2 f = reinterpret_cast<const double2 *>(p)[0], g = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = f.x; v[1] = f.y; v[2] = g.x; v[3] = g.y;
+    }
+    static __device__ __forceinline__ void st(double *__restrict__ p, const double (&v)[4]) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    }
+};
+
+template <int V> __device__ __forceinline__ void ld_vec(const float2 *__restrict__ p, float2 (&v)[V]) { VecIO<float, V>::ld(p, v); }
+template <int V> __device__ __forceinline__ void ld_vec(const double2 *__restrict__ p, double2 (&v)[V]) { VecIO<double, V>::ld(p, v); }
+template <int V> __device__ __forceinline__ void ld_vec(const float *__restrict__ p, float (&v)[V]) { VecIOr<V>::ld(p, v); }
+template <int V> __device__ __forceinline__ void ld_vec(const double *__restrict__ p, double (&v)[V]) { VecIOr<V>::ld(p, v); }
+template <int V> __device__ __forceinline__ void st_vec(float2 *__restrict__ p, const float2 (&v)[V]) { VecIO<float, V>::st(p, v); }
+template <int V> __device__ __forceinline__ void st_vec(double2 *__restrict__ p, const double2 (&v)[V]) { VecIO<double, V>::st(p, v); }
+template <int V> __device__ __forceinline__ void st_vec(float *__restrict__ p, const float (&v)[V]) { VecIOr<V>::st(p, v); }
+template <int V> __device__ __forceinline__ void st_vec(double *__restrict__ p, const double (&v)[V]) { VecIOr<V>::st(p, v); }
 
 // ---------------------------------------------------------------- forward rotation
 
@@ -109,80 +153,82 @@ __device__ __forceinline__ void st_vec(cplx<R> *__restrict__ p, const cplx<R> (&
 // and the sign is the same across the group only if no sign-mask bit lies below
 // log2(V) -- it is therefore evaluated per amplitude.  Two groups per iteration keep
 // four independent vector loads in flight per thread.
-template <typename R, int NB, int V>
-__global__ void __launch_bounds__(kThreads) k_rotate(cplx<R> *__restrict__ psi, uint32_t ngroups, OpArgs a) {
+template <typename A, int NB, int V>
+__global__ void __launch_bounds__(kThreads) k_rotate(A *__restrict__ psi, uint32_t ngroups, OpArgs a) {
+    using R = real_of<A>;
     const R c = (R)a.c, sn = (R)a.s;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += 2 * stride) {
         const uint32_t g2 = g + stride;
         const bool two = g2 < ngroups;
         const uint32_t x = pair_index<NB>(g * V, a), x2 = two ? pair_index<NB>(g2 * V, a) : x;
-        cplx<R> u[V], v[V], u2[V], v2[V];
-        ld_vec<R, V>(psi + x, u);
-        ld_vec<R, V>(psi + (x ^ a.m), v);
+        A u[V], v[V], u2[V], v2[V];
+        ld_vec<V>(psi + x, u);
+        ld_vec<V>(psi + (x ^ a.m), v);
         if (two) {
-            ld_vec<R, V>(psi + x2, u2);
-            ld_vec<R, V>(psi + (x2 ^ a.m), v2);
+            ld_vec<V>(psi + x2, u2);
+            ld_vec<V>(psi + (x2 ^ a.m), v2);
         }
         #pragma unroll
         for (int i = 0; i < V; ++i) {
             const R ss = (__popc((x + i) & a.sm) & 1) ? -sn : sn;
-            cplx<R> p = u[i], q = v[i];
-            u[i] = mk<R>(c * p.x - ss * q.x, c * p.y - ss * q.y);
-            v[i] = mk<R>(c * q.x + ss * p.x, c * q.y + ss * p.y);
+            const A p = u[i], q = v[i];
+            u[i] = lin2<A>(c, p, -ss, q);
+            v[i] = lin2<A>(c, q, ss, p);
         }
-        st_vec<R, V>(psi + x, u);
-        st_vec<R, V>(psi + (x ^ a.m), v);
+        st_vec<V>(psi + x, u);
+        st_vec<V>(psi + (x ^ a.m), v);
         if (two) {
             #pragma unroll
             for (int i = 0; i < V; ++i) {
                 const R ss = (__popc((x2 + i) & a.sm) & 1) ? -sn : sn;
-                cplx<R> p = u2[i], q = v2[i];
-                u2[i] = mk<R>(c * p.x - ss * q.x, c * p.y - ss * q.y);
-                v2[i] = mk<R>(c * q.x + ss * p.x, c * q.y + ss * p.y);
+                const A p = u2[i], q = v2[i];
+                u2[i] = lin2<A>(c, p, -ss, q);
+                v2[i] = lin2<A>(c, q, ss, p);
             }
-            st_vec<R, V>(psi + x2, u2);
-            st_vec<R, V>(psi + (x2 ^ a.m), v2);
+            st_vec<V>(psi + x2, u2);
+            st_vec<V>(psi + (x2 ^ a.m), v2);
         }
     }
 }
 
 // ---------------------------------------------------------------- adjoint step
 
-template <typename R, int NB, int V>
-__global__ void __launch_bounds__(kThreads) k_adjoint(cplx<R> *__restrict__ psi, cplx<R> *__restrict__ lam,
+template <typename A, int NB, int V>
+__global__ void __launch_bounds__(kThreads) k_adjoint(A *__restrict__ psi, A *__restrict__ lam,
                                                       uint32_t ngroups, OpArgs a, double *__restrict__ partial) {
+    using R = real_of<A>;
     __shared__ double red[kThreads / 32];
     const R c = (R)a.c, sn = (R)a.s;
     const uint32_t stride = gridDim.x * blockDim.x;
     double acc = 0.0;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
         const uint32_t x = pair_index<NB>(g * V, a), xp = x ^ a.m;
-        cplx<R> u[V], v[V], lu[V], lv[V];
-        ld_vec<R, V>(psi + x, u);
-        ld_vec<R, V>(psi + xp, v);
-        ld_vec<R, V>(lam + x, lu);
-        ld_vec<R, V>(lam + xp, lv);
+        A u[V], v[V], lu[V], lv[V];
+        ld_vec<V>(psi + x, u);
+        ld_vec<V>(psi + xp, v);
+        ld_vec<V>(lam + x, lu);
+        ld_vec<V>(lam + xp, lv);
         R t = 0;
         #pragma unroll
         for (int i = 0; i < V; ++i) {
             const bool neg = __popc((x + i) & a.sm) & 1;
             // <lambda|G psi> on the pair: conj(lu) (-s v) + conj(lv) (s u); real part
-            R ti = (lv[i].x * u[i].x + lv[i].y * u[i].y) - (lu[i].x * v[i].x + lu[i].y * v[i].y);
+            const R ti = re_dot(lv[i], u[i]) - re_dot(lu[i], v[i]);
             t += neg ? -ti : ti;
             // U^dagger: psi'[x] = c u + s sn v ; psi'[x'] = c v - s sn u  (lambda alike)
             const R ss = neg ? -sn : sn;
-            cplx<R> p = u[i], q = v[i], lp = lu[i], lq = lv[i];
-            u[i] = mk<R>(c * p.x + ss * q.x, c * p.y + ss * q.y);
-            v[i] = mk<R>(c * q.x - ss * p.x, c * q.y - ss * p.y);
-            lu[i] = mk<R>(c * lp.x + ss * lq.x, c * lp.y + ss * lq.y);
-            lv[i] = mk<R>(c * lq.x - ss * lp.x, c * lq.y - ss * lp.y);
+            const A p = u[i], q = v[i], lp = lu[i], lq = lv[i];
+            u[i] = lin2<A>(c, p, ss, q);
+            v[i] = lin2<A>(c, q, -ss, p);
+            lu[i] = lin2<A>(c, lp, ss, lq);
+            lv[i] = lin2<A>(c, lq, -ss, lp);
         }
         acc += (double)t;
-        st_vec<R, V>(psi + x, u);
-        st_vec<R, V>(psi + xp, v);
-        st_vec<R, V>(lam + x, lu);
-        st_vec<R, V>(lam + xp, lv);
+        st_vec<V>(psi + x, u);
+        st_vec<V>(psi + xp, v);
+        st_vec<V>(lam + x, lu);
+        st_vec<V>(lam + xp, lv);
     }
     double s = block_sum(acc, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -196,8 +242,8 @@ struct PermArgs {
     int n;
 };
 
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_permute(const cplx<R> *__restrict__ in, cplx<R> *__restrict__ out,
+template <typename A>
+__global__ void __launch_bounds__(kThreads) k_permute(const A *__restrict__ in, A *__restrict__ out,
                                                       uint64_t dim, PermArgs p) {
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < dim; t += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t v = (uint32_t)t;
@@ -214,17 +260,16 @@ cudaError_t launch_permute(const void *in, void *out, int dtype, int n, const in
     uint64_t dim = 1ull << n;
     uint64_t want = (dim + kThreads - 1) / kThreads, cap = (uint64_t)sm_count * 16;
     int grid = (int)(want < cap ? want : cap);
-    if (dtype == SV_C64) k_permute<float><<<grid, kThreads, 0, st>>>((const float2 *)in, (float2 *)out, dim, p);
-    else k_permute<double><<<grid, kThreads, 0, st>>>((const double2 *)in, (double2 *)out, dim, p);
+    SV_DISPATCH_AMP(dtype, k_permute<A><<<grid, kThreads, 0, st>>>((const A *)in, (A *)out, dim, p));
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- sampling
 
 // out[i] = psi[addr[i]] (addresses already in the storage layout)
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_gather(const cplx<R> *__restrict__ psi, const uint32_t *__restrict__ addr,
-                                                     int count, cplx<R> *__restrict__ out) {
+template <typename A>
+__global__ void __launch_bounds__(kThreads) k_gather(const A *__restrict__ psi, const uint32_t *__restrict__ addr,
+                                                     int count, A *__restrict__ out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) out[i] = psi[addr[i]];
 }
 
@@ -232,8 +277,7 @@ cudaError_t launch_gather(const void *psi, int dtype, const uint32_t *addr, int 
     if (count <= 0) return cudaSuccess;
     int grid = (count + kThreads - 1) / kThreads;
     if (grid > 1024) grid = 1024;
-    if (dtype == SV_C64) k_gather<float><<<grid, kThreads, 0, st>>>((const float2 *)psi, addr, count, (float2 *)out);
-    else k_gather<double><<<grid, kThreads, 0, st>>>((const double2 *)psi, addr, count, (double2 *)out);
+    SV_DISPATCH_AMP(dtype, k_gather<A><<<grid, kThreads, 0, st>>>((const A *)psi, addr, count, (A *)out));
     return cudaGetLastError();
 }
 
@@ -262,50 +306,44 @@ int rotate_grid(uint64_t npairs, int sm_count, int bps) {
 }
 
 cudaError_t launch_set_basis(void *psi, int dtype, uint32_t x, cudaStream_t st) {
-    if (dtype == SV_C64) k_set_basis<float><<<1, 1, 0, st>>>((float2 *)psi, x);
-    else k_set_basis<double><<<1, 1, 0, st>>>((double2 *)psi, x);
+    SV_DISPATCH_AMP(dtype, k_set_basis<A><<<1, 1, 0, st>>>((A *)psi, x));
     return cudaGetLastError();
 }
 
 // Vector width: as many consecutive amplitudes as fit in 32 bytes, limited by the
 // lowest mask position (the pairs of a group must be consecutive on both sides).
 static int vec_log2(int dtype, const OpDesc &d, int n) {
-    int vmax = dtype == SV_C64 ? 2 : 1;
+    int vmax = dtype == SV_C128 ? 1 : 2;  // 32-byte words (16 for real floats)
     int v = d.pos[0] < vmax ? d.pos[0] : vmax;
     while (v > 0 && (n - d.nbits) < v) --v;
     return v;
 }
 
-template <typename R, int NB>
+template <typename A, int NB>
 static void rot_v(void *psi, int v, uint32_t npairs, OpArgs a, int sm_count, int bps, cudaStream_t st) {
     uint32_t ng = npairs >> v;
     int grid = rotate_grid((ng + 1) / 2, sm_count, bps);
-    if (v == 0) k_rotate<R, NB, 1><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, ng, a);
-    else if (v == 1) k_rotate<R, NB, 2><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, ng, a);
-    else k_rotate<R, NB, 4><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, ng, a);
+    if (v == 0) k_rotate<A, NB, 1><<<grid, kThreads, 0, st>>>((A *)psi, ng, a);
+    else if (v == 1) k_rotate<A, NB, 2><<<grid, kThreads, 0, st>>>((A *)psi, ng, a);
+    else k_rotate<A, NB, 4><<<grid, kThreads, 0, st>>>((A *)psi, ng, a);
 }
 
 cudaError_t launch_rotate(void *psi, int dtype, int n, const OpDesc &d, int sm_count, int bps, cudaStream_t st) {
     OpArgs a = to_args(d);
     uint32_t npairs = (uint32_t)(1ull << (n - d.nbits));
     int v = vec_log2(dtype, d, n);
-    if (dtype == SV_C64) {
-        if (d.nbits == 2) rot_v<float, 2>(psi, v, npairs, a, sm_count, bps, st);
-        else rot_v<float, 4>(psi, v, npairs, a, sm_count, bps, st);
-    } else {
-        if (d.nbits == 2) rot_v<double, 2>(psi, v, npairs, a, sm_count, bps, st);
-        else rot_v<double, 4>(psi, v, npairs, a, sm_count, bps, st);
-    }
+    SV_DISPATCH_AMP(dtype, if (d.nbits == 2) rot_v<A, 2>(psi, v, npairs, a, sm_count, bps, st);
+                           else rot_v<A, 4>(psi, v, npairs, a, sm_count, bps, st));
     return cudaGetLastError();
 }
 
-template <typename R, int NB>
+template <typename A, int NB>
 static void adj_v(void *psi, void *lam, int v, uint32_t npairs, OpArgs a, int grid, double *partial,
                   cudaStream_t st) {
     uint32_t ng = npairs >> v;
-    if (v == 0) k_adjoint<R, NB, 1><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, (cplx<R> *)lam, ng, a, partial);
-    else if (v == 1) k_adjoint<R, NB, 2><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, (cplx<R> *)lam, ng, a, partial);
-    else k_adjoint<R, NB, 4><<<grid, kThreads, 0, st>>>((cplx<R> *)psi, (cplx<R> *)lam, ng, a, partial);
+    if (v == 0) k_adjoint<A, NB, 1><<<grid, kThreads, 0, st>>>((A *)psi, (A *)lam, ng, a, partial);
+    else if (v == 1) k_adjoint<A, NB, 2><<<grid, kThreads, 0, st>>>((A *)psi, (A *)lam, ng, a, partial);
+    else k_adjoint<A, NB, 4><<<grid, kThreads, 0, st>>>((A *)psi, (A *)lam, ng, a, partial);
 }
 
 // `grid` blocks write partial[0 .. grid); the caller gives every op the same grid.
@@ -314,13 +352,8 @@ cudaError_t launch_adjoint(void *psi, void *lam, int dtype, int n, const OpDesc 
     OpArgs a = to_args(d);
     uint32_t npairs = (uint32_t)(1ull << (n - d.nbits));
     int v = vec_log2(dtype, d, n);
-    if (dtype == SV_C64) {
-        if (d.nbits == 2) adj_v<float, 2>(psi, lam, v, npairs, a, grid, partial, st);
-        else adj_v<float, 4>(psi, lam, v, npairs, a, grid, partial, st);
-    } else {
-        if (d.nbits == 2) adj_v<double, 2>(psi, lam, v, npairs, a, grid, partial, st);
-        else adj_v<double, 4>(psi, lam, v, npairs, a, grid, partial, st);
-    }
+    SV_DISPATCH_AMP(dtype, if (d.nbits == 2) adj_v<A, 2>(psi, lam, v, npairs, a, grid, partial, st);
+                           else adj_v<A, 4>(psi, lam, v, npairs, a, grid, partial, st));
     return cudaGetLastError();
 }
 

@@ -70,6 +70,7 @@ cudaError_t launch_compact(const void *psi, void *C, int dtype, const uint32_t *
 cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &T, const double *hdiag,
                               const double *Jp, double e_shift, double *partial, int K, cudaStream_t st);
 int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want);
+const int *sigma_ab_sizes(int dtype);
 
 DevTables::~DevTables() {
     void *ptrs[] = {dbl, sgl, W, hdiag, Jp, hdiag_s, Jp_s, eri_r, hm_r, Dt, Jt, W2, pass_dbl, pass_sgl, pass_W};
@@ -398,7 +399,7 @@ static sv_status get_tables(sv_handle h, sv_ham_handle ham, DevTables **out) {
     std::unique_ptr<DevTables> T(new DevTables());
     T->n = h->n;
     T->dtype = h->dtype;
-    if (h->dtype == SV_C64) SV_TRY(upload_tables<float>(h, ham, *T));
+    if (single_prec(h->dtype)) SV_TRY(upload_tables<float>(h, ham, *T));
     else SV_TRY(upload_tables<double>(h, ham, *T));
     *out = T.get();
     ham->dev[key] = std::move(T);
@@ -581,7 +582,7 @@ static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void 
         h->launches++;
         return SV_OK;
     }
-    if (h->expect_variant != 1) {
+    if (h->expect_variant != 1 || !is_complex(h->dtype)) {  // the record scan serves complex states
         // string rows (default)
         SV_TRY(ensure_strings(h));
         SV_TRY(ensure_partials(h, 3 * (size_t)h->Db));
@@ -705,8 +706,7 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
     {
         RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
                     T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db, T->W2};
-        const int sizes64[] = {2, 4, 6, 8}, sizes128[] = {1, 2, 3, 4};
-        const int *sizes = h->dtype == SV_C64 ? sizes64 : sizes128;
+        const int *sizes = sigma_ab_sizes(h->dtype);
         int best_v = 2;
         int64_t best_k = 0;
         float best_t = -1.f;
@@ -831,7 +831,8 @@ static sv_status create_common(int n_qubits, sv_dtype dtype, void *cuda_stream, 
     *out = nullptr;
     if (n_qubits < 2 || n_qubits > SV_MAX_QUBITS || (n_qubits & 1))
         return fail(nullptr, SV_ERR_ARG, "n_qubits must be even and in [2, 32]");
-    if (dtype != SV_C64 && dtype != SV_C128) return fail(nullptr, SV_ERR_ARG, "dtype must be SV_C64 or SV_C128");
+    if (dtype != SV_C64 && dtype != SV_C128 && dtype != SV_R32 && dtype != SV_R64)
+        return fail(nullptr, SV_ERR_ARG, "dtype must be SV_C64, SV_C128, SV_R32 or SV_R64");
     if ((psi_dev && ((uintptr_t)psi_dev & 255)) || (lam_dev && ((uintptr_t)lam_dev & 255)))
         return fail(nullptr, SV_ERR_ARG, "device buffers must be 256-byte aligned");
     sv_handle h = new sv_ctx();
@@ -847,7 +848,7 @@ static sv_status create_common(int n_qubits, sv_dtype dtype, void *cuda_stream, 
         h->elems = binom(n_qubits / 2, sect_na) * binom(n_qubits / 2, sect_nb);
         h->layout_auto = false;
     }
-    h->amp_bytes = dtype == SV_C64 ? 8 : 16;
+    h->amp_bytes = amp_size(dtype);
     for (int q = 0; q < 32; ++q) h->perm[q] = q;
     if (cudaGetDevice(&h->device) != cudaSuccess) {
         cudaGetLastError();
@@ -957,13 +958,12 @@ sv_status sv_prepare_state(sv_handle h, const void *amplitudes_host, int n_alpha
     double best = -1.0;
     uint32_t best_x = 0;
     for (uint64_t x = 0; x < h->dim; ++x) {
-        double re, im;
-        if (h->dtype == SV_C64) {
-            const float *a = (const float *)amplitudes_host + 2 * x;
-            re = a[0]; im = a[1];
-        } else {
-            const double *a = (const double *)amplitudes_host + 2 * x;
-            re = a[0]; im = a[1];
+        double re = 0.0, im = 0.0;
+        switch (h->dtype) {
+            case SV_C64: re = ((const float *)amplitudes_host)[2 * x]; im = ((const float *)amplitudes_host)[2 * x + 1]; break;
+            case SV_C128: re = ((const double *)amplitudes_host)[2 * x]; im = ((const double *)amplitudes_host)[2 * x + 1]; break;
+            case SV_R32: re = ((const float *)amplitudes_host)[x]; break;
+            default: re = ((const double *)amplitudes_host)[x]; break;
         }
         if (!std::isfinite(re) || !std::isfinite(im)) return fail(h, SV_ERR_ARG, "non-finite amplitude");
         double w = re * re + im * im;
@@ -1064,7 +1064,7 @@ sv_status sv_get_amplitudes(sv_handle h, const uint64_t *basis, int count, void 
     // scratch: the addresses, then the gathered amplitudes, in the reduction buffer
     const size_t addr_doubles = ((size_t)count * 4 + 7) / 8;
     const size_t out_off = (addr_doubles + 1) / 2 * 2;  // 16-byte aligned for complex128
-    const size_t amp_doubles = (size_t)count * h->amp_bytes / 8;
+    const size_t amp_doubles = ((size_t)count * h->amp_bytes + 7) / 8;
     SV_TRY(ensure_partials(h, out_off + amp_doubles));
     uint32_t *d_addr = (uint32_t *)h->partials;
     void *d_out = h->partials + out_off;
@@ -1181,7 +1181,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     size_t need = 0;
     if (sect) {
         need = 3 * (size_t)h->Db;
-    } else if (h->expect_variant == 1) {
+    } else if (h->expect_variant == 1 && is_complex(h->dtype)) {
         SV_TRY(ensure_sector(h));
         need = 2 * (size_t)expect_gather_grid(h->sector_len, h->sm_count);
     } else {
@@ -1319,7 +1319,7 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
     SV_TRY(check_ready(h));
     if (!re_out) return fail(h, SV_ERR_ARG, "NULL re_out");
     DeviceGuard g(h->device);
-    if (h->storage == 1 || h->rdm_variant != 1) {
+    if (h->storage == 1 || h->rdm_variant != 1 || !is_complex(h->dtype)) {
         // string rows: on the state itself (sector storage) or on its compact copy
         SV_TRY(ensure_strings(h));
         const int n_el = rdm_rows_elements(h->n);

@@ -14,7 +14,21 @@
 
 struct sv_ham;
 
+// Runs the statement(s) with `A` bound to the amplitude type of a state dtype.
+#define SV_DISPATCH_AMP(dtype, ...)                      \
+    switch (dtype) {                                     \
+        case SV_C64: { using A = float2; __VA_ARGS__; } break;  \
+        case SV_C128: { using A = double2; __VA_ARGS__; } break; \
+        case SV_R32: { using A = float; __VA_ARGS__; } break;    \
+        default: { using A = double; __VA_ARGS__; } break;       \
+    }
+
 namespace svk {
+
+// Bytes of one amplitude, and whether the state's arithmetic is single precision.
+inline size_t amp_size(int dtype) { return dtype == SV_C64 ? 8 : dtype == SV_C128 ? 16 : dtype == SV_R32 ? 4 : 8; }
+inline bool single_prec(int dtype) { return dtype == SV_C64 || dtype == SV_R32; }
+inline bool is_complex(int dtype) { return dtype == SV_C64 || dtype == SV_C128; }
 
 // ---------------------------------------------------------------- excitation ops
 

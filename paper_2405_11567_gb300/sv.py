@@ -12,7 +12,20 @@ import numpy as np
 
 from . import build as _build
 
-SV_C64, SV_C128 = 0, 1
+SV_C64, SV_C128, SV_R32, SV_R64 = 0, 1, 2, 3
+# numpy element type of each state dtype (host views of a handle's amplitudes)
+NP_DTYPE = {SV_C64: np.complex64, SV_C128: np.complex128, SV_R32: np.float32, SV_R64: np.float64}
+_DTYPE_NAMES = {"c64": SV_C64, "c128": SV_C128, "r32": SV_R32, "r64": SV_R64,
+                np.complex64: SV_C64, np.complex128: SV_C128, np.float32: SV_R32, np.float64: SV_R64}
+
+
+def dtype_code(dtype) -> int:
+    """SV_* code of a dtype given as "c64" / "c128" / "r32" / "r64", a numpy type or a code."""
+    if isinstance(dtype, int) and dtype in NP_DTYPE:
+        return dtype
+    if dtype in _DTYPE_NAMES:
+        return _DTYPE_NAMES[dtype]
+    raise ValueError("unknown state dtype %r" % (dtype,))
 SV_OPT_CHECKPOINT_INTERVAL, SV_OPT_MAX_BYTES, SV_OPT_EXPECT_VARIANT, SV_OPT_RDM_VARIANT = 1, 2, 3, 4
 SV_OPT_PROFILE = 5
 SV_OPT_LAYOUT_AUTO = 6
@@ -171,22 +184,32 @@ def sv_prepare_hf(h, occ):
     _ck(lib().sv_prepare_hf(h, _ptr(occ), len(occ)), h)
 
 
-def sv_prepare_state(h, amplitudes, n_alpha: int, n_beta: int):
-    a = np.ascontiguousarray(amplitudes)
-    if a.dtype not in (np.complex64, np.complex128):
-        raise TypeError("amplitudes must be complex64 or complex128 (the handle's dtype)")
+def sv_prepare_state(h, amplitudes, n_alpha: int, n_beta: int, dtype=None):
+    """Amplitudes in the handle's dtype (converted when `dtype` is given; a complex array for a
+    real handle must have zero imaginary parts)."""
+    a = np.asarray(amplitudes)
+    if dtype is not None:
+        want = NP_DTYPE[dtype_code(dtype)]
+        if np.issubdtype(want, np.floating) and np.iscomplexobj(a):
+            if np.any(a.imag != 0):
+                raise ValueError("a real-amplitude handle needs a real state")
+            a = a.real
+        a = a.astype(want)
+    a = np.ascontiguousarray(a)
+    if a.dtype.type not in (np.complex64, np.complex128, np.float32, np.float64):
+        raise TypeError("amplitudes must be complex64, complex128, float32 or float64 (the handle's dtype)")
     _ck(lib().sv_prepare_state(h, _ptr(a), int(n_alpha), int(n_beta)), h)
 
 
 def sv_get_state(h, n_qubits: int, dtype: int) -> np.ndarray:
-    out = np.empty(1 << n_qubits, dtype=np.complex64 if dtype == SV_C64 else np.complex128)
+    out = np.empty(1 << n_qubits, dtype=NP_DTYPE[dtype_code(dtype)])
     _ck(lib().sv_get_state(h, _ptr(out)), h)
     return out
 
 
 def sv_get_amplitudes(h, basis, dtype: int) -> np.ndarray:
     idx = np.ascontiguousarray(np.asarray(basis, dtype=np.uint64).reshape(-1))
-    out = np.empty(len(idx), dtype=np.complex64 if dtype == SV_C64 else np.complex128)
+    out = np.empty(len(idx), dtype=NP_DTYPE[dtype_code(dtype)])
     _ck(lib().sv_get_amplitudes(h, _ptr(idx), len(idx), _ptr(out)), h)
     return out
 
@@ -354,7 +377,7 @@ class Batch:
     """Owns an ``sv_batch_handle``: many independent problems in one persistent launch."""
 
     def __init__(self, problems, dtype="c64", stream=None):
-        self.dtype = SV_C64 if dtype in ("c64", SV_C64) else SV_C128
+        self.dtype = dtype_code(dtype)
         self.sizes = [len(p["ops"]) for p in problems]
         self.n_inst = len(problems)
         self.total_ops = int(sum(self.sizes))
@@ -416,7 +439,7 @@ class StateVector:
 
     def __init__(self, n_qubits: int, dtype="c64", stream=None, sector=None):
         self.n = int(n_qubits)
-        self.dtype = SV_C64 if dtype in ("c64", SV_C64, np.complex64) else SV_C128
+        self.dtype = dtype_code(dtype)
         self.sector = None if sector is None else (int(sector[0]), int(sector[1]))
         self.handle = None
         if self.sector is None:
@@ -439,7 +462,8 @@ class StateVector:
         sv_prepare_hf(self.handle, occ)
 
     def prepare_state(self, amplitudes, n_alpha, n_beta):
-        sv_prepare_state(self.handle, amplitudes, n_alpha, n_beta)
+        """Any dense 2^n amplitude array of the (n_alpha, n_beta) sector, converted to the handle's dtype."""
+        sv_prepare_state(self.handle, amplitudes, n_alpha, n_beta, dtype=self.dtype)
 
     def state(self) -> np.ndarray:
         return sv_get_state(self.handle, self.n, self.dtype)

@@ -16,7 +16,8 @@ from paper_2405_11567_gb300 import inputs, sv
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-TOL = {"c128": dict(E=1e-10, g=1e-9, rdm=1e-11, amp=1e-11), "c64": dict(E=1e-5, g=1e-5, rdm=2e-6, amp=2e-6)}
+TOL = {"c128": dict(E=1e-10, g=1e-9, rdm=1e-11, amp=1e-11), "c64": dict(E=1e-5, g=1e-5, rdm=2e-6, amp=2e-6),
+       "r64": dict(E=1e-10, g=1e-9, rdm=1e-11, amp=1e-11), "r32": dict(E=1e-5, g=1e-5, rdm=2e-6, amp=2e-6)}
 
 
 @pytest.fixture(scope="module")
@@ -36,7 +37,7 @@ def golden():
 
 
 @pytest.mark.parametrize("storage", ["dense", "sector"])
-@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("dtype", ["c64", "c128", "r32", "r64"])
 def test_config5_energy_gradient_rdm_and_state(golden, dtype, storage):
     p, g = golden
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
