@@ -10,8 +10,9 @@ paper's molecules (config 5 of the workload list).
 Headline: the dense 2^30-amplitude complex64 state (8 GiB per vector, float64
 reductions), the state-vector method the metric is defined on; complex128 beside
 it.  Also timed: the same step in sector storage (only the C(15,5)^2 = 9,018,009
-amplitudes of the (5, 5) sector, 72 MB, a separate row with its own roofline) and
-the batched small-instance launch (config 4).  L2 is flushed (a 256 MB write)
+amplitudes of the (5, 5) sector, 72 MB, a separate row with its own roofline), with
+real float32 amplitudes (the real-angle ansatz keeps psi real), and the batched
+small-instance launch (config 4).  L2 is flushed (a 256 MB write)
 before every timed step, outside its events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -351,6 +352,8 @@ def run_ours(args, rank, world, local_rank):
     head128 = None if args.no_c128 else timed("c128", sector=False)
     s64 = None if args.no_sector else timed("c64", sector=True)
     s128 = None if (args.no_sector or args.no_c128) else timed("c128", sector=True)
+    r32d = None if args.no_real else timed("r32", sector=False)
+    r32s = None if (args.no_real or args.no_sector) else timed("r32", sector=True)
     rbatch = None if (args.qubits or args.no_batch) else timed_batch()
     if rank != 0:
         return 0
@@ -435,6 +438,20 @@ def run_ours(args, rank, world, local_rank):
             if head128 is not None:
                 sect["abs_dE_vs_dense_c128"] = abs(s128["out"]["E"] - head128["out"]["E"])
         line["sector_storage"] = sect
+    if r32d is not None:
+        # real-amplitude float32 state (the real-angle ansatz keeps psi real): half the bytes per amplitude
+        rb4 = touched_bytes(p["ops"], n, 4)
+        t_adj = r32d["phases"]["reverse"] / L / 1000.0
+        a = 2.0 * rb4.sum() / L / t_adj / 1e9
+        real = {"state": "real float32 amplitudes, float64 reductions",
+                "dense": {"value": throughput(world, K, r32d["ms"]), "ms_per_step": r32d["ms"] / K,
+                          "phases_ms": r32d["phases"], "adjoint_step_gbs": a, "adjoint_step_frac": a / peak,
+                          "abs_dE_vs_c64": abs(r32d["out"]["E"] - head["out"]["E"]),
+                          "max_abs_dg_vs_c64": float(np.max(np.abs(r32d["out"]["g"] - head["out"]["g"])))}}
+        if r32s is not None:
+            real["sector"] = {"value": throughput(world, K, r32s["ms"]), "ms_per_step": r32s["ms"] / K,
+                              "phases_ms": r32s["phases"]}
+        line["real_state"] = real
     if rbatch is not None:
         line["batch_config4"] = rbatch
     if world == 1 and not args.no_cpu_baseline and not args.qubits:
@@ -498,6 +515,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) timing")
     ap.add_argument("--no-sector", action="store_true", help="skip the sector-storage timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch choices")
+    ap.add_argument("--no-real", action="store_true", help="skip the real-amplitude (float32) timing")
     ap.add_argument("--op-profile", action="store_true",
                     help="per-operator rotation bandwidth by lowest address bit (diagnostic, not the bench line)")
     ap.add_argument("--qubits", type=int, default=0,
