@@ -348,6 +348,12 @@ def run_ours(args, rank, world, local_rank):
         b.close()
         return out
 
+    if args.sector_only:  # profiling runs: only the sector-storage complex64 step, a few GB on the device
+        so = timed("c64", sector=True)
+        if rank == 0:
+            print(json.dumps({"profile": "sector-only (not the bench line)", "ms_per_step": so["ms"] / args.steps,
+                              "phases_ms": so["phases"], "tuned": so["tuned"]}), flush=True)
+        return 0
     head = timed("c64", sector=False)
     head128 = None if args.no_c128 else timed("c128", sector=False)
     s64 = None if args.no_sector else timed("c64", sector=True)
@@ -516,6 +522,8 @@ def main():
     ap.add_argument("--no-sector", action="store_true", help="skip the sector-storage timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch choices")
     ap.add_argument("--no-real", action="store_true", help="skip the real-amplitude (float32) timing")
+    ap.add_argument("--sector-only", action="store_true",
+                    help="profiling only: time just the sector-storage complex64 step (prints no bench line)")
     ap.add_argument("--op-profile", action="store_true",
                     help="per-operator rotation bandwidth by lowest address bit (diagnostic, not the bench line)")
     ap.add_argument("--qubits", type=int, default=0,
