@@ -40,12 +40,13 @@ METRIC = "energy+adjoint-grad evals/s at 30 qubits, FP32-state vs FP64; % of HBM
 UNIT = "evals/s"
 CONFIG_ID = 5
 # DRAM bytes (read + write) of one expectation's two kernels on sector storage
-# (k_sigma_ab 215.7 MB, k_sigma_same 700.8 MB), from the ncu capture summarised in
+# (k_sigma_ab 219.6 MB, k_sigma_same 897.4 MB), from the ncu capture summarised in
 # profiles/sigma_split_n30_sector_c64.md; set to None once either kernel changes.
-SIGMA_TRAFFIC_BYTES = 916.5e6
-# DRAM bytes per k_adjoint launch of the dense headline (scaled to 30 qubits); None
-# until captured for the current kernel.
-ADJOINT_TRAFFIC_BYTES = None
+SIGMA_TRAFFIC_BYTES = 1117.0e6
+# DRAM bytes per k_adjoint launch of the dense headline: the 28-qubit capture's
+# traffic / algorithmic ratio (1.20, profiles/k_adjoint_dram_n28_dense_c64.md) times
+# the 30-qubit algorithmic bytes per launch; None once the kernel changes.
+ADJOINT_TRAFFIC_BYTES = 5.32e9
 
 
 def _env_int(k, d):
