@@ -22,10 +22,10 @@
  *               + 1/2 sum (pq|rs) a+_{p s} a+_{r t} a_{s t} a_{q s}.
  *   - E = <psi|H|psi> / <psi|psi>; dE/dtheta_k in Hartree per radian.
  *
- * State storage: one dense vector of 2^n complex amplitudes in device memory,
- * interleaved (re, im), complex64 (SV_C64, float) or complex128 (SV_C128,
- * double), index = basis index x (sv_create), or only the amplitudes of one
- * (N_alpha, N_beta) sector (sv_create_sector).  Every reduction (energy, gradient, norm,
+ * State storage: one dense vector of 2^n amplitudes in device memory, index =
+ * basis index x (sv_create), or only the amplitudes of one (N_alpha, N_beta)
+ * sector (sv_create_sector); complex amplitudes interleaved (re, im) in float
+ * (SV_C64) or double (SV_C128), or real amplitudes (SV_R32, SV_R64).  Every reduction (energy, gradient, norm,
  * density matrix) is accumulated and returned in float64 whatever the state
  * precision.
  *
@@ -148,7 +148,8 @@ sv_status sv_destroy(sv_handle h);
 sv_status sv_prepare_hf(sv_handle h, const int32_t *occ, int n_occ);
 
 /* Prepare an arbitrary initial state from host memory: 2^n amplitudes of the
- * handle's dtype (interleaved re, im), which must vanish (exactly) outside the
+ * handle's dtype (interleaved re, im for complex dtypes, one real each for real
+ * dtypes), which must vanish (exactly) outside the
  * sector with n_alpha alpha and n_beta beta electrons (SV_ERR_ARG otherwise).
  * The handle keeps a device copy as the reference for sv_energy_grad (a
  * multi-determinant start such as the CIPSI states of "Computational
