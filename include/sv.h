@@ -25,9 +25,9 @@
  * State storage: one dense vector of 2^n amplitudes in device memory, index =
  * basis index x (sv_create), or only the amplitudes of one (N_alpha, N_beta)
  * sector (sv_create_sector); complex amplitudes interleaved (re, im) in float
- * (SV_C64) or double (SV_C128), or real amplitudes (SV_R32, SV_R64).  Every reduction (energy, gradient, norm,
- * density matrix) is accumulated and returned in float64 whatever the state
- * precision.
+ * (SV_C64) or double (SV_C128), or real amplitudes (SV_R32, SV_R64).  Every
+ * reduction (energy, gradient, norm, density matrix) is accumulated and returned
+ * in float64 whatever the state precision.
  *
  * Ownership: the caller owns every host array passed in and out; the library
  * copies what it keeps.  Device buffers are owned by the library unless they
@@ -294,10 +294,13 @@ sv_status sv_batch_set_time_limit(sv_batch_handle b, double ms);
 uint64_t sv_batch_launch_count(sv_batch_handle b);
 
 /* Autotuner for the persistent batched launch: times the captured launch (angles
- * up, kernel, results down) with 1, 2, 3 and 4 blocks per SM (capped by the
- * instance count) at the angles theta (as for sv_batch_energy_grad) and keeps the
- * fastest grid for later calls; *grid_out (may be NULL) receives it.  Results do not
- * depend on the grid.  No counterpart in the paper. */
+ * up, kernel, results down) at the angles theta (as for sv_batch_energy_grad) with
+ * 256, 512 and 1024 threads per block and 1, 2 or 4 blocks per SM (at most 2048
+ * threads per SM; grids capped by the instance count) and keeps the fastest for later
+ * calls; *grid_out (may be NULL) receives the grid.  Each instance runs whole in one
+ * block with fixed-order sums, so results depend on the block size only through the
+ * order of those sums (rounding) and reruns with one choice are bit-identical.  No
+ * counterpart in the paper. */
 sv_status sv_batch_autotune(sv_batch_handle b, const double *theta, int *grid_out);
 
 sv_status sv_batch_destroy(sv_batch_handle b);

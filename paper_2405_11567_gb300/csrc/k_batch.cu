@@ -74,10 +74,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_batch(BatchArgs<R> B) {
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT) k_batch(BatchArgs<R> B) {
     __shared__ int s_inst;
-    __shared__ double red[2 * kThreads / 32];
+    __shared__ double red[2 * NT / 32];
     __shared__ unsigned long long s_t0;
     cplx<R> *psi = B.scratch + (size_t)blockIdx.x * 2 * B.Dmax;
     cplx<R> *lam = psi + B.Dmax;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BatchArgs<R> B) {
             e_acc += (double)c0.x * (double)s.x + (double)c0.y * (double)s.y;
             n_acc += (double)c0.x * (double)c0.x + (double)c0.y * (double)c0.y;
         }
-        block_sum2(e_acc, n_acc, red);  // contains the barrier that publishes lambda
+        block_sum2_nt<NT>(e_acc, n_acc, red);  // contains the barrier that publishes lambda
         __shared__ double s_norm;
         if (threadIdx.x == 0) {
             s_norm = n_acc;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BatchArgs<R> B) {
                 lam[i] = mk<R>(csk.x * lu.x + ss * lv.x, csk.x * lu.y + ss * lv.y);
                 lam[j] = mk<R>(csk.x * lv.x - ss * lu.x, csk.x * lv.y - ss * lu.y);
             }
-            const double gs = block_sum(g, red);
+            const double gs = block_sum_nt<NT>(g, red);
             if (threadIdx.x == 0) B.out[I.out + 1 + k] = 2.0 * gs / nrm;
         }
         __syncthreads();
@@ -195,6 +195,7 @@ struct sv_batch {
     sv_dtype dtype = SV_C64;
     cudaStream_t stream = nullptr;
     int device = 0, sm_count = 148, grid = 0, grid_max = 0, Dmax = 0;
+    int threads = kThreads;  // block size of the persistent kernel: 256, 512 or 1024
     std::vector<int> L;
     std::vector<long long> cs_off, out_off;
     long long total_ops = 0, total_out = 0;
@@ -422,7 +423,9 @@ sv_status capture(sv_batch *b) {
     if (e != cudaSuccess) return bfail(SV_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
     cudaMemcpyAsync(b->d_cs, b->h_cs, std::max<long long>(b->total_ops, 1) * sizeof(cplx<R>), cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(b->d_ctrl, 0, 2 * sizeof(int), st);
-    k_batch<R><<<b->grid, kThreads, 0, st>>>(a);
+    if (b->threads == 1024) k_batch<R, 1024><<<b->grid, 1024, 0, st>>>(a);
+    else if (b->threads == 512) k_batch<R, 512><<<b->grid, 512, 0, st>>>(a);
+    else k_batch<R, 256><<<b->grid, 256, 0, st>>>(a);
     cudaMemcpyAsync(b->h_out, b->d_out, std::max<long long>(b->total_out, 1) * sizeof(double), cudaMemcpyDeviceToHost,
                     st);
     cudaMemcpyAsync(b->h_ctrl, b->d_ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -554,14 +557,18 @@ sv_status sv_batch_autotune(sv_batch_handle b, const double *theta, int *grid_ou
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     sv_status s = SV_OK;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) s = bfail(SV_ERR_CUDA, "event creation failed");
-    const int keep = b->grid;
-    int best = keep;
+    const int keep = b->grid, keep_t = b->threads;
+    int best = keep, best_threads = keep_t;
     float best_t = -1.f;
-    for (int mult = 1; s == SV_OK && mult <= 4; ++mult) {
-        const int g = std::max(1, std::min(b->n_inst, b->sm_count * mult));
-        if (g > b->grid_max || (mult > 1 && g == std::min(b->n_inst, b->sm_count * (mult - 1)))) continue;
+    // (threads per block, blocks per SM): at most 2048 resident threads per SM
+    const int cands[][2] = {{256, 1}, {256, 2}, {256, 4}, {512, 1}, {512, 2}, {1024, 1}, {1024, 2}};
+    for (const auto &cd : cands) {
+        if (s != SV_OK) break;
+        const int g = std::max(1, std::min(b->n_inst, b->sm_count * cd[1]));
+        if (g > b->grid_max) continue;
         drop_graph(b);
         b->grid = g;
+        b->threads = cd[0];
         s = b->dtype == SV_C64 ? capture<float>(b) : capture<double>(b);
         float ms = 0.f;
         for (int r = 0; s == SV_OK && r < 2; ++r) {  // the second run is timed
@@ -580,10 +587,12 @@ sv_status sv_batch_autotune(sv_batch_handle b, const double *theta, int *grid_ou
         if (s == SV_OK && (best_t < 0.f || ms < best_t)) {
             best_t = ms;
             best = g;
+            best_threads = cd[0];
         }
     }
     drop_graph(b);
     b->grid = s == SV_OK ? best : keep;
+    b->threads = s == SV_OK ? best_threads : keep_t;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (grid_out) *grid_out = b->grid;

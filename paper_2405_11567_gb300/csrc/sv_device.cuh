@@ -130,4 +130,41 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *red) {
     __syncthreads();
 }
 
+// block_sum / block_sum2 for a block of NT threads (NT a multiple of 32, <= 1024);
+// `red` must hold NT/32 (block_sum_nt) or 2 NT/32 (block_sum2_nt) doubles.
+template <int NT>
+__device__ __forceinline__ double block_sum_nt(double v, double *red) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        #pragma unroll
+        for (int i = 0; i < NT / 32; ++i) s += red[i];
+    }
+    __syncthreads();
+    return s;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_sum2_nt(double &a, double &b, double *red) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { red[w] = a; red[NT / 32 + w] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0;
+        #pragma unroll
+        for (int i = 0; i < NT / 32; ++i) { sa += red[i]; sb += red[NT / 32 + i]; }
+        a = sa; b = sb;
+    }
+    __syncthreads();
+}
+
 }  // namespace svk

@@ -1,7 +1,7 @@
 """The autotuners (sv_autotune, sv_batch_autotune): they choose among launch forms and
-geometries only, so after tuning every result still matches the oracle, the state the
-tuner ran beside is unchanged bit for bit, and the chosen values come from the
-candidate sets."""
+geometries only (which can change the order of sums), so after tuning every result still
+matches the oracle or the untuned run to the precision's rounding, the state the tuner ran
+beside is unchanged bit for bit, and the chosen values come from the candidate sets."""
 import numpy as np
 import pytest
 
@@ -69,5 +69,9 @@ def test_batch_autotune_keeps_results():
     grid = b.autotune(theta)
     assert grid >= 1
     e2, g2 = b.energy_grad(theta)
-    assert np.array_equal(e1, e2) and all(np.array_equal(x, y) for x, y in zip(g1, g2))
+    # the block size changes the order of the per-instance sums: equal to complex64 rounding
+    assert np.max(np.abs(e1 - e2)) <= 1e-5
+    assert max(float(np.max(np.abs(x - y))) if len(x) else 0.0 for x, y in zip(g1, g2)) <= 1e-5
+    e3, g3 = b.energy_grad(theta)                     # and a rerun with the tuned choice is bit-identical
+    assert np.array_equal(e2, e3) and all(np.array_equal(x, y) for x, y in zip(g2, g3))
     b.close()
