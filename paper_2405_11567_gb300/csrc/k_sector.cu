@@ -25,10 +25,10 @@
 
 namespace svk {
 
+// An op's sign mask and its alpha / beta string flip masks and "from" patterns.
 struct SectOp {
     uint32_t sm;
-    uint32_t ma, fa, mb, fb;  // alpha / beta string flip masks and "from" patterns
-    double c, s;
+    uint32_t ma, fa, mb, fb;
 };
 
 struct SectTabs {
@@ -269,7 +269,7 @@ static SectTabs tabs(const uint32_t *sa, const uint32_t *sb, const uint16_t *str
 }
 
 // Alpha / beta string parts of a qubit-space op.
-void sect_op_from(const OpDesc &d, int N, void *dst) {
+static void sect_op_from(const OpDesc &d, int N, SectOp *dst) {
     SectOp o;
     o.sm = d.sm;
     o.ma = o.fa = o.mb = o.fb = 0;
@@ -279,9 +279,7 @@ void sect_op_from(const OpDesc &d, int N, void *dst) {
         if ((d.m >> (2 * q + 1)) & 1u) o.mb |= 1u << q;
         if ((d.from >> (2 * q + 1)) & 1u) o.fb |= 1u << q;
     }
-    o.c = d.c;
-    o.s = d.s;
-    *(SectOp *)dst = o;
+    *dst = o;
 }
 
 // Blocks of the list kernels: one per beta-list entry, at most bps per SM (8 by default).

@@ -40,7 +40,6 @@ cudaError_t launch_pool_grad(const void *C, const void *L, int dtype, const void
 cudaError_t launch_rdm_gather(const void *psi, int dtype, const uint32_t *sector, uint64_t count,
                               const void *elems, int n_el, int grid, double *partial, cudaStream_t st);
 // sector storage (k_sector.cu)
-void sect_op_from(const OpDesc &d, int N, void *dst);
 int sector_grid(int Db, int sm_count, int bps);
 size_t list_op_bytes();
 void list_op_from(const OpDesc &d, int N, int na, int nb, uint32_t a_off, void *dst, int *na_l, int *nb_l);
