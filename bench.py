@@ -349,6 +349,11 @@ def run_ours(args, rank, world, local_rank):
         b.close()
         return out
 
+    if args.batch_only:  # profiling runs: only the batched launch (config 4)
+        rb = timed_batch()
+        if rank == 0:
+            print(json.dumps({"profile": "batch-only (not the bench line)", "batch_config4": rb}), flush=True)
+        return 0
     if args.sector_only:  # profiling runs: only the sector-storage complex64 step, a few GB on the device
         so = timed("c64", sector=True)
         if rank == 0:
@@ -523,6 +528,8 @@ def main():
     ap.add_argument("--no-sector", action="store_true", help="skip the sector-storage timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch choices")
     ap.add_argument("--no-real", action="store_true", help="skip the real-amplitude (float32) timing")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="profiling only: time just the batched launch (prints no bench line)")
     ap.add_argument("--sector-only", action="store_true",
                     help="profiling only: time just the sector-storage complex64 step (prints no bench line)")
     ap.add_argument("--op-profile", action="store_true",

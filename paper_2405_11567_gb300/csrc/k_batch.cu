@@ -75,7 +75,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 template <typename R, int NT>
-__global__ void __launch_bounds__(NT) k_batch(BatchArgs<R> B) {
+__global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchArgs<R> B) {
     __shared__ int s_inst;
     __shared__ double red[2 * NT / 32];
     __shared__ unsigned long long s_t0;

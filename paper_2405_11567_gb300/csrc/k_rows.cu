@@ -246,17 +246,6 @@ __device__ __forceinline__ double flip_sign<double>(double v, uint32_t bit) {
     return __longlong_as_double(__double_as_longlong(v) ^ (long long)((unsigned long long)bit << 63));
 }
 
-// Parity prefix of an orbital string: bit u = parity of the bits of s below u.
-__device__ __forceinline__ uint32_t prefix_parity(uint32_t s) {
-    uint32_t y = s << 1;
-    y ^= y << 1;
-    y ^= y << 2;
-    y ^= y << 4;
-    y ^= y << 8;
-    y ^= y << 16;
-    return y;
-}
-
 __device__ __forceinline__ int pair_index(int p, int q, int N) { return p * N - p * (p + 1) / 2 + (q - p - 1); }
 
 // Split form, first kernel: the diagonal, alpha singles, alpha-alpha doubles and

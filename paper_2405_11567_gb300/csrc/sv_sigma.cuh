@@ -23,6 +23,17 @@ __device__ __forceinline__ uint32_t between(int a, int b) {
 
 __device__ __forceinline__ int par(uint32_t v) { return __popc(v) & 1; }
 
+// Parity prefix of an orbital string: bit u = parity of the bits of s below u.
+__device__ __forceinline__ uint32_t prefix_parity(uint32_t s) {
+    uint32_t y = s << 1;
+    y ^= y << 1;
+    y ^= y << 2;
+    y ^= y << 4;
+    y ^= y << 8;
+    y ^= y << 16;
+    return y;
+}
+
 template <typename R>
 struct SigmaTables {
     const uint32_t *sa;     // [Da] alpha spread (even bits), qubit space
@@ -67,7 +78,19 @@ __device__ __forceinline__ void fma_c(cplx<R> &acc, R v, const cplx<R> &c) {
     acc.y += v * c.y;
 }
 
+// Orbital-order part of the Jordan-Wigner sign of a same-spin double p1<p2 -> q1<q2
+// taken as -(a+_q1 a_p2)(a+_q2 a_p1): the string-dependent part is the parity of the
+// prefix-parity word over the four orbitals.
+__device__ __forceinline__ uint32_t double_order_sign(int p1, int p2, int q1, int q2) {
+    return (uint32_t)((p1 < q2) ^ (q2 < p2) ^ (p1 < q1) ^ (p2 < q1));
+}
+
 // sigma at (rank a = Ia, rank b = Ib) for amplitudes C ([Db][Da]); c0 = C[Ib][Ia].
+// Signs from prefix-parity words (bit u = parity of the bits below u): with
+// interleaved spin-orbitals the bits of x strictly between 2p and 2q are the alpha
+// orbitals strictly between p and q and the beta orbitals in [min, max), so an alpha
+// excitation's sign is the parity of pp(a) ^ pp(b) over its orbitals (plus an
+// orbital-order term), and a beta excitation's that of pp(b) ^ pp(a) ^ a.
 template <typename R>
 __device__ __forceinline__ cplx<R> sigma_at(const SigmaTables<R> &A, const cplx<R> *__restrict__ C, int Ia, int Ib,
                                             cplx<R> c0) {
@@ -75,9 +98,10 @@ __device__ __forceinline__ cplx<R> sigma_at(const SigmaTables<R> &A, const cplx<
     const uint32_t b = A.strb[Ib], xb = A.sb[Ib];
     const uint32_t eb = ~b & A.maskN;
     const cplx<R> *row = C + (size_t)Ib * Da;
-    (void)N;
     const uint32_t a = A.stra[Ia], xa = A.sa[Ia], x = xa | xb;
     const uint32_t ea = ~a & A.maskN;
+    const uint32_t ppa = prefix_parity(a), ppb = prefix_parity(b);
+    const uint32_t PPa = ppa ^ ppb, PPb = ppb ^ ppa ^ a;  // alpha / beta excitation parity words
     // diagonal (float64), including E_nuc - c
     double d = A.e_shift;
     for (uint32_t o = x; o; o &= o - 1u) {
@@ -91,9 +115,10 @@ __device__ __forceinline__ cplx<R> sigma_at(const SigmaTables<R> &A, const cplx<
         const int p = __ffs(o) - 1;
         for (uint32_t e = ea; e; e &= e - 1u) {
             const int q = __ffs(e) - 1;
+            const uint32_t m = (1u << p) | (1u << q);
             R v = single_value<R>(A, p, q, a, b);
-            if (par(x & between(2 * p, 2 * q))) v = -v;
-            fma_c<R>(acc, v, row[A.ra[a ^ (1u << p) ^ (1u << q)]]);
+            if ((uint32_t)par(PPa & m) ^ (uint32_t)(p < q)) v = -v;
+            fma_c<R>(acc, v, row[A.ra[a ^ m]]);
         }
     }
     // alpha-alpha doubles (p1<p2 occupied -> q1<q2 empty), partner in this row
@@ -105,13 +130,10 @@ __device__ __forceinline__ cplx<R> sigma_at(const SigmaTables<R> &A, const cplx<
                 const int q1 = __ffs(e) - 1;
                 for (uint32_t e2 = e & (e - 1u); e2; e2 &= e2 - 1u) {
                     const int q2 = __ffs(e2) - 1;
+                    const uint32_t m = (1u << p1) | (1u << p2) | (1u << q1) | (1u << q2);
                     R v = eri4<R>(A, q1, p1, q2, p2) - eri4<R>(A, q1, p2, q2, p1);
-                    // T = a+_a a+_b a_j a_i, i=2p1, j=2p2, a=2q1, b=2q2: -(a+_a a_j)(a+_b a_i)
-                    const int i = 2 * p1, j = 2 * p2, aa = 2 * q1, bb = 2 * q2;
-                    const uint32_t x1 = x ^ (1u << i) ^ (1u << bb);
-                    const int s = 1 ^ par(x & between(i, bb)) ^ par(x1 & between(j, aa));
-                    if (s) v = -v;
-                    fma_c<R>(acc, v, row[A.ra[a ^ (1u << p1) ^ (1u << p2) ^ (1u << q1) ^ (1u << q2)]]);
+                    if ((uint32_t)par(PPa & m) ^ double_order_sign(p1, p2, q1, q2)) v = -v;
+                    fma_c<R>(acc, v, row[A.ra[a ^ m]]);
                 }
             }
         }
@@ -121,10 +143,10 @@ __device__ __forceinline__ cplx<R> sigma_at(const SigmaTables<R> &A, const cplx<
         const int r = __ffs(o) - 1;
         for (uint32_t e = eb; e; e &= e - 1u) {
             const int s = __ffs(e) - 1;
-            const int Jb = A.rb[b ^ (1u << r) ^ (1u << s)];
+            const uint32_t m = (1u << r) | (1u << s);
             R v = single_value<R>(A, r, s, b, a);
-            if (par(x & between(2 * r + 1, 2 * s + 1))) v = -v;
-            fma_c<R>(acc, v, C[(size_t)Jb * Da + Ia]);
+            if ((uint32_t)par(PPb & m) ^ (uint32_t)(r < s)) v = -v;
+            fma_c<R>(acc, v, C[(size_t)A.rb[b ^ m] * Da + Ia]);
         }
     }
     // beta-beta doubles
@@ -136,34 +158,33 @@ __device__ __forceinline__ cplx<R> sigma_at(const SigmaTables<R> &A, const cplx<
                 const int s1 = __ffs(e) - 1;
                 for (uint32_t e2 = e & (e - 1u); e2; e2 &= e2 - 1u) {
                     const int s2 = __ffs(e2) - 1;
+                    const uint32_t m = (1u << r1) | (1u << r2) | (1u << s1) | (1u << s2);
                     R v = eri4<R>(A, s1, r1, s2, r2) - eri4<R>(A, s1, r2, s2, r1);
-                    const int i = 2 * r1 + 1, j = 2 * r2 + 1, aa = 2 * s1 + 1, bb = 2 * s2 + 1;
-                    const uint32_t x1 = x ^ (1u << i) ^ (1u << bb);
-                    const int sg = 1 ^ par(x & between(i, bb)) ^ par(x1 & between(j, aa));
-                    if (sg) v = -v;
-                    const int Jb = A.rb[b ^ (1u << r1) ^ (1u << r2) ^ (1u << s1) ^ (1u << s2)];
-                    fma_c<R>(acc, v, C[(size_t)Jb * Da + Ia]);
+                    if ((uint32_t)par(PPb & m) ^ double_order_sign(r1, r2, s1, s2)) v = -v;
+                    fma_c<R>(acc, v, C[(size_t)A.rb[b ^ m] * Da + Ia]);
                 }
             }
         }
     }
-    // alpha-beta doubles: beta r -> s and alpha p -> q, value (qp|sr);
-    // <x'|(a+_q a_p)(a+_s a_r)|x>: beta single on x, then alpha single on x_beta
+    // alpha-beta doubles: beta r -> s on x, then alpha p -> q on x' (beta string b'),
+    // value (qp|sr); alpha partner ranks and signs hoisted out of the beta loop
     for (uint32_t o = b; o; o &= o - 1u) {
         const int r = __ffs(o) - 1;
         for (uint32_t e = eb; e; e &= e - 1u) {
             const int s = __ffs(e) - 1;
-            const int Jb = A.rb[b ^ (1u << r) ^ (1u << s)];
-            const cplx<R> *prow = C + (size_t)Jb * Da;
-            const int sb_ = par(x & between(2 * r + 1, 2 * s + 1));
-            const uint32_t xbeta = x ^ (1u << (2 * r + 1)) ^ (1u << (2 * s + 1));
+            const uint32_t mb = (1u << r) | (1u << s);
+            const cplx<R> *prow = C + (size_t)A.rb[b ^ mb] * Da;
+            const uint32_t sb = (uint32_t)par(PPb & mb) ^ (uint32_t)(r < s);
+            const uint32_t PPx = ppa ^ prefix_parity(b ^ mb);  // alpha parity word on x'
+            const R *er = A.eri + s * N + r;                   // (qp|sr) at er[(q N + p) N^2]
             for (uint32_t oa = a; oa; oa &= oa - 1u) {
                 const int p = __ffs(oa) - 1;
                 for (uint32_t ee = ea; ee; ee &= ee - 1u) {
                     const int q = __ffs(ee) - 1;
-                    R v = eri4<R>(A, q, p, s, r);
-                    if (sb_ ^ par(xbeta & between(2 * p, 2 * q))) v = -v;
-                    fma_c<R>(acc, v, prow[A.ra[a ^ (1u << p) ^ (1u << q)]]);
+                    const uint32_t m = (1u << p) | (1u << q);
+                    R v = er[(q * N + p) * N * N];
+                    if (sb ^ (uint32_t)par(PPx & m) ^ (uint32_t)(p < q)) v = -v;
+                    fma_c<R>(acc, v, prow[A.ra[a ^ m]]);
                 }
             }
         }
