@@ -474,15 +474,20 @@ static sv_status prepare_reference(sv_handle h) {
 }
 
 // Sector storage: the alpha and beta pair lists of every op (k_build_lists), kept
-// on the device and rebuilt only when the ops' masks change.
+// on the device and rebuilt only when the ops' masks (or the sector) change.
 static sv_status ensure_op_lists(sv_handle h, const std::vector<OpDesc> &ops) {
     SV_TRY(ensure_strings(h));
-    uint64_t key = 1469598103934665603ull;
-    auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
-    mix(ops.size());
-    mix((uint64_t)h->na << 32 | (uint32_t)h->nb);
-    for (const OpDesc &d : ops) mix((uint64_t)d.m << 32 | d.from), mix(d.sm);
-    if (h->list_buf && key == h->list_key && h->list_info.size() == 4 * ops.size()) return SV_OK;
+    // the lists depend on the ops' masks and the sector only: reuse them when those match exactly
+    std::vector<uint32_t> key;
+    key.reserve(3 * ops.size() + 2);
+    key.push_back((uint32_t)h->na);
+    key.push_back((uint32_t)h->nb);
+    for (const OpDesc &d : ops) {
+        key.push_back(d.m);
+        key.push_back(d.from);
+        key.push_back(d.sm);
+    }
+    if (h->list_buf && key == h->list_key) return SV_OK;
     const int N = h->n / 2;
     const size_t ob = list_op_bytes();
     std::vector<uint8_t> host((ops.size() ? ops.size() : 1) * ob);

@@ -203,7 +203,7 @@ struct sv_ctx {
     // sector storage: per-op alpha / beta pair lists (k_build_lists), then the op records
     void *list_buf = nullptr;
     size_t list_bytes = 0;
-    uint64_t list_key = 0;
+    std::vector<uint32_t> list_key;  // sector counts and every op's masks the lists were built for
     std::vector<int> list_info;  // per op: alpha offset, alpha length, beta offset, beta length
     // reduction scratch
     double *partials = nullptr;
