@@ -257,6 +257,25 @@ def sigma_terms(p):
     return D, per
 
 
+def pool_pairs(pool, n_orb, na, nb):
+    """Determinant pairs an operator screening visits: per fermionic operator (kind, i, j, a, b;
+    i, j annihilated, a, b created) the alpha strings matching its alpha pattern times the beta
+    strings matching its beta pattern, C(N - |touched|, n_sigma - |annihilated|) per spin."""
+    from math import comb
+
+    total = 0
+    for op in pool:
+        ann = [int(op[1])] + ([int(op[2])] if op[0] == 2 else [])
+        cre = [int(op[3])] + ([int(op[4])] if op[0] == 2 else [])
+        cnt = 1
+        for spin, ne in ((0, na), (1, nb)):
+            touched = len({j // 2 for j in ann + cre if j % 2 == spin})
+            k = ne - sum(j % 2 == spin for j in ann)
+            cnt *= comb(n_orb - touched, k) if 0 <= k <= n_orb - touched else 0
+        total += cnt
+    return total
+
+
 def fp32_peak_tflops(sm_mhz):
     """Plain (non-tensor) FP32 FMA peak: 152 SMs x 128 lanes x 2 flops x the SM clock."""
     return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
@@ -349,6 +368,60 @@ def run_ours(args, rank, world, local_rank):
         b.close()
         return out
 
+    def timed_pool(dtype, sector, variant):
+        """ADAPT operator screening: the gradient of every operator of the UCCSD pool from the HF
+        reference (config 5: 3,500 operators) at the ansatz state, one sv_pool_gradients call."""
+        pool = inputs.uccsd_pool(n, p["na"] + p["nb"])
+        st = sv.StateVector(n, dtype, stream, sector=(p["na"], p["nb"]) if sector else None)
+        st.set_option(sv.SV_OPT_POOL_VARIANT, variant)
+        st.prepare_hf(p["occ"])
+        st.apply_ansatz(p["ops"], p["theta"])
+        for _ in range(args.warmup):
+            E, g = st.pool_gradients(ham, pool)
+        torch.cuda.synchronize()
+        evs = []
+        l0 = st.launches
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            E, g = st.pool_gradients(ham, pool)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        out = {"ms_per_screening": ms, "operators": len(pool), "operators_per_s": len(pool) / (ms / 1000.0),
+               "gpu_launches_per_screening": (st.launches - l0) // args.steps, "E": E,
+               "max_abs_grad": float(np.max(np.abs(g)))}
+        st.close()
+        return out, g
+
+    def pool_rows():
+        rows = {}
+        ref_g = None
+        for label, dtype, sector, variant in (("dense_c64_lists", "c64", False, 2), ("sector_c64_lists", "c64", True, 2),
+                                              ("sector_c64_scan", "c64", True, 1),
+                                              ("sector_c128_lists", "c128", True, 2)):
+            if args.no_c128 and dtype == "c128":
+                continue
+            r, g = timed_pool(dtype, sector, variant)
+            if ref_g is None:
+                ref_g = g
+            else:
+                r["max_abs_dg_vs_dense_c64"] = float(np.max(np.abs(g - ref_g)))
+            rows[label] = r
+        pairs = pool_pairs(inputs.uccsd_pool(n, p["na"] + p["nb"]), p["n_orb"], p["na"], p["nb"])
+        rows["pairs_per_screening"] = int(pairs)
+        rows["workload"] = "UCCSD pool of %d operators from the HF reference, %d qubits, %d electrons" % (
+            len(inputs.uccsd_pool(n, p["na"] + p["nb"])), n, p["na"] + p["nb"])
+        return rows
+
+    if args.pool_only:  # profiling runs: only the operator screening
+        pr = pool_rows()
+        if rank == 0:
+            print(json.dumps({"profile": "pool-only (not the bench line)", "pool_screening": pr}), flush=True)
+        return 0
     if args.batch_only:  # profiling runs: only the batched launch (config 4)
         rb = timed_batch()
         if rank == 0:
@@ -367,6 +440,7 @@ def run_ours(args, rank, world, local_rank):
     r32d = None if args.no_real else timed("r32", sector=False)
     r32s = None if (args.no_real or args.no_sector) else timed("r32", sector=True)
     rbatch = None if (args.qubits or args.no_batch) else timed_batch()
+    rpool = None if args.no_pool else pool_rows()
     if rank != 0:
         return 0
     K = args.steps
@@ -466,6 +540,8 @@ def run_ours(args, rank, world, local_rank):
         line["real_state"] = real
     if rbatch is not None:
         line["batch_config4"] = rbatch
+    if rpool is not None:
+        line["pool_screening"] = rpool
     if world == 1 and not args.no_cpu_baseline and not args.qubits:
         import oracle
         v, sample, _ = oracle_eval_sample(p)
@@ -528,6 +604,9 @@ def main():
     ap.add_argument("--no-sector", action="store_true", help="skip the sector-storage timing")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch choices")
     ap.add_argument("--no-real", action="store_true", help="skip the real-amplitude (float32) timing")
+    ap.add_argument("--no-pool", action="store_true", help="skip the operator-screening timing")
+    ap.add_argument("--pool-only", action="store_true",
+                    help="profiling: time only the operator screening (no bench line)")
     ap.add_argument("--batch-only", action="store_true",
                     help="profiling only: time just the batched launch (prints no bench line)")
     ap.add_argument("--sector-only", action="store_true",

@@ -219,7 +219,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
  * grad_out[k] = dE/dtheta at theta = 0 of exp(theta G_k) psi = 2 Re <psi|H G_k|psi>
  * / <psi|psi> for each of the n_pool pool operators (any kinds), and *e_out (may
  * be NULL) = E(psi).  One expectation pass writing lambda = (H - c) psi in compact
- * form, then one block per pool operator. */
+ * form, then one block per pool operator (SV_OPT_POOL_VARIANT). */
 sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation *pool, int n_pool, double *e_out,
                             double *grad_out);
 
@@ -335,7 +335,12 @@ typedef enum {
                                        default 8) */
     SV_OPT_SECT_BLOCKS_PER_SM = 9,  /* the same for the sector rotation / adjoint kernels
                                        (default 8) */
-    SV_OPT_RDM_BLOCKS_PER_SM = 10   /* the same for the string-row 1-RDM (default 4) */
+    SV_OPT_RDM_BLOCKS_PER_SM = 10,  /* the same for the string-row 1-RDM (default 4) */
+    SV_OPT_POOL_VARIANT = 11        /* sv_pool_gradients: 0 auto (= 2); 1 string scan: one
+                                       block per operator tests every alpha / beta string;
+                                       2 pair lists: per-operator pair lists built once per
+                                       pool (kept while the pool's operators are unchanged),
+                                       amplitudes and lambda read interleaved */
 } sv_option;
 
 /* Options change launch choices or summation order only: results agree within the

@@ -37,6 +37,10 @@ size_t pool_op_bytes();
 cudaError_t launch_pool_grad(const void *C, const void *L, int dtype, const void *ops, int n_ops, const uint32_t *sa,
                              const uint32_t *sb, const uint16_t *stra, const uint16_t *strb, const uint16_t *ra,
                              const uint16_t *rb, int Da, int Db, double *out, cudaStream_t st);
+cudaError_t launch_interleave(const void *C, const void *L, int dtype, void *CL, size_t count, int sm_count,
+                              cudaStream_t st);
+cudaError_t launch_pool_grad_l(const void *CL, int dtype, const uint32_t *lists, const int *info, int n_ops, int Da,
+                               double *out, cudaStream_t st);
 cudaError_t launch_rdm_gather(const void *psi, int dtype, const uint32_t *sector, uint64_t count,
                               const void *elems, int n_el, int grid, double *partial, cudaStream_t st);
 // sector storage (k_sector.cu)
@@ -475,7 +479,7 @@ static sv_status prepare_reference(sv_handle h) {
 
 // Sector storage: the alpha and beta pair lists of every op (k_build_lists), kept
 // on the device and rebuilt only when the ops' masks (or the sector) change.
-static sv_status ensure_op_lists(sv_handle h, const std::vector<OpDesc> &ops) {
+static sv_status ensure_op_lists(sv_handle h, const std::vector<OpDesc> &ops, OpLists &cache) {
     SV_TRY(ensure_strings(h));
     // the lists depend on the ops' masks and the sector only: reuse them when those match exactly
     std::vector<uint32_t> key;
@@ -487,48 +491,55 @@ static sv_status ensure_op_lists(sv_handle h, const std::vector<OpDesc> &ops) {
         key.push_back(d.from);
         key.push_back(d.sm);
     }
-    if (h->list_buf && key == h->list_key) return SV_OK;
+    if (cache.buf && key == cache.key) return SV_OK;
     const int N = h->n / 2;
     const size_t ob = list_op_bytes();
     std::vector<uint8_t> host((ops.size() ? ops.size() : 1) * ob);
     std::vector<int> info(4 * ops.size());
-    uint32_t off = 0;
+    uint64_t off = 0;
     for (size_t k = 0; k < ops.size(); ++k) {
         int na_l = 0, nb_l = 0;  // the op's beta list follows its alpha list
-        list_op_from(ops[k], N, h->na, h->nb, off, host.data() + k * ob, &na_l, &nb_l);
+        list_op_from(ops[k], N, h->na, h->nb, (uint32_t)off, host.data() + k * ob, &na_l, &nb_l);
         info[4 * k] = (int)off;
         info[4 * k + 1] = na_l;
         info[4 * k + 2] = (int)off + na_l;
         info[4 * k + 3] = nb_l;
-        off += (uint32_t)(na_l + nb_l);
+        off += (uint64_t)(na_l + nb_l);
+        if (off > (uint64_t)INT32_MAX) return fail(h, SV_ERR_ARG, "operator pair lists exceed 2^31 entries");
     }
-    const size_t lb = ((size_t)off * 4 + 16) / 16 * 16, ob_all = std::max<size_t>(host.size(), 16);
-    if (h->list_bytes < lb + ob_all) {
-        dev_free(h, h->list_buf, h->list_bytes);
-        h->list_buf = nullptr;
-        h->list_bytes = 0;
-        SV_TRY(dev_alloc(h, &h->list_buf, lb + ob_all, "operator pair lists"));
-        h->list_bytes = lb + ob_all;
+    auto r16 = [](size_t x) { return (x + 15) / 16 * 16; };
+    const size_t lb = r16((size_t)off * 4 + 16), obb = r16(std::max<size_t>(host.size(), 16)),
+                 ib = r16(std::max<size_t>(info.size() * sizeof(int), 16));
+    if (cache.bytes < lb + obb + ib) {
+        dev_free(h, cache.buf, cache.bytes);
+        cache.buf = nullptr;
+        cache.bytes = 0;
+        cache.key.clear();
+        SV_TRY(dev_alloc(h, &cache.buf, lb + obb + ib, "operator pair lists"));
+        cache.bytes = lb + obb + ib;
     }
-    uint8_t *dops = (uint8_t *)h->list_buf + lb;  // op records after the lists
+    uint8_t *dops = (uint8_t *)cache.buf + lb;  // op records after the lists, then the int4 records
+    int *dinfo = (int *)(dops + obb);
     SV_CUDA(h, cudaMemcpyAsync(dops, host.data(), ops.size() * ob, cudaMemcpyHostToDevice, h->stream));
+    SV_CUDA(h, cudaMemcpyAsync(dinfo, info.data(), info.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
     SV_CUDA(h, launch_build_lists(dops, (int)ops.size(), h->str_sa, h->str_sb, h->str_a, h->str_b, h->rank_a,
-                                  h->rank_b, h->Da, h->Db, (uint32_t *)h->list_buf, h->stream));
+                                  h->rank_b, h->Da, h->Db, (uint32_t *)cache.buf, h->stream));
     h->launches++;
-    SV_CUDA(h, cudaStreamSynchronize(h->stream));  // the host staging vector goes out of scope
-    h->list_key = key;
-    h->list_info = info;
+    SV_CUDA(h, cudaStreamSynchronize(h->stream));  // the host staging vectors go out of scope
+    cache.key = key;
+    cache.info = info;
+    cache.dinfo = dinfo;
     return SV_OK;
 }
 
 static sv_status forward(sv_handle h, const std::vector<OpDesc> &ops, bool checkpoints) {
     const int64_t C = h->ckpt_interval;
-    if (h->storage == 1 && !ops.empty()) SV_TRY(ensure_op_lists(h, ops));
-    const uint32_t *L = (const uint32_t *)h->list_buf;
+    if (h->storage == 1 && !ops.empty()) SV_TRY(ensure_op_lists(h, ops, h->lists));
+    const uint32_t *L = (const uint32_t *)h->lists.buf;
     const int G = sector_grid(h->Db, h->sm_count, h->sect_bps);
     for (size_t k = 0; k < ops.size(); ++k) {
         if (h->storage == 1) {
-            const int *li = &h->list_info[4 * k];
+            const int *li = &h->lists.info[4 * k];
             SV_CUDA(h, launch_rotate_l(h->psi, h->dtype, L + li[0], li[1], L + li[2], li[3], h->Da, ops[k].c,
                                        ops[k].s, G, h->stream));
         } else {
@@ -746,13 +757,13 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
         const int cands[] = {4, 8, 16, 32};
         int best_b = 8;
         float best_t = -1.f;
-        if (h->storage == 1) SV_TRY(ensure_op_lists(h, d));
+        if (h->storage == 1) SV_TRY(ensure_op_lists(h, d, h->lists));
         SV_TRY(ensure_partials(h, (size_t)h->sm_count * 32));
         for (int b : cands) {
             float t;
             if (h->storage == 1) {
-                const uint32_t *L = (const uint32_t *)h->list_buf;
-                const int *li = &h->list_info[4 * k];
+                const uint32_t *L = (const uint32_t *)h->lists.buf;
+                const int *li = &h->lists.info[4 * k];
                 const int G = sector_grid(h->Db, h->sm_count, b);
                 t = time_best(h, e0, e1, [&]() -> sv_status {
                     SV_CUDA(h, launch_rotate_l(h->lam, h->dtype, L + li[0], li[1], L + li[2], li[3], h->Da, d[k].c,
@@ -914,7 +925,9 @@ sv_status sv_destroy(sv_handle h) {
         if (p) cudaFree(p);
     dev_free(h, h->Cbuf, h->Cbuf_bytes);
     dev_free(h, h->Lbuf, h->Lbuf_bytes);
-    dev_free(h, h->list_buf, h->list_bytes);
+    dev_free(h, h->lists.buf, h->lists.bytes);
+    dev_free(h, h->pool_lists.buf, h->pool_lists.bytes);
+    dev_free(h, h->CLbuf, h->CLbuf_bytes);
     dev_free(h, h->partials, h->partials_cap * sizeof(double));
     dev_free(h, h->dout, h->dout_cap * sizeof(double));
     if (h->hpinned) cudaFreeHost(h->hpinned);
@@ -1211,8 +1224,8 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     const int64_t C = h->ckpt_interval;
     for (size_t kk = L; kk-- > 0;) {
         if (sect) {
-            const uint32_t *LB = (const uint32_t *)h->list_buf;
-            const int *li = &h->list_info[4 * kk];
+            const uint32_t *LB = (const uint32_t *)h->lists.buf;
+            const int *li = &h->lists.info[4 * kk];
             SV_CUDA(h, launch_adjoint_l(h->psi, h->lam, h->dtype, LB + li[0], li[1], LB + li[2], li[3], h->Da,
                                         d[kk].c, d[kk].s, G, h->partials + kk * (size_t)G, h->stream));
         } else {
@@ -1261,8 +1274,11 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
     if (n_pool < 0 || (n_pool > 0 && (!pool || !grad_out))) return fail(h, SV_ERR_ARG, "bad pool arguments");
     const int ident[32] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15,
                            16, 17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31};
+    const bool use_lists = h->pool_variant != 1;
     const size_t ob = pool_op_bytes();
-    std::vector<uint8_t> host_ops((size_t)n_pool * ob);
+    std::vector<uint8_t> host_ops(use_lists ? 0 : (size_t)n_pool * ob);
+    std::vector<OpDesc> descs;
+    descs.reserve(n_pool);
     for (int k = 0; k < n_pool; ++k) {
         OpDesc d;
         std::string why;
@@ -1271,7 +1287,8 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
             snprintf(buf, sizeof buf, "pool op %d: ", k);
             return fail(h, SV_ERR_ARG, buf + why);
         }
-        pool_op_from(d, h->n / 2, host_ops.data() + (size_t)k * ob);
+        if (use_lists) descs.push_back(d);
+        else pool_op_from(d, h->n / 2, host_ops.data() + (size_t)k * ob);
     }
     DeviceGuard g(h->device);
     DevTables *T;
@@ -1285,7 +1302,17 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
         SV_TRY(dev_alloc(h, &h->Lbuf, std::max<size_t>(cb, 16), "compact sigma"));
         h->Lbuf_bytes = std::max<size_t>(cb, 16);
     }
-    const size_t op_doubles = ((size_t)n_pool * ob + 7) / 8;
+    if (use_lists && n_pool > 0) {
+        SV_TRY(ensure_op_lists(h, descs, h->pool_lists));
+        if (h->CLbuf_bytes < 2 * cb) {
+            dev_free(h, h->CLbuf, h->CLbuf_bytes);
+            h->CLbuf = nullptr;
+            h->CLbuf_bytes = 0;
+            SV_TRY(dev_alloc(h, &h->CLbuf, std::max<size_t>(2 * cb, 16), "interleaved amplitudes and sigma"));
+            h->CLbuf_bytes = std::max<size_t>(2 * cb, 16);
+        }
+    }
+    const size_t op_doubles = ((size_t)host_ops.size() + 7) / 8;
     SV_TRY(ensure_partials(h, 3 * (size_t)h->Db + op_doubles));
     SV_TRY(ensure_out(h, 2 + (size_t)n_pool));
     const double c = shift_for(h, ham);
@@ -1303,7 +1330,13 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
     h->launches += K ? 2 : 1;
     SV_CUDA(h, launch_reduce_rows(h->partials, 2, h->Db, h->dout, h->stream));
     h->launches++;
-    if (n_pool > 0) {
+    if (n_pool > 0 && use_lists) {
+        SV_CUDA(h, launch_interleave(Cm, h->Lbuf, h->dtype, h->CLbuf, (size_t)h->Da * h->Db, h->sm_count,
+                                     h->stream));
+        SV_CUDA(h, launch_pool_grad_l(h->CLbuf, h->dtype, (const uint32_t *)h->pool_lists.buf, h->pool_lists.dinfo,
+                                      n_pool, h->Da, h->dout + 2, h->stream));
+        h->launches += 2;
+    } else if (n_pool > 0) {
         void *d_ops = h->partials + 3 * (size_t)h->Db;
         SV_CUDA(h, cudaMemcpyAsync(d_ops, host_ops.data(), host_ops.size(), cudaMemcpyHostToDevice, h->stream));
         SV_CUDA(h, launch_pool_grad(Cm, h->Lbuf, h->dtype, d_ops, n_pool, h->str_sa, h->str_sb, h->str_a,
@@ -1426,6 +1459,7 @@ sv_status sv_get_option(sv_handle h, sv_option opt, int64_t *value) {
         case SV_OPT_ROT_BLOCKS_PER_SM: *value = h->rot_bps; return SV_OK;
         case SV_OPT_SECT_BLOCKS_PER_SM: *value = h->sect_bps; return SV_OK;
         case SV_OPT_RDM_BLOCKS_PER_SM: *value = h->rdm_bps; return SV_OK;
+        case SV_OPT_POOL_VARIANT: *value = h->pool_variant; return SV_OK;
     }
     return fail(h, SV_ERR_ARG, "unknown option");
 }
@@ -1480,6 +1514,10 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
         case SV_OPT_RDM_VARIANT:
             if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "rdm variant must be 0, 1 or 2");
             h->rdm_variant = (int)value;
+            return SV_OK;
+        case SV_OPT_POOL_VARIANT:
+            if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "pool variant must be 0, 1 or 2");
+            h->pool_variant = (int)value;
             return SV_OK;
         case SV_OPT_PROFILE:
             h->profile = value != 0;

@@ -165,6 +165,16 @@ struct sv_ham {
     int device = -1;
 };
 
+// Per-operator pair lists kept on the device: the lists, then the op records, then
+// per op (alpha offset, alpha length, beta offset, beta length) as int4.
+struct OpLists {
+    void *buf = nullptr;
+    size_t bytes = 0;
+    std::vector<uint32_t> key;  // sector counts and every op's masks the lists were built for
+    std::vector<int> info;      // the per-op int4 records, host copy
+    const int *dinfo = nullptr; // their device copy (inside buf)
+};
+
 struct sv_ctx {
     int n = 0;
     sv_dtype dtype = SV_C64;
@@ -200,11 +210,11 @@ struct sv_ctx {
     size_t Cbuf_bytes = 0;
     void *Lbuf = nullptr;      // compact sigma [Db][Da] (operator screening)
     size_t Lbuf_bytes = 0;
-    // sector storage: per-op alpha / beta pair lists (k_build_lists), then the op records
-    void *list_buf = nullptr;
-    size_t list_bytes = 0;
-    std::vector<uint32_t> list_key;  // sector counts and every op's masks the lists were built for
-    std::vector<int> list_info;  // per op: alpha offset, alpha length, beta offset, beta length
+    // per-op alpha / beta pair lists (k_build_lists): the ansatz's (sector storage
+    // rotations and adjoint steps) and the screened pool's
+    OpLists lists, pool_lists;
+    void *CLbuf = nullptr;     // compact amplitudes and sigma interleaved [Db][Da][2] (screening)
+    size_t CLbuf_bytes = 0;
     // reduction scratch
     double *partials = nullptr;
     size_t partials_cap = 0;   // doubles
@@ -225,6 +235,7 @@ struct sv_ctx {
     int sect_bps = 8;          // sector k_rotate_l / k_adjoint_l
     int rdm_bps = 4;           // k_rdm_rows
     int rdm_variant = 0;
+    int pool_variant = 0;      // 0 auto (= 2); 1 string scan; 2 pair lists
     // storage layout: address bit perm[q] holds qubit q (identity by default);
     // layout_auto: sv_energy_grad picks it from its operator list
     int perm[32];

@@ -69,3 +69,23 @@ def test_sigma_connection_count_brute_force():
         D, per = bench.sigma_terms({"n_orb": N, "na": na, "nb": nb})
         assert D == len(dets) and counts == {per}
     assert bench.sigma_terms({"n_orb": 15, "na": 5, "nb": 5}) == (9018009, 3501)
+
+
+def test_pool_pair_count_brute_force():
+    """bench.pool_pairs (the pairs one operator screening visits) against a count of the sector
+    determinants on which each pool operator's excitation does not vanish."""
+    sys.path.insert(0, ROOT)
+    import itertools
+    import bench
+    from paper_2405_11567_gb300 import inputs
+    for N, na, nb, ne_pool in [(5, 2, 1, 3), (4, 2, 2, 4), (6, 3, 2, 4), (5, 1, 3, 4)]:
+        sa = [sum(1 << (2 * q) for q in c) for c in itertools.combinations(range(N), na)]
+        sb = [sum(1 << (2 * q + 1) for q in c) for c in itertools.combinations(range(N), nb)]
+        dets = [a | b for a in sa for b in sb]
+        pool = inputs.uccsd_pool(2 * N, ne_pool)
+        want = 0
+        for op in pool:
+            ann = [int(op[1])] + ([int(op[2])] if op[0] == 2 else [])
+            cre = [int(op[3])] + ([int(op[4])] if op[0] == 2 else [])
+            want += sum(1 for x in dets if all(x >> j & 1 for j in ann) and not any(x >> j & 1 for j in cre))
+        assert bench.pool_pairs(pool, N, na, nb) == want

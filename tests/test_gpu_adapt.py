@@ -19,8 +19,9 @@ def _lib():
     sv.lib()
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("dtype,tol", [("c128", 1e-10), ("c64", 1e-5)])
-def test_pool_gradients_match_oracle(dtype, tol):
+def test_pool_gradients_match_oracle(dtype, tol, variant):
     n = 14
     p = inputs.make_problem(n, 6, 30, seed=202)
     pool = np.vstack([inputs.uccsd_pool(n, 6), inputs.qeb_pool(n, 6)[::5]])
@@ -33,6 +34,7 @@ def test_pool_gradients_match_oracle(dtype, tol):
     Eref = np.vdot(psi, sig).real / nrm
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
     st = sv.StateVector(n, dtype)
+    st.set_option(sv.SV_OPT_POOL_VARIANT, variant)
     st.prepare_hf(p["occ"])
     st.apply_ansatz(p["ops"], theta)
     E, g = st.pool_gradients(ham, pool)

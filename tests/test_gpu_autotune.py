@@ -59,6 +59,10 @@ def test_option_round_trip_and_range():
         st.set_option(sv.SV_OPT_ROT_BLOCKS_PER_SM, 0)
     with pytest.raises(sv.SvError):
         st.set_option(sv.SV_OPT_RDM_BLOCKS_PER_SM, 65)
+    st.set_option(sv.SV_OPT_POOL_VARIANT, 1)
+    assert st.option(sv.SV_OPT_POOL_VARIANT) == 1
+    with pytest.raises(sv.SvError):
+        st.set_option(sv.SV_OPT_POOL_VARIANT, 3)
 
 
 def test_batch_autotune_keeps_results():

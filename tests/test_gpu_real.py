@@ -110,8 +110,10 @@ def test_pool_gradients_and_autotune_real(dtype):
         before = st.state()
         st.autotune(ham, p["ops"], theta)
         assert np.array_equal(st.state(), before)
-        _, g = st.pool_gradients(ham, pool)
-        assert np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
+        for variant in (1, 2):
+            st.set_option(sv.SV_OPT_POOL_VARIANT, variant)
+            _, g = st.pool_gradients(ham, pool)
+            assert np.max(np.abs(g - gref)) <= TOL[dtype]["g"]
 
 
 def test_real_handles_reject_complex_only_calls():

@@ -145,8 +145,9 @@ def test_rdm1_matches_oracle(dtype):
     assert np.max(np.abs(st.rdm1() - A.rdm1(sec, psi))) <= TOL[dtype]["rdm"]
 
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("dtype,tol", [("c128", 1e-9), ("c64", 1e-5)])
-def test_pool_gradients_match_oracle(dtype, tol):
+def test_pool_gradients_match_oracle(dtype, tol, variant):
     n = 14
     p = inputs.make_problem(n, 6, 30, seed=202)
     pool = np.vstack([inputs.uccsd_pool(n, 6), inputs.qeb_pool(n, 6)[::5]])
@@ -157,11 +158,58 @@ def test_pool_gradients_match_oracle(dtype, tol):
     nrm = np.vdot(psi, psi).real
     gref = np.array([2 * np.vdot(sig, A.generator_apply(sec, op, psi)).real / nrm for op in pool])
     st = _state(n, 3, 3, dtype)
+    st.set_option(sv.SV_OPT_POOL_VARIANT, variant)
     st.prepare_hf(p["occ"])
     st.apply_ansatz(p["ops"], theta)
-    E, g = st.pool_gradients(sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"]), pool)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    E, g = st.pool_gradients(ham, pool)
     assert abs(E - np.vdot(psi, sig).real / nrm) <= (1e-10 if dtype == "c128" else 1e-5)
     assert np.max(np.abs(g - gref)) <= tol
+    # the pool's pair lists are kept beside the ansatz's: alternating calls, and a
+    # changed pool, give the same answers
+    E2, g2 = st.energy_grad(ham, p["ops"], theta)
+    Eg, gg = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, A.hf_state(sec, p["occ"]))
+    assert abs(E2 - Eg) <= (1e-10 if dtype == "c128" else 1e-5) and np.max(np.abs(g2 - gg)) <= tol
+    _, g3 = st.pool_gradients(ham, pool[::-3])
+    assert np.max(np.abs(g3 - gref[::-3])) <= tol
+    _, g4 = st.pool_gradients(ham, pool)
+    assert np.array_equal(g4, g)
+
+
+def _applies_in(sec, op):
+    """Whether op has a pair in the sector: it annihilates at most N_alpha alpha and
+    N_beta beta spin-orbitals (uccsd_pool rows: kind, i, j, a, b with i, j annihilated)."""
+    ann = [int(op[1])] + ([int(op[2])] if op[0] == 2 else [])
+    return sum(j % 2 == 0 for j in ann) <= sec.na and sum(j % 2 == 1 for j in ann) <= sec.nb
+
+
+@pytest.mark.parametrize("storage", ["dense", "sector"])
+@pytest.mark.parametrize("variant", [1, 2])
+def test_pool_gradients_ops_outside_the_sector(storage, variant):
+    """One alpha electron: every alpha-alpha double has no pair in the sector (empty
+    alpha list), so its gradient is exactly zero; the other operators still match."""
+    n = 12
+    p = inputs.make_problem(n, 4, 20, seed=515)
+    occ = [0, 1, 3, 5]                                       # alpha orbital 0; beta 0, 1, 2
+    sec = oracle.Sector(n, 1, 3)
+    psi0 = A.hf_state(sec, occ)
+    pool = inputs.uccsd_pool(n, 4)
+    rng = np.random.default_rng(5)
+    # an ansatz of beta singles / alpha-beta doubles that stays in the (1, 3) sector
+    keep = [op for op in pool if _applies_in(sec, op)]
+    ans = np.array(keep[:12])
+    theta = rng.uniform(-0.4, 0.4, len(ans))
+    psi = A.apply_ansatz(sec, ans, theta, psi0)
+    sig = A.hamiltonian_apply(sec, p["h"], p["eri"], p["e_nuc"], psi)
+    gref = np.array([2 * np.vdot(sig, A.generator_apply(sec, op, psi)).real for op in pool])
+    st = sv.StateVector(n, "c128", sector=(1, 3) if storage == "sector" else None)
+    st.set_option(sv.SV_OPT_POOL_VARIANT, variant)
+    st.prepare_hf(occ)
+    st.apply_ansatz(ans, theta)
+    _, g = st.pool_gradients(sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"]), pool)
+    assert np.max(np.abs(g - gref)) <= 1e-9
+    dead = [k for k, op in enumerate(pool) if not _applies_in(sec, op)]
+    assert dead and all(g[k] == 0.0 for k in dead)
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
