@@ -28,6 +28,8 @@ struct OpArgs {
     uint32_t m, from, sm;
     int pos0, pos1, pos2, pos3;
     double c, s;
+    double t;    // tan(theta / 2) = s / (1 + c), for the shear form
+    int shear;   // 1 when c > 0 (|t| < 1): float64 amplitudes rotate by three shears
 };
 
 static OpArgs to_args(const OpDesc &d) {
@@ -35,8 +37,28 @@ static OpArgs to_args(const OpDesc &d) {
     a.m = d.m; a.from = d.from; a.sm = d.sm;
     a.pos0 = d.pos[0]; a.pos1 = d.pos[1]; a.pos2 = d.pos[2]; a.pos3 = d.pos[3];
     a.c = d.c; a.s = d.s;
+    a.shear = d.c > 0.0;
+    a.t = a.shear ? d.s / (1.0 + d.c) : 0.0;
     return a;
 }
+
+// (p, q) <- (c p - s q, s p + c q), the rotation [[c, -s], [s, c]], as three shears
+// (Paeth's decomposition, valid for c > -1 with t = tan of the half angle):
+// p1 = p - t q, q' = q + s p1, p' = p1 - t q'.  Three multiply-adds per component
+// instead of four: the float64 kernels are bound by GB300's FP64 pipe, not by HBM, so
+// this is what moves them.  Rounding differs from the direct form only in the last
+// bits; a quarter turn (t = 1, s = 1) still maps basis states exactly.
+template <typename R>
+__device__ __forceinline__ void shear3(R &p, R &q, R t, R s) {
+    const R p1 = fma(-t, q, p);
+    q = fma(s, p1, q);
+    p = fma(-t, q, p1);
+}
+__device__ __forceinline__ void rot_shear(double2 &p, double2 &q, double t, double s) {
+    shear3(p.x, q.x, t, s);
+    shear3(p.y, q.y, t, s);
+}
+__device__ __forceinline__ void rot_shear(double &p, double &q, double t, double s) { shear3(p, q, t, s); }
 
 template <int NB>
 __device__ __forceinline__ uint32_t pair_index(uint32_t k, const OpArgs &a) {
@@ -153,10 +175,29 @@ template <int V> __device__ __forceinline__ void st_vec(double *__restrict__ p, 
 // and the sign is the same across the group only if no sign-mask bit lies below
 // log2(V) -- it is therefore evaluated per amplitude.  Two groups per iteration keep
 // four independent vector loads in flight per thread.
+// psi'[x] = c psi[x] - s sn psi[x'], psi'[x'] = c psi[x'] + s sn psi[x] on one pair
+// (s = -1 when neg); float64 amplitudes use the shear form when the op allows it.
+template <typename A>
+__device__ __forceinline__ void rotate_pair(A &p, A &q, bool neg, real_of<A> c, real_of<A> sn, real_of<A> th,
+                                            bool shear) {
+    using R = real_of<A>;
+    const R ss = neg ? -sn : sn;
+    if constexpr (sizeof(R) == 8) {
+        if (shear) {
+            rot_shear(p, q, neg ? -th : th, ss);
+            return;
+        }
+    }
+    const A p0 = p, q0 = q;
+    p = lin2<A>(c, p0, -ss, q0);
+    q = lin2<A>(c, q0, ss, p0);
+}
+
 template <typename A, int NB, int V>
 __global__ void __launch_bounds__(kThreads) k_rotate(A *__restrict__ psi, uint32_t ngroups, OpArgs a) {
     using R = real_of<A>;
-    const R c = (R)a.c, sn = (R)a.s;
+    const R c = (R)a.c, sn = (R)a.s, th = (R)a.t;
+    const bool shear = a.shear != 0;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += 2 * stride) {
         const uint32_t g2 = g + stride;
@@ -170,22 +211,13 @@ __global__ void __launch_bounds__(kThreads) k_rotate(A *__restrict__ psi, uint32
             ld_vec<V>(psi + (x2 ^ a.m), v2);
         }
         #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            const R ss = (__popc((x + i) & a.sm) & 1) ? -sn : sn;
-            const A p = u[i], q = v[i];
-            u[i] = lin2<A>(c, p, -ss, q);
-            v[i] = lin2<A>(c, q, ss, p);
-        }
+        for (int i = 0; i < V; ++i) rotate_pair<A>(u[i], v[i], (__popc((x + i) & a.sm) & 1) != 0, c, sn, th, shear);
         st_vec<V>(psi + x, u);
         st_vec<V>(psi + (x ^ a.m), v);
         if (two) {
             #pragma unroll
-            for (int i = 0; i < V; ++i) {
-                const R ss = (__popc((x2 + i) & a.sm) & 1) ? -sn : sn;
-                const A p = u2[i], q = v2[i];
-                u2[i] = lin2<A>(c, p, -ss, q);
-                v2[i] = lin2<A>(c, q, ss, p);
-            }
+            for (int i = 0; i < V; ++i)
+                rotate_pair<A>(u2[i], v2[i], (__popc((x2 + i) & a.sm) & 1) != 0, c, sn, th, shear);
             st_vec<V>(psi + x2, u2);
             st_vec<V>(psi + (x2 ^ a.m), v2);
         }
@@ -199,7 +231,8 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(A *__restrict__ psi, A *__
                                                       uint32_t ngroups, OpArgs a, double *__restrict__ partial) {
     using R = real_of<A>;
     __shared__ double red[kThreads / 32];
-    const R c = (R)a.c, sn = (R)a.s;
+    const R c = (R)a.c, sn = (R)a.s, th = (R)a.t;
+    const bool shear = a.shear != 0;
     const uint32_t stride = gridDim.x * blockDim.x;
     double acc = 0.0;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
@@ -213,16 +246,29 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(A *__restrict__ psi, A *__
         #pragma unroll
         for (int i = 0; i < V; ++i) {
             const bool neg = __popc((x + i) & a.sm) & 1;
-            // <lambda|G psi> on the pair: conj(lu) (-s v) + conj(lv) (s u); real part
-            const R ti = re_dot(lv[i], u[i]) - re_dot(lu[i], v[i]);
-            t += neg ? -ti : ti;
-            // U^dagger: psi'[x] = c u + s sn v ; psi'[x'] = c v - s sn u  (lambda alike)
-            const R ss = neg ? -sn : sn;
-            const A p = u[i], q = v[i], lp = lu[i], lq = lv[i];
-            u[i] = lin2<A>(c, p, ss, q);
-            v[i] = lin2<A>(c, q, -ss, p);
-            lu[i] = lin2<A>(c, lp, ss, lq);
-            lv[i] = lin2<A>(c, lq, -ss, lp);
+            // <lambda|G psi> on the pair: conj(lu) (-s v) + conj(lv) (s u); real part.
+            // U^dagger: psi'[x] = c u + s sn v ; psi'[x'] = c v - s sn u  (lambda alike),
+            // the forward rotation with the sign of the angle flipped.
+            if constexpr (sizeof(R) == 8) {
+                // float64: the product terms chained into t by multiply-adds (sign on the
+                // lambda operand), four per complex pair instead of six
+                A plv = lv[i], plu = lu[i];
+                if (neg) {
+                    plv = mka<A>(-re(plv), -im(plv));
+                    plu = mka<A>(-re(plu), -im(plu));
+                }
+                t = fma(re(plv), re(u[i]), t);
+                t = fma(-re(plu), re(v[i]), t);
+                if constexpr (AmpT<A>::kCplx) {
+                    t = fma(im(plv), im(u[i]), t);
+                    t = fma(-im(plu), im(v[i]), t);
+                }
+            } else {
+                const R ti = re_dot(lv[i], u[i]) - re_dot(lu[i], v[i]);
+                t += neg ? -ti : ti;
+            }
+            rotate_pair<A>(u[i], v[i], !neg, c, sn, th, shear);
+            rotate_pair<A>(lu[i], lv[i], !neg, c, sn, th, shear);
         }
         acc += (double)t;
         st_vec<V>(psi + x, u);

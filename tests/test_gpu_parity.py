@@ -119,6 +119,29 @@ def test_config2_energy_grad(dtype):
     assert np.max(np.abs(st.state()[sec.dets.astype(np.int64)] - psi)) <= TOL[dtype]["amp"] * 10
 
 
+@pytest.mark.parametrize("dtype", ["c128", "r64", "c64"])
+def test_large_angles_both_rotation_forms(dtype):
+    """Angles over the whole circle: float64 amplitudes rotate by three shears when
+    cos(theta) > 0 and by the direct form otherwise; both match the oracle, including
+    exact quarter and half turns."""
+    n = 10
+    p = inputs.make_problem(n, 4, 40, seed=616)
+    rng = np.random.default_rng(17)
+    theta = rng.uniform(-np.pi, np.pi, len(p["ops"]))
+    theta[:4] = [np.pi / 2, -np.pi / 2, np.pi, -np.pi]
+    sec = _oracle_problem(p)
+    psi0 = A.hf_state(sec, p["occ"])
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(n, dtype)
+    st.prepare_hf(p["occ"])
+    E, g = st.energy_grad(ham, p["ops"], theta)
+    tol = TOL["c64" if dtype == "c64" else "c128"]
+    assert abs(E - Eref) <= tol["E"] and np.max(np.abs(g - gref)) <= tol["g"]
+    psi = A.apply_ansatz(sec, p["ops"], theta, psi0)
+    assert np.max(np.abs(st.state()[sec.dets.astype(np.int64)] - psi)) <= tol["amp"] * 10
+
+
 def test_config2_gradient_central_differences():
     p = inputs.config_problem(2)
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
