@@ -403,13 +403,13 @@ def run_ours(args, rank, world, local_rank):
         for label, dtype, sector, variant in (("dense_c64_lists", "c64", False, 2), ("sector_c64_lists", "c64", True, 2),
                                               ("sector_c64_scan", "c64", True, 1),
                                               ("sector_c128_lists", "c128", True, 2)):
-            if args.no_c128 and dtype == "c128":
+            if (args.no_c128 and dtype == "c128") or (args.pool_storage == "sector" and not sector):
                 continue
             r, g = timed_pool(dtype, sector, variant)
             if ref_g is None:
-                ref_g = g
+                ref_g, ref_label = g, label
             else:
-                r["max_abs_dg_vs_dense_c64"] = float(np.max(np.abs(g - ref_g)))
+                r["max_abs_dg_vs_" + ref_label] = float(np.max(np.abs(g - ref_g)))
             rows[label] = r
         pairs = pool_pairs(inputs.uccsd_pool(n, p["na"] + p["nb"]), p["n_orb"], p["na"], p["nb"])
         rows["pairs_per_screening"] = int(pairs)
@@ -607,6 +607,8 @@ def main():
     ap.add_argument("--no-pool", action="store_true", help="skip the operator-screening timing")
     ap.add_argument("--pool-only", action="store_true",
                     help="profiling: time only the operator screening (no bench line)")
+    ap.add_argument("--pool-storage", choices=["all", "sector"], default="all",
+                    help="operator screening rows: every storage, or sector storage only (no 2^n vector)")
     ap.add_argument("--batch-only", action="store_true",
                     help="profiling only: time just the batched launch (prints no bench line)")
     ap.add_argument("--sector-only", action="store_true",

@@ -313,13 +313,22 @@ typedef enum {
                                        (0 = none; default 0) */
     SV_OPT_MAX_BYTES = 2,           /* cap on device bytes this handle may allocate
                                        (0 = no cap); checkpoints are dropped to fit */
-    SV_OPT_EXPECT_VARIANT = 3,      /* 0 auto (= 3 where its rows fit in shared memory,
-                                       else 2); 1 record scan: one thread per sector
-                                       determinant tests every mask group (dense storage
-                                       only); 2 string rows: compact alpha/beta-string
-                                       matrix, one block per beta string; 3 string rows
-                                       split: the alpha-beta doubles in a second kernel
-                                       that stages partner rows in shared memory */
+    SV_OPT_EXPECT_VARIANT = 3,      /* 0 auto (= 4 for complex64 / real float32 states
+                                       of at least 2^20 sector determinants whose
+                                       same-spin couplings fill at least 5% of a string
+                                       space of at most 4096 strings; else 3 where its
+                                       rows fit in shared memory; else 2); 1 record scan:
+                                       one thread per sector determinant tests every mask
+                                       group (dense storage only); 2 string rows: compact
+                                       alpha/beta-string matrix, one block per beta
+                                       string; 3 string rows split: the alpha-beta
+                                       doubles in a second kernel that stages partner rows
+                                       in shared memory; 4 (single precision; float64
+                                       states take 3): split, with the same-spin part as
+                                       two dense float32 products (cuBLAS) in the
+                                       string-blocked basis, Ma X + X Mb^T; Ma, Mb are
+                                       built once per Hamiltonian and sector (4 (Da^2 +
+                                       Db^2) bytes) */
     SV_OPT_RDM_VARIANT = 4,         /* 0 auto (= 2); 1 sector gather: one thread per sector
                                        determinant (dense storage only); 2 string rows: one
                                        block per beta string of the compact matrix */

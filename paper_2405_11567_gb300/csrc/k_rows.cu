@@ -33,6 +33,8 @@
 // in shared memory with coalesced loads and sums the alpha-beta part of sigma (and
 // its energy share); k_sigma_rows<SPLIT> then adds every other group, reading its
 // own row from shared memory, and completes sigma and the row's energy.
+#include <cublas_v2.h>
+
 #include "sv_internal.h"
 #include "sv_sigma.cuh"
 
@@ -52,6 +54,7 @@ struct RowArgs {
     double *partial;        // [3][Db]: energy, norm, alpha-beta energy share
     const R *W2;            // [NP][NP] same-spin antisymmetrised (q1p1|q2p2) - (q1p2|q2p1), pair-indexed
     int Db;
+    int same_gemm;          // 1: k_sigma_ab leaves the string-only parts to the same-spin products
 };
 
 // Per-block lists of everything that depends only on the block's beta string b.
@@ -75,7 +78,7 @@ struct BetaDouble {
 
 constexpr int kMaxOrb = 16;
 constexpr int kMaxPairs = 120;   // C(16, 2)
-constexpr int kMaxBS = 64;       // nb (N - nb) <= 8 * 8
+constexpr int kMaxBS = 65;       // nb (N - nb) <= 8 * 8, plus the row's own slot (variant 4)
 constexpr int kMaxBD = 784;      // C(8, 2)^2
 
 template <typename Amp>
@@ -534,11 +537,25 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
                 s_M[k] = between(2 * r + 1, 2 * s + 1);
                 s_bf[k] = bf;
                 s_cb[k] = par(xb & s_M[k]);
-                R v = T.hm[s * N + r];
-                for (uint32_t o2 = b; o2; o2 &= o2 - 1u) v += T.Dt[(s * N + r) * N + __ffs(o2) - 1];
+                R v = 0;
+                if (!A.same_gemm) {  // else the beta string's own part is in the beta product
+                    v = T.hm[s * N + r];
+                    for (uint32_t o2 = b; o2; o2 &= o2 - 1u) v += T.Dt[(s * N + r) * N + __ffs(o2) - 1];
+                }
                 s_vb[k] = v;
                 ++k;
             }
+        }
+        if (A.same_gemm) {
+            // the row itself as one more staged row: the part of the alpha singles that
+            // depends on b, sum_{k in b} (qp|kk), with no beta excitation (s_t = -1)
+            s_Jb[k] = Ib;
+            s_t[k] = -1;
+            s_M[k] = 0;
+            s_bf[k] = b;
+            s_cb[k] = 0;
+            s_vb[k] = 0;
+            ++k;
         }
         n_bs = k;
     }
@@ -565,13 +582,20 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
             if (k < kn && p != q) {
                 const int lo = min(p, q), hi = max(p, q);
                 const uint32_t mB = ((1u << hi) - 1u) & ~((1u << lo) - 1u);  // beta orbitals lo..hi-1
-                v = flip_sign<R>(T.eri[(size_t)qp * NN + s_t[k0 + k]], (uint32_t)par(s_bf[k0 + k] & mB));
+                const int t = s_t[k0 + k];
+                R w = 0;
+                if (t >= 0) {
+                    w = T.eri[(size_t)qp * NN + t];
+                } else {  // own row: sum over the beta string's orbitals of (qp|kk)
+                    for (uint32_t o = b; o; o &= o - 1u) w += T.Jt[(size_t)qp * N + __ffs(o) - 1];
+                }
+                v = flip_sign<R>(w, (uint32_t)par(s_bf[k0 + k] & mB));
             }
             eriS[i] = v;
         }
         for (int i = threadIdx.x; i < K * N; i += kAbThreads) {
             const int k = i / N, o = i - k * N;
-            JtS[i] = k < kn ? T.Jt[(size_t)s_t[k0 + k] * N + o] : (R)0;
+            JtS[i] = (k < kn && s_t[k0 + k] >= 0) ? T.Jt[(size_t)s_t[k0 + k] * N + o] : (R)0;
         }
         __syncthreads();
         uint32_t Mk[K];
@@ -661,6 +685,146 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
     }
 }
 
+// ---------------------------------------------------------------- same-spin products
+//
+// Expectation variant 4 (single-precision states).  In the string-blocked basis
+// (alpha creators before beta creators) the same-spin part of H is a matrix on one
+// string index times the identity on the other:
+//   Ma[a][a'] = alpha singles p -> q with h_qp + sum_{k in a} ((qp|kk) - (qk|kp)),
+//               and alpha-alpha doubles (q1p1|q2p2) - (q1p2|q2p1),
+// with the sign of the excitation on the alpha string alone; Mb likewise for beta.
+// So two dense products, G = Ma X + X Mb^T over the phased matrix X = phi C, give that
+// part of sigma~ = phi sigma.  The rest stays in k_sigma_ab (alpha-beta doubles, the
+// beta singles' dependence on a, and the alpha singles' dependence on b through the
+// row's own slot) and k_sigma_comb (diagonal, phase back, sum, energy).  The dense
+// products do every multiply of a matrix with 17% nonzeros at 30 qubits, but on the
+// FMA pipe at full rate instead of through scattered shared-memory gathers.
+
+// Block I < Da builds alpha row I of Ma, block Da + I beta row I of Mb; thread 0 also
+// writes the string's one-spin diagonal energy sum_k h_kk + sum_{k<l} [kk|ll]-[kl|lk]
+// (spin-orbital tables hdiag, Jp) to dA / dB.  Ma and Mb must be zeroed before.
+__global__ void __launch_bounds__(128) k_same_mats(SigmaTables<float> T, int Db, float *__restrict__ Ma,
+                                                    float *__restrict__ Mb, double *__restrict__ dA,
+                                                    double *__restrict__ dB) {
+    __shared__ uint8_t occ[kMaxOrb], emp[kMaxOrb];
+    __shared__ int s_no, s_ne;
+    const bool beta = (int)blockIdx.x >= T.Da;
+    const int I = beta ? (int)blockIdx.x - T.Da : (int)blockIdx.x, D = beta ? Db : T.Da, N = T.N, spin = beta;
+    const uint16_t *rk = beta ? T.rb : T.ra;
+    const uint32_t str = beta ? T.strb[I] : T.stra[I], pps = prefix_parity(str);
+    float *row = (beta ? Mb : Ma) + (size_t)I * D;
+    if (threadIdx.x == 0) {
+        int no = 0, ne = 0;
+        for (int o = 0; o < N; ++o) {
+            if ((str >> o) & 1u) occ[no++] = (uint8_t)o;
+            else emp[ne++] = (uint8_t)o;
+        }
+        s_no = no;
+        s_ne = ne;
+        double d = 0.0;
+        for (int i = 0; i < no; ++i) {
+            const int k = 2 * occ[i] + spin;
+            d += T.hdiag[k];
+            for (int j = i + 1; j < no; ++j) d += T.Jp[k * T.n + 2 * occ[j] + spin];
+        }
+        (beta ? dB : dA)[I] = d;
+    }
+    __syncthreads();
+    const int no = s_no, ne = s_ne, nsg = no * ne, npo = no * (no - 1) / 2, npe = ne * (ne - 1) / 2;
+    for (int t = threadIdx.x; t < nsg + npo * npe; t += blockDim.x) {
+        float v;
+        uint32_t m, sg;
+        if (t < nsg) {
+            const int p = occ[t / ne], q = emp[t % ne];
+            m = (1u << p) | (1u << q);
+            v = T.hm[q * N + p];
+            const float *dt = T.Dt + (q * N + p) * N;
+            for (uint32_t o = str; o; o &= o - 1u) v += dt[__ffs(o) - 1];
+            sg = (uint32_t)par(pps & m) ^ (uint32_t)(p < q);
+        } else {
+            int io = (t - nsg) / npe, ie = (t - nsg) % npe, i1 = 0, e1 = 0;
+            while (io >= no - 1 - i1) io -= no - 1 - i1++;  // pair index -> (i1, i1 + 1 + io)
+            while (ie >= ne - 1 - e1) ie -= ne - 1 - e1++;
+            const int p1 = occ[i1], p2 = occ[i1 + 1 + io], q1 = emp[e1], q2 = emp[e1 + 1 + ie];
+            m = (1u << p1) | (1u << p2) | (1u << q1) | (1u << q2);
+            v = eri4<float>(T, q1, p1, q2, p2) - eri4<float>(T, q1, p2, q2, p1);
+            sg = (uint32_t)par(pps & m) ^ double_order_sign(p1, p2, q1, q2);
+        }
+        row[rk[str ^ m]] = sg ? -v : v;
+    }
+}
+
+// X[plane][Ib][Ia] = phi(a, b) * component of C[Ib][Ia] (planes: re, im).
+template <typename Amp>
+__global__ void __launch_bounds__(kThreads) k_phase_planar(const Amp *__restrict__ C, const uint16_t *__restrict__ stra,
+                                                           const uint16_t *__restrict__ strb, int Da, int Db,
+                                                           float *__restrict__ X) {
+    const size_t plane = (size_t)Da * Db;
+    for (int Ib = blockIdx.x; Ib < Db; Ib += gridDim.x) {
+        const uint32_t ppb = prefix_parity(strb[Ib]);
+        const size_t off = (size_t)Ib * Da;
+        for (int Ia = threadIdx.x; Ia < Da; Ia += blockDim.x) {
+            const uint32_t neg = (uint32_t)par(stra[Ia] & ppb);
+            const Amp c = C[off + Ia];
+            X[off + Ia] = flip_sign<float>(re(c), neg);
+            if constexpr (AmpT<Amp>::kCplx) X[plane + off + Ia] = flip_sign<float>(im(c), neg);
+        }
+    }
+}
+
+// One block per row b: sigma[b][a] = (sigma_ab part already in the output) + d(a, b) C
+// + phi(a, b) G[b][a], with the diagonal d = E_nuc - c + dA[a] + dB[b] + sum over
+// alpha orbitals p in a of sum over beta orbitals q in b of [2p | 2q+1] (float64);
+// the row's energy and norm as in k_sigma_same (fixed-order float64 sums).
+template <typename Amp>
+__global__ void __launch_bounds__(kThreads) k_sigma_comb(RowArgs<Amp> A, SameGemm g) {
+    using R = real_of<Amp>;
+    __shared__ double xb[kMaxOrb];
+    __shared__ double red[2 * kThreads / 32];
+    const SigmaTables<R> &T = A.T;
+    const int Ib = blockIdx.x, Da = T.Da, N = T.N;
+    const uint32_t b = T.strb[Ib], ppb = prefix_parity(b);
+    if ((int)threadIdx.x < N) {
+        const int k = 2 * (int)threadIdx.x;
+        double sx = 0.0;
+        for (uint32_t o = b; o; o &= o - 1u) {
+            const int l = 2 * (__ffs(o) - 1) + 1;
+            sx += T.Jp[min(k, l) * T.n + max(k, l)];
+        }
+        xb[threadIdx.x] = sx;
+    }
+    __syncthreads();
+    const double db = T.e_shift + g.dB[Ib];
+    const size_t plane = (size_t)Da * A.Db, off = (size_t)Ib * Da;
+    double e_acc = 0.0, n_acc = 0.0;
+    for (int Ia = threadIdx.x; Ia < Da; Ia += blockDim.x) {
+        const uint32_t a = T.stra[Ia], neg = (uint32_t)par(a & ppb);
+        double d = db + g.dA[Ia];
+        for (uint32_t o = a; o; o &= o - 1u) d += xb[__ffs(o) - 1];
+        const Amp c0 = A.C[off + Ia];
+        Amp acc;
+        if constexpr (AmpT<Amp>::kCplx)
+            acc = mka<Amp>(fmaf((R)d, re(c0), flip_sign<float>(g.G[off + Ia], neg)),
+                           fmaf((R)d, im(c0), flip_sign<float>(g.G[plane + off + Ia], neg)));
+        else
+            acc = mka<Amp>(fmaf((R)d, re(c0), flip_sign<float>(g.G[off + Ia], neg)), (R)0);
+        e_acc += dre_dot(c0, acc);
+        n_acc += dre_dot(c0, c0);
+        if (A.lam) {
+            const Amp u = A.lam[A.sa_s[Ia] | A.sb_s[Ib]];
+            A.lam[A.sa_s[Ia] | A.sb_s[Ib]] = add_a<Amp>(acc, u);
+        } else if (A.lamc) {
+            const Amp u = A.lamc[off + Ia];
+            A.lamc[off + Ia] = add_a<Amp>(acc, u);
+        }
+    }
+    block_sum2(e_acc, n_acc, red);
+    if (threadIdx.x == 0) {
+        A.partial[Ib] = e_acc + A.partial[2 * A.Db + Ib];
+        A.partial[A.Db + Ib] = n_acc;
+    }
+}
+
 // C[Ib][Ia] = psi[sa[Ia] | sb[Ib]]
 template <typename A>
 __global__ void __launch_bounds__(kThreads) k_compact(const A *__restrict__ psi, A *__restrict__ C,
@@ -703,6 +867,7 @@ static RowArgs<Amp> row_args(const void *C, void *lam, void *lamc, int n, const 
     A.T.N = T.N; A.T.n = n; A.T.Da = T.Da; A.T.maskN = (1u << T.N) - 1u;
     A.C = (const Amp *)C; A.lam = (Amp *)lam; A.lamc = (Amp *)lamc; A.sa_s = T.sa_s; A.sb_s = T.sb_s;
     A.partial = partial; A.Db = T.Db; A.W2 = (const R *)T.W2;
+    A.same_gemm = 0;
     return A;
 }
 
@@ -791,12 +956,48 @@ static cudaError_t launch_ab_k(const RowArgs<double> &A, int K, size_t smem, cud
     return launch_ab_k4<double, 2, 4, 6, 8>(A, K, smem, st);
 }
 
+// G = Ma X + X Mb^T on every plane (column-major views: X and G are Da x (planes Db),
+// Ma is Da x Da, Mb Db x Db; both symmetric).
+static cudaError_t same_products(const SameGemm &g, int Da, int Db) {
+    cublasHandle_t hb = (cublasHandle_t)g.blas;
+    const float one = 1.f, zero = 0.f;
+    cublasStatus_t s = cublasSgemm(hb, CUBLAS_OP_N, CUBLAS_OP_N, Da, g.planes * Db, Da, &one, g.Ma, Da, g.X, Da,
+                                   &zero, g.G, Da);
+    if (s != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    s = cublasSgemmStridedBatched(hb, CUBLAS_OP_N, CUBLAS_OP_N, Da, Db, Db, &one, g.X, Da, (long long)Da * Db, g.Mb,
+                                  Db, 0, &one, g.G, Da, (long long)Da * Db, g.planes);
+    if (s != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
+    return cudaGetLastError();
+}
+
 template <typename Amp>
-static cudaError_t launch_rows_t(const RowArgs<Amp> &A, const RowTables &T, int dtype, int K, cudaStream_t st) {
+static cudaError_t launch_same_t(RowArgs<Amp> A, const RowTables &T, int dtype, int K, const SameGemm &g,
+                                 int sm_count, cudaStream_t st) {
+    if constexpr (sizeof(real_of<Amp>) != 4) {
+        return cudaErrorInvalidValue;  // single-precision states only
+    } else {
+        const int grid = T.Db < sm_count * 8 ? T.Db : sm_count * 8;
+        k_phase_planar<Amp><<<grid, kThreads, 0, st>>>(A.C, T.stra, T.strb, T.Da, T.Db, g.X);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = same_products(g, T.Da, T.Db);
+        if (e != cudaSuccess) return e;
+        A.same_gemm = 1;
+        e = launch_ab_k(A, K, ab_smem(dtype, K, T), st);
+        if (e != cudaSuccess) return e;
+        k_sigma_comb<Amp><<<T.Db, kThreads, 0, st>>>(A, g);
+        return cudaGetLastError();
+    }
+}
+
+template <typename Amp>
+static cudaError_t launch_rows_t(const RowArgs<Amp> &A, const RowTables &T, int dtype, int K, const SameGemm *g,
+                                 int sm_count, cudaStream_t st) {
     if (K == 0) {
         k_sigma_rows<Amp><<<T.Db, kRowThreads, 0, st>>>(A);
         return cudaGetLastError();
     }
+    if (g) return launch_same_t<Amp>(A, T, dtype, K, *g, sm_count, st);
     cudaError_t e = launch_ab_k(A, K, ab_smem(dtype, K, T), st);
     if (e != cudaSuccess) return e;
     if (same_smem(dtype, T, true) <= kSameSmemCap) {
@@ -815,12 +1016,26 @@ static cudaError_t launch_rows_t(const RowArgs<Amp> &A, const RowTables &T, int 
 
 // K: rows per chunk of the split form (sigma_ab_chunk), 0 for the single-kernel form.
 // partial must hold 3 * Db doubles (rows: energy, norm, alpha-beta energy share).
+// g (may be NULL): the same-spin products of variant 4 (single-precision states, K > 0):
+// launches the phase kernel, two cuBLAS products, k_sigma_ab and k_sigma_comb.
 cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &T, const double *hdiag,
-                              const double *Jp, double e_shift, double *partial, int K, cudaStream_t st) {
+                              const double *Jp, double e_shift, double *partial, int K, cudaStream_t st,
+                              const SameGemm *g, int sm_count) {
     cudaError_t e = cudaErrorInvalidValue;
     SV_DISPATCH_AMP(dtype, e = launch_rows_t<A>(row_args<A>(C, lam, lamc, n, T, hdiag, Jp, e_shift, partial), T, dtype,
-                                                K, st));
+                                                K, g, sm_count, st));
     return e;
+}
+
+// Ma, Mb (zeroed here), dA, dB of the sector for single-precision tables.
+cudaError_t launch_same_mats(int n, const RowTables &T, const double *hdiag, const double *Jp, float *Ma, float *Mb,
+                             double *dA, double *dB, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(Ma, 0, sizeof(float) * (size_t)T.Da * T.Da, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(Mb, 0, sizeof(float) * (size_t)T.Db * T.Db, st);
+    if (e != cudaSuccess) return e;
+    RowArgs<float> A = row_args<float>(nullptr, nullptr, nullptr, n, T, hdiag, Jp, 0.0, nullptr);
+    k_same_mats<<<T.Da + T.Db, 128, 0, st>>>(A.T, T.Db, Ma, Mb, dA, dB);
+    return cudaGetLastError();
 }
 
 }  // namespace svk

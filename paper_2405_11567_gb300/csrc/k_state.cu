@@ -48,6 +48,14 @@ static OpArgs to_args(const OpDesc &d) {
 // instead of four: the float64 kernels are bound by GB300's FP64 pipe, not by HBM, so
 // this is what moves them.  Rounding differs from the direct form only in the last
 // bits; a quarter turn (t = 1, s = 1) still maps basis states exactly.
+// x or -x by flipping the sign bit (an integer operation: keeps the FP64 pipe free).
+__device__ __forceinline__ double neg_if(double x, bool neg) {
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)neg << 63));
+}
+__device__ __forceinline__ float neg_if(float x, bool neg) {
+    return __int_as_float(__float_as_int(x) ^ ((int)neg << 31));
+}
+
 template <typename R>
 __device__ __forceinline__ void shear3(R &p, R &q, R t, R s) {
     const R p1 = fma(-t, q, p);
@@ -181,13 +189,18 @@ template <typename A>
 __device__ __forceinline__ void rotate_pair(A &p, A &q, bool neg, real_of<A> c, real_of<A> sn, real_of<A> th,
                                             bool shear) {
     using R = real_of<A>;
-    const R ss = neg ? -sn : sn;
     if constexpr (sizeof(R) == 8) {
+        const R ss = neg_if(sn, neg);
         if (shear) {
-            rot_shear(p, q, neg ? -th : th, ss);
+            rot_shear(p, q, neg_if(th, neg), ss);
             return;
         }
+        const A p0 = p, q0 = q;
+        p = lin2<A>(c, p0, -ss, q0);
+        q = lin2<A>(c, q0, ss, p0);
+        return;
     }
+    const R ss = neg ? -sn : sn;
     const A p0 = p, q0 = q;
     p = lin2<A>(c, p0, -ss, q0);
     q = lin2<A>(c, q0, ss, p0);
@@ -252,16 +265,11 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(A *__restrict__ psi, A *__
             if constexpr (sizeof(R) == 8) {
                 // float64: the product terms chained into t by multiply-adds (sign on the
                 // lambda operand), four per complex pair instead of six
-                A plv = lv[i], plu = lu[i];
-                if (neg) {
-                    plv = mka<A>(-re(plv), -im(plv));
-                    plu = mka<A>(-re(plu), -im(plu));
-                }
-                t = fma(re(plv), re(u[i]), t);
-                t = fma(-re(plu), re(v[i]), t);
+                t = fma(neg_if(re(lv[i]), neg), re(u[i]), t);
+                t = fma(neg_if(re(lu[i]), !neg), re(v[i]), t);
                 if constexpr (AmpT<A>::kCplx) {
-                    t = fma(im(plv), im(u[i]), t);
-                    t = fma(-im(plu), im(v[i]), t);
+                    t = fma(neg_if(im(lv[i]), neg), im(u[i]), t);
+                    t = fma(neg_if(im(lu[i]), !neg), im(v[i]), t);
                 }
             } else {
                 const R ti = re_dot(lv[i], u[i]) - re_dot(lu[i], v[i]);

@@ -6,6 +6,7 @@
 // path itself runs in the kernels of k_state.cu (rotations, adjoint sweep),
 // k_rows.cu and k_expect.cu (expectation), k_rdm.cu, k_pool.cu and k_sector.cu
 // (sector storage).
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -71,7 +72,10 @@ struct RowTables {
 cudaError_t launch_compact(const void *psi, void *C, int dtype, const uint32_t *sa, const uint32_t *sb, int Da,
                            int Db, int sm_count, cudaStream_t st);
 cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &T, const double *hdiag,
-                              const double *Jp, double e_shift, double *partial, int K, cudaStream_t st);
+                              const double *Jp, double e_shift, double *partial, int K, cudaStream_t st,
+                              const SameGemm *g, int sm_count);
+cudaError_t launch_same_mats(int n, const RowTables &T, const double *hdiag, const double *Jp, float *Ma, float *Mb,
+                             double *dA, double *dB, cudaStream_t st);
 int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want);
 const int *sigma_ab_sizes(int dtype);
 
@@ -399,7 +403,9 @@ static sv_status get_tables(sv_handle h, sv_ham_handle ham, DevTables **out) {
         *out = it->second.get();
         return SV_OK;
     }
+    static uint64_t serial_counter = 0;  // guarded like the rest of a handle's calls: one caller at a time
     std::unique_ptr<DevTables> T(new DevTables());
+    T->serial = ++serial_counter;
     T->n = h->n;
     T->dtype = h->dtype;
     if (single_prec(h->dtype)) SV_TRY(upload_tables<float>(h, ham, *T));
@@ -579,6 +585,94 @@ static int row_chunk(sv_handle h, const RowTables &R) {
     return sigma_ab_chunk(h->dtype, R, h->nb, (int)h->ab_chunk);
 }
 
+// Whether the string-row expectation takes the same-spin products (variant 4):
+// single-precision states whose split form fits and whose strings number at most
+// 4096 per spin (matrices up to 64 MB).  Automatic choice (variant 0): where the
+// sector has at least 2^20 determinants and every string at least 5% of the strings
+// of its spin as same-spin partners (singles and doubles), so that the dense
+// products do at most 20 times the multiplies of the sparse sums.
+static bool use_same_gemm(sv_handle h, int K) {
+    if (!single_prec(h->dtype) || K == 0 || h->Da > 4096 || h->Db > 4096) return false;
+    if (h->expect_variant == 4) return true;
+    if (h->expect_variant != 0) return false;
+    const int N = h->n / 2;
+    auto c2 = [](long x) { return x * (x - 1) / 2; };
+    auto dens = [&](int ne, int D) {
+        const long ns = (long)ne * (N - ne), nd = c2(ne) * c2(N - ne);
+        return (double)(ns + nd) / (double)D;
+    };
+    return (double)h->Da * h->Db >= (double)(1 << 20) && dens(h->na, h->Da) >= 0.05 && dens(h->nb, h->Db) >= 0.05;
+}
+
+// The same-spin matrices of the table set and sector (built on first use, kept until
+// either changes), the two work planes and the cuBLAS handle on the handle's stream.
+static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R, SameGemm *g) {
+    if (!h->blas) {
+        cublasHandle_t hb = nullptr;
+        if (cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS) return fail(h, SV_ERR_CUDA, "cublasCreate failed");
+        h->blas = hb;
+        const size_t ws = (size_t)32 << 20;
+        SV_TRY(dev_alloc(h, &h->blas_ws, ws, "cuBLAS workspace"));
+        h->blas_ws_bytes = ws;
+        if (cublasSetWorkspace(hb, h->blas_ws, ws) != CUBLAS_STATUS_SUCCESS)
+            return fail(h, SV_ERR_CUDA, "cublasSetWorkspace failed");
+    }
+    if (cublasSetStream((cublasHandle_t)h->blas, h->stream) != CUBLAS_STATUS_SUCCESS)
+        return fail(h, SV_ERR_CUDA, "cublasSetStream failed");
+    const size_t Da = (size_t)h->Da, Db = (size_t)h->Db;
+    const size_t mf = (Da * Da + Db * Db) * sizeof(float), mb = (mf + 15) / 16 * 16 + (Da + Db) * sizeof(double);
+    float *Ma = nullptr;
+    if (!h->sg_mats || h->sg_serial != T->serial || h->sg_na != h->na || h->sg_nb != h->nb) {
+        if (h->sg_mats_bytes < mb) {
+            dev_free(h, h->sg_mats, h->sg_mats_bytes);
+            h->sg_mats = nullptr;
+            h->sg_mats_bytes = 0;
+            SV_TRY(dev_alloc(h, &h->sg_mats, mb, "same-spin matrices"));
+            h->sg_mats_bytes = mb;
+        }
+        Ma = (float *)h->sg_mats;
+        double *dA = (double *)((uint8_t *)h->sg_mats + (mf + 15) / 16 * 16);
+        SV_CUDA(h, launch_same_mats(h->n, R, T->hdiag, T->Jp, Ma, Ma + Da * Da, dA, dA + Da, h->stream));
+        h->launches++;
+        h->sg_serial = T->serial;
+        h->sg_na = h->na;
+        h->sg_nb = h->nb;
+    }
+    Ma = (float *)h->sg_mats;
+    const int planes = is_complex(h->dtype) ? 2 : 1;
+    const size_t pb = sizeof(float) * planes * Da * Db;
+    if (h->sg_buf_bytes < 2 * pb) {
+        dev_free(h, h->sg_buf, h->sg_buf_bytes);
+        h->sg_buf = nullptr;
+        h->sg_buf_bytes = 0;
+        SV_TRY(dev_alloc(h, &h->sg_buf, 2 * pb, "same-spin product planes"));
+        h->sg_buf_bytes = 2 * pb;
+    }
+    g->Ma = Ma;
+    g->Mb = Ma + Da * Da;
+    g->dA = (const double *)((const uint8_t *)h->sg_mats + (mf + 15) / 16 * 16);
+    g->dB = g->dA + Da;
+    g->X = (float *)h->sg_buf;
+    g->G = g->X + (size_t)planes * Da * Db;
+    g->blas = h->blas;
+    g->planes = planes;
+    return SV_OK;
+}
+
+// The string-row expectation (sigma into lam at storage addresses, or into lamc in
+// compact form), with or without the same-spin products; counts the launches.
+static sv_status sigma_rows(sv_handle h, DevTables *T, const RowTables &R, const void *C, void *lam, void *lamc,
+                            double e_shift) {
+    const int K = row_chunk(h, R);
+    SameGemm g;
+    const bool sg = use_same_gemm(h, K);
+    if (sg) SV_TRY(ensure_same_gemm(h, T, R, &g));
+    SV_CUDA(h, launch_sigma_rows(C, lam, lamc, h->dtype, h->n, R, T->hdiag, T->Jp, e_shift, h->partials, K,
+                                 h->stream, sg ? &g : nullptr, h->sm_count));
+    h->launches += sg ? 3 : (K ? 2 : 1);  // cuBLAS's own kernels are not counted
+    return SV_OK;
+}
+
 // Expectation pass over the current state: writes the float64 sums of
 // <psi|(H - c)|psi> and <psi|psi> into dout[out_off], dout[out_off + 1] (device),
 // and sigma = (H - c) psi into `sigma` when it is not NULL.
@@ -589,10 +683,7 @@ static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void 
         SV_TRY(ensure_partials(h, 3 * (size_t)h->Db));
         RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
                     T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db, T->W2};
-        const int K = row_chunk(h, R);
-        SV_CUDA(h, launch_sigma_rows(h->psi, nullptr, sigma, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
-                                     h->partials, K, h->stream));
-        h->launches += K ? 2 : 1;
+        SV_TRY(sigma_rows(h, T, R, h->psi, nullptr, sigma, ham->e_nuc - c));
         SV_CUDA(h, launch_reduce_rows(h->partials, 2, h->Db, h->dout + out_off, h->stream));
         h->launches++;
         return SV_OK;
@@ -607,10 +698,7 @@ static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void 
         h->launches++;
         RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
                     T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db, T->W2};
-        const int K = row_chunk(h, R);
-        SV_CUDA(h, launch_sigma_rows(h->Cbuf, sigma, nullptr, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
-                                     h->partials, K, h->stream));
-        h->launches += K ? 2 : 1;
+        SV_TRY(sigma_rows(h, T, R, h->Cbuf, sigma, nullptr, ham->e_nuc - c));
         SV_CUDA(h, launch_reduce_rows(h->partials, 2, h->Db, h->dout + out_off, h->stream));
         h->launches++;
         return SV_OK;
@@ -725,10 +813,12 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
         int best_v = 2;
         int64_t best_k = 0;
         float best_t = -1.f;
-        for (int i = -1; i < 4; ++i) {
-            h->expect_variant = i < 0 ? 2 : 3;
-            h->ab_chunk = i < 0 ? 0 : sizes[i];
-            if (i >= 0 && row_chunk(h, R) != sizes[i]) continue;  // that size does not fit
+        const int nv = single_prec(h->dtype) ? 2 : 1;  // split form; same-spin products (single precision)
+        for (int i = -1; i < 4 * nv; ++i) {
+            h->expect_variant = i < 0 ? 2 : (i < 4 ? 3 : 4);
+            h->ab_chunk = i < 0 ? 0 : sizes[i & 3];
+            if (i >= 0 && row_chunk(h, R) != sizes[i & 3]) continue;  // that size does not fit
+            if (i >= 4 && !use_same_gemm(h, sizes[i & 3])) continue;
             const float t = time_best(h, e0, e1, [&] { return expectation(h, ham, T, h->lam, c, 0); });
             if (t < 0.f) return fail(h, SV_ERR_CUDA, "autotune: expectation candidate failed");
             if (best_t < 0.f || t < best_t) {
@@ -925,6 +1015,10 @@ sv_status sv_destroy(sv_handle h) {
         if (p) cudaFree(p);
     dev_free(h, h->Cbuf, h->Cbuf_bytes);
     dev_free(h, h->Lbuf, h->Lbuf_bytes);
+    dev_free(h, h->sg_mats, h->sg_mats_bytes);
+    dev_free(h, h->sg_buf, h->sg_buf_bytes);
+    dev_free(h, h->blas_ws, h->blas_ws_bytes);
+    if (h->blas) cublasDestroy((cublasHandle_t)h->blas);
     dev_free(h, h->lists.buf, h->lists.bytes);
     dev_free(h, h->pool_lists.buf, h->pool_lists.bytes);
     dev_free(h, h->CLbuf, h->CLbuf_bytes);
@@ -1324,10 +1418,7 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
     }
     RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
                 T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db, T->W2};
-    const int K = row_chunk(h, R);
-    SV_CUDA(h, launch_sigma_rows(Cm, nullptr, h->Lbuf, h->dtype, h->n, R, T->hdiag, T->Jp, ham->e_nuc - c,
-                                 h->partials, K, h->stream));
-    h->launches += K ? 2 : 1;
+    SV_TRY(sigma_rows(h, T, R, Cm, nullptr, h->Lbuf, ham->e_nuc - c));
     SV_CUDA(h, launch_reduce_rows(h->partials, 2, h->Db, h->dout, h->stream));
     h->launches++;
     if (n_pool > 0 && use_lists) {
@@ -1508,7 +1599,7 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
             h->max_bytes = value;
             return SV_OK;
         case SV_OPT_EXPECT_VARIANT:
-            if (value < 0 || value > 3) return fail(h, SV_ERR_ARG, "expect variant must be 0, 1, 2 or 3");
+            if (value < 0 || value > 4) return fail(h, SV_ERR_ARG, "expect variant must be 0, 1, 2, 3 or 4");
             h->expect_variant = (int)value;
             return SV_OK;
         case SV_OPT_RDM_VARIANT:

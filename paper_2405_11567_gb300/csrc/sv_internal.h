@@ -110,7 +110,23 @@ struct HostTables {
 };
 
 // Device copy of the tables, built lazily per (n, dtype) and cached in the Hamiltonian.
+// Same-spin part of sigma as dense products in the string-blocked basis (expectation
+// variant 4, single-precision states): with the determinant written as the alpha
+// creators followed by the beta creators, an alpha excitation's sign depends on the
+// alpha string alone and a beta excitation's on the beta string alone, so
+//   sigma~_same[b][a] = sum_a' Ma[a][a'] C~[b][a'] + sum_b' Mb[b][b'] C~[b'][a]
+// with C~[b][a] = phi(a, b) C[b][a], phi = (-1)^popc(a & pp(b)) the reordering sign
+// between the interleaved and the blocked creator orders (pp = prefix parity).
+struct SameGemm {
+    const float *Ma = nullptr, *Mb = nullptr;  // [Da][Da], [Db][Db], symmetric
+    const double *dA = nullptr, *dB = nullptr; // one-spin diagonal energies per string (float64)
+    float *X = nullptr, *G = nullptr;          // [planes][Db][Da]: phased psi, same-spin sigma~
+    void *blas = nullptr;                      // cublasHandle_t on the handle's stream
+    int planes = 2;                            // 2 complex (re, im), 1 real
+};
+
 struct DevTables {
+    uint64_t serial = 0;   // unique per table set (keys the per-handle same-spin matrices)
     int n = 0;
     int dtype = 0;
     int n_dbl = 0, n_sgl = 0;
@@ -236,6 +252,17 @@ struct sv_ctx {
     int rdm_bps = 4;           // k_rdm_rows
     int rdm_variant = 0;
     int pool_variant = 0;      // 0 auto (= 2); 1 string scan; 2 pair lists
+    // same-spin products (expectation variant 4): matrices for one table set and sector,
+    // the phased-psi / product planes, and the cuBLAS handle with its workspace
+    void *sg_mats = nullptr;
+    size_t sg_mats_bytes = 0;
+    uint64_t sg_serial = 0;
+    int sg_na = -1, sg_nb = -1;
+    void *sg_buf = nullptr;
+    size_t sg_buf_bytes = 0;
+    void *blas = nullptr;
+    void *blas_ws = nullptr;
+    size_t blas_ws_bytes = 0;
     // storage layout: address bit perm[q] holds qubit q (identity by default);
     // layout_auto: sv_energy_grad picks it from its operator list
     int perm[32];

@@ -24,9 +24,10 @@ def _state(n, na, nb, dtype, storage):
     return sv.StateVector(n, dtype, sector=None if storage == "dense" else (na, nb))
 
 
+@pytest.mark.parametrize("variant", [0, 4])
 @pytest.mark.parametrize("storage", ["dense", "sector"])
 @pytest.mark.parametrize("dtype", ["r64", "r32"])
-def test_energy_grad_rdm_state(dtype, storage):
+def test_energy_grad_rdm_state(dtype, storage, variant):
     p = inputs.make_problem(14, 6, 80, seed=515)
     sec = oracle.Sector(14, 3, 3)
     psi0 = A.hf_state(sec, p["occ"])
@@ -35,6 +36,7 @@ def test_energy_grad_rdm_state(dtype, storage):
     psi = A.apply_ansatz(sec, p["ops"], theta, psi0)
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
     st = _state(14, 3, 3, dtype, storage)
+    st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)  # 4: same-spin products (float32; float64 keeps 3)
     st.prepare_hf(p["occ"])
     E, g = st.energy_grad(ham, p["ops"], theta)
     t = TOL[dtype]

@@ -307,10 +307,12 @@ def test_adapt_vqe_on_sector_storage_reaches_fci():
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("chunk", [1, 2, 3, 4, 6, 8])
-@pytest.mark.parametrize("variant", [2, 3])
+@pytest.mark.parametrize("variant", [2, 3, 4])
 def test_expectation_forms_and_chunks(variant, chunk, dtype):
-    """Single-kernel (2) and split (3) string-row expectation, every partner-row chunk size, on an
-    open-shell complex start: the same energy, gradient and pool gradients to float64 rounding."""
+    """Single-kernel (2), split (3) and split with same-spin products (4; complex64 only,
+    complex128 keeps 3) string-row expectation, every partner-row chunk size, on an
+    open-shell complex start: the same energy, gradient and pool gradients to the precision's
+    rounding."""
     n, na, nb = 14, 4, 2
     p = inputs.make_problem(n, 6, 30, seed=91)
     dense0 = inputs.random_sector_state(n, na, nb, np.random.default_rng(21))
