@@ -345,11 +345,21 @@ typedef enum {
     SV_OPT_SECT_BLOCKS_PER_SM = 9,  /* the same for the sector rotation / adjoint kernels
                                        (default 8) */
     SV_OPT_RDM_BLOCKS_PER_SM = 10,  /* the same for the string-row 1-RDM (default 4) */
-    SV_OPT_POOL_VARIANT = 11        /* sv_pool_gradients: 0 auto (= 2); 1 string scan: one
+    SV_OPT_POOL_VARIANT = 11,       /* sv_pool_gradients: 0 auto (= 2); 1 string scan: one
                                        block per operator tests every alpha / beta string;
                                        2 pair lists: per-operator pair lists built once per
                                        pool (kept while the pool's operators are unchanged),
                                        amplitudes and lambda read interleaved */
+    SV_OPT_L2_FETCH = 12,           /* dense storage: before each sweep the handle sets the
+                                       CUDA context's maximum L2 fetch granularity
+                                       (cudaLimitMaxL2FetchGranularity) to this many bytes
+                                       (32, 64 or 128; default 32), and the context keeps
+                                       it; 0 leaves the context's value alone.  Rotations
+                                       of excitations on low address bits touch runs of
+                                       32-64 bytes, which larger fetches double */
+    SV_OPT_GEMM_MATH = 13           /* expectation variant 4's products: 0 (default) plain
+                                       float32; 1 float32 emulated with bf16 tensor-core
+                                       products (cuBLAS BF16x9: at least float32 accuracy) */
 } sv_option;
 
 /* Options change launch choices or summation order only: results agree within the

@@ -538,8 +538,20 @@ static sv_status ensure_op_lists(sv_handle h, const std::vector<OpDesc> &ops, Op
     return SV_OK;
 }
 
+// Dense sweeps touch runs as short as one amplitude: a 32-byte maximum L2 fetch
+// granularity (a limit of the CUDA context, so it stays in force for the context's
+// later work) keeps the L2 from fetching larger blocks around runs of 32 or 64 bytes.
+// A hint: a refusal is ignored.
+static void set_l2_fetch(sv_handle h) {
+    if (h->storage != 0 || h->l2_fetch <= 0) return;
+    size_t cur = 0;
+    if (cudaDeviceGetLimit(&cur, cudaLimitMaxL2FetchGranularity) == cudaSuccess && cur == (size_t)h->l2_fetch) return;
+    if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)h->l2_fetch) != cudaSuccess) cudaGetLastError();
+}
+
 static sv_status forward(sv_handle h, const std::vector<OpDesc> &ops, bool checkpoints) {
     const int64_t C = h->ckpt_interval;
+    set_l2_fetch(h);
     if (h->storage == 1 && !ops.empty()) SV_TRY(ensure_op_lists(h, ops, h->lists));
     const uint32_t *L = (const uint32_t *)h->lists.buf;
     const int G = sector_grid(h->Db, h->sm_count, h->sect_bps);
@@ -619,6 +631,9 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
     }
     if (cublasSetStream((cublasHandle_t)h->blas, h->stream) != CUBLAS_STATUS_SUCCESS)
         return fail(h, SV_ERR_CUDA, "cublasSetStream failed");
+    if (cublasSetMathMode((cublasHandle_t)h->blas, h->gemm_math ? CUBLAS_FP32_EMULATED_BF16X9_MATH
+                                                                 : CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS)
+        return fail(h, SV_ERR_CUDA, "cublasSetMathMode failed");
     const size_t Da = (size_t)h->Da, Db = (size_t)h->Db;
     const size_t mf = (Da * Da + Db * Db) * sizeof(float), mb = (mf + 15) / 16 * 16 + (Da + Db) * sizeof(double);
     float *Ma = nullptr;
@@ -1551,6 +1566,8 @@ sv_status sv_get_option(sv_handle h, sv_option opt, int64_t *value) {
         case SV_OPT_SECT_BLOCKS_PER_SM: *value = h->sect_bps; return SV_OK;
         case SV_OPT_RDM_BLOCKS_PER_SM: *value = h->rdm_bps; return SV_OK;
         case SV_OPT_POOL_VARIANT: *value = h->pool_variant; return SV_OK;
+        case SV_OPT_L2_FETCH: *value = h->l2_fetch; return SV_OK;
+        case SV_OPT_GEMM_MATH: *value = h->gemm_math; return SV_OK;
     }
     return fail(h, SV_ERR_ARG, "unknown option");
 }
@@ -1605,6 +1622,15 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
         case SV_OPT_RDM_VARIANT:
             if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "rdm variant must be 0, 1 or 2");
             h->rdm_variant = (int)value;
+            return SV_OK;
+        case SV_OPT_GEMM_MATH:
+            if (value < 0 || value > 1) return fail(h, SV_ERR_ARG, "GEMM math must be 0 or 1");
+            h->gemm_math = (int)value;
+            return SV_OK;
+        case SV_OPT_L2_FETCH:
+            if (value != 0 && value != 32 && value != 64 && value != 128)
+                return fail(h, SV_ERR_ARG, "L2 fetch granularity must be 0, 32, 64 or 128");
+            h->l2_fetch = (int)value;
             return SV_OK;
         case SV_OPT_POOL_VARIANT:
             if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "pool variant must be 0, 1 or 2");

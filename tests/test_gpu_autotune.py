@@ -63,6 +63,16 @@ def test_option_round_trip_and_range():
     assert st.option(sv.SV_OPT_POOL_VARIANT) == 1
     with pytest.raises(sv.SvError):
         st.set_option(sv.SV_OPT_POOL_VARIANT, 3)
+    assert st.option(sv.SV_OPT_L2_FETCH) == 32
+    for v in (0, 64, 128, 32):
+        st.set_option(sv.SV_OPT_L2_FETCH, v)
+        assert st.option(sv.SV_OPT_L2_FETCH) == v
+    with pytest.raises(sv.SvError):
+        st.set_option(sv.SV_OPT_L2_FETCH, 48)
+    st.set_option(sv.SV_OPT_GEMM_MATH, 1)
+    assert st.option(sv.SV_OPT_GEMM_MATH) == 1
+    with pytest.raises(sv.SvError):
+        st.set_option(sv.SV_OPT_GEMM_MATH, 2)
 
 
 def test_batch_autotune_keeps_results():

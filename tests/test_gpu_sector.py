@@ -176,6 +176,39 @@ def test_pool_gradients_match_oracle(dtype, tol, variant):
     assert np.array_equal(g4, g)
 
 
+@pytest.mark.parametrize("math", [0, 1])
+@pytest.mark.parametrize("storage", ["sector", "dense"])
+def test_same_spin_products_match_oracle(storage, math):
+    """Expectation variant 4 (same-spin part as two dense float32 products in the
+    string-blocked basis), with plain and bf16-emulated float32 products, on an open-shell
+    complex start: energy, gradient and pool gradients within the complex64 tolerance, and
+    reruns bit-identical."""
+    n, na, nb = 16, 3, 4
+    p = inputs.make_problem(n, 7, 40, seed=303)
+    dense0 = inputs.random_sector_state(n, na, nb, np.random.default_rng(31))
+    sec = oracle.Sector(n, na, nb)
+    psi0 = dense0[sec.dets.astype(np.int64)]
+    theta = p["theta"] * 5
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = sv.StateVector(n, "c64", sector=(na, nb) if storage == "sector" else None)
+    st.set_option(sv.SV_OPT_EXPECT_VARIANT, 4)
+    st.set_option(sv.SV_OPT_GEMM_MATH, math)
+    runs = []
+    for _ in range(2):
+        st.prepare_state(dense0.astype(np.complex64), na, nb)
+        runs.append(st.energy_grad(ham, p["ops"], theta))
+    E, g = runs[0]
+    assert abs(E - Eref) <= TOL["c64"]["E"] and np.max(np.abs(g - gref)) <= TOL["c64"]["g"]
+    assert runs[1][0] == E and np.array_equal(runs[1][1], g)
+    pool = inputs.uccsd_pool(n, 7)[::5]
+    psi = A.apply_ansatz(sec, p["ops"], theta, psi0)
+    sig = A.hamiltonian_apply(sec, p["h"], p["eri"], p["e_nuc"], psi)
+    gp_ref = np.array([2 * np.vdot(sig, A.generator_apply(sec, op, psi)).real for op in pool])
+    _, gp = st.pool_gradients(ham, pool)
+    assert np.max(np.abs(gp - gp_ref)) <= TOL["c64"]["g"]
+
+
 def _applies_in(sec, op):
     """Whether op has a pair in the sector: it annihilates at most N_alpha alpha and
     N_beta beta spin-orbitals (uccsd_pool rows: kind, i, j, a, b with i, j annihilated)."""
