@@ -39,14 +39,14 @@ if ROOT not in sys.path:
 METRIC = "energy+adjoint-grad evals/s at 30 qubits, FP32-state vs FP64; % of HBM peak"
 UNIT = "evals/s"
 CONFIG_ID = 5
-# DRAM bytes (read + write) of one expectation's two kernels on sector storage
-# (k_sigma_ab 219.6 MB, k_sigma_same 897.4 MB), from the ncu capture summarised in
-# profiles/sigma_split_n30_sector_c64.md; set to None once either kernel changes.
-SIGMA_TRAFFIC_BYTES = 1117.0e6
+# DRAM bytes (read + write) of one sector-storage expectation (same-spin product form:
+# k_phase_planar, two float32 products, k_sigma_ab, k_sigma_comb) from the ncu capture
+# summarised in profiles/sigma_products_n30_sector_c64.md; None once a kernel changes.
+SIGMA_TRAFFIC_BYTES = 1020.3e6
 # DRAM bytes per k_adjoint launch of the dense headline: the 28-qubit capture's
-# traffic / algorithmic ratio (1.20, profiles/k_adjoint_dram_n28_dense_c64.md) times
+# traffic / algorithmic ratio (1.115, profiles/k_adjoint_dram_n28_dense_c64.md) times
 # the 30-qubit algorithmic bytes per launch; None once the kernel changes.
-ADJOINT_TRAFFIC_BYTES = 5.32e9
+ADJOINT_TRAFFIC_BYTES = 4.93e9
 
 
 def _env_int(k, d):
@@ -301,6 +301,8 @@ def run_ours(args, rank, world, local_rank):
     def timed(dtype, sector):
         st = sv.StateVector(n, dtype, stream, sector=(p["na"], p["nb"]) if sector else None)
         st.set_option(sv.SV_OPT_PROFILE, 1)
+        if args.expect_variant is not None:  # a fixed expectation form (profiling; with --no-autotune)
+            st.set_option(sv.SV_OPT_EXPECT_VARIANT, args.expect_variant)
         outs = {}
         tuned = None
         if not args.no_autotune:  # launch choices timed on this problem, before any timed step
@@ -504,7 +506,10 @@ def run_ours(args, rank, world, local_rank):
         sect = {"storage": "sector: C(15,5)^2 = 9,018,009 amplitudes (72 MB complex64), L2-resident",
                 "value": throughput(world, K, s64["ms"]), "unit": UNIT, "ms_per_step": s64["ms"] / K,
                 "phases_ms": s64["phases"], "clocks": s64["clocks"], "gpu_launches": int(s64["launches"]),
-                "roofline": {"bound": "alu", "kernel": "expectation: k_sigma_ab + k_sigma_same (two launches)",
+                "roofline": {"bound": "alu", "kernel": (
+                    "expectation: k_phase_planar + two float32 products (cuBLAS) + k_sigma_ab + k_sigma_comb"
+                    if (s64["tuned"] or {}).get("expect_variant", 4) == 4
+                    else "expectation: k_sigma_ab + k_sigma_same (two launches)"),
                              "achieved": ach, "peak": fpeak, "unit": "TFLOP/s", "frac": ach / fpeak,
                              "traffic": SIGMA_TRAFFIC_BYTES,
                              "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz"
@@ -605,6 +610,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch choices")
     ap.add_argument("--no-real", action="store_true", help="skip the real-amplitude (float32) timing")
     ap.add_argument("--no-pool", action="store_true", help="skip the operator-screening timing")
+    ap.add_argument("--expect-variant", type=int, default=None, choices=[0, 1, 2, 3, 4],
+                    help="profiling: force an expectation form (SV_OPT_EXPECT_VARIANT); use with --no-autotune")
     ap.add_argument("--pool-only", action="store_true",
                     help="profiling: time only the operator screening (no bench line)")
     ap.add_argument("--pool-storage", choices=["all", "sector"], default="all",

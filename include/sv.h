@@ -350,16 +350,13 @@ typedef enum {
                                        2 pair lists: per-operator pair lists built once per
                                        pool (kept while the pool's operators are unchanged),
                                        amplitudes and lambda read interleaved */
-    SV_OPT_L2_FETCH = 12,           /* dense storage: before each sweep the handle sets the
+    SV_OPT_L2_FETCH = 12            /* dense storage: before each sweep the handle sets the
                                        CUDA context's maximum L2 fetch granularity
                                        (cudaLimitMaxL2FetchGranularity) to this many bytes
                                        (32, 64 or 128; default 32), and the context keeps
                                        it; 0 leaves the context's value alone.  Rotations
                                        of excitations on low address bits touch runs of
                                        32-64 bytes, which larger fetches double */
-    SV_OPT_GEMM_MATH = 13           /* expectation variant 4's products: 0 (default) plain
-                                       float32; 1 float32 emulated with bf16 tensor-core
-                                       products (cuBLAS BF16x9: at least float32 accuracy) */
 } sv_option;
 
 /* Options change launch choices or summation order only: results agree within the

@@ -961,11 +961,13 @@ static cudaError_t launch_ab_k(const RowArgs<double> &A, int K, size_t smem, cud
 static cudaError_t same_products(const SameGemm &g, int Da, int Db) {
     cublasHandle_t hb = (cublasHandle_t)g.blas;
     const float one = 1.f, zero = 0.f;
-    cublasStatus_t s = cublasSgemm(hb, CUBLAS_OP_N, CUBLAS_OP_N, Da, g.planes * Db, Da, &one, g.Ma, Da, g.X, Da,
-                                   &zero, g.G, Da);
+    const cublasComputeType_t ct = CUBLAS_COMPUTE_32F;
+    cublasStatus_t s = cublasGemmEx(hb, CUBLAS_OP_N, CUBLAS_OP_N, Da, g.planes * Db, Da, &one, g.Ma, CUDA_R_32F, Da,
+                                    g.X, CUDA_R_32F, Da, &zero, g.G, CUDA_R_32F, Da, ct, CUBLAS_GEMM_DEFAULT);
     if (s != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    s = cublasSgemmStridedBatched(hb, CUBLAS_OP_N, CUBLAS_OP_N, Da, Db, Db, &one, g.X, Da, (long long)Da * Db, g.Mb,
-                                  Db, 0, &one, g.G, Da, (long long)Da * Db, g.planes);
+    s = cublasGemmStridedBatchedEx(hb, CUBLAS_OP_N, CUBLAS_OP_N, Da, Db, Db, &one, g.X, CUDA_R_32F, Da,
+                                   (long long)Da * Db, g.Mb, CUDA_R_32F, Db, 0, &one, g.G, CUDA_R_32F, Da,
+                                   (long long)Da * Db, g.planes, ct, CUBLAS_GEMM_DEFAULT);
     if (s != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
     return cudaGetLastError();
 }

@@ -631,8 +631,7 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
     }
     if (cublasSetStream((cublasHandle_t)h->blas, h->stream) != CUBLAS_STATUS_SUCCESS)
         return fail(h, SV_ERR_CUDA, "cublasSetStream failed");
-    if (cublasSetMathMode((cublasHandle_t)h->blas, h->gemm_math ? CUBLAS_FP32_EMULATED_BF16X9_MATH
-                                                                 : CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS)
+    if (cublasSetMathMode((cublasHandle_t)h->blas, CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS)
         return fail(h, SV_ERR_CUDA, "cublasSetMathMode failed");
     const size_t Da = (size_t)h->Da, Db = (size_t)h->Db;
     const size_t mf = (Da * Da + Db * Db) * sizeof(float), mb = (mf + 15) / 16 * 16 + (Da + Db) * sizeof(double);
@@ -1567,7 +1566,6 @@ sv_status sv_get_option(sv_handle h, sv_option opt, int64_t *value) {
         case SV_OPT_RDM_BLOCKS_PER_SM: *value = h->rdm_bps; return SV_OK;
         case SV_OPT_POOL_VARIANT: *value = h->pool_variant; return SV_OK;
         case SV_OPT_L2_FETCH: *value = h->l2_fetch; return SV_OK;
-        case SV_OPT_GEMM_MATH: *value = h->gemm_math; return SV_OK;
     }
     return fail(h, SV_ERR_ARG, "unknown option");
 }
@@ -1622,10 +1620,6 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
         case SV_OPT_RDM_VARIANT:
             if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "rdm variant must be 0, 1 or 2");
             h->rdm_variant = (int)value;
-            return SV_OK;
-        case SV_OPT_GEMM_MATH:
-            if (value < 0 || value > 1) return fail(h, SV_ERR_ARG, "GEMM math must be 0 or 1");
-            h->gemm_math = (int)value;
             return SV_OK;
         case SV_OPT_L2_FETCH:
             if (value != 0 && value != 32 && value != 64 && value != 128)

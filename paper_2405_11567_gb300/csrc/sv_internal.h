@@ -253,7 +253,6 @@ struct sv_ctx {
     int rdm_variant = 0;
     int pool_variant = 0;      // 0 auto (= 2); 1 string scan; 2 pair lists
     int l2_fetch = 32;         // context L2 fetch granularity set before dense sweeps (0: leave it)
-    int gemm_math = 0;         // same-spin products: 0 float32, 1 float32 emulated on bf16 tensor cores
     // same-spin products (expectation variant 4): matrices for one table set and sector,
     // the phased-psi / product planes, and the cuBLAS handle with its workspace
     void *sg_mats = nullptr;

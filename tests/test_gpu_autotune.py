@@ -69,10 +69,6 @@ def test_option_round_trip_and_range():
         assert st.option(sv.SV_OPT_L2_FETCH) == v
     with pytest.raises(sv.SvError):
         st.set_option(sv.SV_OPT_L2_FETCH, 48)
-    st.set_option(sv.SV_OPT_GEMM_MATH, 1)
-    assert st.option(sv.SV_OPT_GEMM_MATH) == 1
-    with pytest.raises(sv.SvError):
-        st.set_option(sv.SV_OPT_GEMM_MATH, 2)
 
 
 def test_batch_autotune_keeps_results():

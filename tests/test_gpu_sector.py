@@ -176,13 +176,11 @@ def test_pool_gradients_match_oracle(dtype, tol, variant):
     assert np.array_equal(g4, g)
 
 
-@pytest.mark.parametrize("math", [0, 1])
 @pytest.mark.parametrize("storage", ["sector", "dense"])
-def test_same_spin_products_match_oracle(storage, math):
+def test_same_spin_products_match_oracle(storage):
     """Expectation variant 4 (same-spin part as two dense float32 products in the
-    string-blocked basis), with plain and bf16-emulated float32 products, on an open-shell
-    complex start: energy, gradient and pool gradients within the complex64 tolerance, and
-    reruns bit-identical."""
+    string-blocked basis) on an open-shell complex start: energy, gradient and pool
+    gradients within the complex64 tolerance, and reruns bit-identical."""
     n, na, nb = 16, 3, 4
     p = inputs.make_problem(n, 7, 40, seed=303)
     dense0 = inputs.random_sector_state(n, na, nb, np.random.default_rng(31))
@@ -193,7 +191,6 @@ def test_same_spin_products_match_oracle(storage, math):
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
     st = sv.StateVector(n, "c64", sector=(na, nb) if storage == "sector" else None)
     st.set_option(sv.SV_OPT_EXPECT_VARIANT, 4)
-    st.set_option(sv.SV_OPT_GEMM_MATH, math)
     runs = []
     for _ in range(2):
         st.prepare_state(dense0.astype(np.complex64), na, nb)
