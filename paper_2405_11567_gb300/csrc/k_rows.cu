@@ -429,6 +429,10 @@ constexpr int kAbIpt = 8;  // alpha strings per thread: Da <= 4096
 template <typename R, int K>
 struct AbLayout {
     static constexpr int KP = sizeof(R) == 4 ? (K + 3) & ~3 : (K + 1) & ~1;
+    // row stride of the staged integral table: an odd number of 16-byte words, so rows
+    // start in every group of four banks (an even stride starts them in half the groups)
+    static constexpr int W16 = KP * (int)sizeof(R) / 16;
+    static constexpr int KPS = (W16 & 1) ? KP : KP + 16 / (int)sizeof(R);
 };
 
 // K consecutive real amplitudes from 16-byte-aligned shared memory (K a multiple of
@@ -511,7 +515,7 @@ __device__ __forceinline__ void lds_r(const double *p, double (&v)[KP]) {
 template <typename Amp, int K>
 __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
     using R = real_of<Amp>;
-    constexpr int KP = AbLayout<R, K>::KP;
+    constexpr int KP = AbLayout<R, K>::KP, KPS = AbLayout<R, K>::KPS;
     extern __shared__ __align__(16) unsigned char ab_dyn[];
     __shared__ int s_Jb[kMaxBS], s_t[kMaxBS], s_cb[kMaxBS];
     __shared__ uint32_t s_M[kMaxBS], s_bf[kMaxBS];
@@ -521,8 +525,8 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
     const SigmaTables<R> &T = A.T;
     const int Ib = blockIdx.x, N = T.N, Da = T.Da, NN = N * N;
     Amp *part = reinterpret_cast<Amp *>(ab_dyn);                  // [Da][K]
-    R *eriS = reinterpret_cast<R *>(part + (size_t)K * Da);       // [N*N][KP]
-    R *JtS = eriS + (size_t)NN * KP;                              // [K][N]: (s_k r_k|kk)
+    R *eriS = reinterpret_cast<R *>(part + (size_t)K * Da);       // [N*N][KPS]
+    R *JtS = eriS + (size_t)NN * KPS;                             // [K][N]: (s_k r_k|kk)
     uint16_t *raS = reinterpret_cast<uint16_t *>(JtS + (size_t)K * N);  // [2^N]
     const uint32_t b = T.strb[Ib], xb = T.sb[Ib], eb = ~b & T.maskN;
     if (threadIdx.x == 0) {
@@ -591,7 +595,7 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
                 }
                 v = flip_sign<R>(w, (uint32_t)par(s_bf[k0 + k] & mB));
             }
-            eriS[i] = v;
+            eriS[qp * KPS + k] = v;
         }
         for (int i = threadIdx.x; i < K * N; i += kAbThreads) {
             const int k = i / N, o = i - k * N;
@@ -642,8 +646,8 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
                     R v0[KP], v1[KP];
                     lds_c<K>(part + (size_t)J0 * K, c0);
                     lds_c<K>(part + (size_t)J1 * K, c1);
-                    lds_r<KP>(eriS + (q0 * N + p) * KP, v0);
-                    lds_r<KP>(eriS + (q1 * N + p) * KP, v1);
+                    lds_r<KP>(eriS + (q0 * N + p) * KPS, v0);
+                    lds_r<KP>(eriS + (q1 * N + p) * KPS, v1);
                     #pragma unroll
                     for (int k = 0; k < K; ++k) {
                         const R w0 = flip_sign<R>(v0[k], s0);
@@ -877,7 +881,8 @@ constexpr size_t kAbSmemCap = 225 * 1024;  // dynamic shared memory a split kern
 static size_t ab_smem(int dtype, int K, const RowTables &T) {
     const size_t amp = amp_size(dtype), real = single_prec(dtype) ? 4 : 8;
     const size_t KP = real == 4 ? (size_t)((K + 3) & ~3) : (size_t)((K + 1) & ~1);
-    return (size_t)K * T.Da * amp + (size_t)T.N * T.N * KP * real + (size_t)K * T.N * real + ((size_t)2 << T.N);
+    const size_t KPS = ((KP * real / 16) & 1) ? KP : KP + 16 / real;  // AbLayout<R, K>::KPS
+    return (size_t)K * T.Da * amp + (size_t)T.N * T.N * KPS * real + (size_t)K * T.N * real + ((size_t)2 << T.N);
 }
 
 // k_sigma_same's dynamic shared memory, with or without the alpha rank table; its
