@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_l(A *__restrict__ psi, A *
 //   beta occupations             the row norm when b holds p
 //   alpha pairs p < q            sum over a with q in a, p not in a of
 //                                conj(C[b][a']) C[b][a] (-1)^popc(x & between(2p, 2q)), a' = a - q + p
+//                                (those a from the pair's list, built once per sector)
 //   beta pairs p < q (b holds q, not p)
 //                                sum_a conj(C[b'][a]) C[b][a] (-1)^popc(x & between(2p+1, 2q+1))
 // (x = spread(a) | spread(b)), in the element order norm, n occupations
@@ -163,6 +164,8 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_l(A *__restrict__ psi, A *
 // running sums, written to partial[e][blockIdx.x] at the end: fixed-order sums.
 template <typename A>
 __global__ void __launch_bounds__(kThreads) k_rdm_rows(const A *__restrict__ C, SectTabs T, int N,
+                                                       const uint32_t *__restrict__ alist,
+                                                       const int4 *__restrict__ ainfo,
                                                        double *__restrict__ partial) {
     using R = real_of<A>;
     extern __shared__ double rdm_s[];  // [2 n_el] running sums, then [kThreads/32][2 n_el] warp slots
@@ -213,15 +216,19 @@ __global__ void __launch_bounds__(kThreads) k_rdm_rows(const A *__restrict__ C, 
                     const uint32_t bm = between(2 * p + s, 2 * q + s);
                     R re = 0, im = 0;
                     if (s == 0) {
-                        for (int Ia = threadIdx.x; Ia < T.Da; Ia += blockDim.x) {
-                            const uint32_t a = T.stra[Ia];
-                            if ((a & m) != f) continue;
-                            const A u = row[Ia], v = row[T.ra[a ^ m]];
+                        // the alpha strings holding q but not p, from the pair's list: entry =
+                        // rank | parity of its alpha bits under bm << 15 | partner rank << 16
+                        const int4 li = ainfo[e - 1 - n];
+                        const uint32_t *L = alist + li.x, rsg = (uint32_t)par(xb & bm);
+                        for (int i = threadIdx.x; i < li.y; i += blockDim.x) {
+                            const uint32_t ea = L[i];
+                            const A u = row[ea & 0x7FFFu], v = row[ea >> 16];
                             R ar = re_dot(v, u), ai = im_dot(v, u);  // conj(v) u
-                            if (par((T.sa[Ia] | xb) & bm)) { ar = -ar; ai = -ai; }
+                            if (((ea >> 15) & 1u) ^ rsg) { ar = -ar; ai = -ai; }
                             re += ar;
                             im += ai;
                         }
+                        (void)f;
                     } else if ((b & m) == f) {
                         const A *row2 = C + (size_t)T.rb[b ^ m] * T.Da;
                         for (int Ia = threadIdx.x; Ia < T.Da; Ia += blockDim.x) {
@@ -348,12 +355,16 @@ int rdm_rows_grid(int Db, int sm_count, int bps) {
 }
 
 // partial: [2 n_el][grid] doubles (n_el = rdm_rows_elements(n)), reduced by launch_reduce_rows.
+// alist / ainfo: the alpha-pair lists (one list op per pair p < q in (p, q) order with flip
+// mask {p, q}, "from" pattern {q} and sign mask between(2p, 2q)) and their int4 records.
 cudaError_t launch_rdm_rows(const void *C, int dtype, int n, const uint32_t *sa, const uint32_t *sb,
                             const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb, int Da,
-                            int Db, int grid, double *partial, cudaStream_t st) {
+                            int Db, int grid, const uint32_t *alist, const int *ainfo, double *partial,
+                            cudaStream_t st) {
     SectTabs T = tabs(sa, sb, stra, strb, ra, rb, Da, Db);
     const size_t smem = sizeof(double) * 2 * rdm_rows_elements(n) * (1 + kThreads / 32);  // <= 40 KB (n <= 32)
-    SV_DISPATCH_AMP(dtype, k_rdm_rows<A><<<grid, kThreads, smem, st>>>((const A *)C, T, n / 2, partial));
+    SV_DISPATCH_AMP(dtype, k_rdm_rows<A><<<grid, kThreads, smem, st>>>((const A *)C, T, n / 2, alist,
+                                                                       (const int4 *)ainfo, partial));
     return cudaGetLastError();
 }
 

@@ -59,7 +59,8 @@ int rdm_rows_elements(int n);
 int rdm_rows_grid(int Db, int sm_count, int bps);
 cudaError_t launch_rdm_rows(const void *C, int dtype, int n, const uint32_t *sa, const uint32_t *sb,
                             const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb, int Da,
-                            int Db, int grid, double *partial, cudaStream_t st);
+                            int Db, int grid, const uint32_t *alist, const int *ainfo, double *partial,
+                            cudaStream_t st);
 cudaError_t launch_gather_c(const void *psi, int dtype, const uint32_t *idx, int count, void *out, cudaStream_t st);
 
 struct RowTables {
@@ -549,6 +550,30 @@ static void set_l2_fetch(sv_handle h) {
     if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)h->l2_fetch) != cudaSuccess) cudaGetLastError();
 }
 
+// The 1-RDM's alpha-pair lists: for each orbital pair p < q (in (p, q) order) the alpha
+// strings holding q but not p with their partners (q -> p) and the parity of their alpha
+// bits strictly between spin-orbitals 2p and 2q; kept while the sector is unchanged.
+static sv_status ensure_rdm_lists(sv_handle h) {
+    const int N = h->n / 2;
+    std::vector<OpDesc> ops;
+    for (int p = 0; p < N; ++p)
+        for (int q = p + 1; q < N; ++q) {
+            OpDesc d;
+            d.m = (1u << (2 * p)) | (1u << (2 * q));
+            d.from = 1u << (2 * q);
+            d.sm = ((1u << (2 * q)) - 1u) & ~((2u << (2 * p)) - 1u);
+            d.nbits = 2;
+            d.pos[0] = 2 * p;
+            d.pos[1] = 2 * q;
+            ops.push_back(d);
+        }
+    if (ops.empty()) {
+        SV_TRY(ensure_strings(h));  // one orbital: no pairs; the kernel reads no list
+        return SV_OK;
+    }
+    return ensure_op_lists(h, ops, h->rdm_lists);
+}
+
 static sv_status forward(sv_handle h, const std::vector<OpDesc> &ops, bool checkpoints) {
     const int64_t C = h->ckpt_interval;
     set_l2_fetch(h);
@@ -896,6 +921,7 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
     }
     // 3. 1-RDM launch geometry
     {
+        SV_TRY(ensure_rdm_lists(h));
         const void *Cm = h->psi;
         if (h->storage == 0) {
             SV_CUDA(h, launch_compact(h->psi, h->Cbuf, h->dtype, h->str_sa_s, h->str_sb_s, h->Da, h->Db, h->sm_count,
@@ -911,7 +937,8 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
             const int grid = rdm_rows_grid(h->Db, h->sm_count, b);
             const float t = time_best(h, e0, e1, [&]() -> sv_status {
                 SV_CUDA(h, launch_rdm_rows(Cm, h->dtype, h->n, h->str_sa, h->str_sb, h->str_a, h->str_b, h->rank_a,
-                                           h->rank_b, h->Da, h->Db, grid, h->partials, h->stream));
+                                           h->rank_b, h->Da, h->Db, grid, (const uint32_t *)h->rdm_lists.buf,
+                                           h->rdm_lists.dinfo, h->partials, h->stream));
                 return SV_OK;
             });
             if (t < 0.f) return fail(h, SV_ERR_CUDA, "autotune: 1-RDM candidate failed");
@@ -1035,6 +1062,7 @@ sv_status sv_destroy(sv_handle h) {
     if (h->blas) cublasDestroy((cublasHandle_t)h->blas);
     dev_free(h, h->lists.buf, h->lists.bytes);
     dev_free(h, h->pool_lists.buf, h->pool_lists.bytes);
+    dev_free(h, h->rdm_lists.buf, h->rdm_lists.bytes);
     dev_free(h, h->CLbuf, h->CLbuf_bytes);
     dev_free(h, h->partials, h->partials_cap * sizeof(double));
     dev_free(h, h->dout, h->dout_cap * sizeof(double));
@@ -1464,6 +1492,7 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
     if (h->storage == 1 || h->rdm_variant != 1 || !is_complex(h->dtype)) {
         // string rows: on the state itself (sector storage) or on its compact copy
         SV_TRY(ensure_strings(h));
+        SV_TRY(ensure_rdm_lists(h));
         const int n_el = rdm_rows_elements(h->n);
         const int grid = rdm_rows_grid(h->Db, h->sm_count, h->rdm_bps);
         SV_TRY(ensure_partials(h, (size_t)2 * n_el * grid));
@@ -1477,7 +1506,8 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
             Cm = h->Cbuf;
         }
         SV_CUDA(h, launch_rdm_rows(Cm, h->dtype, h->n, h->str_sa, h->str_sb, h->str_a, h->str_b, h->rank_a,
-                                   h->rank_b, h->Da, h->Db, grid, h->partials, h->stream));
+                                   h->rank_b, h->Da, h->Db, grid, (const uint32_t *)h->rdm_lists.buf,
+                                   h->rdm_lists.dinfo, h->partials, h->stream));
         h->launches++;
         SV_CUDA(h, launch_reduce_rows(h->partials, 2 * n_el, grid, h->dout, h->stream));
         h->launches++;

@@ -229,6 +229,7 @@ struct sv_ctx {
     // per-op alpha / beta pair lists (k_build_lists): the ansatz's (sector storage
     // rotations and adjoint steps) and the screened pool's
     OpLists lists, pool_lists;
+    OpLists rdm_lists;         // the 1-RDM's alpha-pair lists (one per orbital pair p < q)
     void *CLbuf = nullptr;     // compact amplitudes and sigma interleaved [Db][Da][2] (screening)
     size_t CLbuf_bytes = 0;
     // reduction scratch
