@@ -48,7 +48,16 @@ struct BatchInst {
     long long sa, sb;            // offsets into the uint32 spread arena
     long long stra, strb, ra, rb;  // offsets into the uint16 string arena
     long long out;               // E at out, gradient at out + 1 ...
+    int fast;                    // 1: sigma by the string-blocked tables (both string counts <= kBatchSmax)
+    int na, nb;                  // electrons per spin
 };
+
+// Largest string count per spin for which an instance's sigma runs from per-block
+// dense same-spin matrices and excitation tables (matrices of kBatchSmax^2 values).
+constexpr int kBatchSmax = 512;
+// Dynamic shared memory the launch may take for the string-blocked sigma's data (the
+// kernel's static shared memory stays below 8 KB, the block limit is 227 KB).
+constexpr size_t kBatchSmemCap = 200 * 1024;
 
 template <typename R>
 struct BatchArgs {
@@ -64,6 +73,11 @@ struct BatchArgs {
     double *out;
     cplx<R> *scratch;            // per block: psi then lambda, Dmax each
     int Dmax;
+    unsigned char *work;         // per block: the string-blocked sigma's work area (fast instances)
+    size_t work_stride;          // its bytes per block
+    int Smax, Xmax;              // its sizes: strings per spin, table entries per string
+    int smem_mode;               // 1: C~, the integrals and the tables in dynamic shared memory
+    int Dfast, Nmax;             // largest sector and orbital count of the fast instances
     int *ctrl;                   // [0] work counter, [1] timeout flag
     unsigned long long budget_ns;
 };
@@ -74,8 +88,184 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// ---------------------------------------------------------------- string-blocked sigma
+//
+// For an instance whose string counts are at most kBatchSmax, sigma is taken in the
+// string-blocked basis (all alpha creators before all beta creators; amplitudes
+// C~ = phi C with phi(a, b) = (-1)^popc(a & pp(b)), pp = prefix parity), where an
+// alpha excitation's sign depends on the alpha string alone and a beta excitation's
+// on the beta string alone:
+//   sigma~[b][a] = (E_nuc - c + dA[a] + dB[b]) C~[b][a]
+//                + sum_a' Ma[a][a'] C~[b][a'] + sum_b' Mb[b][b'] C~[b'][a]
+//                + sum_k sum_j s_j s_k (q_j p_j | s_k r_k) C~[b'_k][a'_j]
+// Ma holds the alpha singles' string-only coefficient h_qp + sum_{o in a} ((qp|oo) -
+// (qo|op)) and the alpha-alpha doubles (a dense Da x Da matrix: at 20 qubits 84 of
+// its 120 entries per row are nonzero), dA the alpha one-spin diagonal energy; Mb and
+// dB the same for beta.  j runs over the alpha single excitations p -> q of a and,
+// as "diagonal" entries p = q, over the occupied alpha orbitals; k likewise for b.
+// A diagonal entry on one side and an excitation on the other gives the singles'
+// dependence on the other spin's string (sum_{o in b} (qp|oo)); two diagonal entries
+// give the alpha-beta part of the diagonal energy, sum (pp|qq).  Table entry:
+// partner rank | sign << 14 | (q N + p) << 16.  sigma = phi sigma~.
+__host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Per-block work area: C~ [Dmax], Ma and Mb [Smax^2 each], the alpha and beta tables
+// [Smax x Xmax each], dA and dB [Smax each, float64].
+__host__ __device__ constexpr size_t blocked_work_bytes(int Dmax, int Smax, int Xmax, size_t real) {
+    return align256(2 * real * (size_t)Dmax) + 2 * align256(real * (size_t)Smax * Smax) +
+           2 * align256(4 * (size_t)Smax * Xmax) + 2 * align256(8 * (size_t)Smax);
+}
+
+// Dynamic shared memory of the shared-memory mode: C~ [Dfast], the integrals
+// [Nmax^4] and both tables [Xmax x Smax], each from a 16-byte boundary.
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+__host__ __device__ constexpr size_t blocked_smem_bytes(int Dfast, int Nmax, int Smax, int Xmax, size_t real) {
+    return align16(2 * real * (size_t)Dfast) + align16(real * (size_t)Nmax * Nmax * Nmax * Nmax) +
+           2 * align16(4 * (size_t)Smax * Xmax);
+}
+
+template <typename R>
+struct BlockedWork {
+    cplx<R> *ct;
+    const R *eri;      // the instance's (pq|rs): its shared copy in shared-memory mode
+    R *eri_s;          // that copy (nullptr otherwise)
+    R *Ma, *Mb;
+    uint32_t *xa, *xb; // entry j of string I at x[j * D + I]
+    double *dA, *dB;
+};
+
+template <typename R>
+__device__ __forceinline__ BlockedWork<R> blocked_work(const BatchArgs<R> &B, const R *eri_g, unsigned char *smem) {
+    unsigned char *w = B.work + (size_t)blockIdx.x * B.work_stride;
+    const size_t S2 = align256(sizeof(R) * (size_t)B.Smax * B.Smax), X = align256(4 * (size_t)B.Smax * B.Xmax),
+                 Sd = align256(8 * (size_t)B.Smax);
+    BlockedWork<R> W;
+    W.ct = reinterpret_cast<cplx<R> *>(w);
+    w += align256(2 * sizeof(R) * (size_t)B.Dmax);
+    W.Ma = reinterpret_cast<R *>(w);
+    W.Mb = reinterpret_cast<R *>(w + S2);
+    w += 2 * S2;
+    W.xa = reinterpret_cast<uint32_t *>(w);
+    W.xb = reinterpret_cast<uint32_t *>(w + X);
+    w += 2 * X;
+    W.dA = reinterpret_cast<double *>(w);
+    W.dB = reinterpret_cast<double *>(w + Sd);
+    W.eri = eri_g;
+    W.eri_s = nullptr;
+    if (B.smem_mode) {
+        const size_t n4 = (size_t)B.Nmax * B.Nmax * B.Nmax * B.Nmax;
+        W.ct = reinterpret_cast<cplx<R> *>(smem);
+        smem += align16(2 * sizeof(R) * (size_t)B.Dfast);
+        W.eri_s = reinterpret_cast<R *>(smem);
+        W.eri = W.eri_s;
+        smem += align16(sizeof(R) * n4);
+        W.xa = reinterpret_cast<uint32_t *>(smem);
+        W.xb = reinterpret_cast<uint32_t *>(smem + align16(4 * (size_t)B.Smax * B.Xmax));
+    }
+    return W;
+}
+
+// Index of the u-th set bit of x (u counts from 0; x has more than u set bits).
+__device__ __forceinline__ int nth_bit(uint32_t x, int u) {
+    for (; u > 0; --u) x &= x - 1u;
+    return __ffs(x) - 1;
+}
+
+// One spin's matrix M (D x D, row = output string), excitation table X (entry u of
+// string I at X[u D + I], so a warp's strings read consecutive words) and one-spin
+// diagonal dS, by the whole block.  M must be zero on entry.
+template <typename R>
+__device__ void build_spin_tables(const SigmaTables<R> &T, int spin, int D, int ne, R *M, uint32_t *X, double *dS) {
+    const uint16_t *str = spin ? T.strb : T.stra, *rk = spin ? T.rb : T.ra;
+    const int N = T.N, nv = N - ne, nsg = ne * nv, npo = ne * (ne - 1) / 2, npe = nv * (nv - 1) / 2;
+    const int items = nsg + npo * npe + ne;
+    for (int t = threadIdx.x; t < D * items; t += blockDim.x) {
+        const int I = t / items, u = t - I * items;
+        const uint32_t a = str[I], e = ~a & T.maskN, pps = prefix_parity(a);
+        if (u < nsg) {  // single p -> q: matrix entry (own-string part) and table entry
+            const int p = nth_bit(a, u / nv), q = nth_bit(e, u % nv);
+            const uint32_t m = (1u << p) | (1u << q), sg = (uint32_t)par(pps & m) ^ (uint32_t)(p < q);
+            const int J = rk[a ^ m];
+            R v = T.hm[q * N + p];
+            const R *dt = T.Dt + (q * N + p) * N;
+            for (uint32_t o = a; o; o &= o - 1u) v += dt[__ffs(o) - 1];
+            M[(size_t)I * D + J] = sg ? -v : v;
+            X[(size_t)u * D + I] = (uint32_t)J | (sg << 14) | ((uint32_t)(q * N + p) << 16);
+        } else if (u < nsg + npo * npe) {  // same-spin double p1 < p2 -> q1 < q2
+            int io = (u - nsg) / npe, ie = (u - nsg) % npe, i1 = 0, e1 = 0;
+            while (io >= ne - 1 - i1) io -= ne - 1 - i1++;
+            while (ie >= nv - 1 - e1) ie -= nv - 1 - e1++;
+            const int p1 = nth_bit(a, i1), p2 = nth_bit(a, i1 + 1 + io), q1 = nth_bit(e, e1), q2 = nth_bit(e, e1 + 1 + ie);
+            const uint32_t m = (1u << p1) | (1u << p2) | (1u << q1) | (1u << q2);
+            const uint32_t sg = (uint32_t)par(pps & m) ^ double_order_sign(p1, p2, q1, q2);
+            const R v = eri4<R>(T, q1, p1, q2, p2) - eri4<R>(T, q1, p2, q2, p1);
+            M[(size_t)I * D + rk[a ^ m]] = sg ? -v : v;
+        } else {  // occupied orbital o: diagonal table entry
+            const int o = nth_bit(a, u - nsg - npo * npe);
+            X[(size_t)(nsg + (u - nsg - npo * npe)) * D + I] = (uint32_t)I | ((uint32_t)(o * N + o) << 16);
+        }
+    }
+    for (int I = threadIdx.x; I < D; I += blockDim.x) {
+        double d = 0.0;
+        for (uint32_t o = str[I]; o; o &= o - 1u) {
+            const int k = 2 * (__ffs(o) - 1) + spin;
+            d += T.hdiag[k];
+            for (uint32_t o2 = o & (o - 1u); o2; o2 &= o2 - 1u) d += T.Jp[k * T.n + 2 * (__ffs(o2) - 1) + spin];
+        }
+        dS[I] = d;
+    }
+}
+
+// sigma~ at (Ia, Ib) from C~ (W.ct) and the instance's tables.
+template <typename R>
+__device__ __forceinline__ cplx<R> sigma_blocked(const SigmaTables<R> &T, const BlockedWork<R> &W, int Ia, int Ib,
+                                                 int Db, int nxa, int nxb) {
+    const int Da = T.Da, NN = T.N * T.N;
+    const cplx<R> *ct = W.ct;
+    const cplx<R> c0 = ct[(size_t)Ib * Da + Ia];
+    const double d = T.e_shift + W.dA[Ia] + W.dB[Ib];
+    R ar = (R)d * c0.x, ai = (R)d * c0.y;
+    const cplx<R> *row = ct + (size_t)Ib * Da;
+    for (int j = 0; j < Da; ++j) {  // alpha same-spin: Ma symmetric, read by column for coalescing
+        const R w = W.Ma[(size_t)j * Da + Ia];
+        const cplx<R> c = row[j];
+        ar = fma(w, c.x, ar);
+        ai = fma(w, c.y, ai);
+    }
+    const R *mb = W.Mb + (size_t)Ib * Db;
+    for (int k = 0; k < Db; ++k) {  // beta same-spin
+        const R w = mb[k];
+        const cplx<R> c = ct[(size_t)k * Da + Ia];
+        ar = fma(w, c.x, ar);
+        ai = fma(w, c.y, ai);
+    }
+    const uint32_t *xa = W.xa + Ia, *xb = W.xb + Ib;
+    for (int k = 0; k < nxb; ++k) {  // alpha-beta, singles' cross-spin parts, alpha-beta diagonal
+        const uint32_t eb = xb[(size_t)k * Db];
+        const cplx<R> *prow = ct + (size_t)(eb & 0x3FFFu) * Da;
+        const R *er = W.eri + (eb >> 16);
+        R tr = 0, ti = 0;
+        for (int j = 0; j < nxa; ++j) {
+            const uint32_t ea = xa[(size_t)j * Da];
+            R w = er[(size_t)(ea >> 16) * NN];
+            if ((ea >> 14) & 1u) w = -w;
+            const cplx<R> c = prow[ea & 0x3FFFu];
+            tr = fma(w, c.x, tr);
+            ti = fma(w, c.y, ti);
+        }
+        if ((eb >> 14) & 1u) {
+            tr = -tr;
+            ti = -ti;
+        }
+        ar += tr;
+        ai += ti;
+    }
+    return mk<R>(ar, ai);
+}
+
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchArgs<R> B) {
+    extern __shared__ __align__(16) unsigned char batch_smem[];
     __shared__ int s_inst;
     __shared__ double red[2 * NT / 32];
     __shared__ unsigned long long s_t0;
@@ -128,13 +318,39 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchArgs<R> B) {
         }
         // sigma and the energy
         double e_acc = 0.0, n_acc = 0.0;
-        for (int i = threadIdx.x; i < D; i += blockDim.x) {
-            const int Ib = i / Da, Ia = i - Ib * Da;
-            const cplx<R> c0 = psi[i];
-            const cplx<R> s = sigma_at<R>(T, psi, Ia, Ib, c0);
-            lam[i] = s;
-            e_acc += (double)c0.x * (double)s.x + (double)c0.y * (double)s.y;
-            n_acc += (double)c0.x * (double)c0.x + (double)c0.y * (double)c0.y;
+        if (I.fast) {
+            const BlockedWork<R> W = blocked_work<R>(B, T.eri, batch_smem);
+            const int Db = I.Db, nxa = I.na * (I.N - I.na) + I.na, nxb = I.nb * (I.N - I.nb) + I.nb;
+            for (int i = threadIdx.x; i < Da * Da; i += blockDim.x) W.Ma[i] = (R)0;
+            for (int i = threadIdx.x; i < Db * Db; i += blockDim.x) W.Mb[i] = (R)0;
+            if (W.eri_s)
+                for (int i = threadIdx.x; i < I.N * I.N * I.N * I.N; i += blockDim.x) W.eri_s[i] = T.eri[i];
+            for (int i = threadIdx.x; i < D; i += blockDim.x) {  // C~ = phi C
+                const int Ib = i / Da, Ia = i - Ib * Da;
+                const cplx<R> c = psi[i];
+                W.ct[i] = par(T.stra[Ia] & prefix_parity(T.strb[Ib])) ? mk<R>(-c.x, -c.y) : c;
+            }
+            __syncthreads();
+            build_spin_tables<R>(T, 0, Da, I.na, W.Ma, W.xa, W.dA);
+            build_spin_tables<R>(T, 1, Db, I.nb, W.Mb, W.xb, W.dB);
+            __syncthreads();
+            for (int i = threadIdx.x; i < D; i += blockDim.x) {
+                const int Ib = i / Da, Ia = i - Ib * Da;
+                const cplx<R> c0 = W.ct[i];
+                const cplx<R> s = sigma_blocked<R>(T, W, Ia, Ib, Db, nxa, nxb);
+                lam[i] = par(T.stra[Ia] & prefix_parity(T.strb[Ib])) ? mk<R>(-s.x, -s.y) : s;
+                e_acc += (double)c0.x * (double)s.x + (double)c0.y * (double)s.y;
+                n_acc += (double)c0.x * (double)c0.x + (double)c0.y * (double)c0.y;
+            }
+        } else {
+            for (int i = threadIdx.x; i < D; i += blockDim.x) {
+                const int Ib = i / Da, Ia = i - Ib * Da;
+                const cplx<R> c0 = psi[i];
+                const cplx<R> s = sigma_at<R>(T, psi, Ia, Ib, c0);
+                lam[i] = s;
+                e_acc += (double)c0.x * (double)s.x + (double)c0.y * (double)s.y;
+                n_acc += (double)c0.x * (double)c0.x + (double)c0.y * (double)c0.y;
+            }
         }
         block_sum2_nt<NT>(e_acc, n_acc, red);  // contains the barrier that publishes lambda
         __shared__ double s_norm;
@@ -195,6 +411,10 @@ struct sv_batch {
     sv_dtype dtype = SV_C64;
     cudaStream_t stream = nullptr;
     int device = 0, sm_count = 148, grid = 0, grid_max = 0, Dmax = 0;
+    int Smax = 0, Xmax = 0;      // the string-blocked sigma's sizes (0: no instance takes it)
+    int Dfast = 0, Nmax = 0;     // largest sector / orbital count among those instances
+    size_t work_stride = 0, smem = 0;  // dynamic shared memory of the launch (0: global-memory mode)
+    void *d_work = nullptr;
     int threads = kThreads;  // block size of the persistent kernel: 256, 512 or 1024
     std::vector<int> L;
     std::vector<long long> cs_off, out_off;
@@ -293,6 +513,14 @@ sv_status build_plan(sv_batch *b, int n_inst, const sv_instance *inst) {
         b->Dmax = std::max<int>(b->Dmax, (int)D);
         BatchInst I{};
         I.n = n; I.N = N; I.Da = sa.count; I.Db = sb.count; I.L = in.n_ops;
+        I.na = na; I.nb = nb;
+        I.fast = sa.count <= kBatchSmax && sb.count <= kBatchSmax;
+        if (I.fast) {
+            b->Dfast = std::max<int>(b->Dfast, (int)D);
+            b->Nmax = std::max(b->Nmax, N);
+            b->Smax = std::max(b->Smax, std::max(sa.count, sb.count));
+            b->Xmax = std::max(b->Xmax, std::max(na * (N - na) + na, nb * (N - nb) + nb));
+        }
         I.sa = sa.spread; I.sb = sb.spread; I.stra = sa.str; I.strb = sb.str; I.ra = sa.rank; I.rb = sb.rank;
         // reference index
         uint32_t ra_str = 0, rb_str = 0;
@@ -402,6 +630,12 @@ sv_status build_plan(sv_batch *b, int n_inst, const sv_instance *inst) {
     b->grid_max = std::max(1, std::min(n_inst, b->sm_count * 4));
     b->grid = std::max(1, std::min(n_inst, b->sm_count * 2));
     if ((s = up(&b->d_scratch, nullptr, (size_t)b->grid_max * 2 * b->Dmax * sizeof(cplx<R>))) != SV_OK) return s;
+    b->work_stride = b->Smax > 0 ? blocked_work_bytes(b->Dmax, b->Smax, b->Xmax, sizeof(R)) : 0;
+    {   // C~, the integrals and the tables in shared memory when they fit beside the static part
+        const size_t sm = b->Smax > 0 ? blocked_smem_bytes(b->Dfast, b->Nmax, b->Smax, b->Xmax, sizeof(R)) : 0;
+        b->smem = (sm > 0 && sm <= kBatchSmemCap) ? sm : 0;
+    }
+    if ((s = up(&b->d_work, nullptr, (size_t)b->grid_max * b->work_stride)) != SV_OK) return s;
     if (cudaMallocHost(&b->h_cs, std::max<long long>(cs, 1) * sizeof(cplx<R>)) != cudaSuccess ||
         cudaMallocHost((void **)&b->h_out, std::max<long long>(out, 1) * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void **)&b->h_ctrl, 2 * sizeof(int)) != cudaSuccess) {
@@ -418,14 +652,26 @@ sv_status capture(sv_batch *b) {
     a.cs = (const cplx<R> *)b->d_cs; a.rarena = (const R *)b->d_r; a.darena = b->d_d;
     a.u32 = b->d_u32; a.u16 = b->d_u16; a.out = b->d_out; a.scratch = (cplx<R> *)b->d_scratch;
     a.Dmax = b->Dmax; a.ctrl = b->d_ctrl; a.budget_ns = b->budget_ns;
+    a.work = (unsigned char *)b->d_work; a.work_stride = b->work_stride; a.Smax = b->Smax; a.Xmax = b->Xmax;
+    a.smem_mode = b->smem > 0; a.Dfast = b->Dfast; a.Nmax = b->Nmax;
     cudaStream_t st = b->stream;
-    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaSuccess;
+    if (b->smem > 48 * 1024) {  // dynamic shared memory above the default limit
+        e = b->threads == 1024 ? cudaFuncSetAttribute(k_batch<R, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem)
+            : b->threads == 512 ? cudaFuncSetAttribute(k_batch<R, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem)
+                                : cudaFuncSetAttribute(k_batch<R, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(SV_ERR_CUDA, std::string("batch shared memory: ") + cudaGetErrorString(e));
+        }
+    }
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bfail(SV_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
     cudaMemcpyAsync(b->d_cs, b->h_cs, std::max<long long>(b->total_ops, 1) * sizeof(cplx<R>), cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(b->d_ctrl, 0, 2 * sizeof(int), st);
-    if (b->threads == 1024) k_batch<R, 1024><<<b->grid, 1024, 0, st>>>(a);
-    else if (b->threads == 512) k_batch<R, 512><<<b->grid, 512, 0, st>>>(a);
-    else k_batch<R, 256><<<b->grid, 256, 0, st>>>(a);
+    if (b->threads == 1024) k_batch<R, 1024><<<b->grid, 1024, b->smem, st>>>(a);
+    else if (b->threads == 512) k_batch<R, 512><<<b->grid, 512, b->smem, st>>>(a);
+    else k_batch<R, 256><<<b->grid, 256, b->smem, st>>>(a);
     cudaMemcpyAsync(b->h_out, b->d_out, std::max<long long>(b->total_out, 1) * sizeof(double), cudaMemcpyDeviceToHost,
                     st);
     cudaMemcpyAsync(b->h_ctrl, b->d_ctrl, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
