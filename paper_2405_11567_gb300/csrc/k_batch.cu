@@ -35,6 +35,7 @@ namespace svk {
 struct BatchOp {
     uint32_t m, from, sm;  // qubit-space flip mask, "from" pattern, sign mask
     uint32_t mab;          // low 16 bits: alpha-string flip mask, high 16: beta-string flip mask
+    uint32_t fab;          // the same for the "from" pattern
 };
 
 struct BatchInst {
@@ -77,6 +78,7 @@ struct BatchArgs {
     size_t work_stride;          // its bytes per block
     int Smax, Xmax;              // its sizes: strings per spin, table entries per string
     int smem_mode;               // 1: C~, the integrals and the tables in dynamic shared memory
+    int Lmax;                    // most operators of a fast instance (its per-operator pair lists)
     int Dfast, Nmax;             // largest sector and orbital count of the fast instances
     int *ctrl;                   // [0] work counter, [1] timeout flag
     unsigned long long budget_ns;
@@ -110,10 +112,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Per-block work area: C~ [Dmax], Ma and Mb [Smax^2 each], the alpha and beta tables
-// [Smax x Xmax each], dA and dB [Smax each, float64].
-__host__ __device__ constexpr size_t blocked_work_bytes(int Dmax, int Smax, int Xmax, size_t real) {
+// [Smax x Xmax each], dA and dB [Smax each, float64], then each operator's alpha and
+// beta pair lists [Lmax x Smax each] and their lengths [2 Lmax].
+__host__ __device__ constexpr size_t blocked_work_bytes(int Dmax, int Smax, int Xmax, int Lmax, size_t real) {
     return align256(2 * real * (size_t)Dmax) + 2 * align256(real * (size_t)Smax * Smax) +
-           2 * align256(4 * (size_t)Smax * Xmax) + 2 * align256(8 * (size_t)Smax);
+           2 * align256(4 * (size_t)Smax * Xmax) + 2 * align256(8 * (size_t)Smax) +
+           2 * align256(4 * (size_t)Lmax * Smax) + align256(8 * (size_t)Lmax);
 }
 
 // Dynamic shared memory of the shared-memory mode: C~ [Dfast], the integrals
@@ -132,6 +136,8 @@ struct BlockedWork {
     R *Ma, *Mb;
     uint32_t *xa, *xb; // entry j of string I at x[j * D + I]
     double *dA, *dB;
+    uint32_t *la, *lb; // operator k's alpha / beta pair list at l[k * Smax]: rank | sign << 14 | partner << 16
+    int *lc;           // their lengths: lc[2 k], lc[2 k + 1]
 };
 
 template <typename R>
@@ -150,6 +156,11 @@ __device__ __forceinline__ BlockedWork<R> blocked_work(const BatchArgs<R> &B, co
     w += 2 * X;
     W.dA = reinterpret_cast<double *>(w);
     W.dB = reinterpret_cast<double *>(w + Sd);
+    w += 2 * Sd;
+    const size_t Lb = align256(4 * (size_t)B.Lmax * B.Smax);
+    W.la = reinterpret_cast<uint32_t *>(w);
+    W.lb = reinterpret_cast<uint32_t *>(w + Lb);
+    W.lc = reinterpret_cast<int *>(w + 2 * Lb);
     W.eri = eri_g;
     W.eri_s = nullptr;
     if (B.smem_mode) {
@@ -300,8 +311,56 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchArgs<R> B) {
         __syncthreads();
         if (threadIdx.x == 0) psi[I.hf] = mk<R>(1, 0);
         __syncthreads();
+        const BlockedWork<R> W = blocked_work<R>(B, T.eri, batch_smem);
+        if (I.fast) {
+            // every operator's pair lists (alpha strings matching its alpha pattern x beta
+            // strings matching its beta pattern), one warp per operator and spin, in rank
+            // order by ballot compaction
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+            for (int t = warp; t < 2 * I.L; t += nwarp) {
+                const int k = t >> 1, spin = t & 1;
+                const BatchOp op = B.ops[I.ops + k];
+                const uint32_t m = spin ? (op.mab >> 16) : (op.mab & 0xFFFFu), f = spin ? (op.fab >> 16) : (op.fab & 0xFFFFu);
+                const int Ds = spin ? I.Db : Da;
+                const uint16_t *str = spin ? T.strb : T.stra, *rk = spin ? T.rb : T.ra;
+                const uint32_t *spr = spin ? T.sb : T.sa;
+                uint32_t *dst = (spin ? W.lb : W.la) + (size_t)k * B.Smax;
+                int cnt = 0;
+                for (int base = 0; base < Ds; base += 32) {
+                    const int Is = base + lane;
+                    uint32_t sv = 0;
+                    bool hit = false;
+                    if (Is < Ds) {
+                        sv = str[Is];
+                        hit = (sv & m) == f;
+                    }
+                    const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+                    if (hit)
+                        dst[cnt + __popc(bal & ((1u << lane) - 1u))] =
+                            (uint32_t)Is | ((uint32_t)par(spr[Is] & op.sm) << 14) | ((uint32_t)rk[sv ^ m] << 16);
+                    cnt += __popc(bal);
+                }
+                if (lane == 0) W.lc[t] = cnt;
+            }
+            __syncthreads();
+        }
         // forward sweep
-        for (int k = 0; k < I.L; ++k) {
+        for (int k = 0; k < I.L && I.fast; ++k) {  // over the operator's pairs
+            const cplx<R> csk = B.cs[I.cs + k];
+            const uint32_t *LA = W.la + (size_t)k * B.Smax, *LB = W.lb + (size_t)k * B.Smax;
+            const int nA = W.lc[2 * k], np = nA * W.lc[2 * k + 1];
+            for (int q = threadIdx.x; q < np; q += blockDim.x) {
+                const int ib = q / nA;
+                const uint32_t ea = LA[q - ib * nA], eb = LB[ib];
+                const int i = (int)(eb & 0x3FFFu) * Da + (int)(ea & 0x3FFFu), j = (int)(eb >> 16) * Da + (int)(ea >> 16);
+                const R ss = ((ea ^ eb) >> 14) & 1u ? -csk.y : csk.y;
+                const cplx<R> u = psi[i], v = psi[j];
+                psi[i] = mk<R>(csk.x * u.x - ss * v.x, csk.x * u.y - ss * v.y);
+                psi[j] = mk<R>(csk.x * v.x + ss * u.x, csk.x * v.y + ss * u.y);
+            }
+            __syncthreads();
+        }
+        for (int k = 0; k < I.L && !I.fast; ++k) {
             const BatchOp op = B.ops[I.ops + k];
             const cplx<R> csk = B.cs[I.cs + k];
             for (int i = threadIdx.x; i < D; i += blockDim.x) {
@@ -319,7 +378,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchArgs<R> B) {
         // sigma and the energy
         double e_acc = 0.0, n_acc = 0.0;
         if (I.fast) {
-            const BlockedWork<R> W = blocked_work<R>(B, T.eri, batch_smem);
             const int Db = I.Db, nxa = I.na * (I.N - I.na) + I.na, nxb = I.nb * (I.N - I.nb) + I.nb;
             for (int i = threadIdx.x; i < Da * Da; i += blockDim.x) W.Ma[i] = (R)0;
             for (int i = threadIdx.x; i < Db * Db; i += blockDim.x) W.Mb[i] = (R)0;
@@ -365,12 +423,25 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchArgs<R> B) {
             const BatchOp op = B.ops[I.ops + k];
             const cplx<R> csk = B.cs[I.cs + k];
             double g = 0.0;
-            for (int i = threadIdx.x; i < D; i += blockDim.x) {
-                const int Ib = i / Da, Ia = i - Ib * Da;
-                const uint32_t x = T.sa[Ia] | T.sb[Ib];
-                if ((x & op.m) != op.from) continue;
-                const int j = (int)T.rb[T.strb[Ib] ^ (op.mab >> 16)] * Da + T.ra[T.stra[Ia] ^ (op.mab & 0xFFFFu)];
-                const bool neg = par(x & op.sm);
+            const uint32_t *LA = W.la + (size_t)k * B.Smax, *LB = W.lb + (size_t)k * B.Smax;
+            const int nA = I.fast ? W.lc[2 * k] : 0, np = I.fast ? nA * W.lc[2 * k + 1] : D;
+            for (int q = threadIdx.x; q < np; q += blockDim.x) {
+                int i, j;
+                bool neg;
+                if (I.fast) {  // over the operator's pairs
+                    const int ib = q / nA;
+                    const uint32_t ea = LA[q - ib * nA], eb = LB[ib];
+                    i = (int)(eb & 0x3FFFu) * Da + (int)(ea & 0x3FFFu);
+                    j = (int)(eb >> 16) * Da + (int)(ea >> 16);
+                    neg = ((ea ^ eb) >> 14) & 1u;
+                } else {  // every determinant, with the op's "from" test
+                    i = q;
+                    const int Ib = i / Da, Ia = i - Ib * Da;
+                    const uint32_t x = T.sa[Ia] | T.sb[Ib];
+                    if ((x & op.m) != op.from) continue;
+                    j = (int)T.rb[T.strb[Ib] ^ (op.mab >> 16)] * Da + T.ra[T.stra[Ia] ^ (op.mab & 0xFFFFu)];
+                    neg = par(x & op.sm);
+                }
                 const cplx<R> u = psi[i], v = psi[j], lu = lam[i], lv = lam[j];
                 const R t = (lv.x * u.x + lv.y * u.y) - (lu.x * v.x + lu.y * v.y);
                 g += (double)(neg ? -t : t);
@@ -413,6 +484,7 @@ struct sv_batch {
     int device = 0, sm_count = 148, grid = 0, grid_max = 0, Dmax = 0;
     int Smax = 0, Xmax = 0;      // the string-blocked sigma's sizes (0: no instance takes it)
     int Dfast = 0, Nmax = 0;     // largest sector / orbital count among those instances
+    int Lmax = 0;                // most operators among them
     size_t work_stride = 0, smem = 0;  // dynamic shared memory of the launch (0: global-memory mode)
     void *d_work = nullptr;
     int threads = kThreads;  // block size of the persistent kernel: 256, 512 or 1024
@@ -520,6 +592,7 @@ sv_status build_plan(sv_batch *b, int n_inst, const sv_instance *inst) {
             b->Nmax = std::max(b->Nmax, N);
             b->Smax = std::max(b->Smax, std::max(sa.count, sb.count));
             b->Xmax = std::max(b->Xmax, std::max(na * (N - na) + na, nb * (N - nb) + nb));
+            b->Lmax = std::max(b->Lmax, in.n_ops);
         }
         I.sa = sa.spread; I.sb = sb.spread; I.stra = sa.str; I.strb = sb.str; I.ra = sa.rank; I.rb = sb.rank;
         // reference index
@@ -582,7 +655,12 @@ sv_status build_plan(sv_batch *b, int n_inst, const sv_instance *inst) {
                 if ((d.m >> (2 * p)) & 1u) ma |= 1u << p;
                 if ((d.m >> (2 * p + 1)) & 1u) mb |= 1u << p;
             }
-            hops.push_back(BatchOp{d.m, d.from, d.sm, ma | (mb << 16)});
+            uint32_t fa = 0, fb = 0;
+            for (int p = 0; p < N; ++p) {
+                if ((d.from >> (2 * p)) & 1u) fa |= 1u << p;
+                if ((d.from >> (2 * p + 1)) & 1u) fb |= 1u << p;
+            }
+            hops.push_back(BatchOp{d.m, d.from, d.sm, ma | (mb << 16), fa | (fb << 16)});
         }
         I.cs = cs;
         b->cs_off[t] = cs;
@@ -630,7 +708,7 @@ sv_status build_plan(sv_batch *b, int n_inst, const sv_instance *inst) {
     b->grid_max = std::max(1, std::min(n_inst, b->sm_count * 4));
     b->grid = std::max(1, std::min(n_inst, b->sm_count * 2));
     if ((s = up(&b->d_scratch, nullptr, (size_t)b->grid_max * 2 * b->Dmax * sizeof(cplx<R>))) != SV_OK) return s;
-    b->work_stride = b->Smax > 0 ? blocked_work_bytes(b->Dmax, b->Smax, b->Xmax, sizeof(R)) : 0;
+    b->work_stride = b->Smax > 0 ? blocked_work_bytes(b->Dmax, b->Smax, b->Xmax, b->Lmax, sizeof(R)) : 0;
     {   // C~, the integrals and the tables in shared memory when they fit beside the static part
         const size_t sm = b->Smax > 0 ? blocked_smem_bytes(b->Dfast, b->Nmax, b->Smax, b->Xmax, sizeof(R)) : 0;
         b->smem = (sm > 0 && sm <= kBatchSmemCap) ? sm : 0;
@@ -653,7 +731,7 @@ sv_status capture(sv_batch *b) {
     a.u32 = b->d_u32; a.u16 = b->d_u16; a.out = b->d_out; a.scratch = (cplx<R> *)b->d_scratch;
     a.Dmax = b->Dmax; a.ctrl = b->d_ctrl; a.budget_ns = b->budget_ns;
     a.work = (unsigned char *)b->d_work; a.work_stride = b->work_stride; a.Smax = b->Smax; a.Xmax = b->Xmax;
-    a.smem_mode = b->smem > 0; a.Dfast = b->Dfast; a.Nmax = b->Nmax;
+    a.smem_mode = b->smem > 0; a.Dfast = b->Dfast; a.Nmax = b->Nmax; a.Lmax = b->Lmax;
     cudaStream_t st = b->stream;
     cudaError_t e = cudaSuccess;
     if (b->smem > 48 * 1024) {  // dynamic shared memory above the default limit
