@@ -281,7 +281,8 @@ sv_status sv_batch_create(int n_inst, const sv_instance *inst, sv_dtype dtype, v
 
 /* Energy and gradient of every instance for the angles theta (concatenated in
  * instance order, sum of n_ops values): e_out[i] = E_i, grad_out (same layout as
- * theta) = dE_i/dtheta.  One graph launch (angles up, kernel, results down), then
+ * theta) = dE_i/dtheta.  One graph launch (angles up, their cosines and sines in
+ * float64 on the device, the batched kernel, results down), then
  * a stream synchronisation.  SV_ERR_TIMEOUT when the time limit stopped the
  * kernel early: the outputs of instances not run are NaN. */
 sv_status sv_batch_energy_grad(sv_batch_handle b, const double *theta, double *e_out, double *grad_out);
@@ -290,7 +291,9 @@ sv_status sv_batch_energy_grad(sv_batch_handle b, const double *theta, double *e
  * is spent (checked before each instance; no block ever waits on another). */
 sv_status sv_batch_set_time_limit(sv_batch_handle b, double ms);
 
-/* Kernels launched by this batch so far (one per sv_batch_energy_grad). */
+/* Kernels launched by this batch so far (two per sv_batch_energy_grad: the angles'
+ * cosines and sines, then the batched kernel; one when the instances have no
+ * operators). */
 uint64_t sv_batch_launch_count(sv_batch_handle b);
 
 /* Autotuner for the persistent batched launch: times the captured launch (angles

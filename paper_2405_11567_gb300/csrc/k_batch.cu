@@ -274,6 +274,18 @@ __device__ __forceinline__ cplx<R> sigma_blocked(const SigmaTables<R> &T, const 
     return mk<R>(ar, ai);
 }
 
+// (cos, sin) of every instance's angles, in float64, then to the state precision: the
+// first node of the batch graph (the host only copies the angles).
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_batch_sincos(const double *__restrict__ theta, cplx<R> *__restrict__ cs,
+                                                          long long n) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        double sn, cn;
+        sincos(theta[k], &sn, &cn);
+        cs[k] = mk<R>((R)cn, (R)sn);
+    }
+}
+
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_batch(BatchArgs<R> B) {
     extern __shared__ __align__(16) unsigned char batch_smem[];
@@ -472,9 +484,6 @@ sv_status bfail(sv_status s, const std::string &m) {
     return s;
 }
 
-template <typename R> cplx<R> mk_host(double c, double s);
-template <> float2 mk_host<float>(double c, double s) { return make_float2((float)c, (float)s); }
-template <> double2 mk_host<double>(double c, double s) { return make_double2(c, s); }
 }  // namespace
 
 struct sv_batch {
@@ -496,10 +505,11 @@ struct sv_batch {
     int *d_order = nullptr, *d_ctrl = nullptr;
     BatchOp *d_ops = nullptr;
     void *d_cs = nullptr, *d_r = nullptr, *d_scratch = nullptr;
+    double *d_theta = nullptr;
     double *d_d = nullptr, *d_out = nullptr;
     uint32_t *d_u32 = nullptr;
     uint16_t *d_u16 = nullptr;
-    void *h_cs = nullptr;
+    void *h_cs = nullptr;  // pinned: the angles of the next launch (float64)
     double *h_out = nullptr;
     int *h_ctrl = nullptr;
     unsigned long long budget_ns = 0;
@@ -702,6 +712,7 @@ sv_status build_plan(sv_batch *b, int n_inst, const sv_instance *inst) {
     if ((s = up((void **)&b->d_u32, A.u32.data(), A.u32.size() * sizeof(uint32_t))) != SV_OK) return s;
     if ((s = up((void **)&b->d_u16, A.u16.data(), A.u16.size() * sizeof(uint16_t))) != SV_OK) return s;
     if ((s = up(&b->d_cs, nullptr, std::max<long long>(cs, 1) * sizeof(cplx<R>))) != SV_OK) return s;
+    if ((s = up((void **)&b->d_theta, nullptr, std::max<long long>(cs, 1) * sizeof(double))) != SV_OK) return s;
     if ((s = up((void **)&b->d_out, nullptr, std::max<long long>(out, 1) * sizeof(double))) != SV_OK) return s;
     if ((s = up((void **)&b->d_ctrl, nullptr, 2 * sizeof(int))) != SV_OK) return s;
     // scratch slots for the largest grid sv_batch_autotune may try (4 blocks per SM)
@@ -714,7 +725,7 @@ sv_status build_plan(sv_batch *b, int n_inst, const sv_instance *inst) {
         b->smem = (sm > 0 && sm <= kBatchSmemCap) ? sm : 0;
     }
     if ((s = up(&b->d_work, nullptr, (size_t)b->grid_max * b->work_stride)) != SV_OK) return s;
-    if (cudaMallocHost(&b->h_cs, std::max<long long>(cs, 1) * sizeof(cplx<R>)) != cudaSuccess ||
+    if (cudaMallocHost(&b->h_cs, std::max<long long>(cs, 1) * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void **)&b->h_out, std::max<long long>(out, 1) * sizeof(double)) != cudaSuccess ||
         cudaMallocHost((void **)&b->h_ctrl, 2 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
@@ -745,7 +756,12 @@ sv_status capture(sv_batch *b) {
     }
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bfail(SV_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
-    cudaMemcpyAsync(b->d_cs, b->h_cs, std::max<long long>(b->total_ops, 1) * sizeof(cplx<R>), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(b->d_theta, b->h_cs, std::max<long long>(b->total_ops, 1) * sizeof(double), cudaMemcpyHostToDevice,
+                    st);
+    if (b->total_ops > 0) {
+        const long long g = std::min<long long>((b->total_ops + kThreads - 1) / kThreads, (long long)b->sm_count * 4);
+        k_batch_sincos<R><<<(int)g, kThreads, 0, st>>>(b->d_theta, (cplx<R> *)b->d_cs, b->total_ops);
+    }
     cudaMemsetAsync(b->d_ctrl, 0, 2 * sizeof(int), st);
     if (b->threads == 1024) k_batch<R, 1024><<<b->grid, 1024, b->smem, st>>>(a);
     else if (b->threads == 512) k_batch<R, 512><<<b->grid, 512, b->smem, st>>>(a);
@@ -768,8 +784,7 @@ sv_status capture(sv_batch *b) {
 
 template <typename R>
 void fill_cs(sv_batch *b, const double *theta) {
-    cplx<R> *h = (cplx<R> *)b->h_cs;
-    for (long long k = 0; k < b->total_ops; ++k) h[k] = mk_host<R>(std::cos(theta[k]), std::sin(theta[k]));
+    if (b->total_ops > 0) std::memcpy(b->h_cs, theta, (size_t)b->total_ops * sizeof(double));
 }
 
 }  // namespace
@@ -843,7 +858,7 @@ sv_status sv_batch_energy_grad(sv_batch_handle b, const double *theta, double *e
             cudaGetLastError();
             s = bfail(SV_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
         } else {
-            b->launches++;
+            b->launches += b->total_ops > 0 ? 2 : 1;
         }
     }
     if (s == SV_OK) {
@@ -905,7 +920,7 @@ sv_status sv_batch_autotune(sv_batch_handle b, const double *theta, int *grid_ou
                 cudaGetLastError();
                 s = bfail(SV_ERR_CUDA, std::string("batch autotune launch: ") + cudaGetErrorString(e));
             } else {
-                b->launches++;
+                b->launches += b->total_ops > 0 ? 2 : 1;
             }
         }
         if (s == SV_OK && (best_t < 0.f || ms < best_t)) {
