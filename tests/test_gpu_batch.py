@@ -106,3 +106,25 @@ def test_batch_edges_and_errors():
     assert e.value.status == 1
     with pytest.raises(sv.SvError):
         b.energy_grad(np.full(2 * len(p["ops"]), np.nan))
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_batch_generic_path_for_large_string_spaces(dtype):
+    """An instance with more than 512 alpha strings (24 qubits, 5 alpha + 1 beta electrons:
+    792 x 12 determinants) takes the generic per-element sigma and filtered sweeps; batched
+    beside instances that take the string-blocked path, every instance matches the oracle."""
+    big = inputs.make_problem(24, 6, 12, seed=4242)
+    big["occ"] = np.array([0, 2, 4, 6, 8, 1], dtype=np.int32)   # alpha orbitals 0-4, beta orbital 0
+    big["na"], big["nb"] = 5, 1
+    probs = [big] + inputs.batch_problems(3, first=7)
+    b = sv.Batch(probs, dtype)
+    theta = np.concatenate([p["theta"] for p in probs]) * 4
+    E, g = b.energy_grad(theta)
+    tE, tg = TOL[dtype]
+    off = 0
+    for k, p in enumerate(probs):
+        q = dict(p, theta=theta[off:off + len(p["ops"])])
+        off += len(p["ops"])
+        Er, gr = _oracle(q)
+        assert abs(E[k] - Er) <= tE, (k, E[k], Er)
+        assert np.max(np.abs(g[k] - gr)) <= tg, k
