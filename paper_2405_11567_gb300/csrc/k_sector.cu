@@ -8,8 +8,8 @@
 // An excitation (or a density-matrix element a+_p a_q) acts on the determinants
 // whose alpha string matches its alpha "from" pattern and whose beta string
 // matches its beta pattern; its partner is found through the string ranks.  The
-// kernels below give each block one beta string (row) and its threads the alpha
-// strings of that row, so a launch touches only the pairs it rotates:
+// rotation kernels spread an operator's pairs (its alpha list x beta list) over the
+// whole grid, so a launch touches only the pairs it rotates:
 //   k_rotate_l   psi'[x] = c psi[x] - s sn psi[x'],  psi'[x'] = c psi[x'] + s sn psi[x]
 //                over the op's pairs (alpha list x beta list, built by k_build_lists)
 //   k_adjoint_l  g += s (Re conj(lam[x']) psi[x] - Re conj(lam[x]) psi[x']), then U^dagger
@@ -93,30 +93,70 @@ __global__ void __launch_bounds__(kThreads) k_build_lists(const ListOp *__restri
     }
 }
 
-// psi <- exp(theta G) psi over the op's pairs: block r takes beta entries r, r + grid,
-// ..., its threads the alpha entries.
+// The op's pairs (beta entry r, alpha entry i) in flattened order r na + i, spread
+// over the whole grid: thread t takes pairs t, t + T, ... (T = threads in the grid),
+// four at a time so their loads are in flight together.  Pair (r, i) is (I, J) with
+//   I = rank_b(r) Da + rank_a(i),  J = partner_b(r) Da + partner_a(i),
+// and the Jordan-Wigner sign the XOR of the two entries' sign bits.
+struct PairWalk {
+    int r, i, dr, di, na;
+    __device__ __forceinline__ PairWalk(int na_l) : na(na_l) {
+        const int T = (int)(gridDim.x * blockDim.x), g = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+        r = g / na_l;
+        i = g - r * na_l;
+        dr = T / na_l;
+        di = T - dr * na_l;
+    }
+    __device__ __forceinline__ void next() {
+        r += dr;
+        i += di;
+        if (i >= na) {
+            i -= na;
+            ++r;
+        }
+    }
+};
+
+constexpr int kPairBatch = 4;
+
+// psi <- exp(theta G) psi over the op's pairs.
 template <typename A>
 __global__ void __launch_bounds__(kThreads) k_rotate_l(A *__restrict__ psi, const uint32_t *__restrict__ al,
                                                        int na_l, const uint32_t *__restrict__ bl, int nb_l, int Da,
                                                        real_of<A> c, real_of<A> sn) {
     using R = real_of<A>;
-    for (int r = blockIdx.x; r < nb_l; r += gridDim.x) {
-        const uint32_t eb = bl[r];
-        const size_t rowI = (size_t)(eb & 0x7FFFu) * Da, rowJ = (size_t)(eb >> 16) * Da;
-        const uint32_t sgb = eb & 0x8000u;
-        for (int i = threadIdx.x; i < na_l; i += blockDim.x) {
-            const uint32_t ea = al[i];
-            const size_t I = rowI + (ea & 0x7FFFu), J = rowJ + (ea >> 16);
-            const R ss = ((ea & 0x8000u) ^ sgb) ? -sn : sn;
-            const A u = psi[I], v = psi[J];
-            psi[I] = lin2<A>(c, u, -ss, v);
-            psi[J] = lin2<A>(c, v, ss, u);
+    if (na_l <= 0) return;
+    PairWalk w(na_l);
+    while (w.r < nb_l) {
+        size_t I[kPairBatch], J[kPairBatch];
+        bool ok[kPairBatch];
+        R ss[kPairBatch];
+        #pragma unroll
+        for (int v = 0; v < kPairBatch; ++v) {
+            ok[v] = w.r < nb_l;
+            const uint32_t eb = ok[v] ? bl[w.r] : 0u, ea = ok[v] ? al[w.i] : 0u;  // 0: rank 0, in bounds
+            I[v] = (size_t)(eb & 0x7FFFu) * Da + (ea & 0x7FFFu);
+            J[v] = (size_t)(eb >> 16) * Da + (ea >> 16);
+            ss[v] = ((ea ^ eb) & 0x8000u) ? -sn : sn;
+            w.next();
+        }
+        A u[kPairBatch], x[kPairBatch];
+        #pragma unroll
+        for (int v = 0; v < kPairBatch; ++v) {
+            u[v] = psi[I[v]];
+            x[v] = psi[J[v]];
+        }
+        #pragma unroll
+        for (int v = 0; v < kPairBatch; ++v) {
+            if (!ok[v]) continue;
+            psi[I[v]] = lin2<A>(c, u[v], -ss[v], x[v]);
+            psi[J[v]] = lin2<A>(c, x[v], ss[v], u[v]);
         }
     }
 }
 
 // Adjoint step over the op's pairs: the gradient term, then U^dagger on psi and
-// lambda; one float64 partial per block (fixed order).
+// lambda; one float64 partial per block (fixed order: every block writes its entry).
 template <typename A>
 __global__ void __launch_bounds__(kThreads) k_adjoint_l(A *__restrict__ psi, A *__restrict__ lam,
                                                         const uint32_t *__restrict__ al, int na_l,
@@ -125,25 +165,42 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_l(A *__restrict__ psi, A *
     using R = real_of<A>;
     __shared__ double red[kThreads / 32];
     double acc = 0.0;
-    for (int r = blockIdx.x; r < nb_l; r += gridDim.x) {
-        const uint32_t eb = bl[r];
-        const size_t rowI = (size_t)(eb & 0x7FFFu) * Da, rowJ = (size_t)(eb >> 16) * Da;
-        const uint32_t sgb = eb & 0x8000u;
-        R t = 0;
-        for (int i = threadIdx.x; i < na_l; i += blockDim.x) {
-            const uint32_t ea = al[i];
-            const size_t I = rowI + (ea & 0x7FFFu), J = rowJ + (ea >> 16);
-            const bool neg = (ea & 0x8000u) ^ sgb;
-            const A u = psi[I], v = psi[J], lu = lam[I], lv = lam[J];
-            const R ti = re_dot(lv, u) - re_dot(lu, v);
-            t += neg ? -ti : ti;
-            const R ss = neg ? -sn : sn;
-            psi[I] = lin2<A>(c, u, ss, v);
-            psi[J] = lin2<A>(c, v, -ss, u);
-            lam[I] = lin2<A>(c, lu, ss, lv);
-            lam[J] = lin2<A>(c, lv, -ss, lu);
+    if (na_l > 0) {
+        PairWalk w(na_l);
+        while (w.r < nb_l) {
+            size_t I[kPairBatch], J[kPairBatch];
+            bool ok[kPairBatch], neg[kPairBatch];
+            #pragma unroll
+            for (int v = 0; v < kPairBatch; ++v) {
+                ok[v] = w.r < nb_l;
+                const uint32_t eb = ok[v] ? bl[w.r] : 0u, ea = ok[v] ? al[w.i] : 0u;
+                I[v] = (size_t)(eb & 0x7FFFu) * Da + (ea & 0x7FFFu);
+                J[v] = (size_t)(eb >> 16) * Da + (ea >> 16);
+                neg[v] = ((ea ^ eb) & 0x8000u) != 0u;
+                w.next();
+            }
+            A u[kPairBatch], x[kPairBatch], lu[kPairBatch], lx[kPairBatch];
+            #pragma unroll
+            for (int v = 0; v < kPairBatch; ++v) {
+                u[v] = psi[I[v]];
+                x[v] = psi[J[v]];
+                lu[v] = lam[I[v]];
+                lx[v] = lam[J[v]];
+            }
+            R t = 0;
+            #pragma unroll
+            for (int v = 0; v < kPairBatch; ++v) {
+                if (!ok[v]) continue;
+                const R ti = re_dot(lx[v], u[v]) - re_dot(lu[v], x[v]);
+                t += neg[v] ? -ti : ti;
+                const R ss = neg[v] ? -sn : sn;
+                psi[I[v]] = lin2<A>(c, u[v], ss, x[v]);
+                psi[J[v]] = lin2<A>(c, x[v], -ss, u[v]);
+                lam[I[v]] = lin2<A>(c, lu[v], ss, lx[v]);
+                lam[J[v]] = lin2<A>(c, lx[v], -ss, lu[v]);
+            }
+            acc += (double)t;
         }
-        acc += (double)t;
     }
     const double s = block_sum(acc, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
