@@ -363,3 +363,26 @@ def test_expectation_forms_and_chunks(variant, chunk, dtype):
     gp_ref = np.array([2 * np.vdot(sig, A.generator_apply(sec, op, psi)).real for op in pool])
     _, gp = st.pool_gradients(ham, pool)
     assert np.max(np.abs(gp - gp_ref)) <= TOL[dtype]["g"]
+
+
+@pytest.mark.parametrize("na,nb", [(0, 3), (4, 0), (5, 2), (1, 5)])
+@pytest.mark.parametrize("variant", [3, 4])
+def test_expectation_degenerate_string_spaces(na, nb, variant):
+    """Sectors where one spin has a single string (no electrons, or every orbital filled):
+    1 x 1 same-spin matrices, no excitations of that spin, empty pair lists; energy,
+    gradient and 1-RDM match the oracle in both split forms (complex64)."""
+    n = 10
+    p = inputs.make_problem(n, 4, 24, seed=919)
+    dense0 = inputs.random_sector_state(n, na, nb, np.random.default_rng(na * 7 + nb))
+    sec = oracle.Sector(n, na, nb)
+    psi0 = dense0[sec.dets.astype(np.int64)]
+    theta = p["theta"] * 6
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
+    psi = A.apply_ansatz(sec, p["ops"], theta, psi0)
+    for storage in ("sector", "dense"):
+        st = sv.StateVector(n, "c64", sector=(na, nb) if storage == "sector" else None)
+        st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
+        st.prepare_state(dense0.astype(np.complex64), na, nb)
+        E, g = st.energy_grad(sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"]), p["ops"], theta)
+        assert abs(E - Eref) <= TOL["c64"]["E"] and np.max(np.abs(g - gref)) <= TOL["c64"]["g"], storage
+        assert np.max(np.abs(st.rdm1() - A.rdm1(sec, psi))) <= TOL["c64"]["rdm"], storage
