@@ -353,13 +353,20 @@ typedef enum {
                                        2 pair lists: per-operator pair lists built once per
                                        pool (kept while the pool's operators are unchanged),
                                        amplitudes and lambda read interleaved */
-    SV_OPT_L2_FETCH = 12            /* dense storage: before each sweep the handle sets the
+    SV_OPT_L2_FETCH = 12,           /* dense storage: before each sweep the handle sets the
                                        CUDA context's maximum L2 fetch granularity
                                        (cudaLimitMaxL2FetchGranularity) to this many bytes
                                        (32, 64 or 128; default 32), and the context keeps
                                        it; 0 leaves the context's value alone.  Rotations
                                        of excitations on low address bits touch runs of
                                        32-64 bytes, which larger fetches double */
+    SV_OPT_SAME_PRODUCTS = 13       /* expectation variant 4's two dense products: 0 auto
+                                       (= 2); 1 cuBLAS float32 on the FP32 pipe; 2 the
+                                       library's tensor-core kernel (tcgen05 bf16 MMAs on
+                                       operands split into three bf16 pieces, six
+                                       products: float32-level accuracy; TMA copies; a
+                                       bounded wait that runs out makes the next
+                                       synchronising call fail with SV_ERR_CUDA) */
 } sv_option;
 
 /* Options change launch choices or summation order only: results agree within the

@@ -34,6 +34,7 @@
 // its energy share); k_sigma_rows<SPLIT> then adds every other group, reading its
 // own row from shared memory, and completes sigma and the row's energy.
 #include <cublas_v2.h>
+#include <cuda_bf16.h>
 
 #include "sv_internal.h"
 #include "sv_sigma.cuh"
@@ -709,14 +710,14 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
 // (spin-orbital tables hdiag, Jp) to dA / dB.  Ma and Mb must be zeroed before.
 __global__ void __launch_bounds__(128) k_same_mats(SigmaTables<float> T, int Db, float *__restrict__ Ma,
                                                     float *__restrict__ Mb, double *__restrict__ dA,
-                                                    double *__restrict__ dB) {
+                                                    double *__restrict__ dB, int lda, int ldb) {
     __shared__ uint8_t occ[kMaxOrb], emp[kMaxOrb];
     __shared__ int s_no, s_ne;
     const bool beta = (int)blockIdx.x >= T.Da;
     const int I = beta ? (int)blockIdx.x - T.Da : (int)blockIdx.x, D = beta ? Db : T.Da, N = T.N, spin = beta;
     const uint16_t *rk = beta ? T.rb : T.ra;
     const uint32_t str = beta ? T.strb[I] : T.stra[I], pps = prefix_parity(str);
-    float *row = (beta ? Mb : Ma) + (size_t)I * D;
+    float *row = (beta ? Mb : Ma) + (size_t)I * (beta ? ldb : lda);
     if (threadIdx.x == 0) {
         int no = 0, ne = 0;
         for (int o = 0; o < N; ++o) {
@@ -759,19 +760,39 @@ __global__ void __launch_bounds__(128) k_same_mats(SigmaTables<float> T, int Db,
 }
 
 // X[plane][Ib][Ia] = phi(a, b) * component of C[Ib][Ia] (planes: re, im).
+// Three bf16 pieces of a float: x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2).
+__device__ __forceinline__ void bf16x3(float v, uint16_t *p, size_t piece) {
+    const __nv_bfloat16 a = __float2bfloat16_rn(v);
+    const float r = v - __bfloat162float(a);
+    const __nv_bfloat16 b = __float2bfloat16_rn(r);
+    const __nv_bfloat16 c = __float2bfloat16_rn(r - __bfloat162float(b));
+    p[0] = __bfloat16_as_ushort(a);
+    p[piece] = __bfloat16_as_ushort(b);
+    p[2 * piece] = __bfloat16_as_ushort(c);
+}
+
+// With Xp (tensor-core form) the planes are written as three bf16 pieces at stride px
+// instead of float32 X.
 template <typename Amp>
 __global__ void __launch_bounds__(kThreads) k_phase_planar(const Amp *__restrict__ C, const uint16_t *__restrict__ stra,
                                                            const uint16_t *__restrict__ strb, int Da, int Db,
-                                                           float *__restrict__ X) {
-    const size_t plane = (size_t)Da * Db;
+                                                           float *__restrict__ X, int ld, uint16_t *__restrict__ Xp,
+                                                           size_t px) {
+    const size_t plane = (size_t)ld * Db;  // rows padded to ld (the padding stays zero)
     for (int Ib = blockIdx.x; Ib < Db; Ib += gridDim.x) {
         const uint32_t ppb = prefix_parity(strb[Ib]);
-        const size_t off = (size_t)Ib * Da;
+        const size_t off = (size_t)Ib * Da, xo = (size_t)Ib * ld;
         for (int Ia = threadIdx.x; Ia < Da; Ia += blockDim.x) {
             const uint32_t neg = (uint32_t)par(stra[Ia] & ppb);
             const Amp c = C[off + Ia];
-            X[off + Ia] = flip_sign<float>(re(c), neg);
-            if constexpr (AmpT<Amp>::kCplx) X[plane + off + Ia] = flip_sign<float>(im(c), neg);
+            const float xr = flip_sign<float>(re(c), neg);
+            if (Xp) bf16x3(xr, Xp + xo + Ia, px);
+            else X[xo + Ia] = xr;
+            if constexpr (AmpT<Amp>::kCplx) {
+                const float xi = flip_sign<float>(im(c), neg);
+                if (Xp) bf16x3(xi, Xp + plane + xo + Ia, px);
+                else X[plane + xo + Ia] = xi;
+            }
         }
     }
 }
@@ -961,17 +982,20 @@ static cudaError_t launch_ab_k(const RowArgs<double> &A, int K, size_t smem, cud
     return launch_ab_k4<double, 2, 4, 6, 8>(A, K, smem, st);
 }
 
+cudaError_t launch_same_tc(const uint16_t *M, size_t pm, const uint16_t *X, size_t px, uint16_t *Xt, size_t pt,
+                           float *G, int planes, int Da, int Db, int lda, int ldb, int *err, cudaStream_t st);
+
 // G = Ma X + X Mb^T on every plane (column-major views: X and G are Da x (planes Db),
 // Ma is Da x Da, Mb Db x Db; both symmetric).
 static cudaError_t same_products(const SameGemm &g, int Da, int Db) {
     cublasHandle_t hb = (cublasHandle_t)g.blas;
     const float one = 1.f, zero = 0.f;
     const cublasComputeType_t ct = CUBLAS_COMPUTE_32F;
-    cublasStatus_t s = cublasGemmEx(hb, CUBLAS_OP_N, CUBLAS_OP_N, Da, g.planes * Db, Da, &one, g.Ma, CUDA_R_32F, Da,
-                                    g.X, CUDA_R_32F, Da, &zero, g.G, CUDA_R_32F, Da, ct, CUBLAS_GEMM_DEFAULT);
+    cublasStatus_t s = cublasGemmEx(hb, CUBLAS_OP_N, CUBLAS_OP_N, Da, g.planes * Db, Da, &one, g.Ma, CUDA_R_32F, g.lda,
+                                    g.X, CUDA_R_32F, g.lda, &zero, g.G, CUDA_R_32F, Da, ct, CUBLAS_GEMM_DEFAULT);
     if (s != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    s = cublasGemmStridedBatchedEx(hb, CUBLAS_OP_N, CUBLAS_OP_N, Da, Db, Db, &one, g.X, CUDA_R_32F, Da,
-                                   (long long)Da * Db, g.Mb, CUDA_R_32F, Db, 0, &one, g.G, CUDA_R_32F, Da,
+    s = cublasGemmStridedBatchedEx(hb, CUBLAS_OP_N, CUBLAS_OP_N, Da, Db, Db, &one, g.X, CUDA_R_32F, g.lda,
+                                   (long long)g.lda * Db, g.Mb, CUDA_R_32F, g.ldb, 0, &one, g.G, CUDA_R_32F, Da,
                                    (long long)Da * Db, g.planes, ct, CUBLAS_GEMM_DEFAULT);
     if (s != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
     return cudaGetLastError();
@@ -984,10 +1008,13 @@ static cudaError_t launch_same_t(RowArgs<Amp> A, const RowTables &T, int dtype, 
         return cudaErrorInvalidValue;  // single-precision states only
     } else {
         const int grid = T.Db < sm_count * 8 ? T.Db : sm_count * 8;
-        k_phase_planar<Amp><<<grid, kThreads, 0, st>>>(A.C, T.stra, T.strb, T.Da, T.Db, g.X);
+        k_phase_planar<Amp><<<grid, kThreads, 0, st>>>(A.C, T.stra, T.strb, T.Da, T.Db, g.X, g.lda,
+                                                       g.tc ? g.Xp : nullptr, g.px);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        e = same_products(g, T.Da, T.Db);
+        e = g.tc ? launch_same_tc(g.Mp, g.pm, g.Xp, g.px, g.Xtp, g.pt, g.G, g.planes, T.Da, T.Db, g.lda, g.ldb, g.err,
+                                  st)
+                 : same_products(g, T.Da, T.Db);
         if (e != cudaSuccess) return e;
         A.same_gemm = 1;
         e = launch_ab_k(A, K, ab_smem(dtype, K, T), st);
@@ -1034,14 +1061,15 @@ cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, i
     return e;
 }
 
-// Ma, Mb (zeroed here), dA, dB of the sector for single-precision tables.
+// Ma [Da][lda], Mb [Db][ldb] (zeroed here, padding included), dA, dB of the sector for
+// single-precision tables.
 cudaError_t launch_same_mats(int n, const RowTables &T, const double *hdiag, const double *Jp, float *Ma, float *Mb,
-                             double *dA, double *dB, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(Ma, 0, sizeof(float) * (size_t)T.Da * T.Da, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(Mb, 0, sizeof(float) * (size_t)T.Db * T.Db, st);
+                             double *dA, double *dB, int lda, int ldb, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(Ma, 0, sizeof(float) * (size_t)T.Da * lda, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(Mb, 0, sizeof(float) * (size_t)T.Db * ldb, st);
     if (e != cudaSuccess) return e;
     RowArgs<float> A = row_args<float>(nullptr, nullptr, nullptr, n, T, hdiag, Jp, 0.0, nullptr);
-    k_same_mats<<<T.Da + T.Db, 128, 0, st>>>(A.T, T.Db, Ma, Mb, dA, dB);
+    k_same_mats<<<T.Da + T.Db, 128, 0, st>>>(A.T, T.Db, Ma, Mb, dA, dB, lda, ldb);
     return cudaGetLastError();
 }
 

@@ -76,7 +76,8 @@ cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, i
                               const double *Jp, double e_shift, double *partial, int K, cudaStream_t st,
                               const SameGemm *g, int sm_count);
 cudaError_t launch_same_mats(int n, const RowTables &T, const double *hdiag, const double *Jp, float *Ma, float *Mb,
-                             double *dA, double *dB, cudaStream_t st);
+                             double *dA, double *dB, int lda, int ldb, cudaStream_t st);
+cudaError_t launch_split_bf16x3(const float *x, uint16_t *out, size_t n, size_t piece, int sm_count, cudaStream_t st);
 int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want);
 const int *sigma_ab_sizes(int dtype);
 
@@ -642,24 +643,44 @@ static bool use_same_gemm(sv_handle h, int K) {
 }
 
 // The same-spin matrices of the table set and sector (built on first use, kept until
-// either changes), the two work planes and the cuBLAS handle on the handle's stream.
+// either changes), the work planes, and for the cuBLAS form its handle on the
+// handle's stream.  Rows of Ma, X and of Mb, Xt are padded to a multiple of 8
+// elements with zeros (16-byte row strides of the bf16 pieces, as TMA requires).
 static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R, SameGemm *g) {
-    if (!h->blas) {
-        cublasHandle_t hb = nullptr;
-        if (cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS) return fail(h, SV_ERR_CUDA, "cublasCreate failed");
-        h->blas = hb;
-        const size_t ws = (size_t)32 << 20;
-        SV_TRY(dev_alloc(h, &h->blas_ws, ws, "cuBLAS workspace"));
-        h->blas_ws_bytes = ws;
-        if (cublasSetWorkspace(hb, h->blas_ws, ws) != CUBLAS_STATUS_SUCCESS)
-            return fail(h, SV_ERR_CUDA, "cublasSetWorkspace failed");
+    const bool tc = h->same_products != 1;
+    if (!tc) {
+        if (!h->blas) {
+            cublasHandle_t hb = nullptr;
+            if (cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS) return fail(h, SV_ERR_CUDA, "cublasCreate failed");
+            h->blas = hb;
+            const size_t ws = (size_t)32 << 20;
+            SV_TRY(dev_alloc(h, &h->blas_ws, ws, "cuBLAS workspace"));
+            h->blas_ws_bytes = ws;
+            if (cublasSetWorkspace(hb, h->blas_ws, ws) != CUBLAS_STATUS_SUCCESS)
+                return fail(h, SV_ERR_CUDA, "cublasSetWorkspace failed");
+        }
+        if (cublasSetStream((cublasHandle_t)h->blas, h->stream) != CUBLAS_STATUS_SUCCESS)
+            return fail(h, SV_ERR_CUDA, "cublasSetStream failed");
+        if (cublasSetMathMode((cublasHandle_t)h->blas, CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS)
+            return fail(h, SV_ERR_CUDA, "cublasSetMathMode failed");
+    } else {
+        if (!h->kerr) {
+            SV_TRY(dev_alloc(h, (void **)&h->kerr, 16, "kernel error flag"));
+            SV_CUDA(h, cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream));
+        }
+        if (!h->hkerr) {
+            if (cudaMallocHost((void **)&h->hkerr, sizeof(int)) != cudaSuccess) {
+                cudaGetLastError();
+                h->hkerr = nullptr;
+                return fail(h, SV_ERR_OOM, "pinned host allocation failed");
+            }
+            *h->hkerr = 0;
+        }
     }
-    if (cublasSetStream((cublasHandle_t)h->blas, h->stream) != CUBLAS_STATUS_SUCCESS)
-        return fail(h, SV_ERR_CUDA, "cublasSetStream failed");
-    if (cublasSetMathMode((cublasHandle_t)h->blas, CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS)
-        return fail(h, SV_ERR_CUDA, "cublasSetMathMode failed");
-    const size_t Da = (size_t)h->Da, Db = (size_t)h->Db;
-    const size_t mf = (Da * Da + Db * Db) * sizeof(float), mb = (mf + 15) / 16 * 16 + (Da + Db) * sizeof(double);
+    const size_t Da = (size_t)h->Da, Db = (size_t)h->Db, lda = (Da + 7) / 8 * 8, ldb = (Db + 7) / 8 * 8;
+    // [Ma | Mb] (float32), the one-spin diagonals, then the three bf16 pieces of [Ma | Mb]
+    const size_t nm = Da * lda + Db * ldb, mf = nm * sizeof(float), dof = (mf + 255) / 256 * 256,
+                 sof = (dof + (Da + Db) * sizeof(double) + 255) / 256 * 256, mb = sof + 3 * nm * sizeof(uint16_t);
     float *Ma = nullptr;
     if (!h->sg_mats || h->sg_serial != T->serial || h->sg_na != h->na || h->sg_nb != h->nb) {
         if (h->sg_mats_bytes < mb) {
@@ -670,31 +691,69 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
             h->sg_mats_bytes = mb;
         }
         Ma = (float *)h->sg_mats;
-        double *dA = (double *)((uint8_t *)h->sg_mats + (mf + 15) / 16 * 16);
-        SV_CUDA(h, launch_same_mats(h->n, R, T->hdiag, T->Jp, Ma, Ma + Da * Da, dA, dA + Da, h->stream));
-        h->launches++;
+        double *dA = (double *)((uint8_t *)h->sg_mats + dof);
+        SV_CUDA(h, launch_same_mats(h->n, R, T->hdiag, T->Jp, Ma, Ma + Da * lda, dA, dA + Da, (int)lda, (int)ldb,
+                                    h->stream));
+        SV_CUDA(h, launch_split_bf16x3(Ma, (uint16_t *)((uint8_t *)h->sg_mats + sof), nm, nm, h->sm_count,
+                                       h->stream));
+        h->launches += 2;
         h->sg_serial = T->serial;
         h->sg_na = h->na;
         h->sg_nb = h->nb;
     }
     Ma = (float *)h->sg_mats;
     const int planes = is_complex(h->dtype) ? 2 : 1;
-    const size_t pb = sizeof(float) * planes * Da * Db;
-    if (h->sg_buf_bytes < 2 * pb) {
-        dev_free(h, h->sg_buf, h->sg_buf_bytes);
-        h->sg_buf = nullptr;
-        h->sg_buf_bytes = 0;
-        SV_TRY(dev_alloc(h, &h->sg_buf, 2 * pb, "same-spin product planes"));
-        h->sg_buf_bytes = 2 * pb;
+    // X [planes][Db][lda], G [planes][Db][Da], Xt [planes][Da][ldb] (tensor-core form)
+    // (each region rounded to 256 bytes: aligned starts for vector loads and TMA)
+    // cuBLAS form: X float32 [planes][Db][lda]; tensor-core form: its three bf16 pieces
+    // and those of the transposes [planes][Da][ldb]; then G float32 [planes][Db][Da]
+    const size_t nx = (size_t)planes * Db * lda, nt = (size_t)planes * Da * ldb, ng = (size_t)planes * Db * Da;
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t xb = tc ? r256(3 * nx * sizeof(uint16_t)) : r256(nx * sizeof(float)),
+                 tb = tc ? r256(3 * nt * sizeof(uint16_t)) : 0;
+    const size_t need = xb + tb + ng * sizeof(float);
+    const uint64_t geom = ((uint64_t)Da << 32) | ((uint64_t)Db << 2) | ((uint64_t)planes << 1) | (tc ? 1u : 0u);
+    if (h->sg_buf_bytes < need || h->sg_buf_geom != geom) {
+        if (h->sg_buf_bytes < need) {
+            dev_free(h, h->sg_buf, h->sg_buf_bytes);
+            h->sg_buf = nullptr;
+            h->sg_buf_bytes = 0;
+            SV_TRY(dev_alloc(h, &h->sg_buf, need, "same-spin product planes"));
+            h->sg_buf_bytes = need;
+        }
+        SV_CUDA(h, cudaMemsetAsync(h->sg_buf, 0, need, h->stream));  // the row padding stays zero
+        h->sg_buf_geom = geom;
     }
     g->Ma = Ma;
-    g->Mb = Ma + Da * Da;
-    g->dA = (const double *)((const uint8_t *)h->sg_mats + (mf + 15) / 16 * 16);
+    g->Mb = Ma + Da * lda;
+    g->dA = (const double *)((const uint8_t *)h->sg_mats + dof);
     g->dB = g->dA + Da;
-    g->X = (float *)h->sg_buf;
-    g->G = g->X + (size_t)planes * Da * Db;
+    uint8_t *B = (uint8_t *)h->sg_buf;
+    g->Mp = (const uint16_t *)((const uint8_t *)h->sg_mats + sof);
+    g->pm = nm;
+    g->X = tc ? nullptr : (float *)B;
+    g->Xp = tc ? (uint16_t *)B : nullptr;
+    g->px = nx;
+    g->Xtp = tc ? (uint16_t *)(B + xb) : nullptr;
+    g->pt = nt;
+    g->G = (float *)(B + xb + tb);
     g->blas = h->blas;
     g->planes = planes;
+    g->lda = (int)lda;
+    g->ldb = (int)ldb;
+    g->tc = tc ? 1 : 0;
+    g->err = h->kerr;
+    return SV_OK;
+}
+
+// After a stream synchronisation: a kernel whose bounded wait ran out (k_same_tc).
+static sv_status check_kernel_flag(sv_handle h) {
+    if (h->hkerr && *h->hkerr) {
+        *h->hkerr = 0;
+        if (h->kerr) cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream);
+        h->failed = true;
+        return fail(h, SV_ERR_CUDA, "same-spin products: a tensor-core wait ran out");
+    }
     return SV_OK;
 }
 
@@ -708,7 +767,8 @@ static sv_status sigma_rows(sv_handle h, DevTables *T, const RowTables &R, const
     if (sg) SV_TRY(ensure_same_gemm(h, T, R, &g));
     SV_CUDA(h, launch_sigma_rows(C, lam, lamc, h->dtype, h->n, R, T->hdiag, T->Jp, e_shift, h->partials, K,
                                  h->stream, sg ? &g : nullptr, h->sm_count));
-    h->launches += sg ? 3 : (K ? 2 : 1);  // cuBLAS's own kernels are not counted
+    h->launches += sg ? (g.tc ? 5 : 3) : (K ? 2 : 1);  // cuBLAS's own kernels are not counted
+    if (sg && g.tc) SV_CUDA(h, cudaMemcpyAsync(h->hkerr, h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     return SV_OK;
 }
 
@@ -1058,6 +1118,8 @@ sv_status sv_destroy(sv_handle h) {
     dev_free(h, h->Lbuf, h->Lbuf_bytes);
     dev_free(h, h->sg_mats, h->sg_mats_bytes);
     dev_free(h, h->sg_buf, h->sg_buf_bytes);
+    dev_free(h, h->kerr, 16);
+    if (h->hkerr) cudaFreeHost(h->hkerr);
     dev_free(h, h->blas_ws, h->blas_ws_bytes);
     if (h->blas) cublasDestroy((cublasHandle_t)h->blas);
     dev_free(h, h->lists.buf, h->lists.bytes);
@@ -1298,6 +1360,7 @@ sv_status sv_energy(sv_handle h, sv_ham_handle ham, double *e_out) {
     SV_TRY(expectation(h, ham, T, nullptr, c, 0));
     SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    SV_TRY(check_kernel_flag(h));
     *e_out = c + h->hpinned[0] / h->hpinned[1];
     return SV_OK;
 }
@@ -1389,6 +1452,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     }
     SV_TRY(mark(h, 6));
     SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    SV_TRY(check_kernel_flag(h));
     if (h->profile) {
         h->phase_ms[0] = elapsed(h, 0, 1);
         h->phase_ms[1] = elapsed(h, 1, 2);
@@ -1479,6 +1543,7 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
     SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, (2 + (size_t)n_pool) * sizeof(double), cudaMemcpyDeviceToHost,
                                h->stream));
     SV_CUDA(h, cudaStreamSynchronize(h->stream));
+    SV_TRY(check_kernel_flag(h));
     const double nrm = h->hpinned[1];
     if (e_out) *e_out = c + h->hpinned[0] / nrm;
     for (int k = 0; k < n_pool; ++k) grad_out[k] = 2.0 * h->hpinned[2 + k] / nrm;
@@ -1596,6 +1661,7 @@ sv_status sv_get_option(sv_handle h, sv_option opt, int64_t *value) {
         case SV_OPT_RDM_BLOCKS_PER_SM: *value = h->rdm_bps; return SV_OK;
         case SV_OPT_POOL_VARIANT: *value = h->pool_variant; return SV_OK;
         case SV_OPT_L2_FETCH: *value = h->l2_fetch; return SV_OK;
+        case SV_OPT_SAME_PRODUCTS: *value = h->same_products; return SV_OK;
     }
     return fail(h, SV_ERR_ARG, "unknown option");
 }
@@ -1650,6 +1716,10 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
         case SV_OPT_RDM_VARIANT:
             if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "rdm variant must be 0, 1 or 2");
             h->rdm_variant = (int)value;
+            return SV_OK;
+        case SV_OPT_SAME_PRODUCTS:
+            if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "same-spin product form must be 0, 1 or 2");
+            h->same_products = (int)value;
             return SV_OK;
         case SV_OPT_L2_FETCH:
             if (value != 0 && value != 32 && value != 64 && value != 128)

@@ -2,6 +2,8 @@
 (N_alpha, N_beta) sector, C[rank(beta string)][rank(alpha string)], against the
 CPU oracle, with the tolerances of the dense path.  Integer work (signs, partner
 ranks, which amplitudes are exactly zero) is compared bit for bit."""
+import math
+
 import numpy as np
 import pytest
 
@@ -176,11 +178,13 @@ def test_pool_gradients_match_oracle(dtype, tol, variant):
     assert np.array_equal(g4, g)
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("storage", ["sector", "dense"])
-def test_same_spin_products_match_oracle(storage):
-    """Expectation variant 4 (same-spin part as two dense float32 products in the
-    string-blocked basis) on an open-shell complex start: energy, gradient and pool
-    gradients within the complex64 tolerance, and reruns bit-identical."""
+def test_same_spin_products_match_oracle(storage, form):
+    """Expectation variant 4 (same-spin part as two dense products in the string-blocked
+    basis; form 1 cuBLAS float32, form 2 the tensor-core kernel on bf16x3 operands)
+    on an open-shell complex start: energy, gradient and pool gradients within the
+    complex64 tolerance, and reruns bit-identical."""
     n, na, nb = 16, 3, 4
     p = inputs.make_problem(n, 7, 40, seed=303)
     dense0 = inputs.random_sector_state(n, na, nb, np.random.default_rng(31))
@@ -191,6 +195,7 @@ def test_same_spin_products_match_oracle(storage):
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
     st = sv.StateVector(n, "c64", sector=(na, nb) if storage == "sector" else None)
     st.set_option(sv.SV_OPT_EXPECT_VARIANT, 4)
+    st.set_option(sv.SV_OPT_SAME_PRODUCTS, form)
     runs = []
     for _ in range(2):
         st.prepare_state(dense0.astype(np.complex64), na, nb)
@@ -204,6 +209,33 @@ def test_same_spin_products_match_oracle(storage):
     gp_ref = np.array([2 * np.vdot(sig, A.generator_apply(sec, op, psi)).real for op in pool])
     _, gp = st.pool_gradients(ham, pool)
     assert np.max(np.abs(gp - gp_ref)) <= TOL["c64"]["g"]
+
+
+def test_same_spin_products_several_tiles():
+    """The tensor-core same-spin products over several output tiles with ragged edges in
+    both directions (D_alpha = 330: three 128-row tiles, the last 74 rows; D_beta = 462:
+    two 256-column tiles, the last 206) and K blocks of 32 with a ragged last block, on
+    an open-shell complex start: energy and gradient match the oracle within the
+    complex64 tolerance in both product forms, and the forms agree to rounding."""
+    n, na, nb = 22, 4, 5
+    p = inputs.make_problem(n, 9, 6, seed=404)
+    dense0 = inputs.random_sector_state(n, na, nb, np.random.default_rng(5))
+    sec = oracle.Sector(n, na, nb)
+    assert (math.comb(n // 2, na), math.comb(n // 2, nb)) == (330, 462)
+    psi0 = dense0[sec.dets.astype(np.int64)]
+    theta = p["theta"] * 5
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    out = {}
+    for form in (1, 2):
+        st = _state(n, na, nb, "c64")
+        st.set_option(sv.SV_OPT_EXPECT_VARIANT, 4)
+        st.set_option(sv.SV_OPT_SAME_PRODUCTS, form)
+        st.prepare_state(dense0.astype(np.complex64), na, nb)
+        E, g = st.energy_grad(ham, p["ops"], theta)
+        assert abs(E - Eref) <= TOL["c64"]["E"] and np.max(np.abs(g - gref)) <= TOL["c64"]["g"], form
+        out[form] = (E, g)
+    assert abs(out[1][0] - out[2][0]) <= TOL["c64"]["E"]
 
 
 def _applies_in(sec, op):
