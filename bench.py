@@ -40,9 +40,10 @@ METRIC = "energy+adjoint-grad evals/s at 30 qubits, FP32-state vs FP64; % of HBM
 UNIT = "evals/s"
 CONFIG_ID = 5
 # DRAM bytes (read + write) of one sector-storage expectation (same-spin product form:
-# k_phase_planar, two float32 products, k_sigma_ab, k_sigma_comb) from the ncu capture
-# summarised in profiles/sigma_products_n30_sector_c64.md; None once a kernel changes.
-SIGMA_TRAFFIC_BYTES = 1020.3e6
+# k_phase_planar, k_transpose_pieces, k_same_tc, k_sigma_ab, k_sigma_comb) from the ncu
+# capture summarised in profiles/sigma_products_n30_sector_c64.md; None once a kernel
+# changes.
+SIGMA_TRAFFIC_BYTES = 1555.6e6
 # DRAM bytes per k_adjoint launch of the dense headline: the 28-qubit capture's
 # traffic / algorithmic ratio (1.115, profiles/k_adjoint_dram_n28_dense_c64.md) times
 # the 30-qubit algorithmic bytes per launch; None once the kernel changes.
@@ -511,7 +512,8 @@ def run_ours(args, rank, world, local_rank):
                 "value": throughput(world, K, s64["ms"]), "unit": UNIT, "ms_per_step": s64["ms"] / K,
                 "phases_ms": s64["phases"], "clocks": s64["clocks"], "gpu_launches": int(s64["launches"]),
                 "roofline": {"bound": "alu", "kernel": (
-                    "expectation: k_phase_planar + two float32 products (cuBLAS) + k_sigma_ab + k_sigma_comb"
+                    "expectation: k_phase_planar + k_transpose_pieces + k_same_tc (same-spin products, tcgen05 "
+                    "bf16x3) + k_sigma_ab + k_sigma_comb"
                     if (s64["tuned"] or {}).get("expect_variant", 4) == 4
                     else "expectation: k_sigma_ab + k_sigma_same (two launches)"),
                              "achieved": ach, "peak": fpeak, "unit": "TFLOP/s", "frac": ach / fpeak,
