@@ -328,10 +328,17 @@ typedef enum {
                                        doubles in a second kernel that stages partner rows
                                        in shared memory; 4 (single precision; float64
                                        states take 3): split, with the same-spin part as
-                                       two dense float32 products (cuBLAS) in the
+                                       two dense products (SV_OPT_SAME_PRODUCTS) in the
                                        string-blocked basis, Ma X + X Mb^T; Ma, Mb are
                                        built once per Hamiltonian and sector (4 (Da^2 +
-                                       Db^2) bytes) */
+                                       Db^2) bytes plus their bf16 pieces); 5 (single
+                                       precision, N <= 16 spatial orbitals, at most 4096
+                                       strings per spin; else 4): as 4, with the
+                                       alpha-beta part too as tensor-core products, one
+                                       per (alpha tile, partner beta string), into
+                                       planes of planes x Db x (nb (N - nb) + 1) x Da
+                                       floats (3.7 GB at 30 qubits, complex64) gathered
+                                       in a fixed order */
     SV_OPT_RDM_VARIANT = 4,         /* 0 auto (= 2); 1 sector gather: one thread per sector
                                        determinant (dense storage only); 2 string rows: one
                                        block per beta string of the compact matrix */

@@ -1,0 +1,533 @@
+// k_abtc.cu -- the alpha-beta part of sigma~ = phi sigma (expectation variant 5) as
+// products on the tensor cores.
+//
+// In the string-blocked basis (all alpha creators before all beta creators) the
+// alpha-beta part of H is sum_{pq,rs} (pq|rs) E^a_pq E^b_rs with the sign of E^a_pq
+// taken on the alpha string alone and that of E^b_rs on the beta string alone (a pair
+// of fermion operators passes the other spin's creators without a sign).  For an
+// output string pair (a, b):
+//   sigma~_ab(a, b) = sum over beta excitations r -> s of b (partner b' = b - r + s) of
+//                       s_b(b, rs) H[b'][col(b', rs)][a]  +  H[b][own][a]
+//   H[b'][j][a] = sum_kappa A_b'[a][kappa] B[j(b')][kappa]
+// over kappa = the N orbitals p (diagonal, kappa = p) and the N (N - 1) / 2 unordered
+// pairs p < q (kappa = N + pair index): (pq|rs) = (qp|rs) for real orbitals, so one K
+// entry serves both directions, and for a given a at most one direction applies:
+//   A_b'[a][p]      = X(a, b') if p in a, else 0,
+//   A_b'[a][{p,q}]  = s_a(a, pq) X(a ^ {p, q}, b') if exactly one of p, q is in a, else 0,
+//   B[j][p]         = (pp|sr),  B[j][{p,q}] = (qp|sr) for the j-th excitation (s in b',
+//                     r not in b') of b',
+//   B[own][p] = 0,  B[own][{p,q}] = sum_{l in b'} (qp|ll),
+// with X = phi C (phi(a, b) = (-1)^popc(a & pp(b))) and s_a the parity of a's bits
+// strictly between p and q.  The p = q, own-column term (the alpha-beta Coulomb
+// diagonal) is left to the diagonal.  Per b' the columns are its nb (N - nb)
+// excitations plus the own column, <= 65, padded to 64 or 80; K = N (N + 1) / 2 <= 136,
+// padded to a multiple of 16.
+//
+// k_ab_tc: a persistent kernel over units (128-string alpha tile, partner row b').
+// Eight builder warps stage the b' row of X as bf16 pieces (written once per sigma by
+// the phase kernel: per amplitude three words (re_k | im_k << 16), k = 1..2..3;
+// asynchronous copies, one unit ahead), gather A for the tile's rows K = 16 at a time
+// through a per-tile table (partner rank | sign | nonzero per row and kappa, rebuilt
+// when the tile changes) straight into the canonical no-swizzle K-major layout (core
+// matrices of 8 rows x 16 bytes), flipping sign bits and pairing halves only, and copy
+// the unit's B rows (pieces of a precomputed table);
+// lane 0 of warp 8 issues tcgen05.mma kind::f16 (six piece products per plane:
+// float32-level accuracy) into one of two tensor-memory accumulators; after building
+// a unit the builders drain the previous unit's accumulator into H.  Stage ring with
+// full / empty mbarriers; all waits bounded (past the limit: *err set, copies and MMAs
+// waited for, tensor memory freed, return).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "sv_internal.h"
+
+namespace svk {
+
+namespace {
+
+constexpr int kAbBuild = 256;                  // builder threads (8 warps): 2 per tile row
+constexpr int kAbThreadsTc = kAbBuild + 32;    // + the MMA warp
+constexpr int kAbM = 128;                      // alpha strings per tile
+constexpr int kAbKc = 16;                      // K (orbitals and orbital pairs) per stage
+constexpr int kAbS = 3;                        // stages
+constexpr int kAbMaxK = 144;                   // N (N + 1) / 2 <= 136 for N <= 16, padded to 16
+constexpr int kAbMaxN = 80;                    // columns per accumulator (<= 65 used)
+constexpr int kAbABytes = kAbM * kAbKc * 2;    // one bf16 piece of one plane of A: 4 KB
+constexpr uint32_t kAbSpins = 1u << 22;
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool ab_try(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool ab_wait(uint32_t mbar, uint32_t parity) {
+    for (uint32_t it = 0; it < kAbSpins; ++it) {
+        if (ab_try(mbar, parity)) return true;
+        __nanosleep(32);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void ab_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void ab_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kAbBuild) : "memory"); }
+
+// Barrier over the builder warps that also returns, to every builder thread, whether
+// any of them passed `v` true: a decision all builders take the same way.
+__device__ __forceinline__ bool builders_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kAbBuild)
+        : "memory");
+    return r != 0;
+}
+
+// Canonical no-swizzle K-major descriptor: K-adjacent core matrices 128 bytes apart,
+// adjacent 8-row groups 256 bytes apart (16 K elements = two 16-byte cores per row).
+__device__ __forceinline__ uint64_t ab_desc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(128u >> 4) << 16;
+    d |= (uint64_t)(256u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// byte offset of (row r, 16-byte column kc) in a tile of 16 K
+__device__ __forceinline__ uint32_t ab_off(int r, int kc) { return (uint32_t)(((r >> 3) * 2 + kc) * 128 + (r & 7) * 16); }
+
+__device__ __forceinline__ void split3(float v, uint32_t &p1, uint32_t &p2, uint32_t &p3) {
+    const __nv_bfloat16 a = __float2bfloat16_rn(v);
+    const float r = v - __bfloat162float(a);
+    const __nv_bfloat16 b = __float2bfloat16_rn(r);
+    const __nv_bfloat16 c = __float2bfloat16_rn(r - __bfloat162float(b));
+    p1 = __bfloat16_as_ushort(a);
+    p2 = __bfloat16_as_ushort(b);
+    p3 = __bfloat16_as_ushort(c);
+}
+
+__device__ __forceinline__ int ab_par(uint32_t x) { return __popc(x) & 1; }
+
+// bits strictly between i and j
+__device__ __forceinline__ uint32_t ab_between(int i, int j) {
+    const int lo = min(i, j), hi = max(i, j);
+    return ((1u << hi) - 1u) & ~((1u << (lo + 1)) - 1u);
+}
+
+__device__ __forceinline__ uint32_t ab_prefix_parity(uint32_t x) {
+    // bit k: parity of the bits of x below k
+    uint32_t y = x << 1;
+    y ^= y << 1;
+    y ^= y << 2;
+    y ^= y << 4;
+    y ^= y << 8;
+    y ^= y << 16;
+    return y;
+}
+
+}  // namespace
+
+struct AbTcArgs {
+    const uint32_t *Xi;       // [Db][ldi][3]: per amplitude of X = phi C, words (re_k | im_k << 16), k = 1, 2, 3
+    int ldi;                  // row stride of Xi in amplitudes (a multiple of 4: 16-byte rows)
+    const uint16_t *stra, *strb, *ra;
+    const uint16_t *Bp;       // pieces [3][rowsB][256] of the B table (rows: N^2 integral rows, Db own rows, a zero row)
+    size_t pb;                // piece stride of Bp (elements)
+    float *H;                 // planes [P][Db][ncols][Da]
+    size_t hplane;
+    int Da, Db, N, na, nb, ncols, nK, units;
+    uint32_t maskN;
+    int *err;
+};
+
+// K entries per tile row in the table (nK * 16) plus 8: an odd number of 16-byte words
+// per row, so the builders' 16-byte reads of 8 consecutive rows hit distinct banks.
+__host__ __device__ __forceinline__ int ab_tstride(int nK) { return nK * kAbKc + 8; }
+
+template <int P>
+__global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
+    extern __shared__ uint8_t ab_smem[];
+    __shared__ __align__(8) uint64_t full[kAbS], empty[kAbS], accf[2], acce[2], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int s_fail;
+    __shared__ int s_rowB[kAbMaxN];
+    __shared__ uint8_t s_kp[kAbMaxK], s_kq[kAbMaxK];
+    // dynamic: stage ring (1024-aligned), the two staged X rows, the tile's table
+    constexpr int kStageBytes = 2 * 3 * kAbABytes + 3 * kAbMaxN * kAbKc * 2;
+    const uint32_t raw = su32(ab_smem), sbase = (raw + 1023u) & ~1023u;
+    uint8_t *ring = ab_smem + (sbase - raw);
+    uint32_t *xrow = reinterpret_cast<uint32_t *>(ring + kAbS * kStageBytes);  // [2][ldi][3]
+    uint16_t *tbl = reinterpret_cast<uint16_t *>(xrow + 2 * (size_t)g.ldi * 3); // [128][tstride]
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int N = g.N, ncolsP = g.ncols <= 64 ? 64 : kAbMaxN, tstride = ab_tstride(g.nK);
+    const int Ktot = N * (N + 1) / 2;
+    const int Ac = 2 * 3 * kAbABytes;  // A bytes per stage (both planes)
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(&tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == kAbBuild) {
+        s_fail = 0;
+        for (int s = 0; s < kAbS; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&full[s])), "n"(kAbBuild) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&empty[s])) : "memory");
+        }
+        for (int t = 0; t < 2; ++t) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&accf[t])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&acce[t])), "n"(kAbBuild) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // kappa -> (p, q): p = q = kappa below N, then the pairs p < q in order
+    for (int k = tid; k < kAbMaxK; k += kAbThreadsTc) {
+        int p = 0, q = 0;
+        if (k < N) {
+            p = q = k;
+        } else if (k < Ktot) {
+            int pi = k - N;
+            while (pi >= N - 1 - p) { pi -= N - 1 - p; ++p; }
+            q = p + 1 + pi;
+        }
+        s_kp[k] = (uint8_t)p;
+        s_kq[k] = (uint8_t)q;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    if (warp < kAbBuild / 32) {
+        // ------------------------------------------------------------ builders
+        const int r = tid & (kAbM - 1), hf = tid >> 7;  // tile row; which 8 of a stage's 16 K
+        const int rowbytes = g.ldi * 12;                // a multiple of 16
+        auto stage_row = [&](int u, int buf) {          // asynchronous copy of X row u % Db
+            const uint8_t *src = reinterpret_cast<const uint8_t *>(g.Xi) + (size_t)(u % g.Db) * rowbytes;
+            uint8_t *dst = reinterpret_cast<uint8_t *>(xrow) + (size_t)buf * rowbytes;
+            for (int i = tid * 16; i < rowbytes; i += kAbBuild * 16)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst + i)), "l"(src + i) : "memory");
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        int cur_tile = -1, it = 0, gch = 0;
+        int Ia = 0;
+        bool valid = false;
+        int prev_bp = 0, prev_Ia = 0;
+        bool prev_valid = false;
+        bool failed = false;
+        // drain the accumulator of unit `iu` (row bp, this thread's alpha string) into H
+        auto epilogue = [&](int iu, int bp, int ia, bool ok_row) -> bool {
+            const int t = iu & 1;
+            bool bad = false;
+            if (tid == 0) {
+                if (!ab_wait(su32(&accf[t]), (uint32_t)((iu >> 1) & 1))) s_fail = 1;
+                bad = s_fail != 0;
+            }
+            if (builders_any(bad)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int quarter = warp & 3;
+            // plane = hf for complex; for real states the two halves split the columns
+            const int plane = P == 2 ? hf : 0;
+            const int c0 = P == 2 ? 0 : hf * (ncolsP / 2), c1 = P == 2 ? g.ncols : min(g.ncols, (hf + 1) * (ncolsP / 2));
+            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * 2 * kAbMaxN + plane * kAbMaxN);
+            float *Hp = g.H + (size_t)plane * g.hplane + (size_t)bp * g.ncols * g.Da + ia;
+            for (int c = c0 & ~7; c < c1; c += 8) {
+                uint32_t v[8];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                               "=r"(v[7])
+                             : "r"(tbase + (uint32_t)c)
+                             : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (ok_row) {
+                    #pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (c + j >= c0 && c + j < c1) Hp[(size_t)(c + j) * g.Da] = __uint_as_float(v[j]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            ab_arrive(su32(&acce[t]));
+            return true;
+        };
+        stage_row(blockIdx.x, 0);
+        for (int u = blockIdx.x; u < g.units; u += gridDim.x, ++it) {
+            const int atile = u / g.Db, bp = u - atile * g.Db, buf = it & 1;
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            // this unit's row has landed; every builder is done with the previous unit
+            if (builders_any(tid == 0 && s_fail)) { failed = true; break; }
+            if (u + (int)gridDim.x < g.units) stage_row(u + gridDim.x, buf ^ 1);
+            if (atile != cur_tile) {
+                // the tile's table: per row and kappa, partner rank (12 bits) | sign << 12 |
+                // nonzero << 13 (this thread: half hf of the row's entries)
+                cur_tile = atile;
+                Ia = atile * kAbM + r;
+                valid = Ia < g.Da;
+                const uint32_t a = valid ? g.stra[Ia] : 0u;
+                const int half = tstride / 2;
+                for (int k = hf * half; k < (hf + 1) * half; ++k) {
+                    uint32_t e = 0;
+                    if (valid && k < Ktot) {
+                        const int p = s_kp[k], q = s_kq[k];
+                        if (p == q) {
+                            if ((a >> p) & 1u) e = (uint32_t)Ia | (1u << 13);
+                        } else if (((a >> p) ^ (a >> q)) & 1u) {
+                            const uint32_t ap = a ^ (1u << p) ^ (1u << q);
+                            e = (uint32_t)g.ra[ap] | ((uint32_t)ab_par(a & ab_between(p, q)) << 12) | (1u << 13);
+                        }
+                    }
+                    tbl[r * tstride + k] = (uint16_t)e;
+                }
+            }
+            if (tid < kAbMaxN) {  // the unit's B rows: b''s excitations s (occupied) -> r (empty), own, zero
+                const uint32_t bs = g.strb[bp];
+                const int nbs = g.nb * (N - g.nb);
+                int row = N * N + g.Db;  // the zero row
+                if (tid < nbs) {
+                    const int i = tid / (N - g.nb), j = tid - i * (N - g.nb);
+                    uint32_t o = bs, z = ~bs & g.maskN;
+                    for (int k = 0; k < i; ++k) o &= o - 1u;
+                    for (int k = 0; k < j; ++k) z &= z - 1u;
+                    row = (__ffs(o) - 1) * N + (__ffs(z) - 1);
+                } else if (tid == nbs) {
+                    row = N * N + bp;
+                }
+                s_rowB[tid] = row;
+            }
+            builders_sync();
+            const uint32_t *xr = xrow + (size_t)buf * g.ldi * 3;
+            const uint16_t *trow = tbl + r * tstride + hf * 8;
+            for (int c = 0; c < g.nK; ++c, ++gch) {
+                const int s = gch % kAbS;
+                // B rows of this K block into registers (ncolsP rows x 2 core columns x 3 pieces)
+                uint4 bv[2];
+                int bi[2];
+                #pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int i = tid + k * kAbBuild;  // < ncolsP * 2 * 3
+                    bi[k] = i < ncolsP * 6 ? i : -1;
+                    if (bi[k] >= 0) {
+                        const int piece = i / (ncolsP * 2), rem = i - piece * ncolsP * 2, row = rem >> 1,
+                                  kc = rem & 1;
+                        const uint16_t *src = g.Bp + (size_t)piece * g.pb + (size_t)s_rowB[row] * 256 + c * kAbKc + kc * 8;
+                        bv[k] = *reinterpret_cast<const uint4 *>(src);
+                    }
+                }
+                // this thread's 8 K entries of row r: three words each (pieces 1..3, re | im << 16)
+                uint32_t w[8][3];
+                {
+                    const uint4 tv = *reinterpret_cast<const uint4 *>(trow + c * kAbKc);
+                    const uint32_t te[4] = {tv.x, tv.y, tv.z, tv.w};
+                    #pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const uint32_t e = (te[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+                        const uint32_t flip = (e & (1u << 12)) ? 0x80008000u : 0u;
+                        if (e & (1u << 13)) {
+                            const uint32_t *x = xr + (e & 0xFFFu) * 3;
+                            w[k][0] = x[0] ^ flip;
+                            w[k][1] = x[1] ^ flip;
+                            w[k][2] = x[2] ^ flip;
+                        } else {
+                            w[k][0] = w[k][1] = w[k][2] = 0u;
+                        }
+                    }
+                }
+                if (gch >= kAbS) {
+                    bool bad = false;
+                    if (tid == 0) {
+                        if (!ab_wait(su32(&empty[s]), (uint32_t)(((gch / kAbS) - 1) & 1))) s_fail = 1;
+                        bad = s_fail != 0;
+                    }
+                    if (builders_any(bad)) { failed = true; break; }
+                }
+                uint8_t *st = ring + s * kStageBytes;
+                #pragma unroll
+                for (int pl = 0; pl < P; ++pl) {
+                    const uint32_t sel = pl ? 0x7632u : 0x5410u;  // the im or the re halves of two words
+                    #pragma unroll
+                    for (int pc = 0; pc < 3; ++pc)
+                        *reinterpret_cast<uint4 *>(st + (pl * 3 + pc) * kAbABytes + ab_off(r, hf)) =
+                            make_uint4(__byte_perm(w[0][pc], w[1][pc], sel), __byte_perm(w[2][pc], w[3][pc], sel),
+                                       __byte_perm(w[4][pc], w[5][pc], sel), __byte_perm(w[6][pc], w[7][pc], sel));
+                }
+                #pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (bi[k] >= 0) {
+                        const int i = bi[k], piece = i / (ncolsP * 2), rem = i - piece * ncolsP * 2, row = rem >> 1,
+                                  kc = rem & 1;
+                        *reinterpret_cast<uint4 *>(st + Ac + piece * (ncolsP * kAbKc * 2) + ab_off(row, kc)) = bv[k];
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                ab_arrive(su32(&full[s]));
+            }
+            if (failed) break;
+            if (it >= 1 && !epilogue(it - 1, prev_bp, prev_Ia, prev_valid)) { failed = true; break; }
+            prev_bp = bp;
+            prev_Ia = Ia;
+            prev_valid = valid;
+        }
+        if (!failed && it >= 1 && !epilogue(it - 1, prev_bp, prev_Ia, prev_valid)) failed = true;
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (tid == kAbBuild) {
+        // ------------------------------------------------------------ MMA issuer
+        // kind::f16, D float32, A and B bf16, both K-major, N = ncolsP, M = 128
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ncolsP >> 3) << 17) |
+                               ((uint32_t)(kAbM >> 4) << 24);
+        const int pa[6] = {0, 0, 1, 0, 1, 2}, pbk[6] = {0, 1, 0, 2, 1, 0};
+        int gch = 0, it = 0;
+        bool stop = false;
+        for (int u = blockIdx.x; u < g.units && !stop; u += gridDim.x, ++it) {
+            const int t = it & 1;
+            if (it >= 2 && !ab_wait(su32(&acce[t]), (uint32_t)(((it >> 1) - 1) & 1))) { s_fail = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int c = 0; c < g.nK; ++c, ++gch) {
+                const int s = gch % kAbS;
+                if (!ab_wait(su32(&full[s]), (uint32_t)((gch / kAbS) & 1)) || s_fail) {
+                    s_fail = 1;
+                    stop = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t base = sbase + (uint32_t)(s * kStageBytes);
+                #pragma unroll
+                for (int pl = 0; pl < P; ++pl) {
+                    const uint32_t d = tmem + (uint32_t)(t * 2 * kAbMaxN + pl * kAbMaxN);
+                    #pragma unroll
+                    for (int x = 0; x < 6; ++x) {
+                        const uint64_t da = ab_desc(base + (uint32_t)((pl * 3 + pa[x]) * kAbABytes));
+                        const uint64_t db = ab_desc(base + (uint32_t)(Ac + pbk[x] * ncolsP * kAbKc * 2));
+                        const uint32_t acc = (c > 0 || x > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}\n" ::"r"(d),
+                            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
+                }
+                ab_commit(su32(&empty[s]));
+            }
+            if (!stop) ab_commit(su32(&accf[t]));
+        }
+        ab_commit(su32(&done));  // every MMA issued above has completed when `done` does
+    }
+    __syncwarp();
+    const bool ok = ab_wait(su32(&done), 0u);
+    if (!ok) s_fail = 1;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && s_fail) atomicExch(g.err, 1);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+}
+
+namespace {
+
+// B table rows (K index kappa as in k_ab_tc: p = q = kappa below N, then the pairs
+// p < q): t = s N + r (t < N^2): B[t][kappa] = (qp|sr) = eri[(q N + p) N^2 + t];
+// N^2 + b': sum_{l in b'} (qp|ll) for p != q (Jt[(q N + p) N + l]), 0 for p = q;
+// N^2 + Db: zeros.  Written as three bf16 pieces; rows of 256.
+__global__ void __launch_bounds__(256) k_ab_table(const float *__restrict__ eri, const float *__restrict__ Jt,
+                                                  const uint16_t *__restrict__ strb, int N, int Db,
+                                                  uint16_t *__restrict__ Bp, size_t pb) {
+    const int row = blockIdx.x, kap = threadIdx.x, NN = N * N, Ktot = N * (N + 1) / 2;
+    float v = 0.f;
+    if (kap < Ktot) {
+        int p = 0, q = 0;
+        if (kap < N) {
+            p = q = kap;
+        } else {
+            int pi = kap - N;
+            while (pi >= N - 1 - p) { pi -= N - 1 - p; ++p; }
+            q = p + 1 + pi;
+        }
+        if (row < NN) {
+            v = eri[(size_t)(q * N + p) * NN + row];
+        } else if (row < NN + Db && p != q) {
+            for (uint32_t o = strb[row - NN]; o; o &= o - 1u) v += Jt[(size_t)(q * N + p) * N + __ffs(o) - 1];
+        }
+    }
+    uint32_t a1, a2, a3;
+    split3(v, a1, a2, a3);
+    const size_t at = (size_t)row * 256 + kap;
+    Bp[at] = (uint16_t)a1;
+    Bp[pb + at] = (uint16_t)a2;
+    Bp[2 * pb + at] = (uint16_t)a3;
+}
+
+size_t ab_tc_smem(int Da, int N) {
+    const size_t stage = 2 * 3 * kAbABytes + 3 * kAbMaxN * kAbKc * 2;
+    const int nK = (N * (N + 1) / 2 + kAbKc - 1) / kAbKc;
+    const size_t ldi = ((size_t)Da + 3) / 4 * 4;
+    return 1024 + kAbS * stage + 2 * ldi * 12 + (size_t)kAbM * ab_tstride(nK) * 2;
+}
+
+}  // namespace
+
+// Rows of the B table (and its piece stride): N^2 + Db + 1 rows of 256.
+size_t ab_table_rows(int N, int Db) { return (size_t)N * N + Db + 1; }
+
+cudaError_t launch_ab_table(const float *eri, const float *Jt, const uint16_t *strb, int N, int Db, uint16_t *Bp,
+                            size_t pb, cudaStream_t st) {
+    if (N * N > 256) return cudaErrorInvalidValue;
+    k_ab_table<<<(unsigned)ab_table_rows(N, Db), 256, 0, st>>>(eri, Jt, strb, N, Db, Bp, pb);
+    return cudaGetLastError();
+}
+
+// Whether the tensor-core alpha-beta form applies: N <= 16, D <= 4096 per spin, at most
+// 80 columns, and its shared memory fits.
+bool ab_tc_fits(int planes, int Da, int Db, int na, int nb, int N) {
+    (void)planes;
+    (void)na;
+    if (N > 16 || N < 1 || Da > 4096 || Db > 4096 || Da < 1 || Db < 1) return false;
+    if (nb * (N - nb) + 1 > kAbMaxN) return false;
+    return ab_tc_smem(Da, N) <= 227 * 1024 - 1024;
+}
+
+// Row stride (amplitudes) of the interleaved X pieces the kernel reads.
+int ab_xi_ld(int Da) { return (Da + 3) / 4 * 4; }
+
+// H = the per-partner-row products (see above); Xi [Db][ab_xi_ld(Da)][3] the phased
+// amplitudes as bf16 pieces (phase kernel); Bp the B table pieces; H planes
+// [planes][Db][ncols][Da] (hplane elements apart).
+cudaError_t launch_ab_tc(const uint32_t *Xi, int planes, const uint16_t *stra, const uint16_t *strb,
+                         const uint16_t *ra, const uint16_t *Bp, size_t pb, float *H, size_t hplane, int Da, int Db,
+                         int N, int na, int nb, int *err, int sm_count, cudaStream_t st) {
+    if (!ab_tc_fits(planes, Da, Db, na, nb, N) || ((uintptr_t)Xi & 15) || ((uintptr_t)Bp & 15) || (pb & 7))
+        return cudaErrorInvalidValue;
+    AbTcArgs g;
+    g.Xi = Xi; g.ldi = ab_xi_ld(Da); g.stra = stra; g.strb = strb; g.ra = ra; g.Bp = Bp; g.pb = pb; g.H = H;
+    g.hplane = hplane; g.Da = Da; g.Db = Db; g.N = N; g.na = na; g.nb = nb;
+    g.ncols = nb * (N - nb) + 1;
+    g.nK = (N * (N + 1) / 2 + kAbKc - 1) / kAbKc;
+    g.units = ((Da + kAbM - 1) / kAbM) * Db;
+    g.maskN = (1u << N) - 1u;
+    g.err = err;
+    const int grid = g.units < sm_count ? g.units : sm_count;
+    const size_t sm = ab_tc_smem(Da, N);
+    cudaError_t e;
+    if (planes == 2) {
+        e = cudaFuncSetAttribute(k_ab_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_ab_tc<2><<<grid, kAbThreadsTc, sm, st>>>(g);
+    } else {
+        e = cudaFuncSetAttribute(k_ab_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_ab_tc<1><<<grid, kAbThreadsTc, sm, st>>>(g);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace svk

@@ -772,12 +772,23 @@ __device__ __forceinline__ void bf16x3(float v, uint16_t *p, size_t piece) {
 }
 
 // With Xp (tensor-core form) the planes are written as three bf16 pieces at stride px
-// instead of float32 X.
+// instead of float32 X.  With Xi (variant 5) also, per amplitude, the three words
+// (re_k | im_k << 16), k = 1..3, at Xi[(Ib ldi + Ia) 3 + k - 1].
+__device__ __forceinline__ void bf16x3_u(float v, uint32_t &p1, uint32_t &p2, uint32_t &p3) {
+    const __nv_bfloat16 a = __float2bfloat16_rn(v);
+    const float r = v - __bfloat162float(a);
+    const __nv_bfloat16 b = __float2bfloat16_rn(r);
+    const __nv_bfloat16 c = __float2bfloat16_rn(r - __bfloat162float(b));
+    p1 = __bfloat16_as_ushort(a);
+    p2 = __bfloat16_as_ushort(b);
+    p3 = __bfloat16_as_ushort(c);
+}
+
 template <typename Amp>
 __global__ void __launch_bounds__(kThreads) k_phase_planar(const Amp *__restrict__ C, const uint16_t *__restrict__ stra,
                                                            const uint16_t *__restrict__ strb, int Da, int Db,
                                                            float *__restrict__ X, int ld, uint16_t *__restrict__ Xp,
-                                                           size_t px) {
+                                                           size_t px, uint32_t *__restrict__ Xi, int ldi) {
     const size_t plane = (size_t)ld * Db;  // rows padded to ld (the padding stays zero)
     for (int Ib = blockIdx.x; Ib < Db; Ib += gridDim.x) {
         const uint32_t ppb = prefix_parity(strb[Ib]);
@@ -788,10 +799,20 @@ __global__ void __launch_bounds__(kThreads) k_phase_planar(const Amp *__restrict
             const float xr = flip_sign<float>(re(c), neg);
             if (Xp) bf16x3(xr, Xp + xo + Ia, px);
             else X[xo + Ia] = xr;
+            float xi = 0.f;
             if constexpr (AmpT<Amp>::kCplx) {
-                const float xi = flip_sign<float>(im(c), neg);
+                xi = flip_sign<float>(im(c), neg);
                 if (Xp) bf16x3(xi, Xp + plane + xo + Ia, px);
                 else X[plane + xo + Ia] = xi;
+            }
+            if (Xi) {
+                uint32_t r1, r2, r3, i1, i2, i3;
+                bf16x3_u(xr, r1, r2, r3);
+                bf16x3_u(xi, i1, i2, i3);
+                uint32_t *w = Xi + ((size_t)Ib * ldi + Ia) * 3;
+                w[0] = r1 | (i1 << 16);
+                w[1] = r2 | (i2 << 16);
+                w[2] = r3 | (i3 << 16);
             }
         }
     }
@@ -801,14 +822,43 @@ __global__ void __launch_bounds__(kThreads) k_phase_planar(const Amp *__restrict
 // + phi(a, b) G[b][a], with the diagonal d = E_nuc - c + dA[a] + dB[b] + sum over
 // alpha orbitals p in a of sum over beta orbitals q in b of [2p | 2q+1] (float64);
 // the row's energy and norm as in k_sigma_same (fixed-order float64 sums).
-template <typename Amp>
+// GATHER (variant 5): the alpha-beta part is not in the output but in the planes H of
+// the tensor-core products (k_ab_tc); it is gathered here, in the blocked basis, as
+// sum over the beta excitations r -> s of b (partner b') of
+// (-1)^popc(b & between(r, s)) H[b'][col(b', rs)][a], plus H[b][own][a], in a fixed
+// order, and added to G before the phase; the output is written, not added to.
+template <typename Amp, bool GATHER>
 __global__ void __launch_bounds__(kThreads) k_sigma_comb(RowArgs<Amp> A, SameGemm g) {
     using R = real_of<Amp>;
     __shared__ double xb[kMaxOrb];
     __shared__ double red[2 * kThreads / 32];
+    __shared__ size_t s_hoff[kMaxBS];
+    __shared__ int s_hneg[kMaxBS];
     const SigmaTables<R> &T = A.T;
     const int Ib = blockIdx.x, Da = T.Da, N = T.N;
     const uint32_t b = T.strb[Ib], ppb = prefix_parity(b);
+    int nh = 0;
+    if constexpr (GATHER) {
+        // H rows to gather: entry j = (r, s) in the order of b's occupied r, empty s; the
+        // last one the row's own column
+        const int nb = __popc(b), ne = N - nb, nbs = nb * ne;
+        nh = nbs + 1;
+        if ((int)threadIdx.x < nbs) {
+            const int i = threadIdx.x / ne, j = threadIdx.x - i * ne;
+            uint32_t o = b, z = ~b & T.maskN;
+            for (int k = 0; k < i; ++k) o &= o - 1u;
+            for (int k = 0; k < j; ++k) z &= z - 1u;
+            const int r = __ffs(o) - 1, sx = __ffs(z) - 1;
+            const uint32_t bp = b ^ (1u << r) ^ (1u << sx);
+            // column of (s occupied, r empty) among b''s excitations
+            const int col = __popc(bp & ((1u << sx) - 1u)) * ne + __popc(~bp & T.maskN & ((1u << r) - 1u));
+            s_hoff[threadIdx.x] = ((size_t)T.rb[bp] * g.ncols + col) * Da;
+            s_hneg[threadIdx.x] = par(b & between(r, sx));
+        } else if ((int)threadIdx.x == nbs) {
+            s_hoff[nbs] = ((size_t)Ib * g.ncols + nbs) * Da;
+            s_hneg[nbs] = 0;
+        }
+    }
     if ((int)threadIdx.x < N) {
         const int k = 2 * (int)threadIdx.x;
         double sx = 0.0;
@@ -827,15 +877,29 @@ __global__ void __launch_bounds__(kThreads) k_sigma_comb(RowArgs<Amp> A, SameGem
         double d = db + g.dA[Ia];
         for (uint32_t o = a; o; o &= o - 1u) d += xb[__ffs(o) - 1];
         const Amp c0 = A.C[off + Ia];
+        float gr = g.G[off + Ia], gi = 0.f;
+        if constexpr (AmpT<Amp>::kCplx) gi = g.G[plane + off + Ia];
+        if constexpr (GATHER) {
+            for (int j = 0; j < nh; ++j) {
+                const float *hp = g.H + s_hoff[j] + Ia;
+                float hr = hp[0], hi = 0.f;
+                if constexpr (AmpT<Amp>::kCplx) hi = hp[g.hplane];
+                if (s_hneg[j]) { hr = -hr; hi = -hi; }
+                gr += hr;
+                gi += hi;
+            }
+        }
         Amp acc;
         if constexpr (AmpT<Amp>::kCplx)
-            acc = mka<Amp>(fmaf((R)d, re(c0), flip_sign<float>(g.G[off + Ia], neg)),
-                           fmaf((R)d, im(c0), flip_sign<float>(g.G[plane + off + Ia], neg)));
+            acc = mka<Amp>(fmaf((R)d, re(c0), flip_sign<float>(gr, neg)), fmaf((R)d, im(c0), flip_sign<float>(gi, neg)));
         else
-            acc = mka<Amp>(fmaf((R)d, re(c0), flip_sign<float>(g.G[off + Ia], neg)), (R)0);
+            acc = mka<Amp>(fmaf((R)d, re(c0), flip_sign<float>(gr, neg)), (R)0);
         e_acc += dre_dot(c0, acc);
         n_acc += dre_dot(c0, c0);
-        if (A.lam) {
+        if (GATHER) {
+            if (A.lam) A.lam[A.sa_s[Ia] | A.sb_s[Ib]] = acc;
+            else if (A.lamc) A.lamc[off + Ia] = acc;
+        } else if (A.lam) {
             const Amp u = A.lam[A.sa_s[Ia] | A.sb_s[Ib]];
             A.lam[A.sa_s[Ia] | A.sb_s[Ib]] = add_a<Amp>(acc, u);
         } else if (A.lamc) {
@@ -845,7 +909,7 @@ __global__ void __launch_bounds__(kThreads) k_sigma_comb(RowArgs<Amp> A, SameGem
     }
     block_sum2(e_acc, n_acc, red);
     if (threadIdx.x == 0) {
-        A.partial[Ib] = e_acc + A.partial[2 * A.Db + Ib];
+        A.partial[Ib] = GATHER ? e_acc : e_acc + A.partial[2 * A.Db + Ib];
         A.partial[A.Db + Ib] = n_acc;
     }
 }
@@ -984,6 +1048,9 @@ static cudaError_t launch_ab_k(const RowArgs<double> &A, int K, size_t smem, cud
 
 cudaError_t launch_same_tc(const uint16_t *M, size_t pm, const uint16_t *X, size_t px, uint16_t *Xt, size_t pt,
                            float *G, int planes, int Da, int Db, int lda, int ldb, int *err, cudaStream_t st);
+cudaError_t launch_ab_tc(const uint32_t *Xi, int planes, const uint16_t *stra, const uint16_t *strb,
+                         const uint16_t *ra, const uint16_t *Bp, size_t pb, float *H, size_t hplane, int Da, int Db,
+                         int N, int na, int nb, int *err, int sm_count, cudaStream_t st);
 
 // G = Ma X + X Mb^T on every plane (column-major views: X and G are Da x (planes Db),
 // Ma is Da x Da, Mb Db x Db; both symmetric).
@@ -1009,7 +1076,7 @@ static cudaError_t launch_same_t(RowArgs<Amp> A, const RowTables &T, int dtype, 
     } else {
         const int grid = T.Db < sm_count * 8 ? T.Db : sm_count * 8;
         k_phase_planar<Amp><<<grid, kThreads, 0, st>>>(A.C, T.stra, T.strb, T.Da, T.Db, g.X, g.lda,
-                                                       g.tc ? g.Xp : nullptr, g.px);
+                                                       g.tc ? g.Xp : nullptr, g.px, g.abtc ? g.Xi : nullptr, g.ldi);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = g.tc ? launch_same_tc(g.Mp, g.pm, g.Xp, g.px, g.Xtp, g.pt, g.G, g.planes, T.Da, T.Db, g.lda, g.ldb, g.err,
@@ -1017,9 +1084,16 @@ static cudaError_t launch_same_t(RowArgs<Amp> A, const RowTables &T, int dtype, 
                  : same_products(g, T.Da, T.Db);
         if (e != cudaSuccess) return e;
         A.same_gemm = 1;
-        e = launch_ab_k(A, K, ab_smem(dtype, K, T), st);
-        if (e != cudaSuccess) return e;
-        k_sigma_comb<Amp><<<T.Db, kThreads, 0, st>>>(A, g);
+        if (g.abtc) {
+            e = launch_ab_tc(g.Xi, g.planes, T.stra, T.strb, T.ra, g.Bp, g.pb, g.H, g.hplane, T.Da, T.Db, T.N, g.na,
+                             g.nb, g.err, sm_count, st);
+            if (e != cudaSuccess) return e;
+            k_sigma_comb<Amp, true><<<T.Db, kThreads, 0, st>>>(A, g);
+        } else {
+            e = launch_ab_k(A, K, ab_smem(dtype, K, T), st);
+            if (e != cudaSuccess) return e;
+            k_sigma_comb<Amp, false><<<T.Db, kThreads, 0, st>>>(A, g);
+        }
         return cudaGetLastError();
     }
 }

@@ -78,6 +78,11 @@ cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, i
 cudaError_t launch_same_mats(int n, const RowTables &T, const double *hdiag, const double *Jp, float *Ma, float *Mb,
                              double *dA, double *dB, int lda, int ldb, cudaStream_t st);
 cudaError_t launch_split_bf16x3(const float *x, uint16_t *out, size_t n, size_t piece, int sm_count, cudaStream_t st);
+size_t ab_table_rows(int N, int Db);
+cudaError_t launch_ab_table(const float *eri, const float *Jt, const uint16_t *strb, int N, int Db, uint16_t *Bp,
+                            size_t pb, cudaStream_t st);
+bool ab_tc_fits(int planes, int Da, int Db, int na, int nb, int N);
+int ab_xi_ld(int Da);
 int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want);
 const int *sigma_ab_sizes(int dtype);
 
@@ -631,7 +636,7 @@ static int row_chunk(sv_handle h, const RowTables &R) {
 // products do at most 20 times the multiplies of the sparse sums.
 static bool use_same_gemm(sv_handle h, int K) {
     if (!single_prec(h->dtype) || K == 0 || h->Da > 4096 || h->Db > 4096) return false;
-    if (h->expect_variant == 4) return true;
+    if (h->expect_variant == 4 || h->expect_variant == 5) return true;
     if (h->expect_variant != 0) return false;
     const int N = h->n / 2;
     auto c2 = [](long x) { return x * (x - 1) / 2; };
@@ -640,6 +645,13 @@ static bool use_same_gemm(sv_handle h, int K) {
         return (double)(ns + nd) / (double)D;
     };
     return (double)h->Da * h->Db >= (double)(1 << 20) && dens(h->na, h->Da) >= 0.05 && dens(h->nb, h->Db) >= 0.05;
+}
+
+// Whether the same-spin product form also takes the alpha-beta part as tensor-core
+// products (variant 5; where k_ab_tc's limits hold, else variant 4).
+static bool use_ab_tc(sv_handle h) {
+    if (h->expect_variant != 5) return false;
+    return ab_tc_fits(is_complex(h->dtype) ? 2 : 1, h->Da, h->Db, h->na, h->nb, h->n / 2);
 }
 
 // The same-spin matrices of the table set and sector (built on first use, kept until
@@ -679,8 +691,12 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
     }
     const size_t Da = (size_t)h->Da, Db = (size_t)h->Db, lda = (Da + 7) / 8 * 8, ldb = (Db + 7) / 8 * 8;
     // [Ma | Mb] (float32), the one-spin diagonals, then the three bf16 pieces of [Ma | Mb]
+    // then the three bf16 pieces of the alpha-beta integral table (k_ab_tc) when N^2 <= 256
+    const int N = h->n / 2;
+    const size_t rowsB = N * N <= 256 ? ab_table_rows(N, (int)Db) : 0, pbB = rowsB * 256;
     const size_t nm = Da * lda + Db * ldb, mf = nm * sizeof(float), dof = (mf + 255) / 256 * 256,
-                 sof = (dof + (Da + Db) * sizeof(double) + 255) / 256 * 256, mb = sof + 3 * nm * sizeof(uint16_t);
+                 sof = (dof + (Da + Db) * sizeof(double) + 255) / 256 * 256,
+                 bof = (sof + 3 * nm * sizeof(uint16_t) + 255) / 256 * 256, mb = bof + 3 * pbB * sizeof(uint16_t);
     float *Ma = nullptr;
     if (!h->sg_mats || h->sg_serial != T->serial || h->sg_na != h->na || h->sg_nb != h->nb) {
         if (h->sg_mats_bytes < mb) {
@@ -697,6 +713,11 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
         SV_CUDA(h, launch_split_bf16x3(Ma, (uint16_t *)((uint8_t *)h->sg_mats + sof), nm, nm, h->sm_count,
                                        h->stream));
         h->launches += 2;
+        if (rowsB) {
+            SV_CUDA(h, launch_ab_table((const float *)R.eri, (const float *)R.Jt, h->str_b, N, (int)Db,
+                                       (uint16_t *)((uint8_t *)h->sg_mats + bof), pbB, h->stream));
+            h->launches += 1;
+        }
         h->sg_serial = T->serial;
         h->sg_na = h->na;
         h->sg_nb = h->nb;
@@ -711,8 +732,12 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
     auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t xb = tc ? r256(3 * nx * sizeof(uint16_t)) : r256(nx * sizeof(float)),
                  tb = tc ? r256(3 * nt * sizeof(uint16_t)) : 0;
-    const size_t need = xb + tb + ng * sizeof(float);
-    const uint64_t geom = ((uint64_t)Da << 32) | ((uint64_t)Db << 2) | ((uint64_t)planes << 1) | (tc ? 1u : 0u);
+    // variant 5: then the phased amplitudes as interleaved bf16 pieces [Db][ldi][3] words
+    const bool abtc = use_ab_tc(h) && rowsB;
+    const size_t ldi = ab_xi_ld((int)Da), gb = r256(ng * sizeof(float)), ib = abtc ? r256(Db * ldi * 12) : 0;
+    const size_t need = xb + tb + gb + ib;
+    const uint64_t geom = ((uint64_t)Da << 32) | ((uint64_t)Db << 3) | ((uint64_t)planes << 2) | (abtc ? 2u : 0u) |
+                          (tc ? 1u : 0u);
     if (h->sg_buf_bytes < need || h->sg_buf_geom != geom) {
         if (h->sg_buf_bytes < need) {
             dev_free(h, h->sg_buf, h->sg_buf_bytes);
@@ -743,6 +768,42 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
     g->ldb = (int)ldb;
     g->tc = tc ? 1 : 0;
     g->err = h->kerr;
+    g->abtc = 0;
+    if (abtc) {
+        // H [planes][Db][ncols][Da]
+        const int ncols = h->nb * (N - h->nb) + 1;
+        const size_t hplane = Db * (size_t)ncols * Da, hb = (size_t)planes * hplane * sizeof(float);
+        if (h->ab_H_bytes < hb) {
+            dev_free(h, h->ab_H, h->ab_H_bytes);
+            h->ab_H = nullptr;
+            h->ab_H_bytes = 0;
+            SV_TRY(dev_alloc(h, (void **)&h->ab_H, hb, "alpha-beta product planes"));
+            h->ab_H_bytes = hb;
+        }
+        if (!h->kerr) {
+            SV_TRY(dev_alloc(h, (void **)&h->kerr, 16, "kernel error flag"));
+            SV_CUDA(h, cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream));
+        }
+        if (!h->hkerr) {
+            if (cudaMallocHost((void **)&h->hkerr, sizeof(int)) != cudaSuccess) {
+                cudaGetLastError();
+                h->hkerr = nullptr;
+                return fail(h, SV_ERR_OOM, "pinned host allocation failed");
+            }
+            *h->hkerr = 0;
+        }
+        g->abtc = 1;
+        g->Xi = (uint32_t *)(B + xb + tb + gb);
+        g->ldi = (int)ldi;
+        g->Bp = (const uint16_t *)((const uint8_t *)h->sg_mats + bof);
+        g->pb = pbB;
+        g->H = h->ab_H;
+        g->hplane = hplane;
+        g->ncols = ncols;
+        g->na = h->na;
+        g->nb = h->nb;
+        g->err = h->kerr;
+    }
     return SV_OK;
 }
 
@@ -752,7 +813,7 @@ static sv_status check_kernel_flag(sv_handle h) {
         *h->hkerr = 0;
         if (h->kerr) cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream);
         h->failed = true;
-        return fail(h, SV_ERR_CUDA, "same-spin products: a tensor-core wait ran out");
+        return fail(h, SV_ERR_CUDA, "tensor-core products: a bounded wait ran out");
     }
     return SV_OK;
 }
@@ -768,7 +829,8 @@ static sv_status sigma_rows(sv_handle h, DevTables *T, const RowTables &R, const
     SV_CUDA(h, launch_sigma_rows(C, lam, lamc, h->dtype, h->n, R, T->hdiag, T->Jp, e_shift, h->partials, K,
                                  h->stream, sg ? &g : nullptr, h->sm_count));
     h->launches += sg ? (g.tc ? 5 : 3) : (K ? 2 : 1);  // cuBLAS's own kernels are not counted
-    if (sg && g.tc) SV_CUDA(h, cudaMemcpyAsync(h->hkerr, h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if (sg && (g.tc || g.abtc))
+        SV_CUDA(h, cudaMemcpyAsync(h->hkerr, h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     return SV_OK;
 }
 
@@ -1118,6 +1180,7 @@ sv_status sv_destroy(sv_handle h) {
     dev_free(h, h->Lbuf, h->Lbuf_bytes);
     dev_free(h, h->sg_mats, h->sg_mats_bytes);
     dev_free(h, h->sg_buf, h->sg_buf_bytes);
+    dev_free(h, h->ab_H, h->ab_H_bytes);
     dev_free(h, h->kerr, 16);
     if (h->hkerr) cudaFreeHost(h->hkerr);
     dev_free(h, h->blas_ws, h->blas_ws_bytes);
@@ -1710,7 +1773,7 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
             h->max_bytes = value;
             return SV_OK;
         case SV_OPT_EXPECT_VARIANT:
-            if (value < 0 || value > 4) return fail(h, SV_ERR_ARG, "expect variant must be 0, 1, 2, 3 or 4");
+            if (value < 0 || value > 5) return fail(h, SV_ERR_ARG, "expect variant must be 0 to 5");
             h->expect_variant = (int)value;
             return SV_OK;
         case SV_OPT_RDM_VARIANT:

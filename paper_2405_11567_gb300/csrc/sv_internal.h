@@ -130,7 +130,18 @@ struct SameGemm {
     int planes = 2;                            // 2 complex (re, im), 1 real
     int lda = 0, ldb = 0;                      // row strides of Ma / X and Mb / Xt: D rounded up to 4, zero padded
     int tc = 0;                                // 1: the products on the tensor cores (k_same_tc), 0: cuBLAS float32
-    int *err = nullptr;                        // device flag set by k_same_tc when a wait runs out
+    int *err = nullptr;                        // device flag set by k_same_tc / k_ab_tc when a wait runs out
+    // variant 5: the alpha-beta part on the tensor cores (k_ab_tc) into planes H
+    // [planes][Db][ncols][Da] (hplane floats apart), gathered by k_sigma_comb; Bp: the
+    // bf16 pieces [3][N^2 + Db + 1][256] of its integral table (piece stride pb)
+    int abtc = 0;
+    uint32_t *Xi = nullptr;                    // phased amplitudes as interleaved bf16 pieces [Db][ldi][3]
+    int ldi = 0;
+    const uint16_t *Bp = nullptr;
+    size_t pb = 0;
+    float *H = nullptr;
+    size_t hplane = 0;
+    int ncols = 0, na = 0, nb = 0;
 };
 
 struct DevTables {
@@ -262,8 +273,8 @@ struct sv_ctx {
     int rdm_variant = 0;
     int pool_variant = 0;      // 0 auto (= 2); 1 string scan; 2 pair lists
     int l2_fetch = 32;         // context L2 fetch granularity set before dense sweeps (0: leave it)
-    int same_products = 0;     // variant 4's products: 0 auto (= 2), 1 cuBLAS float32, 2 tensor cores (3xTF32)
-    int *kerr = nullptr;       // device flag of kernels with bounded waits (k_same_tc)
+    int same_products = 0;     // variant 4's products: 0 auto (= 2), 1 cuBLAS float32, 2 tensor cores (bf16x3)
+    int *kerr = nullptr;       // device flag of kernels with bounded waits (k_same_tc, k_ab_tc)
     int *hkerr = nullptr;      // its pinned host copy, checked after stream synchronisations
     // same-spin products (expectation variant 4): matrices for one table set and sector,
     // the phased-psi / product planes, and the cuBLAS handle with its workspace
@@ -274,6 +285,8 @@ struct sv_ctx {
     void *sg_buf = nullptr;
     size_t sg_buf_bytes = 0;
     uint64_t sg_buf_geom = 0;  // the planes' geometry (their row padding is zeroed when it changes)
+    float *ab_H = nullptr;     // variant 5: the alpha-beta product planes
+    size_t ab_H_bytes = 0;
     void *blas = nullptr;
     void *blas_ws = nullptr;
     size_t blas_ws_bytes = 0;

@@ -323,11 +323,12 @@ def test_errors_are_reported_not_raised_on_device():
     assert np.isfinite(st.energy(ham))
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_expectation_variants_match_oracle(variant, dtype):
-    """Record scan (1), string rows in one kernel (2), split (3) and split with same-spin
-    products (4) on an open-shell complex state and on config 2."""
+    """Record scan (1), string rows in one kernel (2), split (3), split with same-spin
+    products (4) and with the alpha-beta part as tensor-core products too (5; complex128
+    keeps 3) on an open-shell complex state and on config 2."""
     n, na, nb = 12, 3, 2
     p = inputs.make_problem(n, 4, 30, seed=88)
     rng = np.random.default_rng(11)

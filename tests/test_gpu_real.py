@@ -24,7 +24,7 @@ def _state(n, na, nb, dtype, storage):
     return sv.StateVector(n, dtype, sector=None if storage == "dense" else (na, nb))
 
 
-@pytest.mark.parametrize("variant", [0, 4])
+@pytest.mark.parametrize("variant", [0, 4, 5])
 @pytest.mark.parametrize("storage", ["dense", "sector"])
 @pytest.mark.parametrize("dtype", ["r64", "r32"])
 def test_energy_grad_rdm_state(dtype, storage, variant):
@@ -36,7 +36,7 @@ def test_energy_grad_rdm_state(dtype, storage, variant):
     psi = A.apply_ansatz(sec, p["ops"], theta, psi0)
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
     st = _state(14, 3, 3, dtype, storage)
-    st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)  # 4: same-spin products (float32; float64 keeps 3)
+    st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)  # 4, 5: tensor-core products (float32; float64 keeps 3)
     st.prepare_hf(p["occ"])
     E, g = st.energy_grad(ham, p["ops"], theta)
     t = TOL[dtype]

@@ -178,13 +178,15 @@ def test_pool_gradients_match_oracle(dtype, tol, variant):
     assert np.array_equal(g4, g)
 
 
+@pytest.mark.parametrize("variant", [4, 5])
 @pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("storage", ["sector", "dense"])
-def test_same_spin_products_match_oracle(storage, form):
+def test_same_spin_products_match_oracle(storage, form, variant):
     """Expectation variant 4 (same-spin part as two dense products in the string-blocked
-    basis; form 1 cuBLAS float32, form 2 the tensor-core kernel on bf16x3 operands)
-    on an open-shell complex start: energy, gradient and pool gradients within the
-    complex64 tolerance, and reruns bit-identical."""
+    basis; form 1 cuBLAS float32, form 2 the tensor-core kernel on bf16x3 operands;
+    variant 5 also the alpha-beta part as tensor-core products) on an open-shell complex
+    start: energy, gradient and pool gradients within the complex64 tolerance, and reruns
+    bit-identical."""
     n, na, nb = 16, 3, 4
     p = inputs.make_problem(n, 7, 40, seed=303)
     dense0 = inputs.random_sector_state(n, na, nb, np.random.default_rng(31))
@@ -194,7 +196,7 @@ def test_same_spin_products_match_oracle(storage, form):
     Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
     st = sv.StateVector(n, "c64", sector=(na, nb) if storage == "sector" else None)
-    st.set_option(sv.SV_OPT_EXPECT_VARIANT, 4)
+    st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
     st.set_option(sv.SV_OPT_SAME_PRODUCTS, form)
     runs = []
     for _ in range(2):
@@ -211,12 +213,15 @@ def test_same_spin_products_match_oracle(storage, form):
     assert np.max(np.abs(gp - gp_ref)) <= TOL["c64"]["g"]
 
 
-def test_same_spin_products_several_tiles():
+@pytest.mark.parametrize("variant", [4, 5])
+def test_same_spin_products_several_tiles(variant):
     """The tensor-core same-spin products over several output tiles with ragged edges in
     both directions (D_alpha = 330: three 128-row tiles, the last 74 rows; D_beta = 462:
     two 256-column tiles, the last 206) and K blocks of 32 with a ragged last block, on
     an open-shell complex start: energy and gradient match the oracle within the
-    complex64 tolerance in both product forms, and the forms agree to rounding."""
+    complex64 tolerance in both product forms, and the forms agree to rounding.  Variant
+    5 adds the alpha-beta products over the same three alpha tiles (units of one tile and
+    one partner row: 3 x 462, spread over the SMs with a ragged last round)."""
     n, na, nb = 22, 4, 5
     p = inputs.make_problem(n, 9, 6, seed=404)
     dense0 = inputs.random_sector_state(n, na, nb, np.random.default_rng(5))
@@ -229,7 +234,7 @@ def test_same_spin_products_several_tiles():
     out = {}
     for form in (1, 2):
         st = _state(n, na, nb, "c64")
-        st.set_option(sv.SV_OPT_EXPECT_VARIANT, 4)
+        st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
         st.set_option(sv.SV_OPT_SAME_PRODUCTS, form)
         st.prepare_state(dense0.astype(np.complex64), na, nb)
         E, g = st.energy_grad(ham, p["ops"], theta)
@@ -369,7 +374,7 @@ def test_adapt_vqe_on_sector_storage_reaches_fci():
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("chunk", [1, 2, 3, 4, 6, 8])
-@pytest.mark.parametrize("variant", [2, 3, 4])
+@pytest.mark.parametrize("variant", [2, 3, 4, 5])
 def test_expectation_forms_and_chunks(variant, chunk, dtype):
     """Single-kernel (2), split (3) and split with same-spin products (4; complex64 only,
     complex128 keeps 3) string-row expectation, every partner-row chunk size, on an
@@ -398,7 +403,7 @@ def test_expectation_forms_and_chunks(variant, chunk, dtype):
 
 
 @pytest.mark.parametrize("na,nb", [(0, 3), (4, 0), (5, 2), (1, 5)])
-@pytest.mark.parametrize("variant", [3, 4])
+@pytest.mark.parametrize("variant", [3, 4, 5])
 def test_expectation_degenerate_string_spaces(na, nb, variant):
     """Sectors where one spin has a single string (no electrons, or every orbital filled):
     1 x 1 same-spin matrices, no excitations of that spin, empty pair lists; energy,
