@@ -617,7 +617,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch choices")
     ap.add_argument("--no-real", action="store_true", help="skip the real-amplitude (float32) timing")
     ap.add_argument("--no-pool", action="store_true", help="skip the operator-screening timing")
-    ap.add_argument("--expect-variant", type=int, default=None, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--expect-variant", type=int, default=None, choices=[0, 1, 2, 3, 4, 5],
                     help="profiling: force an expectation form (SV_OPT_EXPECT_VARIANT); use with --no-autotune")
     ap.add_argument("--pool-only", action="store_true",
                     help="profiling: time only the operator screening (no bench line)")

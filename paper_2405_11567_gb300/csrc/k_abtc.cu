@@ -32,8 +32,9 @@
 // matrices of 8 rows x 16 bytes), flipping sign bits and pairing halves only, and copy
 // the unit's B rows (pieces of a precomputed table);
 // lane 0 of warp 8 issues tcgen05.mma kind::f16 (six piece products per plane:
-// float32-level accuracy) into one of two tensor-memory accumulators; after building
-// a unit the builders drain the previous unit's accumulator into H.  Stage ring with
+// float32-level accuracy) into one of two tensor-memory accumulators; four epilogue
+// warps (one per tensor-memory lane quarter) drain each finished accumulator into H
+// while the next unit is built.  Stage ring with full / empty mbarriers, accumulator
 // full / empty mbarriers; all waits bounded (past the limit: *err set, copies and MMAs
 // waited for, tensor memory freed, return).
 #include <cuda_bf16.h>
@@ -46,7 +47,8 @@ namespace svk {
 namespace {
 
 constexpr int kAbBuild = 256;                  // builder threads (8 warps): 2 per tile row
-constexpr int kAbThreadsTc = kAbBuild + 32;    // + the MMA warp
+constexpr int kAbEpi = 128;                    // epilogue threads (4 warps: one per tensor-memory lane quarter)
+constexpr int kAbThreadsTc = kAbBuild + 32 + kAbEpi;  // builders, the MMA warp, the epilogue warps
 constexpr int kAbM = 128;                      // alpha strings per tile
 constexpr int kAbKc = 16;                      // K (orbitals and orbital pairs) per stage
 constexpr int kAbS = 3;                        // stages
@@ -85,14 +87,24 @@ __device__ __forceinline__ void ab_commit(uint32_t mbar) {
 
 __device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kAbBuild) : "memory"); }
 
-// Barrier over the builder warps that also returns, to every builder thread, whether
-// any of them passed `v` true: a decision all builders take the same way.
+// Barrier over the builder warps (named barrier 1) or the epilogue warps (2) that also
+// returns, to every thread of the group, whether any of them passed `v` true: a
+// decision the whole group takes the same way.
 __device__ __forceinline__ bool builders_any(bool v) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
         : "=r"(r)
         : "r"((uint32_t)v), "n"(kAbBuild)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ bool epi_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 2, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kAbEpi)
         : "memory");
     return r != 0;
 }
@@ -128,16 +140,6 @@ __device__ __forceinline__ uint32_t ab_between(int i, int j) {
     return ((1u << hi) - 1u) & ~((1u << (lo + 1)) - 1u);
 }
 
-__device__ __forceinline__ uint32_t ab_prefix_parity(uint32_t x) {
-    // bit k: parity of the bits of x below k
-    uint32_t y = x << 1;
-    y ^= y << 1;
-    y ^= y << 2;
-    y ^= y << 4;
-    y ^= y << 8;
-    y ^= y << 16;
-    return y;
-}
 
 }  // namespace
 
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
         }
         for (int t = 0; t < 2; ++t) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&accf[t])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&acce[t])), "n"(kAbBuild) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&acce[t])), "n"(kAbEpi) : "memory");
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&done)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -226,49 +228,12 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
         int cur_tile = -1, it = 0, gch = 0;
         int Ia = 0;
         bool valid = false;
-        int prev_bp = 0, prev_Ia = 0;
-        bool prev_valid = false;
-        bool failed = false;
-        // drain the accumulator of unit `iu` (row bp, this thread's alpha string) into H
-        auto epilogue = [&](int iu, int bp, int ia, bool ok_row) -> bool {
-            const int t = iu & 1;
-            bool bad = false;
-            if (tid == 0) {
-                if (!ab_wait(su32(&accf[t]), (uint32_t)((iu >> 1) & 1))) s_fail = 1;
-                bad = s_fail != 0;
-            }
-            if (builders_any(bad)) return false;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int quarter = warp & 3;
-            // plane = hf for complex; for real states the two halves split the columns
-            const int plane = P == 2 ? hf : 0;
-            const int c0 = P == 2 ? 0 : hf * (ncolsP / 2), c1 = P == 2 ? g.ncols : min(g.ncols, (hf + 1) * (ncolsP / 2));
-            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * 2 * kAbMaxN + plane * kAbMaxN);
-            float *Hp = g.H + (size_t)plane * g.hplane + (size_t)bp * g.ncols * g.Da + ia;
-            for (int c = c0 & ~7; c < c1; c += 8) {
-                uint32_t v[8];
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                               "=r"(v[7])
-                             : "r"(tbase + (uint32_t)c)
-                             : "memory");
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (ok_row) {
-                    #pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (c + j >= c0 && c + j < c1) Hp[(size_t)(c + j) * g.Da] = __uint_as_float(v[j]);
-                }
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            ab_arrive(su32(&acce[t]));
-            return true;
-        };
         stage_row(blockIdx.x, 0);
         for (int u = blockIdx.x; u < g.units; u += gridDim.x, ++it) {
             const int atile = u / g.Db, bp = u - atile * g.Db, buf = it & 1;
             asm volatile("cp.async.wait_all;" ::: "memory");
             // this unit's row has landed; every builder is done with the previous unit
-            if (builders_any(tid == 0 && s_fail)) { failed = true; break; }
+            if (builders_any(tid == 0 && s_fail)) break;
             if (u + (int)gridDim.x < g.units) stage_row(u + gridDim.x, buf ^ 1);
             if (atile != cur_tile) {
                 // the tile's table: per row and kappa, partner rank (12 bits) | sign << 12 |
@@ -331,28 +296,30 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                 {
                     const uint4 tv = *reinterpret_cast<const uint4 *>(trow + c * kAbKc);
                     const uint32_t te[4] = {tv.x, tv.y, tv.z, tv.w};
+                    // branch-free: an entry that is zero reads amplitude 0 and masks it out
                     #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const uint32_t e = (te[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+                        const uint32_t *x = xr + (e & 0xFFFu) * 3;
+                        w[k][0] = x[0];
+                        w[k][1] = x[1];
+                        w[k][2] = x[2];
+                    }
+                    #pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const uint32_t e = (te[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+                        const uint32_t keep = (e & (1u << 13)) ? 0xFFFFFFFFu : 0u;
                         const uint32_t flip = (e & (1u << 12)) ? 0x80008000u : 0u;
-                        if (e & (1u << 13)) {
-                            const uint32_t *x = xr + (e & 0xFFFu) * 3;
-                            w[k][0] = x[0] ^ flip;
-                            w[k][1] = x[1] ^ flip;
-                            w[k][2] = x[2] ^ flip;
-                        } else {
-                            w[k][0] = w[k][1] = w[k][2] = 0u;
-                        }
+                        w[k][0] = (w[k][0] ^ flip) & keep;
+                        w[k][1] = (w[k][1] ^ flip) & keep;
+                        w[k][2] = (w[k][2] ^ flip) & keep;
                     }
                 }
-                if (gch >= kAbS) {
-                    bool bad = false;
-                    if (tid == 0) {
-                        if (!ab_wait(su32(&empty[s]), (uint32_t)(((gch / kAbS) - 1) & 1))) s_fail = 1;
-                        bad = s_fail != 0;
-                    }
-                    if (builders_any(bad)) { failed = true; break; }
-                }
+                // the stage is free once the MMAs of K block gch - kAbS are done; every builder
+                // waits itself (a timeout sets s_fail, which ends the other waits at once; the
+                // builders then stop together at the next unit)
+                if (gch >= kAbS && !s_fail && !ab_wait(su32(&empty[s]), (uint32_t)(((gch / kAbS) - 1) & 1)))
+                    s_fail = 1;
                 uint8_t *st = ring + s * kStageBytes;
                 #pragma unroll
                 for (int pl = 0; pl < P; ++pl) {
@@ -374,14 +341,49 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 ab_arrive(su32(&full[s]));
             }
-            if (failed) break;
-            if (it >= 1 && !epilogue(it - 1, prev_bp, prev_Ia, prev_valid)) { failed = true; break; }
-            prev_bp = bp;
-            prev_Ia = Ia;
-            prev_valid = valid;
         }
-        if (!failed && it >= 1 && !epilogue(it - 1, prev_bp, prev_Ia, prev_valid)) failed = true;
         asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (tid >= kAbBuild + 32) {
+        // ------------------------------------------------------------ epilogue warps
+        // drain each unit's accumulator (row bp, tile row r = this thread's lane) into H
+        const int quarter = warp & 3, r = quarter * 32 + (tid & 31);
+        int it = 0;
+        for (int u = blockIdx.x; u < g.units; u += gridDim.x, ++it) {
+            const int atile = u / g.Db, bp = u - atile * g.Db, t = it & 1, ia = atile * kAbM + r;
+            bool bad = false;
+            if (tid == kAbBuild + 32) {
+                if (!ab_wait(su32(&accf[t]), (uint32_t)((it >> 1) & 1))) s_fail = 1;
+                bad = s_fail != 0;
+            }
+            if (epi_any(bad)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const bool ok_row = ia < g.Da;
+            #pragma unroll
+            for (int pl = 0; pl < P; ++pl) {
+                const uint32_t tbase =
+                    tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * 2 * kAbMaxN + pl * kAbMaxN);
+                float *Hp = g.H + (size_t)pl * g.hplane + (size_t)bp * g.ncols * g.Da + ia;
+                for (int c = 0; c < g.ncols; c += 16) {
+                    uint32_t v[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                        "[%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                          "=r"(v[15])
+                        : "r"(tbase + (uint32_t)c)
+                        : "memory");
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (ok_row) {
+                        #pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c + j < g.ncols) Hp[(size_t)(c + j) * g.Da] = __uint_as_float(v[j]);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            ab_arrive(su32(&acce[t]));
+        }
     } else if (tid == kAbBuild) {
         // ------------------------------------------------------------ MMA issuer
         // kind::f16, D float32, A and B bf16, both K-major, N = ncolsP, M = 128
