@@ -39,11 +39,18 @@ if ROOT not in sys.path:
 METRIC = "energy+adjoint-grad evals/s at 30 qubits, FP32-state vs FP64; % of HBM peak"
 UNIT = "evals/s"
 CONFIG_ID = 5
-# DRAM bytes (read + write) of one sector-storage expectation (same-spin product form:
-# k_phase_planar, k_transpose_pieces, k_same_tc, k_sigma_ab, k_sigma_comb) from the ncu
-# capture summarised in profiles/sigma_products_n30_sector_c64.md; None once a kernel
+# DRAM bytes (read + write) of one sector-storage expectation per expectation form, from
+# the ncu captures summarised in profiles/sigma_products_n30_sector_c64.md (form 4:
+# k_phase_planar, k_transpose_pieces, k_same_tc, k_sigma_ab, k_sigma_comb; form 5: the
+# same with k_ab_tc for k_sigma_ab and the gathering k_sigma_comb); None once a kernel
 # changes.
-SIGMA_TRAFFIC_BYTES = 1555.6e6
+SIGMA_TRAFFIC_BYTES = {4: 1555.6e6, 5: None}
+SIGMA_KERNELS = {
+    3: "expectation: k_sigma_ab + k_sigma_same (two launches)",
+    4: "expectation: k_phase_planar + k_transpose_pieces + k_same_tc (same-spin products, tcgen05 bf16x3) "
+       "+ k_sigma_ab + k_sigma_comb",
+    5: "expectation: k_phase_planar + k_transpose_pieces + k_same_tc (same-spin products) + k_ab_tc "
+       "(alpha-beta products; both tcgen05 bf16x3) + k_sigma_comb (gathers the alpha-beta planes)"}
 # DRAM bytes per k_adjoint launch of the dense headline: the 28-qubit capture's
 # traffic / algorithmic ratio (1.115, profiles/k_adjoint_dram_n28_dense_c64.md) times
 # the 30-qubit algorithmic bytes per launch; None once the kernel changes.
@@ -506,18 +513,15 @@ def run_ours(args, rank, world, local_rank):
         fpeak = fp32_peak_tflops(sm_mhz)
         ach = flops / t_sig / 1e12
         sb = sector_touched_bytes(p["ops"], p["n_orb"], p["na"], p["nb"], 8)
+        sv_form = int((s64["tuned"] or {}).get("expect_variant", s64.get("variant", 5)))
         t_rot = s64["phases"]["forward"] / L / 1000.0
         t_adj = s64["phases"]["reverse"] / L / 1000.0
         sect = {"storage": "sector: C(15,5)^2 = 9,018,009 amplitudes (72 MB complex64), L2-resident",
                 "value": throughput(world, K, s64["ms"]), "unit": UNIT, "ms_per_step": s64["ms"] / K,
                 "phases_ms": s64["phases"], "clocks": s64["clocks"], "gpu_launches": int(s64["launches"]),
-                "roofline": {"bound": "alu", "kernel": (
-                    "expectation: k_phase_planar + k_transpose_pieces + k_same_tc (same-spin products, tcgen05 "
-                    "bf16x3) + k_sigma_ab + k_sigma_comb"
-                    if (s64["tuned"] or {}).get("expect_variant", 4) == 4
-                    else "expectation: k_sigma_ab + k_sigma_same (two launches)"),
+                "roofline": {"bound": "alu", "kernel": SIGMA_KERNELS.get(sv_form, "expectation form %d" % sv_form),
                              "achieved": ach, "peak": fpeak, "unit": "TFLOP/s", "frac": ach / fpeak,
-                             "traffic": SIGMA_TRAFFIC_BYTES,
+                             "traffic": SIGMA_TRAFFIC_BYTES.get(sv_form),
                              "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz"
                                           % (sm_mhz or 2070.0),
                              "algorithmic": "%d determinants x %d connections x 4 flops = %.1f GFLOP"

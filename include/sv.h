@@ -316,11 +316,14 @@ typedef enum {
                                        (0 = none; default 0) */
     SV_OPT_MAX_BYTES = 2,           /* cap on device bytes this handle may allocate
                                        (0 = no cap); checkpoints are dropped to fit */
-    SV_OPT_EXPECT_VARIANT = 3,      /* 0 auto (= 4 for complex64 / real float32 states
+    SV_OPT_EXPECT_VARIANT = 3,      /* 0 auto (= 5 for complex64 / real float32 states
                                        of at least 2^20 sector determinants whose
                                        same-spin couplings fill at least 5% of a string
-                                       space of at most 4096 strings; else 3 where its
-                                       rows fit in shared memory; else 2); 1 record scan:
+                                       space of at most 4096 strings, where variant 5's
+                                       limits hold and its planes take at most 16 GiB
+                                       within the byte cap, else 4 for those states;
+                                       else 3 where its rows fit in shared memory; else
+                                       2); 1 record scan:
                                        one thread per sector determinant tests every mask
                                        group (dense storage only); 2 string rows: compact
                                        alpha/beta-string matrix, one block per beta

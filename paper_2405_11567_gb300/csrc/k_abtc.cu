@@ -172,8 +172,10 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
     constexpr int kStageBytes = 2 * 3 * kAbABytes + 3 * kAbMaxN * kAbKc * 2;
     const uint32_t raw = su32(ab_smem), sbase = (raw + 1023u) & ~1023u;
     uint8_t *ring = ab_smem + (sbase - raw);
-    uint32_t *xrow = reinterpret_cast<uint32_t *>(ring + kAbS * kStageBytes);  // [2][ldi][3]
-    uint16_t *tbl = reinterpret_cast<uint16_t *>(xrow + 2 * (size_t)g.ldi * 3); // [128][tstride]
+    // staged X rows: ldi amplitudes copied, then 4 zero amplitudes (what zero table entries read)
+    const int xstride = (g.ldi + 4) * 3;                                        // words per row buffer
+    uint32_t *xrow = reinterpret_cast<uint32_t *>(ring + kAbS * kStageBytes);  // [2][ldi + 4][3]
+    uint16_t *tbl = reinterpret_cast<uint16_t *>(xrow + 2 * (size_t)xstride);  // [128][tstride]
     const int tid = threadIdx.x, warp = tid >> 5;
     const int N = g.N, ncolsP = g.ncols <= 64 ? 64 : kAbMaxN, tstride = ab_tstride(g.nK);
     const int Ktot = N * (N + 1) / 2;
@@ -195,6 +197,10 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&done)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = tid; i < 12; i += kAbThreadsTc) {  // the zero amplitudes after each row buffer
+        xrow[g.ldi * 3 + i] = 0u;
+        xrow[xstride + g.ldi * 3 + i] = 0u;
     }
     // kappa -> (p, q): p = q = kappa below N, then the pairs p < q in order
     for (int k = tid; k < kAbMaxK; k += kAbThreadsTc) {
@@ -220,14 +226,23 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
         const int rowbytes = g.ldi * 12;                // a multiple of 16
         auto stage_row = [&](int u, int buf) {          // asynchronous copy of X row u % Db
             const uint8_t *src = reinterpret_cast<const uint8_t *>(g.Xi) + (size_t)(u % g.Db) * rowbytes;
-            uint8_t *dst = reinterpret_cast<uint8_t *>(xrow) + (size_t)buf * rowbytes;
+            uint8_t *dst = reinterpret_cast<uint8_t *>(xrow + (size_t)buf * xstride);
             for (int i = tid * 16; i < rowbytes; i += kAbBuild * 16)
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst + i)), "l"(src + i) : "memory");
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
         int cur_tile = -1, it = 0, gch = 0;
-        int Ia = 0;
-        bool valid = false;
+        // this thread's share of the B copies: entries i = tid + 256 k of (piece, row, core
+        // column); shared-memory offsets fixed, global rows set per unit
+        int bdst[2], bsel[2];
+        #pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int i = tid + k * kAbBuild;
+            bsel[k] = i < ncolsP * 6 ? i : -1;
+            const int ii = bsel[k] < 0 ? 0 : i, piece = ii / (ncolsP * 2), rem = ii - piece * ncolsP * 2;
+            bdst[k] = Ac + piece * (ncolsP * kAbKc * 2) + (int)ab_off(rem >> 1, rem & 1);
+        }
+        const uint16_t *bsrc[2] = {g.Bp, g.Bp};
         stage_row(blockIdx.x, 0);
         for (int u = blockIdx.x; u < g.units; u += gridDim.x, ++it) {
             const int atile = u / g.Db, bp = u - atile * g.Db, buf = it & 1;
@@ -236,22 +251,23 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
             if (builders_any(tid == 0 && s_fail)) break;
             if (u + (int)gridDim.x < g.units) stage_row(u + gridDim.x, buf ^ 1);
             if (atile != cur_tile) {
-                // the tile's table: per row and kappa, partner rank (12 bits) | sign << 12 |
-                // nonzero << 13 (this thread: half hf of the row's entries)
+                // the tile's table: per row and kappa, the word offset in a row buffer of the
+                // partner amplitude (3 J; 3 ldi, a zero amplitude, where the entry is zero)
+                // | sign << 14 (this thread: half hf of the row's entries)
                 cur_tile = atile;
-                Ia = atile * kAbM + r;
-                valid = Ia < g.Da;
-                const uint32_t a = valid ? g.stra[Ia] : 0u;
+                const int Ia = atile * kAbM + r;
+                const bool valid = Ia < g.Da;
+                const uint32_t a = valid ? g.stra[Ia] : 0u, zero = (uint32_t)g.ldi * 3;
                 const int half = tstride / 2;
                 for (int k = hf * half; k < (hf + 1) * half; ++k) {
-                    uint32_t e = 0;
+                    uint32_t e = zero;
                     if (valid && k < Ktot) {
                         const int p = s_kp[k], q = s_kq[k];
                         if (p == q) {
-                            if ((a >> p) & 1u) e = (uint32_t)Ia | (1u << 13);
+                            if ((a >> p) & 1u) e = 3u * (uint32_t)Ia;
                         } else if (((a >> p) ^ (a >> q)) & 1u) {
                             const uint32_t ap = a ^ (1u << p) ^ (1u << q);
-                            e = (uint32_t)g.ra[ap] | ((uint32_t)ab_par(a & ab_between(p, q)) << 12) | (1u << 13);
+                            e = 3u * (uint32_t)g.ra[ap] | ((uint32_t)ab_par(a & ab_between(p, q)) << 14);
                         }
                     }
                     tbl[r * tstride + k] = (uint16_t)e;
@@ -273,46 +289,41 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                 s_rowB[tid] = row;
             }
             builders_sync();
-            const uint32_t *xr = xrow + (size_t)buf * g.ldi * 3;
+            #pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int ii = bsel[k] < 0 ? 0 : bsel[k], piece = ii / (ncolsP * 2), rem = ii - piece * ncolsP * 2;
+                bsrc[k] = g.Bp + (size_t)piece * g.pb + (size_t)s_rowB[rem >> 1] * 256 + (rem & 1) * 8;
+            }
+            const uint32_t *xr = xrow + (size_t)buf * xstride;
             const uint16_t *trow = tbl + r * tstride + hf * 8;
             for (int c = 0; c < g.nK; ++c, ++gch) {
                 const int s = gch % kAbS;
                 // B rows of this K block into registers (ncolsP rows x 2 core columns x 3 pieces)
                 uint4 bv[2];
-                int bi[2];
                 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int i = tid + k * kAbBuild;  // < ncolsP * 2 * 3
-                    bi[k] = i < ncolsP * 6 ? i : -1;
-                    if (bi[k] >= 0) {
-                        const int piece = i / (ncolsP * 2), rem = i - piece * ncolsP * 2, row = rem >> 1,
-                                  kc = rem & 1;
-                        const uint16_t *src = g.Bp + (size_t)piece * g.pb + (size_t)s_rowB[row] * 256 + c * kAbKc + kc * 8;
-                        bv[k] = *reinterpret_cast<const uint4 *>(src);
-                    }
-                }
-                // this thread's 8 K entries of row r: three words each (pieces 1..3, re | im << 16)
+                for (int k = 0; k < 2; ++k)
+                    if (bsel[k] >= 0) bv[k] = *reinterpret_cast<const uint4 *>(bsrc[k] + c * kAbKc);
+                // this thread's 8 K entries of row r: three words each (pieces 1..3, re | im << 16),
+                // sign bits flipped by the entry's sign
                 uint32_t w[8][3];
                 {
                     const uint4 tv = *reinterpret_cast<const uint4 *>(trow + c * kAbKc);
                     const uint32_t te[4] = {tv.x, tv.y, tv.z, tv.w};
-                    // branch-free: an entry that is zero reads amplitude 0 and masks it out
                     #pragma unroll
                     for (int k = 0; k < 8; ++k) {
-                        const uint32_t e = (te[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
-                        const uint32_t *x = xr + (e & 0xFFFu) * 3;
+                        const uint32_t e = (k & 1) ? te[k >> 1] >> 16 : te[k >> 1] & 0xFFFFu;
+                        const uint32_t *x = xr + (e & 0x3FFFu);
                         w[k][0] = x[0];
                         w[k][1] = x[1];
                         w[k][2] = x[2];
                     }
                     #pragma unroll
                     for (int k = 0; k < 8; ++k) {
-                        const uint32_t e = (te[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
-                        const uint32_t keep = (e & (1u << 13)) ? 0xFFFFFFFFu : 0u;
-                        const uint32_t flip = (e & (1u << 12)) ? 0x80008000u : 0u;
-                        w[k][0] = (w[k][0] ^ flip) & keep;
-                        w[k][1] = (w[k][1] ^ flip) & keep;
-                        w[k][2] = (w[k][2] ^ flip) & keep;
+                        const uint32_t e = (k & 1) ? te[k >> 1] >> 16 : te[k >> 1] & 0xFFFFu;
+                        const uint32_t flip = (e >> 14) * 0x80008000u;
+                        w[k][0] ^= flip;
+                        w[k][1] ^= flip;
+                        w[k][2] ^= flip;
                     }
                 }
                 // the stage is free once the MMAs of K block gch - kAbS are done; every builder
@@ -331,13 +342,8 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                                        __byte_perm(w[4][pc], w[5][pc], sel), __byte_perm(w[6][pc], w[7][pc], sel));
                 }
                 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    if (bi[k] >= 0) {
-                        const int i = bi[k], piece = i / (ncolsP * 2), rem = i - piece * ncolsP * 2, row = rem >> 1,
-                                  kc = rem & 1;
-                        *reinterpret_cast<uint4 *>(st + Ac + piece * (ncolsP * kAbKc * 2) + ab_off(row, kc)) = bv[k];
-                    }
-                }
+                for (int k = 0; k < 2; ++k)
+                    if (bsel[k] >= 0) *reinterpret_cast<uint4 *>(st + bdst[k]) = bv[k];
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 ab_arrive(su32(&full[s]));
             }
@@ -473,7 +479,7 @@ size_t ab_tc_smem(int Da, int N) {
     const size_t stage = 2 * 3 * kAbABytes + 3 * kAbMaxN * kAbKc * 2;
     const int nK = (N * (N + 1) / 2 + kAbKc - 1) / kAbKc;
     const size_t ldi = ((size_t)Da + 3) / 4 * 4;
-    return 1024 + kAbS * stage + 2 * ldi * 12 + (size_t)kAbM * ab_tstride(nK) * 2;
+    return 1024 + kAbS * stage + 2 * (ldi + 4) * 12 + (size_t)kAbM * ab_tstride(nK) * 2;
 }
 
 }  // namespace

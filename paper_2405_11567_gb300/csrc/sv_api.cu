@@ -648,10 +648,18 @@ static bool use_same_gemm(sv_handle h, int K) {
 }
 
 // Whether the same-spin product form also takes the alpha-beta part as tensor-core
-// products (variant 5; where k_ab_tc's limits hold, else variant 4).
+// products (variant 5; where k_ab_tc's limits hold, else variant 4).  Automatic choice
+// (variant 0, once the same-spin products are chosen): where its product planes
+// (planes x Db x (nb (N - nb) + 1) x Da floats) take at most 16 GiB and fit under the
+// handle's byte cap.
 static bool use_ab_tc(sv_handle h) {
-    if (h->expect_variant != 5) return false;
-    return ab_tc_fits(is_complex(h->dtype) ? 2 : 1, h->Da, h->Db, h->na, h->nb, h->n / 2);
+    if (h->expect_variant != 5 && h->expect_variant != 0) return false;
+    const int planes = is_complex(h->dtype) ? 2 : 1, N = h->n / 2;
+    if (!ab_tc_fits(planes, h->Da, h->Db, h->na, h->nb, N)) return false;
+    if (h->expect_variant == 5) return true;
+    const double hb = 4.0 * planes * (double)h->Db * (h->nb * (N - h->nb) + 1) * (double)h->Da;
+    if (hb > (double)(16ull << 30)) return false;
+    return h->max_bytes <= 0 || (double)h->bytes_owned + (h->ab_H_bytes >= hb ? 0.0 : hb) <= (double)h->max_bytes;
 }
 
 // The same-spin matrices of the table set and sector (built on first use, kept until
@@ -974,12 +982,14 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
         int best_v = 2;
         int64_t best_k = 0;
         float best_t = -1.f;
-        const int nv = single_prec(h->dtype) ? 2 : 1;  // split form; same-spin products (single precision)
-        for (int i = -1; i < 4 * nv; ++i) {
-            h->expect_variant = i < 0 ? 2 : (i < 4 ? 3 : 4);
-            h->ab_chunk = i < 0 ? 0 : sizes[i & 3];
-            if (i >= 0 && row_chunk(h, R) != sizes[i & 3]) continue;  // that size does not fit
-            if (i >= 4 && !use_same_gemm(h, sizes[i & 3])) continue;
+        // split form; same-spin products and the tensor-core alpha-beta form (single precision)
+        const int nv = single_prec(h->dtype) ? 2 : 1;
+        for (int i = -1; i < 4 * nv + (nv > 1 ? 1 : 0); ++i) {
+            h->expect_variant = i < 0 ? 2 : (i < 4 ? 3 : (i < 8 ? 4 : 5));
+            h->ab_chunk = i < 0 ? 0 : (i < 8 ? sizes[i & 3] : 0);
+            if (i >= 0 && i < 8 && row_chunk(h, R) != sizes[i & 3]) continue;  // that size does not fit
+            if (i >= 4 && !use_same_gemm(h, row_chunk(h, R))) continue;
+            if (i == 8 && !use_ab_tc(h)) continue;
             const float t = time_best(h, e0, e1, [&] { return expectation(h, ham, T, h->lam, c, 0); });
             if (t < 0.f) return fail(h, SV_ERR_CUDA, "autotune: expectation candidate failed");
             if (best_t < 0.f || t < best_t) {
