@@ -20,8 +20,8 @@
 // with X = phi C (phi(a, b) = (-1)^popc(a & pp(b))) and s_a the parity of a's bits
 // strictly between p and q.  The p = q, own-column term (the alpha-beta Coulomb
 // diagonal) is left to the diagonal.  Per b' the columns are its nb (N - nb)
-// excitations plus the own column, <= 65, padded to 64 or 80; K = N (N + 1) / 2 <= 136,
-// padded to a multiple of 16.
+// excitations plus the own column (at most 51 where N <= 16 and each spin has at most 4096
+// strings), padded to 64; K = N (N + 1) / 2 <= 136, padded to a multiple of 16.
 //
 // k_ab_tc: a persistent kernel over units (128-string alpha tile, partner row b').
 // Eight builder warps stage the b' row of X as bf16 pieces (written once per sigma by
@@ -53,7 +53,7 @@ constexpr int kAbM = 128;                      // alpha strings per tile
 constexpr int kAbKc = 16;                      // K (orbitals and orbital pairs) per stage
 constexpr int kAbS = 3;                        // stages
 constexpr int kAbMaxK = 144;                   // N (N + 1) / 2 <= 136 for N <= 16, padded to 16
-constexpr int kAbMaxN = 80;                    // columns per accumulator (<= 65 used)
+constexpr int kAbMaxN = 64;                    // columns per accumulator: nb (N - nb) + 1 <= 51 within the limits
 constexpr int kAbABytes = kAbM * kAbKc * 2;    // one bf16 piece of one plane of A: 4 KB
 constexpr uint32_t kAbSpins = 1u << 22;
 
@@ -177,11 +177,11 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
     uint32_t *xrow = reinterpret_cast<uint32_t *>(ring + kAbS * kStageBytes);  // [2][ldi + 4][3]
     uint16_t *tbl = reinterpret_cast<uint16_t *>(xrow + 2 * (size_t)xstride);  // [128][tstride]
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int N = g.N, ncolsP = g.ncols <= 64 ? 64 : kAbMaxN, tstride = ab_tstride(g.nK);
+    const int N = g.N, ncolsP = kAbMaxN, tstride = ab_tstride(g.nK);
     const int Ktot = N * (N + 1) / 2;
     const int Ac = 2 * 3 * kAbABytes;  // A bytes per stage (both planes)
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(&tmem_base))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(su32(&tmem_base))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (tid == 0 && s_fail) atomicExch(g.err, 1);
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
 namespace {
@@ -495,7 +495,7 @@ cudaError_t launch_ab_table(const float *eri, const float *Jt, const uint16_t *s
 }
 
 // Whether the tensor-core alpha-beta form applies: N <= 16, D <= 4096 per spin, at most
-// 80 columns, and its shared memory fits.
+// 64 columns, and its shared memory fits.
 bool ab_tc_fits(int planes, int Da, int Db, int na, int nb, int N) {
     (void)planes;
     (void)na;

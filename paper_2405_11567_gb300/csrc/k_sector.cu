@@ -206,6 +206,66 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_l(A *__restrict__ psi, A *
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// The same adjoint step on the interleaved matrix CL[2 e] = psi[e], CL[2 e + 1] = lam[e]:
+// one vector load / store per amplitude moves both, so each pair costs two scattered
+// accesses instead of four and every 32-byte L2 sector it touches carries twice the
+// useful bytes.  Same arithmetic in the same order as k_adjoint_l.
+template <typename A>
+struct alignas(2 * sizeof(A)) AmpPair {
+    A c, l;
+};
+
+template <typename A>
+__global__ void __launch_bounds__(kThreads) k_adjoint_li(A *__restrict__ CL, const uint32_t *__restrict__ al, int na_l,
+                                                         const uint32_t *__restrict__ bl, int nb_l, int Da,
+                                                         real_of<A> c, real_of<A> sn, double *__restrict__ partial) {
+    using R = real_of<A>;
+    __shared__ double red[kThreads / 32];
+    AmpPair<A> *P = reinterpret_cast<AmpPair<A> *>(CL);
+    double acc = 0.0;
+    if (na_l > 0) {
+        PairWalk w(na_l);
+        while (w.r < nb_l) {
+            size_t I[kPairBatch], J[kPairBatch];
+            bool ok[kPairBatch], neg[kPairBatch];
+            #pragma unroll
+            for (int v = 0; v < kPairBatch; ++v) {
+                ok[v] = w.r < nb_l;
+                const uint32_t eb = ok[v] ? bl[w.r] : 0u, ea = ok[v] ? al[w.i] : 0u;
+                I[v] = (size_t)(eb & 0x7FFFu) * Da + (ea & 0x7FFFu);
+                J[v] = (size_t)(eb >> 16) * Da + (ea >> 16);
+                neg[v] = ((ea ^ eb) & 0x8000u) != 0u;
+                w.next();
+            }
+            AmpPair<A> pu[kPairBatch], px[kPairBatch];
+            #pragma unroll
+            for (int v = 0; v < kPairBatch; ++v) {
+                pu[v] = P[I[v]];
+                px[v] = P[J[v]];
+            }
+            R t = 0;
+            #pragma unroll
+            for (int v = 0; v < kPairBatch; ++v) {
+                if (!ok[v]) continue;
+                const A u = pu[v].c, x = px[v].c, lu = pu[v].l, lx = px[v].l;
+                const R ti = re_dot(lx, u) - re_dot(lu, x);
+                t += neg[v] ? -ti : ti;
+                const R ss = neg[v] ? -sn : sn;
+                AmpPair<A> ou, ox;
+                ou.c = lin2<A>(c, u, ss, x);
+                ox.c = lin2<A>(c, x, -ss, u);
+                ou.l = lin2<A>(c, lu, ss, lx);
+                ox.l = lin2<A>(c, lx, -ss, lu);
+                P[I[v]] = ou;
+                P[J[v]] = ox;
+            }
+            acc += (double)t;
+        }
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
 // Density matrix by rows: a block takes beta strings (rows) Ib = blockIdx.x,
 // blockIdx.x + gridDim.x, ...; for each row its warps sum, in the state precision,
 //   norm and alpha occupations   sum_a |C[b][a]|^2 (a_p)
@@ -401,6 +461,14 @@ cudaError_t launch_adjoint_l(void *psi, void *lam, int dtype, const uint32_t *al
                              int nb_l, int Da, double c, double s, int grid, double *partial, cudaStream_t st) {
     SV_DISPATCH_AMP(dtype, k_adjoint_l<A><<<grid, kThreads, 0, st>>>((A *)psi, (A *)lam, al, na_l, bl, nb_l, Da,
                                                                       (real_of<A>)c, (real_of<A>)s, partial));
+    return cudaGetLastError();
+}
+
+// CL: the interleaved (psi, lam) matrix (launch_interleave), 16-byte aligned.
+cudaError_t launch_adjoint_li(void *CL, int dtype, const uint32_t *al, int na_l, const uint32_t *bl, int nb_l, int Da,
+                              double c, double s, int grid, double *partial, cudaStream_t st) {
+    SV_DISPATCH_AMP(dtype, k_adjoint_li<A><<<grid, kThreads, 0, st>>>((A *)CL, al, na_l, bl, nb_l, Da,
+                                                                       (real_of<A>)c, (real_of<A>)s, partial));
     return cudaGetLastError();
 }
 

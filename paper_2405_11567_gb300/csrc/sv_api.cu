@@ -53,6 +53,8 @@ cudaError_t launch_build_lists(const void *ops, int n_ops, const uint32_t *sa, c
                                int Da, int Db, uint32_t *out, cudaStream_t st);
 cudaError_t launch_rotate_l(void *psi, int dtype, const uint32_t *al, int na_l, const uint32_t *bl, int nb_l, int Da,
                             double c, double s, int grid, cudaStream_t st);
+cudaError_t launch_adjoint_li(void *CL, int dtype, const uint32_t *al, int na_l, const uint32_t *bl, int nb_l, int Da,
+                              double c, double s, int grid, double *partial, cudaStream_t st);
 cudaError_t launch_adjoint_l(void *psi, void *lam, int dtype, const uint32_t *al, int na_l, const uint32_t *bl,
                              int nb_l, int Da, double c, double s, int grid, double *partial, cudaStream_t st);
 int rdm_rows_elements(int n);
@@ -166,6 +168,19 @@ static void dev_free(sv_handle h, void *p, size_t bytes) {
 // Bytes of one state-sized vector: 2^n amplitudes (dense storage) or the
 // C(N, na) C(N, nb) amplitudes of the sector (sector storage).
 static size_t vec_bytes(sv_handle h) { return (size_t)h->elems * h->amp_bytes; }
+
+// The interleaved (amplitude, sigma) matrix of sector-sized vectors: 2 Da Db amplitudes
+// (pool screening over pair lists, the sector adjoint sweep).
+static sv_status ensure_clbuf(sv_handle h) {
+    const size_t need = std::max<size_t>(2 * (size_t)h->Da * h->Db * h->amp_bytes, 16);
+    if (h->CLbuf_bytes >= need) return SV_OK;
+    dev_free(h, h->CLbuf, h->CLbuf_bytes);
+    h->CLbuf = nullptr;
+    h->CLbuf_bytes = 0;
+    SV_TRY(dev_alloc(h, &h->CLbuf, need, "interleaved amplitudes and sigma"));
+    h->CLbuf_bytes = need;
+    return SV_OK;
+}
 
 static sv_status ensure_lam(sv_handle h) {
     if (h->lam) return SV_OK;
@@ -1020,6 +1035,16 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
         float best_t = -1.f;
         if (h->storage == 1) SV_TRY(ensure_op_lists(h, d, h->lists));
         SV_TRY(ensure_partials(h, (size_t)h->sm_count * 32));
+        // sector storage: the adjoint step as sv_energy_grad runs it (interleaved unless checkpoints resync psi)
+        bool inter = h->storage == 1 && adj && h->ckpt_interval <= 0;
+        if (inter && ensure_clbuf(h) != SV_OK) {
+            cudaGetLastError();
+            inter = false;
+        }
+        if (inter) {
+            SV_CUDA(h, launch_interleave(h->lam, h->saved, h->dtype, h->CLbuf, (size_t)h->Da * h->Db, h->sm_count,
+                                         h->stream));
+        }
         for (int b : cands) {
             float t;
             if (h->storage == 1) {
@@ -1029,7 +1054,10 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
                 t = time_best(h, e0, e1, [&]() -> sv_status {
                     SV_CUDA(h, launch_rotate_l(h->lam, h->dtype, L + li[0], li[1], L + li[2], li[3], h->Da, d[k].c,
                                                d[k].s, G, h->stream));
-                    if (adj)
+                    if (inter)
+                        SV_CUDA(h, launch_adjoint_li(h->CLbuf, h->dtype, L + li[0], li[1], L + li[2], li[3], h->Da,
+                                                     d[k].c, d[k].s, G, h->partials, h->stream));
+                    else if (adj)
                         SV_CUDA(h, launch_adjoint_l(h->lam, h->saved, h->dtype, L + li[0], li[1], L + li[2], li[3],
                                                     h->Da, d[k].c, d[k].s, G, h->partials, h->stream));
                     return SV_OK;
@@ -1494,8 +1522,26 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     SV_TRY(mark(h, 4));
     // reverse sweep
     const int64_t C = h->ckpt_interval;
+    // sector storage without checkpoint resynchronisation: the sweep runs on the
+    // interleaved (psi, lambda) matrix, psi itself keeps psi(theta) (where the matrix
+    // cannot be allocated under the byte cap, the sweep runs on psi and lambda)
+    bool inter = sect && C <= 0 && L > 0;
+    if (inter && ensure_clbuf(h) != SV_OK) {
+        cudaGetLastError();
+        inter = false;
+    }
+    if (inter) {
+        SV_CUDA(h, launch_interleave(h->psi, h->lam, h->dtype, h->CLbuf, (size_t)h->Da * h->Db, h->sm_count,
+                                     h->stream));
+        h->launches++;
+    }
     for (size_t kk = L; kk-- > 0;) {
-        if (sect) {
+        if (inter) {
+            const uint32_t *LB = (const uint32_t *)h->lists.buf;
+            const int *li = &h->lists.info[4 * kk];
+            SV_CUDA(h, launch_adjoint_li(h->CLbuf, h->dtype, LB + li[0], li[1], LB + li[2], li[3], h->Da, d[kk].c,
+                                         d[kk].s, G, h->partials + kk * (size_t)G, h->stream));
+        } else if (sect) {
             const uint32_t *LB = (const uint32_t *)h->lists.buf;
             const int *li = &h->lists.info[4 * kk];
             SV_CUDA(h, launch_adjoint_l(h->psi, h->lam, h->dtype, LB + li[0], li[1], LB + li[2], li[3], h->Da,
@@ -1516,8 +1562,9 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     h->launches++;
     SV_TRY(mark(h, 5));
     SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, (2 + L) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    // leave psi(theta) in the handle
-    if (h->saved) {
+    // leave psi(theta) in the handle (the interleaved sweep left it there)
+    if (inter) {
+    } else if (h->saved) {
         SV_CUDA(h, cudaMemcpyAsync(h->psi, h->saved, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
     } else {
         SV_TRY(prepare_reference(h));
@@ -1577,13 +1624,7 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
     }
     if (use_lists && n_pool > 0) {
         SV_TRY(ensure_op_lists(h, descs, h->pool_lists));
-        if (h->CLbuf_bytes < 2 * cb) {
-            dev_free(h, h->CLbuf, h->CLbuf_bytes);
-            h->CLbuf = nullptr;
-            h->CLbuf_bytes = 0;
-            SV_TRY(dev_alloc(h, &h->CLbuf, std::max<size_t>(2 * cb, 16), "interleaved amplitudes and sigma"));
-            h->CLbuf_bytes = std::max<size_t>(2 * cb, 16);
-        }
+        SV_TRY(ensure_clbuf(h));
     }
     const size_t op_doubles = ((size_t)host_ops.size() + 7) / 8;
     SV_TRY(ensure_partials(h, 3 * (size_t)h->Db + op_doubles));
