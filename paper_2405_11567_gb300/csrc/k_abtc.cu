@@ -27,10 +27,12 @@
 // Eight builder warps stage the b' row of X as bf16 pieces (written once per sigma by
 // the phase kernel: per amplitude three words (re_k | im_k << 16), k = 1..2..3;
 // asynchronous copies, one unit ahead), gather A for the tile's rows K = 16 at a time
-// through a per-tile table (partner rank | sign | nonzero per row and kappa, rebuilt
-// when the tile changes) straight into the canonical no-swizzle K-major layout (core
-// matrices of 8 rows x 16 bytes), flipping sign bits and pairing halves only, and copy
-// the unit's B rows (pieces of a precomputed table);
+// through a per-tile table (partner offset | sign per row and kappa, rebuilt when the
+// tile changes), flipping sign bits and pairing halves only, and write it to tensor
+// memory (tcgen05.st: each builder warp its lane quarter, row = lane, two K per column),
+// where the MMAs read A; they copy the unit's B rows (pieces of a precomputed table)
+// into shared memory in the canonical no-swizzle K-major layout (core matrices of 8 rows
+// x 16 bytes);
 // lane 0 of warp 8 issues tcgen05.mma kind::f16 (six piece products per plane:
 // float32-level accuracy) into one of two tensor-memory accumulators; four epilogue
 // warps (one per tensor-memory lane quarter) drain each finished accumulator into H
@@ -51,10 +53,14 @@ constexpr int kAbEpi = 128;                    // epilogue threads (4 warps: one
 constexpr int kAbThreadsTc = kAbBuild + 32 + kAbEpi;  // builders, the MMA warp, the epilogue warps
 constexpr int kAbM = 128;                      // alpha strings per tile
 constexpr int kAbKc = 16;                      // K (orbitals and orbital pairs) per stage
-constexpr int kAbS = 3;                        // stages
+constexpr int kAbS = 4;                        // stages
 constexpr int kAbMaxK = 144;                   // N (N + 1) / 2 <= 136 for N <= 16, padded to 16
 constexpr int kAbMaxN = 64;                    // columns per accumulator: nb (N - nb) + 1 <= 51 within the limits
-constexpr int kAbABytes = kAbM * kAbKc * 2;    // one bf16 piece of one plane of A: 4 KB
+constexpr int kAbACols = kAbKc / 2;            // tensor-memory columns of one bf16 piece of A (two K per column)
+constexpr int kAbAccCols = 2 * kAbMaxN;        // one accumulator: both planes
+constexpr int kAbAStage = 6 * kAbACols;        // A columns per stage: 2 planes x 3 pieces
+constexpr int kAbABase = 2 * kAbAccCols;       // first A column (after the two accumulators)
+static_assert(kAbABase + kAbS * kAbAStage <= 512, "tensor memory: accumulators and A stages in 512 columns");
 constexpr uint32_t kAbSpins = 1u << 22;
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -168,8 +174,9 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
     __shared__ volatile int s_fail;
     __shared__ int s_rowB[kAbMaxN];
     __shared__ uint8_t s_kp[kAbMaxK], s_kq[kAbMaxK];
-    // dynamic: stage ring (1024-aligned), the two staged X rows, the tile's table
-    constexpr int kStageBytes = 2 * 3 * kAbABytes + 3 * kAbMaxN * kAbKc * 2;
+    // dynamic: stage ring of B (1024-aligned), the two staged X rows, the tile's table; the A
+    // stages live in tensor memory (columns kAbABase + s kAbAStage + (plane 3 + piece) kAbACols)
+    constexpr int kStageBytes = 3 * kAbMaxN * kAbKc * 2;
     const uint32_t raw = su32(ab_smem), sbase = (raw + 1023u) & ~1023u;
     uint8_t *ring = ab_smem + (sbase - raw);
     // staged X rows: ldi amplitudes copied, then 4 zero amplitudes (what zero table entries read)
@@ -179,9 +186,8 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
     const int tid = threadIdx.x, warp = tid >> 5;
     const int N = g.N, ncolsP = kAbMaxN, tstride = ab_tstride(g.nK);
     const int Ktot = N * (N + 1) / 2;
-    const int Ac = 2 * 3 * kAbABytes;  // A bytes per stage (both planes)
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(su32(&tmem_base))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(su32(&tmem_base))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
             const int i = tid + k * kAbBuild;
             bsel[k] = i < ncolsP * 6 ? i : -1;
             const int ii = bsel[k] < 0 ? 0 : i, piece = ii / (ncolsP * 2), rem = ii - piece * ncolsP * 2;
-            bdst[k] = Ac + piece * (ncolsP * kAbKc * 2) + (int)ab_off(rem >> 1, rem & 1);
+            bdst[k] = piece * (ncolsP * kAbKc * 2) + (int)ab_off(rem >> 1, rem & 1);
         }
         const uint16_t *bsrc[2] = {g.Bp, g.Bp};
         stage_row(blockIdx.x, 0);
@@ -332,19 +338,27 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                 if (gch >= kAbS && !s_fail && !ab_wait(su32(&empty[s]), (uint32_t)(((gch / kAbS) - 1) & 1)))
                     s_fail = 1;
                 uint8_t *st = ring + s * kStageBytes;
+                // A: this thread's row (its tensor-memory lane) and 8 K = 4 columns of each piece
+                __syncwarp();
                 #pragma unroll
                 for (int pl = 0; pl < P; ++pl) {
                     const uint32_t sel = pl ? 0x7632u : 0x5410u;  // the im or the re halves of two words
                     #pragma unroll
-                    for (int pc = 0; pc < 3; ++pc)
-                        *reinterpret_cast<uint4 *>(st + (pl * 3 + pc) * kAbABytes + ab_off(r, hf)) =
-                            make_uint4(__byte_perm(w[0][pc], w[1][pc], sel), __byte_perm(w[2][pc], w[3][pc], sel),
-                                       __byte_perm(w[4][pc], w[5][pc], sel), __byte_perm(w[6][pc], w[7][pc], sel));
+                    for (int pc = 0; pc < 3; ++pc) {
+                        const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                                            (uint32_t)(kAbABase + s * kAbAStage + (pl * 3 + pc) * kAbACols + hf * 4);
+                        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta),
+                                     "r"(__byte_perm(w[0][pc], w[1][pc], sel)), "r"(__byte_perm(w[2][pc], w[3][pc], sel)),
+                                     "r"(__byte_perm(w[4][pc], w[5][pc], sel)), "r"(__byte_perm(w[6][pc], w[7][pc], sel))
+                                     : "memory");
+                    }
                 }
                 #pragma unroll
                 for (int k = 0; k < 2; ++k)
                     if (bsel[k] >= 0) *reinterpret_cast<uint4 *>(st + bdst[k]) = bv[k];
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B, for the MMAs' reads
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");   // A written
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 ab_arrive(su32(&full[s]));
             }
         }
@@ -367,7 +381,7 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
             #pragma unroll
             for (int pl = 0; pl < P; ++pl) {
                 const uint32_t tbase =
-                    tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * 2 * kAbMaxN + pl * kAbMaxN);
+                    tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * kAbAccCols + pl * kAbMaxN);
                 float *Hp = g.H + (size_t)pl * g.hplane + (size_t)bp * g.ncols * g.Da + ia;
                 for (int c = 0; c < g.ncols; c += 16) {
                     uint32_t v[16];
@@ -411,18 +425,20 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t base = sbase + (uint32_t)(s * kStageBytes);
+                const uint32_t abase = tmem + (uint32_t)(kAbABase + s * kAbAStage);
                 #pragma unroll
                 for (int pl = 0; pl < P; ++pl) {
-                    const uint32_t d = tmem + (uint32_t)(t * 2 * kAbMaxN + pl * kAbMaxN);
+                    const uint32_t d = tmem + (uint32_t)(t * kAbAccCols + pl * kAbMaxN);
                     #pragma unroll
                     for (int x = 0; x < 6; ++x) {
-                        const uint64_t da = ab_desc(base + (uint32_t)((pl * 3 + pa[x]) * kAbABytes));
-                        const uint64_t db = ab_desc(base + (uint32_t)(Ac + pbk[x] * ncolsP * kAbKc * 2));
+                        // A from tensor memory (lanes = tile rows, two K per column), B from shared memory
+                        const uint32_t ta = abase + (uint32_t)((pl * 3 + pa[x]) * kAbACols);
+                        const uint64_t db = ab_desc(base + (uint32_t)(pbk[x] * ncolsP * kAbKc * 2));
                         const uint32_t acc = (c > 0 || x > 0) ? 1u : 0u;
                         asm volatile(
                             "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}\n" ::"r"(d),
-                            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, q;\n\t}\n" ::"r"(d),
+                            "r"(ta), "l"(db), "r"(idesc), "r"(acc)
                             : "memory");
                     }
                 }
@@ -438,7 +454,7 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (tid == 0 && s_fail) atomicExch(g.err, 1);
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 
 namespace {
@@ -476,7 +492,7 @@ __global__ void __launch_bounds__(256) k_ab_table(const float *__restrict__ eri,
 }
 
 size_t ab_tc_smem(int Da, int N) {
-    const size_t stage = 2 * 3 * kAbABytes + 3 * kAbMaxN * kAbKc * 2;
+    const size_t stage = 3 * kAbMaxN * kAbKc * 2;
     const int nK = (N * (N + 1) / 2 + kAbKc - 1) / kAbKc;
     const size_t ldi = ((size_t)Da + 3) / 4 * 4;
     return 1024 + kAbS * stage + 2 * (ldi + 4) * 12 + (size_t)kAbM * ab_tstride(nK) * 2;
