@@ -24,7 +24,7 @@
 // strings), padded to 64; K = N (N + 1) / 2 <= 136, padded to a multiple of 16.
 //
 // k_ab_tc: a persistent kernel over units (128-string alpha tile, partner row b').
-// Eight builder warps stage the b' row of X as bf16 pieces (written once per sigma by
+// Sixteen builder warps stage the b' row of X as bf16 pieces (written once per sigma by
 // the phase kernel: per amplitude three words (re_k | im_k << 16), k = 1..2..3;
 // asynchronous copies, one unit ahead), gather A for the tile's rows K = 16 at a time
 // through a per-tile table (partner offset | sign per row and kappa, rebuilt when the
@@ -33,7 +33,7 @@
 // where the MMAs read A; they copy the unit's B rows (pieces of a precomputed table)
 // into shared memory in the canonical no-swizzle K-major layout (core matrices of 8 rows
 // x 16 bytes);
-// lane 0 of warp 8 issues tcgen05.mma kind::f16 (six piece products per plane:
+// lane 0 of warp 16 issues tcgen05.mma kind::f16 (six piece products per plane:
 // float32-level accuracy) into one of two tensor-memory accumulators; four epilogue
 // warps (one per tensor-memory lane quarter) drain each finished accumulator into H
 // while the next unit is built.  Stage ring with full / empty mbarriers, accumulator
@@ -48,7 +48,8 @@ namespace svk {
 
 namespace {
 
-constexpr int kAbBuild = 256;                  // builder threads (8 warps): 2 per tile row
+constexpr int kAbBuild = 512;                  // builder threads (16 warps): 4 per tile row
+constexpr int kAbKpt = 4;                      // K entries of a stage per builder thread (16 / 4)
 constexpr int kAbEpi = 128;                    // epilogue threads (4 warps: one per tensor-memory lane quarter)
 constexpr int kAbThreadsTc = kAbBuild + 32 + kAbEpi;  // builders, the MMA warp, the epilogue warps
 constexpr int kAbM = 128;                      // alpha strings per tile
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
 
     if (warp < kAbBuild / 32) {
         // ------------------------------------------------------------ builders
-        const int r = tid & (kAbM - 1), hf = tid >> 7;  // tile row; which 8 of a stage's 16 K
+        const int r = tid & (kAbM - 1), hf = tid >> 7;  // tile row; which 4 of a stage's 16 K
         const int rowbytes = g.ldi * 12;                // a multiple of 16
         auto stage_row = [&](int u, int buf) {          // asynchronous copy of X row u % Db
             const uint8_t *src = reinterpret_cast<const uint8_t *>(g.Xi) + (size_t)(u % g.Db) * rowbytes;
@@ -240,15 +241,15 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
         int cur_tile = -1, it = 0, gch = 0;
         // this thread's share of the B copies: entries i = tid + 256 k of (piece, row, core
         // column); shared-memory offsets fixed, global rows set per unit
-        int bdst[2], bsel[2];
+        int bdst[1], bsel[1];
         #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 1; ++k) {
             const int i = tid + k * kAbBuild;
             bsel[k] = i < ncolsP * 6 ? i : -1;
             const int ii = bsel[k] < 0 ? 0 : i, piece = ii / (ncolsP * 2), rem = ii - piece * ncolsP * 2;
             bdst[k] = piece * (ncolsP * kAbKc * 2) + (int)ab_off(rem >> 1, rem & 1);
         }
-        const uint16_t *bsrc[2] = {g.Bp, g.Bp};
+        const uint16_t *bsrc[1] = {g.Bp};
         stage_row(blockIdx.x, 0);
         for (int u = blockIdx.x; u < g.units; u += gridDim.x, ++it) {
             const int atile = u / g.Db, bp = u - atile * g.Db, buf = it & 1;
@@ -259,13 +260,13 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
             if (atile != cur_tile) {
                 // the tile's table: per row and kappa, the word offset in a row buffer of the
                 // partner amplitude (3 J; 3 ldi, a zero amplitude, where the entry is zero)
-                // | sign << 14 (this thread: half hf of the row's entries)
+                // | sign << 14 (this thread: quarter hf of the row's entries)
                 cur_tile = atile;
                 const int Ia = atile * kAbM + r;
                 const bool valid = Ia < g.Da;
                 const uint32_t a = valid ? g.stra[Ia] : 0u, zero = (uint32_t)g.ldi * 3;
-                const int half = tstride / 2;
-                for (int k = hf * half; k < (hf + 1) * half; ++k) {
+                const int part = tstride / (kAbBuild / kAbM);
+                for (int k = hf * part; k < (hf + 1) * part; ++k) {
                     uint32_t e = zero;
                     if (valid && k < Ktot) {
                         const int p = s_kp[k], q = s_kq[k];
@@ -296,27 +297,27 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
             }
             builders_sync();
             #pragma unroll
-            for (int k = 0; k < 2; ++k) {
+            for (int k = 0; k < 1; ++k) {
                 const int ii = bsel[k] < 0 ? 0 : bsel[k], piece = ii / (ncolsP * 2), rem = ii - piece * ncolsP * 2;
                 bsrc[k] = g.Bp + (size_t)piece * g.pb + (size_t)s_rowB[rem >> 1] * 256 + (rem & 1) * 8;
             }
             const uint32_t *xr = xrow + (size_t)buf * xstride;
-            const uint16_t *trow = tbl + r * tstride + hf * 8;
+            const uint16_t *trow = tbl + r * tstride + hf * kAbKpt;
             for (int c = 0; c < g.nK; ++c, ++gch) {
                 const int s = gch % kAbS;
                 // B rows of this K block into registers (ncolsP rows x 2 core columns x 3 pieces)
-                uint4 bv[2];
+                uint4 bv[1];
                 #pragma unroll
-                for (int k = 0; k < 2; ++k)
+                for (int k = 0; k < 1; ++k)
                     if (bsel[k] >= 0) bv[k] = *reinterpret_cast<const uint4 *>(bsrc[k] + c * kAbKc);
                 // this thread's 8 K entries of row r: three words each (pieces 1..3, re | im << 16),
                 // sign bits flipped by the entry's sign
-                uint32_t w[8][3];
+                uint32_t w[kAbKpt][3];
                 {
-                    const uint4 tv = *reinterpret_cast<const uint4 *>(trow + c * kAbKc);
-                    const uint32_t te[4] = {tv.x, tv.y, tv.z, tv.w};
+                    const uint2 tv = *reinterpret_cast<const uint2 *>(trow + c * kAbKc);
+                    const uint32_t te[2] = {tv.x, tv.y};
                     #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
+                    for (int k = 0; k < kAbKpt; ++k) {
                         const uint32_t e = (k & 1) ? te[k >> 1] >> 16 : te[k >> 1] & 0xFFFFu;
                         const uint32_t *x = xr + (e & 0x3FFFu);
                         w[k][0] = x[0];
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                         w[k][2] = x[2];
                     }
                     #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
+                    for (int k = 0; k < kAbKpt; ++k) {
                         const uint32_t e = (k & 1) ? te[k >> 1] >> 16 : te[k >> 1] & 0xFFFFu;
                         const uint32_t flip = (e >> 14) * 0x80008000u;
                         w[k][0] ^= flip;
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                 if (gch >= kAbS && !s_fail && !ab_wait(su32(&empty[s]), (uint32_t)(((gch / kAbS) - 1) & 1)))
                     s_fail = 1;
                 uint8_t *st = ring + s * kStageBytes;
-                // A: this thread's row (its tensor-memory lane) and 8 K = 4 columns of each piece
+                // A: this thread's row (its tensor-memory lane) and 4 K = 2 columns of each piece
                 __syncwarp();
                 #pragma unroll
                 for (int pl = 0; pl < P; ++pl) {
@@ -346,15 +347,14 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                     #pragma unroll
                     for (int pc = 0; pc < 3; ++pc) {
                         const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
-                                            (uint32_t)(kAbABase + s * kAbAStage + (pl * 3 + pc) * kAbACols + hf * 4);
-                        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(ta),
-                                     "r"(__byte_perm(w[0][pc], w[1][pc], sel)), "r"(__byte_perm(w[2][pc], w[3][pc], sel)),
-                                     "r"(__byte_perm(w[4][pc], w[5][pc], sel)), "r"(__byte_perm(w[6][pc], w[7][pc], sel))
+                                            (uint32_t)(kAbABase + s * kAbAStage + (pl * 3 + pc) * kAbACols + hf * 2);
+                        asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(ta),
+                                     "r"(__byte_perm(w[0][pc], w[1][pc], sel)), "r"(__byte_perm(w[2][pc], w[3][pc], sel))
                                      : "memory");
                     }
                 }
                 #pragma unroll
-                for (int k = 0; k < 2; ++k)
+                for (int k = 0; k < 1; ++k)
                     if (bsel[k] >= 0) *reinterpret_cast<uint4 *>(st + bdst[k]) = bv[k];
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B, for the MMAs' reads
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");   // A written
