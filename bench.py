@@ -44,7 +44,7 @@ CONFIG_ID = 5
 # k_phase_planar, k_transpose_pieces, k_same_tc, k_sigma_ab, k_sigma_comb; form 5: the
 # same with k_ab_tc for k_sigma_ab and the gathering k_sigma_comb); None once a kernel
 # changes.
-SIGMA_TRAFFIC_BYTES = {4: 1555.6e6, 5: 12275.6e6}
+SIGMA_TRAFFIC_BYTES = {4: 1555.6e6, 5: 12283.4e6}
 SIGMA_KERNELS = {
     3: "expectation: k_sigma_ab + k_sigma_same (two launches)",
     4: "expectation: k_phase_planar + k_transpose_pieces + k_same_tc (same-spin products, tcgen05 bf16x3) "
