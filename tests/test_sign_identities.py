@@ -12,6 +12,7 @@ with PP = pp(a) ^ pp(b) (the orbital-order terms are folded into its integral ta
 import itertools
 
 import numpy as np
+import pytest
 
 
 def _par(v):
@@ -110,3 +111,114 @@ def test_blocked_basis_same_spin_signs():
                     blocked = jw ^ phi(a, b) ^ phi(a2, b2)
                     order = int(p1 < q2) ^ int(q2 < p2) ^ int(p1 < q1) ^ int(p2 < q1)
                     assert blocked == _par(_pp(own) & m) ^ order
+
+
+def _jw_ops(n):
+    """Annihilation operators a_j (j = 0..n-1, qubit j = bit j of the basis index) by the
+    Jordan-Wigner construction: Z on every qubit below j, sigma^- on qubit j."""
+    import scipy.sparse as sp
+    Z = sp.csr_matrix(np.diag([1.0, -1.0]))
+    I2 = sp.identity(2, format="csr")
+    lower = sp.csr_matrix(np.array([[0.0, 1.0], [0.0, 0.0]]))  # |0><1|: removes an occupation
+    ops = []
+    for j in range(n):
+        m = sp.identity(1, format="csr")
+        for k in range(n - 1, -1, -1):  # kron order: qubit n-1 first, so qubit k is bit k
+            m = sp.kron(m, lower if k == j else (Z if k < j else I2), format="csr")
+        ops.append(m)
+    return ops
+
+
+def _sym_eri(N, rng):
+    g = rng.normal(size=(N, N, N, N))
+    e = np.zeros_like(g)
+    for perm in ((0, 1, 2, 3), (1, 0, 2, 3), (0, 1, 3, 2), (1, 0, 3, 2),
+                 (2, 3, 0, 1), (3, 2, 0, 1), (2, 3, 1, 0), (3, 2, 1, 0)):
+        e += g.transpose(perm)
+    return e / 8.0
+
+
+@pytest.mark.parametrize("N,na,nb,seed", [(5, 2, 3, 21), (4, 4, 1, 22), (5, 3, 2, 23)])
+def test_blocked_basis_alpha_beta_products(N, na, nb, seed):
+    """Expectation variant 5 takes the alpha-beta part of H = sum (pq|rs) E^a_pq E^b_rs as
+    products in the string-blocked basis: with X = phi C,
+        H[b'][j][a] = sum_kappa A_b'[a][kappa] B[j][kappa]
+    over kappa = the orbitals p (A = X(a, b') if p in a) and the unordered pairs p < q
+    (A = s_a X(a ^ {p, q}, b') if exactly one of p, q is in a, s_a the parity of a's bits
+    between them), columns j = b''s excitations (s in b' -> r not in b', B = (qp|sr)) and an
+    own column (B = sum_{l in b'} (qp|ll), 0 on the diagonal); then
+        sigma~_ab(a, b) = sum_{r in b, s not in b} (-1)^popc(b & between(r, s)) H[b ^ {r, s}][col][a]
+                          + H[b][own][a],
+    sigma_ab = phi sigma~_ab + sum_{p in a, l in b} (pp|ll) C.  Checked against the operator
+    built from Jordan-Wigner fermion operators (interleaved spin-orbitals 2p + spin)."""
+    pytest.importorskip("scipy")
+    import math
+    rng = np.random.default_rng(seed)
+    n = 2 * N
+    eri = _sym_eri(N, rng)
+    strs_a = [s for s in range(1 << N) if bin(s).count("1") == na]
+    strs_b = [s for s in range(1 << N) if bin(s).count("1") == nb]
+    ra = {s: i for i, s in enumerate(strs_a)}
+    rb = {s: i for i, s in enumerate(strs_b)}
+    Da, Db = len(strs_a), len(strs_b)
+    assert (Da, Db) == (math.comb(N, na), math.comb(N, nb))
+    C = rng.normal(size=(Db, Da)) + 1j * rng.normal(size=(Db, Da))
+    # reference: the operator on the full 2^n space
+    psi = np.zeros(1 << n, dtype=complex)
+    for ib, b in enumerate(strs_b):
+        for ia, a in enumerate(strs_a):
+            psi[_spread(a, 0, N) | _spread(b, 1, N)] = C[ib, ia]
+    ann = _jw_ops(n)
+    cre = [m.T.tocsr() for m in ann]
+    ref = np.zeros_like(psi)
+    for r in range(N):
+        for s in range(N):
+            eb = cre[2 * r + 1] @ (ann[2 * s + 1] @ psi)  # E^b_rs psi
+            if not np.any(eb):
+                continue
+            for p in range(N):
+                for q in range(N):
+                    ref += eri[p, q, r, s] * (cre[2 * p] @ (ann[2 * q] @ eb))
+    # the decomposition
+    phi = np.array([[_par(a & _pp(b)) for a in strs_a] for b in strs_b])
+    X = np.where(phi == 1, -C, C)
+    kap = [(p, p) for p in range(N)] + [(p, q) for p in range(N) for q in range(p + 1, N)]
+    assert len(kap) == N * (N + 1) // 2
+    ncols = nb * (N - nb) + 1
+    H = np.zeros((Db, ncols, Da), dtype=complex)
+    for jb, bp in enumerate(strs_b):
+        occ = [o for o in range(N) if (bp >> o) & 1]
+        emp = [o for o in range(N) if not (bp >> o) & 1]
+        B = np.zeros((ncols, len(kap)))
+        for k, (p, q) in enumerate(kap):
+            for i, s in enumerate(occ):
+                for jj, r in enumerate(emp):
+                    B[i * len(emp) + jj, k] = eri[q, p, s, r]
+            if p != q:
+                B[ncols - 1, k] = sum(eri[q, p, l, l] for l in occ)
+        A = np.zeros((Da, len(kap)), dtype=complex)
+        for ia, a in enumerate(strs_a):
+            for k, (p, q) in enumerate(kap):
+                if p == q:
+                    if (a >> p) & 1:
+                        A[ia, k] = X[jb, ia]
+                elif ((a >> p) ^ (a >> q)) & 1:
+                    sgn = -1.0 if _par(a & _between(p, q)) else 1.0
+                    A[ia, k] = sgn * X[jb, ra[a ^ (1 << p) ^ (1 << q)]]
+        H[jb] = (A @ B.T).T
+    out = np.zeros_like(psi)
+    for ib, b in enumerate(strs_b):
+        occ = [o for o in range(N) if (b >> o) & 1]
+        emp = [o for o in range(N) if not (b >> o) & 1]
+        st = H[ib, ncols - 1].copy()
+        for r in occ:
+            for s in emp:
+                bp = b ^ (1 << r) ^ (1 << s)
+                col = bin(bp & ((1 << s) - 1)).count("1") * (N - nb) + \
+                    bin(~bp & ((1 << N) - 1) & ((1 << r) - 1)).count("1")
+                st += (-1.0 if _par(b & _between(r, s)) else 1.0) * H[rb[bp], col]
+        for ia, a in enumerate(strs_a):
+            d = sum(eri[p, p, l, l] for p in range(N) if (a >> p) & 1 for l in occ)
+            val = (-st[ia] if phi[ib, ia] else st[ia]) + d * C[ib, ia]
+            out[_spread(a, 0, N) | _spread(b, 1, N)] = val
+    assert np.max(np.abs(out - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
