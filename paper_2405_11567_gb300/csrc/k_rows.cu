@@ -26,13 +26,15 @@
 // The energy and norm are float64 sums per row, reduced in a fixed order; the
 // accumulation over the groups of one amplitude is in the state precision.
 //
-// Split form (default where the rows fit in shared memory): the alpha-beta doubles
-// -- 2,500 of the 3,500 connections of an amplitude at 30 qubits -- read their
-// partners at scattered columns of 50 other rows, which from L2 costs a 32-byte
-// sector per 8-byte amplitude.  k_sigma_ab stages those partner rows, K at a time,
-// in shared memory with coalesced loads and sums the alpha-beta part of sigma (and
-// its energy share); k_sigma_rows<SPLIT> then adds every other group, reading its
-// own row from shared memory, and completes sigma and the row's energy.
+// Split form (variant 3: float64 states and small sectors, where the rows fit in
+// shared memory): the alpha-beta doubles -- 2,500 of the 3,500 connections of an
+// amplitude at 30 qubits -- read their partners at scattered columns of 50 other rows,
+// which from L2 costs a 32-byte sector per 8-byte amplitude.  k_sigma_ab stages those
+// partner rows, K at a time, in shared memory with coalesced loads and sums the
+// alpha-beta part of sigma (and its energy share); k_sigma_same then adds every other
+// group and completes sigma and the row's energy.  Product forms (variants 4 and 5,
+// single-precision states of large sectors): below, "same-spin products", and
+// k_abtc.cu for the alpha-beta part.
 #include <cublas_v2.h>
 #include <cuda_bf16.h>
 
@@ -1124,8 +1126,10 @@ static cudaError_t launch_rows_t(const RowArgs<Amp> &A, const RowTables &T, int 
 
 // K: rows per chunk of the split form (sigma_ab_chunk), 0 for the single-kernel form.
 // partial must hold 3 * Db doubles (rows: energy, norm, alpha-beta energy share).
-// g (may be NULL): the same-spin products of variant 4 (single-precision states, K > 0):
-// launches the phase kernel, two cuBLAS products, k_sigma_ab and k_sigma_comb.
+// g (may be NULL): the product forms (single-precision states, K > 0): the phase kernel,
+// the same-spin products (k_transpose_pieces + k_same_tc, or two cuBLAS float32
+// products), then k_sigma_ab (variant 4) or k_ab_tc (variant 5, g->abtc), and
+// k_sigma_comb (which in variant 5 also gathers the alpha-beta planes).
 cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &T, const double *hdiag,
                               const double *Jp, double e_shift, double *partial, int K, cudaStream_t st,
                               const SameGemm *g, int sm_count) {
