@@ -792,17 +792,24 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
     g->tc = tc ? 1 : 0;
     g->err = h->kerr;
     g->abtc = 0;
-    if (abtc) {
-        // H [planes][Db][ncols][Da]
-        const int ncols = h->nb * (N - h->nb) + 1;
-        const size_t hplane = Db * (size_t)ncols * Da, hb = (size_t)planes * hplane * sizeof(float);
-        if (h->ab_H_bytes < hb) {
-            dev_free(h, h->ab_H, h->ab_H_bytes);
-            h->ab_H = nullptr;
-            h->ab_H_bytes = 0;
-            SV_TRY(dev_alloc(h, (void **)&h->ab_H, hb, "alpha-beta product planes"));
+    bool ab_ok = abtc;
+    const int ncols = h->nb * (N - h->nb) + 1;
+    const size_t hplane = Db * (size_t)ncols * Da, hb = (size_t)planes * hplane * sizeof(float);
+    if (ab_ok && h->ab_H_bytes < hb) {
+        // H [planes][Db][ncols][Da]; where the automatic choice cannot have it, variant 4 runs
+        dev_free(h, h->ab_H, h->ab_H_bytes);
+        h->ab_H = nullptr;
+        h->ab_H_bytes = 0;
+        const sv_status st = dev_alloc(h, (void **)&h->ab_H, hb, "alpha-beta product planes");
+        if (st != SV_OK && h->expect_variant != 0) return st;
+        if (st != SV_OK) {
+            cudaGetLastError();
+            ab_ok = false;
+        } else {
             h->ab_H_bytes = hb;
         }
+    }
+    if (ab_ok) {
         if (!h->kerr) {
             SV_TRY(dev_alloc(h, (void **)&h->kerr, 16, "kernel error flag"));
             SV_CUDA(h, cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream));
@@ -830,7 +837,7 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
     return SV_OK;
 }
 
-// After a stream synchronisation: a kernel whose bounded wait ran out (k_same_tc).
+// After a stream synchronisation: a kernel whose bounded wait ran out (k_same_tc, k_ab_tc).
 static sv_status check_kernel_flag(sv_handle h) {
     if (h->hkerr && *h->hkerr) {
         *h->hkerr = 0;
