@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(128) k_same_mats(SigmaTables<float> T, int Db,
     __shared__ uint8_t occ[kMaxOrb], emp[kMaxOrb];
     __shared__ int s_no, s_ne;
     const bool beta = (int)blockIdx.x >= T.Da;
-    const int I = beta ? (int)blockIdx.x - T.Da : (int)blockIdx.x, D = beta ? Db : T.Da, N = T.N, spin = beta;
+    const int I = beta ? (int)blockIdx.x - T.Da : (int)blockIdx.x, N = T.N, spin = beta;
     const uint16_t *rk = beta ? T.rb : T.ra;
     const uint32_t str = beta ? T.strb[I] : T.stra[I], pps = prefix_parity(str);
     float *row = (beta ? Mb : Ma) + (size_t)I * (beta ? ldb : lda);
