@@ -710,7 +710,7 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
 // Block I < Da builds alpha row I of Ma, block Da + I beta row I of Mb; thread 0 also
 // writes the string's one-spin diagonal energy sum_k h_kk + sum_{k<l} [kk|ll]-[kl|lk]
 // (spin-orbital tables hdiag, Jp) to dA / dB.  Ma and Mb must be zeroed before.
-__global__ void __launch_bounds__(128) k_same_mats(SigmaTables<float> T, int Db, float *__restrict__ Ma,
+__global__ void __launch_bounds__(128) k_same_mats(SigmaTables<float> T, float *__restrict__ Ma,
                                                     float *__restrict__ Mb, double *__restrict__ dA,
                                                     double *__restrict__ dB, int lda, int ldb) {
     __shared__ uint8_t occ[kMaxOrb], emp[kMaxOrb];
@@ -1147,7 +1147,7 @@ cudaError_t launch_same_mats(int n, const RowTables &T, const double *hdiag, con
     if (e == cudaSuccess) e = cudaMemsetAsync(Mb, 0, sizeof(float) * (size_t)T.Db * ldb, st);
     if (e != cudaSuccess) return e;
     RowArgs<float> A = row_args<float>(nullptr, nullptr, nullptr, n, T, hdiag, Jp, 0.0, nullptr);
-    k_same_mats<<<T.Da + T.Db, 128, 0, st>>>(A.T, T.Db, Ma, Mb, dA, dB, lda, ldb);
+    k_same_mats<<<T.Da + T.Db, 128, 0, st>>>(A.T, Ma, Mb, dA, dB, lda, ldb);
     return cudaGetLastError();
 }
 
