@@ -694,18 +694,20 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
 
 // ---------------------------------------------------------------- same-spin products
 //
-// Expectation variant 4 (single-precision states).  In the string-blocked basis
+// Expectation variants 4 and 5 (single-precision states).  In the string-blocked basis
 // (alpha creators before beta creators) the same-spin part of H is a matrix on one
 // string index times the identity on the other:
 //   Ma[a][a'] = alpha singles p -> q with h_qp + sum_{k in a} ((qp|kk) - (qk|kp)),
 //               and alpha-alpha doubles (q1p1|q2p2) - (q1p2|q2p1),
 // with the sign of the excitation on the alpha string alone; Mb likewise for beta.
 // So two dense products, G = Ma X + X Mb^T over the phased matrix X = phi C, give that
-// part of sigma~ = phi sigma.  The rest stays in k_sigma_ab (alpha-beta doubles, the
-// beta singles' dependence on a, and the alpha singles' dependence on b through the
-// row's own slot) and k_sigma_comb (diagonal, phase back, sum, energy).  The dense
-// products do every multiply of a matrix with 17% nonzeros at 30 qubits, but on the
-// FMA pipe at full rate instead of through scattered shared-memory gathers.
+// part of sigma~ = phi sigma.  The rest is the alpha-beta part (alpha-beta doubles, the
+// beta singles' dependence on a, and the alpha singles' dependence on b) -- k_sigma_ab
+// (variant 4, the latter through the row's own slot) or k_ab_tc (variant 5) -- and
+// k_sigma_comb (diagonal, phase back, sum, energy).  The dense products (k_same_tc on
+// the tensor cores, or cuBLAS float32) do every multiply of a matrix with 17% nonzeros
+// at 30 qubits, on a pipe whose rate repays it, instead of scattered shared-memory
+// gathers.
 
 // Block I < Da builds alpha row I of Ma, block Da + I beta row I of Mb; thread 0 also
 // writes the string's one-spin diagonal energy sum_k h_kk + sum_{k<l} [kk|ll]-[kl|lk]
