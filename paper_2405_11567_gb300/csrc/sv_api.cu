@@ -1521,22 +1521,24 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     SV_TRY(mark(h, 1));
     SV_TRY(forward(h, d, true));
     SV_TRY(mark(h, 2));
-    if (h->saved)
-        SV_CUDA(h, cudaMemcpyAsync(h->saved, h->psi, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
-    const double c = shift_for(h, ham);
-    SV_TRY(mark(h, 3));
-    SV_TRY(expectation(h, ham, T, h->lam, c, 0));
-    SV_TRY(mark(h, 4));
-    // reverse sweep
+    // The reverse sweep un-applies the ops to a working copy of psi(theta), so that psi
+    // keeps psi(theta): in sector storage without checkpoint resynchronisation, the
+    // interleaved (psi, lambda) matrix; else the saved-state buffer.  Where neither can be
+    // allocated under the byte cap, the sweep runs on psi and psi(theta) is recomputed.
     const int64_t C = h->ckpt_interval;
-    // sector storage without checkpoint resynchronisation: the sweep runs on the
-    // interleaved (psi, lambda) matrix, psi itself keeps psi(theta) (where the matrix
-    // cannot be allocated under the byte cap, the sweep runs on psi and lambda)
     bool inter = sect && C <= 0 && L > 0;
     if (inter && ensure_clbuf(h) != SV_OK) {
         cudaGetLastError();
         inter = false;
     }
+    void *wpsi = (!inter && h->saved) ? h->saved : h->psi;
+    if (wpsi != h->psi)
+        SV_CUDA(h, cudaMemcpyAsync(wpsi, h->psi, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    const double c = shift_for(h, ham);
+    SV_TRY(mark(h, 3));
+    SV_TRY(expectation(h, ham, T, h->lam, c, 0));
+    SV_TRY(mark(h, 4));
+    // reverse sweep
     if (inter) {
         SV_CUDA(h, launch_interleave(h->psi, h->lam, h->dtype, h->CLbuf, (size_t)h->Da * h->Db, h->sm_count,
                                      h->stream));
@@ -1551,29 +1553,27 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
         } else if (sect) {
             const uint32_t *LB = (const uint32_t *)h->lists.buf;
             const int *li = &h->lists.info[4 * kk];
-            SV_CUDA(h, launch_adjoint_l(h->psi, h->lam, h->dtype, LB + li[0], li[1], LB + li[2], li[3], h->Da,
+            SV_CUDA(h, launch_adjoint_l(wpsi, h->lam, h->dtype, LB + li[0], li[1], LB + li[2], li[3], h->Da,
                                         d[kk].c, d[kk].s, G, h->partials + kk * (size_t)G, h->stream));
         } else {
-            SV_CUDA(h, launch_adjoint(h->psi, h->lam, h->dtype, h->n, d[kk], G, h->partials + kk * (size_t)G,
+            SV_CUDA(h, launch_adjoint(wpsi, h->lam, h->dtype, h->n, d[kk], G, h->partials + kk * (size_t)G,
                                       h->stream));
         }
         h->launches++;
-        // psi now holds the state after ops[0..kk-1]; resynchronise from a checkpoint if one holds it
-        if (C > 0 && kk > 0 && kk % (size_t)C == 0) {
+        // the working copy now holds the state after ops[0..kk-1]; resynchronise it from a
+        // checkpoint if one holds it
+        if (!inter && C > 0 && kk > 0 && kk % (size_t)C == 0) {
             size_t j = kk / (size_t)C - 1;
             if (j < h->ckpt.size() && h->ckpt[j])
-                SV_CUDA(h, cudaMemcpyAsync(h->psi, h->ckpt[j], vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+                SV_CUDA(h, cudaMemcpyAsync(wpsi, h->ckpt[j], vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
         }
     }
     SV_CUDA(h, launch_reduce_rows(h->partials, (int)L, G, h->dout + 2, h->stream));
     h->launches++;
     SV_TRY(mark(h, 5));
     SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, (2 + L) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    // leave psi(theta) in the handle (the interleaved sweep left it there)
-    if (inter) {
-    } else if (h->saved) {
-        SV_CUDA(h, cudaMemcpyAsync(h->psi, h->saved, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
-    } else {
+    // leave psi(theta) in the handle (only a sweep on psi itself took it away)
+    if (!inter && wpsi == h->psi) {
         SV_TRY(prepare_reference(h));
         SV_TRY(forward(h, d, false));
     }
