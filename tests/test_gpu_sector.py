@@ -423,3 +423,23 @@ def test_expectation_degenerate_string_spaces(na, nb, variant):
         E, g = st.energy_grad(sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"]), p["ops"], theta)
         assert abs(E - Eref) <= TOL["c64"]["E"] and np.max(np.abs(g - gref)) <= TOL["c64"]["g"], storage
         assert np.max(np.abs(st.rdm1() - A.rdm1(sec, psi))) <= TOL["c64"]["rdm"], storage
+
+
+@pytest.mark.parametrize("variant", [3, 5])
+def test_sixteen_orbitals(variant):
+    """N = 16 spatial orbitals (32 qubits), the most the string tables and the tensor-core
+    alpha-beta form take (K = 16 orbitals + 120 pairs = 136: nine K blocks of 16, the last
+    partly padding), in sector storage from the Hartree-Fock state with a 24-operator
+    ansatz (2 + 2 electrons: 120 x 120 strings): energy and gradient match the oracle
+    within the complex64 tolerance, in the tensor-core form and in the split form."""
+    n, ne = 32, 4
+    p = inputs.make_problem(n, ne, 24, seed=3232)
+    sec = oracle.Sector(n, ne // 2, ne // 2)
+    psi0 = A.hf_state(sec, p["occ"])
+    theta = p["theta"] * 8
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
+    st = _state(n, ne // 2, ne // 2, "c64")
+    st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
+    st.prepare_hf(p["occ"])
+    E, g = st.energy_grad(sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"]), p["ops"], theta)
+    assert abs(E - Eref) <= TOL["c64"]["E"] and np.max(np.abs(g - gref)) <= TOL["c64"]["g"]
