@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Conventions (the readings of the paper listed in the design doc):
+Conventions (this implementation's readings where the paper is silent or ambiguous):
 
 * qubit j = spin-orbital j = 2p + sigma (sigma = 0 alpha, 1 beta); bit j of a
   basis index is its occupation (introduction; Methodology, Strategy 2, the
