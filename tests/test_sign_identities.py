@@ -222,3 +222,80 @@ def test_blocked_basis_alpha_beta_products(N, na, nb, seed):
             val = (-st[ia] if phi[ib, ia] else st[ia]) + d * C[ib, ia]
             out[_spread(a, 0, N) | _spread(b, 1, N)] = val
     assert np.max(np.abs(out - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("N,na,nb,seed", [(5, 2, 3, 31), (4, 1, 3, 32), (5, 3, 3, 33)])
+def test_blocked_basis_same_spin_products(N, na, nb, seed):
+    """Expectation variants 4 and 5 take the same-spin part of H as Ma (x) 1 + 1 (x) Mb in the
+    string-blocked basis (X = phi C; sigma~ = Ma X + X Mb^T), with
+        Ma[a][a - p + q] = s (h_qp + sum_{o in a} ((qp|oo) - (qo|op)))        singles p -> q,
+        Ma[a][a - p1 - p2 + q1 + q2] = s ((q1p1|q2p2) - (q1p2|q2p1))          doubles,
+        dA[a] = sum_{k in a} h_kk + sum_{k < l in a} ((kk|ll) - (kl|lk))      on the diagonal,
+    s = (-1)^(popc(pp(a) & m) + the orbital-order terms) from the string alone; Mb, dB
+    likewise.  Checked against the same-spin part of H built from Jordan-Wigner fermion
+    matrices: sum h_pq a+_p a_q + 1/2 sum (pq|rs) a+_p a+_r a_s a_q over spin-orbitals of
+    one spin, both spins."""
+    pytest.importorskip("scipy")
+    rng = np.random.default_rng(seed)
+    n = 2 * N
+    eri = _sym_eri(N, rng)
+    h = rng.normal(size=(N, N))
+    h = 0.5 * (h + h.T)
+    strs_a = [s for s in range(1 << N) if bin(s).count("1") == na]
+    strs_b = [s for s in range(1 << N) if bin(s).count("1") == nb]
+    Da, Db = len(strs_a), len(strs_b)
+    C = rng.normal(size=(Db, Da)) + 1j * rng.normal(size=(Db, Da))
+    psi = np.zeros(1 << n, dtype=complex)
+    for ib, b in enumerate(strs_b):
+        for ia, a in enumerate(strs_a):
+            psi[_spread(a, 0, N) | _spread(b, 1, N)] = C[ib, ia]
+    ann = _jw_ops(n)
+    cre = [m.T.tocsr() for m in ann]
+    ref = np.zeros_like(psi)
+    for spin in (0, 1):
+        for p in range(N):
+            for q in range(N):
+                ref += h[p, q] * (cre[2 * p + spin] @ (ann[2 * q + spin] @ psi))
+        for q in range(N):
+            for s in range(N):
+                t = ann[2 * s + spin] @ (ann[2 * q + spin] @ psi)
+                if not np.any(t):
+                    continue
+                for p in range(N):
+                    for r in range(N):
+                        ref += 0.5 * eri[p, q, r, s] * (cre[2 * p + spin] @ (cre[2 * r + spin] @ t))
+
+    def order(p1, p2, q1, q2):
+        return int(p1 < q2) ^ int(q2 < p2) ^ int(p1 < q1) ^ int(p2 < q1)
+
+    def one_spin(strs):
+        rank = {s: i for i, s in enumerate(strs)}
+        M = np.zeros((len(strs), len(strs)))
+        for i, a in enumerate(strs):
+            occ = [o for o in range(N) if (a >> o) & 1]
+            emp = [o for o in range(N) if not (a >> o) & 1]
+            M[i, i] = sum(h[k, k] for k in occ) + sum(eri[k, k, l, l] - eri[k, l, l, k]
+                                                    for k, l in itertools.combinations(occ, 2))
+            for p in occ:
+                for q in emp:
+                    m = (1 << p) | (1 << q)
+                    v = h[q, p] + sum(eri[q, p, o, o] - eri[q, o, o, p] for o in occ)
+                    sg = _par(_pp(a) & m) ^ int(p < q)
+                    M[i, rank[a ^ m]] = -v if sg else v
+            for p1, p2 in itertools.combinations(occ, 2):
+                for q1, q2 in itertools.combinations(emp, 2):
+                    m = (1 << p1) | (1 << p2) | (1 << q1) | (1 << q2)
+                    v = eri[q1, p1, q2, p2] - eri[q1, p2, q2, p1]
+                    sg = _par(_pp(a) & m) ^ order(p1, p2, q1, q2)
+                    M[i, rank[a ^ m]] = -v if sg else v
+        return M
+
+    Ma, Mb = one_spin(strs_a), one_spin(strs_b)
+    phi = np.array([[_par(a & _pp(b)) for a in strs_a] for b in strs_b])
+    X = np.where(phi == 1, -C, C)
+    G = X @ Ma.T + Mb @ X  # rows b, columns a: sum_a' Ma[a][a'] X[b][a'] + sum_b' Mb[b][b'] X[b'][a]
+    out = np.zeros_like(psi)
+    for ib, b in enumerate(strs_b):
+        for ia, a in enumerate(strs_a):
+            out[_spread(a, 0, N) | _spread(b, 1, N)] = -G[ib, ia] if phi[ib, ia] else G[ib, ia]
+    assert np.max(np.abs(out - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
