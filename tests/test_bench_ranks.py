@@ -89,3 +89,47 @@ def test_pool_pair_count_brute_force():
             cre = [int(op[3])] + ([int(op[4])] if op[0] == 2 else [])
             want += sum(1 for x in dets if all(x >> j & 1 for j in ann) and not any(x >> j & 1 for j in cre))
         assert bench.pool_pairs(pool, N, na, nb) == want
+
+
+def _pattern_count(xs, op):
+    """Amplitudes an excitation rotates among the basis indices xs: those holding its
+    annihilated spin-orbitals and not its created ones, and their partners."""
+    ann = [int(op[1])] + ([int(op[2])] if op[0] in (2, 4) else [])
+    cre = [int(op[3])] + ([int(op[4])] if op[0] in (2, 4) else [])
+    fwd = sum(1 for x in xs if all(x >> j & 1 for j in ann) and not any(x >> j & 1 for j in cre))
+    bwd = sum(1 for x in xs if all(x >> j & 1 for j in cre) and not any(x >> j & 1 for j in ann))
+    return fwd + bwd
+
+
+def test_touched_bytes_brute_force():
+    """bench.touched_bytes (the algorithmic bytes of the headline's rotation and adjoint
+    kernels: read + write of every amplitude a rotation pairs) against a count over all
+    2^n basis indices, for fermionic and qubit singles and doubles."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    n = 8
+    xs = range(1 << n)
+    ops = np.array([[1, 0, 0, 4, 0], [1, 3, 0, 7, 0], [2, 0, 2, 4, 6], [2, 1, 3, 5, 7], [2, 0, 1, 2, 3],
+                    [3, 2, 0, 6, 0], [4, 0, 1, 6, 7]], dtype=np.int32)
+    got = bench.touched_bytes(ops, n, 8)
+    want = [2 * _pattern_count(xs, op) * 8 for op in ops]
+    assert list(got) == want
+
+
+def test_sector_touched_bytes_brute_force():
+    """bench.sector_touched_bytes (the algorithmic bytes of the sector-storage rotation and
+    adjoint kernels) against a count over the sector's determinants."""
+    sys.path.insert(0, ROOT)
+    import itertools
+    import numpy as np
+    import bench
+    from paper_2405_11567_gb300 import inputs
+    for N, na, nb, ne_pool in [(5, 2, 1, 3), (4, 2, 2, 4), (6, 3, 2, 4), (5, 1, 3, 4)]:
+        sa = [sum(1 << (2 * q) for q in c) for c in itertools.combinations(range(N), na)]
+        sb = [sum(1 << (2 * q + 1) for q in c) for c in itertools.combinations(range(N), nb)]
+        dets = [a | b for a in sa for b in sb]
+        pool = inputs.uccsd_pool(2 * N, ne_pool)
+        got = bench.sector_touched_bytes(pool, N, na, nb, 8)
+        want = [2 * _pattern_count(dets, op) * 8 for op in pool]
+        assert list(got) == want
