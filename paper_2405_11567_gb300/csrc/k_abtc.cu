@@ -24,15 +24,15 @@
 // strings), padded to 64; K = N (N + 1) / 2 <= 136, padded to a multiple of 16.
 //
 // k_ab_tc: a persistent kernel over units (128-string alpha tile, partner row b').
-// Sixteen builder warps stage the b' row of X as bf16 pieces (written once per sigma by
-// the phase kernel: per amplitude three words (re_k | im_k << 16), k = 1..2..3;
-// asynchronous copies, one unit ahead), gather A for the tile's rows K = 16 at a time
-// through a per-tile table (partner offset | sign per row and kappa, rebuilt when the
-// tile changes), flipping sign bits and pairing halves only, and write it to tensor
-// memory (tcgen05.st: each builder warp its lane quarter, row = lane, two K per column),
-// where the MMAs read A; they copy the unit's B rows (pieces of a precomputed table)
-// into shared memory in the canonical no-swizzle K-major layout (core matrices of 8 rows
-// x 16 bytes);
+// Sixteen builder warps (four per tile row, four K each) stage the b' row of X as bf16
+// pieces (written once per sigma by the phase kernel: per amplitude three words
+// (re_k | im_k << 16), k = 1, 2, 3; asynchronous copies, one unit ahead), gather A for
+// the tile's rows K = 16 at a time through a per-tile table (partner offset | sign per
+// row and kappa, rebuilt when the tile changes), flipping sign bits and pairing halves
+// only, and write it to tensor memory (tcgen05.st: each builder warp its lane quarter,
+// row = lane, two K per column), where the MMAs read A; they copy the unit's B rows
+// (pieces of a precomputed table) into shared memory in the canonical no-swizzle
+// K-major layout (core matrices of 8 rows x 16 bytes);
 // lane 0 of warp 16 issues tcgen05.mma kind::f16 (six piece products per plane:
 // float32-level accuracy) into one of two tensor-memory accumulators; four epilogue
 // warps (one per tensor-memory lane quarter) drain each finished accumulator into H
