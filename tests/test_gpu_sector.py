@@ -443,3 +443,27 @@ def test_sixteen_orbitals(variant):
     st.prepare_hf(p["occ"])
     E, g = st.energy_grad(sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"]), p["ops"], theta)
     assert abs(E - Eref) <= TOL["c64"]["E"] and np.max(np.abs(g - gref)) <= TOL["c64"]["g"]
+
+
+def test_automatic_form_and_the_byte_cap():
+    """The automatic expectation form on a sector of 1.66 M determinants (26 qubits, 5 + 5
+    electrons, 1,287 strings per spin): the tensor-core alpha-beta form (variant 5,
+    bit-identical to choosing it) where its planes (2 x 1287 x 41 x 1287 floats, 543 MB)
+    fit, and variant 4 (bit-identical to choosing it) under a byte cap they do not fit."""
+    n, na, nb = 26, 5, 5
+    p = inputs.make_problem(n, 10, 12, seed=2626)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+
+    def energy(variant, cap=0):
+        st = _state(n, na, nb, "c64")
+        st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
+        if cap:
+            st.set_option(sv.SV_OPT_MAX_BYTES, cap)
+        st.prepare_hf(p["occ"])
+        st.apply_ansatz(p["ops"], p["theta"] * 5)
+        return st.energy(ham)
+
+    E4, E5 = energy(4), energy(5)
+    assert energy(0) == E5
+    assert energy(0, cap=400 << 20) == E4
+    assert abs(E4 - E5) <= TOL["c64"]["E"]
