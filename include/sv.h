@@ -331,8 +331,12 @@ typedef enum {
                                        doubles in a second kernel that stages partner rows
                                        in shared memory; 4 (single precision; float64
                                        states take 3): split, with the same-spin part as
-                                       two dense products (SV_OPT_SAME_PRODUCTS) in the
-                                       string-blocked basis, Ma X + X Mb^T; Ma, Mb are
+                                       two dense products in the string-blocked basis,
+                                       Ma X + X Mb^T, on the tensor cores (tcgen05 bf16
+                                       MMAs on operands split into three bf16 pieces, six
+                                       products: float32-level accuracy; TMA copies; a
+                                       bounded wait that runs out makes the next
+                                       synchronising call fail with SV_ERR_CUDA); Ma, Mb are
                                        built once per Hamiltonian and sector (4 (Da^2 +
                                        Db^2) bytes plus their bf16 pieces); 5 (single
                                        precision, N <= 16 spatial orbitals, at most 4096
@@ -363,20 +367,18 @@ typedef enum {
                                        2 pair lists: per-operator pair lists built once per
                                        pool (kept while the pool's operators are unchanged),
                                        amplitudes and lambda read interleaved */
-    SV_OPT_L2_FETCH = 12,           /* dense storage: before each sweep the handle sets the
-                                       CUDA context's maximum L2 fetch granularity
-                                       (cudaLimitMaxL2FetchGranularity) to this many bytes
-                                       (32, 64 or 128; default 32), and the context keeps
-                                       it; 0 leaves the context's value alone.  Rotations
-                                       of excitations on low address bits touch runs of
+    SV_OPT_L2_FETCH = 12            /* dense storage: while sv_apply_ansatz, sv_energy_grad
+                                       and sv_autotune run, the CUDA context's maximum L2
+                                       fetch granularity (cudaLimitMaxL2FetchGranularity,
+                                       a limit of the whole context) is this many bytes
+                                       (32, 64 or 128; default 32); each of those calls
+                                       puts the context's previous value back when it
+                                       returns (sv_apply_ansatz returns before its
+                                       kernels finish: the limit is a hint, so only
+                                       their speed can depend on when it changes back).
+                                       0 leaves the context's value alone.  Rotations of
+                                       excitations on low address bits touch runs of
                                        32-64 bytes, which larger fetches double */
-    SV_OPT_SAME_PRODUCTS = 13       /* expectation variant 4's two dense products: 0 auto
-                                       (= 2); 1 cuBLAS float32 on the FP32 pipe; 2 the
-                                       library's tensor-core kernel (tcgen05 bf16 MMAs on
-                                       operands split into three bf16 pieces, six
-                                       products: float32-level accuracy; TMA copies; a
-                                       bounded wait that runs out makes the next
-                                       synchronising call fail with SV_ERR_CUDA) */
 } sv_option;
 
 /* Options change launch choices or summation order only: results agree within the

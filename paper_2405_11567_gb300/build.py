@@ -66,8 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(cmds))) as ex:
         list(ex.map(run, cmds))
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cuda_lib = os.path.realpath(os.path.join(os.path.dirname(os.path.realpath(nvcc)), "..", "lib64"))
-    run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-L" + cuda_lib, "-lcublas", "-Xlinker", "-rpath=" + cuda_lib])
+    run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs)
     os.replace(tmp, LIB)
     return LIB
 

@@ -35,7 +35,6 @@
 // group and completes sigma and the row's energy.  Product forms (variants 4 and 5,
 // single-precision states of large sectors): below, "same-spin products", and
 // k_abtc.cu for the alpha-beta part.
-#include <cublas_v2.h>
 #include <cuda_bf16.h>
 
 #include "sv_internal.h"
@@ -705,7 +704,7 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
 // beta singles' dependence on a, and the alpha singles' dependence on b) -- k_sigma_ab
 // (variant 4, the latter through the row's own slot) or k_ab_tc (variant 5) -- and
 // k_sigma_comb (diagonal, phase back, sum, energy).  The dense products (k_same_tc on
-// the tensor cores, or cuBLAS float32) do every multiply of a matrix with 17% nonzeros
+// the tensor cores) do every multiply of a matrix with 17% nonzeros
 // at 30 qubits, on a pipe whose rate repays it, instead of scattered shared-memory
 // gathers.
 
@@ -791,8 +790,8 @@ __device__ __forceinline__ void bf16x3_u(float v, uint32_t &p1, uint32_t &p2, ui
 template <typename Amp>
 __global__ void __launch_bounds__(kThreads) k_phase_planar(const Amp *__restrict__ C, const uint16_t *__restrict__ stra,
                                                            const uint16_t *__restrict__ strb, int Da, int Db,
-                                                           float *__restrict__ X, int ld, uint16_t *__restrict__ Xp,
-                                                           size_t px, uint32_t *__restrict__ Xi, int ldi) {
+                                                           int ld, uint16_t *__restrict__ Xp, size_t px,
+                                                           uint32_t *__restrict__ Xi, int ldi) {
     const size_t plane = (size_t)ld * Db;  // rows padded to ld (the padding stays zero)
     for (int Ib = blockIdx.x; Ib < Db; Ib += gridDim.x) {
         const uint32_t ppb = prefix_parity(strb[Ib]);
@@ -801,13 +800,11 @@ __global__ void __launch_bounds__(kThreads) k_phase_planar(const Amp *__restrict
             const uint32_t neg = (uint32_t)par(stra[Ia] & ppb);
             const Amp c = C[off + Ia];
             const float xr = flip_sign<float>(re(c), neg);
-            if (Xp) bf16x3(xr, Xp + xo + Ia, px);
-            else X[xo + Ia] = xr;
+            bf16x3(xr, Xp + xo + Ia, px);
             float xi = 0.f;
             if constexpr (AmpT<Amp>::kCplx) {
                 xi = flip_sign<float>(im(c), neg);
-                if (Xp) bf16x3(xi, Xp + plane + xo + Ia, px);
-                else X[plane + xo + Ia] = xi;
+                bf16x3(xi, Xp + plane + xo + Ia, px);
             }
             if (Xi) {
                 uint32_t r1, r2, r3, i1, i2, i3;
@@ -1056,22 +1053,6 @@ cudaError_t launch_ab_tc(const uint32_t *Xi, int planes, const uint16_t *stra, c
                          const uint16_t *ra, const uint16_t *Bp, size_t pb, float *H, size_t hplane, int Da, int Db,
                          int N, int na, int nb, int *err, int sm_count, cudaStream_t st);
 
-// G = Ma X + X Mb^T on every plane (column-major views: X and G are Da x (planes Db),
-// Ma is Da x Da, Mb Db x Db; both symmetric).
-static cudaError_t same_products(const SameGemm &g, int Da, int Db) {
-    cublasHandle_t hb = (cublasHandle_t)g.blas;
-    const float one = 1.f, zero = 0.f;
-    const cublasComputeType_t ct = CUBLAS_COMPUTE_32F;
-    cublasStatus_t s = cublasGemmEx(hb, CUBLAS_OP_N, CUBLAS_OP_N, Da, g.planes * Db, Da, &one, g.Ma, CUDA_R_32F, g.lda,
-                                    g.X, CUDA_R_32F, g.lda, &zero, g.G, CUDA_R_32F, Da, ct, CUBLAS_GEMM_DEFAULT);
-    if (s != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    s = cublasGemmStridedBatchedEx(hb, CUBLAS_OP_N, CUBLAS_OP_N, Da, Db, Db, &one, g.X, CUDA_R_32F, g.lda,
-                                   (long long)g.lda * Db, g.Mb, CUDA_R_32F, g.ldb, 0, &one, g.G, CUDA_R_32F, Da,
-                                   (long long)Da * Db, g.planes, ct, CUBLAS_GEMM_DEFAULT);
-    if (s != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    return cudaGetLastError();
-}
-
 template <typename Amp>
 static cudaError_t launch_same_t(RowArgs<Amp> A, const RowTables &T, int dtype, int K, const SameGemm &g,
                                  int sm_count, cudaStream_t st) {
@@ -1079,13 +1060,11 @@ static cudaError_t launch_same_t(RowArgs<Amp> A, const RowTables &T, int dtype, 
         return cudaErrorInvalidValue;  // single-precision states only
     } else {
         const int grid = T.Db < sm_count * 8 ? T.Db : sm_count * 8;
-        k_phase_planar<Amp><<<grid, kThreads, 0, st>>>(A.C, T.stra, T.strb, T.Da, T.Db, g.X, g.lda,
-                                                       g.tc ? g.Xp : nullptr, g.px, g.abtc ? g.Xi : nullptr, g.ldi);
+        k_phase_planar<Amp><<<grid, kThreads, 0, st>>>(A.C, T.stra, T.strb, T.Da, T.Db, g.lda, g.Xp, g.px,
+                                                       g.abtc ? g.Xi : nullptr, g.ldi);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        e = g.tc ? launch_same_tc(g.Mp, g.pm, g.Xp, g.px, g.Xtp, g.pt, g.G, g.planes, T.Da, T.Db, g.lda, g.ldb, g.err,
-                                  st)
-                 : same_products(g, T.Da, T.Db);
+        e = launch_same_tc(g.Mp, g.pm, g.Xp, g.px, g.Xtp, g.pt, g.G, g.planes, T.Da, T.Db, g.lda, g.ldb, g.err, st);
         if (e != cudaSuccess) return e;
         A.same_gemm = 1;
         if (g.abtc) {
@@ -1129,8 +1108,7 @@ static cudaError_t launch_rows_t(const RowArgs<Amp> &A, const RowTables &T, int 
 // K: rows per chunk of the split form (sigma_ab_chunk), 0 for the single-kernel form.
 // partial must hold 3 * Db doubles (rows: energy, norm, alpha-beta energy share).
 // g (may be NULL): the product forms (single-precision states, K > 0): the phase kernel,
-// the same-spin products (k_transpose_pieces + k_same_tc, or two cuBLAS float32
-// products), then k_sigma_ab (variant 4) or k_ab_tc (variant 5, g->abtc), and
+// the same-spin products (k_transpose_pieces + k_same_tc), then k_sigma_ab (variant 4) or k_ab_tc (variant 5, g->abtc), and
 // k_sigma_comb (which in variant 5 also gathers the alpha-beta planes).
 cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &T, const double *hdiag,
                               const double *Jp, double e_shift, double *partial, int K, cudaStream_t st,

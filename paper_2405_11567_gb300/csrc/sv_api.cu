@@ -6,7 +6,6 @@
 // path itself runs in the kernels of k_state.cu (rotations, adjoint sweep),
 // k_rows.cu and k_expect.cu (expectation), k_rdm.cu, k_pool.cu and k_sector.cu
 // (sector storage).
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -561,15 +560,32 @@ static sv_status ensure_op_lists(sv_handle h, const std::vector<OpDesc> &ops, Op
 }
 
 // Dense sweeps touch runs as short as one amplitude: a 32-byte maximum L2 fetch
-// granularity (a limit of the CUDA context, so it stays in force for the context's
-// later work) keeps the L2 from fetching larger blocks around runs of 32 or 64 bytes.
-// A hint: a refusal is ignored.
-static void set_l2_fetch(sv_handle h) {
-    if (h->storage != 0 || h->l2_fetch <= 0) return;
-    size_t cur = 0;
-    if (cudaDeviceGetLimit(&cur, cudaLimitMaxL2FetchGranularity) == cudaSuccess && cur == (size_t)h->l2_fetch) return;
-    if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)h->l2_fetch) != cudaSuccess) cudaGetLastError();
-}
+// granularity keeps the L2 from fetching larger blocks around runs of 32 or 64 bytes.
+// The granularity is a limit of the whole CUDA context, so the entry points that run
+// dense sweeps set the handle's value for the duration of the call and put the
+// context's previous value back when they return (a hint: a refusal is ignored).
+struct L2FetchScope {
+    size_t prev = 0;
+    bool restore = false;
+    explicit L2FetchScope(sv_handle h) {
+        if (h->storage != 0 || h->l2_fetch <= 0) return;
+        if (cudaDeviceGetLimit(&prev, cudaLimitMaxL2FetchGranularity) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        if (prev == (size_t)h->l2_fetch) return;
+        if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)h->l2_fetch) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        restore = true;
+    }
+    ~L2FetchScope() {
+        if (restore && cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, prev) != cudaSuccess) cudaGetLastError();
+    }
+    L2FetchScope(const L2FetchScope &) = delete;
+    L2FetchScope &operator=(const L2FetchScope &) = delete;
+};
 
 // The 1-RDM's alpha-pair lists: for each orbital pair p < q (in (p, q) order) the alpha
 // strings holding q but not p with their partners (q -> p) and the parity of their alpha
@@ -597,7 +613,6 @@ static sv_status ensure_rdm_lists(sv_handle h) {
 
 static sv_status forward(sv_handle h, const std::vector<OpDesc> &ops, bool checkpoints) {
     const int64_t C = h->ckpt_interval;
-    set_l2_fetch(h);
     if (h->storage == 1 && !ops.empty()) SV_TRY(ensure_op_lists(h, ops, h->lists));
     const uint32_t *L = (const uint32_t *)h->lists.buf;
     const int G = sector_grid(h->Db, h->sm_count, h->sect_bps);
@@ -678,39 +693,21 @@ static bool use_ab_tc(sv_handle h) {
 }
 
 // The same-spin matrices of the table set and sector (built on first use, kept until
-// either changes), the work planes, and for the cuBLAS form its handle on the
-// handle's stream.  Rows of Ma, X and of Mb, Xt are padded to a multiple of 8
-// elements with zeros (16-byte row strides of the bf16 pieces, as TMA requires).
+// either changes) and the work planes.  Rows of Ma, X and of Mb, Xt are padded to a
+// multiple of 8 elements with zeros (16-byte row strides of the bf16 pieces, as TMA
+// requires).
 static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R, SameGemm *g) {
-    const bool tc = h->same_products != 1;
-    if (!tc) {
-        if (!h->blas) {
-            cublasHandle_t hb = nullptr;
-            if (cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS) return fail(h, SV_ERR_CUDA, "cublasCreate failed");
-            h->blas = hb;
-            const size_t ws = (size_t)32 << 20;
-            SV_TRY(dev_alloc(h, &h->blas_ws, ws, "cuBLAS workspace"));
-            h->blas_ws_bytes = ws;
-            if (cublasSetWorkspace(hb, h->blas_ws, ws) != CUBLAS_STATUS_SUCCESS)
-                return fail(h, SV_ERR_CUDA, "cublasSetWorkspace failed");
+    if (!h->kerr) {
+        SV_TRY(dev_alloc(h, (void **)&h->kerr, 16, "kernel error flag"));
+        SV_CUDA(h, cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream));
+    }
+    if (!h->hkerr) {
+        if (cudaMallocHost((void **)&h->hkerr, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            h->hkerr = nullptr;
+            return fail(h, SV_ERR_OOM, "pinned host allocation failed");
         }
-        if (cublasSetStream((cublasHandle_t)h->blas, h->stream) != CUBLAS_STATUS_SUCCESS)
-            return fail(h, SV_ERR_CUDA, "cublasSetStream failed");
-        if (cublasSetMathMode((cublasHandle_t)h->blas, CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS)
-            return fail(h, SV_ERR_CUDA, "cublasSetMathMode failed");
-    } else {
-        if (!h->kerr) {
-            SV_TRY(dev_alloc(h, (void **)&h->kerr, 16, "kernel error flag"));
-            SV_CUDA(h, cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream));
-        }
-        if (!h->hkerr) {
-            if (cudaMallocHost((void **)&h->hkerr, sizeof(int)) != cudaSuccess) {
-                cudaGetLastError();
-                h->hkerr = nullptr;
-                return fail(h, SV_ERR_OOM, "pinned host allocation failed");
-            }
-            *h->hkerr = 0;
-        }
+        *h->hkerr = 0;
     }
     const size_t Da = (size_t)h->Da, Db = (size_t)h->Db, lda = (Da + 7) / 8 * 8, ldb = (Db + 7) / 8 * 8;
     // [Ma | Mb] (float32), the one-spin diagonals, then the three bf16 pieces of [Ma | Mb]
@@ -749,18 +746,16 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
     const int planes = is_complex(h->dtype) ? 2 : 1;
     // X [planes][Db][lda], G [planes][Db][Da], Xt [planes][Da][ldb] (tensor-core form)
     // (each region rounded to 256 bytes: aligned starts for vector loads and TMA)
-    // cuBLAS form: X float32 [planes][Db][lda]; tensor-core form: its three bf16 pieces
-    // and those of the transposes [planes][Da][ldb]; then G float32 [planes][Db][Da]
+    // the three bf16 pieces of X and those of the transposes [planes][Da][ldb]; then G
+    // float32 [planes][Db][Da]
     const size_t nx = (size_t)planes * Db * lda, nt = (size_t)planes * Da * ldb, ng = (size_t)planes * Db * Da;
     auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t xb = tc ? r256(3 * nx * sizeof(uint16_t)) : r256(nx * sizeof(float)),
-                 tb = tc ? r256(3 * nt * sizeof(uint16_t)) : 0;
+    const size_t xb = r256(3 * nx * sizeof(uint16_t)), tb = r256(3 * nt * sizeof(uint16_t));
     // variant 5: then the phased amplitudes as interleaved bf16 pieces [Db][ldi][3] words
     const bool abtc = use_ab_tc(h) && rowsB;
     const size_t ldi = ab_xi_ld((int)Da), gb = r256(ng * sizeof(float)), ib = abtc ? r256(Db * ldi * 12) : 0;
     const size_t need = xb + tb + gb + ib;
-    const uint64_t geom = ((uint64_t)Da << 32) | ((uint64_t)Db << 3) | ((uint64_t)planes << 2) | (abtc ? 2u : 0u) |
-                          (tc ? 1u : 0u);
+    const uint64_t geom = ((uint64_t)Da << 32) | ((uint64_t)Db << 3) | ((uint64_t)planes << 2) | (abtc ? 2u : 0u);
     if (h->sg_buf_bytes < need || h->sg_buf_geom != geom) {
         if (h->sg_buf_bytes < need) {
             dev_free(h, h->sg_buf, h->sg_buf_bytes);
@@ -779,17 +774,14 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
     uint8_t *B = (uint8_t *)h->sg_buf;
     g->Mp = (const uint16_t *)((const uint8_t *)h->sg_mats + sof);
     g->pm = nm;
-    g->X = tc ? nullptr : (float *)B;
-    g->Xp = tc ? (uint16_t *)B : nullptr;
+    g->Xp = (uint16_t *)B;
     g->px = nx;
-    g->Xtp = tc ? (uint16_t *)(B + xb) : nullptr;
+    g->Xtp = (uint16_t *)(B + xb);
     g->pt = nt;
     g->G = (float *)(B + xb + tb);
-    g->blas = h->blas;
     g->planes = planes;
     g->lda = (int)lda;
     g->ldb = (int)ldb;
-    g->tc = tc ? 1 : 0;
     g->err = h->kerr;
     g->abtc = 0;
     bool ab_ok = abtc;
@@ -810,18 +802,6 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
         }
     }
     if (ab_ok) {
-        if (!h->kerr) {
-            SV_TRY(dev_alloc(h, (void **)&h->kerr, 16, "kernel error flag"));
-            SV_CUDA(h, cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream));
-        }
-        if (!h->hkerr) {
-            if (cudaMallocHost((void **)&h->hkerr, sizeof(int)) != cudaSuccess) {
-                cudaGetLastError();
-                h->hkerr = nullptr;
-                return fail(h, SV_ERR_OOM, "pinned host allocation failed");
-            }
-            *h->hkerr = 0;
-        }
         g->abtc = 1;
         g->Xi = (uint32_t *)(B + xb + tb + gb);
         g->ldi = (int)ldi;
@@ -858,8 +838,8 @@ static sv_status sigma_rows(sv_handle h, DevTables *T, const RowTables &R, const
     if (sg) SV_TRY(ensure_same_gemm(h, T, R, &g));
     SV_CUDA(h, launch_sigma_rows(C, lam, lamc, h->dtype, h->n, R, T->hdiag, T->Jp, e_shift, h->partials, K,
                                  h->stream, sg ? &g : nullptr, h->sm_count));
-    h->launches += sg ? (g.tc ? 5 : 3) : (K ? 2 : 1);  // cuBLAS's own kernels are not counted
-    if (sg && (g.tc || g.abtc))
+    h->launches += sg ? 5 : (K ? 2 : 1);
+    if (sg)
         SV_CUDA(h, cudaMemcpyAsync(h->hkerr, h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     return SV_OK;
 }
@@ -1228,8 +1208,6 @@ sv_status sv_destroy(sv_handle h) {
     dev_free(h, h->ab_H, h->ab_H_bytes);
     dev_free(h, h->kerr, 16);
     if (h->hkerr) cudaFreeHost(h->hkerr);
-    dev_free(h, h->blas_ws, h->blas_ws_bytes);
-    if (h->blas) cublasDestroy((cublasHandle_t)h->blas);
     dev_free(h, h->lists.buf, h->lists.bytes);
     dev_free(h, h->pool_lists.buf, h->pool_lists.bytes);
     dev_free(h, h->rdm_lists.buf, h->rdm_lists.bytes);
@@ -1452,6 +1430,7 @@ sv_status sv_apply_ansatz(sv_handle h, const sv_excitation *ops, int n_ops, cons
     std::vector<OpDesc> d;
     SV_TRY(build_ops(h, ops, n_ops, theta, d));
     DeviceGuard g(h->device);
+    L2FetchScope l2(h);
     SV_TRY(forward(h, d, false));
     return SV_OK;
 }
@@ -1481,6 +1460,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     std::vector<OpDesc> d;
     SV_TRY(build_ops(h, ops, n_ops, theta, d));  // validates in any layout
     DeviceGuard g(h->device);
+    L2FetchScope l2(h);
     if (h->layout_auto && n_ops > 0 && h->storage == 0) {
         int np[32];
         layout_from_ops(h->n, ops, n_ops, np);
@@ -1754,6 +1734,7 @@ sv_status sv_autotune(sv_handle h, sv_ham_handle ham, const sv_excitation *ops, 
     std::vector<OpDesc> d;
     SV_TRY(build_ops(h, ops, n_ops, theta, d));
     DeviceGuard g(h->device);
+    L2FetchScope l2(h);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     SV_CUDA(h, cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1782,7 +1763,6 @@ sv_status sv_get_option(sv_handle h, sv_option opt, int64_t *value) {
         case SV_OPT_RDM_BLOCKS_PER_SM: *value = h->rdm_bps; return SV_OK;
         case SV_OPT_POOL_VARIANT: *value = h->pool_variant; return SV_OK;
         case SV_OPT_L2_FETCH: *value = h->l2_fetch; return SV_OK;
-        case SV_OPT_SAME_PRODUCTS: *value = h->same_products; return SV_OK;
     }
     return fail(h, SV_ERR_ARG, "unknown option");
 }
@@ -1837,10 +1817,6 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
         case SV_OPT_RDM_VARIANT:
             if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "rdm variant must be 0, 1 or 2");
             h->rdm_variant = (int)value;
-            return SV_OK;
-        case SV_OPT_SAME_PRODUCTS:
-            if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "same-spin product form must be 0, 1 or 2");
-            h->same_products = (int)value;
             return SV_OK;
         case SV_OPT_L2_FETCH:
             if (value != 0 && value != 32 && value != 64 && value != 128)

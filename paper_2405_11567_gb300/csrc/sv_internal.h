@@ -120,16 +120,14 @@ struct HostTables {
 struct SameGemm {
     const float *Ma = nullptr, *Mb = nullptr;  // [Da][Da], [Db][Db], symmetric
     const double *dA = nullptr, *dB = nullptr; // one-spin diagonal energies per string (float64)
-    float *X = nullptr, *G = nullptr;          // phased psi [planes][Db][lda], same-spin sigma~ [planes][Db][Da]
-    // tensor-core form: every operand as three bf16 pieces at a piece stride: [Ma | Mb]
-    // (Mp, pm), the phased planes (Xp, px), their transposes [planes][Da][ldb] (Xtp, pt)
+    float *G = nullptr;                        // same-spin sigma~ [planes][Db][Da]
+    // every operand as three bf16 pieces at a piece stride: [Ma | Mb] (Mp, pm), the
+    // phased planes [planes][Db][lda] (Xp, px), their transposes [planes][Da][ldb] (Xtp, pt)
     const uint16_t *Mp = nullptr;
     uint16_t *Xp = nullptr, *Xtp = nullptr;
     size_t pm = 0, px = 0, pt = 0;
-    void *blas = nullptr;                      // cublasHandle_t on the handle's stream
     int planes = 2;                            // 2 complex (re, im), 1 real
     int lda = 0, ldb = 0;                      // row strides of Ma / X and Mb / Xt: D rounded up to 4, zero padded
-    int tc = 0;                                // 1: the products on the tensor cores (k_same_tc), 0: cuBLAS float32
     int *err = nullptr;                        // device flag set by k_same_tc / k_ab_tc when a wait runs out
     // variant 5: the alpha-beta part on the tensor cores (k_ab_tc) into planes H
     // [planes][Db][ncols][Da] (hplane floats apart), gathered by k_sigma_comb; Bp: the
@@ -272,12 +270,11 @@ struct sv_ctx {
     int rdm_bps = 4;           // k_rdm_rows
     int rdm_variant = 0;
     int pool_variant = 0;      // 0 auto (= 2); 1 string scan; 2 pair lists
-    int l2_fetch = 32;         // context L2 fetch granularity set before dense sweeps (0: leave it)
-    int same_products = 0;     // variant 4's products: 0 auto (= 2), 1 cuBLAS float32, 2 tensor cores (bf16x3)
+    int l2_fetch = 32;         // context L2 fetch granularity during dense sweeps (0: leave it)
     int *kerr = nullptr;       // device flag of kernels with bounded waits (k_same_tc, k_ab_tc)
     int *hkerr = nullptr;      // its pinned host copy, checked after stream synchronisations
     // same-spin products (expectation variant 4): matrices for one table set and sector,
-    // the phased-psi / product planes, and the cuBLAS handle with its workspace
+    // and the phased-psi / product planes
     void *sg_mats = nullptr;
     size_t sg_mats_bytes = 0;
     uint64_t sg_serial = 0;
@@ -287,9 +284,6 @@ struct sv_ctx {
     uint64_t sg_buf_geom = 0;  // the planes' geometry (their row padding is zeroed when it changes)
     float *ab_H = nullptr;     // variant 5: the alpha-beta product planes
     size_t ab_H_bytes = 0;
-    void *blas = nullptr;
-    void *blas_ws = nullptr;
-    size_t blas_ws_bytes = 0;
     // storage layout: address bit perm[q] holds qubit q (identity by default);
     // layout_auto: sv_energy_grad picks it from its operator list
     int perm[32];

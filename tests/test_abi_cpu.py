@@ -38,6 +38,20 @@ def test_library_built_for_sm_103a_only():
     assert "arch=compute_103a,code=sm_103a" in " ".join(libbuild.ARCH)
 
 
+def test_library_needs_no_blas(cabi):
+    """Every product on the path is the library's own kernel: the shared library's
+    dynamic section names no cuBLAS / cuBLASLt dependency."""
+    import shutil
+    import subprocess
+    readelf = shutil.which("readelf")
+    if readelf is None:
+        pytest.skip("readelf not available")
+    out = subprocess.run([readelf, "-d", libbuild.LIB], capture_output=True, text=True, check=True).stdout
+    needed = re.findall(r"\(NEEDED\)\s+Shared library: \[([^\]]+)\]", out)
+    assert needed, out
+    assert not [x for x in needed if "blas" in x.lower()], needed
+
+
 def test_ham_create_validates_on_host(cabi):
     N = 3
     rng = np.random.default_rng(0)

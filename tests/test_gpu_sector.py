@@ -179,12 +179,11 @@ def test_pool_gradients_match_oracle(dtype, tol, variant):
 
 
 @pytest.mark.parametrize("variant", [4, 5])
-@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("storage", ["sector", "dense"])
-def test_same_spin_products_match_oracle(storage, form, variant):
+def test_same_spin_products_match_oracle(storage, variant):
     """Expectation variant 4 (same-spin part as two dense products in the string-blocked
-    basis; form 1 cuBLAS float32, form 2 the tensor-core kernel on bf16x3 operands;
-    variant 5 also the alpha-beta part as tensor-core products) on an open-shell complex
+    basis, on the tensor cores with bf16x3 operands; variant 5 also the alpha-beta part
+    as tensor-core products) on an open-shell complex
     start: energy, gradient and pool gradients within the complex64 tolerance, and reruns
     bit-identical."""
     n, na, nb = 16, 3, 4
@@ -197,7 +196,6 @@ def test_same_spin_products_match_oracle(storage, form, variant):
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
     st = sv.StateVector(n, "c64", sector=(na, nb) if storage == "sector" else None)
     st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
-    st.set_option(sv.SV_OPT_SAME_PRODUCTS, form)
     runs = []
     for _ in range(2):
         st.prepare_state(dense0.astype(np.complex64), na, nb)
@@ -219,7 +217,8 @@ def test_same_spin_products_several_tiles(variant):
     both directions (D_alpha = 330: three 128-row tiles, the last 74 rows; D_beta = 462:
     two 256-column tiles, the last 206) and K blocks of 32 with a ragged last block, on
     an open-shell complex start: energy and gradient match the oracle within the
-    complex64 tolerance in both product forms, and the forms agree to rounding.  Variant
+    complex64 tolerance, and agree to rounding with the split gather form (variant 3,
+    no products on the tensor cores).  Variant
     5 adds the alpha-beta products over the same three alpha tiles (units of one tile and
     one partner row: 3 x 462, spread over the SMs with a ragged last round)."""
     n, na, nb = 22, 4, 5
@@ -232,15 +231,15 @@ def test_same_spin_products_several_tiles(variant):
     Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
     out = {}
-    for form in (1, 2):
+    for v in (3, variant):
         st = _state(n, na, nb, "c64")
-        st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
-        st.set_option(sv.SV_OPT_SAME_PRODUCTS, form)
+        st.set_option(sv.SV_OPT_EXPECT_VARIANT, v)
         st.prepare_state(dense0.astype(np.complex64), na, nb)
         E, g = st.energy_grad(ham, p["ops"], theta)
-        assert abs(E - Eref) <= TOL["c64"]["E"] and np.max(np.abs(g - gref)) <= TOL["c64"]["g"], form
-        out[form] = (E, g)
-    assert abs(out[1][0] - out[2][0]) <= TOL["c64"]["E"]
+        assert abs(E - Eref) <= TOL["c64"]["E"] and np.max(np.abs(g - gref)) <= TOL["c64"]["g"], v
+        out[v] = (E, g)
+    assert abs(out[3][0] - out[variant][0]) <= TOL["c64"]["E"]
+    assert np.max(np.abs(out[3][1] - out[variant][1])) <= TOL["c64"]["g"]
 
 
 def _applies_in(sec, op):
