@@ -367,7 +367,7 @@ typedef enum {
                                        2 pair lists: per-operator pair lists built once per
                                        pool (kept while the pool's operators are unchanged),
                                        amplitudes and lambda read interleaved */
-    SV_OPT_L2_FETCH = 12            /* dense storage: while sv_apply_ansatz, sv_energy_grad
+    SV_OPT_L2_FETCH = 12,           /* dense storage: while sv_apply_ansatz, sv_energy_grad
                                        and sv_autotune run, the CUDA context's maximum L2
                                        fetch granularity (cudaLimitMaxL2FetchGranularity,
                                        a limit of the whole context) is this many bytes
@@ -379,6 +379,15 @@ typedef enum {
                                        0 leaves the context's value alone.  Rotations of
                                        excitations on low address bits touch runs of
                                        32-64 bytes, which larger fetches double */
+    SV_OPT_REVERSE_INTERLEAVED = 14 /* dense storage: 1 (default) sv_energy_grad runs its
+                                       reverse sweep on psi(theta) and lambda interleaved
+                                       by amplitude in one buffer (element x holds psi[x]
+                                       then lambda[x]), so an excitation's touched runs
+                                       are twice as long as in two separate vectors; used
+                                       where the handle's adjoint vector and working copy
+                                       are one allocation (not with a caller-provided
+                                       adjoint vector, checkpoints or the record-scan
+                                       expectation); 0 two separate vectors */
 } sv_option;
 
 /* Options change launch choices or summation order only: results agree within the

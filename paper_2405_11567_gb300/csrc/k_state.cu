@@ -167,6 +167,17 @@ template <> struct VecIOr<4> {
     }
 };
 
+template <> struct VecIOr<8> {
+    static __device__ __forceinline__ void ld(const float *__restrict__ p, float (&v)[8]) {
+        const float4 f = reinterpret_cast<const float4 *>(p)[0], g = reinterpret_cast<const float4 *>(p)[1];
+        v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w; v[4] = g.x; v[5] = g.y; v[6] = g.z; v[7] = g.w;
+    }
+    static __device__ __forceinline__ void st(float *__restrict__ p, const float (&v)[8]) {
+        reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+};
+
 template <int V> __device__ __forceinline__ void ld_vec(const float2 *__restrict__ p, float2 (&v)[V]) { VecIO<float, V>::ld(p, v); }
 template <int V> __device__ __forceinline__ void ld_vec(const double2 *__restrict__ p, double2 (&v)[V]) { VecIO<double, V>::ld(p, v); }
 template <int V> __device__ __forceinline__ void ld_vec(const float *__restrict__ p, float (&v)[V]) { VecIOr<V>::ld(p, v); }
@@ -239,6 +250,32 @@ __global__ void __launch_bounds__(kThreads) k_rotate(A *__restrict__ psi, uint32
 
 // ---------------------------------------------------------------- adjoint step
 
+// One pair of the adjoint step: adds the pair's term of Re <lambda|G psi> to t and
+// applies U^dagger to (u, v) (psi) and (lu, lv) (lambda).  <lambda|G psi> on the pair:
+// conj(lu) (-s v) + conj(lv) (s u), real part.  U^dagger: psi'[x] = c u + s sn v,
+// psi'[x'] = c v - s sn u (lambda alike), the forward rotation with the sign of the
+// angle flipped.
+template <typename A>
+__device__ __forceinline__ void adjoint_pair(A &u, A &v, A &lu, A &lv, bool neg, real_of<A> c, real_of<A> sn,
+                                             real_of<A> th, bool shear, real_of<A> &t) {
+    using R = real_of<A>;
+    if constexpr (sizeof(R) == 8) {
+        // float64: the product terms chained into t by multiply-adds (sign on the
+        // lambda operand), four per complex pair instead of six
+        t = fma(neg_if(re(lv), neg), re(u), t);
+        t = fma(neg_if(re(lu), !neg), re(v), t);
+        if constexpr (AmpT<A>::kCplx) {
+            t = fma(neg_if(im(lv), neg), im(u), t);
+            t = fma(neg_if(im(lu), !neg), im(v), t);
+        }
+    } else {
+        const R ti = re_dot(lv, u) - re_dot(lu, v);
+        t += neg ? -ti : ti;
+    }
+    rotate_pair<A>(u, v, !neg, c, sn, th, shear);
+    rotate_pair<A>(lu, lv, !neg, c, sn, th, shear);
+}
+
 template <typename A, int NB, int V>
 __global__ void __launch_bounds__(kThreads) k_adjoint(A *__restrict__ psi, A *__restrict__ lam,
                                                       uint32_t ngroups, OpArgs a, double *__restrict__ partial) {
@@ -257,27 +294,8 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(A *__restrict__ psi, A *__
         ld_vec<V>(lam + xp, lv);
         R t = 0;
         #pragma unroll
-        for (int i = 0; i < V; ++i) {
-            const bool neg = __popc((x + i) & a.sm) & 1;
-            // <lambda|G psi> on the pair: conj(lu) (-s v) + conj(lv) (s u); real part.
-            // U^dagger: psi'[x] = c u + s sn v ; psi'[x'] = c v - s sn u  (lambda alike),
-            // the forward rotation with the sign of the angle flipped.
-            if constexpr (sizeof(R) == 8) {
-                // float64: the product terms chained into t by multiply-adds (sign on the
-                // lambda operand), four per complex pair instead of six
-                t = fma(neg_if(re(lv[i]), neg), re(u[i]), t);
-                t = fma(neg_if(re(lu[i]), !neg), re(v[i]), t);
-                if constexpr (AmpT<A>::kCplx) {
-                    t = fma(neg_if(im(lv[i]), neg), im(u[i]), t);
-                    t = fma(neg_if(im(lu[i]), !neg), im(v[i]), t);
-                }
-            } else {
-                const R ti = re_dot(lv[i], u[i]) - re_dot(lu[i], v[i]);
-                t += neg ? -ti : ti;
-            }
-            rotate_pair<A>(u[i], v[i], !neg, c, sn, th, shear);
-            rotate_pair<A>(lu[i], lv[i], !neg, c, sn, th, shear);
-        }
+        for (int i = 0; i < V; ++i)
+            adjoint_pair<A>(u[i], v[i], lu[i], lv[i], (__popc((x + i) & a.sm) & 1) != 0, c, sn, th, shear, t);
         acc += (double)t;
         st_vec<V>(psi + x, u);
         st_vec<V>(psi + xp, v);
@@ -286,6 +304,88 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(A *__restrict__ psi, A *__
     }
     double s = block_sum(acc, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// ---------------------------------------------------------------- adjoint step, interleaved
+
+// The same step on one buffer holding psi and lambda interleaved by amplitude,
+// cl[2x] = psi[x], cl[2x + 1] = lambda[x].  A touched run of 2^b amplitudes is then
+// one run of 2^(b+1) words instead of one run of 2^b in each of two vectors, so an
+// excitation whose lowest address bit is b moves runs twice as long: HBM moves
+// 32-byte sectors, runs of 8 or 16 bytes use half of each, and runs of 128 bytes or
+// more stream at about the copy rate.  Two groups of V pairs per iteration (four
+// vector loads in flight per thread).
+template <typename A, int NB, int V>
+__global__ void __launch_bounds__(kThreads) k_adjoint_i(A *__restrict__ cl, uint32_t ngroups, OpArgs a,
+                                                        double *__restrict__ partial) {
+    using R = real_of<A>;
+    __shared__ double red[kThreads / 32];
+    const R c = (R)a.c, sn = (R)a.s, th = (R)a.t;
+    const bool shear = a.shear != 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    double acc = 0.0;
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += 2 * stride) {
+        const uint32_t g2 = g + stride;
+        const bool two = g2 < ngroups;
+        const uint32_t x = pair_index<NB>(g * V, a), x2 = two ? pair_index<NB>(g2 * V, a) : x;
+        A *const p = cl + 2 * (size_t)x, *const q = cl + 2 * (size_t)(x ^ a.m);
+        A *const p2 = cl + 2 * (size_t)x2, *const q2 = cl + 2 * (size_t)(x2 ^ a.m);
+        A u[2 * V], v[2 * V], u2[2 * V], v2[2 * V];
+        ld_vec<2 * V>(p, u);
+        ld_vec<2 * V>(q, v);
+        if (two) {
+            ld_vec<2 * V>(p2, u2);
+            ld_vec<2 * V>(q2, v2);
+        }
+        R t = 0;
+        #pragma unroll
+        for (int i = 0; i < V; ++i)
+            adjoint_pair<A>(u[2 * i], v[2 * i], u[2 * i + 1], v[2 * i + 1], (__popc((x + i) & a.sm) & 1) != 0, c,
+                            sn, th, shear, t);
+        acc += (double)t;
+        st_vec<2 * V>(p, u);
+        st_vec<2 * V>(q, v);
+        if (two) {
+            R t2 = 0;
+            #pragma unroll
+            for (int i = 0; i < V; ++i)
+                adjoint_pair<A>(u2[2 * i], v2[2 * i], u2[2 * i + 1], v2[2 * i + 1],
+                                (__popc((x2 + i) & a.sm) & 1) != 0, c, sn, th, shear, t2);
+            acc += (double)t2;
+            st_vec<2 * V>(p2, u2);
+            st_vec<2 * V>(q2, v2);
+        }
+    }
+    double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// cl[2x] = psi[x], cl[2x + 1] = 0 for every x (two amplitudes per thread and step:
+// one 16- or 32-byte load, one 32- or 64-byte store).
+template <typename A>
+__global__ void __launch_bounds__(kThreads) k_interleave_zero(const A *__restrict__ psi, A *__restrict__ cl,
+                                                              uint64_t pairs) {
+    const A z = mka<A>(real_of<A>(0), real_of<A>(0));
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < pairs;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        A u[2], w[4];
+        ld_vec<2>(psi + 2 * t, u);
+        w[0] = u[0]; w[1] = z; w[2] = u[1]; w[3] = z;
+        st_vec<4>(cl + 4 * t, w);
+    }
+}
+
+// The odd words of the interleaved buffer at the sector's storage addresses:
+// cl[2 (sa_s[a] | sb_s[b]) + 1] = lamc[b Da + a] (one block per beta string).
+template <typename A>
+__global__ void __launch_bounds__(kThreads) k_scatter_odd(const A *__restrict__ lamc, A *__restrict__ cl,
+                                                          const uint32_t *__restrict__ sa_s,
+                                                          const uint32_t *__restrict__ sb_s, int Da, int Db) {
+    for (int Ib = blockIdx.x; Ib < Db; Ib += gridDim.x) {
+        const uint32_t xb = sb_s[Ib];
+        const A *row = lamc + (size_t)Ib * Da;
+        for (int Ia = threadIdx.x; Ia < Da; Ia += blockDim.x) cl[2 * (size_t)(sa_s[Ia] | xb) + 1] = row[Ia];
+    }
 }
 
 // ---------------------------------------------------------------- layout change
@@ -408,6 +508,53 @@ cudaError_t launch_adjoint(void *psi, void *lam, int dtype, int n, const OpDesc 
     int v = vec_log2(dtype, d, n);
     SV_DISPATCH_AMP(dtype, if (d.nbits == 2) adj_v<A, 2>(psi, lam, v, npairs, a, grid, partial, st);
                            else adj_v<A, 4>(psi, lam, v, npairs, a, grid, partial, st));
+    return cudaGetLastError();
+}
+
+// Interleaved adjoint step: V elements (psi, lambda pairs) per vector access, at most
+// 32 bytes, limited as for the separate vectors by the lowest mask position.
+static int vec_log2_i(int dtype, const OpDesc &d, int n) {
+    const int ebytes = 2 * (int)amp_size(dtype);
+    int vmax = ebytes >= 32 ? 0 : ebytes == 16 ? 1 : 2;
+    int v = d.pos[0] < vmax ? d.pos[0] : vmax;
+    while (v > 0 && (n - d.nbits) < v) --v;
+    return v;
+}
+
+template <typename A, int NB>
+static void adj_i_v(void *cl, int v, uint32_t npairs, OpArgs a, int grid, double *partial, cudaStream_t st) {
+    uint32_t ng = npairs >> v;
+    if (v == 0) k_adjoint_i<A, NB, 1><<<grid, kThreads, 0, st>>>((A *)cl, ng, a, partial);
+    else if (v == 1) k_adjoint_i<A, NB, 2><<<grid, kThreads, 0, st>>>((A *)cl, ng, a, partial);
+    else {
+        if constexpr (sizeof(A) == 4) k_adjoint_i<A, NB, 4><<<grid, kThreads, 0, st>>>((A *)cl, ng, a, partial);
+    }
+}
+
+// `grid` blocks write partial[0 .. grid); the caller gives every op the same grid.
+cudaError_t launch_adjoint_i(void *cl, int dtype, int n, const OpDesc &d, int grid, double *partial,
+                             cudaStream_t st) {
+    OpArgs a = to_args(d);
+    uint32_t npairs = (uint32_t)(1ull << (n - d.nbits));
+    int v = vec_log2_i(dtype, d, n);
+    SV_DISPATCH_AMP(dtype, if (d.nbits == 2) adj_i_v<A, 2>(cl, v, npairs, a, grid, partial, st);
+                           else adj_i_v<A, 4>(cl, v, npairs, a, grid, partial, st));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interleave_zero(const void *psi, void *cl, int dtype, int n, int sm_count, cudaStream_t st) {
+    const uint64_t pairs = 1ull << (n - 1);
+    uint64_t want = (pairs + kThreads - 1) / kThreads, cap = (uint64_t)sm_count * 16;
+    const int grid = (int)(want < cap ? want : cap);
+    SV_DISPATCH_AMP(dtype, k_interleave_zero<A><<<grid, kThreads, 0, st>>>((const A *)psi, (A *)cl, pairs));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_odd(const void *lamc, void *cl, int dtype, const uint32_t *sa_s, const uint32_t *sb_s,
+                               int Da, int Db, int sm_count, cudaStream_t st) {
+    if (Da <= 0 || Db <= 0) return cudaSuccess;
+    const int grid = Db < sm_count * 8 ? Db : sm_count * 8;
+    SV_DISPATCH_AMP(dtype, k_scatter_odd<A><<<grid, kThreads, 0, st>>>((const A *)lamc, (A *)cl, sa_s, sb_s, Da, Db));
     return cudaGetLastError();
 }
 

@@ -24,6 +24,10 @@ cudaError_t launch_rotate(void *psi, int dtype, int n, const OpDesc &d, int sm_c
 cudaError_t launch_adjoint(void *psi, void *lam, int dtype, int n, const OpDesc &d, int grid,
                            double *partial, cudaStream_t st);
 cudaError_t launch_reduce_rows(const double *partials, int rows, int cols, double *out, cudaStream_t st);
+cudaError_t launch_adjoint_i(void *cl, int dtype, int n, const OpDesc &d, int grid, double *partial, cudaStream_t st);
+cudaError_t launch_interleave_zero(const void *psi, void *cl, int dtype, int n, int sm_count, cudaStream_t st);
+cudaError_t launch_scatter_odd(const void *lamc, void *cl, int dtype, const uint32_t *sa_s, const uint32_t *sb_s,
+                               int Da, int Db, int sm_count, cudaStream_t st);
 int expect_gather_grid(uint64_t count, int sm_count);
 cudaError_t launch_expect_gather(const void *psi, void *sigma, int dtype, int n, const uint32_t *sector,
                                  uint64_t count, const DevTables &T, double e_shift, int grid,
@@ -181,10 +185,37 @@ static sv_status ensure_clbuf(sv_handle h) {
     return SV_OK;
 }
 
+// The adjoint vector.  Dense storage: lam and the reverse sweep's working copy of
+// psi(theta) (`saved`) in one allocation, lam first, so that the sweep can also run on
+// the two interleaved by amplitude in the same bytes (k_adjoint_i); where two vectors
+// do not fit, lam alone (and `saved` separately, if at all).
 static sv_status ensure_lam(sv_handle h) {
     if (h->lam) return SV_OK;
+    if (h->storage == 0 && !h->saved) {
+        void *p = nullptr;
+        if (dev_alloc(h, &p, 2 * vec_bytes(h), "adjoint vector and working copy") == SV_OK) {
+            h->lam = p;
+            h->own_lam = true;
+            h->lam_pair = true;
+            h->saved = (uint8_t *)p + vec_bytes(h);
+            return SV_OK;
+        }
+        cudaGetLastError();
+    }
     SV_TRY(dev_alloc(h, &h->lam, vec_bytes(h), "adjoint vector"));
     h->own_lam = true;
+    return SV_OK;
+}
+
+// Compact sigma [Db][Da] (sector-sized).
+static sv_status ensure_lbuf(sv_handle h) {
+    const size_t cb = std::max<size_t>((size_t)h->Da * h->Db * h->amp_bytes, 16);
+    if (h->Lbuf_bytes >= cb) return SV_OK;
+    dev_free(h, h->Lbuf, h->Lbuf_bytes);
+    h->Lbuf = nullptr;
+    h->Lbuf_bytes = 0;
+    SV_TRY(dev_alloc(h, &h->Lbuf, cb, "compact sigma"));
+    h->Lbuf_bytes = cb;
     return SV_OK;
 }
 
@@ -846,8 +877,11 @@ static sv_status sigma_rows(sv_handle h, DevTables *T, const RowTables &R, const
 
 // Expectation pass over the current state: writes the float64 sums of
 // <psi|(H - c)|psi> and <psi|psi> into dout[out_off], dout[out_off + 1] (device),
-// and sigma = (H - c) psi into `sigma` when it is not NULL.
-static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void *sigma, double c, int out_off) {
+// and sigma = (H - c) psi into `sigma` when it is not NULL (a state-sized vector), or,
+// for dense storage with the string-row forms, into the compact [Db][Da] matrix
+// `sigma_c` when that is not NULL.
+static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void *sigma, double c, int out_off,
+                             void *sigma_c = nullptr) {
     if (h->storage == 1) {
         // the state is already the compact matrix; sigma is compact too (every entry written)
         SV_TRY(ensure_strings(h));
@@ -863,13 +897,14 @@ static sv_status expectation(sv_handle h, sv_ham_handle ham, DevTables *T, void 
         // string rows (default)
         SV_TRY(ensure_strings(h));
         SV_TRY(ensure_partials(h, 3 * (size_t)h->Db));
+        if (sigma_c) sigma = nullptr;
         if (sigma) SV_CUDA(h, cudaMemsetAsync(sigma, 0, vec_bytes(h), h->stream));
         SV_CUDA(h, launch_compact(h->psi, h->Cbuf, h->dtype, h->str_sa_s, h->str_sb_s, h->Da, h->Db, h->sm_count,
                                   h->stream));
         h->launches++;
         RowTables R{h->str_sa, h->str_sb, h->str_sa_s, h->str_sb_s, h->str_a, h->str_b, h->rank_a, h->rank_b,
                     T->eri_r, T->hm_r, T->Dt, T->Jt, h->n / 2, h->Da, h->Db, T->W2};
-        SV_TRY(sigma_rows(h, T, R, h->Cbuf, sigma, nullptr, ham->e_nuc - c));
+        SV_TRY(sigma_rows(h, T, R, h->Cbuf, sigma, sigma_c, ham->e_nuc - c));
         SV_CUDA(h, launch_reduce_rows(h->partials, 2, h->Db, h->dout + out_off, h->stream));
         h->launches++;
         return SV_OK;
@@ -1050,10 +1085,15 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
                     return SV_OK;
                 });
             } else {
+                // the adjoint step as sv_energy_grad runs it: interleaved in the pair buffer
+                // (its two halves hold copies of psi, read here as interleaved pairs) or not
+                const bool dint = h->lam_pair && h->rev_inter && h->ckpt_interval <= 0;
                 const int G = rotate_grid(1ull << (h->n - 2), h->sm_count, b);
                 t = time_best(h, e0, e1, [&]() -> sv_status {
                     SV_CUDA(h, launch_rotate(h->lam, h->dtype, h->n, d[k], h->sm_count, b, h->stream));
-                    if (adj) SV_CUDA(h, launch_adjoint(h->lam, h->saved, h->dtype, h->n, d[k], G, h->partials, h->stream));
+                    if (dint) SV_CUDA(h, launch_adjoint_i(h->lam, h->dtype, h->n, d[k], G, h->partials, h->stream));
+                    else if (adj)
+                        SV_CUDA(h, launch_adjoint(h->lam, h->saved, h->dtype, h->n, d[k], G, h->partials, h->stream));
                     return SV_OK;
                 });
             }
@@ -1193,9 +1233,9 @@ sv_status sv_destroy(sv_handle h) {
     cudaStreamSynchronize(h->stream);
     cudaGetLastError();
     if (h->own_psi) dev_free(h, h->psi, vec_bytes(h));
-    if (h->own_lam) dev_free(h, h->lam, vec_bytes(h));
+    if (h->own_lam) dev_free(h, h->lam, h->lam_pair ? 2 * vec_bytes(h) : vec_bytes(h));
     dev_free(h, h->ref_vec, vec_bytes(h));
-    dev_free(h, h->saved, vec_bytes(h));
+    if (!h->lam_pair) dev_free(h, h->saved, vec_bytes(h));
     for (void *p : h->ckpt) dev_free(h, p, vec_bytes(h));
     dev_free(h, h->sector, h->sector_len * sizeof(uint32_t));
     for (void *p : {(void *)h->str_sa, (void *)h->str_sb, (void *)h->str_sa_s, (void *)h->str_sb_s,
@@ -1511,12 +1551,32 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
         cudaGetLastError();
         inter = false;
     }
-    void *wpsi = (!inter && h->saved) ? h->saved : h->psi;
+    // dense storage: psi(theta) and lambda interleaved by amplitude in the adjoint pair
+    // buffer (k_adjoint_i), where it exists, checkpoints do not resynchronise the working
+    // copy and sigma comes from the string-row forms (compact, then scattered)
+    bool dint = !sect && C <= 0 && L > 0 && h->lam_pair && h->rev_inter &&
+                !(h->expect_variant == 1 && is_complex(h->dtype));
+    if (dint && ensure_lbuf(h) != SV_OK) {
+        cudaGetLastError();
+        dint = false;
+    }
+    void *wpsi = (!inter && !dint && h->saved) ? h->saved : h->psi;
     if (wpsi != h->psi)
         SV_CUDA(h, cudaMemcpyAsync(wpsi, h->psi, vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    if (dint) {  // lam[2x] = psi[x], lam[2x + 1] = 0: the copy and the zeroing of lambda in one pass
+        SV_CUDA(h, launch_interleave_zero(h->psi, h->lam, h->dtype, h->n, h->sm_count, h->stream));
+        h->launches++;
+    }
     const double c = shift_for(h, ham);
     SV_TRY(mark(h, 3));
-    SV_TRY(expectation(h, ham, T, h->lam, c, 0));
+    if (dint) {
+        SV_TRY(expectation(h, ham, T, nullptr, c, 0, h->Lbuf));
+        SV_CUDA(h, launch_scatter_odd(h->Lbuf, h->lam, h->dtype, h->str_sa_s, h->str_sb_s, h->Da, h->Db, h->sm_count,
+                                      h->stream));
+        h->launches++;
+    } else {
+        SV_TRY(expectation(h, ham, T, h->lam, c, 0));
+    }
     SV_TRY(mark(h, 4));
     // reverse sweep
     if (inter) {
@@ -1535,6 +1595,8 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
             const int *li = &h->lists.info[4 * kk];
             SV_CUDA(h, launch_adjoint_l(wpsi, h->lam, h->dtype, LB + li[0], li[1], LB + li[2], li[3], h->Da,
                                         d[kk].c, d[kk].s, G, h->partials + kk * (size_t)G, h->stream));
+        } else if (dint) {
+            SV_CUDA(h, launch_adjoint_i(h->lam, h->dtype, h->n, d[kk], G, h->partials + kk * (size_t)G, h->stream));
         } else {
             SV_CUDA(h, launch_adjoint(wpsi, h->lam, h->dtype, h->n, d[kk], G, h->partials + kk * (size_t)G,
                                       h->stream));
@@ -1542,7 +1604,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
         h->launches++;
         // the working copy now holds the state after ops[0..kk-1]; resynchronise it from a
         // checkpoint if one holds it
-        if (!inter && C > 0 && kk > 0 && kk % (size_t)C == 0) {
+        if (!inter && !dint && C > 0 && kk > 0 && kk % (size_t)C == 0) {
             size_t j = kk / (size_t)C - 1;
             if (j < h->ckpt.size() && h->ckpt[j])
                 SV_CUDA(h, cudaMemcpyAsync(wpsi, h->ckpt[j], vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
@@ -1553,7 +1615,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     SV_TRY(mark(h, 5));
     SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, (2 + L) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     // leave psi(theta) in the handle (only a sweep on psi itself took it away)
-    if (!inter && wpsi == h->psi) {
+    if (!inter && !dint && wpsi == h->psi) {
         SV_TRY(prepare_reference(h));
         SV_TRY(forward(h, d, false));
     }
@@ -1601,14 +1663,7 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
     DevTables *T;
     SV_TRY(get_tables(h, ham, &T));
     SV_TRY(ensure_strings(h));
-    const size_t cb = (size_t)h->Da * h->Db * h->amp_bytes;
-    if (h->Lbuf_bytes < cb) {
-        dev_free(h, h->Lbuf, h->Lbuf_bytes);
-        h->Lbuf = nullptr;
-        h->Lbuf_bytes = 0;
-        SV_TRY(dev_alloc(h, &h->Lbuf, std::max<size_t>(cb, 16), "compact sigma"));
-        h->Lbuf_bytes = std::max<size_t>(cb, 16);
-    }
+    SV_TRY(ensure_lbuf(h));
     if (use_lists && n_pool > 0) {
         SV_TRY(ensure_op_lists(h, descs, h->pool_lists));
         SV_TRY(ensure_clbuf(h));
@@ -1763,6 +1818,7 @@ sv_status sv_get_option(sv_handle h, sv_option opt, int64_t *value) {
         case SV_OPT_RDM_BLOCKS_PER_SM: *value = h->rdm_bps; return SV_OK;
         case SV_OPT_POOL_VARIANT: *value = h->pool_variant; return SV_OK;
         case SV_OPT_L2_FETCH: *value = h->l2_fetch; return SV_OK;
+        case SV_OPT_REVERSE_INTERLEAVED: *value = h->rev_inter; return SV_OK;
     }
     return fail(h, SV_ERR_ARG, "unknown option");
 }
@@ -1817,6 +1873,10 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
         case SV_OPT_RDM_VARIANT:
             if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "rdm variant must be 0, 1 or 2");
             h->rdm_variant = (int)value;
+            return SV_OK;
+        case SV_OPT_REVERSE_INTERLEAVED:
+            if (value != 0 && value != 1) return fail(h, SV_ERR_ARG, "reverse-sweep interleaving must be 0 or 1");
+            h->rev_inter = (int)value;
             return SV_OK;
         case SV_OPT_L2_FETCH:
             if (value != 0 && value != 32 && value != 64 && value != 128)

@@ -271,6 +271,8 @@ struct sv_ctx {
     int rdm_variant = 0;
     int pool_variant = 0;      // 0 auto (= 2); 1 string scan; 2 pair lists
     int l2_fetch = 32;         // context L2 fetch granularity during dense sweeps (0: leave it)
+    int rev_inter = 1;         // dense reverse sweep on psi and lambda interleaved (k_adjoint_i) where it can
+    bool lam_pair = false;     // lam's allocation holds two vectors: lam, then the working copy `saved`
     int *kerr = nullptr;       // device flag of kernels with bounded waits (k_same_tc, k_ab_tc)
     int *hkerr = nullptr;      // its pinned host copy, checked after stream synchronisations
     // same-spin products (expectation variant 4): matrices for one table set and sector,

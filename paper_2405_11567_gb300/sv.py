@@ -33,6 +33,7 @@ SV_OPT_AB_CHUNK = 7
 SV_OPT_ROT_BLOCKS_PER_SM, SV_OPT_SECT_BLOCKS_PER_SM, SV_OPT_RDM_BLOCKS_PER_SM = 8, 9, 10
 SV_OPT_POOL_VARIANT = 11
 SV_OPT_L2_FETCH = 12
+SV_OPT_REVERSE_INTERLEAVED = 14
 SV_PHASES = 6
 PHASE_NAMES = ("reference", "forward", "expectation", "reverse", "restore", "rdm1")
 STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV_ERR_TIMEOUT", 5: "SV_ERR_STATE"}

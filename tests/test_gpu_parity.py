@@ -465,3 +465,49 @@ def test_qubit_excitation_ansatz_matches_oracle(dtype):
     b = sv.Batch([dict(p, ops=ops, theta=theta)], dtype)
     Eb, gb = b.energy_grad(theta)
     assert abs(Eb[0] - Eref) <= TOL[dtype]["E"] and np.max(np.abs(gb[0] - gref)) <= TOL[dtype]["g"]
+
+
+@pytest.mark.parametrize("layout", ["identity", "auto"])
+@pytest.mark.parametrize("dtype", ["c128", "c64", "r64", "r32"])
+def test_reverse_sweep_interleaved_and_separate(dtype, layout):
+    """The dense reverse sweep on psi(theta) and lambda interleaved in one buffer
+    (SV_OPT_REVERSE_INTERLEAVED = 1, the default) and on two separate vectors (0): both
+    match the oracle's energy and gradient, agree with each other to rounding, and leave
+    psi(theta) in the handle.  With the identity layout the ansatz's excitations sit on
+    address bits 0, 1, 2 and above, so every vector width of the interleaved kernel runs
+    (one, two and, for real float32, four pairs per access); a complex open-shell start
+    for the complex types, the closed-shell HF start (real) for the real ones."""
+    n, ne = 12, 5
+    p = inputs.make_problem(n, ne, 60, seed=515)
+    theta = p["theta"] * 6
+    na, nb = 3, 2
+    sec = oracle.Sector(n, na, nb)
+    if dtype.startswith("c"):
+        dense0 = inputs.random_sector_state(n, na, nb, np.random.default_rng(12))
+    else:
+        dense0 = np.zeros(1 << n)
+        dense0[sum(1 << j for j in (0, 1, 2, 3, 4))] = 1.0
+    psi0 = dense0[sec.dets.astype(np.int64)]
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
+    psi_ref = A.apply_ansatz(sec, p["ops"], theta, psi0)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    tol = TOL["c128" if dtype in ("c128", "r64") else "c64"]
+    npdt = {"c128": np.complex128, "c64": np.complex64, "r64": np.float64, "r32": np.float32}[dtype]
+    out = {}
+    for inter in (1, 0):
+        st = sv.StateVector(n, dtype)
+        if layout == "identity":
+            st.set_option(sv.SV_OPT_LAYOUT_AUTO, 0)
+        st.set_option(sv.SV_OPT_REVERSE_INTERLEAVED, inter)
+        assert st.option(sv.SV_OPT_REVERSE_INTERLEAVED) == inter
+        st.prepare_state(dense0.astype(npdt), na, nb)
+        E, g = st.energy_grad(ham, p["ops"], theta)
+        assert abs(E - Eref) <= tol["E"], (inter, E, Eref)
+        assert np.max(np.abs(g - gref)) <= tol["g"], inter
+        got = st.state()
+        assert np.max(np.abs(got[sec.dets.astype(np.int64)] - psi_ref)) <= tol["amp"], inter
+        assert np.count_nonzero(got[~_sector_mask(n, na, nb)]) == 0
+        out[inter] = (E, g)
+        st.close()
+    assert abs(out[0][0] - out[1][0]) <= tol["E"]
+    assert np.max(np.abs(out[0][1] - out[1][1])) <= tol["g"]
