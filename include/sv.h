@@ -188,8 +188,8 @@ sv_status sv_get_layout(sv_handle h, int32_t *storage_of_qubit);
  * = (pq|rs) with the 8-fold symmetry of real orbitals (checked to 1e-12,
  * SV_ERR_ARG otherwise), e_nuc.  1 <= n_orb <= SV_MAX_QUBITS/2.  The X-mask
  * tables (every group of Pauli strings sharing a flip pattern, evaluated in
- * closed form) and the tile schedule are built lazily per state size and
- * cached in the handle. */
+ * closed form) and the string tables of the expectation are built lazily per
+ * state size and precision and cached in the handle. */
 sv_status sv_ham_create(int n_orb, const double *h, const double *eri, double e_nuc,
                         sv_ham_handle *out);
 sv_status sv_ham_destroy(sv_ham_handle ham);
@@ -241,11 +241,17 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out);
  * that loads it, until the process exits; it holds 4 bytes per sector
  * determinant plus about 1.4 MB of partial sums, so sectors above roughly 1.7
  * million determinants are rejected with SV_ERR_ARG (use sv_rdm1).  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  Every call reuses the same
- * array, so calls whose work overlaps on the GPU (other streams, other threads)
- * race: serialise them.  Runs on cuda_stream (may be NULL) and synchronises it.
- * No counterpart in the paper: an operational variant of sv_rdm1. */
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and keeps it for that device's CUDA context; make that first call before any
+ * stream capture.  After the context changes (cudaDeviceReset) the next call
+ * looks it up again.  Every call reuses the same array, so calls whose work
+ * overlaps on the GPU (other streams, other threads) race: serialise them.
+ * Ordering: the call reads psi_dev on cuda_stream (may be NULL, the legacy
+ * default stream) and synchronises that stream only; work on another stream that
+ * writes psi_dev (a handle created on a non-blocking stream, for instance) must
+ * be ordered before it by the caller (an event the stream waits on, or a
+ * synchronisation).  No counterpart in the paper: an operational variant of
+ * sv_rdm1. */
 sv_status sv_rdm1_noalloc(const void *psi_dev, int n_qubits, sv_dtype dtype, int n_alpha, int n_beta,
                           void *cuda_stream, double *re_out, double *im_out);
 
@@ -379,7 +385,7 @@ typedef enum {
                                        0 leaves the context's value alone.  Rotations of
                                        excitations on low address bits touch runs of
                                        32-64 bytes, which larger fetches double */
-    SV_OPT_REVERSE_INTERLEAVED = 14 /* dense storage: 1 (default) sv_energy_grad runs its
+    SV_OPT_REVERSE_INTERLEAVED = 14, /* dense storage: 1 (default) sv_energy_grad runs its
                                        reverse sweep on psi(theta) and lambda interleaved
                                        by amplitude in one buffer (element x holds psi[x]
                                        then lambda[x]), so an excitation's touched runs
@@ -388,6 +394,21 @@ typedef enum {
                                        are one allocation (not with a caller-provided
                                        adjoint vector, checkpoints or the record-scan
                                        expectation); 0 two separate vectors */
+    SV_OPT_WAIT_POLLS = 15,         /* the tensor-core expectation kernels (variants 4
+                                       and 5): polls of each bounded wait on an mbarrier
+                                       (each poll a try-wait and a 32 ns sleep) before the
+                                       kernel gives up, waits (bounded) for its copies
+                                       and MMAs in flight, frees its tensor memory and
+                                       returns; the call then fails with SV_ERR_CUDA and
+                                       the handle needs sv_prepare_hf / sv_prepare_state.
+                                       1..2^30, default 2^22 */
+    SV_OPT_TEST_STALL = 16          /* failure-detection test hook, 0 (default) off: bit 0
+                                       makes k_same_tc's producer issue no copy, bit 1
+                                       makes k_ab_tc's builders stage and write nothing,
+                                       so that the consumers' first bounded waits run out
+                                       with no copy or MMA in flight (the path of a stuck
+                                       producer).  No fault and no hang: the call reports
+                                       SV_ERR_CUDA */
 } sv_option;
 
 /* Options change launch choices or summation order only: results agree within the

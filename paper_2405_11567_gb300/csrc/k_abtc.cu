@@ -62,7 +62,6 @@ constexpr int kAbAccCols = 2 * kAbMaxN;        // one accumulator: both planes
 constexpr int kAbAStage = 6 * kAbACols;        // A columns per stage: 2 planes x 3 pieces
 constexpr int kAbABase = 2 * kAbAccCols;       // first A column (after the two accumulators)
 static_assert(kAbABase + kAbS * kAbAStage <= 512, "tensor memory: accumulators and A stages in 512 columns");
-constexpr uint32_t kAbSpins = 1u << 22;
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -76,8 +75,8 @@ __device__ __forceinline__ bool ab_try(uint32_t mbar, uint32_t parity) {
     return ok != 0;
 }
 
-__device__ __forceinline__ bool ab_wait(uint32_t mbar, uint32_t parity) {
-    for (uint32_t it = 0; it < kAbSpins; ++it) {
+__device__ __forceinline__ bool ab_wait(uint32_t mbar, uint32_t parity, uint32_t spins) {
+    for (uint32_t it = 0; it < spins; ++it) {
         if (ab_try(mbar, parity)) return true;
         __nanosleep(32);
     }
@@ -161,6 +160,9 @@ struct AbTcArgs {
     int Da, Db, N, na, nb, ncols, nK, units;
     uint32_t maskN;
     int *err;
+    uint32_t spins;           // mbarrier polls (each with a short sleep) before a wait gives up
+    int stall;                // test hook: the builders stage and write nothing, so the MMA issuer's
+                              // and the epilogue's first waits run out with nothing in flight
 };
 
 // K entries per tile row in the table (nK * 16) plus 8: an odd number of 16-byte words
@@ -227,7 +229,9 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
 
-    if (warp < kAbBuild / 32) {
+    if (warp < kAbBuild / 32 && g.stall) {
+        // test hook: no copy, no tensor-memory store, no arrival
+    } else if (warp < kAbBuild / 32) {
         // ------------------------------------------------------------ builders
         const int r = tid & (kAbM - 1), hf = tid >> 7;  // tile row; which 4 of a stage's 16 K
         const int rowbytes = g.ldi * 12;                // a multiple of 16
@@ -336,7 +340,7 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                 // the stage is free once the MMAs of K block gch - kAbS are done; every builder
                 // waits itself (a timeout sets s_fail, which ends the other waits at once; the
                 // builders then stop together at the next unit)
-                if (gch >= kAbS && !s_fail && !ab_wait(su32(&empty[s]), (uint32_t)(((gch / kAbS) - 1) & 1)))
+                if (gch >= kAbS && !s_fail && !ab_wait(su32(&empty[s]), (uint32_t)(((gch / kAbS) - 1) & 1), g.spins))
                     s_fail = 1;
                 uint8_t *st = ring + s * kStageBytes;
                 // A: this thread's row (its tensor-memory lane) and 4 K = 2 columns of each piece
@@ -372,7 +376,7 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
             const int atile = u / g.Db, bp = u - atile * g.Db, t = it & 1, ia = atile * kAbM + r;
             bool bad = false;
             if (tid == kAbBuild + 32) {
-                if (!ab_wait(su32(&accf[t]), (uint32_t)((it >> 1) & 1))) s_fail = 1;
+                if (!ab_wait(su32(&accf[t]), (uint32_t)((it >> 1) & 1), g.spins)) s_fail = 1;
                 bad = s_fail != 0;
             }
             if (epi_any(bad)) break;
@@ -414,11 +418,11 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
         bool stop = false;
         for (int u = blockIdx.x; u < g.units && !stop; u += gridDim.x, ++it) {
             const int t = it & 1;
-            if (it >= 2 && !ab_wait(su32(&acce[t]), (uint32_t)(((it >> 1) - 1) & 1))) { s_fail = 1; break; }
+            if (it >= 2 && !ab_wait(su32(&acce[t]), (uint32_t)(((it >> 1) - 1) & 1), g.spins)) { s_fail = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int c = 0; c < g.nK; ++c, ++gch) {
                 const int s = gch % kAbS;
-                if (!ab_wait(su32(&full[s]), (uint32_t)((gch / kAbS) & 1)) || s_fail) {
+                if (!ab_wait(su32(&full[s]), (uint32_t)((gch / kAbS) & 1), g.spins) || s_fail) {
                     s_fail = 1;
                     stop = true;
                     break;
@@ -449,7 +453,7 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
         ab_commit(su32(&done));  // every MMA issued above has completed when `done` does
     }
     __syncwarp();
-    const bool ok = ab_wait(su32(&done), 0u);
+    const bool ok = ab_wait(su32(&done), 0u, g.spins);
     if (!ok) s_fail = 1;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -526,10 +530,12 @@ int ab_xi_ld(int Da) { return (Da + 3) / 4 * 4; }
 // H = the per-partner-row products (see above); Xi [Db][ab_xi_ld(Da)][3] the phased
 // amplitudes as bf16 pieces (phase kernel); Bp the B table pieces; H planes
 // [planes][Db][ncols][Da] (hplane elements apart).
+// spins: polls of each bounded wait; stall: the test hook of AbTcArgs.
 cudaError_t launch_ab_tc(const uint32_t *Xi, int planes, const uint16_t *stra, const uint16_t *strb,
                          const uint16_t *ra, const uint16_t *Bp, size_t pb, float *H, size_t hplane, int Da, int Db,
-                         int N, int na, int nb, int *err, int sm_count, cudaStream_t st) {
-    if (!ab_tc_fits(planes, Da, Db, na, nb, N) || ((uintptr_t)Xi & 15) || ((uintptr_t)Bp & 15) || (pb & 7))
+                         int N, int na, int nb, int *err, uint32_t spins, int stall, int sm_count, cudaStream_t st) {
+    if (!ab_tc_fits(planes, Da, Db, na, nb, N) || ((uintptr_t)Xi & 15) || ((uintptr_t)Bp & 15) || (pb & 7) ||
+        spins < 1)
         return cudaErrorInvalidValue;
     AbTcArgs g;
     g.Xi = Xi; g.ldi = ab_xi_ld(Da); g.stra = stra; g.strb = strb; g.ra = ra; g.Bp = Bp; g.pb = pb; g.H = H;
@@ -539,6 +545,8 @@ cudaError_t launch_ab_tc(const uint32_t *Xi, int planes, const uint16_t *stra, c
     g.units = ((Da + kAbM - 1) / kAbM) * Db;
     g.maskN = (1u << N) - 1u;
     g.err = err;
+    g.spins = spins;
+    g.stall = stall;
     const int grid = g.units < sm_count ? g.units : sm_count;
     const size_t sm = ab_tc_smem(Da, N);
     cudaError_t e;

@@ -1048,10 +1048,11 @@ static cudaError_t launch_ab_k(const RowArgs<double> &A, int K, size_t smem, cud
 }
 
 cudaError_t launch_same_tc(const uint16_t *M, size_t pm, const uint16_t *X, size_t px, uint16_t *Xt, size_t pt,
-                           float *G, int planes, int Da, int Db, int lda, int ldb, int *err, cudaStream_t st);
+                           float *G, int planes, int Da, int Db, int lda, int ldb, int *err, uint32_t spins, int stall,
+                           cudaStream_t st);
 cudaError_t launch_ab_tc(const uint32_t *Xi, int planes, const uint16_t *stra, const uint16_t *strb,
                          const uint16_t *ra, const uint16_t *Bp, size_t pb, float *H, size_t hplane, int Da, int Db,
-                         int N, int na, int nb, int *err, int sm_count, cudaStream_t st);
+                         int N, int na, int nb, int *err, uint32_t spins, int stall, int sm_count, cudaStream_t st);
 
 template <typename Amp>
 static cudaError_t launch_same_t(RowArgs<Amp> A, const RowTables &T, int dtype, int K, const SameGemm &g,
@@ -1064,12 +1065,13 @@ static cudaError_t launch_same_t(RowArgs<Amp> A, const RowTables &T, int dtype, 
                                                        g.abtc ? g.Xi : nullptr, g.ldi);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        e = launch_same_tc(g.Mp, g.pm, g.Xp, g.px, g.Xtp, g.pt, g.G, g.planes, T.Da, T.Db, g.lda, g.ldb, g.err, st);
+        e = launch_same_tc(g.Mp, g.pm, g.Xp, g.px, g.Xtp, g.pt, g.G, g.planes, T.Da, T.Db, g.lda, g.ldb, g.err,
+                           g.spins, g.stall & 1, st);
         if (e != cudaSuccess) return e;
         A.same_gemm = 1;
         if (g.abtc) {
             e = launch_ab_tc(g.Xi, g.planes, T.stra, T.strb, T.ra, g.Bp, g.pb, g.H, g.hplane, T.Da, T.Db, T.N, g.na,
-                             g.nb, g.err, sm_count, st);
+                             g.nb, g.err, g.spins, (g.stall >> 1) & 1, sm_count, st);
             if (e != cudaSuccess) return e;
             k_sigma_comb<Amp, true><<<T.Db, kThreads, 0, st>>>(A, g);
         } else {

@@ -39,7 +39,6 @@ constexpr int kTcBBytes = kTcN * kTcKb * 2;            // one piece of B in one 
 constexpr int kTcStageBytes = 3 * kTcABytes + 3 * kTcBBytes;
 constexpr int kTcStages = 3;                           // 3 x 72 KB
 constexpr int kTcSmem = kTcStages * kTcStageBytes + 1024;  // + alignment of the ring to 1024 bytes
-constexpr uint32_t kTcSpins = 1u << 22;                // mbarrier polls (with a short sleep) before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -65,8 +64,8 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (uint32_t it = 0; it < kTcSpins; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t spins) {
+    for (uint32_t it = 0; it < spins; ++it) {
         if (mbar_try(mbar, parity)) return true;
         __nanosleep(32);
     }
@@ -94,6 +93,8 @@ struct TcOut {
     float *G;  // [P][Db][Da]
     int Da, Db;
     int *err;
+    uint32_t spins;  // mbarrier polls (each with a short sleep) before a wait gives up
+    int stall;       // test hook: the producer issues no copy, so the MMA issuer's first wait runs out
 };
 
 // Tensor maps (innermost first): ma {K = Da, rows Da, piece}, mb {K = Db, rows Db, piece},
@@ -134,9 +135,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (tid == 0) {
         // producer: K block it into stage it % kTcStages once the MMAs of block it - kTcStages are done
         int it = 0;
-        for (; it < nIt; ++it) {
+        for (; it < (g.stall ? 0 : nIt); ++it) {
             const int s = it % kTcStages;
-            if (it >= kTcStages && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((it / kTcStages - 1) & 1))) {
+            if (it >= kTcStages && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((it / kTcStages - 1) & 1), g.spins)) {
                 s_fail = 1;
                 break;
             }
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         int it = 0;
         for (; it < nIt; ++it) {
             const int s = it % kTcStages;
-            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((it / kTcStages) & 1))) {
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((it / kTcStages) & 1), g.spins)) {
                 s_fail = 1;
                 break;
             }
@@ -197,13 +198,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                      : "memory");
     }
     __syncwarp();
-    bool ok = mbar_wait(smem_u32(&done), 0u);
+    bool ok = mbar_wait(smem_u32(&done), 0u, g.spins);
     if (!ok) s_fail = 1;
     __syncthreads();
     if (s_fail && tid == 0) {
         // copies issued but not consumed by the MMAs: let them land before the CTA exits
         for (int it = s_consumed; it < s_issued; ++it)
-            mbar_wait(smem_u32(&full[it % kTcStages]), (uint32_t)((it / kTcStages) & 1));
+            mbar_wait(smem_u32(&full[it % kTcStages]), (uint32_t)((it / kTcStages) & 1), g.spins);
     }
     __syncthreads();
     ok = !s_fail;
@@ -309,9 +310,11 @@ bool encode_map(CUtensorMap *m, const void *base, int rank, const uint64_t *dims
 // Da lda), X: the pieces of the phased planes (stride px), Xt: room for the transposed
 // pieces (stride pt), written here.  Rows padded to lda / ldb (multiples of 8); the
 // pointers 16-byte aligned and the piece strides multiples of 8 elements (TMA's rules).
+// spins: polls of each bounded wait; stall: the test hook of TcOut.
 cudaError_t launch_same_tc(const uint16_t *M, size_t pm, const uint16_t *X, size_t px, uint16_t *Xt, size_t pt,
-                           float *G, int planes, int Da, int Db, int lda, int ldb, int *err, cudaStream_t st) {
-    if (Da < 1 || Db < 1 || lda % 8 || ldb % 8 || pm % 8 || px % 8 || pt % 8 || ((uintptr_t)M & 15) ||
+                           float *G, int planes, int Da, int Db, int lda, int ldb, int *err, uint32_t spins, int stall,
+                           cudaStream_t st) {
+    if (Da < 1 || Db < 1 || lda % 8 || ldb % 8 || pm % 8 || px % 8 || pt % 8 || spins < 1 || ((uintptr_t)M & 15) ||
         ((uintptr_t)X & 15) || ((uintptr_t)Xt & 15))
         return cudaErrorInvalidValue;
     static bool attr = false;
@@ -335,7 +338,7 @@ cudaError_t launch_same_tc(const uint16_t *M, size_t pm, const uint16_t *X, size
     if (!encode_map(&ma, M, 3, dma, sma, kTcM) || !encode_map(&mb, M + (size_t)Da * lda, 3, dmb, smb, kTcN) ||
         !encode_map(&mx, X, 4, dx, sx, kTcN) || !encode_map(&mt, Xt, 4, dt, stt, kTcM))
         return cudaErrorInvalidValue;
-    const TcOut g{G, Da, Db, err};
+    const TcOut g{G, Da, Db, err, spins, stall};
     k_same_tc<<<dim3((Db + kTcN - 1) / kTcN, (Da + kTcM - 1) / kTcM, planes), kTcThreads, kTcSmem, st>>>(ma, mb, mx,
                                                                                                        mt, g);
     return cudaGetLastError();

@@ -17,6 +17,8 @@
 
 #include "sv_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace svk {
 int rotate_grid(uint64_t npairs, int sm_count, int bps);
 cudaError_t launch_set_basis(void *psi, int dtype, uint32_t x, cudaStream_t st);
@@ -257,13 +259,30 @@ static sv_status ensure_out(sv_handle h, size_t doubles) {
     return SV_OK;
 }
 
-// Phase events: record event i on the handle's stream when profiling.
-static sv_status mark(sv_handle h, int i) {
+// Phase boundary i: closes the handle's open NVTX range and opens one named `range`
+// (none when NULL; the ranges mark the host-side span of each phase's launches for a
+// timeline profiler, and cost nothing without one), and records CUDA event i on the
+// handle's stream when profiling (sv_phase_times).
+static sv_status mark(sv_handle h, int i, const char *range) {
+    if (h->nvtx_open) nvtxRangePop();
+    h->nvtx_open = range != nullptr;
+    if (range) nvtxRangePushA(range);
     if (!h->profile) return SV_OK;
     if (!h->ev[i]) SV_CUDA(h, cudaEventCreate(&h->ev[i]));
     SV_CUDA(h, cudaEventRecord(h->ev[i], h->stream));
     return SV_OK;
 }
+
+// Closes a phase range an early return left open.
+struct NvtxClose {
+    sv_handle h;
+    ~NvtxClose() {
+        if (h && h->nvtx_open) {
+            nvtxRangePop();
+            h->nvtx_open = false;
+        }
+    }
+};
 
 static float elapsed(sv_handle h, int a, int b) {
     float ms = 0.f;
@@ -814,6 +833,8 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
     g->lda = (int)lda;
     g->ldb = (int)ldb;
     g->err = h->kerr;
+    g->spins = (uint32_t)h->wait_polls;
+    g->stall = h->test_stall;
     g->abtc = 0;
     bool ab_ok = abtc;
     const int ncols = h->nb * (N - h->nb) + 1;
@@ -1501,6 +1522,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     SV_TRY(build_ops(h, ops, n_ops, theta, d));  // validates in any layout
     DeviceGuard g(h->device);
     L2FetchScope l2(h);
+    NvtxClose nvtx_close{h};
     if (h->layout_auto && n_ops > 0 && h->storage == 0) {
         int np[32];
         layout_from_ops(h->n, ops, n_ops, np);
@@ -1535,12 +1557,12 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     SV_TRY(ensure_partials(h, std::max<size_t>((size_t)G * std::max<size_t>(L, 1), need)));
     plan_checkpoints(h, L);
     h->prepared = false;
-    SV_TRY(mark(h, 0));
+    SV_TRY(mark(h, 0, "sv_energy_grad: reference"));
     SV_TRY(prepare_reference(h));
     h->prepared = true;
-    SV_TRY(mark(h, 1));
+    SV_TRY(mark(h, 1, "sv_energy_grad: forward sweep"));
     SV_TRY(forward(h, d, true));
-    SV_TRY(mark(h, 2));
+    SV_TRY(mark(h, 2, "sv_energy_grad: working copy"));
     // The reverse sweep un-applies the ops to a working copy of psi(theta), so that psi
     // keeps psi(theta): in sector storage without checkpoint resynchronisation, the
     // interleaved (psi, lambda) matrix; else the saved-state buffer.  Where neither can be
@@ -1568,7 +1590,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
         h->launches++;
     }
     const double c = shift_for(h, ham);
-    SV_TRY(mark(h, 3));
+    SV_TRY(mark(h, 3, "sv_energy_grad: expectation"));
     if (dint) {
         SV_TRY(expectation(h, ham, T, nullptr, c, 0, h->Lbuf));
         SV_CUDA(h, launch_scatter_odd(h->Lbuf, h->lam, h->dtype, h->str_sa_s, h->str_sb_s, h->Da, h->Db, h->sm_count,
@@ -1577,7 +1599,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     } else {
         SV_TRY(expectation(h, ham, T, h->lam, c, 0));
     }
-    SV_TRY(mark(h, 4));
+    SV_TRY(mark(h, 4, "sv_energy_grad: reverse sweep"));
     // reverse sweep
     if (inter) {
         SV_CUDA(h, launch_interleave(h->psi, h->lam, h->dtype, h->CLbuf, (size_t)h->Da * h->Db, h->sm_count,
@@ -1612,14 +1634,14 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     }
     SV_CUDA(h, launch_reduce_rows(h->partials, (int)L, G, h->dout + 2, h->stream));
     h->launches++;
-    SV_TRY(mark(h, 5));
+    SV_TRY(mark(h, 5, "sv_energy_grad: restore"));
     SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, (2 + L) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     // leave psi(theta) in the handle (only a sweep on psi itself took it away)
     if (!inter && !dint && wpsi == h->psi) {
         SV_TRY(prepare_reference(h));
         SV_TRY(forward(h, d, false));
     }
-    SV_TRY(mark(h, 6));
+    SV_TRY(mark(h, 6, nullptr));
     SV_CUDA(h, cudaStreamSynchronize(h->stream));
     SV_TRY(check_kernel_flag(h));
     if (h->profile) {
@@ -1710,6 +1732,7 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
     SV_TRY(check_ready(h));
     if (!re_out) return fail(h, SV_ERR_ARG, "NULL re_out");
     DeviceGuard g(h->device);
+    NvtxClose nvtx_close{h};
     if (h->storage == 1 || h->rdm_variant != 1 || !is_complex(h->dtype)) {
         // string rows: on the state itself (sector storage) or on its compact copy
         SV_TRY(ensure_strings(h));
@@ -1718,7 +1741,7 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
         const int grid = rdm_rows_grid(h->Db, h->sm_count, h->rdm_bps);
         SV_TRY(ensure_partials(h, (size_t)2 * n_el * grid));
         SV_TRY(ensure_out(h, 2 * (size_t)n_el));
-        SV_TRY(mark(h, 0));
+        SV_TRY(mark(h, 0, "sv_rdm1"));
         const void *Cm = h->psi;
         if (h->storage == 0) {
             SV_CUDA(h, launch_compact(h->psi, h->Cbuf, h->dtype, h->str_sa_s, h->str_sb_s, h->Da, h->Db, h->sm_count,
@@ -1732,7 +1755,7 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
         h->launches++;
         SV_CUDA(h, launch_reduce_rows(h->partials, 2 * n_el, grid, h->dout, h->stream));
         h->launches++;
-        SV_TRY(mark(h, 7));
+        SV_TRY(mark(h, 7, nullptr));
         SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, 2 * (size_t)n_el * sizeof(double), cudaMemcpyDeviceToHost,
                                    h->stream));
         SV_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1748,13 +1771,13 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
         SV_TRY(ensure_out(h, 2 * (size_t)n_el));
         double *d_el = h->partials + part;
         SV_CUDA(h, cudaMemcpyAsync(d_el, host_el.data(), host_el.size(), cudaMemcpyHostToDevice, h->stream));
-        SV_TRY(mark(h, 0));
+        SV_TRY(mark(h, 0, "sv_rdm1"));
         SV_CUDA(h, launch_rdm_gather(h->psi, h->dtype, h->sector, h->sector_len, d_el, n_el, grid, h->partials,
                                      h->stream));
         h->launches++;
         SV_CUDA(h, launch_reduce_rows(h->partials, 2 * n_el, grid, h->dout, h->stream));
         h->launches++;
-        SV_TRY(mark(h, 7));
+        SV_TRY(mark(h, 7, nullptr));
         SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, 2 * (size_t)n_el * sizeof(double), cudaMemcpyDeviceToHost,
                                    h->stream));
         SV_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1819,6 +1842,8 @@ sv_status sv_get_option(sv_handle h, sv_option opt, int64_t *value) {
         case SV_OPT_POOL_VARIANT: *value = h->pool_variant; return SV_OK;
         case SV_OPT_L2_FETCH: *value = h->l2_fetch; return SV_OK;
         case SV_OPT_REVERSE_INTERLEAVED: *value = h->rev_inter; return SV_OK;
+        case SV_OPT_WAIT_POLLS: *value = h->wait_polls; return SV_OK;
+        case SV_OPT_TEST_STALL: *value = h->test_stall; return SV_OK;
     }
     return fail(h, SV_ERR_ARG, "unknown option");
 }
@@ -1873,6 +1898,14 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
         case SV_OPT_RDM_VARIANT:
             if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "rdm variant must be 0, 1 or 2");
             h->rdm_variant = (int)value;
+            return SV_OK;
+        case SV_OPT_WAIT_POLLS:
+            if (value < 1 || value > (int64_t)1 << 30) return fail(h, SV_ERR_ARG, "wait polls must be in [1, 2^30]");
+            h->wait_polls = value;
+            return SV_OK;
+        case SV_OPT_TEST_STALL:
+            if (value < 0 || value > 3) return fail(h, SV_ERR_ARG, "test stall must be in [0, 3]");
+            h->test_stall = (int)value;
             return SV_OK;
         case SV_OPT_REVERSE_INTERLEAVED:
             if (value != 0 && value != 1) return fail(h, SV_ERR_ARG, "reverse-sweep interleaving must be 0 or 1");

@@ -129,6 +129,8 @@ struct SameGemm {
     int planes = 2;                            // 2 complex (re, im), 1 real
     int lda = 0, ldb = 0;                      // row strides of Ma / X and Mb / Xt: D rounded up to 4, zero padded
     int *err = nullptr;                        // device flag set by k_same_tc / k_ab_tc when a wait runs out
+    uint32_t spins = 1u << 22;                 // polls of each of their bounded waits
+    int stall = 0;                             // test hook: bit 0 k_same_tc, bit 1 k_ab_tc issue nothing
     // variant 5: the alpha-beta part on the tensor cores (k_ab_tc) into planes H
     // [planes][Db][ncols][Da] (hplane floats apart), gathered by k_sigma_comb; Bp: the
     // bf16 pieces [3][N^2 + Db + 1][256] of its integral table (piece stride pb)
@@ -222,6 +224,7 @@ struct sv_ctx {
     bool own_psi = true, own_lam = true;
     // prepared state
     bool prepared = false;
+    bool nvtx_open = false;    // a phase range of this handle is open (NVTX)
     bool failed = false;
     int na = -1, nb = -1;
     int ref_kind = 0;          // 0 none, 1 HF determinant, 2 stored vector
@@ -274,6 +277,8 @@ struct sv_ctx {
     int rev_inter = 1;         // dense reverse sweep on psi and lambda interleaved (k_adjoint_i) where it can
     bool lam_pair = false;     // lam's allocation holds two vectors: lam, then the working copy `saved`
     int *kerr = nullptr;       // device flag of kernels with bounded waits (k_same_tc, k_ab_tc)
+    int64_t wait_polls = 1 << 22;  // polls of each of their bounded waits (SV_OPT_WAIT_POLLS)
+    int test_stall = 0;        // SV_OPT_TEST_STALL: bit 0 k_same_tc, bit 1 k_ab_tc issue no copy / MMA
     int *hkerr = nullptr;      // its pinned host copy, checked after stream synchronisations
     // same-spin products (expectation variant 4): matrices for one table set and sector,
     // and the phased-psi / product planes

@@ -14,10 +14,14 @@
 //
 // Host code may not use the array's name as a device address, so the first call
 // on each device looks the address up with cudaGetSymbolAddress (with that
-// device current) and keeps it; that first call should come before any stream
-// capture.  All calls share the one array: a call overwrites everything it reads
-// back (the kernel writes every partial it later sums), and two calls whose work
-// overlaps on the GPU race on it.
+// device current) and keeps it, together with the identity of the CUDA context
+// it belongs to; that first call should come before any stream capture.  The
+// address is looked up again only when the device's current context is another
+// one (after cudaDeviceReset the module is loaded anew and the array may move).
+// All calls share the one array: a call overwrites everything it reads back (the
+// kernel writes every partial it later sums), and two calls whose work overlaps
+// on the GPU race on it.
+#include <cuda.h>          // CUcontext / CUresult types; the driver calls are looked up through the runtime
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,7 +51,38 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 std::mutex g_mu;
+// per device: the array's device address and the id of the context it was looked up in
 void *g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};
+
+typedef CUresult (*ctx_current_fn)(CUcontext *);
+typedef CUresult (*ctx_id_fn)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current CUDA context (0 when it cannot be read:
+// the address is then looked up on every call).  Caller holds g_mu.
+unsigned long long current_context_id() {
+    static bool resolved = false;
+    static ctx_current_fn get_current = nullptr;
+    static ctx_id_fn get_id = nullptr;
+    if (!resolved) {
+        resolved = true;
+        void *f = nullptr, *g = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = (ctx_current_fn)f;
+            get_id = (ctx_id_fn)g;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 sv_status nfail(sv_status s, const std::string &m) {
     set_thread_error(m);
@@ -104,17 +139,22 @@ extern "C" sv_status sv_rdm1_noalloc(const void *psi_dev, int n_qubits, sv_dtype
     for (uint32_t a : sa)
         for (uint32_t b : sb) list.push_back(a | b);
     std::sort(list.begin(), list.end());
-    // device address of the static scratch, once per device
+    // device address of the static scratch: once per device and context
     void *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_addr[dev]) {
+        // ctx is 0 on a thread without a current context yet: look the address up (which
+        // makes the device's primary context current) and record that context's id
+        const unsigned long long ctx = current_context_id();
+        if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
+            g_scratch_addr[dev] = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&g_scratch_addr[dev], g_noalloc_scratch);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 g_scratch_addr[dev] = nullptr;
                 return nfail(SV_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             }
+            g_scratch_ctx[dev] = current_context_id();
         }
         base = g_scratch_addr[dev];
     }

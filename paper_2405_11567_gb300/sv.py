@@ -34,6 +34,8 @@ SV_OPT_ROT_BLOCKS_PER_SM, SV_OPT_SECT_BLOCKS_PER_SM, SV_OPT_RDM_BLOCKS_PER_SM = 
 SV_OPT_POOL_VARIANT = 11
 SV_OPT_L2_FETCH = 12
 SV_OPT_REVERSE_INTERLEAVED = 14
+SV_OPT_WAIT_POLLS = 15
+SV_OPT_TEST_STALL = 16
 SV_PHASES = 6
 PHASE_NAMES = ("reference", "forward", "expectation", "reverse", "restore", "rdm1")
 STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV_ERR_TIMEOUT", 5: "SV_ERR_STATE"}
@@ -288,7 +290,11 @@ def sv_rdm1(h, n_orb: int) -> np.ndarray:
 
 
 def sv_rdm1_noalloc(psi_dev: int, n_qubits: int, dtype: int, n_alpha: int, n_beta: int, stream=None) -> np.ndarray:
-    """1-RDM of a device-resident state in qubit order, using only the library's fixed scratch array."""
+    """1-RDM of a device-resident state in qubit order, using only the library's fixed scratch array.
+
+    ``stream`` must be the stream that wrote ``psi_dev`` or one ordered after it (None is the
+    legacy default stream, which is not ordered after non-blocking streams such as torch's):
+    ``StateVector.rdm1_noalloc`` passes its handle's stream."""
     N = n_qubits // 2
     re = np.zeros((2, N, N))
     im = np.zeros((2, N, N))
@@ -444,6 +450,7 @@ class StateVector:
         self.n = int(n_qubits)
         self.dtype = dtype_code(dtype)
         self.sector = None if sector is None else (int(sector[0]), int(sector[1]))
+        self.stream = stream
         self.handle = None
         if self.sector is None:
             self.handle = sv_create(self.n, self.dtype, stream)
@@ -485,6 +492,16 @@ class StateVector:
 
     def rdm1(self) -> np.ndarray:
         return sv_rdm1(self.handle, self.n // 2)
+
+    def rdm1_noalloc(self, n_alpha: int, n_beta: int) -> np.ndarray:
+        """The 1-RDM through sv_rdm1_noalloc (no device allocation) on this handle's stream, so
+        that it is ordered after the handle's queued work.  Dense storage in qubit order only."""
+        if self.sector is not None:
+            raise ValueError("sv_rdm1_noalloc reads a dense 2^n state")
+        if not np.array_equal(self.layout(), np.arange(self.n)):
+            raise ValueError("sv_rdm1_noalloc reads the state in qubit order: set_layout(range(n)) first")
+        return sv_rdm1_noalloc(sv_state_device_ptr(self.handle), self.n, self.dtype, n_alpha, n_beta,
+                               stream=self.stream)
 
     def pool_gradients(self, ham: Hamiltonian, pool):
         """(E, gradients of appending each pool operator at angle 0) for the current state."""
