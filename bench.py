@@ -39,22 +39,54 @@ if ROOT not in sys.path:
 METRIC = "energy+adjoint-grad evals/s at 30 qubits, FP32-state vs FP64; % of HBM peak"
 UNIT = "evals/s"
 CONFIG_ID = 5
-# DRAM bytes (read + write) of one sector-storage expectation per expectation form, from
-# the ncu captures summarised in profiles/sigma_products_n30_sector_c64.md (form 4:
-# k_phase_planar, k_transpose_pieces, k_same_tc, k_sigma_ab, k_sigma_comb; form 5: the
-# same with k_ab_tc for k_sigma_ab and the gathering k_sigma_comb); None once a kernel
-# changes.
-SIGMA_TRAFFIC_BYTES = {4: 1555.6e6, 5: 12283.4e6}
 SIGMA_KERNELS = {
     3: "expectation: k_sigma_ab + k_sigma_same (two launches)",
     4: "expectation: k_phase_planar + k_transpose_pieces + k_same_tc (same-spin products, tcgen05 bf16x3) "
        "+ k_sigma_ab + k_sigma_comb",
     5: "expectation: k_phase_planar + k_transpose_pieces + k_same_tc (same-spin products) + k_ab_tc "
        "(alpha-beta products; both tcgen05 bf16x3) + k_sigma_comb (gathers the alpha-beta planes)"}
-# DRAM bytes per k_adjoint launch of the dense headline: the 28-qubit capture's
-# traffic / algorithmic ratio (1.115, profiles/k_adjoint_dram_n28_dense_c64.md) times
-# the 30-qubit algorithmic bytes per launch; None once the kernel changes.
-ADJOINT_TRAFFIC_BYTES = 4.93e9
+# Measured DRAM traffic lives in a small committed record written from ncu captures
+# (--record-traffic), keyed by a hash of the sources of the kernels it measured: a
+# record whose sources changed since is stale and the bench line reports null.
+TRAFFIC_RECORDS = os.path.join(ROOT, "profiles", "traffic.json")
+CSRC = "paper_2405_11567_gb300/csrc/"
+TRAFFIC_SOURCES = {
+    "dense_adjoint_c64": [CSRC + "k_state.cu", CSRC + "sv_device.cuh"],
+    "sector_sigma_c64": [CSRC + "k_rows.cu", CSRC + "k_tcgemm.cu", CSRC + "k_abtc.cu", CSRC + "sv_sigma.cuh",
+                         CSRC + "sv_device.cuh"],
+}
+GOLDEN = os.path.join(ROOT, "tests", "golden", "config5_oracle.json")
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 rate, nominal
+
+
+def sources_sha256(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in sorted(paths):
+        h.update(rel.encode())
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def traffic_record(name):
+    """The committed traffic record `name` if its kernel sources are unchanged, else None."""
+    if not os.path.exists(TRAFFIC_RECORDS):
+        return None
+    with open(TRAFFIC_RECORDS) as f:
+        rec = json.load(f).get(name)
+    if rec is None or rec.get("sources_sha256") != sources_sha256(TRAFFIC_SOURCES[name]):
+        return None
+    return rec
+
+
+def lowest_bit_class(b):
+    return str(b) if b < 3 else "3+"
+
+
+def op_qubits(op):
+    kind = int(op[0])
+    return [int(op[1]), int(op[3])] if kind in (1, 3) else [int(x) for x in op[1:5]]
 
 
 def _env_int(k, d):
@@ -224,13 +256,18 @@ def run_reference(args, rank, world):
         vals.append(v)
     wall = time.perf_counter() - t0
     value = float(statistics.mean(vals))
+    # one full evaluation takes the oracle tens of minutes at 30 qubits: each step times a bounded
+    # sample of it (ms_per_step is that sample's measured wall time) and `value` is projected from it
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(p),
+        "projected": {"value": value, "from": sample,
+                      "projected_ms_per_eval": 1000.0 / value,
+                      "note": "value is projected to one full evaluation; ms_per_step is the sample's wall time"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": sample, "wall_s": wall,
+                         "sample": sample, "wall_s": wall, "projected": True,
                          "energy_only_evals_per_s": oracle_eval_sample.last["energy_only_evals_per_s"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -286,11 +323,6 @@ def pool_pairs(pool, n_orb, na, nb):
             cnt *= comb(n_orb - touched, k) if 0 <= k <= n_orb - touched else 0
         total += cnt
     return total
-
-
-def fp32_peak_tflops(sm_mhz):
-    """Plain (non-tensor) FP32 FMA peak: 152 SMs x 128 lanes x 2 flops x the SM clock."""
-    return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
 
 
 def run_ours(args, rank, world, local_rank):
@@ -356,8 +388,11 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         ms, t_host = reduce_max([ms, t_host])
         avg = {k: statistics.mean(ph[k] for ph in phases) for k in phases[0]}
+        layout = None if sector else [int(x) for x in st.layout()]
+        variant = st.option(sv.SV_OPT_EXPECT_VARIANT)
         st.close()
-        return dict(ms=ms, t_host=t_host, phases=avg, clocks=clk, launches=launches, out=outs, tuned=tuned)
+        return dict(ms=ms, t_host=t_host, phases=avg, clocks=clk, launches=launches, out=outs, tuned=tuned,
+                    layout=layout, variant=variant)
 
     def timed_batch():
         """Config 4: 512 instances (10-20 qubits, 40 operators each), one graph launch per step."""
@@ -464,7 +499,8 @@ def run_ours(args, rank, world, local_rank):
     rot_bytes = touched_bytes(p["ops"], n, 8)
     kernels = {
         "adjoint_step": dict(phase="reverse", mult=2.0,
-                             desc="fused adjoint step (k_adjoint): psi and lambda pairs, read + write"),
+                             desc="fused adjoint step (k_adjoint_i: psi and lambda interleaved in one buffer): "
+                                  "psi and lambda pairs, read + write"),
         "rotation": dict(phase="forward", mult=1.0, desc="excitation rotation (k_rotate): touched pairs, read + write"),
     }
     rows = {}
@@ -475,10 +511,21 @@ def run_ours(args, rank, world, local_rank):
         rows[name] = {"achieved_gbs": a, "frac": a / peak, "mean_launch_ms": t_launch * 1e3,
                       "bytes_per_launch": per_launch, "launches_per_step": L, "desc": kd["desc"]}
     dom = max(kernels, key=lambda k: head["phases"][kernels[k]["phase"]])
+    traffic, traffic_note = None, "no ncu record for the current kernel sources"
+    rec = traffic_record("dense_adjoint_c64")
+    if dom == "adjoint_step" and rec is not None and head["layout"] is not None:
+        # the record's DRAM / algorithmic ratio of each lowest-address-bit class, weighted by this ansatz's ops
+        ratio = rec["ratio_by_lowest_bit"]
+        tb = 2.0 * rot_bytes
+        cls = [lowest_bit_class(min(head["layout"][q] for q in op_qubits(op))) for op in p["ops"]]
+        traffic = float(sum(t * ratio[c] for t, c in zip(tb, cls)) / L)
+        traffic_note = "ncu DRAM bytes per launch by lowest-address-bit class (%s), weighted by this ansatz" % rec[
+            "capture"]
     roof = {"bound": "hbm", "kernel": dom, "achieved": rows[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
-            "frac": rows[dom]["frac"], "traffic": ADJOINT_TRAFFIC_BYTES if dom == "adjoint_step" else None,
+            "frac": rows[dom]["frac"], "traffic": traffic, "traffic_note": traffic_note,
             "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
             else "fallback 6.8 TB/s"}
+    golden = load_golden()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": head["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -493,52 +540,28 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(head["launches"]),
         "autotune": head["tuned"],
     }
+    if golden is not None:
+        line["vs_oracle"] = vs_golden(head["out"], golden)
     if head128 is not None:
         v128 = throughput(world, K, head128["ms"])
+        fp64 = fp64_peak(torch)
         line["fp64_state"] = {"value": v128, "ms_per_step": head128["ms"] / K, "phases_ms": head128["phases"],
-                              "clocks": head128["clocks"]}
+                              "clocks": head128["clocks"],
+                              "bound": fp64_rooflines(p, head128["phases"], fp64, peak),
+                              "vs_oracle": vs_golden(head128["out"], golden) if golden is not None else None}
         line["speedup_fp32_over_fp64"] = value / v128
+        line["speedup_bounds"] = {
+            "complex64": "HBM: the sweeps move their bytes at %.2f (reverse) / %.2f (forward) of the copy peak"
+                         % (rows["adjoint_step"]["frac"], rows["rotation"]["frac"]),
+            "complex128": "FP64 pipe: see fp64_state.bound (FP64 flops / time against the FP64 peak); the "
+                          "byte ratio alone would give 2x"}
         line["fp32_vs_fp64"] = {
             "abs_dE": abs(head["out"]["E"] - head128["out"]["E"]),
             "max_abs_dg": float(np.max(np.abs(head["out"]["g"] - head128["out"]["g"]))),
             "max_abs_drdm": float(np.max(np.abs(head["out"]["rdm"] - head128["out"]["rdm"]))),
             "E_fp64": head128["out"]["E"]}
     if s64 is not None:
-        # sector storage: a separate row (the state is 0.84% of 2^30 amplitudes and L2-resident), with the
-        # expectation's two kernels against the plain FP32 FMA peak
-        D, per = sigma_terms(p)
-        flops = 4.0 * D * per  # complex amplitude x real matrix element = 2 FMA per connection
-        t_sig = s64["phases"]["expectation"] / 1000.0
-        sm_mhz = s64["clocks"].get("sm_mhz")
-        fpeak = fp32_peak_tflops(sm_mhz)
-        ach = flops / t_sig / 1e12
-        sb = sector_touched_bytes(p["ops"], p["n_orb"], p["na"], p["nb"], 8)
-        sv_form = int((s64["tuned"] or {}).get("expect_variant", s64.get("variant", 5)))
-        t_rot = s64["phases"]["forward"] / L / 1000.0
-        t_adj = s64["phases"]["reverse"] / L / 1000.0
-        sect = {"storage": "sector: C(15,5)^2 = 9,018,009 amplitudes (72 MB complex64), L2-resident",
-                "value": throughput(world, K, s64["ms"]), "unit": UNIT, "ms_per_step": s64["ms"] / K,
-                "phases_ms": s64["phases"], "clocks": s64["clocks"], "gpu_launches": int(s64["launches"]),
-                "roofline": {"bound": "alu", "kernel": SIGMA_KERNELS.get(sv_form, "expectation form %d" % sv_form),
-                             "achieved": ach, "peak": fpeak, "unit": "TFLOP/s", "frac": ach / fpeak,
-                             "traffic": SIGMA_TRAFFIC_BYTES.get(sv_form),
-                             "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz"
-                                          % (sm_mhz or 2070.0),
-                             "algorithmic": "%d determinants x %d connections x 4 flops = %.1f GFLOP"
-                                            % (D, per, flops / 1e9)},
-                "kernels": {"rotation_l": {"algorithmic_gbs": sb.sum() / L / t_rot / 1e9,
-                                           "mean_launch_ms": t_rot * 1e3},
-                            "adjoint_l": {"algorithmic_gbs": 2.0 * sb.sum() / L / t_adj / 1e9,
-                                          "mean_launch_ms": t_adj * 1e3}},
-                "autotune": s64["tuned"],
-                "abs_dE_vs_dense_c64": abs(s64["out"]["E"] - head["out"]["E"]),
-                "max_abs_dg_vs_dense_c64": float(np.max(np.abs(s64["out"]["g"] - head["out"]["g"])))}
-        if s128 is not None:
-            sect["fp64_state"] = {"value": throughput(world, K, s128["ms"]), "ms_per_step": s128["ms"] / K,
-                                  "phases_ms": s128["phases"]}
-            if head128 is not None:
-                sect["abs_dE_vs_dense_c128"] = abs(s128["out"]["E"] - head128["out"]["E"])
-        line["sector_storage"] = sect
+        line["sector_storage"] = sector_row(p, s64, s128, head, head128, world, K, L, golden)
     if r32d is not None:
         # real-amplitude float32 state (the real-angle ansatz keeps psi real): half the bytes per amplitude
         rb4 = touched_bytes(p["ops"], n, 4)
@@ -559,12 +582,254 @@ def run_ours(args, rank, world, local_rank):
         line["pool_screening"] = rpool
     if world == 1 and not args.no_cpu_baseline and not args.qubits:
         import oracle
+        t0 = time.perf_counter()
         v, sample, _ = oracle_eval_sample(p)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                                "sample": sample,
+                                "sample": sample, "projected": True, "sample_wall_s": time.perf_counter() - t0,
                                 "energy_only_evals_per_s": oracle_eval_sample.last["energy_only_evals_per_s"]}
+        if not args.no_per_config:
+            line["per_config"] = per_config_rows(args, stream, peak, rbatch)
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------- bench-line helpers
+
+def load_golden():
+    """The oracle's 30-qubit energy, gradient and 1-RDM (tests/golden, written by the oracle alone)."""
+    if not os.path.exists(GOLDEN):
+        return None
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def vs_golden(out, golden):
+    rdm = np.array(golden["rdm1_re"]) + 1j * np.array(golden["rdm1_im"])
+    return {"abs_dE": abs(out["E"] - golden["energy"]),
+            "max_abs_dg": float(np.max(np.abs(np.asarray(out["g"]) - np.array(golden["gradient"])))),
+            "max_abs_drdm": float(np.max(np.abs(np.asarray(out["rdm"]) - rdm))),
+            "oracle": "tests/golden/config5_oracle.json (route A, complex128, %d threads, %.0f s)"
+                      % (golden["oracle_threads"], golden["seconds"])}
+
+
+def fp64_peak(torch):
+    """FP64 throughput measured in this run: a 4096^3 float64 matrix product (cuBLAS) on the GPU, best of 3."""
+    a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    b = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    best = None
+    for _ in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return 2.0 * 4096 ** 3 / (best / 1e3) / 1e12
+
+
+def fp64_rooflines(p, phases, fp64_tflops, hbm_peak):
+    """complex128 sweeps and expectation against the FP64 pipe (and the sweeps against HBM): FP64 flops
+    per amplitude pair = 12 in the rotation (three shears of the real and imaginary parts, six FMAs) and
+    32 in the adjoint step (two rotations plus four FMAs of the gradient term); the expectation 4 flops per
+    Hamiltonian connection (complex amplitude x real element, two FMAs)."""
+    n, L = p["n_qubits"], len(p["ops"])
+    kind = np.asarray(p["ops"])[:, 0]
+    pairs = np.where((kind == 1) | (kind == 3), 2.0 ** (n - 2), 2.0 ** (n - 4)).sum()
+    D, per = sigma_terms(p)
+    out = {"fp64_peak_tflops": fp64_tflops,
+           "fp64_peak_kind": "measured in this run: 4096^3 float64 matmul (cuBLAS), best of 4; nominal %.2f"
+                             % FP64_NOMINAL_TFLOPS}
+    tb = touched_bytes(p["ops"], n, 16).sum()
+    for name, phase, flops_per_pair, mult in (("rotation", "forward", 12.0, 1.0),
+                                              ("adjoint_step", "reverse", 32.0, 2.0)):
+        t = phases[phase] / 1000.0
+        tf = flops_per_pair * pairs / t / 1e12
+        gbs = mult * tb / t / 1e9
+        out[name] = {"bound": "fp64", "achieved_tflops": tf, "frac_fp64": tf / fp64_tflops,
+                     "hbm_gbs": gbs, "frac_hbm": gbs / hbm_peak, "flops_per_pair": flops_per_pair,
+                     "pairs_per_sweep": pairs, "mean_launch_ms": phases[phase] / L}
+    t = phases["expectation"] / 1000.0
+    tf = 4.0 * D * per / t / 1e12
+    out["expectation"] = {"bound": "fp64", "achieved_tflops": tf, "frac_fp64": tf / fp64_tflops,
+                          "algorithmic": "%d determinants x %d connections x 4 flops" % (D, per)}
+    return out
+
+
+def mma_flops(p, planes=2):
+    """bf16 tensor-core flops the two tcgen05 kernels issue per sigma: k_same_tc, tiles of 128 x 256 over
+    K blocks of 32 (both products, six piece products); k_ab_tc, units of 128 alpha strings x one partner beta
+    string, N = 64 columns over K blocks of 16 (six piece products per plane)."""
+    from math import comb
+    N, na, nb = p["n_orb"], p["na"], p["nb"]
+    Da, Db = comb(N, na), comb(N, nb)
+    cdiv = lambda a, b: (a + b - 1) // b  # noqa: E731
+    same = cdiv(Db, 256) * cdiv(Da, 128) * planes * (cdiv(Da, 32) + cdiv(Db, 32)) * 6 * 2.0 * 128 * 256 * 32
+    units = cdiv(Da, 128) * Db
+    ab = units * planes * cdiv(N * (N + 1) // 2, 16) * 6 * 2.0 * 128 * 64 * 16
+    return same, ab
+
+
+def sector_row(p, s64, s128, head, head128, world, K, L, golden):
+    """Sector storage (the state is 0.84% of 2^30 amplitudes and L2-resident): its own row, with the
+    tensor-core expectation kernels against the tensor pipe's measured bf16 peak."""
+    D, per = sigma_terms(p)
+    useful = 4.0 * D * per  # complex amplitude x real matrix element = 2 FMA per connection
+    ph = s64["phases"]
+    peaks = measured_tensor_peaks()
+    same, ab = mma_flops(p)
+    kern = {}
+    if ph.get("same_products", 0) > 0:
+        kern["k_same_tc"] = {"mma_tflop": same / 1e12, "ms": ph["same_products"],
+                             "achieved_tflops": same / (ph["same_products"] / 1e3) / 1e12,
+                             "note": "includes k_transpose_pieces"}
+    if ph.get("ab_products", 0) > 0:
+        kern["k_ab_tc"] = {"mma_tflop": ab / 1e12, "ms": ph["ab_products"],
+                           "achieved_tflops": ab / (ph["ab_products"] / 1e3) / 1e12}
+    roof = None
+    if kern:
+        dom = max(kern, key=lambda k: kern[k]["ms"])
+        rec = traffic_record("sector_sigma_c64")
+        roof = {"bound": "tensor", "kernel": dom, "achieved": kern[dom]["achieved_tflops"],
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": kern[dom]["achieved_tflops"] /
+                peaks["bf16_tflops"], "peak_kind": peaks["kind"],
+                "traffic": (rec["bytes_per_launch"].get(dom) if rec else None),
+                "traffic_note": ("ncu DRAM bytes of one launch (%s)" % rec["capture"]) if rec else
+                "no ncu record for the current kernel sources",
+                "algorithmic": "bf16 MMA flops issued per launch (six bf16 piece products per float32 product)"}
+    t_sig = ph["expectation"] / 1000.0
+    sb = sector_touched_bytes(p["ops"], p["n_orb"], p["na"], p["nb"], 8)
+    t_rot = ph["forward"] / L / 1000.0
+    t_adj = ph["reverse"] / L / 1000.0
+    rec = traffic_record("sector_sigma_c64")
+    sect = {"storage": "sector: C(15,5)^2 = 9,018,009 amplitudes (72 MB complex64), L2-resident",
+            "value": throughput(world, K, s64["ms"]), "unit": UNIT, "ms_per_step": s64["ms"] / K,
+            "phases_ms": ph, "clocks": s64["clocks"], "gpu_launches": int(s64["launches"]),
+            "expectation_form": SIGMA_KERNELS.get(s64["variant"], "expectation form %d" % s64["variant"]),
+            "roofline": roof, "tensor_kernels": kern,
+            "useful": {"tflops": useful / t_sig / 1e12, "gflop": useful / 1e9,
+                       "algorithmic": "%d determinants x %d connections x 4 flops of sparse work per sigma"
+                                      % (D, per)},
+            "sigma_traffic_bytes": rec["bytes_per_sigma"] if rec else None,
+            "kernels": {"rotation_l": {"algorithmic_gbs": sb.sum() / L / t_rot / 1e9, "mean_launch_ms": t_rot * 1e3},
+                        "adjoint_l": {"algorithmic_gbs": 2.0 * sb.sum() / L / t_adj / 1e9,
+                                      "mean_launch_ms": t_adj * 1e3}},
+            "autotune": s64["tuned"],
+            "abs_dE_vs_dense_c64": abs(s64["out"]["E"] - head["out"]["E"]),
+            "max_abs_dg_vs_dense_c64": float(np.max(np.abs(s64["out"]["g"] - head["out"]["g"])))}
+    if golden is not None:
+        sect["vs_oracle"] = vs_golden(s64["out"], golden)
+    if s128 is not None:
+        sect["fp64_state"] = {"value": throughput(world, K, s128["ms"]), "ms_per_step": s128["ms"] / K,
+                              "phases_ms": s128["phases"],
+                              "vs_oracle": vs_golden(s128["out"], golden) if golden is not None else None}
+        if head128 is not None:
+            sect["abs_dE_vs_dense_c128"] = abs(s128["out"]["E"] - head128["out"]["E"])
+    return sect
+
+
+def measured_tensor_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"bf16_tflops": float(d["bf16_tflops"]), "kind": "measured burst (MEASURED_PEAKS.json bf16_tflops)"}
+    return {"bf16_tflops": 1900.0, "kind": "fallback 1.9 PFLOP/s bf16 burst"}
+
+
+def per_config_rows(args, stream, peak, rbatch):
+    """Configs 1-4 beside the headline: GPU evaluations per second (dense storage, the workload's own
+    dtype; CUDA events, after warm-up) with the roof that binds them, and the CPU oracle timed on full
+    evaluations -- energy only and energy + gradient (+ 1-RDM for config 3) separately -- with the GPU
+    results' deviation from it.  Config 4: the oracle over all 512 instances (energy + gradient)."""
+    import torch
+    import oracle
+    from oracle import route_a as A
+    from paper_2405_11567_gb300 import inputs, sv
+    out = {"cores": oracle.num_threads()}
+    roofs = {1: "launch latency: 4 KiB state, 15 one-launch operators (microseconds each)",
+             2: "launch latency / L2: 1 MiB state, 198 operators",
+             3: "L2 / HBM: 128 MiB (complex64) and 256 MiB (complex128) vectors against a 126 MB L2"}
+    for cid, dtypes in ((1, ("c128",)), (2, ("c128",)), (3, ("c64", "c128"))):
+        p = inputs.config_problem(cid)
+        n, L = p["n_qubits"], len(p["ops"])
+        with_grad, with_rdm = cid >= 2, cid == 3
+        sec = oracle.Sector(n, p["na"], p["nb"])
+        psi0 = A.hf_state(sec, p["occ"])
+        t0 = time.perf_counter()
+        psi = A.apply_ansatz(sec, p["ops"], p["theta"], psi0)
+        E_o = A.energy(sec, p["h"], p["eri"], p["e_nuc"], psi)
+        t_e = time.perf_counter() - t0
+        row = {"workload": "n%d_ne%d_%s_%s" % (n, p["n_elec"], "uccsd" if cid < 3 else "adapt%d" % L,
+                                               "/".join(dtypes)),
+               "oracle": {"energy_only_s": t_e, "energy_only_evals_per_s": 1.0 / t_e}, "gpu": {},
+               "binding_roof": roofs[cid]}
+        g_o = rdm_o = None
+        if with_grad:
+            t0 = time.perf_counter()
+            _, g_o = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], p["theta"], psi0)
+            if with_rdm:
+                rdm_o = A.rdm1(sec, psi)
+            t_g = time.perf_counter() - t0
+            row["oracle"].update({"energy_grad_s": t_g, "energy_grad_evals_per_s": 1.0 / t_g,
+                                  "includes_rdm1": with_rdm})
+        ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+        for dtype in dtypes:
+            st = sv.StateVector(n, dtype, stream)
+            res = {}
+
+            def energy_only():
+                st.prepare_hf(p["occ"])
+                st.apply_ansatz(p["ops"], p["theta"])
+                return st.energy(ham)
+
+            def full():
+                st.prepare_hf(p["occ"])
+                E, g = st.energy_grad(ham, p["ops"], p["theta"])
+                r = st.rdm1() if with_rdm else None
+                return E, g, r
+
+            for name, fn in (("energy_only", energy_only),) + ((("energy_grad", full),) if with_grad else ()):
+                for _ in range(3):
+                    fn()
+                torch.cuda.synchronize()
+                k = 20 if cid < 3 else 5
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(k):
+                    r = fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / k
+                res[name] = {"ms": ms, "evals_per_s": 1000.0 / ms}
+                if name == "energy_only":
+                    res[name]["abs_dE_vs_oracle"] = abs(r - E_o)
+                else:
+                    res[name]["abs_dE_vs_oracle"] = abs(r[0] - E_o)
+                    res[name]["max_abs_dg_vs_oracle"] = float(np.max(np.abs(r[1] - g_o)))
+                    if with_rdm:
+                        res[name]["max_abs_drdm_vs_oracle"] = float(np.max(np.abs(r[2] - rdm_o)))
+            if cid == 3 and "energy_grad" in res:
+                tb = touched_bytes(p["ops"], n, 8 if dtype == "c64" else 16).sum()
+                res["sweeps_algorithmic_gbs"] = 3.0 * tb / (res["energy_grad"]["ms"] / 1e3) / 1e9
+                res["sweeps_frac_of_hbm_peak"] = res["sweeps_algorithmic_gbs"] / peak
+            row["gpu"][dtype] = res
+            st.close()
+        ham.close()
+        out["config%d" % cid] = row
+    # config 4: the oracle over every instance of the batch
+    probs = inputs.batch_problems(512)
+    t0 = time.perf_counter()
+    for q in probs:
+        sec = oracle.Sector(q["n_qubits"], q["na"], q["nb"])
+        A.energy_grad(sec, q["h"], q["eri"], q["e_nuc"], q["ops"], q["theta"], A.hf_state(sec, q["occ"]))
+    t_b = time.perf_counter() - t0
+    row = {"oracle": {"energy_grad_s_all_512": t_b, "instance_evals_per_s": 512 / t_b},
+           "binding_roof": "shared memory and barriers inside one block per instance (persistent launch)"}
+    if rbatch is not None:
+        row["gpu"] = {"ms_per_batch": rbatch["ms_per_batch"], "instance_evals_per_s": rbatch["instance_evals_per_s"]}
+    out["config4"] = row
+    return out
 
 
 def op_profile(args):
@@ -608,6 +873,111 @@ def op_profile(args):
     return 0
 
 
+def traffic_probe(args):
+    """One dense complex64 energy + gradient evaluation (no autotuning, no warm-up) at --qubits: the
+    reverse sweep's k_adjoint_i launches are the op list backwards.  Writes, per launch, the op, its lowest
+    address bit in the automatic layout and its algorithmic bytes, plus up to two launches of each
+    lowest-bit class to capture (ncu -k regex:k_adjoint_i -s <launch> -c 1)."""
+    import torch
+    from paper_2405_11567_gb300 import build as libbuild
+    from paper_2405_11567_gb300 import sv
+    libbuild.build()
+    if not args.qubits:
+        args.qubits = 26
+    p = problem(args)
+    n, L = p["n_qubits"], len(p["ops"])
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = sv.StateVector(n, "c64")
+    st.prepare_hf(p["occ"])
+    st.energy_grad(ham, p["ops"], p["theta"])
+    torch.cuda.synchronize()
+    lay = [int(x) for x in st.layout()]
+    tb = 2.0 * touched_bytes(p["ops"], n, 8)
+    launches, pick = [], {}
+    for j in range(L):
+        k = L - 1 - j
+        b = min(lay[q] for q in op_qubits(p["ops"][k]))
+        launches.append({"launch": j, "op": k, "lowest_bit": b, "alg_bytes": float(tb[k]),
+                         "kind": int(p["ops"][k][0])})
+        c = lowest_bit_class(b)
+        if int(p["ops"][k][0]) in (2, 4) and len(pick.setdefault(c, [])) < 2:
+            pick[c].append(j)
+    out = {"workload": workload_config(p)["workload"], "layout": lay, "launches": launches,
+           "capture": sorted(j for v in pick.values() for j in v)}
+    with open(args.traffic_probe, "w") as f:
+        json.dump(out, f)
+    print(" ".join(str(j) for j in out["capture"]))
+    return 0
+
+
+def _ncu_rows(path):
+    """(kernel name, metric name -> value in base units) per captured launch of an ncu --csv log."""
+    import csv
+    rows = {}
+    with open(path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        key = (r["ID"], r["Kernel Name"])
+        v = r["Metric Value"].replace(",", "")
+        try:
+            rows.setdefault(key, {})[r["Metric Name"]] = float(v)
+        except ValueError:
+            pass
+    return rows
+
+
+def record_traffic(argv):
+    """Write one record of profiles/traffic.json from ncu captures (--metrics dram__bytes_read.sum,
+    dram__bytes_write.sum,gpu__time_duration.sum --print-units base --csv), keyed by the current hash of the
+    measured kernels' sources."""
+    import re
+    what, files = argv[0], argv[1:]
+    recs = {}
+    if os.path.exists(TRAFFIC_RECORDS):
+        with open(TRAFFIC_RECORDS) as f:
+            recs = json.load(f)
+    if what == "dense":
+        with open(files[0]) as f:
+            probe = json.load(f)
+        # DRAM reads / the algorithmic reads of the launch, per lowest-address-bit class.  The kernel
+        # writes back exactly the sectors it read; a capture of a few-GB problem undercounts the writes
+        # (lines still dirty in L2 when the kernel ends), so traffic = 2 x reads is recorded.
+        per, wr = {}, {}
+        for path in files[1:]:
+            j = int(re.search(r"_(\d+)\.csv$", path).group(1))
+            (key, m), = _ncu_rows(path).items()
+            ln = probe["launches"][j]
+            c = lowest_bit_class(ln["lowest_bit"])
+            per.setdefault(c, []).append(2.0 * m["dram__bytes_read.sum"] / ln["alg_bytes"])
+            wr.setdefault(c, []).append(2.0 * m["dram__bytes_write.sum"] / ln["alg_bytes"])
+        ratio = {c: float(np.mean(v)) for c, v in per.items()}
+        recs["dense_adjoint_c64"] = {
+            "kernel": "k_adjoint_i (complex64)", "ratio_by_lowest_bit": ratio,
+            "write_ratio_by_lowest_bit_as_captured": {c: float(np.mean(v)) for c, v in wr.items()},
+            "launches_per_class": {c: len(v) for c, v in per.items()},
+            "capture": "%s, %d launches" % (probe["workload"], sum(len(v) for v in per.values())),
+            "ratio": "2 x DRAM read bytes / algorithmic bytes (reads and write-backs move the same sectors)",
+            "sources_sha256": sources_sha256(TRAFFIC_SOURCES["dense_adjoint_c64"])}
+    elif what == "sector":
+        rows = _ncu_rows(files[0])
+        by = {}
+        for (rid, name), m in rows.items():
+            nm = name.replace("<unnamed>::", "").replace("(anonymous namespace)::", "")
+            base = re.sub(r"<.*", "", nm.split("(")[0]).strip().split()[-1].split("::")[-1]
+            by[base] = by.get(base, 0.0) + m["dram__bytes_read.sum"] + m["dram__bytes_write.sum"]
+        recs["sector_sigma_c64"] = {
+            "kernels": sorted(by), "bytes_per_launch": by, "bytes_per_sigma": float(sum(by.values())),
+            "capture": "30 qubits, sector storage, complex64, one launch of each expectation kernel",
+            "sources_sha256": sources_sha256(TRAFFIC_SOURCES["sector_sigma_c64"])}
+    else:
+        raise SystemExit("--record-traffic dense PROBE CSV... | sector CSV")
+    with open(TRAFFIC_RECORDS, "w") as f:
+        json.dump(recs, f, indent=1, sort_keys=True)
+        f.write("\n")
+    print(json.dumps(recs, indent=1))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -633,6 +1003,15 @@ def main():
                     help="profiling only: time just the sector-storage complex64 step (prints no bench line)")
     ap.add_argument("--op-profile", action="store_true",
                     help="per-operator rotation bandwidth by lowest address bit (diagnostic, not the bench line)")
+    ap.add_argument("--no-per-config", action="store_true",
+                    help="skip the per-config block (configs 1-4 on the GPU and the oracle timed on full evaluations)")
+    ap.add_argument("--traffic-probe", metavar="OUT_JSON", default=None,
+                    help="profiling only: one dense complex64 energy_grad at --qubits (default 26), no autotuning; "
+                         "writes the reverse sweep's launches (op, lowest address bit, algorithmic bytes) to OUT_JSON")
+    ap.add_argument("--record-traffic", nargs="+", metavar="FILE", default=None,
+                    help="write the traffic record of profiles/traffic.json from ncu CSV captures: "
+                         "'dense PROBE_JSON CSV...' (one k_adjoint_i launch per CSV, named ..._<launch>.csv) or "
+                         "'sector CSV' (one launch of each expectation kernel)")
     ap.add_argument("--qubits", type=int, default=0,
                     help="profiling only: a smaller register (same generator, n/3 rounded to even electrons, "
                          "200 operators); the bench line is then not the headline workload")
@@ -640,6 +1019,10 @@ def main():
     rank, world, local_rank = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.record_traffic:
+        return record_traffic(args.record_traffic)
+    if args.traffic_probe:
+        return traffic_probe(args)
     if args.op_profile:
         return op_profile(args)
     if world > 1:

@@ -364,7 +364,7 @@ typedef enum {
                                        fastest estimate among the sizes that fit) */
     SV_OPT_ROT_BLOCKS_PER_SM = 8,   /* launch geometry of the dense rotation and adjoint
                                        kernels: at most this many blocks per SM (1..64,
-                                       default 8) */
+                                       default 32) */
     SV_OPT_SECT_BLOCKS_PER_SM = 9,  /* the same for the sector rotation / adjoint kernels
                                        (default 8) */
     SV_OPT_RDM_BLOCKS_PER_SM = 10,  /* the same for the string-row 1-RDM (default 4) */
@@ -394,21 +394,32 @@ typedef enum {
                                        are one allocation (not with a caller-provided
                                        adjoint vector, checkpoints or the record-scan
                                        expectation); 0 two separate vectors */
-    SV_OPT_WAIT_POLLS = 15,         /* the tensor-core expectation kernels (variants 4
-                                       and 5): polls of each bounded wait on an mbarrier
-                                       (each poll a try-wait and a 32 ns sleep) before the
-                                       kernel gives up, waits (bounded) for its copies
-                                       and MMAs in flight, frees its tensor memory and
-                                       returns; the call then fails with SV_ERR_CUDA and
-                                       the handle needs sv_prepare_hf / sv_prepare_state.
+    SV_OPT_WAIT_POLLS = 15,         /* polls of each bounded wait (each poll a try-wait
+                                       and a 32 ns sleep) before a kernel gives up: the
+                                       tensor-core expectation kernels' mbarrier waits
+                                       (variants 4 and 5: the kernel then waits, bounded,
+                                       for its copies and MMAs in flight, frees its
+                                       tensor memory and returns) and the grid barriers
+                                       of the whole-sweep launches (SV_OPT_SECTOR_SWEEP);
+                                       the call then fails with SV_ERR_CUDA and the
+                                       handle needs sv_prepare_hf / sv_prepare_state.
                                        1..2^30, default 2^22 */
-    SV_OPT_TEST_STALL = 16          /* failure-detection test hook, 0 (default) off: bit 0
+    SV_OPT_TEST_STALL = 16,         /* failure-detection test hook, 0 (default) off: bit 0
                                        makes k_same_tc's producer issue no copy, bit 1
                                        makes k_ab_tc's builders stage and write nothing,
                                        so that the consumers' first bounded waits run out
                                        with no copy or MMA in flight (the path of a stuck
                                        producer).  No fault and no hang: the call reports
                                        SV_ERR_CUDA */
+    SV_OPT_SECTOR_SWEEP = 17        /* sector storage: 1 (default) each forward and reverse
+                                       sweep is one cooperative launch that walks the
+                                       operators in order with a grid-wide barrier
+                                       between them (every barrier wait bounded by
+                                       SV_OPT_WAIT_POLLS: past it the call fails with
+                                       SV_ERR_CUDA); used where no checkpoint copy falls
+                                       inside the sweep and the device accepts the
+                                       cooperative launch, else one launch per operator
+                                       (0 always) */
 } sv_option;
 
 /* Options change launch choices or summation order only: results agree within the
@@ -432,14 +443,17 @@ sv_status sv_autotune(sv_handle h, sv_ham_handle ham, const sv_excitation *ops, 
 /* ---- introspection ------------------------------------------------------------ */
 
 /* Number of phases reported by sv_phase_times. */
-#define SV_PHASES 6
+#define SV_PHASES 8
 
 /* Device time (ms) of each phase of the last sv_energy_grad / sv_rdm1 call,
  * measured with CUDA events on the handle's stream while SV_OPT_PROFILE is 1:
  * [0] reference preparation, [1] forward sweep (one rotation kernel per op),
  * [2] expectation (sigma and energy), [3] reverse sweep (one adjoint kernel per
  * op plus the gradient reduction), [4] restoring psi(theta), [5] the last
- * sv_rdm1.  Writes min(n_out, SV_PHASES) values; phases not run are 0. */
+ * sv_rdm1; inside [2], for the tensor-core expectation forms (variants 4 and 5):
+ * [6] the same-spin products (k_transpose_pieces + k_same_tc), [7] the
+ * alpha-beta products (k_ab_tc, variant 5).  Writes min(n_out, SV_PHASES)
+ * values; phases not run are 0. */
 sv_status sv_phase_times(sv_handle h, double *ms_out, int n_out);
 
 /* Message of the last failing call on h (h == NULL: on this thread). Never NULL. */

@@ -1065,14 +1065,18 @@ static cudaError_t launch_same_t(RowArgs<Amp> A, const RowTables &T, int dtype, 
                                                        g.abtc ? g.Xi : nullptr, g.ldi);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
+        if (g.ev && (e = cudaEventRecord(g.ev[0], st)) != cudaSuccess) return e;
         e = launch_same_tc(g.Mp, g.pm, g.Xp, g.px, g.Xtp, g.pt, g.G, g.planes, T.Da, T.Db, g.lda, g.ldb, g.err,
                            g.spins, g.stall & 1, st);
         if (e != cudaSuccess) return e;
+        if (g.ev && (e = cudaEventRecord(g.ev[1], st)) != cudaSuccess) return e;
         A.same_gemm = 1;
         if (g.abtc) {
+            if (g.ev && (e = cudaEventRecord(g.ev[2], st)) != cudaSuccess) return e;
             e = launch_ab_tc(g.Xi, g.planes, T.stra, T.strb, T.ra, g.Bp, g.pb, g.H, g.hplane, T.Da, T.Db, T.N, g.na,
                              g.nb, g.err, g.spins, (g.stall >> 1) & 1, sm_count, st);
             if (e != cudaSuccess) return e;
+            if (g.ev && (e = cudaEventRecord(g.ev[3], st)) != cudaSuccess) return e;
             k_sigma_comb<Amp, true><<<T.Db, kThreads, 0, st>>>(A, g);
         } else {
             e = launch_ab_k(A, K, ab_smem(dtype, K, T), st);

@@ -266,9 +266,158 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_li(A *__restrict__ CL, con
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// ---------------------------------------------------------------- whole sweeps in one launch
+
+// The forward and reverse sweeps as one persistent launch each: the grid walks the
+// operators in order, every block taking its share of an operator's pairs exactly as
+// k_rotate_l / k_adjoint_li do, with a grid-wide barrier between operators (an
+// operator reads amplitudes the previous one wrote in other blocks).  The per-operator
+// launches of sector storage are latency bound (a few microseconds of work each on
+// L2-resident data): one launch replaces their launch gaps and ramp-ups with barriers.
+// Launched cooperatively, so every block is resident and every barrier can complete;
+// each wait is still bounded -- past the limit the block sets *err and stops, and the
+// call reports the failure.
+struct SweepArgs {
+    const uint32_t *lists;   // the ops' pair lists (k_build_lists)
+    const int4 *info;        // per op: alpha offset, alpha length, beta offset, beta length
+    const double2 *cs;       // per op: (cos theta, sin theta)
+    int n_ops, Da;
+    unsigned int *bar;       // barrier arrivals, zero at launch
+    int *err;                // set to 1 when a barrier wait runs out
+    uint32_t spins;          // polls of a barrier wait
+    double *partial;         // reverse sweep: [n_ops][gridDim.x] gradient partials
+};
+
+// Grid-wide barrier number `gen` (0, 1, ...): every block arrives once per barrier.
+__device__ __forceinline__ bool sweep_barrier(const SweepArgs &g, unsigned int gen, volatile int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(g.bar, 1u);
+        const unsigned int target = (gen + 1u) * gridDim.x;
+        bool ok = true;
+        for (uint32_t it = 0; *(volatile unsigned int *)g.bar < target; ++it) {
+            if (it >= g.spins) {
+                ok = false;
+                atomicExch(g.err, 1);
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok;
+}
+
+template <typename A>
+__global__ void __launch_bounds__(kThreads) k_sweep_rotate_l(A *__restrict__ psi, SweepArgs g) {
+    using R = real_of<A>;
+    __shared__ volatile int s_ok;
+    unsigned int gen = 0;
+    for (int k = 0; k < g.n_ops; ++k) {
+        const int4 li = g.info[k];
+        const int na_l = li.y, nb_l = li.w;
+        if (na_l <= 0 || nb_l <= 0) continue;  // no pair in the sector: nothing written, no barrier
+        if (gen > 0 && !sweep_barrier(g, gen - 1, &s_ok)) return;
+        ++gen;
+        const uint32_t *al = g.lists + li.x, *bl = g.lists + li.z;
+        const R c = (R)g.cs[k].x, sn = (R)g.cs[k].y;
+        PairWalk w(na_l);
+        while (w.r < nb_l) {
+            size_t I[kPairBatch], J[kPairBatch];
+            bool ok[kPairBatch];
+            R ss[kPairBatch];
+            #pragma unroll
+            for (int v = 0; v < kPairBatch; ++v) {
+                ok[v] = w.r < nb_l;
+                const uint32_t eb = ok[v] ? bl[w.r] : 0u, ea = ok[v] ? al[w.i] : 0u;
+                I[v] = (size_t)(eb & 0x7FFFu) * g.Da + (ea & 0x7FFFu);
+                J[v] = (size_t)(eb >> 16) * g.Da + (ea >> 16);
+                ss[v] = ((ea ^ eb) & 0x8000u) ? -sn : sn;
+                w.next();
+            }
+            A u[kPairBatch], x[kPairBatch];
+            #pragma unroll
+            for (int v = 0; v < kPairBatch; ++v) {
+                u[v] = psi[I[v]];
+                x[v] = psi[J[v]];
+            }
+            #pragma unroll
+            for (int v = 0; v < kPairBatch; ++v) {
+                if (!ok[v]) continue;
+                psi[I[v]] = lin2<A>(c, u[v], -ss[v], x[v]);
+                psi[J[v]] = lin2<A>(c, x[v], ss[v], u[v]);
+            }
+        }
+    }
+}
+
+// Reverse sweep on the interleaved (psi, lambda) matrix, ops n_ops - 1 down to 0; the
+// arithmetic of k_adjoint_li, one float64 partial per block and op (fixed order).
+template <typename A>
+__global__ void __launch_bounds__(kThreads) k_sweep_adjoint_li(A *__restrict__ CL, SweepArgs g) {
+    using R = real_of<A>;
+    __shared__ double red[kThreads / 32];
+    __shared__ volatile int s_ok;
+    AmpPair<A> *P = reinterpret_cast<AmpPair<A> *>(CL);
+    unsigned int gen = 0;
+    for (int k = g.n_ops - 1; k >= 0; --k) {
+        const int4 li = g.info[k];
+        const int na_l = li.y, nb_l = li.w;
+        double acc = 0.0;
+        if (na_l > 0 && nb_l > 0) {
+            if (gen > 0 && !sweep_barrier(g, gen - 1, &s_ok)) return;
+            ++gen;
+            const uint32_t *al = g.lists + li.x, *bl = g.lists + li.z;
+            const R c = (R)g.cs[k].x, sn = (R)g.cs[k].y;
+            PairWalk w(na_l);
+            while (w.r < nb_l) {
+                size_t I[kPairBatch], J[kPairBatch];
+                bool ok[kPairBatch], neg[kPairBatch];
+                #pragma unroll
+                for (int v = 0; v < kPairBatch; ++v) {
+                    ok[v] = w.r < nb_l;
+                    const uint32_t eb = ok[v] ? bl[w.r] : 0u, ea = ok[v] ? al[w.i] : 0u;
+                    I[v] = (size_t)(eb & 0x7FFFu) * g.Da + (ea & 0x7FFFu);
+                    J[v] = (size_t)(eb >> 16) * g.Da + (ea >> 16);
+                    neg[v] = ((ea ^ eb) & 0x8000u) != 0u;
+                    w.next();
+                }
+                AmpPair<A> pu[kPairBatch], px[kPairBatch];
+                #pragma unroll
+                for (int v = 0; v < kPairBatch; ++v) {
+                    pu[v] = P[I[v]];
+                    px[v] = P[J[v]];
+                }
+                R t = 0;
+                #pragma unroll
+                for (int v = 0; v < kPairBatch; ++v) {
+                    if (!ok[v]) continue;
+                    const A u = pu[v].c, x = px[v].c, lu = pu[v].l, lx = px[v].l;
+                    const R ti = re_dot(lx, u) - re_dot(lu, x);
+                    t += neg[v] ? -ti : ti;
+                    const R ss = neg[v] ? -sn : sn;
+                    AmpPair<A> ou, ox;
+                    ou.c = lin2<A>(c, u, ss, x);
+                    ox.c = lin2<A>(c, x, -ss, u);
+                    ou.l = lin2<A>(c, lu, ss, lx);
+                    ox.l = lin2<A>(c, lx, -ss, lu);
+                    P[I[v]] = ou;
+                    P[J[v]] = ox;
+                }
+                acc += (double)t;
+            }
+        }
+        const double s = block_sum(acc, red);
+        if (threadIdx.x == 0) g.partial[(size_t)k * gridDim.x + blockIdx.x] = s;
+    }
+}
+
 // Density matrix by rows: a block takes beta strings (rows) Ib = blockIdx.x,
-// blockIdx.x + gridDim.x, ...; for each row its warps sum, in the state precision,
-//   norm and alpha occupations   sum_a |C[b][a]|^2 (a_p)
+// blockIdx.x + gridDim.x, ...; for each row
+//   norm and alpha occupations   sum_a |C[b][a]|^2 (a_p)                (all warps)
 //   beta occupations             the row norm when b holds p
 //   alpha pairs p < q            sum over a with q in a, p not in a of
 //                                conj(C[b][a']) C[b][a] (-1)^popc(x & between(2p, 2q)), a' = a - q + p
@@ -276,9 +425,13 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_li(A *__restrict__ CL, con
 //   beta pairs p < q (b holds q, not p)
 //                                sum_a conj(C[b'][a]) C[b][a] (-1)^popc(x & between(2p+1, 2q+1))
 // (x = spread(a) | spread(b)), in the element order norm, n occupations
-// (j = 2p + sigma), alpha pairs, beta pairs.  Each warp's sum goes to its own
-// shared slot; after each row the block adds the slots in warp order into float64
-// running sums, written to partial[e][blockIdx.x] at the end: fixed-order sums.
+// (j = 2p + sigma), alpha pairs, beta pairs.  Each pair element belongs to one warp
+// (pairs dealt round-robin to the warps), which sums it over the row with its lanes
+// and one warp reduction; the norm and occupations are summed by every warp over a
+// share of the row.  Each warp writes its sums to its own shared slots; after each row
+// the block adds them (the owner's slot for a pair element, the warps in order for the
+// others) into float64 running sums, written to partial[e][blockIdx.x] at the end:
+// fixed-order sums.
 template <typename A>
 __global__ void __launch_bounds__(kThreads) k_rdm_rows(const A *__restrict__ C, SectTabs T, int N,
                                                        const uint32_t *__restrict__ alist,
@@ -287,15 +440,15 @@ __global__ void __launch_bounds__(kThreads) k_rdm_rows(const A *__restrict__ C, 
     using R = real_of<A>;
     extern __shared__ double rdm_s[];  // [2 n_el] running sums, then [kThreads/32][2 n_el] warp slots
     const int n = 2 * N, npair = N * (N - 1) / 2, n_el = 1 + n + 2 * npair, W = 2 * n_el;
+    constexpr int NW = kThreads / 32;
     double *acc = rdm_s, *slot = rdm_s + W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *my = slot + warp * W;
     for (int i = threadIdx.x; i < W; i += blockDim.x) acc[i] = 0.0;
-    const uint32_t maskN = (1u << N) - 1u;
     for (int Ib = blockIdx.x; Ib < T.Db; Ib += gridDim.x) {
         const uint32_t b = T.strb[Ib], xb = T.sb[Ib];
         const A *row = C + (size_t)Ib * T.Da;
-        // norm and alpha occupations
+        // norm and alpha occupations (every warp, a share of the row)
         R nrm = 0, occ[16];
         #pragma unroll
         for (int p = 0; p < 16; ++p) occ[p] = 0;
@@ -324,50 +477,57 @@ __global__ void __launch_bounds__(kThreads) k_rdm_rows(const A *__restrict__ C, 
                 my[2 * (2 + 2 * p) + 1] = 0.0;
             }
         }
-        // alpha pairs (same row) and beta pairs (row b')
-        int e = 1 + n;
-        for (int s = 0; s < 2; ++s)
-            for (int p = 0; p < N; ++p)
-                for (int q = p + 1; q < N; ++q, ++e) {
-                    const uint32_t m = (1u << p) | (1u << q), f = 1u << q;
-                    const uint32_t bm = between(2 * p + s, 2 * q + s);
-                    R re = 0, im = 0;
-                    if (s == 0) {
-                        // the alpha strings holding q but not p, from the pair's list: entry =
-                        // rank | parity of its alpha bits under bm << 15 | partner rank << 16
-                        const int4 li = ainfo[e - 1 - n];
-                        const uint32_t *L = alist + li.x, rsg = (uint32_t)par(xb & bm);
-                        for (int i = threadIdx.x; i < li.y; i += blockDim.x) {
-                            const uint32_t ea = L[i];
-                            const A u = row[ea & 0x7FFFu], v = row[ea >> 16];
-                            R ar = re_dot(v, u), ai = im_dot(v, u);  // conj(v) u
-                            if (((ea >> 15) & 1u) ^ rsg) { ar = -ar; ai = -ai; }
-                            re += ar;
-                            im += ai;
-                        }
-                        (void)f;
-                    } else if ((b & m) == f) {
-                        const A *row2 = C + (size_t)T.rb[b ^ m] * T.Da;
-                        for (int Ia = threadIdx.x; Ia < T.Da; Ia += blockDim.x) {
-                            const A u = row[Ia], v = row2[Ia];
-                            R ar = re_dot(v, u), ai = im_dot(v, u);
-                            if (par((T.sa[Ia] | xb) & bm)) { ar = -ar; ai = -ai; }
-                            re += ar;
-                            im += ai;
-                        }
-                    }
-                    re = warp_sum(re);
-                    im = warp_sum(im);
-                    if (lane == 0) {
-                        my[2 * e] = (double)re;
-                        my[2 * e + 1] = (double)im;
-                    }
+        // pair elements: element e = 1 + n + k (k = 0 .. 2 npair - 1; alpha pairs first) to warp k % NW
+        for (int k = warp; k < 2 * npair; k += NW) {
+            const int s = k >= npair, kk = s ? k - npair : k;
+            int p = 0, rem = kk;
+            while (rem >= N - 1 - p) {
+                rem -= N - 1 - p;
+                ++p;
+            }
+            const int q = p + 1 + rem, e = 1 + n + k;
+            const uint32_t m = (1u << p) | (1u << q), f = 1u << q;
+            const uint32_t bm = between(2 * p + s, 2 * q + s);
+            R re = 0, im = 0;
+            if (s == 0) {
+                // the alpha strings holding q but not p, from the pair's list: entry =
+                // rank | parity of its alpha bits under bm << 15 | partner rank << 16
+                const int4 li = ainfo[kk];
+                const uint32_t *L = alist + li.x, rsg = (uint32_t)par(xb & bm);
+                for (int i = lane; i < li.y; i += 32) {
+                    const uint32_t ea = L[i];
+                    const A u = row[ea & 0x7FFFu], v = row[ea >> 16];
+                    R ar = re_dot(v, u), ai = im_dot(v, u);  // conj(v) u
+                    if (((ea >> 15) & 1u) ^ rsg) { ar = -ar; ai = -ai; }
+                    re += ar;
+                    im += ai;
                 }
-        (void)maskN;
+            } else if ((b & m) == f) {
+                const A *row2 = C + (size_t)T.rb[b ^ m] * T.Da;
+                for (int Ia = lane; Ia < T.Da; Ia += 32) {
+                    const A u = row[Ia], v = row2[Ia];
+                    R ar = re_dot(v, u), ai = im_dot(v, u);
+                    if (par((T.sa[Ia] | xb) & bm)) { ar = -ar; ai = -ai; }
+                    re += ar;
+                    im += ai;
+                }
+            }
+            re = warp_sum(re);
+            im = warp_sum(im);
+            if (lane == 0) {
+                my[2 * e] = (double)re;
+                my[2 * e + 1] = (double)im;
+            }
+        }
         __syncthreads();
         for (int i = threadIdx.x; i < W; i += blockDim.x) {
+            const int e = i >> 1;
             double t = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) t += slot[w * W + i];
+            if (e < 1 + n) {
+                for (int w = 0; w < NW; ++w) t += slot[w * W + i];
+            } else {
+                t = slot[((e - 1 - n) % NW) * W + i];
+            }
             acc[i] += t;
         }
         __syncthreads();
@@ -470,6 +630,50 @@ cudaError_t launch_adjoint_li(void *CL, int dtype, const uint32_t *al, int na_l,
     SV_DISPATCH_AMP(dtype, k_adjoint_li<A><<<grid, kThreads, 0, st>>>((A *)CL, al, na_l, bl, nb_l, Da,
                                                                        (real_of<A>)c, (real_of<A>)s, partial));
     return cudaGetLastError();
+}
+
+// Blocks of a whole-sweep launch: at most bps per SM (8 by default) and no more than
+// can be resident at once (a cooperative launch needs every block resident).
+template <typename K>
+static int sweep_grid_for(K kernel, int Db, int sm_count, int bps) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const int want = bps > 0 ? bps : 8;
+    if (per_sm > want) per_sm = want;
+    const int cap = per_sm * sm_count;
+    return Db < cap ? Db : cap;
+}
+
+int sweep_grid(int dtype, bool adjoint, int Db, int sm_count, int bps) {
+    int grid = 0;
+    SV_DISPATCH_AMP(dtype, grid = adjoint ? sweep_grid_for(k_sweep_adjoint_li<A>, Db, sm_count, bps)
+                                          : sweep_grid_for(k_sweep_rotate_l<A>, Db, sm_count, bps));
+    return grid;
+}
+
+// One cooperative launch of the forward (adjoint = false: ops 0 .. n_ops-1 on psi) or the
+// reverse sweep (adjoint = true: ops n_ops-1 .. 0 on the interleaved matrix, gradient
+// partials [n_ops][grid] into partial).  info: the ops' int4 list records (device), cs
+// their (cos, sin) (device), bar a zeroed device counter, err the device error flag.
+// A refused cooperative launch returns its error (the caller falls back to one launch
+// per op).
+cudaError_t launch_sweep_l(void *buf, int dtype, bool adjoint, const uint32_t *lists, const int *info,
+                           const double *cs, int n_ops, int Da, int grid, unsigned int *bar, int *err, uint32_t spins,
+                           double *partial, cudaStream_t st) {
+    if (n_ops <= 0) return cudaSuccess;
+    if (grid <= 0) return cudaErrorInvalidValue;
+    SweepArgs g;
+    g.lists = lists; g.info = (const int4 *)info; g.cs = (const double2 *)cs; g.n_ops = n_ops; g.Da = Da;
+    g.bar = bar; g.err = err; g.spins = spins; g.partial = partial;
+    void *args[] = {&buf, &g};
+    cudaError_t e = cudaErrorInvalidValue;
+    SV_DISPATCH_AMP(dtype, e = cudaLaunchCooperativeKernel(
+                               adjoint ? (const void *)k_sweep_adjoint_li<A> : (const void *)k_sweep_rotate_l<A>,
+                               dim3(grid), dim3(kThreads), args, 0, st));
+    return e;
 }
 
 int rdm_rows_elements(int n) { return 1 + n + (n / 2) * (n / 2 - 1); }

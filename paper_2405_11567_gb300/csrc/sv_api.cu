@@ -58,6 +58,10 @@ cudaError_t launch_build_lists(const void *ops, int n_ops, const uint32_t *sa, c
                                int Da, int Db, uint32_t *out, cudaStream_t st);
 cudaError_t launch_rotate_l(void *psi, int dtype, const uint32_t *al, int na_l, const uint32_t *bl, int nb_l, int Da,
                             double c, double s, int grid, cudaStream_t st);
+int sweep_grid(int dtype, bool adjoint, int Db, int sm_count, int bps);
+cudaError_t launch_sweep_l(void *buf, int dtype, bool adjoint, const uint32_t *lists, const int *info,
+                           const double *cs, int n_ops, int Da, int grid, unsigned int *bar, int *err, uint32_t spins,
+                           double *partial, cudaStream_t st);
 cudaError_t launch_adjoint_li(void *CL, int dtype, const uint32_t *al, int na_l, const uint32_t *bl, int nb_l, int Da,
                               double c, double s, int grid, double *partial, cudaStream_t st);
 cudaError_t launch_adjoint_l(void *psi, void *lam, int dtype, const uint32_t *al, int na_l, const uint32_t *bl,
@@ -209,6 +213,23 @@ static sv_status ensure_lam(sv_handle h) {
     return SV_OK;
 }
 
+// The device flag of kernels with bounded waits and its pinned host copy.
+static sv_status ensure_kerr(sv_handle h) {
+    if (!h->kerr) {
+        SV_TRY(dev_alloc(h, (void **)&h->kerr, 16, "kernel error flag"));
+        SV_CUDA(h, cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream));
+    }
+    if (!h->hkerr) {
+        if (cudaMallocHost((void **)&h->hkerr, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            h->hkerr = nullptr;
+            return fail(h, SV_ERR_OOM, "pinned host allocation failed");
+        }
+        *h->hkerr = 0;
+    }
+    return SV_OK;
+}
+
 // Compact sigma [Db][Da] (sector-sized).
 static sv_status ensure_lbuf(sv_handle h) {
     const size_t cb = std::max<size_t>((size_t)h->Da * h->Db * h->amp_bytes, 16);
@@ -283,6 +304,16 @@ struct NvtxClose {
         }
     }
 };
+
+// ms between two recorded events (0 when either is missing or unreadable).
+static double elapsed_ev(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (!a || !b || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.0;
+    }
+    return ms;
+}
 
 static float elapsed(sv_handle h, int a, int b) {
     float ms = 0.f;
@@ -661,9 +692,62 @@ static sv_status ensure_rdm_lists(sv_handle h) {
     return ensure_op_lists(h, ops, h->rdm_lists);
 }
 
+// Sector storage: the ops' (cos, sin) on the device for whole-sweep launches (uploaded
+// once per call; the reverse sweep reuses them).
+static sv_status upload_sweep_angles(sv_handle h, const std::vector<OpDesc> &ops) {
+    const size_t need = 256 + 2 * std::max<size_t>(ops.size(), 1) * sizeof(double);
+    if (h->sweep_bytes < need) {
+        dev_free(h, h->sweep_buf, h->sweep_bytes);
+        h->sweep_buf = nullptr;
+        h->sweep_bytes = 0;
+        SV_TRY(dev_alloc(h, &h->sweep_buf, need, "sweep angles"));
+        h->sweep_bytes = need;
+    }
+    h->sweep_host.resize(2 * ops.size());
+    for (size_t k = 0; k < ops.size(); ++k) {
+        h->sweep_host[2 * k] = ops[k].c;
+        h->sweep_host[2 * k + 1] = ops[k].s;
+    }
+    if (!ops.empty())
+        SV_CUDA(h, cudaMemcpyAsync((uint8_t *)h->sweep_buf + 256, h->sweep_host.data(), 2 * ops.size() * sizeof(double),
+                                   cudaMemcpyHostToDevice, h->stream));
+    return SV_OK;
+}
+
+// One launch for a whole sector sweep (forward on psi, or reverse on the interleaved
+// matrix with gradient partials [L][grid]); false (nothing launched) where the
+// cooperative launch is refused or the option is off: the caller then launches per op.
+static bool sweep_once(sv_handle h, bool adjoint, void *buf, size_t L, int grid, double *partial) {
+    if (!h->sweep_mode || L == 0 || grid <= 0 || !h->sweep_buf || !h->kerr) return false;
+    if (cudaMemsetAsync(h->sweep_buf, 0, sizeof(unsigned int), h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const cudaError_t e = launch_sweep_l(buf, h->dtype, adjoint, (const uint32_t *)h->lists.buf, h->lists.dinfo,
+                                         (const double *)((const uint8_t *)h->sweep_buf + 256), (int)L, h->Da, grid,
+                                         (unsigned int *)h->sweep_buf, h->kerr, (uint32_t)h->wait_polls, partial,
+                                         h->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    h->launches++;
+    cudaMemcpyAsync(h->hkerr, h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    return true;
+}
+
 static sv_status forward(sv_handle h, const std::vector<OpDesc> &ops, bool checkpoints) {
     const int64_t C = h->ckpt_interval;
-    if (h->storage == 1 && !ops.empty()) SV_TRY(ensure_op_lists(h, ops, h->lists));
+    if (h->storage == 1 && !ops.empty()) {
+        SV_TRY(ensure_op_lists(h, ops, h->lists));
+        SV_TRY(ensure_kerr(h));
+        SV_TRY(upload_sweep_angles(h, ops));
+        // one launch for the whole sweep unless checkpoint copies are due in the middle
+        if (!(checkpoints && C > 0 && (size_t)C < ops.size()) &&
+            sweep_once(h, false, h->psi, ops.size(), sweep_grid(h->dtype, false, h->Db, h->sm_count, h->sect_bps),
+                       nullptr))
+            return SV_OK;
+    }
     const uint32_t *L = (const uint32_t *)h->lists.buf;
     const int G = sector_grid(h->Db, h->sm_count, h->sect_bps);
     for (size_t k = 0; k < ops.size(); ++k) {
@@ -747,18 +831,7 @@ static bool use_ab_tc(sv_handle h) {
 // multiple of 8 elements with zeros (16-byte row strides of the bf16 pieces, as TMA
 // requires).
 static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R, SameGemm *g) {
-    if (!h->kerr) {
-        SV_TRY(dev_alloc(h, (void **)&h->kerr, 16, "kernel error flag"));
-        SV_CUDA(h, cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream));
-    }
-    if (!h->hkerr) {
-        if (cudaMallocHost((void **)&h->hkerr, sizeof(int)) != cudaSuccess) {
-            cudaGetLastError();
-            h->hkerr = nullptr;
-            return fail(h, SV_ERR_OOM, "pinned host allocation failed");
-        }
-        *h->hkerr = 0;
-    }
+    SV_TRY(ensure_kerr(h));
     const size_t Da = (size_t)h->Da, Db = (size_t)h->Db, lda = (Da + 7) / 8 * 8, ldb = (Db + 7) / 8 * 8;
     // [Ma | Mb] (float32), the one-spin diagonals, then the three bf16 pieces of [Ma | Mb]
     // then the three bf16 pieces of the alpha-beta integral table (k_ab_tc) when N^2 <= 256
@@ -834,6 +907,12 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
     g->ldb = (int)ldb;
     g->err = h->kerr;
     g->spins = (uint32_t)h->wait_polls;
+    g->ev = nullptr;
+    if (h->profile) {
+        for (cudaEvent_t &e : h->tcev)
+            if (!e) SV_CUDA(h, cudaEventCreate(&e));
+        g->ev = h->tcev;
+    }
     g->stall = h->test_stall;
     g->abtc = 0;
     bool ab_ok = abtc;
@@ -875,7 +954,7 @@ static sv_status check_kernel_flag(sv_handle h) {
         *h->hkerr = 0;
         if (h->kerr) cudaMemsetAsync(h->kerr, 0, sizeof(int), h->stream);
         h->failed = true;
-        return fail(h, SV_ERR_CUDA, "tensor-core products: a bounded wait ran out");
+        return fail(h, SV_ERR_CUDA, "a bounded wait ran out (tensor-core products or a sweep's grid barrier)");
     }
     return SV_OK;
 }
@@ -891,6 +970,7 @@ static sv_status sigma_rows(sv_handle h, DevTables *T, const RowTables &R, const
     SV_CUDA(h, launch_sigma_rows(C, lam, lamc, h->dtype, h->n, R, T->hdiag, T->Jp, e_shift, h->partials, K,
                                  h->stream, sg ? &g : nullptr, h->sm_count));
     h->launches += sg ? 5 : (K ? 2 : 1);
+    if (sg && g.ev) h->tc_timed = 1 | (g.abtc ? 2 : 0);
     if (sg)
         SV_CUDA(h, cudaMemcpyAsync(h->hkerr, h->kerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     return SV_OK;
@@ -1273,10 +1353,13 @@ sv_status sv_destroy(sv_handle h) {
     dev_free(h, h->pool_lists.buf, h->pool_lists.bytes);
     dev_free(h, h->rdm_lists.buf, h->rdm_lists.bytes);
     dev_free(h, h->CLbuf, h->CLbuf_bytes);
+    dev_free(h, h->sweep_buf, h->sweep_bytes);
     dev_free(h, h->partials, h->partials_cap * sizeof(double));
     dev_free(h, h->dout, h->dout_cap * sizeof(double));
     if (h->hpinned) cudaFreeHost(h->hpinned);
     for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->tcev)
         if (e) cudaEventDestroy(e);
     delete h;
     return SV_OK;
@@ -1557,6 +1640,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     SV_TRY(ensure_partials(h, std::max<size_t>((size_t)G * std::max<size_t>(L, 1), need)));
     plan_checkpoints(h, L);
     h->prepared = false;
+    h->tc_timed = 0;
     SV_TRY(mark(h, 0, "sv_energy_grad: reference"));
     SV_TRY(prepare_reference(h));
     h->prepared = true;
@@ -1606,7 +1690,18 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
                                      h->stream));
         h->launches++;
     }
-    for (size_t kk = L; kk-- > 0;) {
+    // sector storage: the reverse sweep in one launch where it can (gradient partials
+    // [L][Gs], Gs its grid), else one launch per op ([L][G])
+    int Gred = G;
+    bool swept = false;
+    if (inter) {
+        const int Gs = sweep_grid(h->dtype, true, h->Db, h->sm_count, h->sect_bps);
+        if (Gs > 0 && Gs <= G && sweep_once(h, true, h->CLbuf, L, Gs, h->partials)) {
+            swept = true;
+            Gred = Gs;
+        }
+    }
+    for (size_t kk = swept ? 0 : L; kk-- > 0;) {
         if (inter) {
             const uint32_t *LB = (const uint32_t *)h->lists.buf;
             const int *li = &h->lists.info[4 * kk];
@@ -1632,7 +1727,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
                 SV_CUDA(h, cudaMemcpyAsync(wpsi, h->ckpt[j], vec_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
         }
     }
-    SV_CUDA(h, launch_reduce_rows(h->partials, (int)L, G, h->dout + 2, h->stream));
+    SV_CUDA(h, launch_reduce_rows(h->partials, (int)L, Gred, h->dout + 2, h->stream));
     h->launches++;
     SV_TRY(mark(h, 5, "sv_energy_grad: restore"));
     SV_CUDA(h, cudaMemcpyAsync(h->hpinned, h->dout, (2 + L) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1650,6 +1745,8 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
         h->phase_ms[2] = elapsed(h, 3, 4);
         h->phase_ms[3] = elapsed(h, 4, 5);
         h->phase_ms[4] = elapsed(h, 5, 6);
+        h->phase_ms[6] = (h->tc_timed & 1) ? elapsed_ev(h->tcev[0], h->tcev[1]) : 0.0;
+        h->phase_ms[7] = (h->tc_timed & 2) ? elapsed_ev(h->tcev[2], h->tcev[3]) : 0.0;
     }
     const double nrm = h->hpinned[1];
     if (e_out) *e_out = c + h->hpinned[0] / nrm;
@@ -1843,6 +1940,7 @@ sv_status sv_get_option(sv_handle h, sv_option opt, int64_t *value) {
         case SV_OPT_L2_FETCH: *value = h->l2_fetch; return SV_OK;
         case SV_OPT_REVERSE_INTERLEAVED: *value = h->rev_inter; return SV_OK;
         case SV_OPT_WAIT_POLLS: *value = h->wait_polls; return SV_OK;
+        case SV_OPT_SECTOR_SWEEP: *value = h->sweep_mode; return SV_OK;
         case SV_OPT_TEST_STALL: *value = h->test_stall; return SV_OK;
     }
     return fail(h, SV_ERR_ARG, "unknown option");
@@ -1898,6 +1996,10 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
         case SV_OPT_RDM_VARIANT:
             if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "rdm variant must be 0, 1 or 2");
             h->rdm_variant = (int)value;
+            return SV_OK;
+        case SV_OPT_SECTOR_SWEEP:
+            if (value != 0 && value != 1) return fail(h, SV_ERR_ARG, "sector sweep mode must be 0 or 1");
+            h->sweep_mode = (int)value;
             return SV_OK;
         case SV_OPT_WAIT_POLLS:
             if (value < 1 || value > (int64_t)1 << 30) return fail(h, SV_ERR_ARG, "wait polls must be in [1, 2^30]");

@@ -130,6 +130,8 @@ struct SameGemm {
     int lda = 0, ldb = 0;                      // row strides of Ma / X and Mb / Xt: D rounded up to 4, zero padded
     int *err = nullptr;                        // device flag set by k_same_tc / k_ab_tc when a wait runs out
     uint32_t spins = 1u << 22;                 // polls of each of their bounded waits
+    cudaEvent_t *ev = nullptr;                 // profiling (may be NULL): events around the same-spin
+                                               // products [0], [1] and the alpha-beta products [2], [3]
     int stall = 0;                             // test hook: bit 0 k_same_tc, bit 1 k_ab_tc issue nothing
     // variant 5: the alpha-beta part on the tensor cores (k_ab_tc) into planes H
     // [planes][Db][ncols][Da] (hplane floats apart), gathered by k_sigma_comb; Bp: the
@@ -268,7 +270,7 @@ struct sv_ctx {
     int expect_variant = 0;
     int64_t ab_chunk = 0;      // SV_OPT_AB_CHUNK: partner rows per chunk of k_sigma_ab (0 auto)
     // launch geometry (blocks per SM), set by sv_autotune or the options
-    int rot_bps = 8;           // dense k_rotate / k_adjoint
+    int rot_bps = 32;          // dense k_rotate / k_adjoint / k_adjoint_i
     int sect_bps = 8;          // sector k_rotate_l / k_adjoint_l
     int rdm_bps = 4;           // k_rdm_rows
     int rdm_variant = 0;
@@ -279,6 +281,12 @@ struct sv_ctx {
     int *kerr = nullptr;       // device flag of kernels with bounded waits (k_same_tc, k_ab_tc)
     int64_t wait_polls = 1 << 22;  // polls of each of their bounded waits (SV_OPT_WAIT_POLLS)
     int test_stall = 0;        // SV_OPT_TEST_STALL: bit 0 k_same_tc, bit 1 k_ab_tc issue no copy / MMA
+    // sector storage, whole-sweep launches (k_sweep_rotate_l / k_sweep_adjoint_li): a barrier
+    // counter (first 256 bytes) and the ops' (cos, sin) on the device, their host staging
+    void *sweep_buf = nullptr;
+    size_t sweep_bytes = 0;
+    std::vector<double> sweep_host;
+    int sweep_mode = 1;        // SV_OPT_SECTOR_SWEEP: 1 one launch per sweep where possible, 0 one per op
     int *hkerr = nullptr;      // its pinned host copy, checked after stream synchronisations
     // same-spin products (expectation variant 4): matrices for one table set and sector,
     // and the phased-psi / product planes
@@ -298,7 +306,9 @@ struct sv_ctx {
     // phase profiling (SV_OPT_PROFILE)
     bool profile = false;
     cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    double phase_ms[SV_PHASES] = {0, 0, 0, 0, 0, 0};
+    double phase_ms[SV_PHASES] = {0, 0, 0, 0, 0, 0, 0, 0};
+    cudaEvent_t tcev[4] = {nullptr, nullptr, nullptr, nullptr};  // around the tensor-core products
+    int tc_timed = 0;          // bit 0: same-spin products timed in this call, bit 1: alpha-beta
     // bookkeeping
     uint64_t launches = 0;
     std::string err;

@@ -36,8 +36,9 @@ SV_OPT_L2_FETCH = 12
 SV_OPT_REVERSE_INTERLEAVED = 14
 SV_OPT_WAIT_POLLS = 15
 SV_OPT_TEST_STALL = 16
-SV_PHASES = 6
-PHASE_NAMES = ("reference", "forward", "expectation", "reverse", "restore", "rdm1")
+SV_OPT_SECTOR_SWEEP = 17
+SV_PHASES = 8
+PHASE_NAMES = ("reference", "forward", "expectation", "reverse", "restore", "rdm1", "same_products", "ab_products")
 STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV_ERR_TIMEOUT", 5: "SV_ERR_STATE"}
 
 # every symbol include/sv.h declares

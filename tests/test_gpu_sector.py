@@ -466,3 +466,76 @@ def test_automatic_form_and_the_byte_cap():
     assert energy(0) == E5
     assert energy(0, cap=400 << 20) == E4
     assert abs(E4 - E5) <= TOL["c64"]["E"]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64", "r64", "r32"])
+def test_whole_sweep_launches_match_per_op_and_oracle(dtype):
+    """Sector storage: the forward and reverse sweeps as one cooperative launch each
+    (SV_OPT_SECTOR_SWEEP = 1, grid barriers between operators) and as one launch per
+    operator (0): energy, gradient and psi(theta) match the oracle in both modes and
+    agree with each other to rounding.  The operator list mixes singles, doubles and
+    operators with no pair in the sector (they annihilate more beta electrons than the
+    sector holds: skipped with no barrier, gradient exactly 0); the sector of 20 qubits
+    with 3 + 1 electrons has 120 x 10 strings."""
+    n, na, nb = 20, 3, 1
+    p = inputs.make_problem(n, 4, 80, seed=919)
+    extra = np.array([(2, 1, 3, 11, 13), (2, 1, 3, 15, 17), (2, 3, 5, 7, 9)], np.int32)   # two beta holes each
+    ops = np.vstack([p["ops"][:30], extra[:2], p["ops"][30:], extra[2:]])
+    theta = np.concatenate([p["theta"][:30], [0.3, -0.2], p["theta"][30:], [0.1]]) * 4
+    sec = oracle.Sector(n, na, nb)
+    if dtype.startswith("c"):
+        dense0 = inputs.random_sector_state(n, na, nb, np.random.default_rng(91))
+    else:
+        dense0 = np.zeros(1 << n)
+        dense0[(1 << 0) | (1 << 2) | (1 << 4) | (1 << 1)] = 1.0
+    psi0 = dense0[sec.dets.astype(np.int64)]
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], ops, theta, psi0)
+    psi_ref = A.apply_ansatz(sec, ops, theta, psi0)
+    tol = TOL["c128" if dtype in ("c128", "r64") else "c64"]
+    npdt = {"c128": np.complex128, "c64": np.complex64, "r64": np.float64, "r32": np.float32}[dtype]
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    out = {}
+    for mode in (1, 0):
+        st = _state(n, na, nb, dtype)
+        st.set_option(sv.SV_OPT_SECTOR_SWEEP, mode)
+        assert st.option(sv.SV_OPT_SECTOR_SWEEP) == mode
+        st.prepare_state(dense0.astype(npdt), na, nb)
+        E, g = st.energy_grad(ham, ops, theta)
+        assert abs(E - Eref) <= tol["E"], (mode, E, Eref)
+        assert np.max(np.abs(g - gref)) <= tol["g"], mode
+        assert g[30] == 0.0 and g[31] == 0.0 and g[-1] == 0.0
+        got = st.state()
+        assert np.max(np.abs(got[sec.dets.astype(np.int64)] - psi_ref)) <= tol["amp"]
+        st.prepare_state(dense0.astype(npdt), na, nb)          # the forward sweep alone (sv_apply_ansatz)
+        st.apply_ansatz(ops, theta)
+        assert np.max(np.abs(st.state()[sec.dets.astype(np.int64)] - psi_ref)) <= tol["amp"]
+        out[mode] = (E, g)
+        st.close()
+    assert abs(out[0][0] - out[1][0]) <= tol["E"]
+    assert np.max(np.abs(out[0][1] - out[1][1])) <= tol["g"]
+
+
+def test_whole_sweep_barrier_wait_runs_out_reports_and_recovers():
+    """With one poll per barrier wait the whole-sweep launch's grid barriers run out (no
+    block waits more than a poll; every block then stops): the call reports SV_ERR_CUDA
+    and the handle refuses work until a state is prepared again; with the default limit
+    the same handle matches the oracle."""
+    n, na, nb = 16, 2, 2
+    p = inputs.config_problem(2)
+    sec = oracle.Sector(n, na, nb)
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], p["theta"], A.hf_state(sec, p["occ"]))
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _state(n, na, nb, "c128")
+    st.set_option(sv.SV_OPT_WAIT_POLLS, 1)
+    st.prepare_hf(p["occ"])
+    with pytest.raises(sv.SvError) as e:
+        st.energy_grad(ham, p["ops"], p["theta"])
+    assert e.value.status == 3 and "bounded wait" in str(e.value)
+    with pytest.raises(sv.SvError) as e2:
+        st.energy(ham)
+    assert e2.value.status == 5
+    st.set_option(sv.SV_OPT_WAIT_POLLS, 1 << 22)
+    for _ in range(2):
+        st.prepare_hf(p["occ"])
+        E, g = st.energy_grad(ham, p["ops"], p["theta"])
+        assert abs(E - Eref) <= 1e-10 and np.max(np.abs(g - gref)) <= 1e-9
