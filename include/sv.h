@@ -411,7 +411,7 @@ typedef enum {
                                        with no copy or MMA in flight (the path of a stuck
                                        producer).  No fault and no hang: the call reports
                                        SV_ERR_CUDA */
-    SV_OPT_SECTOR_SWEEP = 17        /* sector storage: 1 (default) each forward and reverse
+    SV_OPT_SECTOR_SWEEP = 17,       /* sector storage: 1 (default) each forward and reverse
                                        sweep is one cooperative launch that walks the
                                        operators in order with a grid-wide barrier
                                        between them (every barrier wait bounded by
@@ -420,6 +420,10 @@ typedef enum {
                                        inside the sweep and the device accepts the
                                        cooperative launch, else one launch per operator
                                        (0 always) */
+    SV_OPT_SWEEP_BLOCKS_PER_SM = 18 /* launch geometry of the whole-sweep launches: at most
+                                       this many blocks per SM, no more than can be
+                                       resident (1..64, default 2; sv_autotune times
+                                       1, 2, 4, 8) */
 } sv_option;
 
 /* Options change launch choices or summation order only: results agree within the
@@ -432,8 +436,10 @@ sv_status sv_get_option(sv_handle h, sv_option opt, int64_t *value);
 /* Autotuner: time, on this handle's device with CUDA events, the candidate launch
  * choices for the given Hamiltonian and ansatz (ops/theta as for sv_energy_grad)
  * and keep the fastest -- the expectation's form and partner-row chunk size
- * (SV_OPT_EXPECT_VARIANT 2 or 3, SV_OPT_AB_CHUNK), the rotation and adjoint kernels'
- * blocks per SM (4, 8, 16, 32; dense or sector storage) and the 1-RDM's (2, 4, 8, 16).
+ * (SV_OPT_EXPECT_VARIANT 2 to 5, SV_OPT_AB_CHUNK), the rotation and adjoint kernels'
+ * blocks per SM (4, 8, 16, 32; dense storage, or sector storage with one launch per
+ * operator), the whole-sweep launches' (1, 2, 4, 8; sector storage,
+ * SV_OPT_SWEEP_BLOCKS_PER_SM) and the 1-RDM's (2, 4, 8, 16).
  * Needs a prepared state; the state itself is left unchanged (candidates run on
  * copies in the adjoint vector and the saved-state buffer, which sv_energy_grad
  * allocates anyway).  Takes tens of launches of each kernel: call it once per problem

@@ -744,7 +744,7 @@ static sv_status forward(sv_handle h, const std::vector<OpDesc> &ops, bool check
         SV_TRY(upload_sweep_angles(h, ops));
         // one launch for the whole sweep unless checkpoint copies are due in the middle
         if (!(checkpoints && C > 0 && (size_t)C < ops.size()) &&
-            sweep_once(h, false, h->psi, ops.size(), sweep_grid(h->dtype, false, h->Db, h->sm_count, h->sect_bps),
+            sweep_once(h, false, h->psi, ops.size(), sweep_grid(h->dtype, false, h->Db, h->sm_count, h->sweep_bps),
                        nullptr))
             return SV_OK;
     }
@@ -1153,11 +1153,18 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
         size_t k = 0;  // a representative op: the first double whose touched runs are long
         for (size_t j = 0; j < d.size(); ++j)
             if (d[j].nbits == 4 && d[j].pos[0] >= 4) { k = j; break; }
-        const int cands[] = {4, 8, 16, 32};
+        // sector storage with whole-sweep launches: the two sweeps themselves are timed, on
+        // copies (blocks per SM 1, 2, 4, 8); else one rotation and one adjoint step
+        const bool sweeps = h->storage == 1 && h->sweep_mode && h->ckpt_interval <= 0 && adj;
+        const int cands_op[] = {4, 8, 16, 32}, cands_sw[] = {1, 2, 4, 8};
         int best_b = 8;
         float best_t = -1.f;
         if (h->storage == 1) SV_TRY(ensure_op_lists(h, d, h->lists));
-        SV_TRY(ensure_partials(h, (size_t)h->sm_count * 32));
+        SV_TRY(ensure_partials(h, (size_t)h->sm_count * 32 * (sweeps ? d.size() : 1)));
+        if (sweeps) {
+            SV_TRY(ensure_kerr(h));
+            SV_TRY(upload_sweep_angles(h, d));
+        }
         // sector storage: the adjoint step as sv_energy_grad runs it (interleaved unless checkpoints resync psi)
         bool inter = h->storage == 1 && adj && h->ckpt_interval <= 0;
         if (inter && ensure_clbuf(h) != SV_OK) {
@@ -1168,9 +1175,19 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
             SV_CUDA(h, launch_interleave(h->lam, h->saved, h->dtype, h->CLbuf, (size_t)h->Da * h->Db, h->sm_count,
                                          h->stream));
         }
-        for (int b : cands) {
+        for (int ci = 0; ci < 4; ++ci) {
+            const int b = (sweeps && inter) ? cands_sw[ci] : cands_op[ci];
             float t;
-            if (h->storage == 1) {
+            if (sweeps && inter) {
+                const int Gf = sweep_grid(h->dtype, false, h->Db, h->sm_count, b),
+                          Gr = sweep_grid(h->dtype, true, h->Db, h->sm_count, b);
+                t = time_best(h, e0, e1, [&]() -> sv_status {
+                    if (!sweep_once(h, false, h->lam, d.size(), Gf, nullptr) ||
+                        !sweep_once(h, true, h->CLbuf, d.size(), Gr, h->partials))
+                        return fail(h, SV_ERR_CUDA, "autotune: whole-sweep launch refused");
+                    return SV_OK;
+                });
+            } else if (h->storage == 1) {
                 const uint32_t *L = (const uint32_t *)h->lists.buf;
                 const int *li = &h->lists.info[4 * k];
                 const int G = sector_grid(h->Db, h->sm_count, b);
@@ -1204,7 +1221,8 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
                 best_b = b;
             }
         }
-        if (h->storage == 1) h->sect_bps = best_b;
+        if (sweeps && inter) h->sweep_bps = best_b;
+        else if (h->storage == 1) h->sect_bps = best_b;
         else h->rot_bps = best_b;
     }
     // 3. 1-RDM launch geometry
@@ -1695,7 +1713,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     int Gred = G;
     bool swept = false;
     if (inter) {
-        const int Gs = sweep_grid(h->dtype, true, h->Db, h->sm_count, h->sect_bps);
+        const int Gs = sweep_grid(h->dtype, true, h->Db, h->sm_count, h->sweep_bps);
         if (Gs > 0 && Gs <= G && sweep_once(h, true, h->CLbuf, L, Gs, h->partials)) {
             swept = true;
             Gred = Gs;
@@ -1941,6 +1959,7 @@ sv_status sv_get_option(sv_handle h, sv_option opt, int64_t *value) {
         case SV_OPT_REVERSE_INTERLEAVED: *value = h->rev_inter; return SV_OK;
         case SV_OPT_WAIT_POLLS: *value = h->wait_polls; return SV_OK;
         case SV_OPT_SECTOR_SWEEP: *value = h->sweep_mode; return SV_OK;
+        case SV_OPT_SWEEP_BLOCKS_PER_SM: *value = h->sweep_bps; return SV_OK;
         case SV_OPT_TEST_STALL: *value = h->test_stall; return SV_OK;
     }
     return fail(h, SV_ERR_ARG, "unknown option");
@@ -1996,6 +2015,10 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
         case SV_OPT_RDM_VARIANT:
             if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "rdm variant must be 0, 1 or 2");
             h->rdm_variant = (int)value;
+            return SV_OK;
+        case SV_OPT_SWEEP_BLOCKS_PER_SM:
+            if (value < 1 || value > 64) return fail(h, SV_ERR_ARG, "blocks per SM must be in [1, 64]");
+            h->sweep_bps = (int)value;
             return SV_OK;
         case SV_OPT_SECTOR_SWEEP:
             if (value != 0 && value != 1) return fail(h, SV_ERR_ARG, "sector sweep mode must be 0 or 1");

@@ -287,6 +287,7 @@ struct sv_ctx {
     size_t sweep_bytes = 0;
     std::vector<double> sweep_host;
     int sweep_mode = 1;        // SV_OPT_SECTOR_SWEEP: 1 one launch per sweep where possible, 0 one per op
+    int sweep_bps = 2;         // SV_OPT_SWEEP_BLOCKS_PER_SM: blocks per SM of a whole-sweep launch
     int *hkerr = nullptr;      // its pinned host copy, checked after stream synchronisations
     // same-spin products (expectation variant 4): matrices for one table set and sector,
     // and the phased-psi / product planes

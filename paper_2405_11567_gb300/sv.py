@@ -37,6 +37,7 @@ SV_OPT_REVERSE_INTERLEAVED = 14
 SV_OPT_WAIT_POLLS = 15
 SV_OPT_TEST_STALL = 16
 SV_OPT_SECTOR_SWEEP = 17
+SV_OPT_SWEEP_BLOCKS_PER_SM = 18
 SV_PHASES = 8
 PHASE_NAMES = ("reference", "forward", "expectation", "reverse", "restore", "rdm1", "same_products", "ab_products")
 STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV_ERR_TIMEOUT", 5: "SV_ERR_STATE"}
@@ -520,7 +521,7 @@ class StateVector:
         return {name: self.option(opt) for name, opt in (
             ("expect_variant", SV_OPT_EXPECT_VARIANT), ("ab_chunk", SV_OPT_AB_CHUNK),
             ("rot_blocks_per_sm", SV_OPT_ROT_BLOCKS_PER_SM), ("sect_blocks_per_sm", SV_OPT_SECT_BLOCKS_PER_SM),
-            ("rdm_blocks_per_sm", SV_OPT_RDM_BLOCKS_PER_SM))}
+            ("rdm_blocks_per_sm", SV_OPT_RDM_BLOCKS_PER_SM), ("sweep_blocks_per_sm", SV_OPT_SWEEP_BLOCKS_PER_SM))}
 
     def set_layout(self, storage_of_qubit):
         sv_set_layout(self.handle, storage_of_qubit)

@@ -41,6 +41,7 @@ def test_autotune_keeps_results(storage, dtype):
         assert choice["ab_chunk"] in ((2, 4, 6, 8) if dtype == "c64" else (1, 2, 3, 4))
     assert choice["rot_blocks_per_sm"] in (4, 8, 16, 32) and choice["sect_blocks_per_sm"] in (4, 8, 16, 32)
     assert choice["rdm_blocks_per_sm"] in (2, 4, 8, 16)
+    assert choice["sweep_blocks_per_sm"] in (1, 2, 4, 8)
     st.prepare_hf(p["occ"])
     E, g = st.energy_grad(ham, p["ops"], theta)
     tE, tg = TOL[dtype]
