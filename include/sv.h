@@ -328,8 +328,11 @@ typedef enum {
                                        space of at most 4096 strings, where variant 5's
                                        limits hold and its planes take at most 16 GiB
                                        within the byte cap, else 4 for those states;
-                                       else 3 where its rows fit in shared memory; else
-                                       2); 1 record scan:
+                                       = 6 for complex128 / real float64 states where
+                                       the split form's rows fit in shared memory (3
+                                       when its two work matrices do not fit the byte
+                                       cap); else 3 where its rows fit in shared
+                                       memory; else 2); 1 record scan:
                                        one thread per sector determinant tests every mask
                                        group (dense storage only); 2 string rows: compact
                                        alpha/beta-string matrix, one block per beta
@@ -351,7 +354,16 @@ typedef enum {
                                        per (alpha tile, partner beta string), into
                                        planes of planes x Db x (nb (N - nb) + 1) x Da
                                        floats (3.7 GB at 30 qubits, complex64) gathered
-                                       in a fixed order */
+                                       in a fixed order; 6 (float64 states; single
+                                       precision takes 3): the split form of 3 with every
+                                       product and sum of an amplitude's connections in
+                                       float-float arithmetic (a float64 value as the
+                                       unevaluated sum of two float32 words, 48-bit
+                                       significand; error-free transformations) on the
+                                       FP32 pipe instead of GB300's much narrower FP64
+                                       pipe; the amplitudes are converted once per call
+                                       and sigma written back as float64 (two work
+                                       matrices of 16 Da Db bytes, complex) */
     SV_OPT_RDM_VARIANT = 4,         /* 0 auto (= 2); 1 sector gather: one thread per sector
                                        determinant (dense storage only); 2 string rows: one
                                        block per beta string of the compact matrix */

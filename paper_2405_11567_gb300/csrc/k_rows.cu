@@ -37,6 +37,7 @@
 // k_abtc.cu for the alpha-beta part.
 #include <cuda_bf16.h>
 
+#include "sv_ff.cuh"
 #include "sv_internal.h"
 #include "sv_sigma.cuh"
 
@@ -249,6 +250,10 @@ __device__ __forceinline__ float flip_sign<float>(float v, uint32_t bit) {
 template <>
 __device__ __forceinline__ double flip_sign<double>(double v, uint32_t bit) {
     return __longlong_as_double(__double_as_longlong(v) ^ (long long)((unsigned long long)bit << 63));
+}
+template <>
+__device__ __forceinline__ ff flip_sign<ff>(ff v, uint32_t bit) {
+    return ff_flip(v, bit);
 }
 
 __device__ __forceinline__ int pair_index(int p, int q, int N) { return p * N - p * (p + 1) / 2 + (q - p - 1); }
@@ -476,6 +481,33 @@ template <int K>
 __device__ __forceinline__ void lds_c(const double2 *p, double2 (&c)[K]) {
     #pragma unroll
     for (int j = 0; j < K; ++j) c[j] = p[j];
+}
+// float-float amplitudes (16 bytes complex, 8 bytes real) and integrals (8 bytes)
+template <int K>
+__device__ __forceinline__ void lds_c(const ffc *p, ffc (&c)[K]) {
+    #pragma unroll
+    for (int j = 0; j < K; ++j) c[j] = p[j];
+}
+template <int K>
+__device__ __forceinline__ void lds_c(const ff *p, ff (&c)[K]) {
+    static_assert(K % 2 == 0, "real float-float chunks hold an even number of rows");
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    #pragma unroll
+    for (int j = 0; j < K / 2; ++j) {
+        const float4 v = q[j];
+        c[2 * j] = ff(v.x, v.y);
+        c[2 * j + 1] = ff(v.z, v.w);
+    }
+}
+template <int KP>
+__device__ __forceinline__ void lds_r(const ff *p, ff (&v)[KP]) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    #pragma unroll
+    for (int j = 0; j < KP / 2; ++j) {
+        const float4 t = q[j];
+        v[2 * j] = ff(t.x, t.y);
+        v[2 * j + 1] = ff(t.z, t.w);
+    }
 }
 template <int KP>
 __device__ __forceinline__ void lds_r(const float *p, float (&v)[KP]) {
@@ -1046,6 +1078,12 @@ static cudaError_t launch_ab_k(const RowArgs<float> &A, int K, size_t smem, cuda
 static cudaError_t launch_ab_k(const RowArgs<double> &A, int K, size_t smem, cudaStream_t st) {
     return launch_ab_k4<double, 2, 4, 6, 8>(A, K, smem, st);
 }
+static cudaError_t launch_ab_k(const RowArgs<ffc> &A, int K, size_t smem, cudaStream_t st) {
+    return launch_ab_k4<ffc, 1, 2, 3, 4>(A, K, smem, st);
+}
+static cudaError_t launch_ab_k(const RowArgs<ff> &A, int K, size_t smem, cudaStream_t st) {
+    return launch_ab_k4<ff, 2, 4, 6, 8>(A, K, smem, st);
+}
 
 cudaError_t launch_same_tc(const uint16_t *M, size_t pm, const uint16_t *X, size_t px, uint16_t *Xt, size_t pt,
                            float *G, int planes, int Da, int Db, int lda, int ldb, int *err, uint32_t spins, int stall,
@@ -1109,6 +1147,94 @@ static cudaError_t launch_rows_t(const RowArgs<Amp> &A, const RowTables &T, int 
         k_sigma_same<Amp, false><<<T.Db, kSameThreads, smem, st>>>(A);
     }
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- float-float form
+
+// Expectation variant 6 (float64 states): the split form's two kernels instantiated on
+// float-float amplitudes and integrals (sv_ff.cuh), so every product and sum of an
+// amplitude's connections runs on the FP32 pipe at about 48-bit precision.  The compact
+// amplitudes are converted once per call (k_to_ff), the kernels sum sigma into a
+// float-float compact matrix, and k_from_ff writes it back as float64 (to the dense
+// vector at the storage addresses, or to the compact output); the energies and norms
+// are float64 sums as in the other forms.
+template <typename A, typename F>
+__global__ void __launch_bounds__(kThreads) k_to_ff(const A *__restrict__ in, F *__restrict__ out, size_t count) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        if constexpr (AmpT<A>::kCplx) {
+            const A v = in[i];
+            ffc c;
+            c.x = ff_from(v.x);
+            c.y = ff_from(v.y);
+            out[i] = c;
+        } else {
+            out[i] = ff_from(in[i]);
+        }
+    }
+}
+
+template <typename F, typename A>
+__global__ void __launch_bounds__(kThreads) k_from_ff(const F *__restrict__ in, A *__restrict__ lam,
+                                                      A *__restrict__ lamc, const uint32_t *__restrict__ sa_s,
+                                                      const uint32_t *__restrict__ sb_s, int Da, int Db) {
+    for (int Ib = blockIdx.x; Ib < Db; Ib += gridDim.x) {
+        const F *row = in + (size_t)Ib * Da;
+        for (int Ia = threadIdx.x; Ia < Da; Ia += blockDim.x) {
+            A v;
+            if constexpr (AmpT<A>::kCplx) v = mka<A>(ff_to(row[Ia].x), ff_to(row[Ia].y));
+            else v = ff_to(row[Ia]);
+            if (lam) lam[sa_s[Ia] | sb_s[Ib]] = v;
+            if (lamc) lamc[(size_t)Ib * Da + Ia] = v;
+        }
+    }
+}
+
+template <typename A, typename F>
+static cudaError_t launch_ff_t(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &Tf,
+                               const double *hdiag, const double *Jp, double e_shift, double *partial, int K,
+                               void *Cf, void *Lf, int sm_count, cudaStream_t st) {
+    const size_t count = (size_t)Tf.Da * Tf.Db;
+    int grid = (int)std::min<size_t>((count + kThreads - 1) / kThreads, (size_t)sm_count * 8);
+    if (grid < 1) grid = 1;
+    k_to_ff<A, F><<<grid, kThreads, 0, st>>>((const A *)C, (F *)Cf, count);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    RowArgs<F> RA = row_args<F>(Cf, nullptr, Lf, n, Tf, hdiag, Jp, e_shift, partial);
+    e = launch_ab_k(RA, K, ab_smem(dtype, K, Tf), st);
+    if (e != cudaSuccess) return e;
+    if (same_smem(dtype, Tf, true) <= kSameSmemCap) {
+        const size_t smem = same_smem(dtype, Tf, true);
+        e = cudaFuncSetAttribute(k_sigma_same<F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sigma_same<F, true><<<Tf.Db, kSameThreads, smem, st>>>(RA);
+    } else {
+        const size_t smem = same_smem(dtype, Tf, false);
+        e = cudaFuncSetAttribute(k_sigma_same<F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sigma_same<F, false><<<Tf.Db, kSameThreads, smem, st>>>(RA);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int g2 = Tf.Db < sm_count * 8 ? Tf.Db : sm_count * 8;
+    k_from_ff<F, A><<<g2, kThreads, 0, st>>>((const F *)Lf, (A *)lam, (A *)lamc, Tf.sa_s, Tf.sb_s, Tf.Da, Tf.Db);
+    return cudaGetLastError();
+}
+
+// The float-float split form for a float64 state (complex128 or real float64): Tf holds
+// the float-float integral tables (eri, hm, Dt, Jt, W2); Cf and Lf are two compact
+// float-float work matrices (Da Db x 16 or 8 bytes each); K as for the split form.
+// Launches k_to_ff, k_sigma_ab, k_sigma_same, k_from_ff.
+cudaError_t launch_sigma_rows_ff(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &Tf,
+                                 const double *hdiag, const double *Jp, double e_shift, double *partial, int K,
+                                 void *Cf, void *Lf, int sm_count, cudaStream_t st) {
+    if (K <= 0) return cudaErrorInvalidValue;
+    if (dtype == SV_C128)
+        return launch_ff_t<double2, ffc>(C, lam, lamc, dtype, n, Tf, hdiag, Jp, e_shift, partial, K, Cf, Lf, sm_count,
+                                         st);
+    if (dtype == SV_R64)
+        return launch_ff_t<double, ff>(C, lam, lamc, dtype, n, Tf, hdiag, Jp, e_shift, partial, K, Cf, Lf, sm_count,
+                                       st);
+    return cudaErrorInvalidValue;
 }
 
 // K: rows per chunk of the split form (sigma_ab_chunk), 0 for the single-kernel form.

@@ -81,6 +81,9 @@ struct RowTables {
     int N, Da, Db;
     const void *W2 = nullptr;  // pair-indexed same-spin integrals (split form)
 };
+cudaError_t launch_sigma_rows_ff(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &Tf,
+                                 const double *hdiag, const double *Jp, double e_shift, double *partial, int K,
+                                 void *Cf, void *Lf, int sm_count, cudaStream_t st);
 cudaError_t launch_compact(const void *psi, void *C, int dtype, const uint32_t *sa, const uint32_t *sb, int Da,
                            int Db, int sm_count, cudaStream_t st);
 cudaError_t launch_sigma_rows(const void *C, void *lam, void *lamc, int dtype, int n, const RowTables &T, const double *hdiag,
@@ -98,7 +101,8 @@ int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want);
 const int *sigma_ab_sizes(int dtype);
 
 DevTables::~DevTables() {
-    void *ptrs[] = {dbl, sgl, W, hdiag, Jp, hdiag_s, Jp_s, eri_r, hm_r, Dt, Jt, W2, pass_dbl, pass_sgl, pass_W};
+    void *ptrs[] = {dbl,    sgl,   W,     hdiag, Jp,       hdiag_s,  Jp_s,  eri_r, hm_r, Dt,
+                    Jt,     W2,    eri_ff, hm_ff, Dt_ff, Jt_ff, W2_ff, pass_dbl, pass_sgl, pass_W};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -494,6 +498,25 @@ static sv_status upload_tables(sv_handle h, sv_ham_handle ham, DevTables &T) {
                     W2[(size_t)pidx(p1, p2) * NP + pidx(q1, q2)] = (R)(s0 ? -v : v);
                 }
     SV_TRY(up(&T.W2, W2.data(), W2.size() * sizeof(R)));
+    if (sizeof(R) == 8) {
+        // float-float copies (hi = nearest float, lo = nearest float of the rest) for variant 6
+        auto split = [](const std::vector<R> &v) {
+            std::vector<float> o(2 * v.size());
+            for (size_t i = 0; i < v.size(); ++i) {
+                const double x = (double)v[i];
+                const float hi = (float)x;
+                o[2 * i] = hi;
+                o[2 * i + 1] = (float)(x - (double)hi);
+            }
+            return o;
+        };
+        const std::vector<float> e2 = split(eri), h2 = split(hm), d2 = split(Dt), j2 = split(Jt), w2 = split(W2);
+        SV_TRY(up(&T.eri_ff, e2.data(), e2.size() * sizeof(float)));
+        SV_TRY(up(&T.hm_ff, h2.data(), h2.size() * sizeof(float)));
+        SV_TRY(up(&T.Dt_ff, d2.data(), d2.size() * sizeof(float)));
+        SV_TRY(up(&T.Jt_ff, j2.data(), j2.size() * sizeof(float)));
+        SV_TRY(up(&T.W2_ff, w2.data(), w2.size() * sizeof(float)));
+    }
     return SV_OK;
 }
 
@@ -961,9 +984,42 @@ static sv_status check_kernel_flag(sv_handle h) {
 
 // The string-row expectation (sigma into lam at storage addresses, or into lamc in
 // compact form), with or without the same-spin products; counts the launches.
+// Whether the expectation takes the float-float split form (variant 6): float64 states
+// whose split form fits; the automatic choice (variant 0) for them.
+static bool use_ff(sv_handle h, int K) {
+    if (single_prec(h->dtype) || K == 0) return false;
+    return h->expect_variant == 6 || h->expect_variant == 0;
+}
+
 static sv_status sigma_rows(sv_handle h, DevTables *T, const RowTables &R, const void *C, void *lam, void *lamc,
                             double e_shift) {
     const int K = row_chunk(h, R);
+    if (use_ff(h, K) && T->eri_ff) {
+        const size_t one = (size_t)h->Da * h->Db * (is_complex(h->dtype) ? 16 : 8), r = (one + 255) / 256 * 256;
+        bool ok = true;
+        if (h->ffbuf_bytes < 2 * r) {
+            dev_free(h, h->ffbuf, h->ffbuf_bytes);
+            h->ffbuf = nullptr;
+            h->ffbuf_bytes = 0;
+            const sv_status st = dev_alloc(h, &h->ffbuf, 2 * r, "float-float sigma work matrices");
+            if (st != SV_OK && h->expect_variant == 6) return st;
+            ok = st == SV_OK;  // the automatic choice falls back to the float64 split form
+            if (ok) h->ffbuf_bytes = 2 * r;
+            else cudaGetLastError();
+        }
+        if (ok) {
+        RowTables Tf = R;
+        Tf.eri = T->eri_ff;
+        Tf.hm = T->hm_ff;
+        Tf.Dt = T->Dt_ff;
+        Tf.Jt = T->Jt_ff;
+        Tf.W2 = T->W2_ff;
+        SV_CUDA(h, launch_sigma_rows_ff(C, lam, lamc, h->dtype, h->n, Tf, T->hdiag, T->Jp, e_shift, h->partials, K,
+                                        h->ffbuf, (uint8_t *)h->ffbuf + r, h->sm_count, h->stream));
+        h->launches += 4;
+        return SV_OK;
+        }
+    }
     SameGemm g;
     const bool sg = use_same_gemm(h, K);
     if (sg) SV_TRY(ensure_same_gemm(h, T, R, &g));
@@ -1120,13 +1176,14 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
         int best_v = 2;
         int64_t best_k = 0;
         float best_t = -1.f;
-        // split form; same-spin products and the tensor-core alpha-beta form (single precision)
-        const int nv = single_prec(h->dtype) ? 2 : 1;
-        for (int i = -1; i < 4 * nv + (nv > 1 ? 1 : 0); ++i) {
-            h->expect_variant = i < 0 ? 2 : (i < 4 ? 3 : (i < 8 ? 4 : 5));
+        // split form; same-spin products and the tensor-core alpha-beta form (single
+        // precision); the float-float split form (float64)
+        const bool sp = single_prec(h->dtype);
+        for (int i = -1; i < (sp ? 9 : 8); ++i) {
+            h->expect_variant = i < 0 ? 2 : (i < 4 ? 3 : (!sp ? 6 : (i < 8 ? 4 : 5)));
             h->ab_chunk = i < 0 ? 0 : (i < 8 ? sizes[i & 3] : 0);
             if (i >= 0 && i < 8 && row_chunk(h, R) != sizes[i & 3]) continue;  // that size does not fit
-            if (i >= 4 && !use_same_gemm(h, row_chunk(h, R))) continue;
+            if (sp && i >= 4 && !use_same_gemm(h, row_chunk(h, R))) continue;
             if (i == 8 && !use_ab_tc(h)) continue;
             const float t = time_best(h, e0, e1, [&] { return expectation(h, ham, T, h->lam, c, 0); });
             if (t < 0.f) return fail(h, SV_ERR_CUDA, "autotune: expectation candidate failed");
@@ -1372,6 +1429,7 @@ sv_status sv_destroy(sv_handle h) {
     dev_free(h, h->rdm_lists.buf, h->rdm_lists.bytes);
     dev_free(h, h->CLbuf, h->CLbuf_bytes);
     dev_free(h, h->sweep_buf, h->sweep_bytes);
+    dev_free(h, h->ffbuf, h->ffbuf_bytes);
     dev_free(h, h->partials, h->partials_cap * sizeof(double));
     dev_free(h, h->dout, h->dout_cap * sizeof(double));
     if (h->hpinned) cudaFreeHost(h->hpinned);
@@ -2009,7 +2067,7 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
             h->max_bytes = value;
             return SV_OK;
         case SV_OPT_EXPECT_VARIANT:
-            if (value < 0 || value > 5) return fail(h, SV_ERR_ARG, "expect variant must be 0 to 5");
+            if (value < 0 || value > 6) return fail(h, SV_ERR_ARG, "expect variant must be 0 to 6");
             h->expect_variant = (int)value;
             return SV_OK;
         case SV_OPT_RDM_VARIANT:

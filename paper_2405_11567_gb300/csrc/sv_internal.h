@@ -164,6 +164,8 @@ struct DevTables {
     void *Dt = nullptr;     // [N^3] (qp|kk) - (qk|kp)
     void *Jt = nullptr;     // [N^3] (qp|kk)
     void *W2 = nullptr;     // [NP][NP] same-spin doubles by (q1<q2, p1<p2) pairs
+    // the same five tables as float-float pairs (float64 tables only; expectation variant 6)
+    void *eri_ff = nullptr, *hm_ff = nullptr, *Dt_ff = nullptr, *Jt_ff = nullptr, *W2_ff = nullptr;
     // tiled-pass schedule (k_expect.cu); empty until first needed
     struct Pass {
         uint32_t S;        // local qubit set (bit mask over storage positions)
@@ -288,6 +290,9 @@ struct sv_ctx {
     std::vector<double> sweep_host;
     int sweep_mode = 1;        // SV_OPT_SECTOR_SWEEP: 1 one launch per sweep where possible, 0 one per op
     int sweep_bps = 2;         // SV_OPT_SWEEP_BLOCKS_PER_SM: blocks per SM of a whole-sweep launch
+    // expectation variant 6: the compact amplitudes and sigma as float-float matrices
+    void *ffbuf = nullptr;
+    size_t ffbuf_bytes = 0;
     int *hkerr = nullptr;      // its pinned host copy, checked after stream synchronisations
     // same-spin products (expectation variant 4): matrices for one table set and sector,
     // and the phased-psi / product planes

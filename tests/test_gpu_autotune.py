@@ -36,8 +36,8 @@ def test_autotune_keeps_results(storage, dtype):
     before = st.state()
     choice = st.autotune(ham, p["ops"], theta)
     assert np.array_equal(st.state(), before)                 # the tuner leaves psi alone
-    assert choice["expect_variant"] in ((2, 3, 4, 5) if dtype == "c64" else (2, 3))
-    if choice["expect_variant"] in (3, 4):
+    assert choice["expect_variant"] in ((2, 3, 4, 5) if dtype == "c64" else (2, 3, 6))
+    if choice["expect_variant"] in (3, 4, 6):
         assert choice["ab_chunk"] in ((2, 4, 6, 8) if dtype == "c64" else (1, 2, 3, 4))
     assert choice["rot_blocks_per_sm"] in (4, 8, 16, 32) and choice["sect_blocks_per_sm"] in (4, 8, 16, 32)
     assert choice["rdm_blocks_per_sm"] in (2, 4, 8, 16)

@@ -323,12 +323,13 @@ def test_errors_are_reported_not_raised_on_device():
     assert np.isfinite(st.energy(ham))
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_expectation_variants_match_oracle(variant, dtype):
     """Record scan (1), string rows in one kernel (2), split (3), split with same-spin
     products (4) and with the alpha-beta part as tensor-core products too (5; complex128
-    keeps 3) on an open-shell complex state and on config 2."""
+    keeps 3), split in float-float arithmetic (6; complex64 keeps 3) on an open-shell
+    complex state and on config 2."""
     n, na, nb = 12, 3, 2
     p = inputs.make_problem(n, 4, 30, seed=88)
     rng = np.random.default_rng(11)
@@ -358,8 +359,9 @@ def test_expectation_variants_match_oracle(variant, dtype):
 
 def test_sigma_vector_matches_oracle():
     """At theta = 0 every gradient entry is 2 Re <(H - c) psi0| G_k psi0>, a projection of sigma
-    onto G_k psi0: a random complex start and many directions G_k probe sigma from both
-    expectation variants in complex128 to 1e-11."""
+    onto G_k psi0: a random complex start and many directions G_k probe sigma from the
+    record scan, the string rows, their split form in float64 and in float-float
+    arithmetic (variants 1, 2, 3, 6) in complex128 to 1e-11."""
     n = 12
     p = inputs.make_problem(n, 4, "uccsd", seed=91)
     sec = _oracle_problem(p)
@@ -370,12 +372,12 @@ def test_sigma_vector_matches_oracle():
     ops = p["ops"][::9]
     zeros = np.zeros(len(ops))
     _, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], ops, zeros, psi0)
-    for variant in (1, 2):
+    for variant in (1, 2, 3, 6):
         st = _gpu_state(n, "c128")
         st.set_option(sv.SV_OPT_EXPECT_VARIANT, variant)
         st.prepare_state(dense0, 2, 2)
         _, g = st.energy_grad(ham, ops, zeros)
-        assert np.max(np.abs(g - gref)) <= 1e-11
+        assert np.max(np.abs(g - gref)) <= 1e-11, variant
 
 
 # ---------------------------------------------------------------- storage layout
@@ -511,3 +513,30 @@ def test_reverse_sweep_interleaved_and_separate(dtype, layout):
         st.close()
     assert abs(out[0][0] - out[1][0]) <= tol["E"]
     assert np.max(np.abs(out[0][1] - out[1][1])) <= tol["g"]
+
+
+def test_float_float_sigma_matches_float64_and_oracle():
+    """Expectation variant 6 (float64 states: the split form's sums in float-float
+    arithmetic on the FP32 pipe) against variant 3 (the same form in float64) and the
+    oracle: energy and gradient on an open-shell complex start, in both storages, with
+    the two forms within 1e-11 / 1e-10 of each other."""
+    n, na, nb = 14, 4, 3
+    p = inputs.make_problem(n, 7, 40, seed=616)
+    dense0 = inputs.random_sector_state(n, na, nb, np.random.default_rng(61))
+    sec = oracle.Sector(n, na, nb)
+    psi0 = dense0[sec.dets.astype(np.int64)]
+    theta = p["theta"] * 6
+    Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    for sector in (None, (na, nb)):
+        res = {}
+        for v in (3, 6):
+            st = sv.StateVector(n, "c128", sector=sector)
+            st.set_option(sv.SV_OPT_EXPECT_VARIANT, v)
+            st.prepare_state(dense0, na, nb)
+            res[v] = st.energy_grad(ham, p["ops"], theta)
+            assert abs(res[v][0] - Eref) <= 1e-10, (sector, v)
+            assert np.max(np.abs(res[v][1] - gref)) <= 1e-9, (sector, v)
+            st.close()
+        assert abs(res[3][0] - res[6][0]) <= 1e-11
+        assert np.max(np.abs(res[3][1] - res[6][1])) <= 1e-10

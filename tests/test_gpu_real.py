@@ -24,7 +24,7 @@ def _state(n, na, nb, dtype, storage):
     return sv.StateVector(n, dtype, sector=None if storage == "dense" else (na, nb))
 
 
-@pytest.mark.parametrize("variant", [0, 4, 5])
+@pytest.mark.parametrize("variant", [0, 4, 5, 6])
 @pytest.mark.parametrize("storage", ["dense", "sector"])
 @pytest.mark.parametrize("dtype", ["r64", "r32"])
 def test_energy_grad_rdm_state(dtype, storage, variant):
