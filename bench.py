@@ -476,8 +476,8 @@ def run_ours(args, rank, world, local_rank):
         if rank == 0:
             print(json.dumps({"profile": "batch-only (not the bench line)", "batch_config4": rb}), flush=True)
         return 0
-    if args.sector_only:  # profiling runs: only the sector-storage complex64 step, a few GB on the device
-        so = timed("c64", sector=True)
+    if args.sector_only:  # profiling runs: only the sector-storage step, a few GB on the device
+        so = timed(args.sector_dtype, sector=True)
         if rank == 0:
             print(json.dumps({"profile": "sector-only (not the bench line)", "ms_per_step": so["ms"] / args.steps,
                               "phases_ms": so["phases"], "tuned": so["tuned"]}), flush=True)
@@ -547,13 +547,15 @@ def run_ours(args, rank, world, local_rank):
         fp64 = fp64_peak(torch)
         line["fp64_state"] = {"value": v128, "ms_per_step": head128["ms"] / K, "phases_ms": head128["phases"],
                               "clocks": head128["clocks"],
-                              "bound": fp64_rooflines(p, head128["phases"], fp64, peak),
+                              "bound": fp64_rooflines(p, head128["phases"], fp64, peak, head128["variant"]),
+                              "expectation_form": head128["variant"],
                               "vs_oracle": vs_golden(head128["out"], golden) if golden is not None else None}
         line["speedup_fp32_over_fp64"] = value / v128
         line["speedup_bounds"] = {
             "complex64": "HBM: the sweeps move their bytes at %.2f (reverse) / %.2f (forward) of the copy peak"
                          % (rows["adjoint_step"]["frac"], rows["rotation"]["frac"]),
-            "complex128": "FP64 pipe: see fp64_state.bound (FP64 flops / time against the FP64 peak); the "
+            "complex128": "the sweeps on the FP64 pipe (fp64_state.bound: FP64 flops / time against the "
+                          "measured FP64 rate), the expectation in float-float arithmetic on the FP32 pipe; the "
                           "byte ratio alone would give 2x"}
         line["fp32_vs_fp64"] = {
             "abs_dE": abs(head["out"]["E"] - head128["out"]["E"]),
@@ -628,11 +630,12 @@ def fp64_peak(torch):
     return 2.0 * 4096 ** 3 / (best / 1e3) / 1e12
 
 
-def fp64_rooflines(p, phases, fp64_tflops, hbm_peak):
-    """complex128 sweeps and expectation against the FP64 pipe (and the sweeps against HBM): FP64 flops
-    per amplitude pair = 12 in the rotation (three shears of the real and imaginary parts, six FMAs) and
-    32 in the adjoint step (two rotations plus four FMAs of the gradient term); the expectation 4 flops per
-    Hamiltonian connection (complex amplitude x real element, two FMAs)."""
+def fp64_rooflines(p, phases, fp64_tflops, hbm_peak, variant=None):
+    """complex128 sweeps against the FP64 pipe and HBM: FP64 flops per amplitude pair = 12 in the rotation
+    (three shears of the real and imaginary parts, six FMAs) and 32 in the adjoint step (two rotations plus
+    four FMAs of the gradient term).  The expectation: 4 flops of float64 work per Hamiltonian connection
+    (complex amplitude x real element, two FMAs) -- on the FP64 pipe (form 3), or in float-float arithmetic
+    on the FP32 pipe (form 6, about 12 FP32 operations per float64 multiply-add)."""
     n, L = p["n_qubits"], len(p["ops"])
     kind = np.asarray(p["ops"])[:, 0]
     pairs = np.where((kind == 1) | (kind == 3), 2.0 ** (n - 2), 2.0 ** (n - 4)).sum()
@@ -651,9 +654,25 @@ def fp64_rooflines(p, phases, fp64_tflops, hbm_peak):
                      "pairs_per_sweep": pairs, "mean_launch_ms": phases[phase] / L}
     t = phases["expectation"] / 1000.0
     tf = 4.0 * D * per / t / 1e12
-    out["expectation"] = {"bound": "fp64", "achieved_tflops": tf, "frac_fp64": tf / fp64_tflops,
-                          "algorithmic": "%d determinants x %d connections x 4 flops" % (D, per)}
+    if variant == 6:
+        ops = 2.0 * D * per * 12.0  # float-float multiply-adds, ~12 FP32 operations each
+        fp32 = fp32_ops_peak()
+        out["expectation"] = {
+            "form": "float-float split (variant 6): float64 values as two float32 words, FP32 pipe",
+            "bound": "shared memory (staged partner rows, 16 bytes per complex amplitude)",
+            "fp64_work_tflops": tf, "fp64_work_frac_of_fp64_peak": tf / fp64_tflops,
+            "fp32_ops_per_s": ops / t / 1e12, "fp32_ops_frac": ops / t / 1e12 / fp32,
+            "algorithmic": "%d determinants x %d connections x 4 flops of float64 work" % (D, per)}
+    else:
+        out["expectation"] = {"form": "float64 split (variant %s)" % variant, "bound": "fp64",
+                              "achieved_tflops": tf, "frac_fp64": tf / fp64_tflops,
+                              "algorithmic": "%d determinants x %d connections x 4 flops" % (D, per)}
     return out
+
+
+def fp32_ops_peak(sm_mhz=2070.0):
+    """FP32 pipe issue rate in tera-operations per second (an FMA counts once): 152 SMs x 128 lanes x clock."""
+    return 152 * 128 * sm_mhz * 1e6 / 1e12
 
 
 def mma_flops(p, planes=2):
@@ -1001,6 +1020,8 @@ def main():
                     help="profiling only: time just the batched launch (prints no bench line)")
     ap.add_argument("--sector-only", action="store_true",
                     help="profiling only: time just the sector-storage complex64 step (prints no bench line)")
+    ap.add_argument("--sector-dtype", choices=["c64", "c128"], default="c64",
+                    help="state type of --sector-only (profiling)")
     ap.add_argument("--op-profile", action="store_true",
                     help="per-operator rotation bandwidth by lowest address bit (diagnostic, not the bench line)")
     ap.add_argument("--no-per-config", action="store_true",

@@ -432,6 +432,17 @@ __global__ void __launch_bounds__(kSameThreads, 1) k_sigma_same(RowArgs<Amp> A) 
 constexpr int kAbThreads = 512;
 constexpr int kAbIpt = 8;  // alpha strings per thread: Da <= 4096
 
+// Row stride (in amplitudes) of the staged partner rows part[a][k]: K amplitudes rounded
+// up so that a row is an odd number of 16-byte words.  The inner loop reads whole rows of
+// random partner strings; with an even number of words every row would start in the same
+// half of the eight 16-byte bank groups (a 64-byte row: two of them), an odd stride spreads
+// the starts over all eight.
+__host__ __device__ constexpr int ab_row_stride(int K, int amp_bytes) {
+    const int per = 16 / amp_bytes;  // amplitudes per 16-byte word (1, 2 or 4)
+    const int words = (K + per - 1) / per;
+    return ((words & 1) ? words : words + 1) * per;
+}
+
 // Integral slots per (q, p) in the staged table: K rounded up to a 16-byte multiple.
 template <typename R, int K>
 struct AbLayout {
@@ -537,7 +548,8 @@ __device__ __forceinline__ void lds_r(const double *p, double (&v)[KP]) {
 // the row's share of <psi|sigma> goes to partial[2 Db + Ib].
 //
 // Partner rows are staged K at a time in shared memory, interleaved by column
-// (part[a][k]), so one vector load brings a column's K partner amplitudes; the
+// (part[a][k], rows padded to an odd number of 16-byte words), so one vector load brings a
+// column's K partner amplitudes; the
 // integrals are staged as eriS[q N + p][k].  Signs (x = spread(a) | spread(b)):
 //   beta single r -> s on x:  popc(x & between(2r+1, 2s+1)) -- per (a, k): applied
 //                             once to row k's sum for this a;
@@ -558,8 +570,9 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
     __shared__ double red[kAbThreads / 32];
     const SigmaTables<R> &T = A.T;
     const int Ib = blockIdx.x, N = T.N, Da = T.Da, NN = N * N;
-    Amp *part = reinterpret_cast<Amp *>(ab_dyn);                  // [Da][K]
-    R *eriS = reinterpret_cast<R *>(part + (size_t)K * Da);       // [N*N][KPS]
+    constexpr int PS = ab_row_stride(K, (int)sizeof(Amp));
+    Amp *part = reinterpret_cast<Amp *>(ab_dyn);                  // [Da][PS]
+    R *eriS = reinterpret_cast<R *>(part + (size_t)PS * Da);      // [N*N][KPS]
     R *JtS = eriS + (size_t)NN * KPS;                             // [K][N]: (s_k r_k|kk)
     uint16_t *raS = reinterpret_cast<uint16_t *>(JtS + (size_t)K * N);  // [2^N]
     const uint32_t b = T.strb[Ib], xb = T.sb[Ib], eb = ~b & T.maskN;
@@ -612,7 +625,7 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
         if (k0) __syncthreads();  // the previous chunk is consumed
         for (int i = threadIdx.x; i < K * Da; i += kAbThreads) {
             const int k = i / Da, c = i - k * Da;
-            part[(size_t)c * K + k] = k < kn ? A.C[(size_t)s_Jb[k0 + k] * Da + c] : mka<Amp>(0, 0);
+            part[(size_t)c * PS + k] = k < kn ? A.C[(size_t)s_Jb[k0 + k] * Da + c] : mka<Amp>(0, 0);
         }
         for (int i = threadIdx.x; i < NN * KP; i += kAbThreads) {
             const int qp = i / KP, k = i - qp * KP, q = qp / N, p = qp - q * N;
@@ -654,7 +667,7 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
             Amp sk[K];
             {   // beta singles: same column of the staged rows
                 Amp c[K];
-                lds_c<K>(part + (size_t)Ia * K, c);
+                lds_c<K>(part + (size_t)Ia * PS, c);
                 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     R v = vbk[k];
@@ -678,8 +691,8 @@ __global__ void __launch_bounds__(kAbThreads, 1) k_sigma_ab(RowArgs<Amp> A) {
                     const uint32_t s1 = (uint32_t)par(ppa & m1) ^ (uint32_t)(p < q1);
                     Amp c0[K], c1[K];
                     R v0[KP], v1[KP];
-                    lds_c<K>(part + (size_t)J0 * K, c0);
-                    lds_c<K>(part + (size_t)J1 * K, c1);
+                    lds_c<K>(part + (size_t)J0 * PS, c0);
+                    lds_c<K>(part + (size_t)J1 * PS, c1);
                     lds_r<KP>(eriS + (q0 * N + p) * KPS, v0);
                     lds_r<KP>(eriS + (q1 * N + p) * KPS, v1);
                     #pragma unroll
@@ -1000,7 +1013,8 @@ static size_t ab_smem(int dtype, int K, const RowTables &T) {
     const size_t amp = amp_size(dtype), real = single_prec(dtype) ? 4 : 8;
     const size_t KP = real == 4 ? (size_t)((K + 3) & ~3) : (size_t)((K + 1) & ~1);
     const size_t KPS = ((KP * real / 16) & 1) ? KP : KP + 16 / real;  // AbLayout<R, K>::KPS
-    return (size_t)K * T.Da * amp + (size_t)T.N * T.N * KPS * real + (size_t)K * T.N * real + ((size_t)2 << T.N);
+    const size_t PS = (size_t)ab_row_stride(K, (int)amp);
+    return PS * T.Da * amp + (size_t)T.N * T.N * KPS * real + (size_t)K * T.N * real + ((size_t)2 << T.N);
 }
 
 // k_sigma_same's dynamic shared memory, with or without the alpha rank table; its
