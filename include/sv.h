@@ -406,8 +406,11 @@ typedef enum {
                                        are one allocation (not with a caller-provided
                                        adjoint vector, checkpoints or the record-scan
                                        expectation); 0 two separate vectors */
-    SV_OPT_WAIT_POLLS = 15,         /* polls of each bounded wait (each poll a try-wait
-                                       and a 32 ns sleep) before a kernel gives up: the
+    SV_OPT_WAIT_POLLS = 15,         /* polls of each bounded wait before a kernel gives up
+                                       (a poll: in k_ab_tc an mbarrier try-wait that
+                                       suspends the thread for at most 64 ns; in k_same_tc
+                                       a try-wait and a 32 ns sleep; at a grid barrier a
+                                       read of its counter and a 32 ns sleep): the
                                        tensor-core expectation kernels' mbarrier waits
                                        (variants 4 and 5: the kernel then waits, bounded,
                                        for its copies and MMAs in flight, frees its

@@ -31,7 +31,8 @@
 // row and kappa, rebuilt when the tile changes), flipping sign bits and pairing halves
 // only, and write it to tensor memory (tcgen05.st: each builder warp its lane quarter,
 // row = lane, two K per column), where the MMAs read A; they copy the unit's B rows
-// (pieces of a precomputed table) into shared memory in the canonical no-swizzle
+// (pieces of a precomputed table, the rows named by a per-partner-row column table read
+// one unit ahead) into shared memory in the canonical no-swizzle
 // K-major layout (core matrices of 8 rows x 16 bytes);
 // lane 0 of warp 16 issues tcgen05.mma kind::f16 (six piece products per plane:
 // float32-level accuracy) into one of two tensor-memory accumulators; four epilogue
@@ -50,7 +51,7 @@ namespace {
 
 constexpr int kAbBuild = 512;                  // builder threads (16 warps): 4 per tile row
 constexpr int kAbKpt = 4;                      // K entries of a stage per builder thread (16 / 4)
-constexpr int kAbEpi = 128;                    // epilogue threads (4 warps: one per tensor-memory lane quarter)
+constexpr int kAbEpi = 256;                    // epilogue threads (8 warps: two per tensor-memory lane quarter)
 constexpr int kAbThreadsTc = kAbBuild + 32 + kAbEpi;  // builders, the MMA warp, the epilogue warps
 constexpr int kAbM = 128;                      // alpha strings per tile
 constexpr int kAbKc = 16;                      // K (orbitals and orbital pairs) per stage
@@ -65,21 +66,23 @@ static_assert(kAbABase + kAbS * kAbAStage <= 512, "tensor memory: accumulators a
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// One poll: a try-wait that suspends the thread until the phase completes or at most
+// kAbPollNs nanoseconds have passed (a thread waiting here wakes as soon as the phase
+// completes, and takes no issue slots meanwhile).
+constexpr uint32_t kAbPollNs = 64;
 __device__ __forceinline__ bool ab_try(uint32_t mbar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(mbar), "r"(parity)
+        : "r"(mbar), "r"(parity), "n"(kAbPollNs)
         : "memory");
     return ok != 0;
 }
 
 __device__ __forceinline__ bool ab_wait(uint32_t mbar, uint32_t parity, uint32_t spins) {
-    for (uint32_t it = 0; it < spins; ++it) {
+    for (uint32_t it = 0; it < spins; ++it)
         if (ab_try(mbar, parity)) return true;
-        __nanosleep(32);
-    }
     return false;
 }
 
@@ -125,6 +128,35 @@ __device__ __forceinline__ uint64_t ab_desc(uint32_t addr) {
     return d;
 }
 
+// The twelve (P = 2) or six MMAs of one K block in stage S: per plane the six piece products
+// (A piece, B piece) = (0,0) (0,1) (1,0) (0,2) (1,1) (2,0) into the plane's accumulator
+// (columns dacc + plane kAbMaxN).  Every operand is a compile-time offset from the
+// loop-invariant tensor-memory base and B descriptor, so the issuing thread spends a
+// few instructions per MMA; `first` starts the accumulation (the unit's first K block).
+constexpr int kAbStageBytes = 3 * kAbMaxN * kAbKc * 2;  // B ring stage: three pieces of 64 rows x 16 K
+template <int P, int S>
+__device__ __forceinline__ void ab_mma_stage(uint32_t tmem, uint64_t d0, uint32_t dacc, uint32_t idesc, uint32_t first) {
+    constexpr int pa[6] = {0, 0, 1, 0, 1, 2}, pbk[6] = {0, 1, 0, 2, 1, 0};
+    constexpr uint32_t kPieceD = (kAbMaxN * kAbKc * 2) >> 4, kStageD = kAbStageBytes >> 4;
+    #pragma unroll
+    for (int pl = 0; pl < P; ++pl) {
+        #pragma unroll
+        for (int x = 0; x < 6; ++x) {
+            // A from tensor memory (lanes = tile rows, two K per column), B from shared memory;
+            // B descriptor: that of the ring's start plus the byte offset in 16-byte units (the
+            // start-address field does not carry: shared addresses < 256 KB)
+            const uint32_t ta = tmem + (uint32_t)(kAbABase + S * kAbAStage + (pl * 3 + pa[x]) * kAbACols);
+            const uint64_t db = d0 + (uint64_t)(S * kStageD + pbk[x] * kPieceD);
+            const uint32_t acc = x > 0 ? 1u : first ^ 1u;
+            asm volatile(
+                "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, q;\n\t}\n" ::"r"(dacc + (uint32_t)(pl * kAbMaxN)),
+                "r"(ta), "l"(db), "r"(idesc), "r"(acc)
+                : "memory");
+        }
+    }
+}
+
 // byte offset of (row r, 16-byte column kc) in a tile of 16 K
 __device__ __forceinline__ uint32_t ab_off(int r, int kc) { return (uint32_t)(((r >> 3) * 2 + kc) * 128 + (r & 7) * 16); }
 
@@ -154,8 +186,10 @@ struct AbTcArgs {
     int ldi;                  // row stride of Xi in amplitudes (a multiple of 4: 16-byte rows)
     const uint16_t *stra, *strb, *ra;
     const uint16_t *Bp;       // pieces [3][rowsB][256] of the B table (rows: N^2 integral rows, Db own rows, a zero row)
+    const uint16_t *rowB;     // [Db][64]: the B-table row of each column of partner row b' (k_ab_rows)
     size_t pb;                // piece stride of Bp (elements)
-    float *H;                 // planes [P][Db][ncols][Da]
+    float *H;                 // planes [P][Db][ncols][ldh]
+    int ldh;                  // row stride of H (floats, a multiple of 32: 128-byte rows)
     size_t hplane;
     int Da, Db, N, na, nb, ncols, nK, units;
     uint32_t maskN;
@@ -165,9 +199,9 @@ struct AbTcArgs {
                               // and the epilogue's first waits run out with nothing in flight
 };
 
-// K entries per tile row in the table (nK * 16) plus 8: an odd number of 16-byte words
-// per row, so the builders' 16-byte reads of 8 consecutive rows hit distinct banks.
-__host__ __device__ __forceinline__ int ab_tstride(int nK) { return nK * kAbKc + 8; }
+// K entries per tile row in the table (nK * 16) plus 4: an odd number of 8-byte words
+// per row, so the builders' 8-byte reads of 16 consecutive rows hit distinct bank pairs.
+__host__ __device__ __forceinline__ int ab_tstride(int nK) { return nK * kAbKc + 4; }
 
 template <int P>
 __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
@@ -175,11 +209,10 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
     __shared__ __align__(8) uint64_t full[kAbS], empty[kAbS], accf[2], acce[2], done;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int s_fail;
-    __shared__ int s_rowB[kAbMaxN];
     __shared__ uint8_t s_kp[kAbMaxK], s_kq[kAbMaxK];
     // dynamic: stage ring of B (1024-aligned), the two staged X rows, the tile's table; the A
     // stages live in tensor memory (columns kAbABase + s kAbAStage + (plane 3 + piece) kAbACols)
-    constexpr int kStageBytes = 3 * kAbMaxN * kAbKc * 2;
+    constexpr int kStageBytes = kAbStageBytes;
     const uint32_t raw = su32(ab_smem), sbase = (raw + 1023u) & ~1023u;
     uint8_t *ring = ab_smem + (sbase - raw);
     // staged X rows: ldi amplitudes copied, then 4 zero amplitudes (what zero table entries read)
@@ -235,8 +268,9 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
         // ------------------------------------------------------------ builders
         const int r = tid & (kAbM - 1), hf = tid >> 7;  // tile row; which 4 of a stage's 16 K
         const int rowbytes = g.ldi * 12;                // a multiple of 16
-        auto stage_row = [&](int u, int buf) {          // asynchronous copy of X row u % Db
-            const uint8_t *src = reinterpret_cast<const uint8_t *>(g.Xi) + (size_t)(u % g.Db) * rowbytes;
+        const uint32_t zoff = (uint32_t)g.ldi * 3;      // table entry of a zero (the zero amplitude)
+        auto stage_row = [&](int row, int buf) {        // asynchronous copy of X row `row`
+            const uint8_t *src = reinterpret_cast<const uint8_t *>(g.Xi) + (size_t)row * rowbytes;
             uint8_t *dst = reinterpret_cast<uint8_t *>(xrow + (size_t)buf * xstride);
             for (int i = tid * 16; i < rowbytes; i += kAbBuild * 16)
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst + i)), "l"(src + i) : "memory");
@@ -254,13 +288,20 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
             bdst[k] = piece * (ncolsP * kAbKc * 2) + (int)ab_off(rem >> 1, rem & 1);
         }
         const uint16_t *bsrc[1] = {g.Bp};
-        stage_row(blockIdx.x, 0);
+        int brow[1];
+        #pragma unroll
+        for (int k = 0; k < 1; ++k) {
+            const int ii = bsel[k] < 0 ? 0 : bsel[k], rem = ii - (ii / (ncolsP * 2)) * ncolsP * 2;
+            brow[k] = g.rowB[(size_t)((int)blockIdx.x % g.Db) * kAbMaxN + (rem >> 1)];
+        }
+        stage_row((int)blockIdx.x % g.Db, 0);
         for (int u = blockIdx.x; u < g.units; u += gridDim.x, ++it) {
-            const int atile = u / g.Db, bp = u - atile * g.Db, buf = it & 1;
+            const int atile = u / g.Db, buf = it & 1;
             asm volatile("cp.async.wait_all;" ::: "memory");
             // this unit's row has landed; every builder is done with the previous unit
             if (builders_any(tid == 0 && s_fail)) break;
-            if (u + (int)gridDim.x < g.units) stage_row(u + gridDim.x, buf ^ 1);
+            const int un = u + (int)gridDim.x;  // the next unit
+            if (un < g.units) stage_row(un % g.Db, buf ^ 1);
             if (atile != cur_tile) {
                 // the tile's table: per row and kappa, the word offset in a row buffer of the
                 // partner amplitude (3 J; 3 ldi, a zero amplitude, where the entry is zero)
@@ -268,10 +309,10 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                 cur_tile = atile;
                 const int Ia = atile * kAbM + r;
                 const bool valid = Ia < g.Da;
-                const uint32_t a = valid ? g.stra[Ia] : 0u, zero = (uint32_t)g.ldi * 3;
+                const uint32_t a = valid ? g.stra[Ia] : 0u;
                 const int part = tstride / (kAbBuild / kAbM);
                 for (int k = hf * part; k < (hf + 1) * part; ++k) {
-                    uint32_t e = zero;
+                    uint32_t e = zoff;
                     if (valid && k < Ktot) {
                         const int p = s_kp[k], q = s_kq[k];
                         if (p == q) {
@@ -283,27 +324,14 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                     }
                     tbl[r * tstride + k] = (uint16_t)e;
                 }
+                builders_sync();  // the rows' entries are read by the other quarters' threads
             }
-            if (tid < kAbMaxN) {  // the unit's B rows: b''s excitations s (occupied) -> r (empty), own, zero
-                const uint32_t bs = g.strb[bp];
-                const int nbs = g.nb * (N - g.nb);
-                int row = N * N + g.Db;  // the zero row
-                if (tid < nbs) {
-                    const int i = tid / (N - g.nb), j = tid - i * (N - g.nb);
-                    uint32_t o = bs, z = ~bs & g.maskN;
-                    for (int k = 0; k < i; ++k) o &= o - 1u;
-                    for (int k = 0; k < j; ++k) z &= z - 1u;
-                    row = (__ffs(o) - 1) * N + (__ffs(z) - 1);
-                } else if (tid == nbs) {
-                    row = N * N + bp;
-                }
-                s_rowB[tid] = row;
-            }
-            builders_sync();
+            // this unit's B rows (read one unit ahead from the per-partner-row table)
             #pragma unroll
             for (int k = 0; k < 1; ++k) {
                 const int ii = bsel[k] < 0 ? 0 : bsel[k], piece = ii / (ncolsP * 2), rem = ii - piece * ncolsP * 2;
-                bsrc[k] = g.Bp + (size_t)piece * g.pb + (size_t)s_rowB[rem >> 1] * 256 + (rem & 1) * 8;
+                bsrc[k] = g.Bp + (size_t)piece * g.pb + (size_t)brow[k] * 256 + (rem & 1) * 8;
+                if (un < g.units) brow[k] = g.rowB[(size_t)(un % g.Db) * kAbMaxN + (rem >> 1)];
             }
             const uint32_t *xr = xrow + (size_t)buf * xstride;
             const uint16_t *trow = tbl + r * tstride + hf * kAbKpt;
@@ -370,7 +398,8 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
     } else if (tid >= kAbBuild + 32) {
         // ------------------------------------------------------------ epilogue warps
         // drain each unit's accumulator (row bp, tile row r = this thread's lane) into H
-        const int quarter = warp & 3, r = quarter * 32 + (tid & 31);
+        // (two warps per lane quarter, taking alternate 16-column chunks)
+        const int quarter = warp & 3, r = quarter * 32 + (tid & 31), eh = (warp - kAbBuild / 32 - 1) >> 2;
         int it = 0;
         for (int u = blockIdx.x; u < g.units; u += gridDim.x, ++it) {
             const int atile = u / g.Db, bp = u - atile * g.Db, t = it & 1, ia = atile * kAbM + r;
@@ -386,8 +415,8 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
             for (int pl = 0; pl < P; ++pl) {
                 const uint32_t tbase =
                     tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * kAbAccCols + pl * kAbMaxN);
-                float *Hp = g.H + (size_t)pl * g.hplane + (size_t)bp * g.ncols * g.Da + ia;
-                for (int c = 0; c < g.ncols; c += 16) {
+                float *Hp = g.H + (size_t)pl * g.hplane + (size_t)bp * g.ncols * g.ldh + ia;
+                for (int c = 16 * eh; c < g.ncols; c += 32) {
                     uint32_t v[16];
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
@@ -401,7 +430,7 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                     if (ok_row) {
                         #pragma unroll
                         for (int j = 0; j < 16; ++j)
-                            if (c + j < g.ncols) Hp[(size_t)(c + j) * g.Da] = __uint_as_float(v[j]);
+                            if (c + j < g.ncols) Hp[(size_t)(c + j) * g.ldh] = __uint_as_float(v[j]);
                     }
                 }
             }
@@ -413,7 +442,7 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
         // kind::f16, D float32, A and B bf16, both K-major, N = ncolsP, M = 128
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ncolsP >> 3) << 17) |
                                ((uint32_t)(kAbM >> 4) << 24);
-        const int pa[6] = {0, 0, 1, 0, 1, 2}, pbk[6] = {0, 1, 0, 2, 1, 0};
+        const uint64_t d0 = ab_desc(sbase);
         int gch = 0, it = 0;
         bool stop = false;
         for (int u = blockIdx.x; u < g.units && !stop; u += gridDim.x, ++it) {
@@ -428,23 +457,13 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t base = sbase + (uint32_t)(s * kStageBytes);
-                const uint32_t abase = tmem + (uint32_t)(kAbABase + s * kAbAStage);
-                #pragma unroll
-                for (int pl = 0; pl < P; ++pl) {
-                    const uint32_t d = tmem + (uint32_t)(t * kAbAccCols + pl * kAbMaxN);
-                    #pragma unroll
-                    for (int x = 0; x < 6; ++x) {
-                        // A from tensor memory (lanes = tile rows, two K per column), B from shared memory
-                        const uint32_t ta = abase + (uint32_t)((pl * 3 + pa[x]) * kAbACols);
-                        const uint64_t db = ab_desc(base + (uint32_t)(pbk[x] * ncolsP * kAbKc * 2));
-                        const uint32_t acc = (c > 0 || x > 0) ? 1u : 0u;
-                        asm volatile(
-                            "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, q;\n\t}\n" ::"r"(d),
-                            "r"(ta), "l"(db), "r"(idesc), "r"(acc)
-                            : "memory");
-                    }
+                const uint32_t dacc = tmem + (uint32_t)(t * kAbAccCols), first = c == 0 ? 1u : 0u;
+                static_assert(kAbS == 4, "one case per stage");
+                switch (s) {
+                    case 0: ab_mma_stage<P, 0>(tmem, d0, dacc, idesc, first); break;
+                    case 1: ab_mma_stage<P, 1>(tmem, d0, dacc, idesc, first); break;
+                    case 2: ab_mma_stage<P, 2>(tmem, d0, dacc, idesc, first); break;
+                    default: ab_mma_stage<P, 3>(tmem, d0, dacc, idesc, first); break;
                 }
                 ab_commit(su32(&empty[s]));
             }
@@ -495,6 +514,25 @@ __global__ void __launch_bounds__(256) k_ab_table(const float *__restrict__ eri,
     Bp[2 * pb + at] = (uint16_t)a3;
 }
 
+// The B-table row of each column of partner row b' (one block of kAbMaxN threads per
+// b'): column j < nb (N - nb) is the j-th excitation s (occupied) -> r (empty) of b', s
+// the (j / (N - nb))-th occupied and r the (j % (N - nb))-th empty orbital in increasing
+// order, row s N + r; column nb (N - nb) is b''s own row N^2 + b'; the rest the zero row.
+__global__ void __launch_bounds__(kAbMaxN) k_ab_rows(const uint16_t *__restrict__ strb, int N, int nb, int Db,
+                                                     uint16_t *__restrict__ rowB) {
+    const int bp = blockIdx.x, t = threadIdx.x, ne = N - nb, nbs = nb * ne;
+    int row = N * N + Db;
+    if (t < nbs) {
+        uint32_t o = strb[bp], z = ~o & ((1u << N) - 1u);
+        for (int k = 0; k < t / ne; ++k) o &= o - 1u;
+        for (int k = 0; k < t % ne; ++k) z &= z - 1u;
+        row = (__ffs(o) - 1) * N + (__ffs(z) - 1);
+    } else if (t == nbs) {
+        row = N * N + bp;
+    }
+    rowB[(size_t)bp * kAbMaxN + t] = (uint16_t)row;
+}
+
 size_t ab_tc_smem(int Da, int N) {
     const size_t stage = 3 * kAbMaxN * kAbKc * 2;
     const int nK = (N * (N + 1) / 2 + kAbKc - 1) / kAbKc;
@@ -507,10 +545,19 @@ size_t ab_tc_smem(int Da, int N) {
 // Rows of the B table (and its piece stride): N^2 + Db + 1 rows of 256.
 size_t ab_table_rows(int N, int Db) { return (size_t)N * N + Db + 1; }
 
-cudaError_t launch_ab_table(const float *eri, const float *Jt, const uint16_t *strb, int N, int Db, uint16_t *Bp,
-                            size_t pb, cudaStream_t st) {
-    if (N * N > 256) return cudaErrorInvalidValue;
+// Elements of the per-partner-row column table (uint16) that launch_ab_table writes.
+size_t ab_rowb_elems(int Db) { return (size_t)Db * kAbMaxN; }
+
+// The B table pieces and, where rowB is given, the column table [Db][64] of the sector
+// with nb beta electrons (two launches).
+cudaError_t launch_ab_table(const float *eri, const float *Jt, const uint16_t *strb, int N, int nb, int Db,
+                            uint16_t *Bp, size_t pb, uint16_t *rowB, cudaStream_t st) {
+    if (N * N > 256 || nb < 0 || nb > N) return cudaErrorInvalidValue;
     k_ab_table<<<(unsigned)ab_table_rows(N, Db), 256, 0, st>>>(eri, Jt, strb, N, Db, Bp, pb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !rowB) return e;
+    if (nb * (N - nb) + 1 > kAbMaxN) return cudaSuccess;  // more columns than k_ab_tc takes: no column table
+    k_ab_rows<<<Db, kAbMaxN, 0, st>>>(strb, N, nb, Db, rowB);
     return cudaGetLastError();
 }
 
@@ -527,19 +574,25 @@ bool ab_tc_fits(int planes, int Da, int Db, int na, int nb, int N) {
 // Row stride (amplitudes) of the interleaved X pieces the kernel reads.
 int ab_xi_ld(int Da) { return (Da + 3) / 4 * 4; }
 
+// Row stride (floats) of the product planes H: whole 128-byte lines, so that each epilogue
+// warp's store of 32 consecutive alpha strings fills one line (tile starts are multiples
+// of 128 strings).
+int ab_h_ld(int Da) { return (Da + 31) / 32 * 32; }
+
 // H = the per-partner-row products (see above); Xi [Db][ab_xi_ld(Da)][3] the phased
 // amplitudes as bf16 pieces (phase kernel); Bp the B table pieces; H planes
-// [planes][Db][ncols][Da] (hplane elements apart).
+// [planes][Db][ncols][ab_h_ld(Da)] (hplane elements apart); rowB the column table of
+// launch_ab_table.
 // spins: polls of each bounded wait; stall: the test hook of AbTcArgs.
 cudaError_t launch_ab_tc(const uint32_t *Xi, int planes, const uint16_t *stra, const uint16_t *strb,
-                         const uint16_t *ra, const uint16_t *Bp, size_t pb, float *H, size_t hplane, int Da, int Db,
+                         const uint16_t *ra, const uint16_t *Bp, size_t pb, const uint16_t *rowB, float *H, size_t hplane, int Da, int Db,
                          int N, int na, int nb, int *err, uint32_t spins, int stall, int sm_count, cudaStream_t st) {
     if (!ab_tc_fits(planes, Da, Db, na, nb, N) || ((uintptr_t)Xi & 15) || ((uintptr_t)Bp & 15) || (pb & 7) ||
-        spins < 1)
+        !rowB || spins < 1)
         return cudaErrorInvalidValue;
     AbTcArgs g;
-    g.Xi = Xi; g.ldi = ab_xi_ld(Da); g.stra = stra; g.strb = strb; g.ra = ra; g.Bp = Bp; g.pb = pb; g.H = H;
-    g.hplane = hplane; g.Da = Da; g.Db = Db; g.N = N; g.na = na; g.nb = nb;
+    g.Xi = Xi; g.ldi = ab_xi_ld(Da); g.stra = stra; g.strb = strb; g.ra = ra; g.Bp = Bp; g.pb = pb; g.rowB = rowB; g.H = H;
+    g.hplane = hplane; g.ldh = ab_h_ld(Da); g.Da = Da; g.Db = Db; g.N = N; g.na = na; g.nb = nb;
     g.ncols = nb * (N - nb) + 1;
     g.nK = (N * (N + 1) / 2 + kAbKc - 1) / kAbKc;
     g.units = ((Da + kAbM - 1) / kAbM) * Db;

@@ -898,10 +898,10 @@ __global__ void __launch_bounds__(kThreads) k_sigma_comb(RowArgs<Amp> A, SameGem
             const uint32_t bp = b ^ (1u << r) ^ (1u << sx);
             // column of (s occupied, r empty) among b''s excitations
             const int col = __popc(bp & ((1u << sx) - 1u)) * ne + __popc(~bp & T.maskN & ((1u << r) - 1u));
-            s_hoff[threadIdx.x] = ((size_t)T.rb[bp] * g.ncols + col) * Da;
+            s_hoff[threadIdx.x] = ((size_t)T.rb[bp] * g.ncols + col) * g.ldh;
             s_hneg[threadIdx.x] = par(b & between(r, sx));
         } else if ((int)threadIdx.x == nbs) {
-            s_hoff[nbs] = ((size_t)Ib * g.ncols + nbs) * Da;
+            s_hoff[nbs] = ((size_t)Ib * g.ncols + nbs) * g.ldh;
             s_hneg[nbs] = 0;
         }
     }
@@ -1103,7 +1103,8 @@ cudaError_t launch_same_tc(const uint16_t *M, size_t pm, const uint16_t *X, size
                            float *G, int planes, int Da, int Db, int lda, int ldb, int *err, uint32_t spins, int stall,
                            cudaStream_t st);
 cudaError_t launch_ab_tc(const uint32_t *Xi, int planes, const uint16_t *stra, const uint16_t *strb,
-                         const uint16_t *ra, const uint16_t *Bp, size_t pb, float *H, size_t hplane, int Da, int Db,
+                         const uint16_t *ra, const uint16_t *Bp, size_t pb, const uint16_t *rowB, float *H,
+                         size_t hplane, int Da, int Db,
                          int N, int na, int nb, int *err, uint32_t spins, int stall, int sm_count, cudaStream_t st);
 
 template <typename Amp>
@@ -1125,7 +1126,7 @@ static cudaError_t launch_same_t(RowArgs<Amp> A, const RowTables &T, int dtype, 
         A.same_gemm = 1;
         if (g.abtc) {
             if (g.ev && (e = cudaEventRecord(g.ev[2], st)) != cudaSuccess) return e;
-            e = launch_ab_tc(g.Xi, g.planes, T.stra, T.strb, T.ra, g.Bp, g.pb, g.H, g.hplane, T.Da, T.Db, T.N, g.na,
+            e = launch_ab_tc(g.Xi, g.planes, T.stra, T.strb, T.ra, g.Bp, g.pb, g.rowB, g.H, g.hplane, T.Da, T.Db, T.N, g.na,
                              g.nb, g.err, g.spins, (g.stall >> 1) & 1, sm_count, st);
             if (e != cudaSuccess) return e;
             if (g.ev && (e = cudaEventRecord(g.ev[3], st)) != cudaSuccess) return e;

@@ -93,10 +93,12 @@ cudaError_t launch_same_mats(int n, const RowTables &T, const double *hdiag, con
                              double *dA, double *dB, int lda, int ldb, cudaStream_t st);
 cudaError_t launch_split_bf16x3(const float *x, uint16_t *out, size_t n, size_t piece, int sm_count, cudaStream_t st);
 size_t ab_table_rows(int N, int Db);
-cudaError_t launch_ab_table(const float *eri, const float *Jt, const uint16_t *strb, int N, int Db, uint16_t *Bp,
-                            size_t pb, cudaStream_t st);
+size_t ab_rowb_elems(int Db);
+cudaError_t launch_ab_table(const float *eri, const float *Jt, const uint16_t *strb, int N, int nb, int Db, uint16_t *Bp,
+                            size_t pb, uint16_t *rowB, cudaStream_t st);
 bool ab_tc_fits(int planes, int Da, int Db, int na, int nb, int N);
 int ab_xi_ld(int Da);
+int ab_h_ld(int Da);
 int sigma_ab_chunk(int dtype, const RowTables &T, int nb, int want);
 const int *sigma_ab_sizes(int dtype);
 
@@ -844,7 +846,7 @@ static bool use_ab_tc(sv_handle h) {
     const int planes = is_complex(h->dtype) ? 2 : 1, N = h->n / 2;
     if (!ab_tc_fits(planes, h->Da, h->Db, h->na, h->nb, N)) return false;
     if (h->expect_variant == 5) return true;
-    const double hb = 4.0 * planes * (double)h->Db * (h->nb * (N - h->nb) + 1) * (double)h->Da;
+    const double hb = 4.0 * planes * (double)h->Db * (h->nb * (N - h->nb) + 1) * (double)ab_h_ld(h->Da);
     if (hb > (double)(16ull << 30)) return false;
     return h->max_bytes <= 0 || (double)h->bytes_owned + (h->ab_H_bytes >= hb ? 0.0 : hb) <= (double)h->max_bytes;
 }
@@ -862,7 +864,9 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
     const size_t rowsB = N * N <= 256 ? ab_table_rows(N, (int)Db) : 0, pbB = rowsB * 256;
     const size_t nm = Da * lda + Db * ldb, mf = nm * sizeof(float), dof = (mf + 255) / 256 * 256,
                  sof = (dof + (Da + Db) * sizeof(double) + 255) / 256 * 256,
-                 bof = (sof + 3 * nm * sizeof(uint16_t) + 255) / 256 * 256, mb = bof + 3 * pbB * sizeof(uint16_t);
+                 bof = (sof + 3 * nm * sizeof(uint16_t) + 255) / 256 * 256,
+                 rbo = (bof + 3 * pbB * sizeof(uint16_t) + 255) / 256 * 256,
+                 mb = rbo + (rowsB ? ab_rowb_elems((int)Db) * sizeof(uint16_t) : 0);
     float *Ma = nullptr;
     if (!h->sg_mats || h->sg_serial != T->serial || h->sg_na != h->na || h->sg_nb != h->nb) {
         if (h->sg_mats_bytes < mb) {
@@ -880,9 +884,10 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
                                        h->stream));
         h->launches += 2;
         if (rowsB) {
-            SV_CUDA(h, launch_ab_table((const float *)R.eri, (const float *)R.Jt, h->str_b, N, (int)Db,
-                                       (uint16_t *)((uint8_t *)h->sg_mats + bof), pbB, h->stream));
-            h->launches += 1;
+            SV_CUDA(h, launch_ab_table((const float *)R.eri, (const float *)R.Jt, h->str_b, N, h->nb, (int)Db,
+                                       (uint16_t *)((uint8_t *)h->sg_mats + bof), pbB,
+                                       (uint16_t *)((uint8_t *)h->sg_mats + rbo), h->stream));
+            h->launches += 2;
         }
         h->sg_serial = T->serial;
         h->sg_na = h->na;
@@ -940,9 +945,9 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
     g->abtc = 0;
     bool ab_ok = abtc;
     const int ncols = h->nb * (N - h->nb) + 1;
-    const size_t hplane = Db * (size_t)ncols * Da, hb = (size_t)planes * hplane * sizeof(float);
+    const size_t hplane = Db * (size_t)ncols * ab_h_ld((int)Da), hb = (size_t)planes * hplane * sizeof(float);
     if (ab_ok && h->ab_H_bytes < hb) {
-        // H [planes][Db][ncols][Da]; where the automatic choice cannot have it, variant 4 runs
+        // H [planes][Db][ncols][ab_h_ld(Da)]; where the automatic choice cannot have it, variant 4 runs
         dev_free(h, h->ab_H, h->ab_H_bytes);
         h->ab_H = nullptr;
         h->ab_H_bytes = 0;
@@ -960,9 +965,11 @@ static sv_status ensure_same_gemm(sv_handle h, DevTables *T, const RowTables &R,
         g->Xi = (uint32_t *)(B + xb + tb + gb);
         g->ldi = (int)ldi;
         g->Bp = (const uint16_t *)((const uint8_t *)h->sg_mats + bof);
+        g->rowB = (const uint16_t *)((const uint8_t *)h->sg_mats + rbo);
         g->pb = pbB;
         g->H = h->ab_H;
         g->hplane = hplane;
+        g->ldh = ab_h_ld((int)Da);
         g->ncols = ncols;
         g->na = h->na;
         g->nb = h->nb;

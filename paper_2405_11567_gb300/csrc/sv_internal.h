@@ -134,15 +134,17 @@ struct SameGemm {
                                                // products [0], [1] and the alpha-beta products [2], [3]
     int stall = 0;                             // test hook: bit 0 k_same_tc, bit 1 k_ab_tc issue nothing
     // variant 5: the alpha-beta part on the tensor cores (k_ab_tc) into planes H
-    // [planes][Db][ncols][Da] (hplane floats apart), gathered by k_sigma_comb; Bp: the
+    // [planes][Db][ncols][ldh] (hplane floats apart), gathered by k_sigma_comb; Bp: the
     // bf16 pieces [3][N^2 + Db + 1][256] of its integral table (piece stride pb)
     int abtc = 0;
     uint32_t *Xi = nullptr;                    // phased amplitudes as interleaved bf16 pieces [Db][ldi][3]
     int ldi = 0;
     const uint16_t *Bp = nullptr;
     size_t pb = 0;
+    const uint16_t *rowB = nullptr;            // [Db][64] B-table row of each column of a partner row
     float *H = nullptr;
     size_t hplane = 0;
+    int ldh = 0;                               // row stride of H (floats, a multiple of 32)
     int ncols = 0, na = 0, nb = 0;
 };
 
