@@ -364,9 +364,16 @@ typedef enum {
                                        pipe; the amplitudes are converted once per call
                                        and sigma written back as float64 (two work
                                        matrices of 16 Da Db bytes, complex) */
-    SV_OPT_RDM_VARIANT = 4,         /* 0 auto (= 2); 1 sector gather: one thread per sector
-                                       determinant (dense storage only); 2 string rows: one
-                                       block per beta string of the compact matrix */
+    SV_OPT_RDM_VARIANT = 4,         /* 0 auto (3 for float64 states, else 2); 1 sector
+                                       gather: one thread per sector determinant (dense
+                                       storage only); 2 string rows: one block per beta
+                                       string of the compact matrix, in the state's own
+                                       arithmetic; 3 string rows in float-float arithmetic
+                                       (float64 states, on the FP32 pipe: the compact
+                                       matrix converted once per call into a work matrix
+                                       of Da Db x 16 or 8 bytes; single-precision states
+                                       take 2).  The automatic choice keeps 2 where that
+                                       matrix cannot be allocated */
     SV_OPT_PROFILE = 5,             /* 1: record CUDA events around each phase (sv_phase_times) */
     SV_OPT_LAYOUT_AUTO = 6,         /* 1 (default): sv_energy_grad chooses the storage layout
                                        from its operator list (sv_set_layout); 0: keep it */

@@ -1252,6 +1252,20 @@ cudaError_t launch_sigma_rows_ff(const void *C, void *lam, void *lamc, int dtype
     return cudaErrorInvalidValue;
 }
 
+// The float-float form (ffc for complex128, ff for float64) of `count` amplitudes of a
+// float64 state, into out (count x 16 or 8 bytes).
+cudaError_t launch_to_ff(const void *C, int dtype, size_t count, void *out, int sm_count, cudaStream_t st) {
+    int grid = (int)std::min<size_t>((count + kThreads - 1) / kThreads, (size_t)sm_count * 8);
+    if (grid < 1) grid = 1;
+    if (dtype == SV_C128)
+        k_to_ff<double2, ffc><<<grid, kThreads, 0, st>>>((const double2 *)C, (ffc *)out, count);
+    else if (dtype == SV_R64)
+        k_to_ff<double, ff><<<grid, kThreads, 0, st>>>((const double *)C, (ff *)out, count);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 // K: rows per chunk of the split form (sigma_ab_chunk), 0 for the single-kernel form.
 // partial must hold 3 * Db doubles (rows: energy, norm, alpha-beta energy share).
 // g (may be NULL): the product forms (single-precision states, K > 0): the phase kernel,

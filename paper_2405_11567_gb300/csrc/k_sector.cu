@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "sv_internal.h"
+#include "sv_ff.cuh"
 #include "sv_sigma.cuh"
 
 namespace svk {
@@ -432,6 +433,27 @@ __global__ void __launch_bounds__(kThreads) k_sweep_adjoint_li(A *__restrict__ C
 // the block adds them (the owner's slot for a pair element, the warps in order for the
 // others) into float64 running sums, written to partial[e][blockIdx.x] at the end:
 // fixed-order sums.
+// The row sums' arithmetic: float32 or float64 for those states, float-float (hi + lo
+// float32 words, error-free transformations) for float64 states converted to it.
+__device__ __forceinline__ double to_double(float x) { return (double)x; }
+__device__ __forceinline__ double to_double(double x) { return x; }
+__device__ __forceinline__ double to_double(ff x) { return ff_to(x); }
+__device__ __forceinline__ ff re_dot(ffc u, ffc v) { return ff_fma(u.y, v.y, u.x * v.x); }
+__device__ __forceinline__ ff im_dot(ffc u, ffc v) { return ff_fma(u.x, v.y, -(u.y * v.x)); }
+__device__ __forceinline__ ff re_dot(ff u, ff v) { return u * v; }
+__device__ __forceinline__ ff im_dot(ff, ff) { return ff(0, 0); }
+// fixed shuffle tree as warp_sum, each step a float-float addition
+__device__ __forceinline__ ff warp_sum(ff v) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ff w;
+        w.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+        v = v + w;
+    }
+    return v;
+}
+
 template <typename A>
 __global__ void __launch_bounds__(kThreads) k_rdm_rows(const A *__restrict__ C, SectTabs T, int N,
                                                        const uint32_t *__restrict__ alist,
@@ -463,7 +485,7 @@ __global__ void __launch_bounds__(kThreads) k_rdm_rows(const A *__restrict__ C, 
         }
         nrm = warp_sum(nrm);
         if (lane == 0) {
-            my[0] = (double)nrm;
+            my[0] = to_double(nrm);
             my[1] = 0.0;
         }
         #pragma unroll
@@ -471,9 +493,9 @@ __global__ void __launch_bounds__(kThreads) k_rdm_rows(const A *__restrict__ C, 
             if (p >= N) break;
             const R s = warp_sum(occ[p]);
             if (lane == 0) {
-                my[2 * (1 + 2 * p)] = (double)s;
+                my[2 * (1 + 2 * p)] = to_double(s);
                 my[2 * (1 + 2 * p) + 1] = 0.0;
-                my[2 * (2 + 2 * p)] = ((b >> p) & 1u) ? (double)nrm : 0.0;
+                my[2 * (2 + 2 * p)] = ((b >> p) & 1u) ? to_double(nrm) : 0.0;
                 my[2 * (2 + 2 * p) + 1] = 0.0;
             }
         }
@@ -515,8 +537,8 @@ __global__ void __launch_bounds__(kThreads) k_rdm_rows(const A *__restrict__ C, 
             re = warp_sum(re);
             im = warp_sum(im);
             if (lane == 0) {
-                my[2 * e] = (double)re;
-                my[2 * e + 1] = (double)im;
+                my[2 * e] = to_double(re);
+                my[2 * e + 1] = to_double(im);
             }
         }
         __syncthreads();
@@ -686,12 +708,23 @@ int rdm_rows_grid(int Db, int sm_count, int bps) {
 // partial: [2 n_el][grid] doubles (n_el = rdm_rows_elements(n)), reduced by launch_reduce_rows.
 // alist / ainfo: the alpha-pair lists (one list op per pair p < q in (p, q) order with flip
 // mask {p, q}, "from" pattern {q} and sign mask between(2p, 2q)) and their int4 records.
-cudaError_t launch_rdm_rows(const void *C, int dtype, int n, const uint32_t *sa, const uint32_t *sb,
+// ff_form: C holds the float-float form of a float64 state (ffc for complex128, ff for
+// float64), as launch_to_ff writes it.
+cudaError_t launch_rdm_rows(const void *C, int dtype, int ff_form, int n, const uint32_t *sa, const uint32_t *sb,
                             const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb, int Da,
                             int Db, int grid, const uint32_t *alist, const int *ainfo, double *partial,
                             cudaStream_t st) {
     SectTabs T = tabs(sa, sb, stra, strb, ra, rb, Da, Db);
     const size_t smem = sizeof(double) * 2 * rdm_rows_elements(n) * (1 + kThreads / 32);  // <= 40 KB (n <= 32)
+    if (ff_form) {
+        if (dtype == SV_C128)
+            k_rdm_rows<ffc><<<grid, kThreads, smem, st>>>((const ffc *)C, T, n / 2, alist, (const int4 *)ainfo, partial);
+        else if (dtype == SV_R64)
+            k_rdm_rows<ff><<<grid, kThreads, smem, st>>>((const ff *)C, T, n / 2, alist, (const int4 *)ainfo, partial);
+        else
+            return cudaErrorInvalidValue;  // single-precision states have no float-float form
+        return cudaGetLastError();
+    }
     SV_DISPATCH_AMP(dtype, k_rdm_rows<A><<<grid, kThreads, smem, st>>>((const A *)C, T, n / 2, alist,
                                                                        (const int4 *)ainfo, partial));
     return cudaGetLastError();

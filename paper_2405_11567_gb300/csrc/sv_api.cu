@@ -68,7 +68,8 @@ cudaError_t launch_adjoint_l(void *psi, void *lam, int dtype, const uint32_t *al
                              int nb_l, int Da, double c, double s, int grid, double *partial, cudaStream_t st);
 int rdm_rows_elements(int n);
 int rdm_rows_grid(int Db, int sm_count, int bps);
-cudaError_t launch_rdm_rows(const void *C, int dtype, int n, const uint32_t *sa, const uint32_t *sb,
+cudaError_t launch_to_ff(const void *C, int dtype, size_t count, void *out, int sm_count, cudaStream_t st);
+cudaError_t launch_rdm_rows(const void *C, int dtype, int ff_form, int n, const uint32_t *sa, const uint32_t *sb,
                             const uint16_t *stra, const uint16_t *strb, const uint16_t *ra, const uint16_t *rb, int Da,
                             int Db, int grid, const uint32_t *alist, const int *ainfo, double *partial,
                             cudaStream_t st);
@@ -998,22 +999,50 @@ static bool use_ff(sv_handle h, int K) {
     return h->expect_variant == 6 || h->expect_variant == 0;
 }
 
+// Bytes of one compact float-float matrix of the state (rounded to 256).
+static size_t ff_matrix_bytes(sv_handle h) {
+    const size_t one = (size_t)h->Da * h->Db * (is_complex(h->dtype) ? 16 : 8);
+    return (one + 255) / 256 * 256;
+}
+
+// The float-float work buffer with at least `bytes` (kept across calls; the expectation
+// takes two matrices, the 1-RDM one).  SV_OK, or the allocation's status with nothing
+// held where the bytes are not available.
+static sv_status ensure_ffbuf(sv_handle h, size_t bytes) {
+    if (h->ffbuf_bytes >= bytes) return SV_OK;
+    dev_free(h, h->ffbuf, h->ffbuf_bytes);
+    h->ffbuf = nullptr;
+    h->ffbuf_bytes = 0;
+    const sv_status st = dev_alloc(h, &h->ffbuf, bytes, "float-float work matrices");
+    if (st == SV_OK) h->ffbuf_bytes = bytes;
+    else cudaGetLastError();
+    return st;
+}
+
+// The 1-RDM rows' input: the compact matrix Cm itself, or, for float64 states under
+// SV_OPT_RDM_VARIANT 3 or the automatic choice, its float-float form in the work buffer
+// (the automatic choice keeps float64 rows where that buffer cannot be had).
+static sv_status rdm_input(sv_handle h, const void *Cm, const void **src, int *ff_form) {
+    *src = Cm;
+    *ff_form = 0;
+    if (single_prec(h->dtype) || (h->rdm_variant != 0 && h->rdm_variant != 3)) return SV_OK;
+    const sv_status st = ensure_ffbuf(h, ff_matrix_bytes(h));
+    if (st != SV_OK) return h->rdm_variant == 3 ? st : SV_OK;
+    SV_CUDA(h, launch_to_ff(Cm, h->dtype, (size_t)h->Da * h->Db, h->ffbuf, h->sm_count, h->stream));
+    h->launches++;
+    *src = h->ffbuf;
+    *ff_form = 1;
+    return SV_OK;
+}
+
 static sv_status sigma_rows(sv_handle h, DevTables *T, const RowTables &R, const void *C, void *lam, void *lamc,
                             double e_shift) {
     const int K = row_chunk(h, R);
     if (use_ff(h, K) && T->eri_ff) {
-        const size_t one = (size_t)h->Da * h->Db * (is_complex(h->dtype) ? 16 : 8), r = (one + 255) / 256 * 256;
-        bool ok = true;
-        if (h->ffbuf_bytes < 2 * r) {
-            dev_free(h, h->ffbuf, h->ffbuf_bytes);
-            h->ffbuf = nullptr;
-            h->ffbuf_bytes = 0;
-            const sv_status st = dev_alloc(h, &h->ffbuf, 2 * r, "float-float sigma work matrices");
-            if (st != SV_OK && h->expect_variant == 6) return st;
-            ok = st == SV_OK;  // the automatic choice falls back to the float64 split form
-            if (ok) h->ffbuf_bytes = 2 * r;
-            else cudaGetLastError();
-        }
+        const size_t r = ff_matrix_bytes(h);
+        const sv_status st = ensure_ffbuf(h, 2 * r);
+        if (st != SV_OK && h->expect_variant == 6) return st;
+        const bool ok = st == SV_OK;  // the automatic choice falls back to the float64 split form
         if (ok) {
         RowTables Tf = R;
         Tf.eri = T->eri_ff;
@@ -1301,13 +1330,16 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
         const int n_el = rdm_rows_elements(h->n);
         const int cands[] = {2, 4, 8, 16};
         SV_TRY(ensure_partials(h, (size_t)2 * n_el * rdm_rows_grid(h->Db, h->sm_count, 16)));
+        const void *src = nullptr;
+        int ff_form = 0;
+        SV_TRY(rdm_input(h, Cm, &src, &ff_form));
         int best_b = 4;
         float best_t = -1.f;
         for (int b : cands) {
             const int grid = rdm_rows_grid(h->Db, h->sm_count, b);
             const float t = time_best(h, e0, e1, [&]() -> sv_status {
-                SV_CUDA(h, launch_rdm_rows(Cm, h->dtype, h->n, h->str_sa, h->str_sb, h->str_a, h->str_b, h->rank_a,
-                                           h->rank_b, h->Da, h->Db, grid, (const uint32_t *)h->rdm_lists.buf,
+                SV_CUDA(h, launch_rdm_rows(src, h->dtype, ff_form, h->n, h->str_sa, h->str_sb, h->str_a, h->str_b,
+                                           h->rank_a, h->rank_b, h->Da, h->Db, grid, (const uint32_t *)h->rdm_lists.buf,
                                            h->rdm_lists.dinfo, h->partials, h->stream));
                 return SV_OK;
             });
@@ -1929,7 +1961,10 @@ sv_status sv_rdm1(sv_handle h, double *re_out, double *im_out) {
             h->launches++;
             Cm = h->Cbuf;
         }
-        SV_CUDA(h, launch_rdm_rows(Cm, h->dtype, h->n, h->str_sa, h->str_sb, h->str_a, h->str_b, h->rank_a,
+        const void *src = nullptr;
+        int ff_form = 0;
+        SV_TRY(rdm_input(h, Cm, &src, &ff_form));
+        SV_CUDA(h, launch_rdm_rows(src, h->dtype, ff_form, h->n, h->str_sa, h->str_sb, h->str_a, h->str_b, h->rank_a,
                                    h->rank_b, h->Da, h->Db, grid, (const uint32_t *)h->rdm_lists.buf,
                                    h->rdm_lists.dinfo, h->partials, h->stream));
         h->launches++;
@@ -2078,7 +2113,7 @@ sv_status sv_set_option(sv_handle h, sv_option opt, int64_t value) {
             h->expect_variant = (int)value;
             return SV_OK;
         case SV_OPT_RDM_VARIANT:
-            if (value < 0 || value > 2) return fail(h, SV_ERR_ARG, "rdm variant must be 0, 1 or 2");
+            if (value < 0 || value > 3) return fail(h, SV_ERR_ARG, "rdm variant must be 0 to 3");
             h->rdm_variant = (int)value;
             return SV_OK;
         case SV_OPT_SWEEP_BLOCKS_PER_SM:

@@ -201,9 +201,11 @@ def test_complex_start_open_shell(dtype):
 
 # ---------------------------------------------------------------- 1-RDM
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_rdm1_matches_oracle(dtype, variant):
+    """Sector gather (1), string rows in the state's arithmetic (2) and in float-float
+    arithmetic (3: float64 states; complex64 takes 2) against the oracle."""
     p = inputs.make_problem(14, 6, 60, seed=66)
     sec = _oracle_problem(p)
     psi = A.apply_ansatz(sec, p["ops"], p["theta"] * 5, A.hf_state(sec, p["occ"]))

@@ -136,12 +136,14 @@ def test_complex_start_open_shell(dtype):
     assert np.max(np.abs(st.rdm1() - rdm_ref)) <= TOL[dtype]["rdm"]
 
 
+@pytest.mark.parametrize("variant", [0, 2, 3])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-def test_rdm1_matches_oracle(dtype):
+def test_rdm1_matches_oracle(dtype, variant):
     p = inputs.make_problem(14, 6, 60, seed=66)
     sec = oracle.Sector(14, 3, 3)
     psi = A.apply_ansatz(sec, p["ops"], p["theta"] * 5, A.hf_state(sec, p["occ"]))
     st = _state(14, 3, 3, dtype)
+    st.set_option(sv.SV_OPT_RDM_VARIANT, variant)
     st.prepare_hf(p["occ"])
     st.apply_ansatz(p["ops"], p["theta"] * 5)
     assert np.max(np.abs(st.rdm1() - A.rdm1(sec, psi))) <= TOL[dtype]["rdm"]
