@@ -539,6 +539,7 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": int((1 + L) * 8 + 2 * 2 * p["n_orb"] ** 2 * 8)},
         "gpu_launches": int(head["launches"]),
         "autotune": head["tuned"],
+        "step_lower_bound": step_lower_bound(rot_bytes, n, 8, head["ms"] / K, peak),
     }
     if golden is not None:
         line["vs_oracle"] = vs_golden(head["out"], golden)
@@ -754,6 +755,18 @@ def measured_tensor_peaks():
             d = json.load(f)
         return {"bf16_tflops": float(d["bf16_tflops"]), "kind": "measured burst (MEASURED_PEAKS.json bf16_tflops)"}
     return {"bf16_tflops": 1900.0, "kind": "fallback 1.9 PFLOP/s bf16 burst"}
+
+
+def step_lower_bound(rot_bytes, n, amp_bytes, ms_step, peak):
+    """The whole evaluation against its algorithmic lower bound: the forward sweep's touched bytes, twice that for
+    the adjoint sweep (psi and lambda), two reads of the state and one write (energy, sigma) -- the bytes the dense
+    method must move -- at the measured copy peak, against the measured step time."""
+    state = float(2 ** n * amp_bytes)
+    fwd = float(rot_bytes.sum())
+    total = fwd + 2.0 * fwd + 3.0 * state
+    t_lb = total / (peak * 1e9) * 1e3
+    return {"bytes": total, "ms_at_peak": t_lb, "ms_measured": ms_step, "frac": t_lb / ms_step,
+            "terms": "forward touched bytes + 2 x forward (adjoint on psi and lambda) + 2 state reads + 1 state write"}
 
 
 def oracle_seconds(fn, budget_s=2.0):
