@@ -197,7 +197,10 @@ sv_status sv_ham_destroy(sv_ham_handle ham);
 /* ---- the hot path ---------------------------------------------------------- */
 
 /* psi <- U_L ... U_1 psi with U_k = exp(theta[k] (T_k - T_k^dagger)), ops[0] first.
- * cos/sin of theta are taken on the host in float64.  One kernel per operator. */
+ * cos/sin of theta are taken on the host in float64.  One kernel per operator (dense
+ * storage; sector storage: one cooperative launch for the whole list, SV_OPT_SECTOR_SWEEP).
+ * On a state still equal to the determinant sv_prepare_hf wrote, with SV_OPT_LAYOUT_AUTO
+ * on, the storage layout first becomes the one the operator list prefers. */
 sv_status sv_apply_ansatz(sv_handle h, const sv_excitation *ops, int n_ops, const double *theta);
 
 /* *e_out = <psi|H|psi> / <psi|psi> of the current state (Fig. 1: the QPU/GPU
@@ -376,7 +379,10 @@ typedef enum {
                                        matrix cannot be allocated */
     SV_OPT_PROFILE = 5,             /* 1: record CUDA events around each phase (sv_phase_times) */
     SV_OPT_LAYOUT_AUTO = 6,         /* 1 (default): sv_energy_grad chooses the storage layout
-                                       from its operator list (sv_set_layout); 0: keep it */
+                                       from its operator list (sv_set_layout), and so does
+                                       sv_apply_ansatz while the state is still the
+                                       determinant sv_prepare_hf wrote (re-written in the new
+                                       layout); 0: keep it (sv_set_layout sets 0) */
     SV_OPT_AB_CHUNK = 7,            /* variant 3: partner rows staged per chunk (complex64:
                                        2, 4, 6 or 8; complex128: 1, 2, 3 or 4; another value
                                        takes the largest compiled size below it; 0 = the

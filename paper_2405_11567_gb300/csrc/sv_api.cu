@@ -1504,6 +1504,7 @@ sv_status sv_prepare_hf(sv_handle h, const int32_t *occ, int n_occ) {
     h->nb = nb;
     SV_TRY(prepare_reference(h));
     h->prepared = true;
+    h->at_ref = true;
     return SV_OK;
 }
 
@@ -1536,6 +1537,7 @@ sv_status sv_prepare_state(sv_handle h, const void *amplitudes_host, int n_alpha
     DeviceGuard g(h->device);
     h->failed = false;
     h->prepared = false;
+    h->at_ref = false;
     if (!h->ref_vec) SV_TRY(dev_alloc(h, &h->ref_vec, vec_bytes(h), "reference copy"));
     if (h->storage == 1) {
         // host order is the dense qubit-order vector: keep its sector entries in C[rank(b)][rank(a)] order
@@ -1640,6 +1642,7 @@ sv_status sv_get_amplitudes(sv_handle h, const uint64_t *basis, int count, void 
 
 sv_status sv_state_device_ptr(sv_handle h, void **psi_dev) {
     if (!h || !psi_dev) return fail(h, SV_ERR_ARG, "NULL argument");
+    h->at_ref = false;  // the caller may write the state through the pointer
     *psi_dev = h->psi;
     return SV_OK;
 }
@@ -1690,6 +1693,21 @@ sv_status sv_apply_ansatz(sv_handle h, const sv_excitation *ops, int n_ops, cons
     SV_TRY(build_ops(h, ops, n_ops, theta, d));
     DeviceGuard g(h->device);
     L2FetchScope l2(h);
+    if (h->layout_auto && n_ops > 0 && h->storage == 0 && h->at_ref && h->ref_kind == 1) {
+        // the state is still the HF determinant: take the layout the operator list prefers
+        // (as sv_energy_grad does) by writing the determinant anew in it, one store
+        int np[32];
+        layout_from_ops(h->n, ops, n_ops, np);
+        bool same = true;
+        for (int q = 0; q < h->n; ++q) same = same && np[q] == h->perm[q];
+        if (!same) {
+            for (int q = 0; q < 32; ++q) h->perm[q] = q < h->n ? np[q] : q;
+            drop_layout_caches(h);
+            SV_TRY(prepare_reference(h));
+            SV_TRY(build_ops(h, ops, n_ops, theta, d));
+        }
+    }
+    h->at_ref = false;
     SV_TRY(forward(h, d, false));
     return SV_OK;
 }
@@ -1718,6 +1736,7 @@ sv_status sv_energy_grad(sv_handle h, sv_ham_handle ham, const sv_excitation *op
     SV_TRY(check_ham(h, ham));
     std::vector<OpDesc> d;
     SV_TRY(build_ops(h, ops, n_ops, theta, d));  // validates in any layout
+    h->at_ref = false;
     DeviceGuard g(h->device);
     L2FetchScope l2(h);
     NvtxClose nvtx_close{h};
@@ -2035,6 +2054,7 @@ sv_status sv_autotune(sv_handle h, sv_ham_handle ham, const sv_excitation *ops, 
         cudaEventDestroy(e0);
         return fail(h, SV_ERR_CUDA, "autotune: event creation failed");
     }
+    h->at_ref = false;
     const sv_status st = autotune_impl(h, ham, d, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -230,6 +230,7 @@ struct sv_ctx {
     bool own_psi = true, own_lam = true;
     // prepared state
     bool prepared = false;
+    bool at_ref = false;       // psi holds the HF reference exactly as sv_prepare_hf wrote it
     bool nvtx_open = false;    // a phase range of this handle is open (NVTX)
     bool failed = false;
     int na = -1, nb = -1;

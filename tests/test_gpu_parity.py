@@ -446,6 +446,37 @@ def test_automatic_layout_moves_frequent_qubits_high():
     assert np.all(np.diff(by_bit) >= 0)
 
 
+def test_apply_ansatz_takes_the_automatic_layout_on_a_fresh_reference():
+    """sv_apply_ansatz on the determinant sv_prepare_hf wrote takes the layout its operator
+    list prefers (the one sv_energy_grad chooses) and gives the oracle's state; applied to any
+    other state, or with SV_OPT_LAYOUT_AUTO off, it keeps the layout."""
+    p = inputs.config_problem(2)
+    n = p["n_qubits"]
+    sec = _oracle_problem(p)
+    psi_ref = A.apply_ansatz(sec, p["ops"], p["theta"], A.hf_state(sec, p["occ"]))
+    ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
+    st = _gpu_state(n, "c128")
+    st.prepare_hf(p["occ"])
+    st.apply_ansatz(p["ops"], p["theta"])
+    lay = st.layout()
+    assert not np.array_equal(lay, np.arange(n))
+    got = st.state()
+    assert np.max(np.abs(got[sec.dets.astype(np.int64)] - psi_ref)) <= TOL["c128"]["amp"]
+    assert np.count_nonzero(np.delete(got, sec.dets.astype(np.int64))) == 0
+    st2 = _gpu_state(n, "c128")
+    st2.prepare_hf(p["occ"])
+    st2.energy_grad(ham, p["ops"], p["theta"])
+    assert np.array_equal(st2.layout(), lay)
+    st.apply_ansatz(p["ops"][:5], p["theta"][:5])        # not the reference any more: layout kept
+    assert np.array_equal(st.layout(), lay)
+    st3 = _gpu_state(n, "c128")
+    st3.set_option(sv.SV_OPT_LAYOUT_AUTO, 0)
+    st3.prepare_hf(p["occ"])
+    st3.apply_ansatz(p["ops"], p["theta"])
+    assert np.array_equal(st3.layout(), np.arange(n))
+    assert np.max(np.abs(st3.state() - got)) <= TOL["c128"]["amp"]
+
+
 # ---------------------------------------------------------------- qubit excitations (QEB pool)
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])

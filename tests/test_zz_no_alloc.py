@@ -46,6 +46,7 @@ def test_rdm1_noalloc_matches_sv_rdm1_on_two_calls(dtype, tol):
     # a closed-shell HF-based state of another size in between reuses the same scratch
     q = inputs.config_problem(2)
     st2 = sv.StateVector(q["n_qubits"], dtype)
+    st2.set_layout(np.arange(q["n_qubits"]))   # qubit order in device memory (the automatic layout off)
     st2.prepare_hf(q["occ"])
     st2.apply_ansatz(q["ops"], q["theta"])
     ref2 = st2.rdm1()
