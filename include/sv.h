@@ -407,7 +407,10 @@ typedef enum {
                                        returns (sv_apply_ansatz returns before its
                                        kernels finish: the limit is a hint, so only
                                        their speed can depend on when it changes back).
-                                       0 leaves the context's value alone.  Rotations of
+                                       0 leaves the context's value alone, and so do
+                                       states smaller than four times the device's L2
+                                       (served from L2; a change of the limit costs about
+                                       half a millisecond of host time).  Rotations of
                                        excitations on low address bits touch runs of
                                        32-64 bytes, which larger fetches double */
     SV_OPT_REVERSE_INTERLEAVED = 14, /* dense storage: 1 (default) sv_energy_grad runs its

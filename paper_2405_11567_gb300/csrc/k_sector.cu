@@ -120,6 +120,24 @@ struct PairWalk {
 
 constexpr int kPairBatch = 4;
 
+// The list entries of a thread's next kPairBatch pairs (ok[v]: pair v exists).  The lists
+// are read-only during a sweep, so the whole-sweep kernels load a batch's entries ahead:
+// the first batch of an operator before its grid barrier, each next batch while the
+// current batch's amplitudes are in flight.
+struct PairBatch {
+    uint32_t ea[kPairBatch], eb[kPairBatch];
+    bool ok[kPairBatch];
+    __device__ __forceinline__ void load(PairWalk &w, const uint32_t *al, const uint32_t *bl, int nb_l) {
+        #pragma unroll
+        for (int v = 0; v < kPairBatch; ++v) {
+            ok[v] = w.r < nb_l;
+            eb[v] = ok[v] ? bl[w.r] : 0u;  // 0: rank 0, in bounds
+            ea[v] = ok[v] ? al[w.i] : 0u;
+            w.next();
+        }
+    }
+};
+
 // psi <- exp(theta G) psi over the op's pairs.
 template <typename A>
 __global__ void __launch_bounds__(kThreads) k_rotate_l(A *__restrict__ psi, const uint32_t *__restrict__ al,
@@ -321,23 +339,22 @@ __global__ void __launch_bounds__(kThreads) k_sweep_rotate_l(A *__restrict__ psi
         const int4 li = g.info[k];
         const int na_l = li.y, nb_l = li.w;
         if (na_l <= 0 || nb_l <= 0) continue;  // no pair in the sector: nothing written, no barrier
+        const uint32_t *al = g.lists + li.x, *bl = g.lists + li.z;
+        PairWalk w(na_l);
+        bool more = w.r < nb_l;
+        PairBatch cur;
+        cur.load(w, al, bl, nb_l);
         if (gen > 0 && !sweep_barrier(g, gen - 1, &s_ok)) return;
         ++gen;
-        const uint32_t *al = g.lists + li.x, *bl = g.lists + li.z;
         const R c = (R)g.cs[k].x, sn = (R)g.cs[k].y;
-        PairWalk w(na_l);
-        while (w.r < nb_l) {
+        while (more) {
             size_t I[kPairBatch], J[kPairBatch];
-            bool ok[kPairBatch];
             R ss[kPairBatch];
             #pragma unroll
             for (int v = 0; v < kPairBatch; ++v) {
-                ok[v] = w.r < nb_l;
-                const uint32_t eb = ok[v] ? bl[w.r] : 0u, ea = ok[v] ? al[w.i] : 0u;
-                I[v] = (size_t)(eb & 0x7FFFu) * g.Da + (ea & 0x7FFFu);
-                J[v] = (size_t)(eb >> 16) * g.Da + (ea >> 16);
-                ss[v] = ((ea ^ eb) & 0x8000u) ? -sn : sn;
-                w.next();
+                I[v] = (size_t)(cur.eb[v] & 0x7FFFu) * g.Da + (cur.ea[v] & 0x7FFFu);
+                J[v] = (size_t)(cur.eb[v] >> 16) * g.Da + (cur.ea[v] >> 16);
+                ss[v] = ((cur.ea[v] ^ cur.eb[v]) & 0x8000u) ? -sn : sn;
             }
             A u[kPairBatch], x[kPairBatch];
             #pragma unroll
@@ -345,12 +362,16 @@ __global__ void __launch_bounds__(kThreads) k_sweep_rotate_l(A *__restrict__ psi
                 u[v] = psi[I[v]];
                 x[v] = psi[J[v]];
             }
+            more = w.r < nb_l;
+            PairBatch nxt;
+            if (more) nxt.load(w, al, bl, nb_l);
             #pragma unroll
             for (int v = 0; v < kPairBatch; ++v) {
-                if (!ok[v]) continue;
+                if (!cur.ok[v]) continue;
                 psi[I[v]] = lin2<A>(c, u[v], -ss[v], x[v]);
                 psi[J[v]] = lin2<A>(c, x[v], ss[v], u[v]);
             }
+            if (more) cur = nxt;
         }
     }
 }
@@ -369,22 +390,22 @@ __global__ void __launch_bounds__(kThreads) k_sweep_adjoint_li(A *__restrict__ C
         const int na_l = li.y, nb_l = li.w;
         double acc = 0.0;
         if (na_l > 0 && nb_l > 0) {
+            const uint32_t *al = g.lists + li.x, *bl = g.lists + li.z;
+            PairWalk w(na_l);
+            bool more = w.r < nb_l;
+            PairBatch cur;
+            cur.load(w, al, bl, nb_l);
             if (gen > 0 && !sweep_barrier(g, gen - 1, &s_ok)) return;
             ++gen;
-            const uint32_t *al = g.lists + li.x, *bl = g.lists + li.z;
             const R c = (R)g.cs[k].x, sn = (R)g.cs[k].y;
-            PairWalk w(na_l);
-            while (w.r < nb_l) {
+            while (more) {
                 size_t I[kPairBatch], J[kPairBatch];
-                bool ok[kPairBatch], neg[kPairBatch];
+                bool neg[kPairBatch];
                 #pragma unroll
                 for (int v = 0; v < kPairBatch; ++v) {
-                    ok[v] = w.r < nb_l;
-                    const uint32_t eb = ok[v] ? bl[w.r] : 0u, ea = ok[v] ? al[w.i] : 0u;
-                    I[v] = (size_t)(eb & 0x7FFFu) * g.Da + (ea & 0x7FFFu);
-                    J[v] = (size_t)(eb >> 16) * g.Da + (ea >> 16);
-                    neg[v] = ((ea ^ eb) & 0x8000u) != 0u;
-                    w.next();
+                    I[v] = (size_t)(cur.eb[v] & 0x7FFFu) * g.Da + (cur.ea[v] & 0x7FFFu);
+                    J[v] = (size_t)(cur.eb[v] >> 16) * g.Da + (cur.ea[v] >> 16);
+                    neg[v] = ((cur.ea[v] ^ cur.eb[v]) & 0x8000u) != 0u;
                 }
                 AmpPair<A> pu[kPairBatch], px[kPairBatch];
                 #pragma unroll
@@ -392,10 +413,13 @@ __global__ void __launch_bounds__(kThreads) k_sweep_adjoint_li(A *__restrict__ C
                     pu[v] = P[I[v]];
                     px[v] = P[J[v]];
                 }
+                more = w.r < nb_l;
+                PairBatch nxt;
+                if (more) nxt.load(w, al, bl, nb_l);
                 R t = 0;
                 #pragma unroll
                 for (int v = 0; v < kPairBatch; ++v) {
-                    if (!ok[v]) continue;
+                    if (!cur.ok[v]) continue;
                     const A u = pu[v].c, x = px[v].c, lu = pu[v].l, lx = px[v].l;
                     const R ti = re_dot(lx, u) - re_dot(lu, x);
                     t += neg[v] ? -ti : ti;
@@ -409,6 +433,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep_adjoint_li(A *__restrict__ C
                     P[J[v]] = ox;
                 }
                 acc += (double)t;
+                if (more) cur = nxt;
             }
         }
         const double s = block_sum(acc, red);
@@ -416,23 +441,6 @@ __global__ void __launch_bounds__(kThreads) k_sweep_adjoint_li(A *__restrict__ C
     }
 }
 
-// Density matrix by rows: a block takes beta strings (rows) Ib = blockIdx.x,
-// blockIdx.x + gridDim.x, ...; for each row
-//   norm and alpha occupations   sum_a |C[b][a]|^2 (a_p)                (all warps)
-//   beta occupations             the row norm when b holds p
-//   alpha pairs p < q            sum over a with q in a, p not in a of
-//                                conj(C[b][a']) C[b][a] (-1)^popc(x & between(2p, 2q)), a' = a - q + p
-//                                (those a from the pair's list, built once per sector)
-//   beta pairs p < q (b holds q, not p)
-//                                sum_a conj(C[b'][a]) C[b][a] (-1)^popc(x & between(2p+1, 2q+1))
-// (x = spread(a) | spread(b)), in the element order norm, n occupations
-// (j = 2p + sigma), alpha pairs, beta pairs.  Each pair element belongs to one warp
-// (pairs dealt round-robin to the warps), which sums it over the row with its lanes
-// and one warp reduction; the norm and occupations are summed by every warp over a
-// share of the row.  Each warp writes its sums to its own shared slots; after each row
-// the block adds them (the owner's slot for a pair element, the warps in order for the
-// others) into float64 running sums, written to partial[e][blockIdx.x] at the end:
-// fixed-order sums.
 // The row sums' arithmetic: float32 or float64 for those states, float-float (hi + lo
 // float32 words, error-free transformations) for float64 states converted to it.
 __device__ __forceinline__ double to_double(float x) { return (double)x; }
@@ -454,6 +462,23 @@ __device__ __forceinline__ ff warp_sum(ff v) {
     return v;
 }
 
+// Density matrix by rows: a block takes beta strings (rows) Ib = blockIdx.x,
+// blockIdx.x + gridDim.x, ...; for each row
+//   norm and alpha occupations   sum_a |C[b][a]|^2 (a_p)                (all warps)
+//   beta occupations             the row norm when b holds p
+//   alpha pairs p < q            sum over a with q in a, p not in a of
+//                                conj(C[b][a']) C[b][a] (-1)^popc(x & between(2p, 2q)), a' = a - q + p
+//                                (those a from the pair's list, built once per sector)
+//   beta pairs p < q (b holds q, not p)
+//                                sum_a conj(C[b'][a]) C[b][a] (-1)^popc(x & between(2p+1, 2q+1))
+// (x = spread(a) | spread(b)), in the element order norm, n occupations
+// (j = 2p + sigma), alpha pairs, beta pairs.  Each pair element belongs to one warp
+// (pairs dealt round-robin to the warps), which sums it over the row with its lanes
+// and one warp reduction; the norm and occupations are summed by every warp over a
+// share of the row.  Each warp writes its sums to its own shared slots; after each row
+// the block adds them (the owner's slot for a pair element, the warps in order for the
+// others) into float64 running sums, written to partial[e][blockIdx.x] at the end:
+// fixed-order sums.
 template <typename A>
 __global__ void __launch_bounds__(kThreads) k_rdm_rows(const A *__restrict__ C, SectTabs T, int N,
                                                        const uint32_t *__restrict__ alist,

@@ -670,12 +670,16 @@ static sv_status ensure_op_lists(sv_handle h, const std::vector<OpDesc> &ops, Op
 // granularity keeps the L2 from fetching larger blocks around runs of 32 or 64 bytes.
 // The granularity is a limit of the whole CUDA context, so the entry points that run
 // dense sweeps set the handle's value for the duration of the call and put the
-// context's previous value back when they return (a hint: a refusal is ignored).
+// context's previous value back when they return (a hint: a refusal is ignored).  Only
+// for states of at least four times the L2: smaller ones are served from L2, where the
+// granularity buys nothing, and each change of the limit costs about half a millisecond
+// of host time (measured on GB300), more than a small state's whole sweep.
 struct L2FetchScope {
     size_t prev = 0;
     bool restore = false;
     explicit L2FetchScope(sv_handle h) {
         if (h->storage != 0 || h->l2_fetch <= 0) return;
+        if (h->l2_bytes > 0 && vec_bytes(h) < 4 * (size_t)h->l2_bytes) return;
         if (cudaDeviceGetLimit(&prev, cudaLimitMaxL2FetchGranularity) != cudaSuccess) {
             cudaGetLastError();
             return;
@@ -1404,6 +1408,10 @@ static sv_status create_common(int n_qubits, sv_dtype dtype, void *cuda_stream, 
         return fail(nullptr, SV_ERR_CUDA, "no CUDA device");
     }
     cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (cudaDeviceGetAttribute(&h->l2_bytes, cudaDevAttrL2CacheSize, h->device) != cudaSuccess) {
+        cudaGetLastError();
+        h->l2_bytes = 0;
+    }
     if (psi_dev) {
         h->psi = psi_dev;
         h->own_psi = false;

@@ -322,4 +322,5 @@ struct sv_ctx {
     uint64_t launches = 0;
     std::string err;
     int sm_count = 148;
+    int l2_bytes = 0;          // the device's L2 size
 };
