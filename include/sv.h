@@ -502,6 +502,18 @@ uint64_t sv_launch_count(sv_handle h);
 /* Library version string. */
 const char *sv_version(void);
 
+/* The checked build (libsv_gb300_check.so: the kernels compiled with SV_CHECK, which test
+ * every index they compute from a host-built table against the size of the buffer it
+ * addresses and, for a bad one, skip the access and record it instead of faulting): the
+ * kinds of out-of-range index seen since the last call on the current device, then
+ * cleared.  Byte 0: the sector kernels (sweeps, 1-RDM rows), byte 1: the string-row
+ * expectation (alpha-beta plane offsets), byte 2: the alpha-beta tensor-core products
+ * (gather offsets); within a byte 1 pair address, 2 string rank, 4 gather offset, 8 plane
+ * offset; bit 31 where a word could not be read.  The default build returns 0.  Only the
+ * kernels built on host tables are checked; the dense kernels' addresses are formed by
+ * bit insertion and stay in range by construction. */
+uint32_t sv_check_status(void);
+
 #ifdef __cplusplus
 }
 #endif

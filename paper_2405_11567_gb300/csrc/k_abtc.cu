@@ -43,6 +43,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "sv_check.cuh"
 #include "sv_internal.h"
 
 namespace svk {
@@ -351,7 +352,9 @@ __global__ void __launch_bounds__(kAbThreadsTc, 1) k_ab_tc(AbTcArgs g) {
                     #pragma unroll
                     for (int k = 0; k < kAbKpt; ++k) {
                         const uint32_t e = (k & 1) ? te[k >> 1] >> 16 : te[k >> 1] & 0xFFFFu;
-                        const uint32_t *x = xr + (e & 0x3FFFu);
+                        // checked build: an offset past the row buffer reads the zero amplitude
+                        const uint32_t *x =
+                            xr + (SV_IN_RANGE((e & 0x3FFFu) + 2u, (uint32_t)xstride, kChkGather) ? (e & 0x3FFFu) : zoff);
                         w[k][0] = x[0];
                         w[k][1] = x[1];
                         w[k][2] = x[2];
@@ -614,5 +617,8 @@ cudaError_t launch_ab_tc(const uint32_t *Xi, int planes, const uint16_t *stra, c
     }
     return cudaGetLastError();
 }
+
+// This unit's check word (checked build), for sv_check_status.
+SV_CHECK_READER(check_word_abtc)
 
 }  // namespace svk

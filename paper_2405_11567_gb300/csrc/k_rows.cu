@@ -37,6 +37,7 @@
 // k_abtc.cu for the alpha-beta part.
 #include <cuda_bf16.h>
 
+#include "sv_check.cuh"
 #include "sv_ff.cuh"
 #include "sv_internal.h"
 #include "sv_sigma.cuh"
@@ -927,6 +928,7 @@ __global__ void __launch_bounds__(kThreads) k_sigma_comb(RowArgs<Amp> A, SameGem
         if constexpr (AmpT<Amp>::kCplx) gi = g.G[plane + off + Ia];
         if constexpr (GATHER) {
             for (int j = 0; j < nh; ++j) {
+                if (!SV_IN_RANGE(s_hoff[j] + Ia, g.hplane, kChkPlane)) continue;  // checked build: skip the term
                 const float *hp = g.H + s_hoff[j] + Ia;
                 float hr = hp[0], hi = 0.f;
                 if constexpr (AmpT<Amp>::kCplx) hi = hp[g.hplane];
@@ -1291,5 +1293,8 @@ cudaError_t launch_same_mats(int n, const RowTables &T, const double *hdiag, con
     k_same_mats<<<T.Da + T.Db, 128, 0, st>>>(A.T, Ma, Mb, dA, dB, lda, ldb);
     return cudaGetLastError();
 }
+
+// This unit's check word (checked build), for sv_check_status.
+SV_CHECK_READER(check_word_rows)
 
 }  // namespace svk

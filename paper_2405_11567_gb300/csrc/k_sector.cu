@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "sv_internal.h"
+#include "sv_check.cuh"
 #include "sv_ff.cuh"
 #include "sv_sigma.cuh"
 
@@ -300,7 +301,7 @@ struct SweepArgs {
     const uint32_t *lists;   // the ops' pair lists (k_build_lists)
     const int4 *info;        // per op: alpha offset, alpha length, beta offset, beta length
     const double2 *cs;       // per op: (cos theta, sin theta)
-    int n_ops, Da;
+    int n_ops, Da, Db;
     unsigned int *bar;       // barrier arrivals, zero at launch
     int *err;                // set to 1 when a barrier wait runs out
     uint32_t spins;          // polls of a barrier wait
@@ -355,6 +356,10 @@ __global__ void __launch_bounds__(kThreads) k_sweep_rotate_l(A *__restrict__ psi
                 I[v] = (size_t)(cur.eb[v] & 0x7FFFu) * g.Da + (cur.ea[v] & 0x7FFFu);
                 J[v] = (size_t)(cur.eb[v] >> 16) * g.Da + (cur.ea[v] >> 16);
                 ss[v] = ((cur.ea[v] ^ cur.eb[v]) & 0x8000u) ? -sn : sn;
+                if (!(SV_IN_RANGE(I[v], (size_t)g.Da * g.Db, kChkPair) && SV_IN_RANGE(J[v], (size_t)g.Da * g.Db, kChkPair))) {
+                    cur.ok[v] = false;  // checked build: skip the pair
+                    I[v] = J[v] = 0;
+                }
             }
             A u[kPairBatch], x[kPairBatch];
             #pragma unroll
@@ -406,6 +411,11 @@ __global__ void __launch_bounds__(kThreads) k_sweep_adjoint_li(A *__restrict__ C
                     I[v] = (size_t)(cur.eb[v] & 0x7FFFu) * g.Da + (cur.ea[v] & 0x7FFFu);
                     J[v] = (size_t)(cur.eb[v] >> 16) * g.Da + (cur.ea[v] >> 16);
                     neg[v] = ((cur.ea[v] ^ cur.eb[v]) & 0x8000u) != 0u;
+                    if (!(SV_IN_RANGE(I[v], (size_t)g.Da * g.Db, kChkPair) &&
+                          SV_IN_RANGE(J[v], (size_t)g.Da * g.Db, kChkPair))) {
+                        cur.ok[v] = false;  // checked build: skip the pair
+                        I[v] = J[v] = 0;
+                    }
                 }
                 AmpPair<A> pu[kPairBatch], px[kPairBatch];
                 #pragma unroll
@@ -543,6 +553,8 @@ __global__ void __launch_bounds__(kThreads) k_rdm_rows(const A *__restrict__ C, 
                 const uint32_t *L = alist + li.x, rsg = (uint32_t)par(xb & bm);
                 for (int i = lane; i < li.y; i += 32) {
                     const uint32_t ea = L[i];
+                    if (!(SV_IN_RANGE(ea & 0x7FFFu, T.Da, kChkRank) && SV_IN_RANGE(ea >> 16, T.Da, kChkRank)))
+                        continue;  // checked build: skip the entry
                     const A u = row[ea & 0x7FFFu], v = row[ea >> 16];
                     R ar = re_dot(v, u), ai = im_dot(v, u);  // conj(v) u
                     if (((ea >> 15) & 1u) ^ rsg) { ar = -ar; ai = -ai; }
@@ -550,13 +562,16 @@ __global__ void __launch_bounds__(kThreads) k_rdm_rows(const A *__restrict__ C, 
                     im += ai;
                 }
             } else if ((b & m) == f) {
-                const A *row2 = C + (size_t)T.rb[b ^ m] * T.Da;
-                for (int Ia = lane; Ia < T.Da; Ia += 32) {
-                    const A u = row[Ia], v = row2[Ia];
-                    R ar = re_dot(v, u), ai = im_dot(v, u);
-                    if (par((T.sa[Ia] | xb) & bm)) { ar = -ar; ai = -ai; }
-                    re += ar;
-                    im += ai;
+                const uint32_t r2 = T.rb[b ^ m];
+                if (SV_IN_RANGE(r2, T.Db, kChkRank)) {  // checked build: a bad rank skips the partner row
+                    const A *row2 = C + (size_t)r2 * T.Da;
+                    for (int Ia = lane; Ia < T.Da; Ia += 32) {
+                        const A u = row[Ia], v = row2[Ia];
+                        R ar = re_dot(v, u), ai = im_dot(v, u);
+                        if (par((T.sa[Ia] | xb) & bm)) { ar = -ar; ai = -ai; }
+                        re += ar;
+                        im += ai;
+                    }
                 }
             }
             re = warp_sum(re);
@@ -708,12 +723,12 @@ int sweep_grid(int dtype, bool adjoint, int Db, int sm_count, int bps) {
 // A refused cooperative launch returns its error (the caller falls back to one launch
 // per op).
 cudaError_t launch_sweep_l(void *buf, int dtype, bool adjoint, const uint32_t *lists, const int *info,
-                           const double *cs, int n_ops, int Da, int grid, unsigned int *bar, int *err, uint32_t spins,
-                           double *partial, cudaStream_t st) {
+                           const double *cs, int n_ops, int Da, int Db, int grid, unsigned int *bar, int *err,
+                           uint32_t spins, double *partial, cudaStream_t st) {
     if (n_ops <= 0) return cudaSuccess;
     if (grid <= 0) return cudaErrorInvalidValue;
     SweepArgs g;
-    g.lists = lists; g.info = (const int4 *)info; g.cs = (const double2 *)cs; g.n_ops = n_ops; g.Da = Da;
+    g.lists = lists; g.info = (const int4 *)info; g.cs = (const double2 *)cs; g.n_ops = n_ops; g.Da = Da; g.Db = Db;
     g.bar = bar; g.err = err; g.spins = spins; g.partial = partial;
     void *args[] = {&buf, &g};
     cudaError_t e = cudaErrorInvalidValue;
@@ -762,5 +777,8 @@ cudaError_t launch_gather_c(const void *psi, int dtype, const uint32_t *idx, int
     SV_DISPATCH_AMP(dtype, k_gather_c<A><<<grid, kThreads, 0, st>>>((const A *)psi, idx, count, (A *)out));
     return cudaGetLastError();
 }
+
+// This unit's check word (checked build), for sv_check_status.
+SV_CHECK_READER(check_word_sector)
 
 }  // namespace svk

@@ -60,8 +60,8 @@ cudaError_t launch_rotate_l(void *psi, int dtype, const uint32_t *al, int na_l, 
                             double c, double s, int grid, cudaStream_t st);
 int sweep_grid(int dtype, bool adjoint, int Db, int sm_count, int bps);
 cudaError_t launch_sweep_l(void *buf, int dtype, bool adjoint, const uint32_t *lists, const int *info,
-                           const double *cs, int n_ops, int Da, int grid, unsigned int *bar, int *err, uint32_t spins,
-                           double *partial, cudaStream_t st);
+                           const double *cs, int n_ops, int Da, int Db, int grid, unsigned int *bar, int *err,
+                           uint32_t spins, double *partial, cudaStream_t st);
 cudaError_t launch_adjoint_li(void *CL, int dtype, const uint32_t *al, int na_l, const uint32_t *bl, int nb_l, int Da,
                               double c, double s, int grid, double *partial, cudaStream_t st);
 cudaError_t launch_adjoint_l(void *psi, void *lam, int dtype, const uint32_t *al, int na_l, const uint32_t *bl,
@@ -119,6 +119,10 @@ static thread_local std::string g_err = "no error";
 
 namespace svk {
 void set_thread_error(const std::string &m) { g_err = m; }
+// the check words of the kernel units (sv_check.cuh)
+uint32_t check_word_sector();
+uint32_t check_word_rows();
+uint32_t check_word_abtc();
 }  // namespace svk
 
 static sv_status fail(sv_handle h, sv_status st, const std::string &msg) {
@@ -754,7 +758,8 @@ static bool sweep_once(sv_handle h, bool adjoint, void *buf, size_t L, int grid,
         return false;
     }
     const cudaError_t e = launch_sweep_l(buf, h->dtype, adjoint, (const uint32_t *)h->lists.buf, h->lists.dinfo,
-                                         (const double *)((const uint8_t *)h->sweep_buf + 256), (int)L, h->Da, grid,
+                                         (const double *)((const uint8_t *)h->sweep_buf + 256), (int)L, h->Da, h->Db,
+                                         grid,
                                          (unsigned int *)h->sweep_buf, h->kerr, (uint32_t)h->wait_polls, partial,
                                          h->stream);
     if (e != cudaSuccess) {
@@ -1364,6 +1369,11 @@ static sv_status autotune_impl(sv_handle h, sv_ham_handle ham, const std::vector
 extern "C" {
 
 const char *sv_version(void) { return "sv-gb300 0.1 (sm_103a)"; }
+
+uint32_t sv_check_status(void) {
+    const uint32_t a = check_word_sector(), b = check_word_rows(), c = check_word_abtc();
+    return (a & 0xFFu) | ((b & 0xFFu) << 8) | ((c & 0xFFu) << 16) | ((a | b | c) & 0x80000000u);
+}
 
 const char *sv_last_error(sv_handle h) { return h ? h->err.c_str() : g_err.c_str(); }
 

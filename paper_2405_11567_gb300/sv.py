@@ -49,7 +49,7 @@ EXPORTS = (
     "sv_energy", "sv_energy_grad", "sv_pool_gradients", "sv_rdm1", "sv_set_option", "sv_phase_times", "sv_last_error",
     "sv_launch_count", "sv_version", "sv_batch_create", "sv_batch_energy_grad", "sv_batch_set_time_limit",
     "sv_batch_launch_count", "sv_batch_destroy", "sv_rdm1_noalloc", "sv_autotune", "sv_get_option",
-    "sv_batch_autotune",
+    "sv_batch_autotune", "sv_check_status",
 )
 
 
@@ -73,7 +73,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The C-ABI library: the default build, or the checked build (SV_CHECK) when the
+    environment variable SV_GB300_CHECKED is 1."""
+    return _build.LIB_CHECK if os.environ.get("SV_GB300_CHECKED") == "1" else _build.LIB
 
 
 def lib():
@@ -111,6 +113,7 @@ def lib():
             "sv_last_error": (ctypes.c_char_p, [vp]),
             "sv_launch_count": (ctypes.c_uint64, [vp]),
             "sv_version": (ctypes.c_char_p, []),
+            "sv_check_status": (ctypes.c_uint32, []),
             "sv_batch_create": (i32, [i32, vp, i32, vp, pp]),
             "sv_batch_energy_grad": (i32, [vp, vp, vp, vp]),
             "sv_batch_set_time_limit": (i32, [vp, dbl]),
@@ -156,6 +159,12 @@ def _stream_ptr(stream):
 
 def sv_version() -> str:
     return lib().sv_version().decode()
+
+
+def sv_check_status() -> int:
+    """Checked build: the kinds of out-of-range table index its kernels skipped since the
+    last call (then cleared); 0 in the default build."""
+    return int(lib().sv_check_status())
 
 
 def sv_last_error(handle=None) -> str:

@@ -24,7 +24,7 @@ def cabi():
 
 def test_header_declares_exactly_the_exports():
     text = open(os.path.join(ROOT, "include", "sv.h")).read()
-    declared = set(re.findall(r"^\s*(?:sv_status|const char \*|uint64_t)\s*\*?\s*(sv_\w+)\s*\(", text, re.M))
+    declared = set(re.findall(r"^\s*(?:sv_status|const char \*|uint64_t|uint32_t)\s*\*?\s*(sv_\w+)\s*\(", text, re.M))
     assert declared == set(sv.EXPORTS)
 
 
@@ -32,6 +32,18 @@ def test_library_exports_every_declared_symbol(cabi):
     for name in sv.EXPORTS:
         assert hasattr(cabi, name), name
     assert "sm_103a" in sv.sv_version()
+
+
+def test_checked_build_exports_the_same_symbols_and_default_reports_nothing(cabi):
+    """The checked build (every source with SV_CHECK=1: kernels record out-of-range table
+    indices instead of faulting) compiles and exports the same C ABI; in the default build
+    sv_check_status is 0 (no GPU call)."""
+    path = libbuild.build(check=True)
+    assert path == libbuild.LIB_CHECK and os.path.exists(path)
+    checked = ctypes.CDLL(path)
+    for name in sv.EXPORTS:
+        assert hasattr(checked, name), name
+    assert sv.sv_check_status() == 0
 
 
 def test_library_built_for_sm_103a_only():
