@@ -35,8 +35,8 @@
 // one unit ahead) into shared memory in the canonical no-swizzle
 // K-major layout (core matrices of 8 rows x 16 bytes);
 // lane 0 of warp 16 issues tcgen05.mma kind::f16 (six piece products per plane:
-// float32-level accuracy) into one of two tensor-memory accumulators; four epilogue
-// warps (one per tensor-memory lane quarter) drain each finished accumulator into H
+// float32-level accuracy) into one of two tensor-memory accumulators; eight epilogue
+// warps (two per tensor-memory lane quarter) drain each finished accumulator into H
 // while the next unit is built.  Stage ring with full / empty mbarriers, accumulator
 // full / empty mbarriers; all waits bounded (past the limit: *err set, copies and MMAs
 // waited for, tensor memory freed, return).
