@@ -508,7 +508,7 @@ const char *sv_version(void);
  * kinds of out-of-range index seen since the last call on the current device, then
  * cleared.  Byte 0: the sector kernels (sweeps, 1-RDM rows), byte 1: the string-row
  * expectation (alpha-beta plane offsets), byte 2: the alpha-beta tensor-core products
- * (gather offsets); within a byte 1 pair address, 2 string rank, 4 gather offset, 8 plane
+ * (gather offsets), bits 24-27: pool screening (pair addresses); within a byte 1 pair address, 2 string rank, 4 gather offset, 8 plane
  * offset; bit 31 where a word could not be read.  The default build returns 0.  Only the
  * kernels built on host tables are checked; the dense kernels' addresses are formed by
  * bit insertion and stay in range by construction. */

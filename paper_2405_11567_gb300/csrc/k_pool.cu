@@ -13,6 +13,7 @@
 // s(x) (Re conj(lambda[x']) psi[x] - Re conj(lambda[x]) psi[x']) in float64, reduced
 // in a fixed order per block (k_pool_grad, the string scan).  k_pool_grad_l visits
 // the same pairs from per-operator pair lists, reading psi and lambda interleaved.
+#include "sv_check.cuh"
 #include "sv_internal.h"
 #include "sv_sigma.cuh"
 
@@ -103,7 +104,7 @@ constexpr int kPoolFlush = 32;
 
 template <typename A>
 __global__ void __launch_bounds__(kThreads) k_pool_grad_l(const A *__restrict__ CL, const uint32_t *__restrict__ lists,
-                                                          const int4 *__restrict__ info, int Da,
+                                                          const int4 *__restrict__ info, int Da, int Db,
                                                           double *__restrict__ out) {
     using R = real_of<A>;
     __shared__ double red[kThreads / 32];
@@ -128,6 +129,10 @@ __global__ void __launch_bounds__(kThreads) k_pool_grad_l(const A *__restrict__ 
                     I[v] = (size_t)(eb & 0x7FFFu) * Da + (ea & 0x7FFFu);
                     J[v] = (size_t)(eb >> 16) * Da + (ea >> 16);
                     neg[v] = (ea ^ eb) & 0x8000u;
+                    if (!(SV_IN_RANGE(I[v], (size_t)Da * Db, kChkPair) && SV_IN_RANGE(J[v], (size_t)Da * Db, kChkPair))) {
+                        ok[v] = false;  // checked build: skip the pair
+                        I[v] = J[v] = 0;
+                    }
                     r += dr;
                     i += di;
                     if (i >= na) {
@@ -193,11 +198,14 @@ cudaError_t launch_interleave(const void *C, const void *L, int dtype, void *CL,
 
 // info: n_ops int4 records (alpha offset, alpha length, beta offset, beta length) into lists.
 cudaError_t launch_pool_grad_l(const void *CL, int dtype, const uint32_t *lists, const int *info, int n_ops, int Da,
-                               double *out, cudaStream_t st) {
+                               int Db, double *out, cudaStream_t st) {
     if (n_ops <= 0) return cudaSuccess;
     SV_DISPATCH_AMP(dtype, k_pool_grad_l<A><<<n_ops, kThreads, 0, st>>>((const A *)CL, lists, (const int4 *)info, Da,
-                                                                         out));
+                                                                         Db, out));
     return cudaGetLastError();
 }
+
+// This unit's check word (checked build), for sv_check_status.
+SV_CHECK_READER(check_word_pool)
 
 }  // namespace svk

@@ -46,7 +46,7 @@ cudaError_t launch_pool_grad(const void *C, const void *L, int dtype, const void
 cudaError_t launch_interleave(const void *C, const void *L, int dtype, void *CL, size_t count, int sm_count,
                               cudaStream_t st);
 cudaError_t launch_pool_grad_l(const void *CL, int dtype, const uint32_t *lists, const int *info, int n_ops, int Da,
-                               double *out, cudaStream_t st);
+                               int Db, double *out, cudaStream_t st);
 cudaError_t launch_rdm_gather(const void *psi, int dtype, const uint32_t *sector, uint64_t count,
                               const void *elems, int n_el, int grid, double *partial, cudaStream_t st);
 // sector storage (k_sector.cu)
@@ -123,6 +123,7 @@ void set_thread_error(const std::string &m) { g_err = m; }
 uint32_t check_word_sector();
 uint32_t check_word_rows();
 uint32_t check_word_abtc();
+uint32_t check_word_pool();
 }  // namespace svk
 
 static sv_status fail(sv_handle h, sv_status st, const std::string &msg) {
@@ -1371,8 +1372,9 @@ extern "C" {
 const char *sv_version(void) { return "sv-gb300 0.1 (sm_103a)"; }
 
 uint32_t sv_check_status(void) {
-    const uint32_t a = check_word_sector(), b = check_word_rows(), c = check_word_abtc();
-    return (a & 0xFFu) | ((b & 0xFFu) << 8) | ((c & 0xFFu) << 16) | ((a | b | c) & 0x80000000u);
+    const uint32_t a = check_word_sector(), b = check_word_rows(), c = check_word_abtc(), d = check_word_pool();
+    return (a & 0xFFu) | ((b & 0xFFu) << 8) | ((c & 0xFFu) << 16) | ((d & 0x0Fu) << 24) |
+           ((a | b | c | d) & 0x80000000u);
 }
 
 const char *sv_last_error(sv_handle h) { return h ? h->err.c_str() : g_err.c_str(); }
@@ -1958,7 +1960,7 @@ sv_status sv_pool_gradients(sv_handle h, sv_ham_handle ham, const sv_excitation 
         SV_CUDA(h, launch_interleave(Cm, h->Lbuf, h->dtype, h->CLbuf, (size_t)h->Da * h->Db, h->sm_count,
                                      h->stream));
         SV_CUDA(h, launch_pool_grad_l(h->CLbuf, h->dtype, (const uint32_t *)h->pool_lists.buf, h->pool_lists.dinfo,
-                                      n_pool, h->Da, h->dout + 2, h->stream));
+                                      n_pool, h->Da, h->Db, h->dout + 2, h->stream));
         h->launches += 2;
     } else if (n_pool > 0) {
         void *d_ops = h->partials + 3 * (size_t)h->Db;

@@ -1,6 +1,6 @@
 """The checked build on the GPU (libsv_gb300_check.so, every kernel source compiled with
-SV_CHECK=1): the sector sweeps, the 1-RDM rows and the tensor-core expectation (variant 5:
-gather tables, plane offsets) run through it in a separate process, match the oracle, and
+SV_CHECK=1): the sector sweeps, the 1-RDM rows, pool screening and the tensor-core
+expectation (variant 5: gather tables, plane offsets) run through it in a separate process, match the oracle, and
 record no out-of-range index (sv_check_status() == 0)."""
 import os
 import subprocess
@@ -29,7 +29,12 @@ CODE = textwrap.dedent("""
     psi0 = A.hf_state(sec, p["occ"])
     theta = p["theta"] * 5
     Eref, gref = A.energy_grad(sec, p["h"], p["eri"], p["e_nuc"], p["ops"], theta, psi0)
-    rdm_ref = A.rdm1(sec, A.apply_ansatz(sec, p["ops"], theta, psi0))
+    psi = A.apply_ansatz(sec, p["ops"], theta, psi0)
+    rdm_ref = A.rdm1(sec, psi)
+    pool = inputs.uccsd_pool(n, 6)[::7]
+    sig = A.hamiltonian_apply(sec, p["h"], p["eri"], p["e_nuc"], psi)
+    nrm = np.vdot(psi, psi).real
+    pref = np.array([2 * np.vdot(sig, A.generator_apply(sec, op, psi)).real / nrm for op in pool])
     ham = sv.Hamiltonian(p["h"], p["eri"], p["e_nuc"])
     for variant in (5, 3):
         st = sv.StateVector(n, "c64", sector=(na, nb))
@@ -38,6 +43,8 @@ CODE = textwrap.dedent("""
         E, g = st.energy_grad(ham, p["ops"], theta)
         assert abs(E - Eref) <= 1e-5 and np.max(np.abs(g - gref)) <= 1e-5, (variant, E, Eref)
         assert np.max(np.abs(st.rdm1() - rdm_ref)) <= 2e-6, variant
+        _, pg = st.pool_gradients(ham, pool)
+        assert np.max(np.abs(pg - pref)) <= 1e-5, variant
         st.close()
     status = sv.sv_check_status()
     assert status == 0, hex(status)
